@@ -1,0 +1,210 @@
+"""Pins of the oracle's modal DG right-hand side (Eq. 1), projection
+(Algorithm 1) and LSERK(5,4) time stepping (Sec. 2).
+
+  * free-stream preservation: a constant state has zero residual;
+  * discrete conservation on periodic meshes: sum_e int R_e = 0;
+  * projection reproduces any state in the modal space exactly;
+  * Algorithm 1 cross-check: the nodal collocated residual on the collapsed
+    Gauss-Legendre grid (Lagrange test functions), mapped with V^T, equals the
+    modal residual -- a second, independent route to the volume and face terms;
+  * LSERK(5,4): stability polynomial 1 + z + z^2/2 + z^3/6 + z^4/24 + c5 z^5
+    (tests/golden/lserk54_stability.txt) and fourth order on y' = lambda y;
+  * L2 convergence of order about N+1 on an advected density wave.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import dg_inputs as di
+from oracle.dg import LSERK_A, LSERK_B, Oracle
+from oracle.elements import collapse, eval_basis
+from oracle.euler import physical_flux, riemann
+from oracle.mesh import from_box
+from oracle.quadrature import gauss_legendre, volume_rule
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make(kind, m, N, seed=1, flux="lf"):
+    return Oracle(from_box(di.box_mesh(m, kind, seed=seed), N), flux=flux)
+
+
+def const_state(o, U0):
+    return o.project(lambda x: np.tile(np.asarray(U0)[:, None], (1, x.shape[0])))
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("kuhn", 2, 3), ("hex", 2, 4), ("mixed", 2, 4)])
+@pytest.mark.parametrize("flux", ["lf", "roe"])
+def test_free_stream(kind, m, N, flux):
+    o = make(kind, m, N, flux=flux)
+    U0 = np.array([1.2, 0.3, -0.2, 0.1, 3.0])
+    Q = const_state(o, U0)
+    # the projected constant has only the first mode nonzero in each block
+    for e in range(o.mesh.n_elems):
+        assert np.abs(o.mesh.block(Q, e)[:, 1:]).max() < 1e-13 * np.abs(Q).max()
+    worst = 0.0
+    for e in range(o.mesh.n_elems):
+        vol = o.volume_term(Q, e)
+        r = vol - o.surface_term(Q, e)
+        worst = max(worst, np.abs(r).max() / np.abs(vol).max())
+    assert worst < 1e-13
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("kuhn", 2, 2), ("mixed", 2, 4)])
+@pytest.mark.parametrize("flux", ["lf", "roe"])
+def test_conservation(kind, m, N, flux):
+    o = make(kind, m, N, flux=flux)
+    Q = o.project(di.tgv_state)
+    R = o.rhs(Q)
+    tot = sum(o.integrate(R, e) for e in range(o.mesh.n_elems))
+    scale = max(np.abs(o.integrate(np.abs(R), e)).max() for e in range(o.mesh.n_elems))
+    assert np.abs(tot).max() < 1e-13 * scale * o.mesh.n_elems
+
+
+def test_projection_reproduces_space():
+    o = make("mixed", 2, 3)
+    rng = np.random.default_rng(0)
+    Q = rng.uniform(-1, 1, o.mesh.n_dof())
+
+    # project the values of the expansion itself, element by element
+    Q2 = np.zeros_like(Q)
+    for e in range(o.mesh.n_elems):
+        op = o.ops[o.mesh.etype[e]]
+        q = o.mesh.block(Q, e) @ op.V.T
+        r = o.mesh.J[e] * (q * op.w) @ op.V
+        Q2[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
+    assert np.abs(Q2 - Q).max() < 1e-13
+
+
+def lagrange(nodes, x):
+    """Lagrange basis l_i(x) and l_i'(x) on nodes; x [k] -> [k, n]."""
+    x = np.asarray(x, dtype=float)[:, None]
+    n = len(nodes)
+    L = np.ones((x.shape[0], n))
+    dL = np.zeros((x.shape[0], n))
+    for i in range(n):
+        for j in range(n):
+            if j == i:
+                continue
+            term = (x[:, 0] - nodes[j]) / (nodes[i] - nodes[j])
+            # product rule for the derivative
+            dL[:, i] = dL[:, i] * term + L[:, i] / (nodes[i] - nodes[j])
+            L[:, i] = L[:, i] * term
+    return L, dL
+
+
+def nodal_residual(o, Q, e):
+    """Residual of Eq. 1 tested with the tensor Lagrange functions of the
+    collapsed GL grid (the nodal form of Algorithm 1), mapped back by V^T."""
+    m = o.mesh
+    t, N = m.etype[e], m.N
+    x, _ = gauss_legendre(N + 1)
+    op = o.ops[t]
+    a, b, c = collapse(t, *op.pts.T)
+    La, dLa = lagrange(x, a)
+    Lb, dLb = lagrange(x, b)
+    Lc, dLc = lagrange(x, c)
+    n = N + 1
+    ell = np.einsum("qi,qj,qk->qijk", La, Lb, Lc).reshape(len(a), n ** 3)
+    dabc = np.stack([np.einsum("qi,qj,qk->qijk", dLa, Lb, Lc),
+                     np.einsum("qi,qj,qk->qijk", La, dLb, Lc),
+                     np.einsum("qi,qj,qk->qijk", La, Lb, dLc)]).reshape(3, len(a), n ** 3)
+    from oracle.elements import collapse_jacobian
+    Jc = collapse_jacobian(t, a, b, c)
+    gxi = np.linalg.solve(np.transpose(Jc, (0, 2, 1)), np.transpose(dabc, (1, 0, 2)))  # [q, 3, m]
+    gx = np.einsum("kd,qkm->dqm", m.dxi_dx[e], gxi)
+    U = m.block(Q, e) @ op.V.T
+    F = physical_flux(U, o.gamma)
+    vol = m.J[e] * np.einsum("dqm,dvq->vm", gx, op.w * F)
+    surf = np.zeros_like(vol)
+    for f, side in m.elem_faces[e]:
+        e0, _, e1, _ = m.faces[f]
+        ref0, ref1, wS, nrm = m.face_geometry(f)
+        UL = m.block(Q, e0) @ eval_basis(m.etype[e0], N, ref0).T
+        UR = m.block(Q, e1) @ eval_basis(m.etype[e1], N, ref1).T
+        Fh = wS * riemann(o.flux, UL, UR, nrm, o.gamma)
+        ref = ref0 if side == 0 else ref1
+        fa, fb, fc = collapse(t, *ref.T)
+        ellf = np.einsum("pi,pj,pk->pijk", lagrange(x, fa)[0], lagrange(x, fb)[0],
+                         lagrange(x, fc)[0]).reshape(len(fa), n ** 3)
+        surf += (Fh @ ellf) if side == 0 else -(Fh @ ellf)
+    # nodal values of the modal basis at the grid: phi_i = sum_m phi_i(x_m) l_m
+    return (vol - surf) @ op.V
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 2, 3), ("kuhn", 2, 2), ("mixed", 3, 2)])
+def test_algorithm1_nodal_equivalence(kind, m, N):
+    o = make(kind, m, N)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
+    for e in range(0, o.mesh.n_elems, 3):
+        modal = o.volume_term(Q, e) - o.surface_term(Q, e)
+        nodal = nodal_residual(o, Q, e)
+        assert np.abs(modal - nodal).max() < 1e-12 * np.abs(modal).max()
+
+
+def lserk_scalar(z):
+    y, k = 1.0 + 0j, 0.0 + 0j
+    for s in range(5):
+        k = LSERK_A[s] * k + z * y
+        y = y + LSERK_B[s] * k
+    return y
+
+
+def test_lserk_stability_polynomial():
+    zs = np.exp(2j * np.pi * np.arange(12) / 12) * 0.5
+    vals = np.array([lserk_scalar(z) for z in zs])
+    V = np.vander(zs, 6, increasing=True)
+    coef = np.linalg.lstsq(V, vals, rcond=None)[0].real
+    golden = np.loadtxt(os.path.join(GOLDEN, "lserk54_stability.txt"))
+    assert np.abs(coef[:5] - golden).max() < 1e-12
+    assert abs(coef[5]) > 1e-4  # a genuine fifth stage term
+
+
+def test_lserk_fourth_order():
+    lam = -1.0 + 2.0j
+    errs = []
+    for nsteps in (20, 40, 80):
+        dt = 1.0 / nsteps
+        y = 1.0 + 0j
+        for _ in range(nsteps):
+            y = lserk_scalar(lam * dt) * y
+        errs.append(abs(y - np.exp(lam)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.8) and np.all(rates < 4.3)
+
+
+def l2_density_error(o, Q, t):
+    """L2 error of the density, measured with a finer rule (N+4 points per
+    direction) than the one the scheme uses."""
+    err = 0.0
+    rules = {}
+    for e in range(o.mesh.n_elems):
+        et = o.mesh.etype[e]
+        if et not in rules:
+            pts, w = volume_rule(et, o.mesh.N + 3)
+            rules[et] = (pts, w, eval_basis(et, o.mesh.N, pts))
+        pts, w, V = rules[et]
+        rho_h = (o.mesh.block(Q, e) @ V.T)[0]
+        rho = di.advected_density_state(o.mesh.to_physical(e, pts), t=t)[0]
+        err += o.mesh.J[e] * (w @ (rho_h - rho) ** 2)
+    return math.sqrt(err)
+
+
+@pytest.mark.parametrize("kind,N,margin", [("hex", 3, 0.4), ("prism", 3, 0.4), ("pyramid", 3, 0.4),
+                                           ("kuhn", 3, 0.4), ("hex", 2, 0.4), ("pyramid", 2, 0.4),
+                                           ("mixed", 3, 0.0)])
+def test_convergence_order(kind, N, margin):
+    """Density error after 5 LSERK steps on 2^3 and 4^3 cube meshes; the
+    coarse pair is slightly pre-asymptotic, so the bar is rate > N + margin
+    (measured: 3.5-3.9 at N = 3 for single-type meshes)."""
+    T, errs = 0.1, []
+    for m in (2, 4):
+        o = make(kind, m, N)
+        Q = o.project(di.advected_density_state)
+        nsteps = 5
+        Q = o.run(Q, T / nsteps, nsteps)
+        errs.append(l2_density_error(o, Q, T))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > N + margin, (errs, rate)
