@@ -157,6 +157,69 @@ def box_mesh(m: int, kind: str = "mixed", seed: int = 1, p_prism: float = 0.5,
                    period=np.array([length] * 3), m=m, kind=kind, seed=seed)
 
 
+
+# Vertex reorderings that map each reference element onto itself (so the
+# element stays an affine image of its reference element, possibly with the
+# opposite orientation).  hex: the 48 symmetries of the cube act on the 3
+# vertex bits (axis permutation + per-axis flip); prism: the 6 symmetries of
+# the triangle (top follows bottom); pyramid: the 8 symmetries of the base
+# square (apex last); tet: all 24 vertex permutations.
+def _hex_syms():
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for flip in range(8):
+            m = []
+            for b in range(8):
+                bits = [(b >> k) & 1 for k in range(3)]
+                nb = [bits[perm[k]] ^ ((flip >> k) & 1) for k in range(3)]
+                m.append(nb[0] | (nb[1] << 1) | (nb[2] << 2))
+            out.append(m)
+    return out
+
+
+def _prism_syms():
+    import itertools
+    return [list(p) + [q + 3 for q in p] for p in itertools.permutations(range(3))]
+
+
+def _pyr_syms():
+    out = []
+    for sw in (0, 1):
+        for fx in (0, 1):
+            for fy in (0, 1):
+                m = []
+                for b in range(4):
+                    x, y = b & 1, b >> 1
+                    if sw:
+                        x, y = y, x
+                    x ^= fx
+                    y ^= fy
+                    m.append(x | (y << 1))
+                out.append(m + [4])
+    return out
+
+
+def _tet_syms():
+    import itertools
+    return [list(p) for p in itertools.permutations(range(4))]
+
+
+def reorder_vertices(box: BoxMesh, seed: int) -> BoxMesh:
+    """Apply a seeded random self-map of the reference element to every
+    element's vertex list (exercises every face orientation case)."""
+    syms = {HEX: _hex_syms(), PRISM: _prism_syms(), PYR: _pyr_syms(), TET: _tet_syms()}
+    rng = np.random.Generator(np.random.PCG64(seed))
+    verts = box.elem_verts.copy()
+    for e in range(box.n_elems):
+        lo, hi = box.elem_vert_off[e], box.elem_vert_off[e + 1]
+        opts = syms[int(box.etype[e])]
+        m = opts[rng.integers(len(opts))]
+        verts[lo:hi] = box.elem_verts[lo:hi][m]
+    return BoxMesh(xyz=box.xyz, etype=box.etype, elem_vert_off=box.elem_vert_off, elem_verts=verts,
+                   period=box.period, m=box.m, kind=box.kind + "+reordered", seed=box.seed)
+
+
 # --------------------------------------------------------------------------
 # Pointwise initial states (conservative variables rho, rho u, rho v, rho w, E)
 # --------------------------------------------------------------------------

@@ -1,0 +1,193 @@
+/*
+ * dg.h - C ABI of the GB300 modal DG hot-path library (libdg.so).
+ *
+ * The library evaluates the right-hand side of the modal discontinuous
+ * Galerkin discretisation of the compressible Euler equations on periodic
+ * affine meshes that mix hexahedra, prisms, pyramids and tetrahedra, and
+ * advances it with a low-storage Runge-Kutta scheme, as described in
+ * "In-Memory Load Balancing for Discontinuous Galerkin Methods on Polytopal
+ * Meshes" (Kopper, Schwarz, Keim, Beck):
+ *   - weak form: Sec. 2, Eq. 1 (volume integral, numerical surface flux);
+ *   - collapsed-coordinate (Duffy) quadrature on non-hex types: Sec. 2;
+ *   - modal time stepping and the projection M^{-1} V^T W J: Sec. 2,
+ *     Algorithm 1;
+ *   - LSERK time integration (method of lines): Sec. 2;
+ *   - space-filling-curve ordering and runtime-timer load balancing: Sec. 3,
+ *     Listing 1 (per-element cost attribution) and the imbalance trigger.
+ * The adjoint entry points (dg_rhs_vjp, dg_rk_vjp) have no counterpart in the
+ * paper; they are the exact transposes of dg_rhs and dg_rk_step.
+ *
+ * Everything is FP64.  All compute runs in CUDA kernels for sm_103a; there is
+ * no CPU fallback: without a usable CUDA device every call that computes
+ * returns DG_ERR_CUDA.
+ *
+ * Conventions shared by all calls
+ *   - Pointers named *_store are DEVICE pointers to FP64 arrays of n_dof
+ *     doubles in the library's storage layout (per element in Hilbert order,
+ *     5 blocks of nM modal coefficients: [slot][var][mode]).  They are owned
+ *     by the caller, must be 8-byte aligned, and must stay valid until the
+ *     work queued on the stream has finished.
+ *   - The external (caller) layout is the same [element][var][mode] blocks in
+ *     the caller's element order.  dg_set_state / dg_get_state are the only
+ *     permutations between the two.
+ *   - Modes are ordered lexicographically in (p, q, r), r fastest, over the
+ *     type's index set (hex p,q,r<=N; prism p+q<=N, r<=N; pyramid p,q<=N,
+ *     r<=N-max(p,q); tet p+q+r<=N).  Variables are (rho, rho u, rho v, rho w, E).
+ *   - Every computing call is asynchronous on the given stream (0 = legacy
+ *     default stream) and never synchronises the device, except
+ *     dg_mesh_create, dg_mesh_destroy, dg_sync and the host-pointer variants
+ *     of dg_set_state / dg_get_state.
+ *   - A call returns DG_OK or a negative dg_status; dg_last_error() gives a
+ *     thread-local message for the last failure.  Device-side conditions
+ *     (non-finite residual) are sticky in the mesh and reported by dg_sync.
+ *     No call aborts the process or throws across the ABI.
+ *   - A mesh object may be used from one host thread at a time.  Calls on the
+ *     same mesh that overlap on the GPU (different streams without ordering)
+ *     race on the library's workspace.
+ */
+#ifndef DG_H_
+#define DG_H_
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh; /* opaque, library-owned */
+
+typedef enum { DG_HEX = 0, DG_PRISM = 1, DG_PYR = 2, DG_TET = 3 } dg_elem_type;
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,         /* invalid argument (null pointer, size, enum)       */
+  DG_ERR_MESH = -2,        /* non-affine element, unmatched or ambiguous face   */
+  DG_ERR_CUDA = -3,        /* a CUDA runtime call failed (no device, launch...) */
+  DG_ERR_OOM = -4,         /* device or host allocation failed                  */
+  DG_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up           */
+  DG_ERR_NONFINITE = -6,   /* a residual or state entry was not finite          */
+  DG_ERR_UNSUPPORTED = -7  /* option outside what the build supports            */
+} dg_status;
+
+typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1 } dg_flux;
+typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1 } dg_scheduler;
+
+/* Mesh description, caller-owned, read only during dg_mesh_create.
+ * Elements are affine images of the reference elements; the local vertex
+ * order of element e (elem_verts[elem_vert_off[e] .. elem_vert_off[e+1]-1])
+ * follows the reference vertex order:
+ *   hex     (-1,-1,-1) (1,-1,-1) (-1,1,-1) (1,1,-1) then the same at zeta=+1
+ *   prism   (-1,-1,-1) (1,-1,-1) (-1,1,-1) then the same at zeta=+1
+ *   pyramid (-1,-1,-1) (1,-1,-1) (-1,1,-1) (1,1,-1) apex (-1,-1,1)
+ *   tet     (-1,-1,-1) (1,-1,-1) (-1,1,-1) (-1,-1,1)
+ * Faces are matched by their vertex positions reduced modulo `period`
+ * (periodic in all three directions); every face must have exactly one
+ * partner, and the vertices of one face must be distinct modulo the period. */
+typedef struct {
+  int64_t n_vertices;
+  const double* xyz;            /* host [n_vertices][3]                          */
+  int64_t n_elems;
+  const int8_t* type;           /* host [n_elems], dg_elem_type                   */
+  const int64_t* elem_vert_off; /* host [n_elems + 1], CSR offsets                */
+  const int64_t* elem_verts;    /* host [elem_vert_off[n_elems]] vertex ids       */
+  const double* period;         /* host [3] box lengths; required (non-NULL)      */
+  int N;                        /* polynomial degree, 1 <= N <= DG_MAX_N          */
+  int flux;                     /* dg_flux                                        */
+  double gamma;                 /* ratio of specific heats (1.4)                  */
+  int scheduler;                /* dg_scheduler                                   */
+  double imbalance_threshold;   /* rebalance when max/mean SM load - 1 exceeds it */
+} dg_mesh_desc;
+
+#define DG_MAX_N 6
+
+/* Build the mesh: reference tables per (type, N), affine metrics, face
+ * connectivity with the owner rule (owner = smaller caller index; flux and
+ * face points on the owner's side), Hilbert ordering of element centroids,
+ * and the device workspace.  Synchronises `stream`.  *out receives a handle
+ * to free with dg_mesh_destroy. */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out);
+dg_status dg_mesh_destroy(dg_mesh* mesh);
+
+/* Host-only validation of a mesh description: runs the same set-up as
+ * dg_mesh_create without touching a GPU.  counts (host, [8], may be NULL):
+ * n_elems, n_faces, hex, prism, pyramid, tet counts, number of distinct
+ * index-permutation face maps, number of interpolating face maps.
+ * quad_xyz (host, [n_elems * (N+1)^3][3], may be NULL) receives the physical
+ * volume quadrature points in caller order (as dg_quad_points).
+ * slot_of_elem (host, [n_elems], may be NULL) receives the Hilbert slots. */
+dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_xyz, int64_t* slot_of_elem);
+
+/* n_dof = 5 * sum_e nM(type_e, N).  slot_of_elem (host, [n_elems], may be
+ * NULL) receives the Hilbert slot of every caller element.  counts (host,
+ * [6], may be NULL) receives n_elems, n_faces, and the number of hex, prism,
+ * pyramid and tet elements. */
+dg_status dg_mesh_layout(const dg_mesh* mesh, int64_t* n_dof, int64_t* slot_of_elem, int64_t* counts);
+
+/* Copy a state between the caller layout Q_ext and the storage layout.
+ * is_device = 1: Q_ext is a device pointer and the call is asynchronous;
+ * is_device = 0: Q_ext is host memory (pinned or pageable) and the call
+ * synchronises `stream` before returning. */
+dg_status dg_set_state(dg_mesh* mesh, const double* Q_ext, int is_device, double* Q_store, cudaStream_t stream);
+dg_status dg_get_state(const dg_mesh* mesh, const double* Q_store, double* Q_ext, int is_device, cudaStream_t stream);
+
+/* Physical volume quadrature points (collapsed Gauss-Legendre, n^3 per element,
+ * n = N+1), caller element order: host [n_elems * n^3][3].  Host-only. */
+dg_status dg_quad_points(const dg_mesh* mesh, double* xyz_out);
+
+/* Algorithm 1 projection Q = M^{-1} V^T W J q of point values q (device,
+ * caller order, [n_elems][5][n^3] at the points of dg_quad_points) onto the
+ * modal space, written to Q_store.  Asynchronous. */
+dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cudaStream_t stream);
+
+/* R = M^{-1}(vol - surf) of Eq. 1 for the state Q_store; R_store (device,
+ * storage layout) is overwritten.  Asynchronous. */
+dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStream_t stream);
+
+/* nsteps LSERK(5,4) steps (Carpenter-Kennedy 2N storage) of size dt, in
+ * place on Q_store; K_store is the second register (its input value is
+ * ignored, K = 0 at every step start).  The stage loop is replayed from a
+ * captured CUDA graph.  Asynchronous. */
+dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps, cudaStream_t stream);
+
+/* Qbar = (dR/dQ)^T Rbar at Q_store (all device, storage layout); Qbar is
+ * overwritten.  No counterpart in the paper.  Asynchronous. */
+dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream);
+
+/* Q0bar = (dQ_K/dQ_0)^T QKbar for nsteps LSERK steps of size dt from Q0_store.
+ * Stage states are recomputed from checkpoints of Q stored every ckpt_every
+ * steps in library memory.  No counterpart in the paper.  Asynchronous. */
+dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
+                    const double* QKbar, double* Q0bar, cudaStream_t stream);
+
+/* Scheduler of the element kernels: DG_SCHED_BALANCED (one persistent launch
+ * per phase, warps take weighted Hilbert-contiguous element chunks from an
+ * atomic queue) or DG_SCHED_NAIVE (one launch per element type and phase,
+ * caller element order).  Results are bitwise identical. */
+dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler);
+
+/* Per-type element cost measured in the balanced kernels with %globaltimer
+ * (Listing 1's per-element attribution, done per element in-kernel):
+ * host [4] mean ns per element of each type (0 if none measured) and the
+ * current per-SM load imbalance (max/mean - 1).  Synchronises `stream`. */
+dg_status dg_cost_table(dg_mesh* mesh, double* ns_per_elem, double* imbalance, cudaStream_t stream);
+
+/* Rebuild the weighted chunk table from the measured costs when the measured
+ * imbalance exceeds the threshold (or always, if force != 0); resets the
+ * counters.  *rebuilt (may be NULL) tells whether it did.  Synchronises. */
+dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stream);
+
+/* Synchronise `stream` and report sticky device errors (DG_ERR_NONFINITE). */
+dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream);
+
+/* Thread-local description of the last error. */
+const char* dg_last_error(void);
+
+/* Measured FP64 throughput of this device (DFMA chains and mma.sync f64
+ * m8n8k4), TFLOP/s, from a ~50 ms probe launch.  Synchronises. */
+dg_status dg_probe_fp64_peak(double* dfma_tflops, double* dmma_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H_ */

@@ -22,7 +22,6 @@ paper (parity unpinned against the paper's own solver).
 from __future__ import annotations
 
 import numpy as np
-from scipy.special import eval_jacobi
 
 HEX, PRISM, PYR, TET = 0, 1, 2, 3
 NAMES = ("hex", "prism", "pyramid", "tet")
@@ -136,16 +135,35 @@ def collapse_jacobian(etype, a, b, c):
 
 # ---------------------------------------------------------------- 1D factors
 
+def jacobi(n, alpha, beta, x):
+    """Jacobi polynomial P_n^(alpha,beta)(x) by its three-term recurrence
+    (Abramowitz & Stegun 22.7.1); accurate to a few ulps on [-1, 1], unlike
+    hypergeometric-series evaluation for large alpha."""
+    x = np.asarray(x, dtype=float)
+    p0 = np.ones_like(x)
+    if n == 0:
+        return p0
+    a, b = float(alpha), float(beta)
+    p1 = 0.5 * (a - b + (a + b + 2.0) * x)
+    for k in range(2, n + 1):
+        s = 2.0 * k + a + b
+        c1 = 2.0 * k * (k + a + b) * (s - 2.0)
+        c2 = (s - 1.0) * (s * (s - 2.0) * x + a * a - b * b)
+        c3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * s
+        p0, p1 = p1, (c2 * p1 - c3 * p0) / c1
+    return p1
+
+
 def jhat(n, alpha, x):
     """Jacobi P_n^(alpha,0) normalised: int ((1-x)/2)^alpha jhat^2 dx = 1."""
-    return eval_jacobi(n, alpha, 0.0, x) * np.sqrt((2 * n + alpha + 1) / 2.0)
+    return jacobi(n, alpha, 0.0, x) * np.sqrt((2 * n + alpha + 1) / 2.0)
 
 
 def jhat_d(n, alpha, x):
     """Derivative of jhat: d/dx P_n^(a,b) = (n+a+b+1)/2 P_{n-1}^(a+1,b+1)."""
     if n == 0:
         return np.zeros_like(np.asarray(x, dtype=float))
-    return 0.5 * (n + alpha + 1) * eval_jacobi(n - 1, alpha + 1, 1.0, x) * np.sqrt((2 * n + alpha + 1) / 2.0)
+    return 0.5 * (n + alpha + 1) * jacobi(n - 1, alpha + 1, 1.0, x) * np.sqrt((2 * n + alpha + 1) / 2.0)
 
 
 def _warped(k, n, alpha, x):

@@ -25,6 +25,14 @@ from .quadrature import face_rule
 QUANT = float(1 << 24)
 
 
+def _corner(ref_verts, point):
+    """Index of the reference vertex at `point`."""
+    hit = np.where(np.all(np.abs(ref_verts - point) < 1e-12, axis=1))[0]
+    if hit.size != 1:
+        raise ValueError("reference vertex not found")
+    return int(hit[0])
+
+
 class OracleMesh:
     def __init__(self, xyz, etype, elem_vert_off, elem_verts, period, N):
         self.xyz = np.asarray(xyz, dtype=float)
@@ -55,8 +63,15 @@ class OracleMesh:
             scale = np.abs(X - X.mean(0)).max()
             if np.abs(resid).max() > 1e-10 * scale:
                 raise ValueError(f"element {e} is not an affine image of its reference element")
-            self.X0[e] = sol[0]
-            self.A[e] = sol[1:].T           # columns = images of the reference axes
+            # The map is affine, so it is fixed exactly by the vertex at the
+            # reference origin corner and the vertices one reference edge away
+            # along each axis; exact vertex differences avoid the fit's rounding.
+            o = _corner(R, -np.ones(3))
+            self.X0[e] = X[o]
+            for k in range(3):
+                tip = -np.ones(3)
+                tip[k] = 1.0
+                self.A[e][:, k] = X[_corner(R, tip)] - X[o]
         det = np.linalg.det(self.A)
         if np.any(np.abs(det) < 1e-300):
             raise ValueError("degenerate element")
@@ -124,7 +139,11 @@ class OracleMesh:
         if self.period is not None:
             d = self.face_centroid(e0, l0) - self.face_centroid(e1, l1)
             shift = np.rint(d / self.period) * self.period
-        ref1 = self.to_reference(e1, x - shift)
+        # invert the neighbour's map at the same physical points, measured from
+        # the neighbour's origin vertex (local differences keep the rounding of
+        # absolute coordinates and of the periodic shift out of the result)
+        x_rel = (self.X0[e0] - shift - self.X0[e1]) + 0.5 * (ref0 + 1.0) @ self.A[e0].T
+        ref1 = 2.0 * np.linalg.solve(self.A[e1], x_rel.T).T - 1.0
         return ref0, ref1, w * S, nrm
 
     def n_dof(self):

@@ -1,0 +1,261 @@
+"""GB300 modal DG hot path: thin Python binding of libdg.so (include/dg.h).
+
+Every function here only marshals arguments to the C ABI; all compute runs in
+the library's CUDA kernels.  Importing the package loads the in-tree
+libdg.so; if it is missing or cannot be loaded the import raises (there is
+no CPU path).  Device buffers are torch tensors (float64, CUDA); torch is used
+for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB, build as _build
+
+__all__ = ["lib", "DGError", "Mesh", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "load"]
+
+FLUX = {"lf": 0, "roe": 1}
+SCHED = {"balanced": 0, "naive": 1}
+STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_OOM",
+          -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_UNSUPPORTED"}
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("xyz", ctypes.c_void_p),
+                ("n_elems", ctypes.c_int64), ("type", ctypes.c_void_p),
+                ("elem_vert_off", ctypes.c_void_p), ("elem_verts", ctypes.c_void_p),
+                ("period", ctypes.c_void_p), ("N", ctypes.c_int), ("flux", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("scheduler", ctypes.c_int),
+                ("imbalance_threshold", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_DP = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "dg_mesh_create": [ctypes.POINTER(MeshDesc), _P, ctypes.POINTER(_P)],
+    "dg_mesh_destroy": [_P],
+    "dg_mesh_check": [ctypes.POINTER(MeshDesc), _P, _P, _P],
+    "dg_mesh_layout": [_P, _P, _P, _P],
+    "dg_set_state": [_P, _P, ctypes.c_int, _P, _P],
+    "dg_get_state": [_P, _P, _P, ctypes.c_int, _P],
+    "dg_quad_points": [_P, _P],
+    "dg_project": [_P, _P, _P, _P],
+    "dg_rhs": [_P, _P, _P, _P],
+    "dg_rk_step": [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P],
+    "dg_rhs_vjp": [_P, _P, _P, _P, _P],
+    "dg_rk_vjp": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
+    "dg_set_scheduler": [_P, ctypes.c_int],
+    "dg_cost_table": [_P, _P, _P, _P],
+    "dg_rebalance": [_P, ctypes.c_int, _P, _P],
+    "dg_sync": [_P, _P],
+    "dg_probe_fp64_peak": [_P, _P],
+}
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the in-tree libdg.so (building it first when absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        if not build_if_missing:
+            raise OSError(f"{LIB} is missing; run paper_2511_08020_gb300.build.build()")
+        _build()
+    lib = ctypes.CDLL(LIB)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.dg_last_error.argtypes = []
+    lib.dg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def lib() -> ctypes.CDLL:
+    return load()
+
+
+def _check(status):
+    if status != 0:
+        raise DGError(status, load().dg_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _desc(box_or_arrays, N, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1):
+    import numpy as np
+    b = box_or_arrays
+    keep = dict(xyz=np.ascontiguousarray(b.xyz, dtype=np.float64),
+                etype=np.ascontiguousarray(b.etype, dtype=np.int8),
+                off=np.ascontiguousarray(b.elem_vert_off, dtype=np.int64),
+                verts=np.ascontiguousarray(b.elem_verts, dtype=np.int64),
+                period=np.ascontiguousarray(b.period, dtype=np.float64))
+    d = MeshDesc(keep["xyz"].shape[0], keep["xyz"].ctypes.data, keep["etype"].shape[0], keep["etype"].ctypes.data,
+                 keep["off"].ctypes.data, keep["verts"].ctypes.data, keep["period"].ctypes.data, int(N),
+                 FLUX[flux] if isinstance(flux, str) else int(flux), float(gamma),
+                 SCHED[scheduler] if isinstance(scheduler, str) else int(scheduler), float(imbalance_threshold))
+    return d, keep
+
+
+def check_mesh(box, N):
+    """dg_mesh_check: host-only set-up; returns (counts[8], quad points [E*n^3, 3], slot_of_elem)."""
+    import numpy as np
+    d, keep = _desc(box, N)
+    n = N + 1
+    counts = np.zeros(8, dtype=np.int64)
+    qp = np.zeros((len(keep["etype"]) * n ** 3, 3))
+    slots = np.zeros(len(keep["etype"]), dtype=np.int64)
+    _check(load().dg_mesh_check(ctypes.byref(d), _ptr(counts), _ptr(qp), _ptr(slots)))
+    return counts, qp, slots
+
+
+def probe_fp64_peak():
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().dg_probe_fp64_peak(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+class Mesh:
+    """Owns a dg_mesh handle.  State tensors are float64 CUDA tensors of n_dof
+    entries in the storage layout (see dg_set_state / dg_get_state)."""
+
+    def __init__(self, box, N, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None):
+        import numpy as np
+        self.N = int(N)
+        self.flux = flux
+        d, keep = _desc(box, N, flux, gamma, scheduler, imbalance_threshold)
+        h = ctypes.c_void_p()
+        _check(load().dg_mesh_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        n_dof = ctypes.c_int64()
+        self.slot_of_elem = np.zeros(len(keep["etype"]), dtype=np.int64)
+        counts = np.zeros(6, dtype=np.int64)
+        _check(load().dg_mesh_layout(h, ctypes.byref(n_dof), _ptr(self.slot_of_elem), _ptr(counts)))
+        self.n_dof = n_dof.value
+        self.n_elems, self.n_faces = int(counts[0]), int(counts[1])
+        self.type_counts = counts[2:].tolist()
+        self.etype = keep["etype"].copy()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _check(load().dg_mesh_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- state
+    def empty(self):
+        import torch
+        return torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+
+    def set_state(self, Q_ext, Q_store=None, stream=None):
+        """Q_ext: CUDA tensor or host (numpy / CPU tensor) in caller layout."""
+        import numpy as np
+        import torch
+        if Q_store is None:
+            Q_store = self.empty()
+        if isinstance(Q_ext, torch.Tensor) and Q_ext.is_cuda:
+            _check(load().dg_set_state(self.handle, _ptr(Q_ext), 1, _ptr(Q_store), _stream(stream)))
+        else:
+            a = Q_ext.numpy() if isinstance(Q_ext, torch.Tensor) else np.ascontiguousarray(Q_ext, dtype=np.float64)
+            _check(load().dg_set_state(self.handle, _ptr(a), 0, _ptr(Q_store), _stream(stream)))
+        return Q_store
+
+    def get_state(self, Q_store, out=None, stream=None):
+        """Caller-layout copy: into `out` (CUDA tensor or numpy array) or a new numpy array."""
+        import numpy as np
+        import torch
+        if out is None:
+            out = np.empty(self.n_dof)
+        if isinstance(out, torch.Tensor) and out.is_cuda:
+            _check(load().dg_get_state(self.handle, _ptr(Q_store), _ptr(out), 1, _stream(stream)))
+        else:
+            a = out.numpy() if isinstance(out, torch.Tensor) else out
+            _check(load().dg_get_state(self.handle, _ptr(Q_store), _ptr(a), 0, _stream(stream)))
+        return out
+
+    def quad_points(self):
+        import numpy as np
+        n = self.N + 1
+        xyz = np.zeros((self.n_elems * n ** 3, 3))
+        _check(load().dg_quad_points(self.handle, _ptr(xyz)))
+        return xyz
+
+    def project(self, q_points, Q_store=None, stream=None):
+        """Algorithm 1 projection of point values [n_elems, 5, n^3] (CUDA tensor)."""
+        if Q_store is None:
+            Q_store = self.empty()
+        _check(load().dg_project(self.handle, _ptr(q_points), _ptr(Q_store), _stream(stream)))
+        return Q_store
+
+    # ---------------------------------------------------------------- hot path
+    def rhs(self, Q_store, R_store=None, stream=None):
+        if R_store is None:
+            R_store = self.empty()
+        _check(load().dg_rhs(self.handle, _ptr(Q_store), _ptr(R_store), _stream(stream)))
+        return R_store
+
+    def rk_step(self, Q_store, K_store, dt, nsteps=1, stream=None):
+        _check(load().dg_rk_step(self.handle, _ptr(Q_store), _ptr(K_store), float(dt), int(nsteps), _stream(stream)))
+        return Q_store
+
+    def rhs_vjp(self, Q_store, Rbar, Qbar=None, stream=None):
+        if Qbar is None:
+            Qbar = self.empty()
+        _check(load().dg_rhs_vjp(self.handle, _ptr(Q_store), _ptr(Rbar), _ptr(Qbar), _stream(stream)))
+        return Qbar
+
+    def rk_vjp(self, Q0_store, dt, nsteps, ckpt_every, QKbar, Q0bar=None, stream=None):
+        if Q0bar is None:
+            Q0bar = self.empty()
+        _check(load().dg_rk_vjp(self.handle, _ptr(Q0_store), float(dt), int(nsteps), int(ckpt_every),
+                                _ptr(QKbar), _ptr(Q0bar), _stream(stream)))
+        return Q0bar
+
+    # ---------------------------------------------------------------- scheduler
+    def set_scheduler(self, kind):
+        _check(load().dg_set_scheduler(self.handle, SCHED[kind] if isinstance(kind, str) else int(kind)))
+
+    def cost_table(self, stream=None):
+        import numpy as np
+        ns = np.zeros(4)
+        imb = ctypes.c_double()
+        _check(load().dg_cost_table(self.handle, _ptr(ns), ctypes.byref(imb), _stream(stream)))
+        return ns, imb.value
+
+    def rebalance(self, force=False, stream=None):
+        r = ctypes.c_int()
+        _check(load().dg_rebalance(self.handle, int(bool(force)), ctypes.byref(r), _stream(stream)))
+        return bool(r.value)
+
+    def sync(self, stream=None):
+        _check(load().dg_sync(self.handle, _stream(stream)))

@@ -1,0 +1,480 @@
+// C ABI of the modal DG library (include/dg.h): mesh upload, launch
+// orchestration of the per-stage phases, CUDA-graph replay of the LSERK stage
+// loop, scheduler and cost table.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_host.h"
+#include "dg_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+dg_status fail(dg_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+dg_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(DG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients.
+const double kLsA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kLsB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * src.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+struct dg_mesh {
+  int device = 0;
+  dgh::HostMesh h;
+  int flux = 0;
+  double gamma = 1.4;
+  int scheduler = DG_SCHED_BALANCED;
+  double threshold = 0.1;
+  int nQmax = 0, wpb = 2, blocks_per_sm = 1, num_sms = 1;
+  // device data
+  double* d_dpool = nullptr;
+  int* d_ipool = nullptr;
+  dgk::TypeTab* d_tabs = nullptr;
+  int* d_slot_tab = nullptr;
+  int8_t* d_slot_type = nullptr;
+  int64_t *d_slot_qoff = nullptr, *d_slot_hoff = nullptr, *d_slot_ftoff = nullptr;
+  int64_t *d_elem_of_slot = nullptr, *d_elem_qoff = nullptr;
+  dgk::ElemGeo* d_geo = nullptr;
+  double* d_H = nullptr;
+  double* d_T = nullptr;
+  dgk::FaceRec* d_faces = nullptr;
+  dgk::FaceBlock* d_fblocks = nullptr;
+  int16_t* d_perms = nullptr;
+  double* d_dense = nullptr;
+  unsigned* d_status = nullptr;
+  unsigned long long* d_cost = nullptr;
+  unsigned long long* d_smns = nullptr;
+  unsigned* d_counters = nullptr;
+  int64_t* d_type_slots[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t* d_chunks = nullptr;
+  int64_t nchunks = 0;
+  double* d_stage = nullptr;
+  // graph cache for dg_rk_step
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_Q = nullptr;
+  const double* g_K = nullptr;
+  double g_dt = 0.0;
+  int g_nsteps = -1, g_sched = -1;
+  int parity = 0;
+
+  dgk::Ctx ctx() const {
+    dgk::Ctx c;
+    c.dpool = d_dpool;
+    c.ipool = d_ipool;
+    c.tabs = d_tabs;
+    c.slot_tab = d_slot_tab;
+    c.slot_type = d_slot_type;
+    c.slot_qoff = d_slot_qoff;
+    c.slot_hoff = d_slot_hoff;
+    c.slot_ftoff = d_slot_ftoff;
+    c.elem_of_slot = d_elem_of_slot;
+    c.elem_qoff = d_elem_qoff;
+    c.geo = d_geo;
+    c.H = d_H;
+    c.T = d_T;
+    c.faces = d_faces;
+    c.fblocks = d_fblocks;
+    c.perms = d_perms;
+    c.dense = d_dense;
+    c.status = d_status;
+    c.cost = d_cost;
+    c.sm_ns = d_smns;
+    c.gamma = gamma;
+    c.flux = flux;
+    c.nQmax = nQmax;
+    return c;
+  }
+
+  int grid_balanced() const { return num_sms * blocks_per_sm; }
+
+  // Weighted contiguous chunks of the Hilbert order (4 per resident warp).
+  cudaError_t build_chunks(const double* type_weight) {
+    const int64_t E = h.n_elems;
+    int64_t target = std::max<int64_t>(1, std::min<int64_t>(E, 4LL * grid_balanced() * wpb));
+    double total = 0.0;
+    for (int64_t s = 0; s < E; ++s) total += type_weight[h.slot_type[s]];
+    std::vector<int64_t> starts;
+    starts.push_back(0);
+    double acc = 0.0;
+    int64_t k = 1;
+    for (int64_t s = 0; s < E; ++s) {
+      acc += type_weight[h.slot_type[s]];
+      if (acc >= total * (double)k / (double)target && s + 1 < E) {
+        starts.push_back(s + 1);
+        while (acc >= total * (double)k / (double)target) ++k;
+      }
+    }
+    starts.push_back(E);
+    nchunks = (int64_t)starts.size() - 1;
+    if (d_chunks) cudaFree(d_chunks);
+    return upload(&d_chunks, starts);
+  }
+
+  void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
+    dgk::Ctx c = ctx();
+    if (scheduler == DG_SCHED_BALANCED && mode != dgk::kProject) {
+      dgk::Sched s{nullptr, nchunks, d_chunks, d_counters + parity, d_counters + (parity ^ 1)};
+      dgk::launch_element(c, mode, a, s, true, grid_balanced(), wpb, st);
+      parity ^= 1;
+    } else {
+      for (int t = 0; t < 4; ++t) {
+        if (h.type_slots[t].empty()) continue;
+        dgk::Sched s{d_type_slots[t], (int64_t)h.type_slots[t].size(), nullptr, nullptr, nullptr};
+        dgk::launch_element(c, mode, a, s, false, 0, wpb, st);
+      }
+    }
+  }
+
+  void face_phase(cudaStream_t st) { dgk::launch_faces(ctx(), (int64_t)h.face_blocks.size(), h.n, st); }
+
+  // Enqueue nsteps LSERK steps (no synchronisation).
+  void enqueue_rk(double* Q, double* K, double dt, int nsteps, cudaStream_t st) {
+    cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
+    parity = 0;
+    dgk::StageArgs a{Q, Q, K, 0.0, 0.0, dt};
+    element_phase(dgk::kFwd, a, st);
+    for (int step = 0; step < nsteps; ++step)
+      for (int s = 0; s < 5; ++s) {
+        face_phase(st);
+        bool last = step == nsteps - 1 && s == 4;
+        a.a = kLsA[s];
+        a.b = kLsB[s];
+        element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, st);
+      }
+  }
+
+  void release() {
+    void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
+                    d_elem_of_slot, d_elem_qoff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
+                    d_cost, d_smns, d_counters, d_chunks, d_stage};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    for (auto& p : d_type_slots)
+      if (p) cudaFree(p);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out) {
+  if (!desc || !out) return fail(DG_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE) return fail(DG_ERR_ARG, "unknown flux");
+  if (desc->scheduler != DG_SCHED_BALANCED && desc->scheduler != DG_SCHED_NAIVE) return fail(DG_ERR_ARG, "unknown scheduler");
+  if (!(desc->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) return fail(DG_ERR_CUDA, "no CUDA device available (the library has no CPU path)");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  dgh::MeshInput in{desc->n_vertices, desc->xyz, desc->n_elems, desc->type, desc->elem_vert_off, desc->elem_verts,
+                    desc->period, desc->N};
+  std::string err;
+  int r = dgh::build_mesh(in, &m->h, &err);
+  if (r != 0) {
+    delete m;
+    return fail((dg_status)r, err);
+  }
+  m->flux = desc->flux;
+  m->gamma = desc->gamma;
+  m->scheduler = desc->scheduler;
+  m->threshold = desc->imbalance_threshold > 0 ? desc->imbalance_threshold : 0.1;
+  cudaGetDevice(&m->device);
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  const dgh::HostMesh& h = m->h;
+  m->nQmax = h.n * h.n * h.n;
+  m->wpb = m->nQmax >= 216 ? 1 : 2;
+  auto fail_cuda = [&](cudaError_t e, const char* what) {
+    m->release();
+    delete m;
+    return cuda_fail(e, what);
+  };
+  cudaError_t e;
+  if ((e = dgk::element_kernel_attributes(m->nQmax, m->wpb, &m->blocks_per_sm)) != cudaSuccess) return fail_cuda(e, "kernel attributes");
+  if (m->blocks_per_sm < 1) m->blocks_per_sm = 1;
+  std::vector<int> slot_tab(h.slot_tab);
+  if ((e = upload(&m->d_dpool, h.tables.dpool)) != cudaSuccess) return fail_cuda(e, "upload tables");
+  if ((e = upload(&m->d_ipool, h.tables.ipool)) != cudaSuccess) return fail_cuda(e, "upload tables");
+  if ((e = upload(&m->d_tabs, h.tables.tabs)) != cudaSuccess) return fail_cuda(e, "upload tables");
+  if ((e = upload(&m->d_slot_tab, slot_tab)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_slot_type, h.slot_type)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_slot_qoff, h.slot_qoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_slot_hoff, h.slot_hoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_slot_ftoff, h.slot_ftoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_elem_of_slot, h.elem_of_slot)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_elem_qoff, h.elem_qoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_geo, h.slot_geo)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+  if ((e = upload(&m->d_faces, h.faces)) != cudaSuccess) return fail_cuda(e, "upload faces");
+  if ((e = upload(&m->d_fblocks, h.face_blocks)) != cudaSuccess) return fail_cuda(e, "upload faces");
+  if ((e = upload(&m->d_perms, h.perms)) != cudaSuccess) return fail_cuda(e, "upload maps");
+  if ((e = upload(&m->d_dense, h.dense)) != cudaSuccess) return fail_cuda(e, "upload maps");
+  for (int t = 0; t < 4; ++t)
+    if ((e = upload(&m->d_type_slots[t], h.type_slots[t])) != cudaSuccess) return fail_cuda(e, "upload type lists");
+  if ((e = cudaMalloc(&m->d_H, sizeof(double) * std::max<int64_t>(1, h.h_total))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_T, sizeof(double) * std::max<int64_t>(1, h.t_total))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_stage, sizeof(double) * std::max<int64_t>(1, h.n_dof))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_status, sizeof(unsigned))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_counters, 2 * sizeof(unsigned))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_cost, 8 * sizeof(unsigned long long))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_smns, (size_t)m->num_sms * sizeof(unsigned long long))) != cudaSuccess) return fail_cuda(e, "workspace");
+  cudaMemset(m->d_status, 0, sizeof(unsigned));
+  cudaMemset(m->d_counters, 0, 2 * sizeof(unsigned));
+  cudaMemset(m->d_cost, 0, 8 * sizeof(unsigned long long));
+  cudaMemset(m->d_smns, 0, (size_t)m->num_sms * sizeof(unsigned long long));
+  double w[4];
+  for (int t = 0; t < 4; ++t) {
+    int ti = h.tables.find(t, h.N);
+    w[t] = ti >= 0 ? dgh::static_cost(h.tables.tabs[ti]) : 1.0;
+  }
+  if ((e = m->build_chunks(w)) != cudaSuccess) return fail_cuda(e, "chunk table");
+  if ((e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking)) != cudaSuccess) return fail_cuda(e, "stream");
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail_cuda(e, "synchronise");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail_cuda(e, "synchronise");
+  *out = m;
+  return DG_OK;
+}
+
+dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_xyz, int64_t* slot_of_elem) {
+  if (!desc) return fail(DG_ERR_ARG, "null argument");
+  dgh::HostMesh h;
+  dgh::MeshInput in{desc->n_vertices, desc->xyz, desc->n_elems, desc->type, desc->elem_vert_off, desc->elem_verts,
+                    desc->period, desc->N};
+  std::string err;
+  int r = dgh::build_mesh(in, &h, &err);
+  if (r != 0) return fail((dg_status)r, err);
+  if (counts) {
+    counts[0] = h.n_elems;
+    counts[1] = h.n_faces;
+    for (int t = 0; t < 4; ++t) counts[2 + t] = h.type_count[t];
+    counts[6] = h.n_perm;
+    counts[7] = h.n_dense;
+  }
+  if (quad_xyz) std::memcpy(quad_xyz, h.quad_xyz.data(), sizeof(double) * h.quad_xyz.size());
+  if (slot_of_elem) std::memcpy(slot_of_elem, h.slot_of_elem.data(), sizeof(int64_t) * h.n_elems);
+  return DG_OK;
+}
+
+dg_status dg_mesh_destroy(dg_mesh* mesh) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  cudaDeviceSynchronize();
+  mesh->release();
+  delete mesh;
+  return DG_OK;
+}
+
+dg_status dg_mesh_layout(const dg_mesh* mesh, int64_t* n_dof, int64_t* slot_of_elem, int64_t* counts) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (n_dof) *n_dof = mesh->h.n_dof;
+  if (slot_of_elem) std::memcpy(slot_of_elem, mesh->h.slot_of_elem.data(), sizeof(int64_t) * mesh->h.n_elems);
+  if (counts) {
+    counts[0] = mesh->h.n_elems;
+    counts[1] = mesh->h.n_faces;
+    for (int t = 0; t < 4; ++t) counts[2 + t] = mesh->h.type_count[t];
+  }
+  return DG_OK;
+}
+
+dg_status dg_set_state(dg_mesh* mesh, const double* Q_ext, int is_device, double* Q_store, cudaStream_t stream) {
+  if (!mesh || !Q_ext || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  const double* src = Q_ext;
+  if (!is_device) {
+    DG_CUDA(cudaMemcpyAsync(mesh->d_stage, Q_ext, sizeof(double) * mesh->h.n_dof, cudaMemcpyHostToDevice, stream));
+    src = mesh->d_stage;
+  }
+  dgk::launch_permute(mesh->ctx(), src, Q_store, mesh->h.n_elems, 1, stream);
+  DG_CUDA(cudaGetLastError());
+  if (!is_device) DG_CUDA(cudaStreamSynchronize(stream));
+  return DG_OK;
+}
+
+dg_status dg_get_state(const dg_mesh* mesh, const double* Q_store, double* Q_ext, int is_device, cudaStream_t stream) {
+  if (!mesh || !Q_ext || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  double* dst = is_device ? Q_ext : mesh->d_stage;
+  dgk::launch_permute(mesh->ctx(), Q_store, dst, mesh->h.n_elems, 0, stream);
+  DG_CUDA(cudaGetLastError());
+  if (!is_device) {
+    DG_CUDA(cudaMemcpyAsync(Q_ext, mesh->d_stage, sizeof(double) * mesh->h.n_dof, cudaMemcpyDeviceToHost, stream));
+    DG_CUDA(cudaStreamSynchronize(stream));
+  }
+  return DG_OK;
+}
+
+dg_status dg_quad_points(const dg_mesh* mesh, double* xyz_out) {
+  if (!mesh || !xyz_out) return fail(DG_ERR_ARG, "null argument");
+  std::memcpy(xyz_out, mesh->h.quad_xyz.data(), sizeof(double) * mesh->h.quad_xyz.size());
+  return DG_OK;
+}
+
+dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cudaStream_t stream) {
+  if (!mesh || !q_points || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  dgk::StageArgs a{q_points, Q_store, nullptr, 0.0, 0.0, 0.0};
+  mesh->element_phase(dgk::kProject, a, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStream_t stream) {
+  if (!mesh || !Q_store || !R_store) return fail(DG_ERR_ARG, "null argument");
+  DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
+  mesh->parity = 0;
+  dgk::StageArgs a{Q_store, R_store, nullptr, 0.0, 0.0, 0.0};
+  mesh->element_phase(dgk::kFwd, a, stream);
+  mesh->face_phase(stream);
+  mesh->element_phase(dgk::kBwdRhs, a, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps, cudaStream_t stream) {
+  if (!mesh || !Q_store || !K_store) return fail(DG_ERR_ARG, "null argument");
+  if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return DG_OK;
+  if (!(std::isfinite(dt))) return fail(DG_ERR_ARG, "dt must be finite");
+  if (!mesh->gexec || mesh->g_Q != Q_store || mesh->g_K != K_store || mesh->g_dt != dt || mesh->g_nsteps != nsteps ||
+      mesh->g_sched != mesh->scheduler) {
+    if (mesh->gexec) {
+      cudaGraphExecDestroy(mesh->gexec);
+      mesh->gexec = nullptr;
+    }
+    cudaGraph_t g;
+    DG_CUDA(cudaStreamBeginCapture(mesh->cap, cudaStreamCaptureModeThreadLocal));
+    mesh->enqueue_rk(Q_store, K_store, dt, nsteps, mesh->cap);
+    cudaError_t e = cudaStreamEndCapture(mesh->cap, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&mesh->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    mesh->g_Q = Q_store;
+    mesh->g_K = K_store;
+    mesh->g_dt = dt;
+    mesh->g_nsteps = nsteps;
+    mesh->g_sched = mesh->scheduler;
+  }
+  DG_CUDA(cudaGraphLaunch(mesh->gexec, stream));
+  return DG_OK;
+}
+
+dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t) {
+  if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp is not built yet");
+}
+
+dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double, int, int, const double* QKbar, double* Q0bar, cudaStream_t) {
+  if (!mesh || !Q0_store || !QKbar || !Q0bar) return fail(DG_ERR_ARG, "null argument");
+  return fail(DG_ERR_UNSUPPORTED, "dg_rk_vjp is not built yet");
+}
+
+dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (scheduler != DG_SCHED_BALANCED && scheduler != DG_SCHED_NAIVE) return fail(DG_ERR_ARG, "unknown scheduler");
+  mesh->scheduler = scheduler;
+  return DG_OK;
+}
+
+dg_status dg_cost_table(dg_mesh* mesh, double* ns_per_elem, double* imbalance, cudaStream_t stream) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  DG_CUDA(cudaStreamSynchronize(stream));
+  unsigned long long cost[8];
+  std::vector<unsigned long long> sm(mesh->num_sms);
+  DG_CUDA(cudaMemcpy(cost, mesh->d_cost, sizeof(cost), cudaMemcpyDeviceToHost));
+  DG_CUDA(cudaMemcpy(sm.data(), mesh->d_smns, sizeof(unsigned long long) * sm.size(), cudaMemcpyDeviceToHost));
+  if (ns_per_elem)
+    for (int t = 0; t < 4; ++t) ns_per_elem[t] = cost[2 * t + 1] ? (double)cost[2 * t] / (double)cost[2 * t + 1] : 0.0;
+  if (imbalance) {
+    double mx = 0.0, sum = 0.0;
+    for (auto v : sm) { mx = std::max(mx, (double)v); sum += (double)v; }
+    double mean = sum / std::max<size_t>(1, sm.size());
+    *imbalance = mean > 0 ? mx / mean - 1.0 : 0.0;
+  }
+  return DG_OK;
+}
+
+dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stream) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  double ns[4], imb = 0.0;
+  dg_status s = dg_cost_table(mesh, ns, &imb, stream);
+  if (s != DG_OK) return s;
+  bool measured = false;
+  for (int t = 0; t < 4; ++t) measured |= ns[t] > 0;
+  bool doit = force || (measured && imb > mesh->threshold);
+  if (rebuilt) *rebuilt = doit ? 1 : 0;
+  if (doit) {
+    double w[4];
+    for (int t = 0; t < 4; ++t) {
+      int ti = mesh->h.tables.find(t, mesh->h.N);
+      w[t] = ns[t] > 0 ? ns[t] : (ti >= 0 ? dgh::static_cost(mesh->h.tables.tabs[ti]) : 1.0);
+    }
+    if (!measured) {
+      for (int t = 0; t < 4; ++t) {
+        int ti = mesh->h.tables.find(t, mesh->h.N);
+        w[t] = ti >= 0 ? dgh::static_cost(mesh->h.tables.tabs[ti]) : 1.0;
+      }
+    }
+    DG_CUDA(mesh->build_chunks(w));
+    if (mesh->gexec) {
+      cudaGraphExecDestroy(mesh->gexec);
+      mesh->gexec = nullptr;
+    }
+  }
+  DG_CUDA(cudaMemset(mesh->d_cost, 0, 8 * sizeof(unsigned long long)));
+  DG_CUDA(cudaMemset(mesh->d_smns, 0, (size_t)mesh->num_sms * sizeof(unsigned long long)));
+  return DG_OK;
+}
+
+dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  DG_CUDA(cudaStreamSynchronize(stream));
+  unsigned st = 0;
+  DG_CUDA(cudaMemcpy(&st, mesh->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st & 1u) {
+    cudaMemset(mesh->d_status, 0, sizeof(unsigned));
+    return fail(DG_ERR_NONFINITE, "a non-finite state value was produced");
+  }
+  return DG_OK;
+}
+
+dg_status dg_probe_fp64_peak(double* dfma_tflops, double* dmma_tflops) {
+  if (!dfma_tflops || !dmma_tflops) return fail(DG_ERR_ARG, "null argument");
+  cudaError_t e = dgk::probe_fp64(dfma_tflops, dmma_tflops);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 probe");
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,887 @@
+// Host set-up: operator tables per (type, N), affine geometry, face
+// connectivity with the owner rule, neighbour maps, Hilbert ordering.
+//
+// The discretisation is the modal weak form of Eq. 1 (Sec. 2 of Kopper et
+// al.): orthonormal modal bases on the reference hex / prism / pyramid / tet,
+// collapsed (Duffy) Gauss-Legendre quadrature with n = N+1 points per
+// direction, faces integrated with the owner's face rule.
+#include "dg_host.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <unordered_map>
+
+namespace dgh {
+
+using dgk::FaceDesc;
+using dgk::TypeTab;
+
+// ============================================================ 1D building blocks
+
+// Gauss-Legendre nodes (ascending) and weights by Newton iteration on the
+// three-term Legendre recurrence, started from the Chebyshev-like guess
+// cos(pi (i + 3/4) / (n + 1/2)); nodes are symmetrised exactly.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[n - 1 - i] = z;
+    x[i] = -z;
+    w[i] = w[n - 1 - i] = wt;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// Jacobi P_n^(alpha,beta)(x) by the standard three-term recurrence.
+double jacobi(int n, double al, double be, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0;
+  double p1 = 0.5 * (al - be + (al + be + 2.0) * x);
+  for (int k = 2; k <= n; ++k) {
+    double a = al + be;
+    double c1 = 2.0 * k * (k + a) * (2.0 * k + a - 2.0);
+    double c2 = (2.0 * k + a - 1.0) * ((2.0 * k + a) * (2.0 * k + a - 2.0) * x + al * al - be * be);
+    double c3 = 2.0 * (k + al - 1.0) * (k + be - 1.0) * (2.0 * k + a);
+    double p2 = (c2 * p1 - c3 * p0) / c1;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+double jhat(int n, int alpha, double x) {
+  return jacobi(n, alpha, 0.0, x) * std::sqrt((2.0 * n + alpha + 1.0) / 2.0);
+}
+
+void lagrange_values(const double* nodes, int n, double x, double* out) {
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) v *= (x - nodes[k]) / (nodes[j] - nodes[k]);
+    out[j] = v;
+  }
+}
+
+// ============================================================ reference elements
+
+const double kRefVerts[4][8][3] = {
+    {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}, {1, 1, 1}},
+    {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}},
+    {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, 1}},
+    {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}},
+};
+const int kNumVerts[4] = {8, 6, 5, 4};
+const int kNumFaces[4] = {6, 5, 5, 4};
+// Local faces as vertex lists; face parameters x(s,t) = c0 + (s+1)/2 (c1-c0) + (t+1)/2 (c2-c0).
+const int kFaceVerts[4][6][4] = {
+    {{0, 1, 2, 3}, {4, 5, 6, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 2, 4, 6}, {1, 3, 5, 7}},
+    {{0, 1, 2, -1}, {3, 4, 5, -1}, {0, 1, 3, 4}, {0, 2, 3, 5}, {1, 2, 4, 5}, {-1, -1, -1, -1}},
+    {{0, 1, 2, 3}, {0, 1, 4, -1}, {0, 2, 4, -1}, {1, 3, 4, -1}, {2, 3, 4, -1}, {-1, -1, -1, -1}},
+    {{0, 1, 2, -1}, {0, 1, 3, -1}, {0, 2, 3, -1}, {1, 2, 3, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}},
+};
+const int kFaceNV[4][6] = {{4, 4, 4, 4, 4, 4}, {3, 3, 4, 4, 4, 0}, {4, 3, 3, 3, 3, 0}, {3, 3, 3, 3, 0, 0}};
+
+// Face points of every local face lie on the collapsed tensor grid: one
+// collapsed coordinate is fixed at an end, the face parameters run along two
+// others.  (Checked numerically in Tables::add.)
+static const FaceDesc kFaceDesc[4][6] = {
+    {{2, 0, 0, 1, 0}, {2, 1, 0, 1, 0}, {1, 0, 0, 2, 0}, {1, 1, 0, 2, 0}, {0, 0, 1, 2, 0}, {0, 1, 1, 2, 0}},
+    {{2, 0, 0, 1, 1}, {2, 1, 0, 1, 1}, {1, 0, 0, 2, 0}, {0, 0, 1, 2, 0}, {0, 1, 1, 2, 0}, {0, 0, 0, 0, 0}},
+    {{2, 0, 0, 1, 0}, {1, 0, 0, 2, 1}, {0, 0, 1, 2, 1}, {0, 1, 1, 2, 1}, {1, 1, 0, 2, 1}, {0, 0, 0, 0, 0}},
+    {{2, 0, 0, 1, 1}, {1, 0, 0, 2, 1}, {0, 0, 1, 2, 1}, {0, 1, 1, 2, 1}, {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}},
+};
+
+int n_modes(int type, int N) {
+  int n = N + 1;
+  switch (type) {
+    case dgk::HEX: return n * n * n;
+    case dgk::PRISM: return n * n * (n + 1) / 2;
+    case dgk::PYR: return n * (n + 1) * (2 * n + 1) / 6;
+    case dgk::TET: return n * (n + 1) * (n + 2) / 6;
+  }
+  return 0;
+}
+
+static int q_count(int type, int N, int p) { return (type == dgk::PRISM || type == dgk::TET) ? N - p + 1 : N + 1; }
+static int r_count(int type, int N, int p, int q) {
+  switch (type) {
+    case dgk::HEX:
+    case dgk::PRISM: return N + 1;
+    case dgk::TET: return N - p - q + 1;
+    case dgk::PYR: return N - std::max(p, q) + 1;
+  }
+  return 0;
+}
+
+// The orthonormal basis phi_pqr = A_p(a) B_pq(b) C_pqr(c):
+//   hex      L_p(a) L_q(b) L_r(c)
+//   prism    L_p(a) ((1-b)/2)^p J_q^(2p+1)(b) L_r(c)
+//   pyramid  L_p(a) L_q(b) ((1-c)/2)^m J_r^(2m+2)(c),        m = max(p, q)
+//   tet      L_p(a) ((1-b)/2)^p J_q^(2p+1)(b) ((1-c)/2)^(p+q) J_r^(2p+2q+2)(c)
+double factor_A(int, int p, double a) { return jhat(p, 0, a); }
+double factor_B(int type, int p, int q, double b) {
+  if (type == dgk::HEX || type == dgk::PYR) return jhat(q, 0, b);
+  return std::pow(0.5 * (1.0 - b), p) * jhat(q, 2 * p + 1, b);
+}
+double factor_C(int type, int p, int q, int r, double c) {
+  switch (type) {
+    case dgk::HEX:
+    case dgk::PRISM: return jhat(r, 0, c);
+    case dgk::TET: return std::pow(0.5 * (1.0 - c), p + q) * jhat(r, 2 * p + 2 * q + 2, c);
+    case dgk::PYR: {
+      int m = std::max(p, q);
+      return std::pow(0.5 * (1.0 - c), m) * jhat(r, 2 * m + 2, c);
+    }
+  }
+  return 0.0;
+}
+
+void uncollapse(int type, double a, double b, double c, double* xi) {
+  switch (type) {
+    case dgk::HEX: xi[0] = a; xi[1] = b; xi[2] = c; break;
+    case dgk::PRISM: xi[0] = 0.5 * (1 + a) * (1 - b) - 1; xi[1] = b; xi[2] = c; break;
+    case dgk::TET:
+      xi[0] = 0.25 * (1 + a) * (1 - b) * (1 - c) - 1;
+      xi[1] = 0.5 * (1 + b) * (1 - c) - 1;
+      xi[2] = c;
+      break;
+    case dgk::PYR:
+      xi[0] = 0.5 * (1 + a) * (1 - c) - 1;
+      xi[1] = 0.5 * (1 + b) * (1 - c) - 1;
+      xi[2] = c;
+      break;
+  }
+}
+
+static void collapse(int type, const double* xi, double* abc) {
+  switch (type) {
+    case dgk::HEX: abc[0] = xi[0]; abc[1] = xi[1]; abc[2] = xi[2]; break;
+    case dgk::PRISM: abc[0] = 2 * (1 + xi[0]) / (1 - xi[1]) - 1; abc[1] = xi[1]; abc[2] = xi[2]; break;
+    case dgk::TET:
+      abc[0] = 2 * (1 + xi[0]) / (-xi[1] - xi[2]) - 1;
+      abc[1] = 2 * (1 + xi[1]) / (1 - xi[2]) - 1;
+      abc[2] = xi[2];
+      break;
+    case dgk::PYR:
+      abc[0] = 2 * (1 + xi[0]) / (1 - xi[2]) - 1;
+      abc[1] = 2 * (1 + xi[1]) / (1 - xi[2]) - 1;
+      abc[2] = xi[2];
+      break;
+  }
+}
+
+// Duffy Jacobian det d(xi)/d(abc) and the inverse map's derivatives
+// d(a,b,c)_l / d(xi,eta,zeta)_k at a collapsed point.
+static double duffy_det(int type, double, double b, double c) {
+  switch (type) {
+    case dgk::HEX: return 1.0;
+    case dgk::PRISM: return 0.5 * (1 - b);
+    case dgk::TET: return 0.5 * (1 - b) * 0.25 * (1 - c) * (1 - c);
+    case dgk::PYR: return 0.25 * (1 - c) * (1 - c);
+  }
+  return 0.0;
+}
+
+static void collapse_metric(int type, double a, double b, double c, double M[3][3]) {
+  std::memset(M, 0, sizeof(double) * 9);
+  M[2][2] = 1.0;
+  switch (type) {
+    case dgk::HEX: M[0][0] = M[1][1] = 1.0; break;
+    case dgk::PRISM:
+      M[0][0] = 2.0 / (1 - b);
+      M[0][1] = (1 + a) / (1 - b);
+      M[1][1] = 1.0;
+      break;
+    case dgk::TET: {
+      double s = 0.5 * (1 - b) * (1 - c);  // -eta - zeta
+      M[0][0] = 2.0 / s;
+      M[0][1] = M[0][2] = (1 + a) / s;
+      M[1][1] = 2.0 / (1 - c);
+      M[1][2] = (1 + b) / (1 - c);
+      break;
+    }
+    case dgk::PYR:
+      M[0][0] = 2.0 / (1 - c);
+      M[0][2] = (1 + a) / (1 - c);
+      M[1][1] = 2.0 / (1 - c);
+      M[1][2] = (1 + b) / (1 - c);
+      break;
+  }
+}
+
+// ============================================================ operator tables
+
+int Tables::find(int type, int N) const {
+  for (size_t i = 0; i < tabs.size(); ++i)
+    if (tabs[i].type == type && tabs[i].N == N) return (int)i;
+  return -1;
+}
+
+int Tables::add(int type, int N, std::string* err) {
+  int have = find(type, N);
+  if (have >= 0) return have;
+  TypeTab t;
+  std::memset(&t, 0, sizeof(t));
+  const int n = N + 1;
+  t.type = type;
+  t.N = N;
+  t.n = n;
+  t.nM = n_modes(type, N);
+  t.nQ = n * n * n;
+  t.nfaces = kNumFaces[type];
+  std::vector<double> x(n), w(n);
+  gauss_legendre(n, x.data(), w.data());
+  auto dput = [&](double v) { dpool.push_back(v); };
+  auto ialloc = [&](int cnt) { int o = (int)ipool.size(); ipool.resize(ipool.size() + cnt, 0); return o; };
+
+  // A
+  t.A = (int)dpool.size();
+  for (int p = 0; p < n; ++p)
+    for (int i = 0; i < n; ++i) dput(factor_A(type, p, x[i]));
+  // columns (p, q) and B
+  std::vector<int> cols_p, cols_q;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < q_count(type, N, p); ++q) { cols_p.push_back(p); cols_q.push_back(q); }
+  t.ncols = (int)cols_p.size();
+  t.p_cbase = ialloc(n);
+  t.p_blen = ialloc(n);
+  t.p_boff = ialloc(n);
+  t.B = (int)dpool.size();
+  {
+    int col = 0;
+    for (int p = 0; p < n; ++p) {
+      ipool[t.p_cbase + p] = col;
+      ipool[t.p_blen + p] = q_count(type, N, p);
+      ipool[t.p_boff + p] = (int)dpool.size() - t.B;
+      for (int q = 0; q < q_count(type, N, p); ++q)
+        for (int j = 0; j < n; ++j) dput(factor_B(type, p, q, x[j]));
+      col += q_count(type, N, p);
+    }
+  }
+  // C and mode bookkeeping
+  t.col_moff = ialloc(t.ncols);
+  t.col_len = ialloc(t.ncols);
+  t.col_coff = ialloc(t.ncols);
+  t.col_p = ialloc(t.ncols);
+  t.mode_col = ialloc(t.nM);
+  t.C = (int)dpool.size();
+  {
+    int mode = 0;
+    for (int col = 0; col < t.ncols; ++col) {
+      int p = cols_p[col], q = cols_q[col];
+      int len = r_count(type, N, p, q);
+      ipool[t.col_moff + col] = mode;
+      ipool[t.col_len + col] = len;
+      ipool[t.col_coff + col] = (int)dpool.size() - t.C;
+      ipool[t.col_p + col] = p;
+      for (int r = 0; r < len; ++r) {
+        ipool[t.mode_col + mode + r] = col;
+        for (int k = 0; k < n; ++k) dput(factor_C(type, p, q, r, x[k]));
+      }
+      mode += len;
+    }
+    if (mode != t.nM) { *err = "internal: mode count mismatch"; return -1; }
+  }
+  // collocation derivative Dt[i'][i] = l'_{i'}(x_i) (barycentric formula)
+  t.Dt = (int)dpool.size();
+  {
+    std::vector<double> lam(n, 1.0);
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k)
+        if (k != j) lam[j] /= (x[j] - x[k]);
+    std::vector<double> D(n * n, 0.0);  // D[i][j] = l'_j(x_i)
+    for (int i = 0; i < n; ++i) {
+      double diag = 0.0;
+      for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+        diag -= D[i * n + j];
+      }
+      D[i * n + i] = diag;
+    }
+    for (int ip = 0; ip < n; ++ip)
+      for (int i = 0; i < n; ++i) dput(D[i * n + ip]);
+  }
+  // extrapolation to the ends
+  t.ext = (int)dpool.size();
+  {
+    std::vector<double> l(n);
+    lagrange_values(x.data(), n, -1.0, l.data());
+    for (int m = 0; m < n; ++m) dput(l[m]);
+    lagrange_values(x.data(), n, 1.0, l.data());
+    for (int m = 0; m < n; ++m) dput(l[m]);
+  }
+  // volume weights times the collapse metric
+  t.wA = (int)dpool.size();
+  std::vector<double> wq(t.nQ);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        int q = (i * n + j) * n + k;
+        wq[q] = w[i] * w[j] * w[k] * duffy_det(type, x[i], x[j], x[k]);
+        double M[3][3];
+        collapse_metric(type, x[i], x[j], x[k], M);
+        for (int l = 0; l < 3; ++l)
+          for (int kk = 0; kk < 3; ++kk) dput(wq[q] * M[l][kk]);
+      }
+  t.W = (int)dpool.size();
+  for (int q = 0; q < t.nQ; ++q) dput(wq[q]);
+  // mass matrix V^T W V: must be diagonal under the collapsed GL rule
+  t.minv = (int)dpool.size();
+  {
+    std::vector<double> V((size_t)t.nQ * t.nM);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+          int q = (i * n + j) * n + k;
+          int mode = 0;
+          for (int col = 0; col < t.ncols; ++col) {
+            int p = cols_p[col], qq = cols_q[col];
+            for (int r = 0; r < r_count(type, N, p, qq); ++r, ++mode)
+              V[(size_t)q * t.nM + mode] = factor_A(type, p, x[i]) * factor_B(type, p, qq, x[j]) *
+                                           factor_C(type, p, qq, r, x[k]);
+          }
+        }
+    double maxd = 0.0, maxoff = 0.0;
+    std::vector<double> diag(t.nM);
+    for (int a = 0; a < t.nM; ++a)
+      for (int b = 0; b < t.nM; ++b) {
+        double s = 0.0;
+        for (int q = 0; q < t.nQ; ++q) s += V[(size_t)q * t.nM + a] * wq[q] * V[(size_t)q * t.nM + b];
+        if (a == b) { diag[a] = s; maxd = std::max(maxd, std::fabs(s)); }
+        else maxoff = std::max(maxoff, std::fabs(s));
+      }
+    if (maxoff > 1e-12 * maxd) { *err = "mass matrix is not diagonal for this (type, N)"; return -7; }
+    for (int a = 0; a < t.nM; ++a) dput(1.0 / diag[a]);
+  }
+  // face descriptors + numerical check that the face rule points lie on the grid
+  t.fw = (int)dpool.size();
+  for (int lf = 0; lf < t.nfaces; ++lf) {
+    FaceDesc d = kFaceDesc[type][lf];
+    t.faces[lf] = d;
+    const int* fv = kFaceVerts[type][lf];
+    const double* c0 = kRefVerts[type][fv[0]];
+    const double* c1 = kRefVerts[type][fv[1]];
+    const double* c2 = kRefVerts[type][fv[2]];
+    for (int ib = 0; ib < n; ++ib)
+      for (int ia = 0; ia < n; ++ia) {
+        double al = x[ia], be = x[ib];
+        double s = d.tri ? 0.5 * (1 + al) * (1 - be) - 1 : al;
+        double tt = be;
+        double xi[3], abc[3];
+        for (int k = 0; k < 3; ++k) xi[k] = c0[k] + 0.5 * (s + 1) * (c1[k] - c0[k]) + 0.5 * (tt + 1) * (c2[k] - c0[k]);
+        collapse(type, xi, abc);
+        double expect[3];
+        expect[d.fixed] = d.end ? 1.0 : -1.0;
+        expect[d.alpha] = al;
+        expect[d.beta] = be;
+        for (int k = 0; k < 3; ++k)
+          if (std::fabs(abc[k] - expect[k]) > 1e-12) { *err = "internal: face table inconsistent"; return -1; }
+        dput(d.tri ? w[ia] * w[ib] * 0.5 * (1 - be) : w[ia] * w[ib]);
+      }
+  }
+  tabs.push_back(t);
+  return (int)tabs.size() - 1;
+}
+
+double static_cost(const TypeTab& t) {
+  // FP64 lane operations of one stage of one element (forward + backward
+  // element work, pointwise flux, face share), used as the initial weight.
+  double n = t.n, nQ = t.nQ;
+  double vpass = 0;  // modal->nodal MACs per variable
+  vpass += n * (double)t.nM;                        // c-pass (sum of r lengths times n)
+  vpass += nQ * (t.type == dgk::PRISM || t.type == dgk::TET ? (n + 1) / 2.0 : n);  // b-pass
+  vpass += nQ * n;                                  // a-pass
+  double per_var = 2 * vpass + 3 * nQ * n + 2 * t.nfaces * n * n * n;
+  return 5 * per_var + 60 * nQ + t.nfaces * n * n * 60;
+}
+
+// ============================================================ Hilbert keys
+
+// Skilling (2004), "Programming the Hilbert curve": transpose form of the
+// Hilbert index from axis coordinates, then bit interleaving into one key.
+uint64_t hilbert_key3(uint32_t x0, uint32_t x1, uint32_t x2, int bits) {
+  uint32_t X[3] = {x0, x1, x2};
+  const uint32_t M = 1u << (bits - 1);
+  for (uint32_t Q = M; Q > 1; Q >>= 1) {
+    uint32_t P = Q - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & Q) {
+        X[0] ^= P;
+      } else {
+        uint32_t t = (X[0] ^ X[i]) & P;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
+  uint32_t t = 0;
+  for (uint32_t Q = M; Q > 1; Q >>= 1)
+    if (X[2] & Q) t ^= Q - 1;
+  for (int i = 0; i < 3; ++i) X[i] ^= t;
+  uint64_t key = 0;
+  for (int b = bits - 1; b >= 0; --b)
+    for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> b) & 1u);
+  return key;
+}
+
+// ============================================================ mesh
+
+namespace {
+
+struct Key3 {
+  int64_t v[3];
+  bool operator<(const Key3& o) const { return std::tie(v[0], v[1], v[2]) < std::tie(o.v[0], o.v[1], o.v[2]); }
+  bool operator==(const Key3& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2]; }
+};
+struct Key3Hash {
+  size_t operator()(const Key3& k) const {
+    uint64_t h = (uint64_t)k.v[0] * 0x9E3779B97F4A7C15ull ^ ((uint64_t)k.v[1] + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full ^
+                 ((uint64_t)k.v[2] + 0x165667B19E3779F9ull);
+    return (size_t)(h ^ (h >> 29));
+  }
+};
+
+const int64_t kQuant = 1ll << 24;
+
+Key3 reduce(const double* p, const double* period) {
+  Key3 k;
+  for (int d = 0; d < 3; ++d) {
+    int64_t q = (int64_t)std::llround(p[d] / period[d] * (double)kQuant);
+    q %= kQuant;
+    if (q < 0) q += kQuant;
+    k.v[d] = q;
+  }
+  return k;
+}
+
+struct FaceKey {
+  Key3 c;
+  Key3 v[4];
+  int nv;
+  bool operator<(const FaceKey& o) const {
+    if (!(c == o.c)) return c < o.c;
+    if (nv != o.nv) return nv < o.nv;
+    for (int i = 0; i < nv; ++i)
+      if (!(v[i] == o.v[i])) return v[i] < o.v[i];
+    return false;
+  }
+};
+
+void cross(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+double det3(const double A[3][3]) {
+  return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+void inv3(const double A[3][3], double Ai[3][3]) {
+  double d = det3(A);
+  Ai[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / d;
+  Ai[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / d;
+  Ai[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / d;
+  Ai[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / d;
+  Ai[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / d;
+  Ai[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / d;
+  Ai[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / d;
+  Ai[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / d;
+  Ai[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / d;
+}
+
+// reference vertices spanning the affine map (images of the reference axes)
+const int kAxisVert[4][3] = {{1, 2, 4}, {1, 2, 3}, {1, 2, 4}, {1, 2, 3}};
+
+}  // namespace
+
+int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
+  HostMesh& M = *out;
+  if (in.N < 1 || in.N > dgk::kMaxN) { *err = "N out of range"; return -1; }
+  if (!in.xyz || !in.type || !in.off || !in.verts || !in.period) { *err = "null pointer in mesh description"; return -1; }
+  if (in.n_elems <= 0 || in.n_vertices <= 0) { *err = "empty mesh"; return -1; }
+  for (int d = 0; d < 3; ++d)
+    if (!(in.period[d] > 0)) { *err = "period must be positive"; return -1; }
+  const int N = in.N, n = N + 1, n2 = n * n;
+  M.N = N;
+  M.n = n;
+  M.n_elems = in.n_elems;
+  M.x1d.resize(n);
+  M.w1d.resize(n);
+  gauss_legendre(n, M.x1d.data(), M.w1d.data());
+  const int64_t E = in.n_elems;
+  int tab_of_type[4] = {-1, -1, -1, -1};
+  for (int64_t e = 0; e < E; ++e) {
+    int t = in.type[e];
+    if (t < 0 || t > 3) { *err = "bad element type"; return -1; }
+    if (in.off[e + 1] - in.off[e] != kNumVerts[t]) { *err = "wrong vertex count for element type"; return -2; }
+    for (int64_t k = in.off[e]; k < in.off[e + 1]; ++k)
+      if (in.verts[k] < 0 || in.verts[k] >= in.n_vertices) { *err = "vertex index out of range"; return -1; }
+    if (tab_of_type[t] < 0) {
+      int r = M.tables.add(t, N, err);
+      if (r < 0) return r;
+      tab_of_type[t] = r;
+    }
+    M.type_count[t]++;
+  }
+
+  // ---- affine geometry (caller order first)
+  std::vector<dgk::ElemGeo> geo(E);
+  std::vector<std::array<double, 12>> affine(E);  // X0, A columns
+  std::vector<std::array<double, 3>> centroid(E);
+  for (int64_t e = 0; e < E; ++e) {
+    int t = in.type[e];
+    const int64_t* V = in.verts + in.off[e];
+    const double* X0 = in.xyz + 3 * V[0];
+    double A[3][3];  // A[d][k]: column k = image of reference axis k
+    for (int k = 0; k < 3; ++k) {
+      const double* Xk = in.xyz + 3 * V[kAxisVert[t][k]];
+      for (int d = 0; d < 3; ++d) A[d][k] = Xk[d] - X0[d];
+    }
+    double scale = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) scale = std::max(scale, std::fabs(A[d][k]));
+    for (int m = 0; m < kNumVerts[t]; ++m) {
+      const double* Xm = in.xyz + 3 * V[m];
+      for (int d = 0; d < 3; ++d) {
+        double pred = X0[d];
+        for (int k = 0; k < 3; ++k) pred += A[d][k] * 0.5 * (kRefVerts[t][m][k] + 1.0);
+        if (std::fabs(pred - Xm[d]) > 1e-10 * scale) { *err = "element is not an affine image of its reference element"; return -2; }
+      }
+    }
+    double det = det3(A);
+    if (!(std::fabs(det) > 1e-300)) { *err = "degenerate element"; return -2; }
+    double J = std::fabs(det) / 8.0;
+    double Ai[3][3];
+    inv3(A, Ai);  // d(xi+1)/2 / dx
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) geo[e].Jg[k * 3 + d] = J * 2.0 * Ai[k][d];
+    geo[e].invJ = 1.0 / J;
+    for (int d = 0; d < 3; ++d) {
+      affine[e][d] = X0[d];
+      for (int k = 0; k < 3; ++k) affine[e][3 + 3 * k + d] = A[d][k];
+    }
+    double c[3] = {0, 0, 0};
+    for (int m = 0; m < kNumVerts[t]; ++m)
+      for (int d = 0; d < 3; ++d) c[d] += in.xyz[3 * V[m] + d] / kNumVerts[t];
+    for (int d = 0; d < 3; ++d) centroid[e][d] = c[d];
+  }
+
+  // ---- Hilbert order of the centroids (ties: caller index)
+  {
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) { lo[d] = 1e300; hi[d] = -1e300; }
+    for (int64_t e = 0; e < E; ++e)
+      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], centroid[e][d]); hi[d] = std::max(hi[d], centroid[e][d]); }
+    const int bits = 21;
+    const double cells = (double)((1u << bits) - 1);
+    std::vector<std::pair<uint64_t, int64_t>> keys(E);
+    for (int64_t e = 0; e < E; ++e) {
+      uint32_t q[3];
+      for (int d = 0; d < 3; ++d) {
+        double span = hi[d] - lo[d];
+        double u = span > 0 ? (centroid[e][d] - lo[d]) / span : 0.0;
+        q[d] = (uint32_t)std::llround(u * cells);
+      }
+      keys[e] = {hilbert_key3(q[0], q[1], q[2], bits), e};
+    }
+    std::sort(keys.begin(), keys.end());
+    M.elem_of_slot.resize(E);
+    M.slot_of_elem.resize(E);
+    for (int64_t s = 0; s < E; ++s) {
+      M.elem_of_slot[s] = keys[s].second;
+      M.slot_of_elem[keys[s].second] = s;
+    }
+  }
+
+  // ---- per-slot records and state offsets
+  M.slot_tab.resize(E);
+  M.slot_type.resize(E);
+  M.slot_qoff.resize(E);
+  M.slot_hoff.resize(E);
+  M.slot_geo.resize(E);
+  M.elem_qoff.resize(E);
+  {
+    int64_t q = 0;
+    for (int64_t e = 0; e < E; ++e) { M.elem_qoff[e] = q; q += 5 * (int64_t)n_modes(in.type[e], N); }
+    M.n_dof = q;
+    int64_t qs = 0, hs = 0;
+    for (int64_t s = 0; s < E; ++s) {
+      int64_t e = M.elem_of_slot[s];
+      int t = in.type[e];
+      M.slot_tab[s] = tab_of_type[t];
+      M.slot_type[s] = (int8_t)t;
+      M.slot_qoff[s] = qs;
+      M.slot_hoff[s] = hs;
+      M.slot_geo[s] = geo[e];
+      qs += 5 * (int64_t)n_modes(t, N);
+      hs += 5 * (int64_t)n * n * n;
+    }
+    M.h_total = hs;
+  }
+  for (int t = 0; t < 4; ++t) M.type_slots[t].clear();
+  for (int64_t e = 0; e < E; ++e) M.type_slots[(int)in.type[e]].push_back(M.slot_of_elem[e]);
+
+  // ---- canonical (periodically reduced) vertex ids
+  std::vector<int64_t> canon(in.n_vertices);
+  {
+    std::unordered_map<Key3, int64_t, Key3Hash> ids;
+    ids.reserve((size_t)in.n_vertices * 2);
+    for (int64_t v = 0; v < in.n_vertices; ++v) {
+      Key3 k = reduce(in.xyz + 3 * v, in.period);
+      auto it = ids.find(k);
+      if (it == ids.end()) it = ids.emplace(k, (int64_t)ids.size()).first;
+      canon[v] = it->second;
+    }
+  }
+
+  // ---- face matching
+  struct Side { int64_t e; int lf; };
+  std::map<FaceKey, std::vector<Side>> table;
+  for (int64_t e = 0; e < E; ++e) {
+    int t = in.type[e];
+    const int64_t* V = in.verts + in.off[e];
+    for (int lf = 0; lf < kNumFaces[t]; ++lf) {
+      FaceKey fk;
+      fk.nv = kFaceNV[t][lf];
+      double c[3] = {0, 0, 0};
+      for (int i = 0; i < fk.nv; ++i) {
+        const double* P = in.xyz + 3 * V[kFaceVerts[t][lf][i]];
+        fk.v[i] = reduce(P, in.period);
+        for (int d = 0; d < 3; ++d) c[d] += P[d] / fk.nv;
+      }
+      fk.c = reduce(c, in.period);
+      std::sort(fk.v, fk.v + fk.nv);
+      table[fk].push_back({e, lf});
+    }
+  }
+  struct FaceTmp { int64_t e0, e1; int l0, l1; };
+  std::vector<FaceTmp> ftmp;
+  ftmp.reserve(table.size());
+  for (auto& kv : table) {
+    if (kv.second.size() != 2) { *err = "a face does not have exactly one partner (mesh must be conforming and periodic)"; return -2; }
+    Side a = kv.second[0], b = kv.second[1];
+    if (std::tie(b.e, b.lf) < std::tie(a.e, a.lf)) std::swap(a, b);  // owner: smaller caller index
+    ftmp.push_back({a.e, b.e, a.lf, b.lf});
+  }
+  // face-kernel order: by owner slot (Hilbert locality)
+  std::sort(ftmp.begin(), ftmp.end(), [&](const FaceTmp& x, const FaceTmp& y) {
+    int64_t sx = M.slot_of_elem[x.e0], sy = M.slot_of_elem[y.e0];
+    if (sx != sy) return sx < sy;
+    return x.l0 < y.l0;
+  });
+  const int64_t F = (int64_t)ftmp.size();
+  M.n_faces = F;
+  M.faces.resize(F);
+  M.slot_ftoff.assign((size_t)E * 6, -1);
+  M.perms.clear();
+  M.dense.clear();
+  std::map<std::vector<int16_t>, int> perm_ids;
+  std::map<std::vector<int>, int> dense_ids;  // key: (nb type, nb lf, sigma, owner tri)
+  const double* x = M.x1d.data();
+  for (int64_t f = 0; f < F; ++f) {
+    const FaceTmp& ft = ftmp[f];
+    int t0 = in.type[ft.e0], t1 = in.type[ft.e1];
+    int nv = kFaceNV[t0][ft.l0];
+    if (kFaceNV[t1][ft.l1] != nv) { *err = "matched faces of different shapes"; return -2; }
+    const int64_t* V0 = in.verts + in.off[ft.e0];
+    const int64_t* V1 = in.verts + in.off[ft.e1];
+    int64_t c0[4], c1[4];
+    for (int i = 0; i < nv; ++i) {
+      c0[i] = canon[V0[kFaceVerts[t0][ft.l0][i]]];
+      c1[i] = canon[V1[kFaceVerts[t1][ft.l1][i]]];
+    }
+    for (int i = 0; i < nv; ++i)
+      for (int j = i + 1; j < nv; ++j)
+        if (c0[i] == c0[j]) { *err = "face vertices coincide modulo the period (box too small)"; return -2; }
+    int sigma[4];  // neighbour slot m <-> owner slot sigma[m]
+    for (int m = 0; m < nv; ++m) {
+      sigma[m] = -1;
+      for (int i = 0; i < nv; ++i)
+        if (c1[m] == c0[i]) sigma[m] = i;
+      if (sigma[m] < 0) { *err = "face vertex correspondence failed"; return -2; }
+    }
+    dgk::FaceRec& R = M.faces[f];
+    R.toff = f * 2 * 5 * (int64_t)n2;
+    R.owner_tab = tab_of_type[t0];
+    R.owner_lf = ft.l0;
+    R.pad = 0;
+    // owner geometry: normal and area scale
+    {
+      const auto& af = affine[ft.e0];
+      const int* fv = kFaceVerts[t0][ft.l0];
+      double ts[3], tt[3];
+      for (int d = 0; d < 3; ++d) {
+        ts[d] = tt[d] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          double A = af[3 + 3 * k + d];
+          ts[d] += 0.25 * A * (kRefVerts[t0][fv[1]][k] - kRefVerts[t0][fv[0]][k]);
+          tt[d] += 0.25 * A * (kRefVerts[t0][fv[2]][k] - kRefVerts[t0][fv[0]][k]);
+        }
+      }
+      double cr[3];
+      cross(ts, tt, cr);
+      double S = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      double fc[3] = {0, 0, 0};
+      for (int i = 0; i < nv; ++i)
+        for (int d = 0; d < 3; ++d) fc[d] += in.xyz[3 * V0[fv[i]] + d] / nv;
+      double dot = 0.0;
+      for (int d = 0; d < 3; ++d) dot += cr[d] * (fc[d] - centroid[ft.e0][d]);
+      double sgn = dot >= 0 ? 1.0 : -1.0;
+      for (int d = 0; d < 3; ++d) R.nrm[d] = sgn * cr[d] / S;
+      R.S = S;
+    }
+    // neighbour map
+    if (nv == 4) {
+      // dihedral map of the Gauss-Legendre tensor grid
+      static const int kap[4][2] = {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
+      int s0 = kap[sigma[0]][0], t0c = kap[sigma[0]][1];
+      int ax[2][2];  // for nb axis a: (owner axis, flip)
+      for (int a = 0; a < 2; ++a) {
+        int m = a == 0 ? 1 : 2;
+        int ds = kap[sigma[m]][0] - s0, dt = kap[sigma[m]][1] - t0c;
+        if (ds != 0 && dt == 0) { ax[a][0] = 0; ax[a][1] = ds < 0; }
+        else if (dt != 0 && ds == 0) { ax[a][0] = 1; ax[a][1] = dt < 0; }
+        else { *err = "quadrilateral face correspondence is not a symmetry"; return -2; }
+      }
+      if (ax[0][0] == ax[1][0]) { *err = "quadrilateral face correspondence is degenerate"; return -2; }
+      std::vector<int16_t> perm(2 * n2);
+      for (int ib = 0; ib < n; ++ib)
+        for (int ia = 0; ia < n; ++ia) {
+          int own[2] = {ia, ib};
+          int j[2];
+          for (int a = 0; a < 2; ++a) {
+            int v = own[ax[a][0]];
+            j[a] = ax[a][1] ? n - 1 - v : v;
+          }
+          int p = ia + n * ib, q = j[0] + n * j[1];
+          perm[p] = (int16_t)q;
+          perm[n2 + q] = (int16_t)p;
+        }
+      auto it = perm_ids.find(perm);
+      if (it == perm_ids.end()) {
+        it = perm_ids.emplace(perm, (int)perm_ids.size()).first;
+        M.perms.insert(M.perms.end(), perm.begin(), perm.end());
+      }
+      R.map = it->second;
+    } else if (sigma[2] == 2) {
+      // collapse vertex shared: the collapsed grid maps onto itself (alpha -> +-alpha)
+      bool flip = sigma[0] != 0;
+      std::vector<int16_t> perm(2 * n2);
+      for (int ib = 0; ib < n; ++ib)
+        for (int ia = 0; ia < n; ++ia) {
+          int p = ia + n * ib, q = (flip ? n - 1 - ia : ia) + n * ib;
+          perm[p] = (int16_t)q;
+          perm[n2 + q] = (int16_t)p;
+        }
+      auto it = perm_ids.find(perm);
+      if (it == perm_ids.end()) {
+        it = perm_ids.emplace(perm, (int)perm_ids.size()).first;
+        M.perms.insert(M.perms.end(), perm.begin(), perm.end());
+      }
+      R.map = it->second;
+    } else {
+      // general triangle correspondence: interpolate the neighbour's face
+      // values (tensor Lagrange in its collapsed face coordinates) at the
+      // owner's points, located by barycentric coordinates.
+      std::vector<int> key = {sigma[0], sigma[1], sigma[2]};
+      auto it = dense_ids.find(key);
+      if (it == dense_ids.end()) {
+        it = dense_ids.emplace(key, (int)dense_ids.size()).first;
+        std::vector<double> la(n), lb(n);
+        size_t base = M.dense.size();
+        M.dense.resize(base + (size_t)n2 * n2);
+        for (int ib = 0; ib < n; ++ib)
+          for (int ia = 0; ia < n; ++ia) {
+            double al = x[ia], be = x[ib];
+            double lam[3];
+            lam[1] = 0.25 * (1 + al) * (1 - be);
+            lam[2] = 0.5 * (1 + be);
+            lam[0] = 1.0 - lam[1] - lam[2];
+            double lp[3];
+            for (int m = 0; m < 3; ++m) lp[m] = lam[sigma[m]];
+            double alp = 2.0 * lp[1] / (1.0 - lp[2]) - 1.0;
+            double bep = 2.0 * lp[2] - 1.0;
+            lagrange_values(x, n, alp, la.data());
+            lagrange_values(x, n, bep, lb.data());
+            int p = ia + n * ib;
+            for (int jb = 0; jb < n; ++jb)
+              for (int ja = 0; ja < n; ++ja) M.dense[base + (size_t)p * n2 + ja + n * jb] = la[ja] * lb[jb];
+          }
+      }
+      R.map = -1 - it->second;
+    }
+    int64_t s0 = M.slot_of_elem[ft.e0], s1 = M.slot_of_elem[ft.e1];
+    M.slot_ftoff[(size_t)s0 * 6 + ft.l0] = R.toff;
+    M.slot_ftoff[(size_t)s1 * 6 + ft.l1] = R.toff + 5 * (int64_t)n2;
+  }
+  M.n_perm = (int)perm_ids.size();
+  M.n_dense = (int)dense_ids.size();
+  M.t_total = F * 2 * 5 * (int64_t)n2;
+  for (int64_t s = 0; s < E; ++s)
+    for (int lf = 0; lf < kNumFaces[M.slot_type[s]]; ++lf)
+      if (M.slot_ftoff[(size_t)s * 6 + lf] < 0) { *err = "internal: unassigned face"; return -1; }
+  // face blocks of up to 32 faces (uniform n)
+  M.face_blocks.clear();
+  for (int64_t f = 0; f < F; f += 32) {
+    dgk::FaceBlock b;
+    b.first = (int)f;
+    b.count = (int)std::min<int64_t>(32, F - f);
+    b.n = n;
+    b.pad = 0;
+    M.face_blocks.push_back(b);
+  }
+
+  // ---- physical quadrature points (caller order)
+  M.quad_xyz.resize((size_t)E * n * n * n * 3);
+  for (int64_t e = 0; e < E; ++e) {
+    int t = in.type[e];
+    const auto& af = affine[e];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+          double xi[3];
+          uncollapse(t, x[i], x[j], x[k], xi);
+          size_t q = (size_t)e * n * n * n + (size_t)(i * n + j) * n + k;
+          for (int d = 0; d < 3; ++d) {
+            double v = af[d];
+            for (int kk = 0; kk < 3; ++kk) v += af[3 + 3 * kk + d] * 0.5 * (xi[kk] + 1.0);
+            M.quad_xyz[3 * q + d] = v;
+          }
+        }
+  }
+  return 0;
+}
+
+}  // namespace dgh

@@ -1,0 +1,87 @@
+// Host-side set-up of the modal DG library: operator tables per (type, N),
+// mesh geometry and connectivity, Hilbert ordering.  Pure C++ (no CUDA).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dg_common.h"
+
+namespace dgh {
+
+// ----------------------------------------------------------------- 1D tools
+void gauss_legendre(int n, double* x, double* w);
+double jacobi(int n, double alpha, double beta, double x);
+double jhat(int n, int alpha, double x);  // int ((1-x)/2)^alpha jhat^2 = 1
+void lagrange_values(const double* nodes, int n, double x, double* out);
+
+// ----------------------------------------------------------------- tables
+struct Tables {
+  std::vector<double> dpool;
+  std::vector<int> ipool;
+  std::vector<dgk::TypeTab> tabs;
+  int find(int type, int N) const;
+  // returns table index or -1 with *err set
+  int add(int type, int N, std::string* err);
+};
+
+int n_modes(int type, int N);
+double factor_A(int type, int p, double a);
+double factor_B(int type, int p, int q, double b);
+double factor_C(int type, int p, int q, int r, double c);
+void uncollapse(int type, double a, double b, double c, double* xi);
+extern const double kRefVerts[4][8][3];
+extern const int kNumVerts[4];
+extern const int kNumFaces[4];
+extern const int kFaceVerts[4][6][4];
+extern const int kFaceNV[4][6];
+
+// ----------------------------------------------------------------- mesh
+struct MeshInput {
+  int64_t n_vertices;
+  const double* xyz;
+  int64_t n_elems;
+  const int8_t* type;
+  const int64_t* off;
+  const int64_t* verts;
+  const double* period;
+  int N;
+};
+
+struct HostMesh {
+  int N = 0, n = 0;
+  int64_t n_elems = 0, n_faces = 0, n_dof = 0, h_total = 0, t_total = 0;
+  int64_t type_count[4] = {0, 0, 0, 0};
+  Tables tables;
+  // per slot (Hilbert order)
+  std::vector<int64_t> elem_of_slot, slot_of_elem;
+  std::vector<int> slot_tab;                 // table index
+  std::vector<int8_t> slot_type;
+  std::vector<int64_t> slot_qoff, slot_hoff; // double offsets
+  std::vector<dgk::ElemGeo> slot_geo;
+  std::vector<int64_t> slot_ftoff;           // [slot][6] trace offset of (face, own side)
+  // per caller element
+  std::vector<int64_t> elem_qoff;            // caller-layout offsets
+  // faces (face-kernel order)
+  std::vector<dgk::FaceRec> faces;
+  std::vector<dgk::FaceBlock> face_blocks;
+  std::vector<int16_t> perms;                // [nperm][2][n^2]: perm then inverse
+  std::vector<double> dense;                 // [ndense][n^2][n^2]
+  int n_perm = 0, n_dense = 0;
+  // per-type slot lists in caller order (naive scheduler)
+  std::vector<int64_t> type_slots[4];
+  // physical quadrature points, caller order [n_elems][n^3][3]
+  std::vector<double> quad_xyz;
+  std::vector<double> x1d, w1d;
+};
+
+// returns 0 on success, -2 (mesh) / -1 (argument) / -7 (unsupported) with *err
+int build_mesh(const MeshInput& in, HostMesh* out, std::string* err);
+
+uint64_t hilbert_key3(uint32_t x, uint32_t y, uint32_t z, int bits);
+
+// Static per-element FP64 work estimate of one stage (initial chunk weights).
+double static_cost(const dgk::TypeTab& t);
+
+}  // namespace dgh

@@ -1,0 +1,602 @@
+// Kernels of the modal DG hot path; see dg_kernels.cuh for the phase layout.
+#include <cstdio>
+
+#include "dg_kernels.cuh"
+
+namespace dgk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int sel3(int i, int j, int k, int w) { return w == 0 ? i : (w == 1 ? j : k); }
+
+__device__ __forceinline__ bool finite_bits(double x) {
+  // exponent field all ones <=> inf or nan (integer test, no FP64 pipe work)
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned smid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// ------------------------------------------------------------------ physics
+// Euler normal flux F(U).n with u.n, p, 1/rho and c^2 as by-products.
+struct NState {
+  double F[5];
+  double un, p, rinv, H;
+};
+
+__device__ __forceinline__ void normal_state(const double* U, const double* n, double gamma, NState& s) {
+  s.rinv = 1.0 / U[0];
+  double u = U[1] * s.rinv, v = U[2] * s.rinv, w = U[3] * s.rinv;
+  s.p = (gamma - 1.0) * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
+  s.un = u * n[0] + v * n[1] + w * n[2];
+  s.F[0] = U[0] * s.un;
+  s.F[1] = U[1] * s.un + s.p * n[0];
+  s.F[2] = U[2] * s.un + s.p * n[1];
+  s.F[3] = U[3] * s.un + s.p * n[2];
+  s.F[4] = (U[4] + s.p) * s.un;
+  s.H = (U[4] + s.p) * s.rinv;
+}
+
+// Lax-Friedrichs: F* = (F- + F+)/2 - lambda (U+ - U-)/2,
+// lambda = max(|u-.n| + c-, |u+.n| + c+).
+__device__ __forceinline__ void flux_lf(const double* UL, const double* UR, const double* n, double gamma, double* Fs) {
+  NState L, R;
+  normal_state(UL, n, gamma, L);
+  normal_state(UR, n, gamma, R);
+  double cL = sqrt(gamma * L.p * L.rinv), cR = sqrt(gamma * R.p * R.rinv);
+  double lam = fmax(fabs(L.un) + cL, fabs(R.un) + cR);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (L.F[v] + R.F[v]) - 0.5 * lam * (UR[v] - UL[v]);
+}
+
+// Roe: F* = (F- + F+)/2 - sum_k |lambda_k| alpha_k r_k / 2 with
+// sqrt(rho)-weighted averages of u and H, no entropy fix.
+__device__ __forceinline__ void flux_roe(const double* UL, const double* UR, const double* n, double gamma, double* Fs) {
+  NState L, R;
+  normal_state(UL, n, gamma, L);
+  normal_state(UR, n, gamma, R);
+  double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  double den = 1.0 / (sL + sR);
+  double uL[3] = {UL[1] * L.rinv, UL[2] * L.rinv, UL[3] * L.rinv};
+  double uR[3] = {UR[1] * R.rinv, UR[2] * R.rinv, UR[3] * R.rinv};
+  double u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = (sL * uL[d] + sR * uR[d]) * den;
+  double H = (sL * L.H + sR * R.H) * den;
+  double rho = sL * sR;
+  double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  double c2 = (gamma - 1.0) * (H - 0.5 * q2);
+  double c = sqrt(c2);
+  double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  double drho = UR[0] - UL[0], dp = R.p - L.p;
+  double du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  double dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
+  double ic2 = 1.0 / c2;
+  double a1 = 0.5 * (dp - rho * c * dun) * ic2;
+  double a5 = 0.5 * (dp + rho * c * dun) * ic2;
+  double a2 = drho - dp * ic2;
+  double l1 = fabs(un - c) * a1, l5 = fabs(un + c) * a5, l2 = fabs(un);
+  double dut[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dut[d] = du[d] - dun * n[d];
+  double D[5];
+  D[0] = l1 + l5 + l2 * a2;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) D[1 + d] = l1 * (u[d] - c * n[d]) + l5 * (u[d] + c * n[d]) + l2 * (a2 * u[d] + rho * dut[d]);
+  double udut = u[0] * dut[0] + u[1] * dut[1] + u[2] * dut[2];
+  D[4] = l1 * (H - c * un) + l5 * (H + c * un) + l2 * (a2 * 0.5 * q2 + rho * udut);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (L.F[v] + R.F[v]) - 0.5 * D[v];
+}
+
+// ------------------------------------------------------------------ element phases
+
+// Modal -> nodal: sQ [5][nM] -> U in bufA [5][nQ]; uses bufB as scratch.
+__device__ void modal_to_nodal(const Ctx& c, const TypeTab& T, const double* sQ, double* bufA, double* bufB, int lane) {
+  const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
+  const double* dp = c.dpool;
+  const int* ip = c.ipool;
+  {
+    const int cnt = T.ncols * n;
+    for (int w = lane; w < 5 * cnt; w += 32) {
+      int v = w / cnt, o = w - v * cnt, col = o / n, k = o - col * n;
+      int len = ip[T.col_len + col];
+      const double* C = dp + T.C + ip[T.col_coff + col] + k;
+      const double* q = sQ + v * nM + ip[T.col_moff + col];
+      double acc = 0.0;
+      for (int t = 0; t < len; ++t) acc = fma(C[t * n], q[t], acc);
+      bufA[v * nQ + o] = acc;
+    }
+  }
+  __syncwarp();
+  for (int w = lane; w < 5 * nQ; w += 32) {
+    int v = w / nQ, o = w - v * nQ, p = o / n2, jk = o - p * n2, j = jk / n, k = jk - j * n;
+    int blen = ip[T.p_blen + p];
+    const double* B = dp + T.B + ip[T.p_boff + p] + j;
+    const double* X = bufA + v * nQ + ip[T.p_cbase + p] * n + k;
+    double acc = 0.0;
+    for (int t = 0; t < blen; ++t) acc = fma(B[t * n], X[t * n], acc);
+    bufB[v * nQ + o] = acc;
+  }
+  __syncwarp();
+  for (int w = lane; w < 5 * nQ; w += 32) {
+    int v = w / nQ, o = w - v * nQ, i = o / n2, jk = o - i * n2;
+    const double* A = dp + T.A + i;
+    const double* Y = bufB + v * nQ + jk;
+    double acc = 0.0;
+    for (int p = 0; p < n; ++p) acc = fma(A[p * n], Y[p * n2], acc);
+    bufA[v * nQ + o] = acc;
+  }
+  __syncwarp();
+}
+
+// Nodal -> modal transpose: bufA [5][nQ] -> r(v, mode) handed to `epi`; uses bufB.
+template <class Epi>
+__device__ void nodal_to_modal(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane, Epi&& epi) {
+  const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
+  const double* dp = c.dpool;
+  const int* ip = c.ipool;
+  for (int w = lane; w < 5 * nQ; w += 32) {
+    int v = w / nQ, o = w - v * nQ, p = o / n2, jk = o - p * n2;
+    const double* A = dp + T.A + p * n;
+    const double* Hs = bufA + v * nQ + jk;
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc = fma(A[i], Hs[i * n2], acc);
+    bufB[v * nQ + o] = acc;
+  }
+  __syncwarp();
+  {
+    const int cnt = T.ncols * n;
+    for (int w = lane; w < 5 * cnt; w += 32) {
+      int v = w / cnt, o = w - v * cnt, col = o / n, k = o - col * n;
+      int p = ip[T.col_p + col];
+      int t = col - ip[T.p_cbase + p];
+      const double* B = dp + T.B + ip[T.p_boff + p] + t * n;
+      const double* Y = bufB + v * nQ + p * n2 + k;
+      double acc = 0.0;
+      for (int j = 0; j < n; ++j) acc = fma(B[j], Y[j * n], acc);
+      bufA[v * nQ + o] = acc;
+    }
+  }
+  __syncwarp();
+  for (int w = lane; w < 5 * nM; w += 32) {
+    int v = w / nM, mode = w - v * nM;
+    int col = ip[T.mode_col + mode];
+    int t = mode - ip[T.col_moff + col];
+    const double* C = dp + T.C + ip[T.col_coff + col] + t * n;
+    const double* X = bufA + v * nQ + col * n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(C[k], X[k], acc);
+    epi(v, mode, acc * dp[T.minv + mode]);
+  }
+  __syncwarp();
+}
+
+// Forward phase of one element at slot s: nodal state, own-face traces,
+// nodal volume residual H.  sQ lives in bufG.
+__device__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG, int lane) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n;
+  const double* dp = c.dpool;
+  modal_to_nodal(c, T, bufG, bufA, bufG, lane);
+  // traces on the element's own face points
+  {
+    const int per_face = 5 * n2, cnt = T.nfaces * per_face;
+    const int64_t* ft = c.slot_ftoff + s * 6;
+    for (int w = lane; w < cnt; w += 32) {
+      int lf = w / per_face, r = w - lf * per_face, v = r / n2, p = r - v * n2;
+      int ia = p % n, ib = p / n;
+      const FaceDesc d = T.faces[lf];
+      int sa = d.alpha == 0 ? n2 : (d.alpha == 1 ? n : 1);
+      int sb = d.beta == 0 ? n2 : (d.beta == 1 ? n : 1);
+      int sf = d.fixed == 0 ? n2 : (d.fixed == 1 ? n : 1);
+      const double* e = dp + T.ext + d.end * n;
+      const double* U = bufA + v * nQ + ia * sa + ib * sb;
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc = fma(e[m], U[m * sf], acc);
+      c.T[ft[lf] + v * n2 + p] = acc;
+    }
+  }
+  // contravariant fluxes G_l at the volume points (bufG, [3][5][nQ])
+  const ElemGeo& g = c.geo[s];
+  double Jg[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+  const double gm1 = c.gamma - 1.0;
+  for (int q = lane; q < nQ; q += 32) {
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = bufA[v * nQ + q];
+    const double* wa = dp + T.wA + q * 9;
+    double M[3][3];
+    switch (T.type) {
+      case HEX: {
+        double w0 = wa[0];
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) M[l][d] = w0 * Jg[l * 3 + d];
+        break;
+      }
+      case PRISM: {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          M[0][d] = wa[0] * Jg[d] + wa[1] * Jg[3 + d];
+          M[1][d] = wa[4] * Jg[3 + d];
+          M[2][d] = wa[8] * Jg[6 + d];
+        }
+        break;
+      }
+      case PYR: {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          M[0][d] = wa[0] * Jg[d] + wa[2] * Jg[6 + d];
+          M[1][d] = wa[4] * Jg[3 + d] + wa[5] * Jg[6 + d];
+          M[2][d] = wa[8] * Jg[6 + d];
+        }
+        break;
+      }
+      default: {  // TET
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          M[0][d] = wa[0] * Jg[d] + wa[1] * Jg[3 + d] + wa[2] * Jg[6 + d];
+          M[1][d] = wa[4] * Jg[3 + d] + wa[5] * Jg[6 + d];
+          M[2][d] = wa[8] * Jg[6 + d];
+        }
+        break;
+      }
+    }
+    double rinv = 1.0 / U[0];
+    double u = U[1] * rinv, v = U[2] * rinv, w = U[3] * rinv;
+    double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
+    double Ep = U[4] + p;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double Vl = M[l][0] * u + M[l][1] * v + M[l][2] * w;
+      double* G = bufG + l * 5 * nQ + q;
+      G[0] = Vl * U[0];
+      G[nQ] = Vl * U[1] + p * M[l][0];
+      G[2 * nQ] = Vl * U[2] + p * M[l][1];
+      G[3 * nQ] = Vl * U[3] + p * M[l][2];
+      G[4 * nQ] = Vl * Ep;
+    }
+  }
+  __syncwarp();
+  // H = sum_l D_l^T G_l
+  {
+    const double* Dt = dp + T.Dt;
+    double* H = c.H + c.slot_hoff[s];
+    for (int w = lane; w < 5 * nQ; w += 32) {
+      int v = w / nQ, o = w - v * nQ, i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      const double* G0 = bufG + v * nQ + jk;
+      const double* G1 = bufG + (5 + v) * nQ + i * n2 + k;
+      const double* G2 = bufG + (10 + v) * nQ + i * n2 + j * n;
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc = fma(Dt[i * n + m], G0[m * n2], acc);
+      for (int m = 0; m < n; ++m) acc = fma(Dt[j * n + m], G1[m * n], acc);
+      for (int m = 0; m < n; ++m) acc = fma(Dt[k * n + m], G2[m], acc);
+      H[w] = acc;
+    }
+  }
+  __syncwarp();
+}
+
+// Backward phase: H minus the lifted face fluxes into bufA.
+__device__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, int lane) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
+  const double* dp = c.dpool;
+  const double* H = c.H + c.slot_hoff[s];
+  const int64_t* ft = c.slot_ftoff + s * 6;
+  for (int w = lane; w < 5 * nQ; w += 32) {
+    int v = w / nQ, o = w - v * nQ, i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+    double h = H[w];
+    for (int lf = 0; lf < nf; ++lf) {
+      const FaceDesc d = T.faces[lf];
+      int m = sel3(i, j, k, d.fixed);
+      int p = sel3(i, j, k, d.alpha) + n * sel3(i, j, k, d.beta);
+      h = fma(-dp[T.ext + d.end * n + m], c.T[ft[lf] + v * n2 + p], h);
+    }
+    bufA[w] = h;
+  }
+  __syncwarp();
+}
+
+struct ElemIO {
+  int mode;
+  StageArgs a;
+};
+
+// One element at slot s in the given mode.  smem: bufA [5 nQmax], bufG [15 nQmax].
+__device__ void process_element(const Ctx& c, const ElemIO& io, int64_t s, double* bufA, double* bufG, int lane) {
+  const int tab = c.slot_tab[s];
+  const TypeTab& T = c.tabs[tab];
+  const int nM = T.nM, nQ = T.nQ;
+  const int64_t qoff = c.slot_qoff[s];
+  const int mode = io.mode;
+  if (mode == kFwd) {
+    const double* Q = io.a.Qin + qoff;
+    for (int w = lane; w < 5 * nM; w += 32) bufG[w] = Q[w];
+    __syncwarp();
+    element_forward(c, T, s, bufA, bufG, lane);
+    return;
+  }
+  if (mode == kProject) {
+    const int64_t e = c.elem_of_slot[s];
+    const double* vals = io.a.Qin + e * 5 * (int64_t)nQ;
+    const double* W = c.dpool + T.W;
+    for (int w = lane; w < 5 * nQ; w += 32) {
+      int q = w % nQ;
+      bufA[w] = W[q] * vals[w];
+    }
+    __syncwarp();
+    double* out = io.a.Qout + qoff;
+    nodal_to_modal(c, T, bufA, bufG, lane, [&](int v, int m, double r) { out[v * nM + m] = r; });
+    return;
+  }
+  // backward modes
+  element_lift(c, T, s, bufA, lane);
+  const double invJ = c.geo[s].invJ;
+  if (mode == kBwdRhs) {
+    double* R = io.a.Qout + qoff;
+    nodal_to_modal(c, T, bufA, bufG, lane, [&](int v, int m, double r) { R[v * nM + m] = r * invJ; });
+    return;
+  }
+  const double a = io.a.a, b = io.a.b, dt = io.a.dt;
+  const double* Qi = io.a.Qin + qoff;
+  double* Qo = io.a.Qout + qoff;
+  double* K = io.a.K + qoff;
+  const bool fwd = mode == kBwdRkFwd;
+  bool bad = false;
+  nodal_to_modal(c, T, bufA, bufG, lane, [&](int v, int m, double r) {
+    int idx = v * nM + m;
+    double R = r * invJ;
+    double k = (a == 0.0) ? dt * R : fma(a, K[idx], dt * R);
+    double qn = fma(b, k, Qi[idx]);
+    K[idx] = k;
+    Qo[idx] = qn;
+    if (fwd) bufG[idx] = qn;
+    bad |= !finite_bits(qn);
+  });
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(c.status, 1u);
+  if (fwd) element_forward(c, T, s, bufA, bufG, lane);
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void elem_naive_kernel(Ctx c, ElemIO io, const int64_t* __restrict__ list, int64_t count) {
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  int64_t idx = (int64_t)blockIdx.x * wpb + warp;
+  if (idx >= count) return;
+  double* bufA = smem + (size_t)warp * 20 * c.nQmax;
+  double* bufG = bufA + 5 * c.nQmax;
+  process_element(c, io, list ? list[idx] : idx, bufA, bufG, lane);
+}
+
+__global__ void elem_balanced_kernel(Ctx c, ElemIO io, const int64_t* __restrict__ chunk_start, int64_t nchunks,
+                                     unsigned int* counter, unsigned int* next_counter) {
+  extern __shared__ double smem[];
+  // The previous launch on this stream used next_counter and has finished.
+  if (blockIdx.x == 0 && threadIdx.x == 0 && next_counter) *next_counter = 0u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* bufA = smem + (size_t)warp * 20 * c.nQmax;
+  double* bufG = bufA + 5 * c.nQmax;
+  unsigned long long ns[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, busy = 0;
+  while (true) {
+    unsigned int ch = 0;
+    if (lane == 0) ch = atomicAdd(counter, 1u);
+    ch = __shfl_sync(kFull, ch, 0);
+    if (ch >= nchunks) break;
+    for (int64_t s = chunk_start[ch]; s < chunk_start[ch + 1]; ++s) {
+      uint64_t t0 = global_ns();
+      process_element(c, io, s, bufA, bufG, lane);
+      __syncwarp();
+      uint64_t dtn = global_ns() - t0;
+      int ty = c.slot_type[s];
+      ns[ty] += dtn;
+      cnt[ty] += 1;
+      busy += dtn;
+    }
+  }
+  if (lane == 0 && c.cost) {
+    for (int t = 0; t < 4; ++t)
+      if (cnt[t]) {
+        atomicAdd(c.cost + 2 * t, ns[t]);
+        atomicAdd(c.cost + 2 * t + 1, cnt[t]);
+      }
+    if (busy) atomicAdd(c.sm_ns + smid(), busy);
+  }
+}
+
+__global__ void face_kernel(Ctx c) {
+  extern __shared__ double sF[];
+  const FaceBlock fb = c.fblocks[blockIdx.x];
+  const int n = fb.n, n2 = n * n, items = fb.count * n2;
+  const double gamma = c.gamma;
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, p = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    const double* T0 = c.T + R.toff;
+    const double* T1 = T0 + 5 * n2;
+    double UL[5], UR[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) UL[v] = T0[v * n2 + p];
+    if (R.map >= 0) {
+      int j = c.perms[(size_t)R.map * 2 * n2 + p];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) UR[v] = T1[v * n2 + j];
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + (size_t)p * n2;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int j = 0; j < n2; ++j) acc = fma(D[j], T1[v * n2 + j], acc);
+        UR[v] = acc;
+      }
+    }
+    double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+    double Fs[5];
+    if (c.flux == 0) flux_lf(UL, UR, nrm, gamma, Fs);
+    else flux_roe(UL, UR, nrm, gamma, Fs);
+    const TypeTab& T = c.tabs[R.owner_tab];
+    double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, q = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    double* T0 = c.T + R.toff;
+    double* T1 = T0 + 5 * n2;
+    const double* F = sF + fl * 5 * n2;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) T0[v * n2 + q] = F[v * n2 + q];
+    if (R.map >= 0) {
+      int p = c.perms[(size_t)R.map * 2 * n2 + n2 + q];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) T1[v * n2 + q] = -F[v * n2 + p];
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + q;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int p = 0; p < n2; ++p) acc = fma(D[(size_t)p * n2], F[v * n2 + p], acc);
+        T1[v * n2 + q] = -acc;
+      }
+    }
+  }
+}
+
+// Storage <-> caller layout copies (warp per element).
+__global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __restrict__ dst, int64_t E, int to_storage) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (s >= E) return;
+  const int nM = c.tabs[c.slot_tab[s]].nM;
+  int64_t so = c.slot_qoff[s], eo = c.elem_qoff[c.elem_of_slot[s]];
+  const double* a = src + (to_storage ? eo : so);
+  double* b = dst + (to_storage ? so : eo);
+  for (int w = lane; w < 5 * nM; w += 32) b[w] = a[w];
+}
+
+// FP64 throughput probes.
+__global__ void dfma_probe_kernel(double* out, int iters, double s) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], s, 1e-7);
+  }
+  double t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+__global__ void dmma_probe_kernel(double* out, int iters) {
+  double a = 1e-3 * (threadIdx.x & 7), b = 1e-3 * (threadIdx.x >> 3);
+  double c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(c0[k]), "+d"(c1[k])
+                   : "d"(a), "d"(b));
+  }
+  double t = 0;
+  for (int k = 0; k < 4; ++k) t += c0[k] + c1[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+}  // namespace
+
+int element_smem_bytes(int nQmax, int wpb) { return wpb * 20 * nQmax * (int)sizeof(double); }
+int face_block_threads(int n) { return 32 * n; }
+
+cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
+  int bytes = element_smem_bytes(nQmax, wpb);
+  cudaError_t e = cudaFuncSetAttribute(elem_naive_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(elem_balanced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
+  e = cudaFuncSetAttribute(face_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fbytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel, 32 * wpb, bytes);
+}
+
+void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb,
+                    cudaStream_t st) {
+  ElemIO io{mode, a};
+  int bytes = element_smem_bytes(c.nQmax, wpb);
+  if (balanced) {
+    elem_balanced_kernel<<<grid, 32 * wpb, bytes, st>>>(c, io, s.chunk_start, s.count, s.counter, s.next_counter);
+  } else {
+    if (s.count <= 0) return;
+    int64_t blocks = (s.count + wpb - 1) / wpb;
+    elem_naive_kernel<<<(unsigned)blocks, 32 * wpb, bytes, st>>>(c, io, s.list, s.count);
+  }
+}
+
+void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  int bytes = 32 * 5 * n * n * (int)sizeof(double);
+  face_kernel<<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+}
+
+void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st) {
+  const int wpb = 4;
+  int64_t blocks = (E + wpb - 1) / wpb;
+  permute_kernel<<<(unsigned)blocks, 32 * wpb, 0, st>>>(c, src, dst, E, to_storage);
+}
+
+cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 4, threads = 128;
+  double* out = nullptr;
+  e = cudaMalloc(&out, sizeof(double) * blocks * threads);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms = 0.f;
+  const int it1 = 4000, it2 = 1000;
+  dfma_probe_kernel<<<blocks, threads>>>(out, 10, 1.0000001);
+  cudaEventRecord(e0);
+  dfma_probe_kernel<<<blocks, threads>>>(out, it1, 1.0000001);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  *dfma_tflops = 2.0 * 8 * it1 * (double)blocks * threads / (ms * 1e-3) / 1e12;
+  dmma_probe_kernel<<<blocks, threads>>>(out, 10);
+  cudaEventRecord(e0);
+  dmma_probe_kernel<<<blocks, threads>>>(out, it2);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  *dmma_tflops = 2.0 * 8 * 8 * 4 * 4 * it2 * (double)blocks * (threads / 32) / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e = cudaGetLastError();
+  cudaFree(out);
+  return e;
+}
+
+}  // namespace dgk

@@ -1,0 +1,86 @@
+// Device side of the modal DG hot path (sm_103a, FP64).
+//
+// Per RK stage the residual of Eq. 1 is evaluated in three phases:
+//   forward  (element kernel)  Q -> nodal U = V Q on the collapsed grid (three
+//            sum-factorised passes), traces of U on the element's own face
+//            points, contravariant fluxes G_l = w J (da_l/dxi) (dxi/dx) F(U)
+//            and the nodal volume residual H = sum_l D_l^T G_l (collocation
+//            derivative, exact because every 1D factor has degree <= N);
+//   faces    (face kernel)     Riemann flux (LF or Roe) at the owner's points,
+//            scaled by w S; the neighbour's share is mapped back to its own
+//            points (permutation or interpolation);
+//   backward (element kernel)  H -= sum_faces E_f^T Fhat_f, then V^T H by the
+//            transposed passes, times the diagonal M_ref^{-1} and 1/J, and the
+//            fused LSERK update K <- a K + dt R, Q <- Q + b K.
+// The backward phase of stage s is fused with the forward phase of stage s+1.
+// One warp owns one element at a time; all work inside an element is spread
+// over (variable, output) pairs so the 32 lanes stay busy for every N.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dg_common.h"
+
+namespace dgk {
+
+enum ElemMode : int {
+  kFwd = 0,        // forward only (prime a stage)
+  kBwdRhs = 1,     // backward, write R
+  kBwdRk = 2,      // backward + LSERK update
+  kBwdRkFwd = 3,   // backward + LSERK update + forward of the new state
+  kProject = 4,    // Algorithm 1 projection of point values
+  kGather = 5,     // copy caller layout -> storage layout
+  kScatter = 6     // copy storage layout -> caller layout
+};
+
+struct Ctx {
+  const double* dpool;
+  const int* ipool;
+  const TypeTab* tabs;
+  const int* slot_tab;
+  const int8_t* slot_type;
+  const int64_t* slot_qoff;
+  const int64_t* slot_hoff;
+  const int64_t* slot_ftoff;   // [slot][6]
+  const int64_t* elem_of_slot;
+  const int64_t* elem_qoff;    // caller layout offsets
+  const ElemGeo* geo;
+  double* H;
+  double* T;
+  const FaceRec* faces;
+  const FaceBlock* fblocks;
+  const int16_t* perms;
+  const double* dense;
+  unsigned int* status;        // bit 0: non-finite state seen
+  unsigned long long* cost;    // [4 types][2]: ns, count
+  unsigned long long* sm_ns;   // [num SMs]
+  double gamma;
+  int flux;                    // 0 LF, 1 Roe
+  int nQmax;
+};
+
+struct StageArgs {
+  const double* Qin;   // state (storage layout) or point values / ext state
+  double* Qout;        // updated state (may alias Qin) or R / storage output
+  double* K;           // LSERK register
+  double a, b, dt;     // K <- a K + dt R (a == 0: K <- dt R), Q <- Q + b K
+};
+
+struct Sched {
+  const int64_t* list;         // naive: slots of one type in caller order
+  int64_t count;               // naive: number of list entries / balanced: n chunks
+  const int64_t* chunk_start;  // balanced: [count + 1] slot ranges
+  unsigned int* counter;       // balanced: atomic queue head (zero at launch)
+  unsigned int* next_counter;  // balanced: zeroed by this launch for the next one
+};
+
+void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid,
+                    int warps_per_block, cudaStream_t st);
+void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
+void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st);
+int element_smem_bytes(int nQmax, int warps_per_block);
+int face_block_threads(int n);
+cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm);
+cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops);
+
+}  // namespace dgk

@@ -1,0 +1,202 @@
+"""GPU parity of the forward hot path against the CPU oracle, through the C ABI:
+dg_rhs (Eq. 1 residual), dg_rk_step (LSERK(5,4)), dg_project (Algorithm 1),
+the state permutations, scheduler equivalence, free-stream preservation, and a
+sampled check at the 16^3 mixed N=4 size in the configuration the benchmark
+times.  Tolerance: relative L-infinity per variable <= 1e-11."""
+import numpy as np
+import pytest
+
+import dg_inputs as di
+from gpu_util import TOL, make_box, rel_err, var_index
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_08020_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def setup(dg, kind, m, N, flux="lf", reorder=None, seed=1, scheduler="balanced"):
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    box = make_box(kind, m, seed=seed, reorder=reorder)
+    o = Oracle(from_box(box, N), flux=flux)
+    mesh = dg.Mesh(box, N, flux=flux, scheduler=scheduler)
+    return box, o, mesh
+
+
+def state(o, seed=3, amp=0.05):
+    return o.project(lambda x: di.perturbed_tgv_state(x, seed=seed, amp=amp))
+
+
+CASES = [("mixed", 4, 3, "lf", None), ("mixed", 4, 3, "roe", None), ("kuhn", 2, 3, "lf", 7),
+         ("kuhn", 2, 2, "roe", 7), ("mixed", 3, 2, "lf", 5), ("mixed", 2, 4, "roe", 5),
+         ("hex", 2, 5, "lf", 3), ("prism", 2, 5, "roe", 3), ("pyramid", 2, 1, "lf", None),
+         ("kuhn", 2, 5, "lf", 11), ("mixed", 3, 1, "roe", 2)]
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder", CASES)
+def test_rhs_parity(dg, kind, m, N, flux, reorder):
+    box, o, mesh = setup(dg, kind, m, N, flux, reorder)
+    Q = state(o)
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    R = mesh.get_state(mesh.rhs(Qs))
+    Rref = o.rhs(Q)
+    err = rel_err(R, Rref, var_index(o.mesh.nM))
+    assert err < TOL, err
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder,nsteps", [("mixed", 4, 3, "lf", None, 1), ("kuhn", 2, 3, "roe", 7, 2),
+                                                          ("mixed", 2, 4, "lf", 5, 1)])
+def test_rk_step_parity(dg, kind, m, N, flux, reorder, nsteps):
+    box, o, mesh = setup(dg, kind, m, N, flux, reorder)
+    Q = state(o)
+    dt = 1e-3
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    K = mesh.empty().fill_(float("nan"))    # the K input is ignored
+    mesh.rk_step(Qs, K, dt, nsteps)
+    Qg = mesh.get_state(Qs)
+    Qref = o.run(Q, dt, nsteps)
+    # the step changes Q by O(dt R); compare the increments
+    err = rel_err(Qg - Q, Qref - Q, var_index(o.mesh.nM))
+    assert err < 1e-10, err
+    assert rel_err(Qg, Qref, var_index(o.mesh.nM)) < TOL
+    mesh.sync()
+
+
+@pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 4, 3, None), ("kuhn", 2, 4, 7), ("hex", 2, 2, 1)])
+def test_project_parity(dg, kind, m, N, reorder):
+    box, o, mesh = setup(dg, kind, m, N, "lf", reorder)
+    n = N + 1
+    xyz = mesh.quad_points()
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Qs = mesh.project(torch.from_numpy(vals).cuda())
+    Qg = mesh.get_state(Qs)
+    Qref = o.project(di.tgv_state)
+    assert rel_err(Qg, Qref, var_index(o.mesh.nM)) < TOL
+
+
+def test_state_roundtrip_and_layout(dg):
+    box, o, mesh = setup(dg, "mixed", 3, 3, "lf", 4)
+    Q = di.random_vector(mesh.n_dof, seed=1)
+    Qs = mesh.set_state(Q)                                   # host path
+    back = mesh.get_state(Qs)
+    assert np.array_equal(back, Q)
+    Qs2 = mesh.set_state(torch.from_numpy(Q).cuda())         # device path
+    assert torch.equal(Qs, Qs2)
+    out = torch.empty(mesh.n_dof, dtype=torch.float64, device="cuda")
+    mesh.get_state(Qs2, out=out)
+    assert np.array_equal(out.cpu().numpy(), Q)
+    # storage layout: element e's block sits at its Hilbert slot
+    st = Qs.cpu().numpy()
+    nM = o.mesh.nM
+    slot_off = np.zeros(box.n_elems + 1, dtype=np.int64)
+    order = np.argsort(mesh.slot_of_elem)
+    slot_off[1:] = np.cumsum(5 * nM[order])
+    for e in (0, box.n_elems // 2, box.n_elems - 1):
+        s = mesh.slot_of_elem[e]
+        assert np.array_equal(st[slot_off[s]:slot_off[s + 1]], Q[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]])
+
+
+@pytest.mark.parametrize("flux", ["lf", "roe"])
+def test_balanced_equals_naive_bitwise(dg, flux):
+    box = make_box("mixed", 6, seed=2)
+    N = 3
+    a = dg.Mesh(box, N, flux=flux, scheduler="balanced")
+    b = dg.Mesh(box, N, flux=flux, scheduler="naive")
+    from oracle.elements import n_modes
+    nM = [n_modes(int(t), N) for t in box.etype]
+    Q = di.random_modal_state(nM, seed=4)
+    Qa = a.set_state(Q)
+    Qb = b.set_state(Q)
+    assert torch.equal(a.get_state(a.rhs(Qa), out=torch.empty_like(Qa)), b.get_state(b.rhs(Qb), out=torch.empty_like(Qb)))
+    Ka, Kb = a.empty(), b.empty()
+    a.rk_step(Qa, Ka, 1e-3, 3)
+    b.rk_step(Qb, Kb, 1e-3, 3)
+    assert torch.equal(a.get_state(Qa, out=torch.empty_like(Qa)), b.get_state(Qb, out=torch.empty_like(Qb)))
+    a.set_scheduler("naive")
+    Qc = a.set_state(Q)
+    a.rk_step(Qc, Ka, 1e-3, 3)
+    assert torch.equal(Qc, a.set_state(a.get_state(Qa)))
+
+
+@pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 3, 4, 1), ("kuhn", 2, 3, 2)])
+def test_free_stream_gpu(dg, kind, m, N, reorder):
+    box, o, mesh = setup(dg, kind, m, N, "roe", reorder)
+    U0 = np.array([1.2, 0.3, -0.2, 0.1, 3.0])
+    Q = o.project(lambda x: np.tile(U0[:, None], (1, x.shape[0])))
+    R = mesh.get_state(mesh.rhs(mesh.set_state(Q)))
+    # scale of the individual volume / face terms: |F| / h ~ 3 / (2 pi / m)
+    assert np.abs(R).max() < 1e-12 * 3.0 * m / (2 * np.pi) * 100
+
+
+def test_conservation_gpu(dg):
+    box, o, mesh = setup(dg, "mixed", 4, 3, "roe", 6)
+    Q = state(o)
+    Qs = mesh.set_state(Q)
+    R = mesh.get_state(mesh.rhs(Qs))
+    tot = sum(o.integrate(R, e) for e in range(box.n_elems))
+    scale = max(np.abs(o.integrate(np.abs(R), e)).max() for e in range(box.n_elems))
+    assert np.abs(tot).max() < 1e-13 * scale * box.n_elems
+    K = mesh.empty()
+    before = sum(o.integrate(Q, e) for e in range(box.n_elems))
+    mesh.rk_step(Qs, K, 2e-3, 2)
+    after = sum(o.integrate(mesh.get_state(Qs), e) for e in range(box.n_elems))
+    assert np.abs(after - before).max() < 1e-12 * np.abs(before).max()
+
+
+def test_full_size_sampled_parity(dg):
+    """16^3 mixed hex/prism/pyramid mesh at N = 4 (the benchmark workload),
+    balanced scheduler: dg_rhs on every element, checked against the oracle on
+    a seeded sample of elements; plus conservation of one graph-replayed
+    LSERK step, and bitwise equality with the naive scheduler."""
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    box = make_box("mixed", 16, seed=2)
+    N = 4
+    o = Oracle(from_box(box, N), flux="lf")
+    mesh = dg.Mesh(box, N, flux="lf", scheduler="balanced")
+    n = N + 1
+    xyz = mesh.quad_points()
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Qs = mesh.project(torch.from_numpy(vals).cuda())
+    Q = mesh.get_state(Qs)
+    R = mesh.get_state(mesh.rhs(Qs))
+    rng = np.random.default_rng(2)
+    sample = np.sort(rng.choice(box.n_elems, size=48, replace=False))
+    Rref = o.rhs(Q, elems=sample)
+    mask = np.zeros(mesh.n_dof, dtype=bool)
+    for e in sample:
+        mask[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = True
+    vidx = var_index(o.mesh.nM)
+    assert rel_err(R, Rref, vidx, mask) < TOL
+    # the same inputs projected by the oracle agree with dg_project
+    Qo = np.zeros_like(Q)
+    for e in sample[:8]:
+        op = o.ops[o.mesh.etype[e]]
+        q = di.tgv_state(o.quad_points(e))
+        r = o.mesh.J[e] * (q * op.w) @ op.V
+        Qo[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
+    m8 = np.zeros(mesh.n_dof, dtype=bool)
+    for e in sample[:8]:
+        m8[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = True
+    assert rel_err(Q, Qo, vidx, m8) < TOL
+    # one LSERK step in the benchmark's configuration: conservation
+    K = mesh.empty()
+    Q2 = Qs.clone()
+    mesh.rk_step(Q2, K, 1e-3, 1)
+    mesh.sync()
+    Qafter = mesh.get_state(Q2)
+    tb = sum(o.integrate(Q, e) for e in range(0, box.n_elems))
+    ta = sum(o.integrate(Qafter, e) for e in range(0, box.n_elems))
+    assert np.abs(ta - tb).max() < 1e-12 * np.abs(tb).max()
+    naive = dg.Mesh(box, N, flux="lf", scheduler="naive")
+    Q3 = naive.set_state(Q)
+    naive.rk_step(Q3, naive.empty(), 1e-3, 1)
+    assert np.array_equal(naive.get_state(Q3), Qafter)

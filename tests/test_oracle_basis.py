@@ -108,3 +108,47 @@ def test_collapse_roundtrip():
         x = uncollapse(t, a, b, c)
         a2, b2, c2 = collapse(t, *x)
         assert np.allclose([a2, b2, c2], [a, b, c], atol=1e-13)
+
+
+def test_jacobi_against_exact_sum():
+    """P_n^(a,b) from the recurrence vs its explicit finite sum
+    sum_s C(n+a, n-s) C(n+b, s) ((x-1)/2)^s ((x+1)/2)^(n-s) evaluated with 50
+    significant digits (mpmath), for the orders and weights the bases use."""
+    mp = pytest.importorskip("mpmath")
+    from oracle.elements import jacobi
+    mp.mp.dps = 50
+    xs = np.linspace(-0.99, 0.99, 23)
+    worst = 0.0
+    for n in range(0, 7):
+        for a in range(0, 15):
+            for b in (0, 1):
+                got = jacobi(n, a, b, xs)
+                for x, g in zip(xs, got):
+                    X = mp.mpf(float(x))
+                    ref = sum(mp.binomial(n + a, n - s) * mp.binomial(n + b, s) * ((X - 1) / 2) ** s * ((X + 1) / 2) ** (n - s)
+                              for s in range(n + 1))
+                    worst = max(worst, abs(g - float(ref)) / max(1.0, abs(float(ref))))
+    assert worst < 2e-14
+
+
+def test_neighbour_points_are_face_points():
+    """The neighbour's reference coordinates of the owner's face points, found
+    by inverting its affine map, form the neighbour's own face point set when
+    the face rule is symmetric (quadrilaterals; triangles sharing the collapse
+    vertex) and always lie on the neighbour's face."""
+    import dg_inputs as di
+    from oracle.mesh import from_box
+    from oracle.quadrature import face_rule
+    for kind, m in (("mixed", 3), ("kuhn", 2)):
+        box = di.reorder_vertices(di.box_mesh(m, kind, seed=1), seed=4)
+        mesh = from_box(box, 3)
+        for f, (e0, l0, e1, l1) in enumerate(mesh.faces):
+            _, ref1, _, _ = mesh.face_geometry(f)
+            fv = FACES[mesh.etype[e1]][l1]
+            C = REF_VERTS[mesh.etype[e1]][fv]
+            nrm = np.cross(C[1] - C[0], C[2] - C[0])
+            assert np.abs((ref1 - C[0]) @ nrm).max() < 1e-14
+            if len(fv) == 4:
+                own, _, _, _ = face_rule(mesh.etype[e1], l1, 3)
+                d = np.abs(ref1[:, None, :] - own[None, :, :]).sum(-1).min(1)
+                assert d.max() < 1e-14
