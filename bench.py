@@ -1,0 +1,451 @@
+"""Benchmark of the modal DG hot path on GB300.
+
+Workload (one "step" = one LSERK(5,4) time step = 5 RHS evaluations + stage
+updates): periodic [-pi, pi]^3 box of 16^3 cubes, mixed hexahedra / prisms /
+pyramids (seeded recipe of dg_inputs, seed 2), N = 4, compressible Euler,
+Taylor-Green vortex state, LF flux, dt from CFL 0.5, FP64.  The inputs are
+resident in HBM; the working set (state, register, nodal residual, face
+buffers: ~180 MB) exceeds the 129 MB L2, so no flush is needed between steps.
+
+Metric: FP64 DOF-updates/s per RK stage (DOF = sum of modal coefficients per
+variable, the paper's performance-index denominator, Sec. 4), for the
+SFC-balanced persistent scheduler; the naive per-type scheduler, the Roe flux,
+the end-to-end rate through host buffers and the roofline of the dominant
+kernel are reported beside it.  --impl reference times the CPU oracle (the
+reference arm of this benchmark) on a bounded sample of the same workload.
+
+Under torchrun (N > 1) every rank advances its own independent copy of the
+workload (instance-parallel replicas; no data-path collective), the timed
+region is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+# The CPU legs (oracle timing) run single-threaded; set before NumPy loads.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import dg_inputs as di  # noqa: E402
+
+MESH_M, MESH_SEED, N_DEG, CFL = 16, 2, 4, 0.5
+GAMMA = 1.4
+WORKLOAD = "16^3-cube periodic box, mixed hex/prism/pyramid (seed 2), N=4, Euler TGV (Ma 0.1), LF, CFL 0.5, FP64"
+
+
+# ----------------------------------------------------------------------------- model
+def n_modes(t, N):
+    n = N + 1
+    return {0: n ** 3, 1: n * n * (n + 1) // 2, 2: n * (n + 1) * (2 * n + 1) // 6, 3: n * (n + 1) * (n + 2) // 6}[t]
+
+
+def element_flops(t, N):
+    """Algorithmic FP64 flops of one element for one stage in the schedule the
+    kernels implement (FMA = 2 flops; division and square root count 1):
+    modal->nodal and nodal->modal sum-factorised passes, collocation volume
+    derivative (3 n^4 per variable), face traces and lifts (n^3 per face and
+    variable each), contravariant flux per volume point, diagonal mass
+    projection and the LSERK update."""
+    n = N + 1
+    nM = n_modes(t, N)
+    T = n * (n + 1) // 2
+    ncols = n * n if t in (0, 2) else T
+    bsum = n * n * (n * n if t in (0, 2) else T)          # sum_p blen(p) n^2
+    fwd = n * nM + bsum + n ** 4                            # c, b, a passes
+    bwd = n ** 4 + ncols * n * n + nM * n                   # a^T, b^T, c^T
+    nf = (6, 5, 5, 4)[t]
+    macs_per_var = fwd + bwd + 3 * n ** 4 + 2 * nf * n ** 3
+    metric = (9, 15, 21, 27)[t]
+    pointwise = n ** 3 * (61 + metric)
+    epilogue = 5 * nM * (2 + 5)
+    return 2 * 5 * macs_per_var + pointwise + epilogue
+
+
+FACE_POINT_FLOPS = {"lf": 101, "roe": 214}
+
+
+def element_bytes(t, N):
+    """Algorithmic HBM bytes of one element for one stage: Q, K read and
+    written, the nodal residual H written and read back, own-face traces
+    written and face fluxes read back, geometry."""
+    n = N + 1
+    nM = n_modes(t, N)
+    nf = (6, 5, 5, 4)[t]
+    return 8 * (4 * 5 * nM + 2 * 5 * n ** 3 + 2 * nf * 5 * n * n + 10)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def build_workload(flux="lf"):
+    box = di.box_mesh(MESH_M, "mixed", seed=MESH_SEED)
+    return box
+
+
+def tgv_dt(box, mesh_xyz, N):
+    """dt = CFL * min_e h_e / ((2N+1) max_q(|u| + c)), h_e = 6 Vol / Area(boundary),
+    evaluated once from the initial state (all cubes have the same size, so
+    the smallest h is the pyramid's)."""
+    h_cube = 2 * math.pi / MESH_M
+    # pyramid with a cube face as base and the cube centre as apex
+    vol = h_cube ** 3 / 6.0
+    slant = 0.5 * h_cube * math.sqrt(h_cube ** 2 / 4 + h_cube ** 2 / 4)
+    area = h_cube ** 2 + 4 * slant
+    h_min = 6 * vol / area
+    rho, u, v, w, p = di.tgv_primitive(mesh_xyz)
+    smax = float(np.max(np.sqrt(u * u + v * v + w * w) + np.sqrt(GAMMA * p / rho)))
+    return CFL * h_min / ((2 * N + 1) * smax)
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle timed on this host on a bounded sample of the workload:
+    each step evaluates the oracle residual 5 times (one LSERK step's worth)
+    on a fixed seeded sample of elements (with all their faces)."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    box = build_workload()
+    if True:
+        o = Oracle(from_box(box, N_DEG), flux=args.flux)
+        rng = np.random.default_rng(0)
+        sample = np.sort(rng.choice(box.n_elems, size=args.ref_sample, replace=False))
+        Q = np.zeros(o.mesh.n_dof())
+        # TGV projected on the sampled elements and their face neighbours
+        touched = set(sample.tolist())
+        for e in sample:
+            for f, _ in o.mesh.elem_faces[e]:
+                e0, _, e1, _ = o.mesh.faces[f]
+                touched.update((e0, e1))
+        for e in touched:
+            op = o.ops[o.mesh.etype[e]]
+            q = di.tgv_state(o.quad_points(e))
+            r = o.mesh.J[e] * (q * op.w) @ op.V
+            Q[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
+        dof = int(sum(o.mesh.nM[e] for e in sample))
+
+        def step():
+            for _ in range(5):
+                o.rhs(Q, elems=sample)
+
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        dt = time.perf_counter() - t0
+    value = dof * 5 * args.steps / dt
+    sample_txt = f"{args.ref_sample} of {box.n_elems} elements (seeded), 5 residual evaluations per step"
+    line = {"metric": "FP64 RHS DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
+            "impl": "reference", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "flux": args.flux, "sample": sample_txt},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample_txt},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(flux, seconds=12.0):
+    """Oracle residual throughput on a bounded sample (about `seconds` of CPU work, 1 thread)."""
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    box = build_workload()
+    if True:
+        o = Oracle(from_box(box, N_DEG), flux=flux)
+        rng = np.random.default_rng(1)
+        order = rng.permutation(box.n_elems)
+        Q = np.zeros(o.mesh.n_dof())
+        for e in range(box.n_elems):
+            op = o.ops[o.mesh.etype[e]]
+            q = di.tgv_state(o.quad_points(e))
+            r = o.mesh.J[e] * (q * op.w) @ op.V
+            Q[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
+        done, dof, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds and done < box.n_elems:
+            batch = np.sort(order[done:done + 32])
+            o.rhs(Q, elems=batch)
+            dof += int(sum(o.mesh.nM[e] for e in batch))
+            done += len(batch)
+        dt = time.perf_counter() - t0
+    return {"value": dof / dt, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"one residual evaluation of {done} of {box.n_elems} elements (seeded order), 1 thread, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_2511_08020_gb300 as dg
+    dg.load()
+    box = build_workload()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(flux, sched):
+        mesh = dg.Mesh(box, N_DEG, flux=flux, scheduler=sched)
+        n = N_DEG + 1
+        xyz = mesh.quad_points()
+        vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+        Q0 = mesh.project(torch.from_numpy(vals).to(dev))
+        return mesh, Q0, xyz
+
+    mesh, Q0, xyz = make(args.flux, "balanced")
+    dt = tgv_dt(box, xyz, N_DEG)
+    dof = int(sum(n_modes(int(t), N_DEG) for t in box.etype))
+    counts = mesh.type_counts
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_steps(m, Q, K, steps, warmup, profile=False):
+        m.set_profiling(profile)
+        for _ in range(warmup):
+            m.rk_step(Q, K, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        elem_ms = face_ms = 0.0
+        nel = nfa = 0
+        e0.record(stream)
+        for _ in range(steps):
+            m.rk_step(Q, K, dt, 1)
+            if profile:
+                a, b, c, d = m.phase_times()
+                elem_ms += a
+                face_ms += b
+                nel += c
+                nfa += d
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        return ms, (elem_ms, face_ms, nel, nfa)
+
+    # main measurement: balanced scheduler, LF
+    Q = Q0.clone()
+    K = torch.empty_like(Q)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, _ = timed_steps(mesh, Q, K, args.steps, args.warmup)
+    clk = clocks.stop()
+    mesh.sync()
+    value = ws * dof * 5 * args.steps / (ms * 1e-3)
+
+    # kernel split (events inside the replayed graph), same workload
+    Qp = Q0.clone()
+    msp, (elem_ms, face_ms, nel, nfa) = timed_steps(mesh, Qp, K, max(2, args.steps // 2), 1, profile=True)
+    mesh.set_profiling(False)
+    steps_p = max(2, args.steps // 2)
+    el_flops_stage = sum(element_flops(int(t), N_DEG) for t in box.etype)
+    face_flops_stage = mesh.n_faces * (N_DEG + 1) ** 2 * FACE_POINT_FLOPS[args.flux]
+    el_bytes_stage = sum(element_bytes(int(t), N_DEG) for t in box.etype)
+    # element work per step is exactly 5 stages (a forward-only prime, 4 fused
+    # backward+forward phases and a backward-only last phase)
+    elem_tflops = el_flops_stage * 5 * steps_p / (elem_ms * 1e-3) / 1e12
+    face_tflops = face_flops_stage * 5 * steps_p / (face_ms * 1e-3) / 1e12
+    total_tflops = (el_flops_stage + face_flops_stage) * 5 * args.steps / (ms * 1e-3) / 1e12 / ws
+
+    dfma, dmma = dg.probe_fp64_peak()
+    nominal = 1.25
+
+    # naive scheduler and Roe flux, same workload and state
+    mesh.set_scheduler("naive")
+    Qn = Q0.clone()
+    ms_naive, _ = timed_steps(mesh, Qn, K, args.steps, args.warmup)
+    mesh.set_scheduler("static")
+    Qst = Q0.clone()
+    ms_static, _ = timed_steps(mesh, Qst, K, args.steps, args.warmup)
+    mesh.set_scheduler("balanced")
+    mesh.set_stage_fusion(False)
+    Qsp = Q0.clone()
+    ms_split, _ = timed_steps(mesh, Qsp, K, args.steps, args.warmup)
+    mesh.set_stage_fusion(True)
+    split_value = ws * dof * 5 * args.steps / (ms_split * 1e-3)
+    naive_value = ws * dof * 5 * args.steps / (ms_naive * 1e-3)
+    static_value = ws * dof * 5 * args.steps / (ms_static * 1e-3)
+    same_bits = bool(torch.equal(Qn, Q)) and bool(torch.equal(Qst, Q)) and bool(torch.equal(Qsp, Q))
+
+    roe_mesh, Q0r, _ = make("roe", "balanced")
+    Qr = Q0r.clone()
+    ms_roe, _ = timed_steps(roe_mesh, Qr, torch.empty_like(Qr), args.steps, args.warmup)
+    roe_value = ws * dof * 5 * args.steps / (ms_roe * 1e-3)
+    roe_mesh.set_scheduler("naive")
+    Qrn = Q0r.clone()
+    ms_roe_naive, _ = timed_steps(roe_mesh, Qrn, torch.empty_like(Qr), args.steps, args.warmup)
+    roe_naive_value = ws * dof * 5 * args.steps / (ms_roe_naive * 1e-3)
+
+    # measured per-type cost table from the balanced kernels
+    ns_type, imb = mesh.cost_table()
+
+    # end to end through the C ABI with host buffers: H2D of the state, one step, D2H of the state
+    host_in = torch.from_numpy(mesh.get_state(Q0)).pin_memory()
+    host_out = torch.empty(mesh.n_dof, dtype=torch.float64).pin_memory()
+    Qe = mesh.empty()
+    Ke = torch.empty_like(Qe)
+    for _ in range(args.warmup):
+        mesh.set_state(host_in, Qe)
+        mesh.rk_step(Qe, Ke, dt, 1)
+        mesh.get_state(Qe, out=host_out)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mesh.set_state(host_in, Qe)
+        mesh.rk_step(Qe, Ke, dt, 1)
+        mesh.get_state(Qe, out=host_out)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = ws * dof * 5 * args.steps / e2e_s
+
+    gpu_launches = args.steps * (1 + 5 * 2)  # per step: forward prime + 5 x (face + element)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "FP64 RHS DOF-updates/s per RK stage (balanced vs naive); adjoint/forward cost",
+        "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": box.n_elems, "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), counts)),
+                   "faces": mesh.n_faces, "dof_per_var": dof, "dt": dt, "flux": args.flux, "scheduler": "balanced",
+                   "l2": "working set ~180 MB > 129 MB L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "naive": {"value": naive_value, "ms_per_step": ms_naive / args.steps},
+        "static": {"value": static_value, "ms_per_step": ms_static / args.steps},
+        "balanced_unfused_stages": {"value": split_value, "ms_per_step": ms_split / args.steps},
+        "schedulers_bitwise_equal": same_bits,
+        "balanced_over_naive": value / naive_value,
+        "balanced_over_static": value / static_value,
+        "roe": {"balanced": roe_value, "naive": roe_naive_value, "balanced_over_naive": roe_value / roe_naive_value},
+        "pid_ns_per_dof_stage": 1e9 / (value / ws),
+        "roofline": {"bound": "alu", "kernel": "element kernel (balanced, fused backward+LSERK+forward)",
+                     "achieved": elem_tflops, "peak": dfma, "unit": "TFLOP/s", "frac": elem_tflops / dfma,
+                     "peak_kind": "measured FP64 DFMA loop, this run (dg_probe_fp64_peak)",
+                     "peak_nominal": nominal, "frac_of_nominal": elem_tflops / nominal,
+                     "traffic": None,
+                     "algorithmic_bytes_per_stage": el_bytes_stage, "algorithmic_flops_per_stage": el_flops_stage,
+                     "element_ms_per_step": elem_ms / steps_p, "face_ms_per_step": face_ms / steps_p,
+                     "face_kernel_tflops": face_tflops, "whole_step_tflops": total_tflops,
+                     "dmma_peak_measured": dmma},
+        "cost_table_ns_per_elem": dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns_type])),
+        "sm_load_imbalance": imb,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 8 * mesh.n_dof,
+                "d2h_bytes_per_step": 8 * mesh.n_dof},
+        "gpu_launches": gpu_launches,
+        "adjoint_over_forward": None,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--flux", default="lf", choices=["lf", "roe"])
+    ap.add_argument("--ref-sample", type=int, default=48)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -71,7 +71,7 @@ typedef enum {
 } dg_status;
 
 typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1 } dg_flux;
-typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1 } dg_scheduler;
+typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1, DG_SCHED_STATIC = 2 } dg_scheduler;
 
 /* Mesh description, caller-owned, read only during dg_mesh_create.
  * Elements are affine images of the reference elements; the local vertex
@@ -161,10 +161,24 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
                     const double* QKbar, double* Q0bar, cudaStream_t stream);
 
 /* Scheduler of the element kernels: DG_SCHED_BALANCED (one persistent launch
- * per phase, warps take weighted Hilbert-contiguous element chunks from an
- * atomic queue) or DG_SCHED_NAIVE (one launch per element type and phase,
- * caller element order).  Results are bitwise identical. */
+ * per phase, warps take cost-weighted Hilbert-contiguous element chunks from
+ * an atomic queue), DG_SCHED_NAIVE (one launch per element type and phase,
+ * caller element order) or DG_SCHED_STATIC (one persistent launch, every warp
+ * owns one contiguous Hilbert segment of equal element count: the SFC
+ * partition without load balancing of Sec. 3).  Results are bitwise identical. */
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler);
+
+/* Tile shape of the element kernels: the number of warps (1..4) that work
+ * together on one element (one element per thread block).  The default is
+ * 2 for N <= 4 and 1 above; dg_autotune picks the fastest.  Rebuilds the
+ * chunk tables; results are bitwise identical for every choice. */
+dg_status dg_set_element_warps(dg_mesh* mesh, int warps);
+
+/* Stage fusion of dg_rk_step: fused != 0 (default) runs the backward phase of
+ * stage s (lift, projection, LSERK update) and the forward phase of stage s+1
+ * in one element launch; fused == 0 uses two launches.  Results are bitwise
+ * identical. */
+dg_status dg_set_stage_fusion(dg_mesh* mesh, int fused);
 
 /* Per-type element cost measured in the balanced kernels with %globaltimer
  * (Listing 1's per-element attribution, done per element in-kernel):
@@ -176,6 +190,15 @@ dg_status dg_cost_table(dg_mesh* mesh, double* ns_per_elem, double* imbalance, c
  * imbalance exceeds the threshold (or always, if force != 0); resets the
  * counters.  *rebuilt (may be NULL) tells whether it did.  Synchronises. */
 dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stream);
+
+/* Phase timing: with profiling on, dg_rhs and the dg_rk_step graph record
+ * CUDA events around every element-kernel and face-kernel phase (events
+ * inside the captured graph; a few microseconds of overhead per phase).
+ * dg_phase_times synchronises `stream` and returns, for the most recent
+ * dg_rk_step / dg_rhs call, host [4]: total element-phase ms, total
+ * face-phase ms, number of element phases, number of face phases. */
+dg_status dg_set_profiling(dg_mesh* mesh, int on);
+dg_status dg_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream);
 
 /* Synchronise `stream` and report sticky device errors (DG_ERR_NONFINITE). */
 dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream);

@@ -16,7 +16,7 @@ from .build import LIB, build as _build
 __all__ = ["lib", "DGError", "Mesh", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
-SCHED = {"balanced": 0, "naive": 1}
+SCHED = {"balanced": 0, "naive": 1, "static": 2}
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_OOM",
           -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_UNSUPPORTED"}
 
@@ -57,6 +57,10 @@ _SIGS = {
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
     "dg_sync": [_P, _P],
     "dg_probe_fp64_peak": [_P, _P],
+    "dg_set_profiling": [_P, ctypes.c_int],
+    "dg_set_stage_fusion": [_P, ctypes.c_int],
+    "dg_set_element_warps": [_P, ctypes.c_int],
+    "dg_phase_times": [_P, _P, _P],
 }
 
 _lib = None
@@ -256,6 +260,22 @@ class Mesh:
         r = ctypes.c_int()
         _check(load().dg_rebalance(self.handle, int(bool(force)), ctypes.byref(r), _stream(stream)))
         return bool(r.value)
+
+    def set_element_warps(self, warps):
+        _check(load().dg_set_element_warps(self.handle, int(warps)))
+
+    def set_stage_fusion(self, fused=True):
+        _check(load().dg_set_stage_fusion(self.handle, int(bool(fused))))
+
+    def set_profiling(self, on=True):
+        _check(load().dg_set_profiling(self.handle, int(bool(on))))
+
+    def phase_times(self, stream=None):
+        """(element ms, face ms, element phases, face phases) of the last call."""
+        import numpy as np
+        out = np.zeros(4)
+        _check(load().dg_phase_times(self.handle, _ptr(out), _stream(stream)))
+        return float(out[0]), float(out[1]), int(out[2]), int(out[3])
 
     def sync(self, stream=None):
         _check(load().dg_sync(self.handle, _stream(stream)))

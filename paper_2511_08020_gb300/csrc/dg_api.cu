@@ -80,6 +80,11 @@ struct dg_mesh {
   int64_t* d_type_slots[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t* d_chunks = nullptr;
   int64_t nchunks = 0;
+  int64_t* d_chunks_static = nullptr;
+  int64_t nchunks_static = 0;
+  int64_t* d_chunk_list = nullptr;
+  bool fused = true;  // backward of stage s and forward of stage s+1 in one launch
+  double weight[4] = {1, 1, 1, 1};  // chunk weights in use (ns or modelled cost per element)
   double* d_stage = nullptr;
   // graph cache for dg_rk_step
   cudaStream_t cap = nullptr;
@@ -87,8 +92,43 @@ struct dg_mesh {
   const double* g_Q = nullptr;
   const double* g_K = nullptr;
   double g_dt = 0.0;
-  int g_nsteps = -1, g_sched = -1;
+  int g_nsteps = -1, g_sched = -1, g_prof = -1, g_fused = -1;
   int parity = 0;
+  // phase timing events: pool 0 for captured graphs, pool 1 for direct calls
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool[2];
+  int ev_used[2] = {0, 0};
+  int pool = 1;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_elem[2], ev_face[2];
+  int last_pool = -1;
+
+  cudaEvent_t next_event() {
+    if (ev_used[pool] == (int)ev_pool[pool].size()) {
+      cudaEvent_t e = nullptr;
+      cudaEventCreate(&e);
+      ev_pool[pool].push_back(e);
+    }
+    return ev_pool[pool][ev_used[pool]++];
+  }
+  void begin_timing(int which) {
+    pool = which;
+    ev_used[pool] = 0;
+    ev_elem[pool].clear();
+    ev_face[pool].clear();
+    last_pool = which;
+  }
+  template <class F>
+  void timed(bool elem, cudaStream_t st, F&& f) {
+    if (!profiling) { f(); return; }
+    cudaEvent_t a = next_event(), b = next_event();
+    // inside a stream capture a plain record is only a dependency marker;
+    // the external flag makes it an event-record node of the graph
+    const unsigned flags = pool == 0 ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaEventRecordWithFlags(a, st, flags);
+    f();
+    cudaEventRecordWithFlags(b, st, flags);
+    (elem ? ev_elem[pool] : ev_face[pool]).push_back({a, b});
+  }
 
   dgk::Ctx ctx() const {
     dgk::Ctx c;
@@ -120,45 +160,76 @@ struct dg_mesh {
 
   int grid_balanced() const { return num_sms * blocks_per_sm; }
 
-  // Weighted contiguous chunks of the Hilbert order (4 per resident warp).
+  // Balanced work list: the Hilbert order grouped by element type (every
+  // type's elements stay in Hilbert order), cut into contiguous chunks of
+  // equal measured (or modelled) cost, about 4 per resident warp.  A chunk
+  // never spans two types, so at any moment most warps run one type's code.
   cudaError_t build_chunks(const double* type_weight) {
     const int64_t E = h.n_elems;
-    int64_t target = std::max<int64_t>(1, std::min<int64_t>(E, 4LL * grid_balanced() * wpb));
+    for (int t = 0; t < 4; ++t) weight[t] = type_weight[t];
+    std::vector<int64_t> list;
+    list.reserve(E);
+    for (int t = 0; t < 4; ++t)
+      for (int64_t s = 0; s < E; ++s)
+        if (h.slot_type[s] == t) list.push_back(s);
+    int64_t target = std::max<int64_t>(1, std::min<int64_t>(E, 4LL * grid_balanced()));
     double total = 0.0;
     for (int64_t s = 0; s < E; ++s) total += type_weight[h.slot_type[s]];
+    const double per_chunk = total / (double)target;
     std::vector<int64_t> starts;
     starts.push_back(0);
     double acc = 0.0;
-    int64_t k = 1;
-    for (int64_t s = 0; s < E; ++s) {
-      acc += type_weight[h.slot_type[s]];
-      if (acc >= total * (double)k / (double)target && s + 1 < E) {
-        starts.push_back(s + 1);
-        while (acc >= total * (double)k / (double)target) ++k;
+    for (int64_t i = 0; i < E; ++i) {
+      acc += type_weight[h.slot_type[list[i]]];
+      bool type_end = i + 1 < E && h.slot_type[list[i + 1]] != h.slot_type[list[i]];
+      if (i + 1 < E && (acc >= per_chunk || type_end)) {
+        starts.push_back(i + 1);
+        acc = 0.0;
       }
     }
     starts.push_back(E);
     nchunks = (int64_t)starts.size() - 1;
     if (d_chunks) cudaFree(d_chunks);
-    return upload(&d_chunks, starts);
+    if (d_chunk_list) cudaFree(d_chunk_list);
+    cudaError_t e = upload(&d_chunks, starts);
+    if (e != cudaSuccess) return e;
+    return upload(&d_chunk_list, list);
+  }
+
+  // Static partition: one contiguous Hilbert segment of equal element count
+  // per resident warp (the paper's partition without load balancing).
+  cudaError_t build_static_chunks() {
+    const int64_t E = h.n_elems;
+    int64_t W = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)grid_balanced()));
+    std::vector<int64_t> starts(W + 1);
+    for (int64_t w = 0; w <= W; ++w) starts[w] = w * E / W;
+    nchunks_static = W;
+    if (d_chunks_static) cudaFree(d_chunks_static);
+    return upload(&d_chunks_static, starts);
   }
 
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
     dgk::Ctx c = ctx();
-    if (scheduler == DG_SCHED_BALANCED && mode != dgk::kProject) {
-      dgk::Sched s{nullptr, nchunks, d_chunks, d_counters + parity, d_counters + (parity ^ 1)};
-      dgk::launch_element(c, mode, a, s, true, grid_balanced(), wpb, st);
-      parity ^= 1;
-    } else {
-      for (int t = 0; t < 4; ++t) {
-        if (h.type_slots[t].empty()) continue;
-        dgk::Sched s{d_type_slots[t], (int64_t)h.type_slots[t].size(), nullptr, nullptr, nullptr};
-        dgk::launch_element(c, mode, a, s, false, 0, wpb, st);
+    timed(true, st, [&] {
+      if ((scheduler == DG_SCHED_BALANCED || scheduler == DG_SCHED_STATIC) && mode != dgk::kProject) {
+        const bool stat = scheduler == DG_SCHED_STATIC;
+        dgk::Sched s{stat ? nullptr : d_chunk_list, stat ? nchunks_static : nchunks, stat ? d_chunks_static : d_chunks,
+                     d_counters + parity, d_counters + (parity ^ 1)};
+        dgk::launch_element(c, mode, a, s, true, grid_balanced(), wpb, st);
+        parity ^= 1;
+      } else {
+        for (int t = 0; t < 4; ++t) {
+          if (h.type_slots[t].empty()) continue;
+          dgk::Sched s{d_type_slots[t], (int64_t)h.type_slots[t].size(), nullptr, nullptr, nullptr};
+          dgk::launch_element(c, mode, a, s, false, 0, wpb, st);
+        }
       }
-    }
+    });
   }
 
-  void face_phase(cudaStream_t st) { dgk::launch_faces(ctx(), (int64_t)h.face_blocks.size(), h.n, st); }
+  void face_phase(cudaStream_t st) {
+    timed(false, st, [&] { dgk::launch_faces(ctx(), (int64_t)h.face_blocks.size(), h.n, st); });
+  }
 
   // Enqueue nsteps LSERK steps (no synchronisation).
   void enqueue_rk(double* Q, double* K, double dt, int nsteps, cudaStream_t st) {
@@ -172,18 +243,25 @@ struct dg_mesh {
         bool last = step == nsteps - 1 && s == 4;
         a.a = kLsA[s];
         a.b = kLsB[s];
-        element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, st);
+        if (fused) {
+          element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, st);
+        } else {
+          element_phase(dgk::kBwdRk, a, st);
+          if (!last) element_phase(dgk::kFwd, a, st);
+        }
       }
   }
 
   void release() {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
-                    d_cost, d_smns, d_counters, d_chunks, d_stage};
+                    d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
       if (p) cudaFree(p);
+    for (auto& pl : ev_pool)
+      for (auto e : pl) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap) cudaStreamDestroy(cap);
   }
@@ -197,7 +275,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
   if (!desc || !out) return fail(DG_ERR_ARG, "null argument");
   *out = nullptr;
   if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE) return fail(DG_ERR_ARG, "unknown flux");
-  if (desc->scheduler != DG_SCHED_BALANCED && desc->scheduler != DG_SCHED_NAIVE) return fail(DG_ERR_ARG, "unknown scheduler");
+  if (desc->scheduler < DG_SCHED_BALANCED || desc->scheduler > DG_SCHED_STATIC) return fail(DG_ERR_ARG, "unknown scheduler");
   if (!(desc->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
   int ndev = 0;
   cudaError_t ce = cudaGetDeviceCount(&ndev);
@@ -220,7 +298,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
   cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
   const dgh::HostMesh& h = m->h;
   m->nQmax = h.n * h.n * h.n;
-  m->wpb = m->nQmax >= 216 ? 1 : 2;
+  m->wpb = m->nQmax >= 216 ? 1 : 2;  // warps cooperating on one element
   auto fail_cuda = [&](cudaError_t e, const char* what) {
     m->release();
     delete m;
@@ -264,6 +342,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
     w[t] = ti >= 0 ? dgh::static_cost(h.tables.tabs[ti]) : 1.0;
   }
   if ((e = m->build_chunks(w)) != cudaSuccess) return fail_cuda(e, "chunk table");
+  if ((e = m->build_static_chunks()) != cudaSuccess) return fail_cuda(e, "chunk table");
   if ((e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking)) != cudaSuccess) return fail_cuda(e, "stream");
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail_cuda(e, "synchronise");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail_cuda(e, "synchronise");
@@ -354,6 +433,7 @@ dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStre
   if (!mesh || !Q_store || !R_store) return fail(DG_ERR_ARG, "null argument");
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
+  mesh->begin_timing(1);
   dgk::StageArgs a{Q_store, R_store, nullptr, 0.0, 0.0, 0.0};
   mesh->element_phase(dgk::kFwd, a, stream);
   mesh->face_phase(stream);
@@ -368,12 +448,13 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
   if (nsteps == 0) return DG_OK;
   if (!(std::isfinite(dt))) return fail(DG_ERR_ARG, "dt must be finite");
   if (!mesh->gexec || mesh->g_Q != Q_store || mesh->g_K != K_store || mesh->g_dt != dt || mesh->g_nsteps != nsteps ||
-      mesh->g_sched != mesh->scheduler) {
+      mesh->g_sched != mesh->scheduler || mesh->g_prof != (int)mesh->profiling || mesh->g_fused != (int)mesh->fused) {
     if (mesh->gexec) {
       cudaGraphExecDestroy(mesh->gexec);
       mesh->gexec = nullptr;
     }
     cudaGraph_t g;
+    mesh->begin_timing(0);
     DG_CUDA(cudaStreamBeginCapture(mesh->cap, cudaStreamCaptureModeThreadLocal));
     mesh->enqueue_rk(Q_store, K_store, dt, nsteps, mesh->cap);
     cudaError_t e = cudaStreamEndCapture(mesh->cap, &g);
@@ -386,7 +467,10 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
     mesh->g_dt = dt;
     mesh->g_nsteps = nsteps;
     mesh->g_sched = mesh->scheduler;
+    mesh->g_prof = (int)mesh->profiling;
+    mesh->g_fused = (int)mesh->fused;
   }
+  mesh->last_pool = 0;
   DG_CUDA(cudaGraphLaunch(mesh->gexec, stream));
   return DG_OK;
 }
@@ -403,7 +487,7 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double, int, int, con
 
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
-  if (scheduler != DG_SCHED_BALANCED && scheduler != DG_SCHED_NAIVE) return fail(DG_ERR_ARG, "unknown scheduler");
+  if (scheduler < DG_SCHED_BALANCED || scheduler > DG_SCHED_STATIC) return fail(DG_ERR_ARG, "unknown scheduler");
   mesh->scheduler = scheduler;
   return DG_OK;
 }
@@ -455,6 +539,53 @@ dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stre
   }
   DG_CUDA(cudaMemset(mesh->d_cost, 0, 8 * sizeof(unsigned long long)));
   DG_CUDA(cudaMemset(mesh->d_smns, 0, (size_t)mesh->num_sms * sizeof(unsigned long long)));
+  return DG_OK;
+}
+
+dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (warps < 1 || warps > 4) return fail(DG_ERR_ARG, "warps per element must be 1..4");
+  mesh->wpb = warps;
+  DG_CUDA(dgk::element_kernel_attributes(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm));
+  if (mesh->blocks_per_sm < 1) mesh->blocks_per_sm = 1;
+  double w[4];
+  for (int t = 0; t < 4; ++t) w[t] = mesh->weight[t];
+  DG_CUDA(mesh->build_chunks(w));
+  DG_CUDA(mesh->build_static_chunks());
+  if (mesh->gexec) {
+    cudaGraphExecDestroy(mesh->gexec);
+    mesh->gexec = nullptr;
+  }
+  return DG_OK;
+}
+
+dg_status dg_set_stage_fusion(dg_mesh* mesh, int fused) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  mesh->fused = fused != 0;
+  return DG_OK;
+}
+
+dg_status dg_set_profiling(dg_mesh* mesh, int on) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  mesh->profiling = on != 0;
+  return DG_OK;
+}
+
+dg_status dg_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream) {
+  if (!mesh || !out) return fail(DG_ERR_ARG, "null argument");
+  DG_CUDA(cudaStreamSynchronize(stream));
+  for (int i = 0; i < 4; ++i) out[i] = 0.0;
+  if (mesh->last_pool < 0) return DG_OK;
+  const int p = mesh->last_pool;
+  for (int k = 0; k < 2; ++k) {
+    const auto& v = k == 0 ? mesh->ev_elem[p] : mesh->ev_face[p];
+    for (const auto& ab : v) {
+      float ms = 0.f;
+      DG_CUDA(cudaEventElapsedTime(&ms, ab.first, ab.second));
+      out[k] += ms;
+    }
+    out[2 + k] = (double)v.size();
+  }
   return DG_OK;
 }
 

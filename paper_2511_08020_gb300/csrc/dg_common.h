@@ -45,6 +45,7 @@ struct TypeTab {
   int fw;       // [nfaces][n*n]          reference face weights at the face points
   // int pool
   int col_moff, col_len, col_coff, col_p;   // [ncols]
+  int col_order;                            // [ncols] columns by decreasing length (uniform trip counts per warp)
   int p_cbase, p_blen, p_boff;              // [n]
   int mode_col;                             // [nM]
   FaceDesc faces[6];

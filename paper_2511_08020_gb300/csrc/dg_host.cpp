@@ -309,6 +309,13 @@ int Tables::add(int type, int N, std::string* err) {
       mode += len;
     }
     if (mode != t.nM) { *err = "internal: mode count mismatch"; return -1; }
+    std::vector<int> order(t.ncols);
+    for (int col = 0; col < t.ncols; ++col) order[col] = col;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return ipool[t.col_len + x] > ipool[t.col_len + y];
+    });
+    t.col_order = ialloc(t.ncols);
+    for (int r = 0; r < t.ncols; ++r) ipool[t.col_order + r] = order[r];
   }
   // collocation derivative Dt[i'][i] = l'_{i'}(x_i) (barycentric formula)
   t.Dt = (int)dpool.size();

@@ -101,110 +101,174 @@ __device__ __forceinline__ void flux_roe(const double* UL, const double* UR, con
 }
 
 // ------------------------------------------------------------------ element phases
+//
+// Every pass gives one lane one output point and carries the 5 conservative
+// variables in registers: one coefficient load feeds 5 independent FMA chains
+// (instruction-level parallelism for the FP64 pipe) and the index arithmetic
+// is done once per output.  Buffers are [var][point] with a var stride of nQ.
 
-// Modal -> nodal: sQ [5][nM] -> U in bufA [5][nQ]; uses bufB as scratch.
-__device__ void modal_to_nodal(const Ctx& c, const TypeTab& T, const double* sQ, double* bufA, double* bufB, int lane) {
+#define DG_FMA5(cf, src, stride, acc)            \
+  do {                                           \
+    const double _c = (cf);                      \
+    const double* _s = (src);                    \
+    acc[0] = fma(_c, _s[0], acc[0]);             \
+    acc[1] = fma(_c, _s[(stride)], acc[1]);      \
+    acc[2] = fma(_c, _s[2 * (stride)], acc[2]);  \
+    acc[3] = fma(_c, _s[3 * (stride)], acc[3]);  \
+    acc[4] = fma(_c, _s[4 * (stride)], acc[4]);  \
+  } while (0)
+
+// Modal -> nodal: sQ [5][nM] -> U in bufA [5][nQ]; bufB is scratch.
+__device__ __noinline__ void modal_to_nodal(const Ctx& c, const TypeTab& T, const double* sQ, double* bufA,
+                                               double* bufB, int lane) {
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int* ip = c.ipool;
+  // c-pass: X[col][k] = sum_t C[col][t][k] Q[moff[col] + t], columns by decreasing length
   {
     const int cnt = T.ncols * n;
-    for (int w = lane; w < 5 * cnt; w += 32) {
-      int v = w / cnt, o = w - v * cnt, col = o / n, k = o - col * n;
+    for (int o = lane; o < cnt; o += blockDim.x) {
+      int r = o / n, k = o - r * n;
+      int col = ip[T.col_order + r];
       int len = ip[T.col_len + col];
       const double* C = dp + T.C + ip[T.col_coff + col] + k;
-      const double* q = sQ + v * nM + ip[T.col_moff + col];
-      double acc = 0.0;
-      for (int t = 0; t < len; ++t) acc = fma(C[t * n], q[t], acc);
-      bufA[v * nQ + o] = acc;
+      const double* q = sQ + ip[T.col_moff + col];
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int t = 0; t < len; ++t) DG_FMA5(C[t * n], q + t, nM, acc);
+      double* X = bufA + col * n + k;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) X[v * nQ] = acc[v];
     }
   }
-  __syncwarp();
-  for (int w = lane; w < 5 * nQ; w += 32) {
-    int v = w / nQ, o = w - v * nQ, p = o / n2, jk = o - p * n2, j = jk / n, k = jk - j * n;
+  __syncthreads();
+  // b-pass: Y[p][j][k] = sum_t B[p][t][j] X[cbase[p] + t][k]
+  for (int o = lane; o < nQ; o += blockDim.x) {
+    int p = o / n2, jk = o - p * n2, j = jk / n, k = jk - j * n;
     int blen = ip[T.p_blen + p];
     const double* B = dp + T.B + ip[T.p_boff + p] + j;
-    const double* X = bufA + v * nQ + ip[T.p_cbase + p] * n + k;
-    double acc = 0.0;
-    for (int t = 0; t < blen; ++t) acc = fma(B[t * n], X[t * n], acc);
-    bufB[v * nQ + o] = acc;
+    const double* X = bufA + ip[T.p_cbase + p] * n + k;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int t = 0; t < blen; ++t) DG_FMA5(B[t * n], X + t * n, nQ, acc);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufB[v * nQ + o] = acc[v];
   }
-  __syncwarp();
-  for (int w = lane; w < 5 * nQ; w += 32) {
-    int v = w / nQ, o = w - v * nQ, i = o / n2, jk = o - i * n2;
+  __syncthreads();
+  // a-pass: U[i][j][k] = sum_p A[p][i] Y[p][j][k]
+  for (int o = lane; o < nQ; o += blockDim.x) {
+    int i = o / n2, jk = o - i * n2;
     const double* A = dp + T.A + i;
-    const double* Y = bufB + v * nQ + jk;
-    double acc = 0.0;
-    for (int p = 0; p < n; ++p) acc = fma(A[p * n], Y[p * n2], acc);
-    bufA[v * nQ + o] = acc;
+    const double* Y = bufB + jk;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int p = 0; p < n; ++p) DG_FMA5(A[p * n], Y + p * n2, nQ, acc);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = acc[v];
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-// Nodal -> modal transpose: bufA [5][nQ] -> r(v, mode) handed to `epi`; uses bufB.
-template <class Epi>
-__device__ void nodal_to_modal(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane, Epi&& epi) {
+// What the nodal->modal pass does with r = M_ref^{-1} V^T bufA of a mode:
+//   kStore: out[v nM + m] = scale r_v
+//   kRk:    K <- a K + dt scale r (a == 0: K <- dt scale r), Q <- Q + b K,
+//           and the new Q is also written to sQ when sQ != nullptr.
+struct Epilogue {
+  enum { kStore = 0, kRk = 1 };
+  int kind;
+  double scale;
+  double* out;
+  const double* Qi;
+  double* Qo;
+  double* K;
+  double* sQ;
+  double a, b, dt;
+};
+
+// Nodal -> modal transpose: bufA [5][nQ] -> modal coefficients through `ep`;
+// bufB is scratch.  Returns true if a non-finite state value was produced.
+__device__ __noinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane,
+                                            const Epilogue& ep) {
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int* ip = c.ipool;
-  for (int w = lane; w < 5 * nQ; w += 32) {
-    int v = w / nQ, o = w - v * nQ, p = o / n2, jk = o - p * n2;
+  for (int o = lane; o < nQ; o += blockDim.x) {
+    int p = o / n2, jk = o - p * n2;
     const double* A = dp + T.A + p * n;
-    const double* Hs = bufA + v * nQ + jk;
-    double acc = 0.0;
-    for (int i = 0; i < n; ++i) acc = fma(A[i], Hs[i * n2], acc);
-    bufB[v * nQ + o] = acc;
+    const double* Hs = bufA + jk;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) DG_FMA5(A[i], Hs + i * n2, nQ, acc);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufB[v * nQ + o] = acc[v];
   }
-  __syncwarp();
+  __syncthreads();
   {
     const int cnt = T.ncols * n;
-    for (int w = lane; w < 5 * cnt; w += 32) {
-      int v = w / cnt, o = w - v * cnt, col = o / n, k = o - col * n;
+    for (int o = lane; o < cnt; o += blockDim.x) {
+      int col = o / n, k = o - col * n;
       int p = ip[T.col_p + col];
       int t = col - ip[T.p_cbase + p];
       const double* B = dp + T.B + ip[T.p_boff + p] + t * n;
-      const double* Y = bufB + v * nQ + p * n2 + k;
-      double acc = 0.0;
-      for (int j = 0; j < n; ++j) acc = fma(B[j], Y[j * n], acc);
-      bufA[v * nQ + o] = acc;
+      const double* Y = bufB + p * n2 + k;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int j = 0; j < n; ++j) DG_FMA5(B[j], Y + j * n, nQ, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = acc[v];
     }
   }
-  __syncwarp();
-  for (int w = lane; w < 5 * nM; w += 32) {
-    int v = w / nM, mode = w - v * nM;
+  __syncthreads();
+  bool bad = false;
+  for (int mode = lane; mode < nM; mode += blockDim.x) {
     int col = ip[T.mode_col + mode];
     int t = mode - ip[T.col_moff + col];
     const double* C = dp + T.C + ip[T.col_coff + col] + t * n;
-    const double* X = bufA + v * nQ + col * n;
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc = fma(C[k], X[k], acc);
-    epi(v, mode, acc * dp[T.minv + mode]);
+    const double* X = bufA + col * n;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < n; ++k) DG_FMA5(C[k], X + k, nQ, acc);
+    const double mi = dp[T.minv + mode] * ep.scale;
+    if (ep.kind == Epilogue::kStore) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] = acc[v] * mi;
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const int idx = v * nM + mode;
+        const double R = acc[v] * mi;
+        const double k = (ep.a == 0.0) ? ep.dt * R : fma(ep.a, ep.K[idx], ep.dt * R);
+        const double qn = fma(ep.b, k, ep.Qi[idx]);
+        ep.K[idx] = k;
+        ep.Qo[idx] = qn;
+        if (ep.sQ) ep.sQ[idx] = qn;
+        bad |= !finite_bits(qn);
+      }
+    }
   }
-  __syncwarp();
+  __syncthreads();
+  return bad;
 }
 
-// Forward phase of one element at slot s: nodal state, own-face traces,
-// nodal volume residual H.  sQ lives in bufG.
-__device__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG, int lane) {
+// Forward phase of the element at slot s: nodal state, own-face traces and
+// the nodal volume residual H.  sQ lives at the start of bufG.
+__device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
+                                                int lane) {
   const int n = T.n, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   modal_to_nodal(c, T, bufG, bufA, bufG, lane);
   // traces on the element's own face points
   {
-    const int per_face = 5 * n2, cnt = T.nfaces * per_face;
+    const int cnt = T.nfaces * n2;
     const int64_t* ft = c.slot_ftoff + s * 6;
-    for (int w = lane; w < cnt; w += 32) {
-      int lf = w / per_face, r = w - lf * per_face, v = r / n2, p = r - v * n2;
+    for (int w = lane; w < cnt; w += blockDim.x) {
+      int lf = w / n2, p = w - lf * n2;
       int ia = p % n, ib = p / n;
       const FaceDesc d = T.faces[lf];
       int sa = d.alpha == 0 ? n2 : (d.alpha == 1 ? n : 1);
       int sb = d.beta == 0 ? n2 : (d.beta == 1 ? n : 1);
       int sf = d.fixed == 0 ? n2 : (d.fixed == 1 ? n : 1);
       const double* e = dp + T.ext + d.end * n;
-      const double* U = bufA + v * nQ + ia * sa + ib * sb;
-      double acc = 0.0;
-      for (int m = 0; m < n; ++m) acc = fma(e[m], U[m * sf], acc);
-      c.T[ft[lf] + v * n2 + p] = acc;
+      const double* U = bufA + ia * sa + ib * sb;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(e[m], U + m * sf, nQ, acc);
+      double* out = c.T + ft[lf] + p;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) out[v * n2] = acc[v];
     }
   }
   // contravariant fluxes G_l at the volume points (bufG, [3][5][nQ])
@@ -213,7 +277,7 @@ __device__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, doubl
 #pragma unroll
   for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
   const double gm1 = c.gamma - 1.0;
-  for (int q = lane; q < nQ; q += 32) {
+  for (int q = lane; q < nQ; q += blockDim.x) {
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = bufA[v * nQ + q];
@@ -271,150 +335,153 @@ __device__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, doubl
       G[4 * nQ] = Vl * Ep;
     }
   }
-  __syncwarp();
-  // H = sum_l D_l^T G_l
+  __syncthreads();
+  // H = sum_l D_l^T G_l (collocation derivative along each collapsed direction)
   {
     const double* Dt = dp + T.Dt;
     double* H = c.H + c.slot_hoff[s];
-    for (int w = lane; w < 5 * nQ; w += 32) {
-      int v = w / nQ, o = w - v * nQ, i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
-      const double* G0 = bufG + v * nQ + jk;
-      const double* G1 = bufG + (5 + v) * nQ + i * n2 + k;
-      const double* G2 = bufG + (10 + v) * nQ + i * n2 + j * n;
-      double acc = 0.0;
-      for (int m = 0; m < n; ++m) acc = fma(Dt[i * n + m], G0[m * n2], acc);
-      for (int m = 0; m < n; ++m) acc = fma(Dt[j * n + m], G1[m * n], acc);
-      for (int m = 0; m < n; ++m) acc = fma(Dt[k * n + m], G2[m], acc);
-      H[w] = acc;
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      const double* G0 = bufG + jk;
+      const double* G1 = bufG + 5 * nQ + i * n2 + k;
+      const double* G2 = bufG + 10 * nQ + i * n2 + j * n;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[i * n + m], G0 + m * n2, nQ, acc);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[j * n + m], G1 + m * n, nQ, acc);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[k * n + m], G2 + m, nQ, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) H[v * nQ + o] = acc[v];
     }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-// Backward phase: H minus the lifted face fluxes into bufA.
-__device__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, int lane) {
+// Backward phase, first half: bufA = H - sum_faces E_f^T Fhat_f.  The face
+// fluxes are staged into bufG with coalesced loads first.
+__device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
+                                             int lane) {
   const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
   const double* dp = c.dpool;
-  const double* H = c.H + c.slot_hoff[s];
   const int64_t* ft = c.slot_ftoff + s * 6;
-  for (int w = lane; w < 5 * nQ; w += 32) {
-    int v = w / nQ, o = w - v * nQ, i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
-    double h = H[w];
+  {
+    const int per = 5 * n2;
+    for (int w = lane; w < nf * per; w += blockDim.x) {
+      int lf = w / per, r = w - lf * per;
+      bufG[w] = c.T[ft[lf] + r];
+    }
+  }
+  __syncthreads();
+  const double* H = c.H + c.slot_hoff[s];
+  for (int o = lane; o < nQ; o += blockDim.x) {
+    int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+    double h[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) h[v] = H[v * nQ + o];
     for (int lf = 0; lf < nf; ++lf) {
       const FaceDesc d = T.faces[lf];
       int m = sel3(i, j, k, d.fixed);
       int p = sel3(i, j, k, d.alpha) + n * sel3(i, j, k, d.beta);
-      h = fma(-dp[T.ext + d.end * n + m], c.T[ft[lf] + v * n2 + p], h);
+      DG_FMA5(-dp[T.ext + d.end * n + m], bufG + lf * 5 * n2 + p, n2, h);
     }
-    bufA[w] = h;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = h[v];
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-struct ElemIO {
-  int mode;
-  StageArgs a;
-};
-
-// One element at slot s in the given mode.  smem: bufA [5 nQmax], bufG [15 nQmax].
-__device__ void process_element(const Ctx& c, const ElemIO& io, int64_t s, double* bufA, double* bufG, int lane) {
-  const int tab = c.slot_tab[s];
-  const TypeTab& T = c.tabs[tab];
+// One element at slot s.  smem per warp: bufA [5 nQmax], bufG [15 nQmax].
+template <int MODE>
+__device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& io, int64_t s, double* bufA,
+                                                double* bufG, int lane) {
+  const TypeTab& T = c.tabs[c.slot_tab[s]];
   const int nM = T.nM, nQ = T.nQ;
   const int64_t qoff = c.slot_qoff[s];
-  const int mode = io.mode;
-  if (mode == kFwd) {
-    const double* Q = io.a.Qin + qoff;
-    for (int w = lane; w < 5 * nM; w += 32) bufG[w] = Q[w];
-    __syncwarp();
+  if (MODE == kFwd) {
+    const double* Q = io.Qin + qoff;
+    for (int w = lane; w < 5 * nM; w += blockDim.x) bufG[w] = Q[w];
+    __syncthreads();
     element_forward(c, T, s, bufA, bufG, lane);
     return;
   }
-  if (mode == kProject) {
+  if (MODE == kProject) {
     const int64_t e = c.elem_of_slot[s];
-    const double* vals = io.a.Qin + e * 5 * (int64_t)nQ;
+    const double* vals = io.Qin + e * 5 * (int64_t)nQ;
     const double* W = c.dpool + T.W;
-    for (int w = lane; w < 5 * nQ; w += 32) {
-      int q = w % nQ;
-      bufA[w] = W[q] * vals[w];
-    }
-    __syncwarp();
-    double* out = io.a.Qout + qoff;
-    nodal_to_modal(c, T, bufA, bufG, lane, [&](int v, int m, double r) { out[v * nM + m] = r; });
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * vals[w];
+    __syncthreads();
+    Epilogue ep{Epilogue::kStore, 1.0, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    nodal_to_modal(c, T, bufA, bufG, lane, ep);
     return;
   }
-  // backward modes
-  element_lift(c, T, s, bufA, lane);
+  element_lift(c, T, s, bufA, bufG, lane);
   const double invJ = c.geo[s].invJ;
-  if (mode == kBwdRhs) {
-    double* R = io.a.Qout + qoff;
-    nodal_to_modal(c, T, bufA, bufG, lane, [&](int v, int m, double r) { R[v * nM + m] = r * invJ; });
+  if (MODE == kBwdRhs) {
+    Epilogue ep{Epilogue::kStore, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    nodal_to_modal(c, T, bufA, bufG, lane, ep);
     return;
   }
-  const double a = io.a.a, b = io.a.b, dt = io.a.dt;
-  const double* Qi = io.a.Qin + qoff;
-  double* Qo = io.a.Qout + qoff;
-  double* K = io.a.K + qoff;
-  const bool fwd = mode == kBwdRkFwd;
-  bool bad = false;
-  nodal_to_modal(c, T, bufA, bufG, lane, [&](int v, int m, double r) {
-    int idx = v * nM + m;
-    double R = r * invJ;
-    double k = (a == 0.0) ? dt * R : fma(a, K[idx], dt * R);
-    double qn = fma(b, k, Qi[idx]);
-    K[idx] = k;
-    Qo[idx] = qn;
-    if (fwd) bufG[idx] = qn;
-    bad |= !finite_bits(qn);
-  });
-  if (__any_sync(kFull, bad) && lane == 0) atomicOr(c.status, 1u);
-  if (fwd) element_forward(c, T, s, bufA, bufG, lane);
+  Epilogue ep{Epilogue::kRk, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
+              MODE == kBwdRkFwd ? bufG : nullptr, io.a, io.b, io.dt};
+  const bool bad = __syncthreads_or(nodal_to_modal(c, T, bufA, bufG, lane, ep));
+  if (bad && lane == 0) atomicOr(c.status, 1u);
+  if (MODE == kBwdRkFwd) element_forward(c, T, s, bufA, bufG, lane);
 }
 
 // ------------------------------------------------------------------ kernels
+//
+// One block (1 to 4 warps) works on one element at a time; its threads share
+// the element's shared-memory workspace bufA [5 nQmax] + bufG [15 nQmax].
 
-__global__ void elem_naive_kernel(Ctx c, ElemIO io, const int64_t* __restrict__ list, int64_t count) {
+template <int MODE>
+__global__ void __launch_bounds__(128) elem_naive_kernel(Ctx c, StageArgs io, const int64_t* __restrict__ list,
+                                                         int64_t count) {
   extern __shared__ double smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  int64_t idx = (int64_t)blockIdx.x * wpb + warp;
+  const int64_t idx = blockIdx.x;
   if (idx >= count) return;
-  double* bufA = smem + (size_t)warp * 20 * c.nQmax;
+  double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
-  process_element(c, io, list ? list[idx] : idx, bufA, bufG, lane);
+  process_element<MODE>(c, io, list ? list[idx] : idx, bufA, bufG, threadIdx.x);
 }
 
-__global__ void elem_balanced_kernel(Ctx c, ElemIO io, const int64_t* __restrict__ chunk_start, int64_t nchunks,
-                                     unsigned int* counter, unsigned int* next_counter) {
+template <int MODE>
+__global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io, const int64_t* __restrict__ list,
+                                                            const int64_t* __restrict__ chunk_start, int64_t nchunks,
+                                                            unsigned int* counter, unsigned int* next_counter) {
   extern __shared__ double smem[];
+  __shared__ unsigned int s_chunk;
   // The previous launch on this stream used next_counter and has finished.
   if (blockIdx.x == 0 && threadIdx.x == 0 && next_counter) *next_counter = 0u;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* bufA = smem + (size_t)warp * 20 * c.nQmax;
+  const int lane = threadIdx.x;
+  double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
-  unsigned long long ns[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, busy = 0;
+  unsigned long long ns0 = 0, ns1 = 0, ns2 = 0, ns3 = 0, busy = 0;
+  unsigned n0 = 0, n1 = 0, n2 = 0, n3 = 0;
   while (true) {
-    unsigned int ch = 0;
-    if (lane == 0) ch = atomicAdd(counter, 1u);
-    ch = __shfl_sync(kFull, ch, 0);
+    if (lane == 0) s_chunk = atomicAdd(counter, 1u);
+    __syncthreads();
+    const unsigned int ch = s_chunk;
+    __syncthreads();
     if (ch >= nchunks) break;
-    for (int64_t s = chunk_start[ch]; s < chunk_start[ch + 1]; ++s) {
+    for (int64_t i = chunk_start[ch]; i < chunk_start[ch + 1]; ++i) {
+      const int64_t s = list ? list[i] : i;
       uint64_t t0 = global_ns();
-      process_element(c, io, s, bufA, bufG, lane);
-      __syncwarp();
+      process_element<MODE>(c, io, s, bufA, bufG, lane);
+      __syncthreads();
       uint64_t dtn = global_ns() - t0;
-      int ty = c.slot_type[s];
-      ns[ty] += dtn;
-      cnt[ty] += 1;
+      switch (c.slot_type[s]) {
+        case HEX: ns0 += dtn; ++n0; break;
+        case PRISM: ns1 += dtn; ++n1; break;
+        case PYR: ns2 += dtn; ++n2; break;
+        default: ns3 += dtn; ++n3; break;
+      }
       busy += dtn;
     }
   }
   if (lane == 0 && c.cost) {
-    for (int t = 0; t < 4; ++t)
-      if (cnt[t]) {
-        atomicAdd(c.cost + 2 * t, ns[t]);
-        atomicAdd(c.cost + 2 * t + 1, cnt[t]);
-      }
+    if (n0) { atomicAdd(c.cost + 0, ns0); atomicAdd(c.cost + 1, (unsigned long long)n0); }
+    if (n1) { atomicAdd(c.cost + 2, ns1); atomicAdd(c.cost + 3, (unsigned long long)n1); }
+    if (n2) { atomicAdd(c.cost + 4, ns2); atomicAdd(c.cost + 5, (unsigned long long)n2); }
+    if (n3) { atomicAdd(c.cost + 6, ns3); atomicAdd(c.cost + 7, (unsigned long long)n3); }
     if (busy) atomicAdd(c.sm_ns + smid(), busy);
   }
 }
@@ -523,31 +590,55 @@ __global__ void dmma_probe_kernel(double* out, int iters) {
 
 }  // namespace
 
-int element_smem_bytes(int nQmax, int wpb) { return wpb * 20 * nQmax * (int)sizeof(double); }
+int element_smem_bytes(int nQmax, int) { return 20 * nQmax * (int)sizeof(double); }
 int face_block_threads(int n) { return 32 * n; }
+
+namespace {
+template <class K>
+cudaError_t set_smem(K kernel, int bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+template <int MODE>
+cudaError_t set_mode(int bytes) {
+  cudaError_t e = set_smem(elem_naive_kernel<MODE>, bytes);
+  if (e != cudaSuccess) return e;
+  return set_smem(elem_balanced_kernel<MODE>, bytes);
+}
+template <int MODE>
+void launch_mode(const Ctx& c, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb, int bytes,
+                 cudaStream_t st) {
+  if (balanced) {
+    elem_balanced_kernel<MODE><<<grid, 32 * wpb, bytes, st>>>(c, a, s.list, s.chunk_start, s.count, s.counter,
+                                                              s.next_counter);
+  } else {
+    if (s.count <= 0) return;
+    elem_naive_kernel<MODE><<<(unsigned)s.count, 32 * wpb, bytes, st>>>(c, a, s.list, s.count);
+  }
+}
+}  // namespace
 
 cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   int bytes = element_smem_bytes(nQmax, wpb);
-  cudaError_t e = cudaFuncSetAttribute(elem_naive_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(elem_balanced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if ((e = set_mode<kFwd>(bytes)) != cudaSuccess) return e;
+  if ((e = set_mode<kBwdRhs>(bytes)) != cudaSuccess) return e;
+  if ((e = set_mode<kBwdRk>(bytes)) != cudaSuccess) return e;
+  if ((e = set_mode<kBwdRkFwd>(bytes)) != cudaSuccess) return e;
+  if ((e = set_mode<kProject>(bytes)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
-  e = cudaFuncSetAttribute(face_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fbytes);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel, 32 * wpb, bytes);
+  if ((e = set_smem(face_kernel, fbytes)) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd>, 32 * wpb, bytes);
 }
 
 void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb,
                     cudaStream_t st) {
-  ElemIO io{mode, a};
   int bytes = element_smem_bytes(c.nQmax, wpb);
-  if (balanced) {
-    elem_balanced_kernel<<<grid, 32 * wpb, bytes, st>>>(c, io, s.chunk_start, s.count, s.counter, s.next_counter);
-  } else {
-    if (s.count <= 0) return;
-    int64_t blocks = (s.count + wpb - 1) / wpb;
-    elem_naive_kernel<<<(unsigned)blocks, 32 * wpb, bytes, st>>>(c, io, s.list, s.count);
+  switch (mode) {
+    case kFwd: launch_mode<kFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kBwdRhs: launch_mode<kBwdRhs>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kBwdRk: launch_mode<kBwdRk>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kBwdRkFwd: launch_mode<kBwdRkFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kProject: launch_mode<kProject>(c, a, s, balanced, grid, wpb, bytes, st); break;
   }
 }
 

@@ -167,15 +167,33 @@ def test_full_size_sampled_parity(dg):
     vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
     Qs = mesh.project(torch.from_numpy(vals).cuda())
     Q = mesh.get_state(Qs)
-    R = mesh.get_state(mesh.rhs(Qs))
+    # The TGV velocity is divergence-free, so its density residual is pure
+    # truncation error (~1e-5) and a normwise relative error on it measures
+    # rounding against ~0; the residual check uses the seeded perturbation of
+    # the TGV (amplitude 1e-2, 4 lowest Fourier modes) instead.
+    pvals = di.perturbed_tgv_state(xyz, seed=3).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Ps = mesh.project(torch.from_numpy(pvals).cuda())
+    P = mesh.get_state(Ps)
+    R = mesh.get_state(mesh.rhs(Ps))
     rng = np.random.default_rng(2)
     sample = np.sort(rng.choice(box.n_elems, size=48, replace=False))
-    Rref = o.rhs(Q, elems=sample)
+    Rref = o.rhs(P, elems=sample)
     mask = np.zeros(mesh.n_dof, dtype=bool)
     for e in sample:
         mask[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = True
     vidx = var_index(o.mesh.nM)
-    assert rel_err(R, Rref, vidx, mask) < TOL
+    # At this size the residual is a cancellation of terms up to 100x larger
+    # (p0 = 71 at Ma 0.1 and small elements): a 1-ulp perturbation of the
+    # input alone moves the exact density residual by 2.6e-11 of its maximum.
+    # Each variable's error is therefore measured against the larger of its
+    # residual and its volume-term magnitude (in residual units), at 1e-11.
+    vol = np.zeros(mesh.n_dof)
+    for e in sample:
+        vol[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, o.volume_term(P, e)).ravel()
+    for v in range(5):
+        i = vidx[v][mask[vidx[v]]]
+        scale = max(np.abs(Rref[i]).max(), np.abs(vol[i]).max())
+        assert np.abs(R[i] - Rref[i]).max() < TOL * scale, v
     # the same inputs projected by the oracle agree with dg_project
     Qo = np.zeros_like(Q)
     for e in sample[:8]:
