@@ -309,6 +309,13 @@ def run_ours(args):
         ms = max_over_ranks(e0.elapsed_time(e1))
         return ms, (elem_ms, face_ms, nel, nfa)
 
+    # tile shape (warps per element) chosen by the library's autotuner per scheduler
+    tuned = {}
+    for sched in ("naive", "static", "balanced"):
+        mesh.set_scheduler(sched)
+        tuned[sched] = mesh.autotune(Q0, dt)
+    tuned_ms = {k: [round(x, 3) for x in v[1].tolist()] for k, v in tuned.items()}
+
     # main measurement: balanced scheduler, LF
     Q = Q0.clone()
     K = torch.empty_like(Q)
@@ -338,12 +345,15 @@ def run_ours(args):
 
     # naive scheduler and Roe flux, same workload and state
     mesh.set_scheduler("naive")
+    mesh.set_element_warps(tuned["naive"][0])
     Qn = Q0.clone()
     ms_naive, _ = timed_steps(mesh, Qn, K, args.steps, args.warmup)
     mesh.set_scheduler("static")
+    mesh.set_element_warps(tuned["static"][0])
     Qst = Q0.clone()
     ms_static, _ = timed_steps(mesh, Qst, K, args.steps, args.warmup)
     mesh.set_scheduler("balanced")
+    mesh.set_element_warps(tuned["balanced"][0])
     mesh.set_stage_fusion(False)
     Qsp = Q0.clone()
     ms_split, _ = timed_steps(mesh, Qsp, K, args.steps, args.warmup)
@@ -353,14 +363,16 @@ def run_ours(args):
     static_value = ws * dof * 5 * args.steps / (ms_static * 1e-3)
     same_bits = bool(torch.equal(Qn, Q)) and bool(torch.equal(Qst, Q)) and bool(torch.equal(Qsp, Q))
 
-    roe_mesh, Q0r, _ = make("roe", "balanced")
+    roe_mesh, Q0r, _ = make("roe", "naive")
+    roe_mesh.autotune(Q0r, dt)
+    Qrn = Q0r.clone()
+    ms_roe_naive, _ = timed_steps(roe_mesh, Qrn, torch.empty_like(Qrn), args.steps, args.warmup)
+    roe_naive_value = ws * dof * 5 * args.steps / (ms_roe_naive * 1e-3)
+    roe_mesh.set_scheduler("balanced")
+    roe_mesh.autotune(Q0r, dt)
     Qr = Q0r.clone()
     ms_roe, _ = timed_steps(roe_mesh, Qr, torch.empty_like(Qr), args.steps, args.warmup)
     roe_value = ws * dof * 5 * args.steps / (ms_roe * 1e-3)
-    roe_mesh.set_scheduler("naive")
-    Qrn = Q0r.clone()
-    ms_roe_naive, _ = timed_steps(roe_mesh, Qrn, torch.empty_like(Qr), args.steps, args.warmup)
-    roe_naive_value = ws * dof * 5 * args.steps / (ms_roe_naive * 1e-3)
 
     # measured per-type cost table from the balanced kernels
     ns_type, imb = mesh.cost_table()
@@ -421,6 +433,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 8 * mesh.n_dof,
                 "d2h_bytes_per_step": 8 * mesh.n_dof},
         "gpu_launches": gpu_launches,
+        "autotune_warps_per_element": {k: v[0] for k, v in tuned.items()},
+        "autotune_ms_per_step_by_warps": tuned_ms,
         "adjoint_over_forward": None,
     }
     if not args.no_cpu_baseline:

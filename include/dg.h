@@ -174,6 +174,18 @@ dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler);
  * chunk tables; results are bitwise identical for every choice. */
 dg_status dg_set_element_warps(dg_mesh* mesh, int warps);
 
+/* Autotuner: times one dg_rk_step of size dt for every element tile shape
+ * (1..4 warps per element) on a scratch copy of Q_store (device, storage
+ * layout; library-allocated scratch of 2 n_dof doubles, freed on return) and
+ * keeps the fastest for this mesh's scheduler and flux.  With the environment
+ * variable DG_AUTOTUNE_CACHE naming a file, results are read from and
+ * appended to it, keyed by device name, N, element counts, scheduler and
+ * flux.  best_warps (may be NULL) receives the choice, ms_per_step (host [4],
+ * may be NULL) the measured times (zeros when taken from the cache).
+ * Synchronises `stream`. */
+dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best_warps, double* ms_per_step,
+                      cudaStream_t stream);
+
 /* Stage fusion of dg_rk_step: fused != 0 (default) runs the backward phase of
  * stage s (lift, projection, LSERK update) and the forward phase of stage s+1
  * in one element launch; fused == 0 uses two launches.  Results are bitwise

@@ -60,6 +60,7 @@ _SIGS = {
     "dg_set_profiling": [_P, ctypes.c_int],
     "dg_set_stage_fusion": [_P, ctypes.c_int],
     "dg_set_element_warps": [_P, ctypes.c_int],
+    "dg_autotune": [_P, _P, ctypes.c_double, _P, _P, _P],
     "dg_phase_times": [_P, _P, _P],
 }
 
@@ -263,6 +264,14 @@ class Mesh:
 
     def set_element_warps(self, warps):
         _check(load().dg_set_element_warps(self.handle, int(warps)))
+
+    def autotune(self, Q_store, dt, stream=None):
+        """Pick the fastest warps-per-element for this mesh; returns (warps, ms per step [4])."""
+        import numpy as np
+        best = ctypes.c_int()
+        ms = np.zeros(4)
+        _check(load().dg_autotune(self.handle, _ptr(Q_store), float(dt), ctypes.byref(best), _ptr(ms), _stream(stream)))
+        return best.value, ms
 
     def set_stage_fusion(self, fused=True):
         _check(load().dg_set_stage_fusion(self.handle, int(bool(fused))))

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -161,30 +163,37 @@ struct dg_mesh {
   int grid_balanced() const { return num_sms * blocks_per_sm; }
 
   // Balanced work list: the Hilbert order grouped by element type (every
-  // type's elements stay in Hilbert order), cut into contiguous chunks of
-  // equal measured (or modelled) cost, about 4 per resident warp.  A chunk
-  // never spans two types, so at any moment most warps run one type's code.
+  // type's elements stay in Hilbert order), types in decreasing cost per
+  // element, cut into contiguous chunks by guided self-scheduling on the
+  // measured (or modelled) cost: each chunk takes a fixed fraction of the
+  // work still unassigned, so chunks are large at first and single elements
+  // at the end, where they set the length of the tail.  A chunk never spans
+  // two types, so at any moment most blocks run one type's code.
   cudaError_t build_chunks(const double* type_weight) {
     const int64_t E = h.n_elems;
     for (int t = 0; t < 4; ++t) weight[t] = type_weight[t];
+    int order[4] = {0, 1, 2, 3};
+    std::stable_sort(order, order + 4, [&](int x, int y) { return type_weight[x] > type_weight[y]; });
     std::vector<int64_t> list;
     list.reserve(E);
-    for (int t = 0; t < 4; ++t)
+    for (int oi = 0; oi < 4; ++oi)
       for (int64_t s = 0; s < E; ++s)
-        if (h.slot_type[s] == t) list.push_back(s);
-    int64_t target = std::max<int64_t>(1, std::min<int64_t>(E, 4LL * grid_balanced()));
-    double total = 0.0;
-    for (int64_t s = 0; s < E; ++s) total += type_weight[h.slot_type[s]];
-    const double per_chunk = total / (double)target;
+        if (h.slot_type[s] == order[oi]) list.push_back(s);
+    double remaining = 0.0;
+    for (int64_t s = 0; s < E; ++s) remaining += type_weight[h.slot_type[s]];
+    const double blocks = (double)std::max(1, grid_balanced());
     std::vector<int64_t> starts;
     starts.push_back(0);
-    double acc = 0.0;
+    double acc = 0.0, target = remaining / (2.0 * blocks);
     for (int64_t i = 0; i < E; ++i) {
-      acc += type_weight[h.slot_type[list[i]]];
+      const double w = type_weight[h.slot_type[list[i]]];
+      acc += w;
+      remaining -= w;
       bool type_end = i + 1 < E && h.slot_type[list[i + 1]] != h.slot_type[list[i]];
-      if (i + 1 < E && (acc >= per_chunk || type_end)) {
+      if (i + 1 < E && (acc >= target || type_end)) {
         starts.push_back(i + 1);
         acc = 0.0;
+        target = remaining / (2.0 * blocks);
       }
     }
     starts.push_back(E);
@@ -556,6 +565,103 @@ dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
     cudaGraphExecDestroy(mesh->gexec);
     mesh->gexec = nullptr;
   }
+  return DG_OK;
+}
+
+namespace {
+
+// Cache line: "<device name>|N=<N>|E=<elements>|h<hex>p<prism>y<pyr>t<tet>|s<sched>|f<flux> <warps>"
+std::string autotune_key(const dg_mesh* m) {
+  cudaDeviceProp p;
+  cudaGetDeviceProperties(&p, m->device);
+  std::string k = std::string(p.name) + "|N=" + std::to_string(m->h.N) + "|E=" + std::to_string(m->h.n_elems) + "|h" +
+                  std::to_string(m->h.type_count[0]) + "p" + std::to_string(m->h.type_count[1]) + "y" +
+                  std::to_string(m->h.type_count[2]) + "t" + std::to_string(m->h.type_count[3]) + "|s" +
+                  std::to_string(m->scheduler) + "|f" + std::to_string(m->flux);
+  for (auto& ch : k)
+    if (ch == ' ') ch = '_';
+  return k;
+}
+
+int autotune_lookup(const char* path, const std::string& key) {
+  FILE* f = path ? std::fopen(path, "r") : nullptr;
+  if (!f) return 0;
+  char line[512];
+  int found = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    char k[480];
+    int w = 0;
+    if (std::sscanf(line, "%479s %d", k, &w) == 2 && key == k) found = w;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void autotune_store(const char* path, const std::string& key, int warps) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d\n", key.c_str(), warps);
+  std::fclose(f);
+}
+
+}  // namespace
+
+dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best_warps, double* ms_per_step,
+                      cudaStream_t stream) {
+  if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  const char* cache = std::getenv("DG_AUTOTUNE_CACHE");
+  const std::string key = autotune_key(mesh);
+  int cached = autotune_lookup(cache, key);
+  if (cached >= 1 && cached <= 4) {
+    dg_status s = dg_set_element_warps(mesh, cached);
+    if (s != DG_OK) return s;
+    if (best_warps) *best_warps = cached;
+    if (ms_per_step) for (int g = 0; g < 4; ++g) ms_per_step[g] = 0.0;
+    return DG_OK;
+  }
+  double *Qs = nullptr, *Ks = nullptr;
+  const size_t bytes = sizeof(double) * mesh->h.n_dof;
+  DG_CUDA(cudaMalloc(&Qs, bytes));
+  if (cudaMalloc(&Ks, bytes) != cudaSuccess) {
+    cudaFree(Qs);
+    return fail(DG_ERR_OOM, "autotune scratch");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  int bestg = mesh->wpb;
+  dg_status st = DG_OK;
+  for (int g = 1; g <= 4 && st == DG_OK; ++g) {
+    st = dg_set_element_warps(mesh, g);
+    if (st != DG_OK) break;
+    cudaMemcpyAsync(Qs, Q_store, bytes, cudaMemcpyDeviceToDevice, stream);
+    st = dg_rk_step(mesh, Qs, Ks, dt, 1, stream);  // captures this shape's graph
+    if (st != DG_OK) break;
+    const int reps = 3;
+    cudaEventRecord(e0, stream);
+    for (int r = 0; r < reps && st == DG_OK; ++r) st = dg_rk_step(mesh, Qs, Ks, dt, 1, stream);
+    cudaEventRecord(e1, stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / reps;
+    if (ms_per_step) ms_per_step[g - 1] = per;
+    if (per < best) {
+      best = per;
+      bestg = g;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Qs);
+  cudaFree(Ks);
+  if (st != DG_OK) return st;
+  dg_status s = dg_set_element_warps(mesh, bestg);
+  if (s != DG_OK) return s;
+  autotune_store(cache, key, bestg);
+  if (best_warps) *best_warps = bestg;
   return DG_OK;
 }
 
