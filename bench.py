@@ -75,6 +75,12 @@ def element_flops(t, N):
 
 FACE_POINT_FLOPS = {"lf": 101, "roe": 214}
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused element launch
+# (backward + LSERK + forward) of this workload, from the ncu capture
+# summarised in profiles/element_kernel_16cube_N4.md; set to None whenever
+# the element kernel changes until it is captured again.
+NCU_TRAFFIC_FUSED_LAUNCH = (187.139328 + 135.315456) * 1e6
+
 
 def element_bytes(t, N):
     """Algorithmic HBM bytes of one element for one stage: Q, K read and
@@ -422,7 +428,8 @@ def run_ours(args):
                      "achieved": elem_tflops, "peak": dfma, "unit": "TFLOP/s", "frac": elem_tflops / dfma,
                      "peak_kind": "measured FP64 DFMA loop, this run (dg_probe_fp64_peak)",
                      "peak_nominal": nominal, "frac_of_nominal": elem_tflops / nominal,
-                     "traffic": None,
+                     "traffic": NCU_TRAFFIC_FUSED_LAUNCH,
+                     "traffic_source": "dram read+write of one fused element launch, profiles/element_kernel_16cube_N4.md",
                      "algorithmic_bytes_per_stage": el_bytes_stage, "algorithmic_flops_per_stage": el_flops_stage,
                      "element_ms_per_step": elem_ms / steps_p, "face_ms_per_step": face_ms / steps_p,
                      "face_kernel_tflops": face_tflops, "whole_step_tflops": total_tflops,
