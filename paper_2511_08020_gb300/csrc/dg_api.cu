@@ -71,6 +71,10 @@ struct dg_mesh {
   dgk::ElemGeo* d_geo = nullptr;
   double* d_H = nullptr;
   double* d_T = nullptr;
+  double* d_Tv = nullptr;       // adjoint face buffer
+  double* d_Kbar = nullptr;     // adjoint LSERK register
+  double* d_ckpt = nullptr;     // dg_rk_vjp checkpoints / stage states
+  size_t ckpt_doubles = 0;
   dgk::FaceRec* d_faces = nullptr;
   dgk::FaceBlock* d_fblocks = nullptr;
   int16_t* d_perms = nullptr;
@@ -147,6 +151,7 @@ struct dg_mesh {
     c.geo = d_geo;
     c.H = d_H;
     c.T = d_T;
+    c.Tv = d_Tv;
     c.faces = d_faces;
     c.fblocks = d_fblocks;
     c.perms = d_perms;
@@ -241,6 +246,48 @@ struct dg_mesh {
   }
 
   // Enqueue nsteps LSERK steps (no synchronisation).
+  // Adjoint workspace (allocated on first use).
+  cudaError_t ensure_adjoint(size_t ckpt_needed) {
+    cudaError_t e = cudaSuccess;
+    if (!d_Tv && (e = cudaMalloc(&d_Tv, sizeof(double) * std::max<int64_t>(1, h.t_total))) != cudaSuccess) return e;
+    if (!d_Kbar && (e = cudaMalloc(&d_Kbar, sizeof(double) * std::max<int64_t>(1, h.n_dof))) != cudaSuccess) return e;
+    if (ckpt_needed > ckpt_doubles) {
+      if (d_ckpt) cudaFree(d_ckpt);
+      d_ckpt = nullptr;
+      ckpt_doubles = 0;
+      if ((e = cudaMalloc(&d_ckpt, sizeof(double) * ckpt_needed)) != cudaSuccess) return e;
+      ckpt_doubles = ckpt_needed;
+    }
+    return e;
+  }
+
+  // One RHS VJP (rk == 0) or one reverse LSERK stage (rk == 1) at state Q.
+  void enqueue_vjp(const dgk::VjpArgs& va, cudaStream_t st) {
+    dgk::Ctx c = ctx();
+    dgk::launch_vjp(c, 0, va, h.n_elems, wpb, st);
+    dgk::launch_faces_vjp(c, (int64_t)h.face_blocks.size(), h.n, st);
+    dgk::launch_vjp(c, 2, va, h.n_elems, wpb, st);
+  }
+
+  // Forward LSERK steps from Q (in place) with the stage inputs copied to
+  // `stages` (5 per step) when non-null.  Non-captured launches.
+  void enqueue_rk_stages(double* Q, double* K, double dt, int nsteps, double* stages, cudaStream_t st) {
+    const size_t bytes = sizeof(double) * h.n_dof;
+    cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
+    parity = 0;
+    dgk::StageArgs a{Q, Q, K, 0.0, 0.0, dt};
+    element_phase(dgk::kFwd, a, st);
+    for (int step = 0; step < nsteps; ++step)
+      for (int s = 0; s < 5; ++s) {
+        if (stages) cudaMemcpyAsync(stages + (size_t)(5 * step + s) * h.n_dof, Q, bytes, cudaMemcpyDeviceToDevice, st);
+        face_phase(st);
+        bool last = step == nsteps - 1 && s == 4;
+        a.a = kLsA[s];
+        a.b = kLsB[s];
+        element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, st);
+      }
+  }
+
   void enqueue_rk(double* Q, double* K, double dt, int nsteps, cudaStream_t st) {
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
     parity = 0;
@@ -264,7 +311,8 @@ struct dg_mesh {
   void release() {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
-                    d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage};
+                    d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
+                    d_Tv, d_Kbar, d_ckpt};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -484,14 +532,54 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
   return DG_OK;
 }
 
-dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t) {
+dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
-  return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp is not built yet");
+  DG_CUDA(mesh->ensure_adjoint(0));
+  dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
+  mesh->enqueue_vjp(va, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
 }
 
-dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double, int, int, const double* QKbar, double* Q0bar, cudaStream_t) {
+// Reverse LSERK through nsteps steps (2N storage, K = 0 at every step start),
+// per stage s = 5..1 at the stage input state Q_{s-1}:
+//   Kbar <- Kbar + B_s Qbar;  Qbar <- Qbar + dt J(Q_{s-1})^T Kbar;  Kbar <- A_s Kbar.
+// Stage inputs are recomputed segment by segment from checkpoints of Q taken
+// every ckpt_every steps (the last segment's forward pass is not needed).
+dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
+                    const double* QKbar, double* Q0bar, cudaStream_t stream) {
   if (!mesh || !Q0_store || !QKbar || !Q0bar) return fail(DG_ERR_ARG, "null argument");
-  return fail(DG_ERR_UNSUPPORTED, "dg_rk_vjp is not built yet");
+  if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
+  const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
+  if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
+  if (nsteps == 0) return DG_OK;
+  const int c = std::min(ckpt_every, nsteps);
+  const int nseg = (nsteps + c - 1) / c;
+  DG_CUDA(mesh->ensure_adjoint((size_t)(2 + nseg + 5 * c) * n));
+  double* Qw = mesh->d_ckpt;
+  double* Kw = Qw + n;
+  double* ck = Kw + n;
+  double* stages = ck + (size_t)nseg * n;
+  DG_CUDA(cudaMemcpyAsync(Qw, Q0_store, bytes, cudaMemcpyDeviceToDevice, stream));
+  for (int seg = 0; seg < nseg - 1; ++seg) {
+    DG_CUDA(cudaMemcpyAsync(ck + (size_t)seg * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
+    mesh->enqueue_rk_stages(Qw, Kw, dt, c, nullptr, stream);
+  }
+  DG_CUDA(cudaMemcpyAsync(ck + (size_t)(nseg - 1) * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
+  DG_CUDA(cudaMemsetAsync(mesh->d_Kbar, 0, bytes, stream));
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int steps = std::min(c, nsteps - seg * c);
+    DG_CUDA(cudaMemcpyAsync(Qw, ck + (size_t)seg * n, bytes, cudaMemcpyDeviceToDevice, stream));
+    mesh->enqueue_rk_stages(Qw, Kw, dt, steps, stages, stream);
+    for (int step = steps - 1; step >= 0; --step)
+      for (int s = 4; s >= 0; --s) {
+        dgk::VjpArgs va{stages + (size_t)(5 * step + s) * n, nullptr, mesh->d_Kbar, Q0bar, kLsA[s], kLsB[s], dt, 1};
+        mesh->enqueue_vjp(va, stream);
+      }
+  }
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
 }
 
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler) {

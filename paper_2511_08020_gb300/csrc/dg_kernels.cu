@@ -100,6 +100,246 @@ __device__ __forceinline__ void flux_roe(const double* UL, const double* UR, con
   for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (L.F[v] + R.F[v]) - 0.5 * D[v];
 }
 
+// ------------------------------------------------------------------ adjoint physics
+// Hand-written reverse mode of the functions above.  Readings at the kinks:
+// d|x|/dx = sign(x) with sign(0) = 0; max(aL, aR) passes its cotangent to the
+// left ('-') argument at ties.
+
+__device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// Cotangents of a side's normal-state quantities -> cotangent of U.
+// Fb: cotangent of F(U).n; unb, pb, Hb: of u.n, p, H; ub: of u (3).
+__device__ __forceinline__ void normal_state_vjp(const double* U, const double* n, double gamma, const NState& s,
+                                                 const double* Fb, double unb, double pb, double Hb, double* ub,
+                                                 double* Ub) {
+  const double gm1 = gamma - 1.0;
+  const double u[3] = {U[1] * s.rinv, U[2] * s.rinv, U[3] * s.rinv};
+  // F[0] = rho un ; F[1+i] = m_i un + p n_i ; F[4] = (E + p) un
+  Ub[0] += Fb[0] * s.un;
+  unb += Fb[0] * U[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Ub[1 + i] += Fb[1 + i] * s.un;
+    unb += Fb[1 + i] * U[1 + i];
+    pb += Fb[1 + i] * n[i];
+  }
+  Ub[4] += Fb[4] * s.un;
+  pb += Fb[4] * s.un;
+  unb += Fb[4] * (U[4] + s.p);
+  // H = (E + p) / rho
+  Ub[4] += Hb * s.rinv;
+  pb += Hb * s.rinv;
+  Ub[0] -= Hb * s.H * s.rinv;
+  // un = u.n
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ub[d] += unb * n[d];
+  // p = (gamma-1)(E - |m|^2 / (2 rho))
+  Ub[4] += gm1 * pb;
+  const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Ub[1 + d] -= gm1 * u[d] * pb;
+  Ub[0] += 0.5 * gm1 * q2 * pb;
+  // u = m / rho
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Ub[1 + d] += ub[d] * s.rinv;
+    Ub[0] -= ub[d] * u[d] * s.rinv;
+  }
+}
+
+// Lax-Friedrichs: given Fsb = cotangent of F*, accumulate UbL, UbR.
+__device__ __forceinline__ void flux_lf_vjp(const double* UL, const double* UR, const double* n, double gamma,
+                                            const double* Fsb, double* UbL, double* UbR) {
+  NState L, R;
+  normal_state(UL, n, gamma, L);
+  normal_state(UR, n, gamma, R);
+  const double cL = sqrt(gamma * L.p * L.rinv), cR = sqrt(gamma * R.p * R.rinv);
+  const double aL = fabs(L.un) + cL, aR = fabs(R.un) + cR;
+  const double lam = aL >= aR ? aL : aR;
+  double Fb[5], lamb = 0.0;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    Fb[v] = 0.5 * Fsb[v];
+    lamb -= 0.5 * Fsb[v] * (UR[v] - UL[v]);
+    UbR[v] -= 0.5 * lam * Fsb[v];
+    UbL[v] += 0.5 * lam * Fsb[v];
+  }
+  const double aLb = aL >= aR ? lamb : 0.0, aRb = aL >= aR ? 0.0 : lamb;
+  // c = sqrt(gamma p / rho): dc = gamma dp / (2 c rho) - c drho / (2 rho)
+  double ubL[3] = {0, 0, 0}, ubR[3] = {0, 0, 0};
+  const double pbL = aLb * gamma * L.rinv / (2.0 * cL), pbR = aRb * gamma * R.rinv / (2.0 * cR);
+  UbL[0] -= aLb * 0.5 * cL * L.rinv;
+  UbR[0] -= aRb * 0.5 * cR * R.rinv;
+  normal_state_vjp(UL, n, gamma, L, Fb, sgn0(L.un) * aLb, pbL, 0.0, ubL, UbL);
+  normal_state_vjp(UR, n, gamma, R, Fb, sgn0(R.un) * aRb, pbR, 0.0, ubR, UbR);
+}
+
+// Roe: given Fsb = cotangent of F*, accumulate UbL, UbR (reverse of flux_roe).
+__device__ __forceinline__ void flux_roe_vjp(const double* UL, const double* UR, const double* n, double gamma,
+                                             const double* Fsb, double* UbL, double* UbR) {
+  NState L, R;
+  normal_state(UL, n, gamma, L);
+  normal_state(UR, n, gamma, R);
+  // forward recomputation
+  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const double den = 1.0 / (sL + sR);
+  const double uL[3] = {UL[1] * L.rinv, UL[2] * L.rinv, UL[3] * L.rinv};
+  const double uR[3] = {UR[1] * R.rinv, UR[2] * R.rinv, UR[3] * R.rinv};
+  double u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = (sL * uL[d] + sR * uR[d]) * den;
+  const double H = (sL * L.H + sR * R.H) * den;
+  const double rho = sL * sR;
+  const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double gm1 = gamma - 1.0;
+  const double c2 = gm1 * (H - 0.5 * q2);
+  const double c = sqrt(c2);
+  const double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  const double dp = R.p - L.p;
+  const double du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  const double dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
+  const double ic2 = 1.0 / c2;
+  const double a1 = 0.5 * (dp - rho * c * dun) * ic2;
+  const double a5 = 0.5 * (dp + rho * c * dun) * ic2;
+  const double a2 = (UR[0] - UL[0]) - dp * ic2;
+  const double e1 = fabs(un - c), e5 = fabs(un + c), l2 = fabs(un);
+  const double l1 = e1 * a1, l5 = e5 * a5;
+  double dut[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dut[d] = du[d] - dun * n[d];
+  const double udut = u[0] * dut[0] + u[1] * dut[1] + u[2] * dut[2];
+  // reverse
+  double Db[5], FbL[5], FbR[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    Db[v] = -0.5 * Fsb[v];
+    FbL[v] = FbR[v] = 0.5 * Fsb[v];
+  }
+  double l1b = 0, l5b = 0, l2b = 0, Hb = 0, cb = 0, unb = 0, a2b = 0, q2b = 0, rhob = 0, udutb = 0;
+  double ub[3] = {0, 0, 0}, dutb[3] = {0, 0, 0};
+  // D4
+  l1b += Db[4] * (H - c * un);
+  l5b += Db[4] * (H + c * un);
+  l2b += Db[4] * (a2 * 0.5 * q2 + rho * udut);
+  Hb += Db[4] * (l1 + l5);
+  cb += Db[4] * (l5 - l1) * un;
+  unb += Db[4] * (l5 - l1) * c;
+  a2b += Db[4] * l2 * 0.5 * q2;
+  q2b += Db[4] * l2 * a2 * 0.5;
+  rhob += Db[4] * l2 * udut;
+  udutb += Db[4] * l2 * rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ub[d] += udutb * dut[d];
+    dutb[d] += udutb * u[d];
+  }
+  // D1..D3
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double b = Db[1 + d];
+    l1b += b * (u[d] - c * n[d]);
+    l5b += b * (u[d] + c * n[d]);
+    l2b += b * (a2 * u[d] + rho * dut[d]);
+    ub[d] += b * (l1 + l5 + l2 * a2);
+    cb += b * (l5 - l1) * n[d];
+    a2b += b * l2 * u[d];
+    rhob += b * l2 * dut[d];
+    dutb[d] += b * l2 * rho;
+  }
+  // D0
+  l1b += Db[0];
+  l5b += Db[0];
+  l2b += Db[0] * a2;
+  a2b += Db[0] * l2;
+  // dut = du - dun n
+  double dub[3], dunb = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dub[d] = dutb[d];
+    dunb -= dutb[d] * n[d];
+  }
+  // eigenvalue magnitudes
+  unb += sgn0(un) * l2b;
+  const double s5 = sgn0(un + c), s1 = sgn0(un - c);
+  unb += s5 * a5 * l5b + s1 * a1 * l1b;
+  cb += s5 * a5 * l5b - s1 * a1 * l1b;
+  const double a5b = e5 * l5b, a1b = e1 * l1b;
+  // wave strengths
+  double dpb = 0, ic2b = 0, drhob = a2b;
+  dpb -= a2b * ic2;
+  ic2b -= a2b * dp;
+  dpb += 0.5 * ic2 * (a5b + a1b);
+  rhob += 0.5 * ic2 * c * dun * (a5b - a1b);
+  cb += 0.5 * ic2 * rho * dun * (a5b - a1b);
+  dunb += 0.5 * ic2 * rho * c * (a5b - a1b);
+  ic2b += 0.5 * (dp + rho * c * dun) * a5b + 0.5 * (dp - rho * c * dun) * a1b;
+  double c2b = -ic2b * ic2 * ic2;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dub[d] += dunb * n[d];
+  // un = u.n
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ub[d] += unb * n[d];
+  // c = sqrt(c2), c2 = (gamma-1)(H - q2/2), q2 = |u|^2
+  c2b += cb / (2.0 * c);
+  Hb += gm1 * c2b;
+  q2b -= 0.5 * gm1 * c2b;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ub[d] += 2.0 * u[d] * q2b;
+  // Roe averages
+  double sLb = rhob * sR, sRb = rhob * sL, denb = 0.0;
+  double HLb = Hb * sL * den, HRb = Hb * sR * den;
+  sLb += Hb * L.H * den;
+  sRb += Hb * R.H * den;
+  denb += Hb * (sL * L.H + sR * R.H);
+  double ubL[3], ubR[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sLb += ub[d] * uL[d] * den;
+    sRb += ub[d] * uR[d] * den;
+    ubL[d] = ub[d] * sL * den - dub[d];
+    ubR[d] = ub[d] * sR * den + dub[d];
+    denb += ub[d] * (sL * uL[d] + sR * uR[d]);
+  }
+  sLb -= denb * den * den;
+  sRb -= denb * den * den;
+  UbL[0] += sLb / (2.0 * sL) - drhob;
+  UbR[0] += sRb / (2.0 * sR) + drhob;
+  normal_state_vjp(UL, n, gamma, L, FbL, 0.0, -dpb, HLb, ubL, UbL);
+  normal_state_vjp(UR, n, gamma, R, FbR, 0.0, dpb, HRb, ubR, UbR);
+}
+
+// Contravariant flux at a volume point (G_l = V_l U + p (0, M_l., V_l),
+// V_l = M_l.u) in reverse: Gb[l][v] -> Ub[v].
+__device__ __forceinline__ void contravariant_vjp(const double* U, const double M[3][3], double gamma,
+                                                  const double Gb[3][5], double* Ub) {
+  const double gm1 = gamma - 1.0;
+  const double rinv = 1.0 / U[0];
+  const double u[3] = {U[1] * rinv, U[2] * rinv, U[3] * rinv};
+  const double p = gm1 * (U[4] - 0.5 * (U[1] * u[0] + U[2] * u[1] + U[3] * u[2]));
+  const double Ep = U[4] + p;
+  double pb = 0.0, ub[3] = {0, 0, 0};
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Ub[v] = 0.0;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const double Vl = M[l][0] * u[0] + M[l][1] * u[1] + M[l][2] * u[2];
+    const double Vb = Gb[l][0] * U[0] + Gb[l][1] * U[1] + Gb[l][2] * U[2] + Gb[l][3] * U[3] + Gb[l][4] * Ep;
+    Ub[0] += Gb[l][0] * Vl;
+    Ub[1] += Gb[l][1] * Vl;
+    Ub[2] += Gb[l][2] * Vl;
+    Ub[3] += Gb[l][3] * Vl;
+    Ub[4] += Gb[l][4] * Vl;
+    pb += Gb[l][1] * M[l][0] + Gb[l][2] * M[l][1] + Gb[l][3] * M[l][2] + Gb[l][4] * Vl;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ub[d] += Vb * M[l][d];
+  }
+  Ub[4] += gm1 * pb;
+  const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Ub[1 + d] += ub[d] * rinv - gm1 * u[d] * pb;
+  Ub[0] += 0.5 * gm1 * q2 * pb - (ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) * rinv;
+}
+
 // ------------------------------------------------------------------ element phases
 //
 // Every pass gives one lane one output point and carries the 5 conservative
@@ -166,13 +406,16 @@ __device__ __noinline__ void modal_to_nodal(const Ctx& c, const TypeTab& T, cons
   __syncthreads();
 }
 
-// What the nodal->modal pass does with r = M_ref^{-1} V^T bufA of a mode:
+// What the nodal->modal pass does with r = M_ref^{-1} V^T bufA of a mode
+// (r = V^T bufA without the mass matrix when minv == false):
 //   kStore: out[v nM + m] = scale r_v
 //   kRk:    K <- a K + dt scale r (a == 0: K <- dt scale r), Q <- Q + b K,
 //           and the new Q is also written to sQ when sQ != nullptr.
+//   kAxpy:  out[v nM + m] += scale r_v
 struct Epilogue {
-  enum { kStore = 0, kRk = 1 };
+  enum { kStore = 0, kRk = 1, kAxpy = 2 };
   int kind;
+  bool minv;
   double scale;
   double* out;
   const double* Qi;
@@ -222,10 +465,13 @@ __device__ __noinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, doub
     const double* X = bufA + col * n;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < n; ++k) DG_FMA5(C[k], X + k, nQ, acc);
-    const double mi = dp[T.minv + mode] * ep.scale;
+    const double mi = ep.minv ? dp[T.minv + mode] * ep.scale : ep.scale;
     if (ep.kind == Epilogue::kStore) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] = acc[v] * mi;
+    } else if (ep.kind == Epilogue::kAxpy) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] += acc[v] * mi;
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -244,6 +490,73 @@ __device__ __noinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, doub
   return bad;
 }
 
+// Values of the nodal field `src` [5][nQ] on the element's own face points,
+// times `scale`, written to the face buffer `dst` at the element's side slots.
+__device__ __forceinline__ void write_traces(const Ctx& c, const TypeTab& T, int64_t s, const double* src,
+                                             double* dst, double scale, int lane) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n;
+  const double* dp = c.dpool;
+  const int cnt = T.nfaces * n2;
+  const int64_t* ft = c.slot_ftoff + s * 6;
+  for (int w = lane; w < cnt; w += blockDim.x) {
+    int lf = w / n2, p = w - lf * n2;
+    int ia = p % n, ib = p / n;
+    const FaceDesc d = T.faces[lf];
+    int sa = d.alpha == 0 ? n2 : (d.alpha == 1 ? n : 1);
+    int sb = d.beta == 0 ? n2 : (d.beta == 1 ? n : 1);
+    int sf = d.fixed == 0 ? n2 : (d.fixed == 1 ? n : 1);
+    const double* e = dp + T.ext + d.end * n;
+    const double* U = src + ia * sa + ib * sb;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < n; ++m) DG_FMA5(e[m], U + m * sf, nQ, acc);
+    double* out = dst + ft[lf] + p;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * n2] = scale * acc[v];
+  }
+}
+
+// M = (w_q d(a,b,c)/d(xi)) (J dxi/dx) at volume point q, using each
+// collapse's sparsity (hex: diagonal; prism, pyramid, tet: triangular).
+__device__ __forceinline__ void point_metric(int type, const double* wa, const double* Jg, double M[3][3]) {
+  switch (type) {
+    case HEX: {
+      double w0 = wa[0];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) M[l][d] = w0 * Jg[l * 3 + d];
+      break;
+    }
+    case PRISM: {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        M[0][d] = wa[0] * Jg[d] + wa[1] * Jg[3 + d];
+        M[1][d] = wa[4] * Jg[3 + d];
+        M[2][d] = wa[8] * Jg[6 + d];
+      }
+      break;
+    }
+    case PYR: {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        M[0][d] = wa[0] * Jg[d] + wa[2] * Jg[6 + d];
+        M[1][d] = wa[4] * Jg[3 + d] + wa[5] * Jg[6 + d];
+        M[2][d] = wa[8] * Jg[6 + d];
+      }
+      break;
+    }
+    default: {  // TET
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        M[0][d] = wa[0] * Jg[d] + wa[1] * Jg[3 + d] + wa[2] * Jg[6 + d];
+        M[1][d] = wa[4] * Jg[3 + d] + wa[5] * Jg[6 + d];
+        M[2][d] = wa[8] * Jg[6 + d];
+      }
+      break;
+    }
+  }
+}
+
 // Forward phase of the element at slot s: nodal state, own-face traces and
 // the nodal volume residual H.  sQ lives at the start of bufG.
 __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
@@ -251,26 +564,7 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
   const int n = T.n, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   modal_to_nodal(c, T, bufG, bufA, bufG, lane);
-  // traces on the element's own face points
-  {
-    const int cnt = T.nfaces * n2;
-    const int64_t* ft = c.slot_ftoff + s * 6;
-    for (int w = lane; w < cnt; w += blockDim.x) {
-      int lf = w / n2, p = w - lf * n2;
-      int ia = p % n, ib = p / n;
-      const FaceDesc d = T.faces[lf];
-      int sa = d.alpha == 0 ? n2 : (d.alpha == 1 ? n : 1);
-      int sb = d.beta == 0 ? n2 : (d.beta == 1 ? n : 1);
-      int sf = d.fixed == 0 ? n2 : (d.fixed == 1 ? n : 1);
-      const double* e = dp + T.ext + d.end * n;
-      const double* U = bufA + ia * sa + ib * sb;
-      double acc[5] = {0, 0, 0, 0, 0};
-      for (int m = 0; m < n; ++m) DG_FMA5(e[m], U + m * sf, nQ, acc);
-      double* out = c.T + ft[lf] + p;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) out[v * n2] = acc[v];
-    }
-  }
+  write_traces(c, T, s, bufA, c.T, 1.0, lane);
   // contravariant fluxes G_l at the volume points (bufG, [3][5][nQ])
   const ElemGeo& g = c.geo[s];
   double Jg[9];
@@ -281,45 +575,8 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = bufA[v * nQ + q];
-    const double* wa = dp + T.wA + q * 9;
     double M[3][3];
-    switch (T.type) {
-      case HEX: {
-        double w0 = wa[0];
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) M[l][d] = w0 * Jg[l * 3 + d];
-        break;
-      }
-      case PRISM: {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          M[0][d] = wa[0] * Jg[d] + wa[1] * Jg[3 + d];
-          M[1][d] = wa[4] * Jg[3 + d];
-          M[2][d] = wa[8] * Jg[6 + d];
-        }
-        break;
-      }
-      case PYR: {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          M[0][d] = wa[0] * Jg[d] + wa[2] * Jg[6 + d];
-          M[1][d] = wa[4] * Jg[3 + d] + wa[5] * Jg[6 + d];
-          M[2][d] = wa[8] * Jg[6 + d];
-        }
-        break;
-      }
-      default: {  // TET
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          M[0][d] = wa[0] * Jg[d] + wa[1] * Jg[3 + d] + wa[2] * Jg[6 + d];
-          M[1][d] = wa[4] * Jg[3 + d] + wa[5] * Jg[6 + d];
-          M[2][d] = wa[8] * Jg[6 + d];
-        }
-        break;
-      }
-    }
+    point_metric(T.type, dp + T.wA + q * 9, Jg, M);
     double rinv = 1.0 / U[0];
     double u = U[1] * rinv, v = U[2] * rinv, w = U[3] * rinv;
     double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
@@ -356,10 +613,12 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
   __syncthreads();
 }
 
-// Backward phase, first half: bufA = H - sum_faces E_f^T Fhat_f.  The face
-// fluxes are staged into bufG with coalesced loads first.
+// Backward phase, first half: bufA = H + sign sum_faces E_f^T F_f with the
+// face values F_f read from `faces` (the lifted fluxes with sign -1; the
+// adjoint's trace cotangents with sign +1).  They are staged into bufG with
+// coalesced loads first.
 __device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
-                                             int lane) {
+                                          int lane, const double* faces, double sign) {
   const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
   const double* dp = c.dpool;
   const int64_t* ft = c.slot_ftoff + s * 6;
@@ -367,7 +626,7 @@ __device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_
     const int per = 5 * n2;
     for (int w = lane; w < nf * per; w += blockDim.x) {
       int lf = w / per, r = w - lf * per;
-      bufG[w] = c.T[ft[lf] + r];
+      bufG[w] = faces[ft[lf] + r];
     }
   }
   __syncthreads();
@@ -381,7 +640,7 @@ __device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_
       const FaceDesc d = T.faces[lf];
       int m = sel3(i, j, k, d.fixed);
       int p = sel3(i, j, k, d.alpha) + n * sel3(i, j, k, d.beta);
-      DG_FMA5(-dp[T.ext + d.end * n + m], bufG + lf * 5 * n2 + p, n2, h);
+      DG_FMA5(sign * dp[T.ext + d.end * n + m], bufG + lf * 5 * n2 + p, n2, h);
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = h[v];
@@ -409,22 +668,120 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     const double* W = c.dpool + T.W;
     for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * vals[w];
     __syncthreads();
-    Epilogue ep{Epilogue::kStore, 1.0, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    Epilogue ep{Epilogue::kStore, true, 1.0, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
     nodal_to_modal(c, T, bufA, bufG, lane, ep);
     return;
   }
-  element_lift(c, T, s, bufA, bufG, lane);
+  element_lift(c, T, s, bufA, bufG, lane, c.T, -1.0);
   const double invJ = c.geo[s].invJ;
   if (MODE == kBwdRhs) {
-    Epilogue ep{Epilogue::kStore, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    Epilogue ep{Epilogue::kStore, true, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
     nodal_to_modal(c, T, bufA, bufG, lane, ep);
     return;
   }
-  Epilogue ep{Epilogue::kRk, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
+  Epilogue ep{Epilogue::kRk, true, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
               MODE == kBwdRkFwd ? bufG : nullptr, io.a, io.b, io.dt};
   const bool bad = __syncthreads_or(nodal_to_modal(c, T, bufA, bufG, lane, ep));
   if (bad && lane == 0) atomicOr(c.status, 1u);
   if (MODE == kBwdRkFwd) element_forward(c, T, s, bufA, bufG, lane);
+}
+
+// ------------------------------------------------------------------ adjoint element phases
+//
+// With r = V^T (H - sum_f E_f^T Fhat_f), R = diag(M_ref^-1 / J) r and
+// H = sum_l D_l^T G_l(U), U = V Q, the cotangent Rbar maps back as
+//   Ybar = V diag(M_ref^-1 / J) Rbar          (nodal, a modal->nodal pass)
+//   seed_f = -E_f Ybar                         (cotangent of Fhat_f, own side)
+//   Gbar_l = D_l Ybar,  Ubar = sum_l (dG_l/dU)^T Gbar_l
+// and, after the face phase turned the seeds into trace cotangents Tbar_f,
+//   Qbar = V^T (Ubar + sum_f E_f^T Tbar_f).
+// smem per block: bufA [5 nQmax], bufG [15 nQmax], bufC [5 nQmax].
+
+// Phase A.  rk == 0: Rbar given.  rk == 1 (one reverse LSERK stage):
+// Kbar <- Kbar + b Qbar is the Rbar of this stage and Kbar <- a (Kbar + b Qbar)
+// is written back.
+__device__ __noinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
+                                           double* bufC, int lane) {
+  const TypeTab& T = c.tabs[c.slot_tab[s]];
+  const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
+  const double* dp = c.dpool;
+  const int64_t qoff = c.slot_qoff[s];
+  const int nQm = c.nQmax;
+  // forward nodal state and its traces (read by the face phase)
+  for (int w = lane; w < 5 * nM; w += blockDim.x) bufC[w] = va.Q[qoff + w];
+  __syncthreads();
+  modal_to_nodal(c, T, bufC, bufA, bufG, lane);
+  write_traces(c, T, s, bufA, c.T, 1.0, lane);
+  // scaled cotangent of the modal residual
+  const double invJ = c.geo[s].invJ;
+  for (int w = lane; w < 5 * nM; w += blockDim.x) {
+    const int m = w % nM;
+    double rb;
+    if (va.rk) {
+      rb = va.Kbar[qoff + w] + va.b * va.Qbar[qoff + w];
+      va.Kbar[qoff + w] = va.a * rb;
+    } else {
+      rb = va.Rbar[qoff + w];
+    }
+    bufG[w] = rb * dp[T.minv + m] * invJ;
+  }
+  __syncthreads();
+  modal_to_nodal(c, T, bufG, bufC, bufG + 5 * nQm, lane);  // Ybar in bufC
+  write_traces(c, T, s, bufC, c.Tv, -1.0, lane);           // seeds
+  // Gbar_l = D_l Ybar (collocation derivative), D[i][i'] = Dt[i'][i]
+  {
+    const double* Dt = dp + T.Dt;
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + i], bufC + m * n2 + jk, nQ, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[v * nQ + o] = acc[v];
+      double acc1[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + j], bufC + i * n2 + m * n + k, nQ, acc1);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[(5 + v) * nQ + o] = acc1[v];
+      double acc2[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + k], bufC + i * n2 + j * n + m, nQ, acc2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[(10 + v) * nQ + o] = acc2[v];
+    }
+  }
+  __syncthreads();
+  // pointwise transpose of the contravariant flux
+  {
+    const ElemGeo& g = c.geo[s];
+    double Jg[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+    double* Hb = c.H + c.slot_hoff[s];
+    for (int q = lane; q < nQ; q += blockDim.x) {
+      double U[5], Gb[3][5], Ub[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = bufA[v * nQ + q];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Gb[l][v] = bufG[(l * 5 + v) * nQ + q];
+      double M[3][3];
+      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      contravariant_vjp(U, M, c.gamma, Gb, Ub);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Hb[v * nQ + q] = Ub[v];
+    }
+  }
+  __syncthreads();
+}
+
+// Phase C: Qbar = V^T (Ubar + sum_f E_f^T Tbar_f); stored (rk == 0) or added
+// with weight dt (rk == 1).
+__device__ __noinline__ void element_vjp_c(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
+                                           int lane) {
+  const TypeTab& T = c.tabs[c.slot_tab[s]];
+  element_lift(c, T, s, bufA, bufG, lane, c.Tv, 1.0);
+  Epilogue ep{va.rk ? Epilogue::kAxpy : Epilogue::kStore, false, va.rk ? va.dt : 1.0, va.Qbar + c.slot_qoff[s],
+              nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+  nodal_to_modal(c, T, bufA, bufG, lane, ep);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -546,6 +903,102 @@ __global__ void face_kernel(Ctx c) {
   }
 }
 
+// ------------------------------------------------------------------ adjoint kernels
+
+__global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va, int phase) {
+  extern __shared__ double smem[];
+  const int64_t s = blockIdx.x;
+  double* bufA = smem;
+  double* bufG = bufA + 5 * c.nQmax;
+  double* bufC = bufG + 15 * c.nQmax;
+  if (phase == 0) element_vjp_a(c, va, s, bufA, bufG, bufC, threadIdx.x);
+  else element_vjp_c(c, va, s, bufA, bufG, threadIdx.x);
+}
+
+// Face phase of the adjoint.  Per owner face point p, with Map the
+// neighbour -> owner point map of the forward face phase:
+//   g(p) = wS_p (seed_own(p) - (Map seed_nb)(p))     (cotangent of F*)
+//   (Tbar-, Tbar+) = (dF*/dU-, dF*/dU+)^T g
+//   Tbar_own = Tbar-,  Tbar_nb = Map^T Tbar+        (written over the seeds)
+__global__ void face_vjp_kernel(Ctx c) {
+  extern __shared__ double sF[];
+  const FaceBlock fb = c.fblocks[blockIdx.x];
+  const int n = fb.n, n2 = n * n, items = fb.count * n2;
+  double* sR = sF + 32 * 5 * n2;
+  const double gamma = c.gamma;
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, p = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    const double* T0 = c.T + R.toff;
+    const double* T1 = T0 + 5 * n2;
+    const double* S0 = c.Tv + R.toff;
+    const double* S1 = S0 + 5 * n2;
+    double UL[5], UR[5], g[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      UL[v] = T0[v * n2 + p];
+      g[v] = S0[v * n2 + p];
+    }
+    if (R.map >= 0) {
+      int j = c.perms[(size_t)R.map * 2 * n2 + p];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        UR[v] = T1[v * n2 + j];
+        g[v] -= S1[v * n2 + j];
+      }
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + (size_t)p * n2;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < n2; ++j) {
+          a = fma(D[j], T1[v * n2 + j], a);
+          b = fma(D[j], S1[v * n2 + j], b);
+        }
+        UR[v] = a;
+        g[v] -= b;
+      }
+    }
+    const TypeTab& T = c.tabs[R.owner_tab];
+    const double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) g[v] *= wS;
+    double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+    double UbL[5] = {0, 0, 0, 0, 0}, UbR[5] = {0, 0, 0, 0, 0};
+    if (c.flux == 0) flux_lf_vjp(UL, UR, nrm, gamma, g, UbL, UbR);
+    else flux_roe_vjp(UL, UR, nrm, gamma, g, UbL, UbR);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      sF[(fl * 5 + v) * n2 + p] = UbL[v];
+      sR[(fl * 5 + v) * n2 + p] = UbR[v];
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, q = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    double* S0 = c.Tv + R.toff;
+    double* S1 = S0 + 5 * n2;
+    const double* Fl = sF + fl * 5 * n2;
+    const double* Fr = sR + fl * 5 * n2;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) S0[v * n2 + q] = Fl[v * n2 + q];
+    if (R.map >= 0) {
+      int p = c.perms[(size_t)R.map * 2 * n2 + n2 + q];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) S1[v * n2 + q] = Fr[v * n2 + p];
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + q;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int p = 0; p < n2; ++p) acc = fma(D[(size_t)p * n2], Fr[v * n2 + p], acc);
+        S1[v * n2 + q] = acc;
+      }
+    }
+  }
+}
+
 // Storage <-> caller layout copies (warp per element).
 __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __restrict__ dst, int64_t E, int to_storage) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -627,6 +1080,8 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   if ((e = set_mode<kProject>(bytes)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_vjp_kernel, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel, 25 * nQmax * (int)sizeof(double))) != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd>, 32 * wpb, bytes);
 }
 
@@ -640,6 +1095,18 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
     case kBwdRkFwd: launch_mode<kBwdRkFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kProject: launch_mode<kProject>(c, a, s, balanced, grid, wpb, bytes, st); break;
   }
+}
+
+void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int wpb, cudaStream_t st) {
+  if (nelem <= 0) return;
+  const int bytes = (phase == 0 ? 25 : 20) * c.nQmax * (int)sizeof(double);
+  elem_vjp_kernel<<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va, phase);
+}
+
+void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  int bytes = 2 * 32 * 5 * n * n * (int)sizeof(double);
+  face_vjp_kernel<<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
 }
 
 void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {

@@ -47,6 +47,7 @@ struct Ctx {
   const ElemGeo* geo;
   double* H;
   double* T;
+  double* Tv;                  // adjoint face buffer (seeds, then trace cotangents)
   const FaceRec* faces;
   const FaceBlock* fblocks;
   const int16_t* perms;
@@ -57,6 +58,18 @@ struct Ctx {
   double gamma;
   int flux;                    // 0 LF, 1 Roe
   int nQmax;
+};
+
+// Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
+// rk == 1: one reverse LSERK stage, Kbar <- a (Kbar + b Qbar) and
+// Qbar += dt (dR/dQ)^T (Kbar + b Qbar) at the stage input state Q.
+struct VjpArgs {
+  const double* Q;
+  const double* Rbar;
+  double* Kbar;
+  double* Qbar;
+  double a, b, dt;
+  int rk;
 };
 
 struct StageArgs {
@@ -77,6 +90,8 @@ struct Sched {
 void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid,
                     int warps_per_block, cudaStream_t st);
 void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
+void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int warps_per_block, cudaStream_t st);
+void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st);
 int element_smem_bytes(int nQmax, int warps_per_block);
 int face_block_threads(int n);
