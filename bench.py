@@ -380,6 +380,33 @@ def run_ours(args):
     ms_roe, _ = timed_steps(roe_mesh, Qr, torch.empty_like(Qr), args.steps, args.warmup)
     roe_value = ws * dof * 5 * args.steps / (ms_roe * 1e-3)
 
+    # adjoint / forward cost: dg_rk_vjp over K steps (checkpoints every 5 steps,
+    # and one segment) against K forward steps, same workload, LF, balanced
+    Kadj = 10
+    Qa = Q0.clone()
+    Ka = torch.empty_like(Qa)
+    wbar = torch.ones_like(Qa)
+    mesh.rk_step(Qa, Ka, dt, Kadj)          # capture the K-step graph
+    mesh.rk_vjp(Q0, dt, Kadj, 5, wbar)      # allocate the adjoint workspace
+    torch.cuda.synchronize()
+
+    def device_ms(fn, reps=2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    fwd_ms = device_ms(lambda: mesh.rk_step(Qa, Ka, dt, Kadj))
+    adj5_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, 5, wbar))
+    adjK_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, Kadj, wbar))
+    rhs_ms = device_ms(lambda: mesh.rhs(Q0), reps=5)
+    vjp_ms = device_ms(lambda: mesh.rhs_vjp(Q0, wbar), reps=5)
+    mesh.sync()
+
     # measured per-type cost table from the balanced kernels
     ns_type, imb = mesh.cost_table()
 
@@ -442,7 +469,10 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "autotune_warps_per_element": {k: v[0] for k, v in tuned.items()},
         "autotune_ms_per_step_by_warps": tuned_ms,
-        "adjoint_over_forward": None,
+        "adjoint_over_forward": adj5_ms / fwd_ms,
+        "adjoint": {"steps": Kadj, "forward_ms": fwd_ms, "rk_vjp_ckpt5_ms": adj5_ms, "rk_vjp_one_segment_ms": adjK_ms,
+                    "ratio_ckpt5": adj5_ms / fwd_ms, "ratio_one_segment": adjK_ms / fwd_ms,
+                    "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms, "rhs_vjp_over_rhs": vjp_ms / rhs_ms},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
