@@ -154,6 +154,29 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
  * overwritten.  No counterpart in the paper.  Asynchronous. */
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream);
 
+/* Allocation-free dg_rhs_vjp (the paper has no counterpart; this is a
+ * library convenience).  Same arguments, result and asynchrony as
+ * dg_rhs_vjp, for callers that must not allocate device memory at call time
+ * - for example code whose device memory is budgeted once at start-up, or
+ * that runs where calling the CUDA allocator is not allowed.  dg_rhs_vjp
+ * allocates its adjoint face buffer with cudaMalloc on first use; this entry
+ * point instead uses a fixed scratch array of 64 MiB (8 Mi doubles) that is
+ * part of the library image, so every GPU that loads the library holds it
+ * until the process exits.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *   - The mesh's face buffer must fit: meshes needing more than 8 Mi doubles
+ *     of face scratch (2 * 5 * (N+1)^2 per face) get DG_ERR_ARG with a
+ *     message; use dg_rhs_vjp for those.
+ *   - The mesh's device must be the current device.  The first call on a
+ *     device looks up the array's device address (cudaGetSymbolAddress) and
+ *     caches it; make that first call before any stream capture.
+ *   - All calls on a device share the one array and it keeps the last
+ *     call's contents (nothing in it has to start at zero: every slot is
+ *     written before it is read).  Calls that overlap on the GPU (different
+ *     streams without ordering, or two meshes at once) race on it. */
+dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
+                             cudaStream_t stream);
+
 /* Q0bar = (dQ_K/dQ_0)^T QKbar for nsteps LSERK steps of size dt from Q0_store.
  * Stage states are recomputed from checkpoints of Q stored every ckpt_every
  * steps in library memory.  No counterpart in the paper.  Asynchronous. */

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -537,6 +538,65 @@ dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, d
   DG_CUDA(mesh->ensure_adjoint(0));
   dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
   mesh->enqueue_vjp(va, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of dg_rhs_vjp.  dg_rhs_vjp allocates its adjoint
+// face buffer with cudaMalloc the first time it runs on a mesh; this variant
+// takes that scratch from a fixed-size array in device global memory that is
+// part of the library image instead, so the call itself never allocates.
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = size_t(8) << 20;  // 64 MiB of FP64 per device
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array for the current device (resolved once
+// per device; in host code the symbol itself is only a host-side stand-in).
+cudaError_t noalloc_scratch(int dev, double** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
+                             cudaStream_t stream) {
+  if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  const size_t need = (size_t)std::max<int64_t>(1, mesh->h.t_total);
+  if (need > kNoAllocScratchDoubles)
+    return fail(DG_ERR_ARG, "dg_rhs_vjp_noalloc: the mesh needs " + std::to_string(need) +
+                                " doubles of face scratch, more than the fixed " +
+                                std::to_string(kNoAllocScratchDoubles) + " (64 MiB); use dg_rhs_vjp");
+  int dev = -1;
+  DG_CUDA(cudaGetDevice(&dev));
+  if (dev != mesh->device) return fail(DG_ERR_ARG, "dg_rhs_vjp_noalloc: the mesh's device is not the current device");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(DG_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(dev, &scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  dgk::Ctx c = mesh->ctx();
+  c.Tv = scratch;  // every face side slot is written (seed) before it is read
+  dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
+  dgk::launch_vjp(c, 0, va, mesh->h.n_elems, mesh->wpb, stream);
+  dgk::launch_faces_vjp(c, (int64_t)mesh->h.face_blocks.size(), mesh->h.n, stream);
+  dgk::launch_vjp(c, 2, va, mesh->h.n_elems, mesh->wpb, stream);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
