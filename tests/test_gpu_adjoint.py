@@ -123,3 +123,28 @@ def test_tet_mesh_k20_central_differences(dg):
     g2 = mesh.get_state(mesh.rk_vjp(Q0, dt, K, 5, mesh.set_state(w2)))
     g12 = mesh.get_state(mesh.rk_vjp(Q0, dt, K, 5, mesh.set_state(w + w2)))
     assert np.abs(g12 - grad - g2).max() < 1e-11 * np.abs(g12).max()
+
+
+def test_autograd_wrappers(dg):
+    """torch.autograd: backward of DGRHS is dg_rhs_vjp, backward of DGRK is
+    dg_rk_vjp; the gradient of a kinetic-energy-like functional agrees with
+    central differences of the forward map."""
+    from paper_2511_08020_gb300.autograd import rhs, rk
+    box, o, mesh = setup(dg, "mixed", 2, 3, "lf", 5)
+    Q0 = mesh.set_state(state(o))
+    W = mesh.set_state(di.random_vector(mesh.n_dof, seed=3))
+    x = Q0.clone().requires_grad_(True)
+    (rhs(x, mesh) * W).sum().backward()
+    assert torch.equal(x.grad, mesh.rhs_vjp(Q0, W))
+    x = Q0.clone().requires_grad_(True)
+    QK = rk(x, mesh, 2e-3, 3, 2)
+    f = (QK * QK * W).sum()
+    f.backward()
+    v = torch.from_numpy(di.random_vector(mesh.n_dof, seed=8)).cuda() * Q0.abs().max() * 1e-3
+    h = 1e-4
+    def F(q):
+        Q = q.clone()
+        mesh.rk_step(Q, torch.empty_like(Q), 2e-3, 3)
+        return (Q * Q * W).sum()
+    fd = (F(Q0 + h * v) - F(Q0 - h * v)) / (2 * h)
+    assert abs(float(fd) - float((x.grad * v).sum())) < 1e-6 * abs(float(fd))
