@@ -149,19 +149,26 @@ def build_workload(flux="lf"):
     return box
 
 
-def tgv_dt(box, mesh_xyz, N):
-    """dt = CFL * min_e h_e / ((2N+1) max_q(|u| + c)), h_e = 6 Vol / Area(boundary),
-    evaluated once from the initial state (all cubes have the same size, so
-    the smallest h is the pyramid's)."""
-    h_cube = 2 * math.pi / MESH_M
-    # pyramid with a cube face as base and the cube centre as apex
+def h_min(m):
+    """Smallest element size h_e = 6 Vol / Area(boundary) of the m^3-cube box:
+    all cubes have the same size, so it is the pyramid's (a cube face as base,
+    the cube centre as apex)."""
+    h_cube = 2 * math.pi / m
     vol = h_cube ** 3 / 6.0
     slant = 0.5 * h_cube * math.sqrt(h_cube ** 2 / 4 + h_cube ** 2 / 4)
     area = h_cube ** 2 + 4 * slant
-    h_min = 6 * vol / area
+    return 6 * vol / area
+
+
+def tgv_smax(mesh_xyz):
     rho, u, v, w, p = di.tgv_primitive(mesh_xyz)
-    smax = float(np.max(np.sqrt(u * u + v * v + w * w) + np.sqrt(GAMMA * p / rho)))
-    return CFL * h_min / ((2 * N + 1) * smax)
+    return float(np.max(np.sqrt(u * u + v * v + w * w) + np.sqrt(GAMMA * p / rho)))
+
+
+def tgv_dt(box, mesh_xyz, N, m=MESH_M):
+    """dt = CFL * min_e h_e / ((2N+1) max_q(|u| + c)), evaluated once from the
+    initial state."""
+    return CFL * h_min(m) / ((2 * N + 1) * tgv_smax(mesh_xyz))
 
 
 def dist_info():
@@ -474,9 +481,85 @@ def run_ours(args):
                     "ratio_ckpt5": adj5_ms / fwd_ms, "ratio_one_segment": adjK_ms / fwd_ms,
                     "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms, "rhs_vjp_over_rhs": vjp_ms / rhs_ms},
     }
+    if args.batch_steps > 0:
+        line["batch"] = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+BATCH_WORKLOAD = ("64 independent periodic mixed hex/prism/pyramid boxes, m uniform on 4..20 cubes per "
+                  "direction, N uniform on {2,3,4,5} (dg_inputs.batch_workload seed 5), Euler TGV, LF, one "
+                  "dt (CFL 0.5 of the finest instance), FP64")
+
+
+def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
+    """Serving-style batch: all instances advance in one handle (one persistent
+    element launch and one face launch per phase, one CUDA graph per step)."""
+    import torch
+    work = di.batch_workload(64, seed=5)
+    boxes = [di.box_mesh(m, "mixed", seed=sd) for m, N, sd in work]
+    Ns = [N for m, N, sd in work]
+    b = dg.Batch(boxes, Ns, flux=args.flux, scheduler="balanced")
+    xyz = b.quad_points()
+    chunks, off = [], 0
+    for box, N in zip(boxes, Ns):
+        P = box.n_elems * (N + 1) ** 3
+        chunks.append(di.tgv_state(xyz[off:off + P]).reshape(5, box.n_elems, (N + 1) ** 3)
+                      .transpose(1, 0, 2).reshape(-1))
+        off += P
+    Q0 = b.project(torch.from_numpy(np.concatenate(chunks)).to(dev))
+    del chunks
+    smax = tgv_smax(xyz)
+    dt = min(CFL * h_min(m) / ((2 * N + 1) * smax) for m, N, _ in work)
+    dof = sum(int(sum(n_modes(int(t), N) for t in box.etype)) for box, N in zip(boxes, Ns))
+    el_flops_stage = sum(sum(element_flops(int(t), N) for t in box.etype) for box, N in zip(boxes, Ns))
+    steps = args.batch_steps
+
+    def timed(Q, K, profile=False):
+        b.set_profiling(profile)
+        for _ in range(args.warmup):
+            b.rk_step(Q, K, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el = 0.0
+        e0.record(stream)
+        for _ in range(steps):
+            b.rk_step(Q, K, dt, 1)
+            if profile:
+                el += b.phase_times()[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        b.set_profiling(False)
+        return max_over_ranks(e0.elapsed_time(e1)), el
+
+    out = {"workload": BATCH_WORKLOAD, "instances": len(work), "elements": b.n_elems, "faces": b.n_faces,
+           "dof_per_var": dof, "degrees": {str(k): Ns.count(k) for k in sorted(set(Ns))},
+           "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), b.type_counts)), "steps": steps, "dt": dt}
+    res = {}
+    for sched in ("naive", "balanced"):
+        b.set_scheduler(sched)
+        warps, _ = b.autotune(Q0, dt)
+        Q = Q0.clone()
+        K = torch.empty_like(Q)
+        ms, _ = timed(Q, K)
+        res[sched] = Q
+        out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps}
+    Qp = Q0.clone()
+    _, el_ms = timed(Qp, torch.empty_like(Qp), profile=True)
+    out["unit"] = "DOF-updates/s"
+    out["balanced_over_naive"] = out["balanced"]["value"] / out["naive"]["value"]
+    out["schedulers_bitwise_equal"] = bool(torch.equal(res["naive"], res["balanced"]))
+    out["element_kernel_tflops"] = el_flops_stage * 5 * steps / (el_ms * 1e-3) / 1e12
+    ns, imb = b.cost_table()
+    out["cost_table_ns_per_elem"] = dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns]))
+    out["sm_load_imbalance"] = imb
+    b.sync()
+    b.close()
+    return out
 
 
 def main():
@@ -489,6 +572,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=10,
+                    help="steps of the 64-instance batch leg (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

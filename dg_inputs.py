@@ -302,3 +302,18 @@ def random_modal_state(n_modes_per_elem, seed: int, mean=(1.0, 0.1, -0.05, 0.02,
 def random_vector(n: int, seed: int, amp=1.0):
     rng = np.random.Generator(np.random.PCG64(seed))
     return amp * rng.uniform(-1.0, 1.0, size=n)
+
+
+def batch_workload(n_instances: int = 64, seed: int = 5, m_min: int = 4, m_max: int = 20,
+                   degrees=(2, 3, 4, 5)):
+    """Serving-style batch recipe: instance i gets m_i cubes per direction,
+    uniform on [m_min, m_max] from splitmix64(seed ^ (2i + 2^40)), a degree
+    N_i uniform on `degrees` from splitmix64(seed ^ (2i + 1 + 2^40)), and a
+    'mixed' box mesh hashed with seed + i.  Returns [(m_i, N_i, mesh_seed_i)]."""
+    out = []
+    span = m_max - m_min + 1
+    for i in range(n_instances):
+        hm = splitmix64((seed ^ (2 * i + (1 << 40))) & MASK64)
+        hn = splitmix64((seed ^ (2 * i + 1 + (1 << 40))) & MASK64)
+        out.append((m_min + hm % span, int(degrees[hn % len(degrees)]), seed + i))
+    return out

@@ -109,6 +109,27 @@ typedef struct {
 dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out);
 dg_status dg_mesh_destroy(dg_mesh* mesh);
 
+/* Batch of independent meshes as one handle.  The paper advances one mesh at
+ * one N; a batch evaluates Eq. 1 on each instance separately (no face couples
+ * two instances), so every call below acts on all instances at once: one
+ * persistent element launch and one face launch per phase cover the whole
+ * batch, whatever the mix of types and N.  descs (host, [n_instances],
+ * caller-owned, read during the call): each instance's mesh and N; flux and
+ * gamma must be equal across instances (DG_ERR_ARG otherwise), scheduler and
+ * imbalance_threshold are taken from descs[0].  Operator tables are shared per
+ * (type, N).  Layouts (caller, storage, point values, quadrature points) are
+ * the instances' own layouts concatenated in instance order; element e of
+ * instance i is caller element instance_elem_off[i] + e.  Errors in one
+ * instance report its index in dg_last_error().  Synchronises `stream`;
+ * free with dg_mesh_destroy. */
+dg_status dg_batch_create(const dg_mesh_desc* descs, int n_instances, cudaStream_t stream, dg_mesh** out);
+
+/* Instance offsets of a handle from dg_batch_create (a plain mesh is a batch
+ * of one).  instance_elem_off, instance_dof_off (host, [n_instances + 1],
+ * may be NULL): first caller element and first state entry of each instance,
+ * the last entry being the totals. */
+dg_status dg_batch_layout(const dg_mesh* mesh, int64_t* instance_elem_off, int64_t* instance_dof_off);
+
 /* Host-only validation of a mesh description: runs the same set-up as
  * dg_mesh_create without touching a GPU.  counts (host, [8], may be NULL):
  * n_elems, n_faces, hex, prism, pyramid, tet counts, number of distinct
@@ -132,12 +153,14 @@ dg_status dg_set_state(dg_mesh* mesh, const double* Q_ext, int is_device, double
 dg_status dg_get_state(const dg_mesh* mesh, const double* Q_store, double* Q_ext, int is_device, cudaStream_t stream);
 
 /* Physical volume quadrature points (collapsed Gauss-Legendre, n^3 per element,
- * n = N+1), caller element order: host [n_elems * n^3][3].  Host-only. */
+ * n = N+1), caller element order: host [n_elems * n^3][3]; for a batch the
+ * instances' arrays concatenated (each with its own n).  Host-only. */
 dg_status dg_quad_points(const dg_mesh* mesh, double* xyz_out);
 
 /* Algorithm 1 projection Q = M^{-1} V^T W J q of point values q (device,
- * caller order, [n_elems][5][n^3] at the points of dg_quad_points) onto the
- * modal space, written to Q_store.  Asynchronous. */
+ * caller order, [n_elems][5][n^3] at the points of dg_quad_points; for a
+ * batch the instances' arrays concatenated) onto the modal space, written to
+ * Q_store.  Asynchronous. */
 dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cudaStream_t stream);
 
 /* R = M^{-1}(vol - surf) of Eq. 1 for the state Q_store; R_store (device,

@@ -13,7 +13,7 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "load"]
+__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
 SCHED = {"balanced": 0, "naive": 1, "static": 2}
@@ -41,6 +41,8 @@ _I64P = ctypes.POINTER(ctypes.c_int64)
 _DP = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "dg_mesh_create": [ctypes.POINTER(MeshDesc), _P, ctypes.POINTER(_P)],
+    "dg_batch_create": [ctypes.POINTER(MeshDesc), ctypes.c_int, _P, ctypes.POINTER(_P)],
+    "dg_batch_layout": [_P, _P, _P],
     "dg_mesh_destroy": [_P],
     "dg_mesh_check": [ctypes.POINTER(MeshDesc), _P, _P, _P],
     "dg_mesh_layout": [_P, _P, _P, _P],
@@ -156,15 +158,20 @@ class Mesh:
         d, keep = _desc(box, N, flux, gamma, scheduler, imbalance_threshold)
         h = ctypes.c_void_p()
         _check(load().dg_mesh_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self._adopt(h, keep["etype"].copy())
+        self.points_per_elem = np.full(self.n_elems, (self.N + 1) ** 3, dtype=np.int64)
+
+    def _adopt(self, h, etype):
+        import numpy as np
         self.handle = h
         n_dof = ctypes.c_int64()
-        self.slot_of_elem = np.zeros(len(keep["etype"]), dtype=np.int64)
+        self.slot_of_elem = np.zeros(len(etype), dtype=np.int64)
         counts = np.zeros(6, dtype=np.int64)
         _check(load().dg_mesh_layout(h, ctypes.byref(n_dof), _ptr(self.slot_of_elem), _ptr(counts)))
         self.n_dof = n_dof.value
         self.n_elems, self.n_faces = int(counts[0]), int(counts[1])
         self.type_counts = counts[2:].tolist()
-        self.etype = keep["etype"].copy()
+        self.etype = etype
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -210,13 +217,14 @@ class Mesh:
 
     def quad_points(self):
         import numpy as np
-        n = self.N + 1
-        xyz = np.zeros((self.n_elems * n ** 3, 3))
+        xyz = np.zeros((int(self.points_per_elem.sum()), 3))
         _check(load().dg_quad_points(self.handle, _ptr(xyz)))
         return xyz
 
     def project(self, q_points, Q_store=None, stream=None):
-        """Algorithm 1 projection of point values [n_elems, 5, n^3] (CUDA tensor)."""
+        """Algorithm 1 projection of point values (CUDA tensor): per caller
+        element its [5, n^3] block, elements concatenated ([n_elems, 5, n^3]
+        for a single mesh)."""
         if Q_store is None:
             Q_store = self.empty()
         _check(load().dg_project(self.handle, _ptr(q_points), _ptr(Q_store), _stream(stream)))
@@ -288,3 +296,44 @@ class Mesh:
 
     def sync(self, stream=None):
         _check(load().dg_sync(self.handle, _stream(stream)))
+
+
+class Batch(Mesh):
+    """Several independent periodic meshes, each with its own degree N,
+    advanced as one (dg_batch_create).  States, residuals and point values are
+    the instances' own layouts concatenated in instance order:
+    instance i owns caller elements elem_off[i]:elem_off[i+1] and state
+    entries dof_off[i]:dof_off[i+1] (in both the caller and the storage
+    layout).  All instances share flux and gamma."""
+
+    def __init__(self, boxes, Ns, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None):
+        import numpy as np
+        if len(boxes) != len(Ns) or not boxes:
+            raise ValueError("one N per mesh, at least one mesh")
+        k = len(boxes)
+        descs = (MeshDesc * k)()
+        self._keep = []
+        for i, (b, N) in enumerate(zip(boxes, Ns)):
+            d, keep = _desc(b, N, flux, gamma, scheduler, imbalance_threshold)
+            descs[i] = d
+            self._keep.append(keep)
+        self.Ns = [int(N) for N in Ns]
+        self.N = max(self.Ns)
+        self.flux = flux
+        h = ctypes.c_void_p()
+        _check(load().dg_batch_create(descs, k, _stream(stream), ctypes.byref(h)))
+        self._adopt(h, np.concatenate([kp["etype"] for kp in self._keep]))
+        self.elem_off = np.zeros(k + 1, dtype=np.int64)
+        self.dof_off = np.zeros(k + 1, dtype=np.int64)
+        _check(load().dg_batch_layout(h, _ptr(self.elem_off), _ptr(self.dof_off)))
+        self.points_per_elem = np.concatenate(
+            [np.full(len(kp["etype"]), (N + 1) ** 3, dtype=np.int64) for kp, N in zip(self._keep, self.Ns)])
+        self._keep = None
+
+    @property
+    def n_instances(self):
+        return len(self.Ns)
+
+    def instance(self, x, i):
+        """Entries of instance i in a batch state (caller or storage layout)."""
+        return x[int(self.dof_off[i]):int(self.dof_off[i + 1])]

@@ -68,7 +68,7 @@ struct dg_mesh {
   int* d_slot_tab = nullptr;
   int8_t* d_slot_type = nullptr;
   int64_t *d_slot_qoff = nullptr, *d_slot_hoff = nullptr, *d_slot_ftoff = nullptr;
-  int64_t *d_elem_of_slot = nullptr, *d_elem_qoff = nullptr;
+  int64_t *d_elem_of_slot = nullptr, *d_elem_qoff = nullptr, *d_elem_voff = nullptr;
   dgk::ElemGeo* d_geo = nullptr;
   double* d_H = nullptr;
   double* d_T = nullptr;
@@ -91,7 +91,14 @@ struct dg_mesh {
   int64_t nchunks_static = 0;
   int64_t* d_chunk_list = nullptr;
   bool fused = true;  // backward of stage s and forward of stage s+1 in one launch
-  double weight[4] = {1, 1, 1, 1};  // chunk weights in use (ns or modelled cost per element)
+  double weight[dgk::kMaxTabs] = {};  // chunk weights in use per (type, N) table (ns or modelled)
+
+  std::vector<double> static_weights() const {
+    std::vector<double> w(dgk::kMaxTabs, 1.0);
+    for (size_t i = 0; i < h.tables.tabs.size() && i < (size_t)dgk::kMaxTabs; ++i)
+      w[i] = dgh::static_cost(h.tables.tabs[i]);
+    return w;
+  }
   double* d_stage = nullptr;
   // graph cache for dg_rk_step
   cudaStream_t cap = nullptr;
@@ -149,6 +156,7 @@ struct dg_mesh {
     c.slot_ftoff = d_slot_ftoff;
     c.elem_of_slot = d_elem_of_slot;
     c.elem_qoff = d_elem_qoff;
+    c.elem_voff = d_elem_voff;
     c.geo = d_geo;
     c.H = d_H;
     c.T = d_T;
@@ -168,34 +176,36 @@ struct dg_mesh {
 
   int grid_balanced() const { return num_sms * blocks_per_sm; }
 
-  // Balanced work list: the Hilbert order grouped by element type (every
-  // type's elements stay in Hilbert order), types in decreasing cost per
+  // Balanced work list: the Hilbert order grouped by (type, N) table (every
+  // group's elements stay in Hilbert order), groups in decreasing cost per
   // element, cut into contiguous chunks by guided self-scheduling on the
   // measured (or modelled) cost: each chunk takes a fixed fraction of the
   // work still unassigned, so chunks are large at first and single elements
   // at the end, where they set the length of the tail.  A chunk never spans
-  // two types, so at any moment most blocks run one type's code.
-  cudaError_t build_chunks(const double* type_weight) {
+  // two groups, so at any moment most blocks run one group's code.
+  cudaError_t build_chunks(const double* tab_weight) {
     const int64_t E = h.n_elems;
-    for (int t = 0; t < 4; ++t) weight[t] = type_weight[t];
-    int order[4] = {0, 1, 2, 3};
-    std::stable_sort(order, order + 4, [&](int x, int y) { return type_weight[x] > type_weight[y]; });
+    const int ntab = (int)h.tables.tabs.size();
+    for (int t = 0; t < dgk::kMaxTabs; ++t) weight[t] = tab_weight[t];
+    std::vector<int> order(ntab);
+    for (int t = 0; t < ntab; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tab_weight[x] > tab_weight[y]; });
     std::vector<int64_t> list;
     list.reserve(E);
-    for (int oi = 0; oi < 4; ++oi)
+    for (int oi = 0; oi < ntab; ++oi)
       for (int64_t s = 0; s < E; ++s)
-        if (h.slot_type[s] == order[oi]) list.push_back(s);
+        if (h.slot_tab[s] == order[oi]) list.push_back(s);
     double remaining = 0.0;
-    for (int64_t s = 0; s < E; ++s) remaining += type_weight[h.slot_type[s]];
+    for (int64_t s = 0; s < E; ++s) remaining += tab_weight[h.slot_tab[s]];
     const double blocks = (double)std::max(1, grid_balanced());
     std::vector<int64_t> starts;
     starts.push_back(0);
     double acc = 0.0, target = remaining / (2.0 * blocks);
     for (int64_t i = 0; i < E; ++i) {
-      const double w = type_weight[h.slot_type[list[i]]];
+      const double w = tab_weight[h.slot_tab[list[i]]];
       acc += w;
       remaining -= w;
-      bool type_end = i + 1 < E && h.slot_type[list[i + 1]] != h.slot_type[list[i]];
+      bool type_end = i + 1 < E && h.slot_tab[list[i + 1]] != h.slot_tab[list[i]];
       if (i + 1 < E && (acc >= target || type_end)) {
         starts.push_back(i + 1);
         acc = 0.0;
@@ -311,7 +321,7 @@ struct dg_mesh {
 
   void release() {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
-                    d_elem_of_slot, d_elem_qoff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
+                    d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
                     d_Tv, d_Kbar, d_ckpt};
     for (void* p : ptrs)
@@ -329,25 +339,84 @@ extern "C" {
 
 const char* dg_last_error(void) { return g_err.c_str(); }
 
-dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out) {
-  if (!desc || !out) return fail(DG_ERR_ARG, "null argument");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+dg_status check_desc(const dg_mesh_desc* desc) {
   if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE) return fail(DG_ERR_ARG, "unknown flux");
   if (desc->scheduler < DG_SCHED_BALANCED || desc->scheduler > DG_SCHED_STATIC) return fail(DG_ERR_ARG, "unknown scheduler");
   if (!(desc->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
+  return DG_OK;
+}
+
+dgh::MeshInput input_of(const dg_mesh_desc* d) {
+  return dgh::MeshInput{d->n_vertices, d->xyz, d->n_elems, d->type, d->elem_vert_off, d->elem_verts, d->period, d->N};
+}
+
+dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out);
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out) {
+  if (!desc || !out) return fail(DG_ERR_ARG, "null argument");
+  *out = nullptr;
+  dg_status st = check_desc(desc);
+  if (st != DG_OK) return st;
   int ndev = 0;
   cudaError_t ce = cudaGetDeviceCount(&ndev);
   if (ce != cudaSuccess || ndev == 0) return fail(DG_ERR_CUDA, "no CUDA device available (the library has no CPU path)");
   dg_mesh* m = new (std::nothrow) dg_mesh();
   if (!m) return fail(DG_ERR_OOM, "host allocation failed");
-  dgh::MeshInput in{desc->n_vertices, desc->xyz, desc->n_elems, desc->type, desc->elem_vert_off, desc->elem_verts,
-                    desc->period, desc->N};
   std::string err;
-  int r = dgh::build_mesh(in, &m->h, &err);
+  int r = dgh::build_mesh(input_of(desc), &m->h, &err);
   if (r != 0) {
     delete m;
     return fail((dg_status)r, err);
   }
+  return create_device_mesh(m, desc, stream, out);
+}
+
+dg_status dg_batch_create(const dg_mesh_desc* descs, int n_instances, cudaStream_t stream, dg_mesh** out) {
+  if (!descs || !out || n_instances < 1) return fail(DG_ERR_ARG, "null argument or empty batch");
+  *out = nullptr;
+  for (int i = 0; i < n_instances; ++i) {
+    dg_status st = check_desc(descs + i);
+    if (st != DG_OK) return st;
+    if (descs[i].flux != descs[0].flux || descs[i].gamma != descs[0].gamma)
+      return fail(DG_ERR_ARG, "all instances of a batch must share flux and gamma");
+  }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) return fail(DG_ERR_CUDA, "no CUDA device available (the library has no CPU path)");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  std::vector<dgh::MeshInput> ins;
+  for (int i = 0; i < n_instances; ++i) ins.push_back(input_of(descs + i));
+  std::string err;
+  int r = dgh::build_batch(ins, &m->h, &err);
+  if (r != 0) {
+    delete m;
+    return fail((dg_status)r, err);
+  }
+  return create_device_mesh(m, descs, stream, out);
+}
+
+dg_status dg_batch_layout(const dg_mesh* mesh, int64_t* instance_elem_off, int64_t* instance_dof_off) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  const size_t k = mesh->h.inst_elem_off.size();
+  if (instance_elem_off) std::memcpy(instance_elem_off, mesh->h.inst_elem_off.data(), sizeof(int64_t) * k);
+  if (instance_dof_off) std::memcpy(instance_dof_off, mesh->h.inst_dof_off.data(), sizeof(int64_t) * k);
+  return DG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out) {
   m->flux = desc->flux;
   m->gamma = desc->gamma;
   m->scheduler = desc->scheduler;
@@ -376,6 +445,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
   if ((e = upload(&m->d_slot_ftoff, h.slot_ftoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_elem_of_slot, h.elem_of_slot)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_elem_qoff, h.elem_qoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
+  if ((e = upload(&m->d_elem_voff, h.elem_voff)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_geo, h.slot_geo)) != cudaSuccess) return fail_cuda(e, "upload geometry");
   if ((e = upload(&m->d_faces, h.faces)) != cudaSuccess) return fail_cuda(e, "upload faces");
   if ((e = upload(&m->d_fblocks, h.face_blocks)) != cudaSuccess) return fail_cuda(e, "upload faces");
@@ -388,18 +458,13 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
   if ((e = cudaMalloc(&m->d_stage, sizeof(double) * std::max<int64_t>(1, h.n_dof))) != cudaSuccess) return fail_cuda(e, "workspace");
   if ((e = cudaMalloc(&m->d_status, sizeof(unsigned))) != cudaSuccess) return fail_cuda(e, "workspace");
   if ((e = cudaMalloc(&m->d_counters, 2 * sizeof(unsigned))) != cudaSuccess) return fail_cuda(e, "workspace");
-  if ((e = cudaMalloc(&m->d_cost, 8 * sizeof(unsigned long long))) != cudaSuccess) return fail_cuda(e, "workspace");
+  if ((e = cudaMalloc(&m->d_cost, 2 * dgk::kMaxTabs * sizeof(unsigned long long))) != cudaSuccess) return fail_cuda(e, "workspace");
   if ((e = cudaMalloc(&m->d_smns, (size_t)m->num_sms * sizeof(unsigned long long))) != cudaSuccess) return fail_cuda(e, "workspace");
   cudaMemset(m->d_status, 0, sizeof(unsigned));
   cudaMemset(m->d_counters, 0, 2 * sizeof(unsigned));
-  cudaMemset(m->d_cost, 0, 8 * sizeof(unsigned long long));
+  cudaMemset(m->d_cost, 0, 2 * dgk::kMaxTabs * sizeof(unsigned long long));
   cudaMemset(m->d_smns, 0, (size_t)m->num_sms * sizeof(unsigned long long));
-  double w[4];
-  for (int t = 0; t < 4; ++t) {
-    int ti = h.tables.find(t, h.N);
-    w[t] = ti >= 0 ? dgh::static_cost(h.tables.tabs[ti]) : 1.0;
-  }
-  if ((e = m->build_chunks(w)) != cudaSuccess) return fail_cuda(e, "chunk table");
+  if ((e = m->build_chunks(m->static_weights().data())) != cudaSuccess) return fail_cuda(e, "chunk table");
   if ((e = m->build_static_chunks()) != cudaSuccess) return fail_cuda(e, "chunk table");
   if ((e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking)) != cudaSuccess) return fail_cuda(e, "stream");
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail_cuda(e, "synchronise");
@@ -407,6 +472,10 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
   *out = m;
   return DG_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_xyz, int64_t* slot_of_elem) {
   if (!desc) return fail(DG_ERR_ARG, "null argument");
@@ -649,52 +718,72 @@ dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler) {
   return DG_OK;
 }
 
+namespace {
+// Per-table cost bins (ns, count) and the per-SM busy times since the last reset.
+cudaError_t read_cost(dg_mesh* mesh, unsigned long long* cost, std::vector<unsigned long long>* sm,
+                      cudaStream_t stream) {
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(cost, mesh->d_cost, 2 * dgk::kMaxTabs * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  sm->assign(mesh->num_sms, 0ull);
+  return cudaMemcpy(sm->data(), mesh->d_smns, sizeof(unsigned long long) * sm->size(), cudaMemcpyDeviceToHost);
+}
+
+double busy_imbalance(const std::vector<unsigned long long>& sm) {
+  double mx = 0.0, sum = 0.0;
+  for (auto v : sm) { mx = std::max(mx, (double)v); sum += (double)v; }
+  double mean = sum / std::max<size_t>(1, sm.size());
+  return mean > 0 ? mx / mean - 1.0 : 0.0;
+}
+}  // namespace
+
 dg_status dg_cost_table(dg_mesh* mesh, double* ns_per_elem, double* imbalance, cudaStream_t stream) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
-  DG_CUDA(cudaStreamSynchronize(stream));
-  unsigned long long cost[8];
-  std::vector<unsigned long long> sm(mesh->num_sms);
-  DG_CUDA(cudaMemcpy(cost, mesh->d_cost, sizeof(cost), cudaMemcpyDeviceToHost));
-  DG_CUDA(cudaMemcpy(sm.data(), mesh->d_smns, sizeof(unsigned long long) * sm.size(), cudaMemcpyDeviceToHost));
-  if (ns_per_elem)
-    for (int t = 0; t < 4; ++t) ns_per_elem[t] = cost[2 * t + 1] ? (double)cost[2 * t] / (double)cost[2 * t + 1] : 0.0;
-  if (imbalance) {
-    double mx = 0.0, sum = 0.0;
-    for (auto v : sm) { mx = std::max(mx, (double)v); sum += (double)v; }
-    double mean = sum / std::max<size_t>(1, sm.size());
-    *imbalance = mean > 0 ? mx / mean - 1.0 : 0.0;
+  unsigned long long cost[2 * dgk::kMaxTabs];
+  std::vector<unsigned long long> sm;
+  DG_CUDA(read_cost(mesh, cost, &sm, stream));
+  if (ns_per_elem) {
+    // per element type, over every N the mesh (or batch) holds
+    double ns[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0};
+    const auto& tabs = mesh->h.tables.tabs;
+    for (size_t t = 0; t < tabs.size(); ++t) {
+      ns[tabs[t].type] += (double)cost[2 * t];
+      cnt[tabs[t].type] += (double)cost[2 * t + 1];
+    }
+    for (int t = 0; t < 4; ++t) ns_per_elem[t] = cnt[t] > 0 ? ns[t] / cnt[t] : 0.0;
   }
+  if (imbalance) *imbalance = busy_imbalance(sm);
   return DG_OK;
 }
 
 dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stream) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
-  double ns[4], imb = 0.0;
-  dg_status s = dg_cost_table(mesh, ns, &imb, stream);
-  if (s != DG_OK) return s;
-  bool measured = false;
-  for (int t = 0; t < 4; ++t) measured |= ns[t] > 0;
+  unsigned long long cost[2 * dgk::kMaxTabs];
+  std::vector<unsigned long long> sm;
+  DG_CUDA(read_cost(mesh, cost, &sm, stream));
+  const double imb = busy_imbalance(sm);
+  const auto& tabs = mesh->h.tables.tabs;
+  // Every table that holds elements must have been timed; otherwise the
+  // modelled weights stay.
+  bool measured = false, complete = true;
+  for (size_t t = 0; t < tabs.size(); ++t) {
+    if (cost[2 * t + 1]) measured = true;
+    else complete = false;
+  }
   bool doit = force || (measured && imb > mesh->threshold);
   if (rebuilt) *rebuilt = doit ? 1 : 0;
   if (doit) {
-    double w[4];
-    for (int t = 0; t < 4; ++t) {
-      int ti = mesh->h.tables.find(t, mesh->h.N);
-      w[t] = ns[t] > 0 ? ns[t] : (ti >= 0 ? dgh::static_cost(mesh->h.tables.tabs[ti]) : 1.0);
-    }
-    if (!measured) {
-      for (int t = 0; t < 4; ++t) {
-        int ti = mesh->h.tables.find(t, mesh->h.N);
-        w[t] = ti >= 0 ? dgh::static_cost(mesh->h.tables.tabs[ti]) : 1.0;
-      }
-    }
-    DG_CUDA(mesh->build_chunks(w));
+    std::vector<double> w = mesh->static_weights();
+    if (measured && complete)
+      for (size_t t = 0; t < tabs.size(); ++t) w[t] = (double)cost[2 * t] / (double)cost[2 * t + 1];
+    DG_CUDA(mesh->build_chunks(w.data()));
     if (mesh->gexec) {
       cudaGraphExecDestroy(mesh->gexec);
       mesh->gexec = nullptr;
     }
   }
-  DG_CUDA(cudaMemset(mesh->d_cost, 0, 8 * sizeof(unsigned long long)));
+  DG_CUDA(cudaMemset(mesh->d_cost, 0, 2 * dgk::kMaxTabs * sizeof(unsigned long long)));
   DG_CUDA(cudaMemset(mesh->d_smns, 0, (size_t)mesh->num_sms * sizeof(unsigned long long)));
   return DG_OK;
 }
@@ -705,9 +794,8 @@ dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
   mesh->wpb = warps;
   DG_CUDA(dgk::element_kernel_attributes(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm));
   if (mesh->blocks_per_sm < 1) mesh->blocks_per_sm = 1;
-  double w[4];
-  for (int t = 0; t < 4; ++t) w[t] = mesh->weight[t];
-  DG_CUDA(mesh->build_chunks(w));
+  std::vector<double> w(mesh->weight, mesh->weight + dgk::kMaxTabs);
+  DG_CUDA(mesh->build_chunks(w.data()));
   DG_CUDA(mesh->build_static_chunks());
   if (mesh->gexec) {
     cudaGraphExecDestroy(mesh->gexec);

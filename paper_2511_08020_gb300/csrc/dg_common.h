@@ -18,6 +18,7 @@ namespace dgk {
 constexpr int kMaxN = 6;
 constexpr int kMaxn = kMaxN + 1;
 constexpr int kNumTypes = 4;
+constexpr int kMaxTabs = kNumTypes * kMaxN;   // (type, N) tables, N = 1..kMaxN
 enum { HEX = 0, PRISM = 1, PYR = 2, TET = 3 };
 
 // Face descriptor of a local face: the face points are the tensor grid of
@@ -61,8 +62,9 @@ struct ElemGeo {
 // Face record for the face kernel.  Side 0 = owner (smaller caller index);
 // its face points and outward normal are used.  The neighbour's face values
 // at its own points are mapped to the owner's points by `map`:
-//   map >= 0 : index permutation perm[map][p] (and its inverse pinv)
-//   map <  0 : dense interpolation matrix I[-1-map][p][j]
+//   map >= 0 : index permutation at perms + map: perm[p] (n^2 entries),
+//              then its inverse (n^2 entries)
+//   map <  0 : dense interpolation matrix I[p][j] at dense + (-1 - map)
 struct FaceRec {
   int64_t toff;     // double offset of side 0 trace block; side 1 at toff + 5 n^2
   int map;

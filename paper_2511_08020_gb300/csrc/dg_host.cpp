@@ -642,6 +642,10 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   {
     int64_t q = 0;
     for (int64_t e = 0; e < E; ++e) { M.elem_qoff[e] = q; q += 5 * (int64_t)n_modes(in.type[e], N); }
+    M.elem_voff.resize(E);
+    for (int64_t e = 0; e < E; ++e) M.elem_voff[e] = e * 5 * (int64_t)n * n * n;
+    M.inst_elem_off = {0, E};
+    M.inst_dof_off = {0, q};
     M.n_dof = q;
     int64_t qs = 0, hs = 0;
     for (int64_t s = 0; s < E; ++s) {
@@ -798,7 +802,7 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
         }
       auto it = perm_ids.find(perm);
       if (it == perm_ids.end()) {
-        it = perm_ids.emplace(perm, (int)perm_ids.size()).first;
+        it = perm_ids.emplace(perm, (int)M.perms.size()).first;
         M.perms.insert(M.perms.end(), perm.begin(), perm.end());
       }
       R.map = it->second;
@@ -814,7 +818,7 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
         }
       auto it = perm_ids.find(perm);
       if (it == perm_ids.end()) {
-        it = perm_ids.emplace(perm, (int)perm_ids.size()).first;
+        it = perm_ids.emplace(perm, (int)M.perms.size()).first;
         M.perms.insert(M.perms.end(), perm.begin(), perm.end());
       }
       R.map = it->second;
@@ -825,7 +829,7 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
       std::vector<int> key = {sigma[0], sigma[1], sigma[2]};
       auto it = dense_ids.find(key);
       if (it == dense_ids.end()) {
-        it = dense_ids.emplace(key, (int)dense_ids.size()).first;
+        it = dense_ids.emplace(key, (int)M.dense.size()).first;
         std::vector<double> la(n), lb(n);
         size_t base = M.dense.size();
         M.dense.resize(base + (size_t)n2 * n2);
@@ -887,6 +891,82 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
             M.quad_xyz[3 * q + d] = v;
           }
         }
+  }
+  return 0;
+}
+
+int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* err) {
+  if (ins.empty()) { *err = "empty batch"; return -1; }
+  HostMesh& M = *out;
+  M = HostMesh();
+  int64_t e_off = 0, q_off = 0, h_off = 0, t_off = 0, v_off = 0, f_off = 0;
+  M.inst_elem_off = {0};
+  M.inst_dof_off = {0};
+  for (size_t i = 0; i < ins.size(); ++i) {
+    HostMesh Mi;
+    Mi.tables = M.tables;  // (type, N) tables are shared by all instances
+    int r = build_mesh(ins[i], &Mi, err);
+    if (r != 0) {
+      *err = "instance " + std::to_string(i) + ": " + *err;
+      return r;
+    }
+    M.tables = std::move(Mi.tables);
+    const int64_t E = Mi.n_elems;
+    const int64_t p_off = (int64_t)M.perms.size(), d_off = (int64_t)M.dense.size();
+    for (int64_t s = 0; s < E; ++s) {
+      M.elem_of_slot.push_back(Mi.elem_of_slot[s] + e_off);
+      M.slot_tab.push_back(Mi.slot_tab[s]);
+      M.slot_type.push_back(Mi.slot_type[s]);
+      M.slot_qoff.push_back(Mi.slot_qoff[s] + q_off);
+      M.slot_hoff.push_back(Mi.slot_hoff[s] + h_off);
+      M.slot_geo.push_back(Mi.slot_geo[s]);
+      for (int lf = 0; lf < 6; ++lf) {
+        int64_t t = Mi.slot_ftoff[(size_t)s * 6 + lf];
+        M.slot_ftoff.push_back(t >= 0 ? t + t_off : -1);
+      }
+    }
+    for (int64_t e = 0; e < E; ++e) {
+      M.slot_of_elem.push_back(Mi.slot_of_elem[e] + e_off);
+      M.elem_qoff.push_back(Mi.elem_qoff[e] + q_off);
+      M.elem_voff.push_back(Mi.elem_voff[e] + v_off);
+    }
+    M.perms.insert(M.perms.end(), Mi.perms.begin(), Mi.perms.end());
+    M.dense.insert(M.dense.end(), Mi.dense.begin(), Mi.dense.end());
+    for (dgk::FaceRec R : Mi.faces) {
+      R.toff += t_off;
+      R.map = R.map >= 0 ? (int)(R.map + p_off) : (int)(-1 - ((-1 - R.map) + d_off));
+      M.faces.push_back(R);
+    }
+    for (dgk::FaceBlock b : Mi.face_blocks) {
+      b.first += (int)f_off;
+      M.face_blocks.push_back(b);
+    }
+    for (int t = 0; t < 4; ++t) {
+      for (int64_t s : Mi.type_slots[t]) M.type_slots[t].push_back(s + e_off);
+      M.type_count[t] += Mi.type_count[t];
+    }
+    M.quad_xyz.insert(M.quad_xyz.end(), Mi.quad_xyz.begin(), Mi.quad_xyz.end());
+    M.n_perm += Mi.n_perm;
+    M.n_dense += Mi.n_dense;
+    M.N = std::max(M.N, Mi.N);
+    M.n = std::max(M.n, Mi.n);
+    e_off += E;
+    q_off += Mi.n_dof;
+    h_off += Mi.h_total;
+    t_off += Mi.t_total;
+    v_off += E * 5 * (int64_t)Mi.n * Mi.n * Mi.n;
+    f_off += Mi.n_faces;
+    M.inst_elem_off.push_back(e_off);
+    M.inst_dof_off.push_back(q_off);
+  }
+  M.n_elems = e_off;
+  M.n_dof = q_off;
+  M.h_total = h_off;
+  M.t_total = t_off;
+  M.n_faces = f_off;
+  if (f_off >= (int64_t)1 << 31 || (int64_t)M.perms.size() >= (int64_t)1 << 31 || (int64_t)M.dense.size() >= (int64_t)1 << 31) {
+    *err = "batch too large for 32-bit face indices";
+    return -7;
   }
   return 0;
 }

@@ -63,6 +63,9 @@ struct HostMesh {
   std::vector<int64_t> slot_ftoff;           // [slot][6] trace offset of (face, own side)
   // per caller element
   std::vector<int64_t> elem_qoff;            // caller-layout offsets
+  std::vector<int64_t> elem_voff;            // offsets of [5][n^3] point values (projection input)
+  // instances of a batch (one instance for a plain mesh): element and dof offsets
+  std::vector<int64_t> inst_elem_off, inst_dof_off;
   // faces (face-kernel order)
   std::vector<dgk::FaceRec> faces;
   std::vector<dgk::FaceBlock> face_blocks;
@@ -78,6 +81,11 @@ struct HostMesh {
 
 // returns 0 on success, -2 (mesh) / -1 (argument) / -7 (unsupported) with *err
 int build_mesh(const MeshInput& in, HostMesh* out, std::string* err);
+
+// Several independent meshes (any mix of N) as one: instances are
+// concatenated (slots, caller elements, states, faces); operator tables are
+// shared per (type, N).
+int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* err);
 
 uint64_t hilbert_key3(uint32_t x, uint32_t y, uint32_t z, int bits);
 

@@ -664,7 +664,7 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
   }
   if (MODE == kProject) {
     const int64_t e = c.elem_of_slot[s];
-    const double* vals = io.Qin + e * 5 * (int64_t)nQ;
+    const double* vals = io.Qin + c.elem_voff[e];
     const double* W = c.dpool + T.W;
     for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * vals[w];
     __syncthreads();
@@ -811,8 +811,11 @@ __global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io,
   const int lane = threadIdx.x;
   double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
-  unsigned long long ns0 = 0, ns1 = 0, ns2 = 0, ns3 = 0, busy = 0;
-  unsigned n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+  // Cost probe: time per element, summed per (type, N) table in shared bins
+  // (thread 0 alone touches them) and flushed once at the end.
+  __shared__ unsigned long long s_cost[2 * kMaxTabs];
+  for (int t = lane; t < 2 * kMaxTabs; t += blockDim.x) s_cost[t] = 0ull;
+  unsigned long long busy = 0;
   while (true) {
     if (lane == 0) s_chunk = atomicAdd(counter, 1u);
     __syncthreads();
@@ -825,20 +828,20 @@ __global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io,
       process_element<MODE>(c, io, s, bufA, bufG, lane);
       __syncthreads();
       uint64_t dtn = global_ns() - t0;
-      switch (c.slot_type[s]) {
-        case HEX: ns0 += dtn; ++n0; break;
-        case PRISM: ns1 += dtn; ++n1; break;
-        case PYR: ns2 += dtn; ++n2; break;
-        default: ns3 += dtn; ++n3; break;
+      if (lane == 0) {
+        const int tab = c.slot_tab[s];
+        s_cost[2 * tab] += dtn;
+        s_cost[2 * tab + 1] += 1ull;
       }
       busy += dtn;
     }
   }
   if (lane == 0 && c.cost) {
-    if (n0) { atomicAdd(c.cost + 0, ns0); atomicAdd(c.cost + 1, (unsigned long long)n0); }
-    if (n1) { atomicAdd(c.cost + 2, ns1); atomicAdd(c.cost + 3, (unsigned long long)n1); }
-    if (n2) { atomicAdd(c.cost + 4, ns2); atomicAdd(c.cost + 5, (unsigned long long)n2); }
-    if (n3) { atomicAdd(c.cost + 6, ns3); atomicAdd(c.cost + 7, (unsigned long long)n3); }
+    for (int t = 0; t < kMaxTabs; ++t)
+      if (s_cost[2 * t + 1]) {
+        atomicAdd(c.cost + 2 * t, s_cost[2 * t]);
+        atomicAdd(c.cost + 2 * t + 1, s_cost[2 * t + 1]);
+      }
     if (busy) atomicAdd(c.sm_ns + smid(), busy);
   }
 }
@@ -857,11 +860,11 @@ __global__ void face_kernel(Ctx c) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) UL[v] = T0[v * n2 + p];
     if (R.map >= 0) {
-      int j = c.perms[(size_t)R.map * 2 * n2 + p];
+      int j = c.perms[(size_t)R.map + p];
 #pragma unroll
       for (int v = 0; v < 5; ++v) UR[v] = T1[v * n2 + j];
     } else {
-      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + (size_t)p * n2;
+      const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         double acc = 0.0;
@@ -888,11 +891,11 @@ __global__ void face_kernel(Ctx c) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) T0[v * n2 + q] = F[v * n2 + q];
     if (R.map >= 0) {
-      int p = c.perms[(size_t)R.map * 2 * n2 + n2 + q];
+      int p = c.perms[(size_t)R.map + n2 + q];
 #pragma unroll
       for (int v = 0; v < 5; ++v) T1[v * n2 + q] = -F[v * n2 + p];
     } else {
-      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + q;
+      const double* D = c.dense + (size_t)(-1 - R.map) + q;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         double acc = 0.0;
@@ -940,14 +943,14 @@ __global__ void face_vjp_kernel(Ctx c) {
       g[v] = S0[v * n2 + p];
     }
     if (R.map >= 0) {
-      int j = c.perms[(size_t)R.map * 2 * n2 + p];
+      int j = c.perms[(size_t)R.map + p];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         UR[v] = T1[v * n2 + j];
         g[v] -= S1[v * n2 + j];
       }
     } else {
-      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + (size_t)p * n2;
+      const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         double a = 0.0, b = 0.0;
@@ -984,11 +987,11 @@ __global__ void face_vjp_kernel(Ctx c) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) S0[v * n2 + q] = Fl[v * n2 + q];
     if (R.map >= 0) {
-      int p = c.perms[(size_t)R.map * 2 * n2 + n2 + q];
+      int p = c.perms[(size_t)R.map + n2 + q];
 #pragma unroll
       for (int v = 0; v < 5; ++v) S1[v * n2 + q] = Fr[v * n2 + p];
     } else {
-      const double* D = c.dense + (size_t)(-1 - R.map) * n2 * n2 + q;
+      const double* D = c.dense + (size_t)(-1 - R.map) + q;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         double acc = 0.0;

@@ -44,6 +44,7 @@ struct Ctx {
   const int64_t* slot_ftoff;   // [slot][6]
   const int64_t* elem_of_slot;
   const int64_t* elem_qoff;    // caller layout offsets
+  const int64_t* elem_voff;    // caller element -> offset of its [5][n^3] point values (projection input)
   const ElemGeo* geo;
   double* H;
   double* T;
@@ -53,7 +54,7 @@ struct Ctx {
   const int16_t* perms;
   const double* dense;
   unsigned int* status;        // bit 0: non-finite state seen
-  unsigned long long* cost;    // [4 types][2]: ns, count
+  unsigned long long* cost;    // [kMaxTabs tables][2]: ns, count
   unsigned long long* sm_ns;   // [num SMs]
   double gamma;
   int flux;                    // 0 LF, 1 Roe

@@ -98,3 +98,23 @@ def test_no_cpu_fallback_without_gpu(dg):
     with pytest.raises(dg.DGError) as ei:
         dg.Mesh(di.box_mesh(2, "hex", seed=1), 2, stream=0)
     assert ei.value.status == -3
+
+
+def test_batch_argument_checks_without_gpu(dg):
+    """dg_batch_create validates its descriptions before touching a device:
+    mixed flux is DG_ERR_ARG, an empty batch is DG_ERR_ARG, and a valid batch
+    without a GPU is DG_ERR_CUDA (no CPU path)."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    b0, b1 = di.box_mesh(2, "hex", seed=1), di.box_mesh(2, "kuhn", seed=2)
+    d0, k0 = dg._desc(b0, 2, flux="lf")
+    d1, k1 = dg._desc(b1, 3, flux="roe")
+    h = ctypes.c_void_p()
+    assert dg.load().dg_batch_create((dg.MeshDesc * 2)(d0, d1), 2, None, ctypes.byref(h)) == -1
+    assert dg.load().dg_batch_create((dg.MeshDesc * 1)(d0), 0, None, ctypes.byref(h)) == -1
+    if torch.cuda.is_available():
+        return
+    d1, k1 = dg._desc(b1, 3, flux="lf")
+    with pytest.raises(dg.DGError) as ei:
+        dg.Batch([b0, b1], [2, 3], stream=0)
+    assert ei.value.status == -3
