@@ -72,6 +72,7 @@ typedef enum {
 
 typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1 } dg_flux;
 typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1, DG_SCHED_STATIC = 2 } dg_scheduler;
+typedef enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 } dg_physics;
 
 /* Mesh description, caller-owned, read only during dg_mesh_create.
  * Elements are affine images of the reference elements; the local vertex
@@ -205,6 +206,24 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
  * steps in library memory.  No counterpart in the paper.  Asynchronous. */
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream);
+
+/* Governing equations of dg_rhs / dg_rk_step (a new mesh solves the Euler
+ * equations).  DG_NAVIER_STOKES: the Navier-Stokes-Fourier equations that
+ * the paper's solver integrates (Sec. 2; Eq. 1 with a flux F(q, grad q); the
+ * viscous TGV of Sec. 4), with constant dynamic viscosity mu (>= 0), Prandtl
+ * number Pr (> 0), Stokes stress and Fourier heat flux
+ * q = -mu gamma / ((gamma - 1) Pr) grad(p / rho).  The paper does not print
+ * its viscous scheme; the library uses BR1 lifting of the primitive
+ * variables W = (rho, u, v, w, p): per element the modal gradient
+ * G_d = M^{-1}(sum_f int phi W* n_d dS - int W dphi/dx_d dx), W* the mean of
+ * both traces, and the central viscous face flux (F_v(U-, G-) + F_v(U+, G+)).n/2
+ * added to the inviscid Riemann flux.  Per RK stage this adds one face phase
+ * (lifting values) and one element phase (gradient, traces, volume term).
+ * Allocates the workspace (nodal state, lifting values, gradient traces: 5
+ * times the face buffer plus the nodal residual) on first use; DG_ERR_OOM if
+ * that fails.  mu and Pr are ignored for DG_EULER.  The adjoint entry points
+ * return DG_ERR_UNSUPPORTED while Navier-Stokes is selected. */
+dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr);
 
 /* Scheduler of the element kernels: DG_SCHED_BALANCED (one persistent launch
  * per phase, warps take cost-weighted Hilbert-contiguous element chunks from

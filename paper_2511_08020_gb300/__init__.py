@@ -13,10 +13,11 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "load"]
+__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "PHYSICS", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
 SCHED = {"balanced": 0, "naive": 1, "static": 2}
+PHYSICS = {"euler": 0, "navier_stokes": 1}
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_OOM",
           -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_UNSUPPORTED"}
 
@@ -55,6 +56,7 @@ _SIGS = {
     "dg_rhs_vjp": [_P, _P, _P, _P, _P],
     "dg_rk_vjp": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "dg_set_scheduler": [_P, ctypes.c_int],
+    "dg_set_physics": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
     "dg_cost_table": [_P, _P, _P, _P],
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
     "dg_sync": [_P, _P],
@@ -253,6 +255,12 @@ class Mesh:
         _check(load().dg_rk_vjp(self.handle, _ptr(Q0_store), float(dt), int(nsteps), int(ckpt_every),
                                 _ptr(QKbar), _ptr(Q0bar), _stream(stream)))
         return Q0bar
+
+    # ---------------------------------------------------------------- physics
+    def set_physics(self, physics="euler", mu=0.0, Pr=0.72):
+        """'euler' or 'navier_stokes' (BR1 lifting, constant mu, Prandtl number Pr)."""
+        _check(load().dg_set_physics(self.handle, PHYSICS[physics] if isinstance(physics, str) else int(physics),
+                                     float(mu), float(Pr)))
 
     # ---------------------------------------------------------------- scheduler
     def set_scheduler(self, kind):

@@ -61,6 +61,10 @@ struct dg_mesh {
   int scheduler = DG_SCHED_BALANCED;
   double threshold = 0.1;
   int nQmax = 0, wpb = 2, blocks_per_sm = 1, num_sms = 1;
+  // Navier-Stokes (BR1): off until dg_set_physics; buffers allocated then
+  int ns = 0, blocks_per_sm_ns = 1;
+  double mu = 0.0, Pr = 0.72;
+  double *d_Unod = nullptr, *d_L = nullptr, *d_Vt = nullptr, *d_fnrm = nullptr;
   // device data
   double* d_dpool = nullptr;
   int* d_ipool = nullptr;
@@ -158,6 +162,13 @@ struct dg_mesh {
     c.elem_qoff = d_elem_qoff;
     c.elem_voff = d_elem_voff;
     c.geo = d_geo;
+    c.ns = ns;
+    c.mu = mu;
+    c.kappa = ns ? mu * gamma / ((gamma - 1.0) * Pr) : 0.0;
+    c.fnrm = d_fnrm;
+    c.Unod = d_Unod;
+    c.L = d_L;
+    c.Vt = d_Vt;
     c.H = d_H;
     c.T = d_T;
     c.Tv = d_Tv;
@@ -175,6 +186,7 @@ struct dg_mesh {
   }
 
   int grid_balanced() const { return num_sms * blocks_per_sm; }
+  int grid_ns() const { return num_sms * blocks_per_sm_ns; }
 
   // Balanced work list: the Hilbert order grouped by (type, N) table (every
   // group's elements stay in Hilbert order), groups in decreasing cost per
@@ -240,7 +252,7 @@ struct dg_mesh {
         const bool stat = scheduler == DG_SCHED_STATIC;
         dgk::Sched s{stat ? nullptr : d_chunk_list, stat ? nchunks_static : nchunks, stat ? d_chunks_static : d_chunks,
                      d_counters + parity, d_counters + (parity ^ 1)};
-        dgk::launch_element(c, mode, a, s, true, grid_balanced(), wpb, st);
+        dgk::launch_element(c, mode, a, s, true, mode == dgk::kNsVolume ? grid_ns() : grid_balanced(), wpb, st);
         parity ^= 1;
       } else {
         for (int t = 0; t < 4; ++t) {
@@ -252,8 +264,19 @@ struct dg_mesh {
     });
   }
 
+  // Face phase of one residual evaluation.  Navier-Stokes inserts the BR1
+  // lifting (face values of W*, then the element volume phase that lifts the
+  // gradient and forms the volume residual) before the flux face kernel.
   void face_phase(cudaStream_t st) {
-    timed(false, st, [&] { dgk::launch_faces(ctx(), (int64_t)h.face_blocks.size(), h.n, st); });
+    const int64_t nb = (int64_t)h.face_blocks.size();
+    if (ns) {
+      timed(false, st, [&] { dgk::launch_faces_ns(ctx(), nb, h.n, 0, st); });
+      dgk::StageArgs none{nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+      element_phase(dgk::kNsVolume, none, st);
+      timed(false, st, [&] { dgk::launch_faces_ns(ctx(), nb, h.n, 1, st); });
+      return;
+    }
+    timed(false, st, [&] { dgk::launch_faces(ctx(), nb, h.n, st); });
   }
 
   // Enqueue nsteps LSERK steps (no synchronisation).
@@ -323,7 +346,7 @@ struct dg_mesh {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
-                    d_Tv, d_Kbar, d_ckpt};
+                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -447,6 +470,7 @@ dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t 
   if ((e = upload(&m->d_elem_qoff, h.elem_qoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_elem_voff, h.elem_voff)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_geo, h.slot_geo)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+  if ((e = upload(&m->d_fnrm, h.slot_fnrm)) != cudaSuccess) return fail_cuda(e, "upload geometry");
   if ((e = upload(&m->d_faces, h.faces)) != cudaSuccess) return fail_cuda(e, "upload faces");
   if ((e = upload(&m->d_fblocks, h.face_blocks)) != cudaSuccess) return fail_cuda(e, "upload faces");
   if ((e = upload(&m->d_perms, h.perms)) != cudaSuccess) return fail_cuda(e, "upload maps");
@@ -604,6 +628,7 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the Euler equations only (dg_set_physics)");
   DG_CUDA(mesh->ensure_adjoint(0));
   dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
   mesh->enqueue_vjp(va, stream);
@@ -648,6 +673,7 @@ extern "C" {
 dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
                              cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the Euler equations only (dg_set_physics)");
   const size_t need = (size_t)std::max<int64_t>(1, mesh->h.t_total);
   if (need > kNoAllocScratchDoubles)
     return fail(DG_ERR_ARG, "dg_rhs_vjp_noalloc: the mesh needs " + std::to_string(need) +
@@ -678,6 +704,7 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream) {
   if (!mesh || !Q0_store || !QKbar || !Q0bar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the Euler equations only (dg_set_physics)");
   if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
@@ -708,6 +735,30 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
       }
   }
   DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
+  if (physics == DG_NAVIER_STOKES) {
+    if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(DG_ERR_ARG, "mu must be finite and >= 0");
+    if (!(Pr > 0.0) || !std::isfinite(Pr)) return fail(DG_ERR_ARG, "Pr must be finite and > 0");
+    const size_t hb = sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.h_total);
+    const size_t tb = sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.t_total);
+    if (!mesh->d_Unod && cudaMalloc(&mesh->d_Unod, hb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
+    if (!mesh->d_L && cudaMalloc(&mesh->d_L, tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
+    if (!mesh->d_Vt && cudaMalloc(&mesh->d_Vt, 3 * tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
+    DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns));
+    if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;
+    mesh->mu = mu;
+    mesh->Pr = Pr;
+  }
+  mesh->ns = physics == DG_NAVIER_STOKES;
+  if (mesh->gexec) {
+    cudaGraphExecDestroy(mesh->gexec);
+    mesh->gexec = nullptr;
+  }
   return DG_OK;
 }
 
@@ -794,6 +845,10 @@ dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
   mesh->wpb = warps;
   DG_CUDA(dgk::element_kernel_attributes(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm));
   if (mesh->blocks_per_sm < 1) mesh->blocks_per_sm = 1;
+  if (mesh->ns) {
+    DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns));
+    if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;
+  }
   std::vector<double> w(mesh->weight, mesh->weight + dgk::kMaxTabs);
   DG_CUDA(mesh->build_chunks(w.data()));
   DG_CUDA(mesh->build_static_chunks());

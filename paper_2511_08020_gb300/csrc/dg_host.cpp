@@ -716,6 +716,7 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   M.n_faces = F;
   M.faces.resize(F);
   M.slot_ftoff.assign((size_t)E * 6, -1);
+  M.slot_fnrm.assign((size_t)E * 18, 0.0);
   M.perms.clear();
   M.dense.clear();
   std::map<std::vector<int16_t>, int> perm_ids;
@@ -856,6 +857,10 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
     int64_t s0 = M.slot_of_elem[ft.e0], s1 = M.slot_of_elem[ft.e1];
     M.slot_ftoff[(size_t)s0 * 6 + ft.l0] = R.toff;
     M.slot_ftoff[(size_t)s1 * 6 + ft.l1] = R.toff + 5 * (int64_t)n2;
+    for (int d = 0; d < 3; ++d) {
+      M.slot_fnrm[((size_t)s0 * 6 + ft.l0) * 3 + d] = R.nrm[d];
+      M.slot_fnrm[((size_t)s1 * 6 + ft.l1) * 3 + d] = -R.nrm[d];
+    }
   }
   M.n_perm = (int)perm_ids.size();
   M.n_dense = (int)dense_ids.size();
@@ -923,6 +928,7 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
       for (int lf = 0; lf < 6; ++lf) {
         int64_t t = Mi.slot_ftoff[(size_t)s * 6 + lf];
         M.slot_ftoff.push_back(t >= 0 ? t + t_off : -1);
+        for (int d = 0; d < 3; ++d) M.slot_fnrm.push_back(Mi.slot_fnrm[((size_t)s * 6 + lf) * 3 + d]);
       }
     }
     for (int64_t e = 0; e < E; ++e) {

@@ -61,6 +61,8 @@ struct HostMesh {
   std::vector<int64_t> slot_qoff, slot_hoff; // double offsets
   std::vector<dgk::ElemGeo> slot_geo;
   std::vector<int64_t> slot_ftoff;           // [slot][6] trace offset of (face, own side)
+  std::vector<double> slot_fnrm;             // [slot][6][3] outward unit normal of each local face
+                                             // (the owner's normal, negated on the neighbour side)
   // per caller element
   std::vector<int64_t> elem_qoff;            // caller-layout offsets
   std::vector<int64_t> elem_voff;            // offsets of [5][n^3] point values (projection input)

@@ -100,6 +100,42 @@ __device__ __forceinline__ void flux_roe(const double* UL, const double* UR, con
   for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (L.F[v] + R.F[v]) - 0.5 * D[v];
 }
 
+// ------------------------------------------------------------------ viscous physics
+//
+// Navier-Stokes-Fourier fluxes with BR1 lifting of the primitive variables
+// W = (rho, u, v, w, p): g[d * 5 + v] = dW_v / dx_d (the lifted gradient),
+//   tau  = mu (grad u + grad u^T - 2/3 div u I)          (Stokes hypothesis)
+//   F_v[d] = (0, tau_{x d}, tau_{y d}, tau_{z d}, u . tau_{. d} + kappa d(p/rho)/dx_d)
+// with kappa = mu gamma / ((gamma - 1) Pr) (Fourier heat flux q = -kappa grad(p/rho)).
+
+__device__ __forceinline__ void primitive(const double* U, double gm1, double* W) {
+  const double r = 1.0 / U[0];
+  W[0] = U[0];
+  W[1] = U[1] * r;
+  W[2] = U[2] * r;
+  W[3] = U[3] * r;
+  W[4] = gm1 * (U[4] - 0.5 * (U[1] * W[1] + U[2] * W[2] + U[3] * W[3]));
+}
+
+__device__ __forceinline__ void viscous_flux(const double* W, const double* g, double mu, double kappa,
+                                             double Fv[3][5]) {
+  const double div = g[1] + g[5 + 2] + g[10 + 3];
+  const double rinv = 1.0 / W[0], Tr = W[4] * rinv;
+  const double lam = (2.0 / 3.0) * mu * div;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tau[i] = mu * (g[d * 5 + 1 + i] + g[i * 5 + 1 + d]) - (i == d ? lam : 0.0);
+    const double dT = (g[d * 5 + 4] - Tr * g[d * 5]) * rinv;
+    Fv[d][0] = 0.0;
+    Fv[d][1] = tau[0];
+    Fv[d][2] = tau[1];
+    Fv[d][3] = tau[2];
+    Fv[d][4] = W[1] * tau[0] + W[2] * tau[1] + W[3] * tau[2] + kappa * dT;
+  }
+}
+
 // ------------------------------------------------------------------ adjoint physics
 // Hand-written reverse mode of the functions above.  Readings at the kinks:
 // d|x|/dx = sign(x) with sign(0) = 0; max(aL, aR) passes its cotangent to the
@@ -493,7 +529,8 @@ __device__ __noinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, doub
 // Values of the nodal field `src` [5][nQ] on the element's own face points,
 // times `scale`, written to the face buffer `dst` at the element's side slots.
 __device__ __forceinline__ void write_traces(const Ctx& c, const TypeTab& T, int64_t s, const double* src,
-                                             double* dst, double scale, int lane) {
+                                             double* dst, double scale, int lane, int ft_mult = 1,
+                                             int64_t ft_add = 0) {
   const int n = T.n, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int cnt = T.nfaces * n2;
@@ -509,7 +546,7 @@ __device__ __forceinline__ void write_traces(const Ctx& c, const TypeTab& T, int
     const double* U = src + ia * sa + ib * sb;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int m = 0; m < n; ++m) DG_FMA5(e[m], U + m * sf, nQ, acc);
-    double* out = dst + ft[lf] + p;
+    double* out = dst + ft_mult * ft[lf] + ft_add + p;
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[v * n2] = scale * acc[v];
   }
@@ -565,6 +602,14 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
   const double* dp = c.dpool;
   modal_to_nodal(c, T, bufG, bufA, bufG, lane);
   write_traces(c, T, s, bufA, c.T, 1.0, lane);
+  if (c.ns) {
+    // Navier-Stokes: the volume residual needs the lifted gradient, which
+    // needs the neighbours' traces; keep the nodal state for that phase.
+    double* Un = c.Unod + c.slot_hoff[s];
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) Un[w] = bufA[w];
+    __syncthreads();
+    return;
+  }
   // contravariant fluxes G_l at the volume points (bufG, [3][5][nQ])
   const ElemGeo& g = c.geo[s];
   double Jg[9];
@@ -648,6 +693,149 @@ __device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_
   __syncthreads();
 }
 
+// BR1 lifting face term: bufA += sum_f coef_f E_f^T L_f with coef_f =
+// sign n_d(f), n(f) the element's outward unit normal of local face f and
+// L_f the face values at its own points (staged through bufS).
+__device__ __noinline__ void lift_scaled(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufS,
+                                         int lane, const double* faces, int d, double sign) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
+  const double* dp = c.dpool;
+  const int64_t* ft = c.slot_ftoff + s * 6;
+  {
+    const int per = 5 * n2;
+    for (int w = lane; w < nf * per; w += blockDim.x) {
+      int lf = w / per, r = w - lf * per;
+      bufS[w] = faces[ft[lf] + r];
+    }
+  }
+  __syncthreads();
+  double coef[6];
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) coef[lf] = lf < nf ? sign * c.fnrm[(s * 6 + lf) * 3 + d] : 0.0;
+  for (int o = lane; o < nQ; o += blockDim.x) {
+    int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+    double h[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) h[v] = bufA[v * nQ + o];
+    for (int lf = 0; lf < nf; ++lf) {
+      const FaceDesc fd = T.faces[lf];
+      int m = sel3(i, j, k, fd.fixed);
+      int p = sel3(i, j, k, fd.alpha) + n * sel3(i, j, k, fd.beta);
+      DG_FMA5(coef[lf] * dp[T.ext + fd.end * n + m], bufS + lf * 5 * n2 + p, n2, h);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = h[v];
+  }
+  __syncthreads();
+}
+
+// Navier-Stokes volume phase of the element at slot s (after the lifting face
+// phase).  Per direction d the BR1 lifted gradient of W = (rho, u, v, w, p):
+//   nodal  Hd = sum_l D_l^T (w J da_l/dx_d W)          (volume term, as H)
+//   modal  G_d = -(1/J) M_ref^{-1} V^T (Hd - sum_f n_d(f) E_f^T L_f)
+//   nodal  grad_d W = V G_d, and its traces on the own face points (Vt);
+// then the total flux F_e(U) - F_v(U, grad W) at the volume points and
+// H = sum_l D_l^T G_l(F) as in the Euler forward phase.
+// smem: bufU [5 nQ] | bufDW [3][5][nQ] | bufG [15 nQ] | bufA [5 nQ].
+__device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, int64_t s, double* smem, int lane) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n;
+  const int nQm = c.nQmax;
+  double* bufU = smem;
+  double* bufDW = smem + 5 * nQm;
+  double* bufG = smem + 20 * nQm;
+  double* bufA = smem + 35 * nQm;
+  const double* dp = c.dpool;
+  const double* Dt = dp + T.Dt;
+  const double gm1 = c.gamma - 1.0;
+  const ElemGeo& g = c.geo[s];
+  double Jg[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+  {
+    const double* Un = c.Unod + c.slot_hoff[s];
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufU[w] = Un[w];
+  }
+  __syncthreads();
+  for (int d = 0; d < 3; ++d) {
+    // G_l = (w da_l/dxi J dxi/dx_d) W at the volume points
+    for (int q = lane; q < nQ; q += blockDim.x) {
+      double U[5], W[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = bufU[v * nQ + q];
+      primitive(U, gm1, W);
+      double M[3][3];
+      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) bufG[(l * 5 + v) * nQ + q] = M[l][d] * W[v];
+    }
+    __syncthreads();
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      const double* G0 = bufG + jk;
+      const double* G1 = bufG + 5 * nQ + i * n2 + k;
+      const double* G2 = bufG + 10 * nQ + i * n2 + j * n;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[i * n + m], G0 + m * n2, nQ, acc);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[j * n + m], G1 + m * n, nQ, acc);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[k * n + m], G2 + m, nQ, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = acc[v];
+    }
+    __syncthreads();
+    lift_scaled(c, T, s, bufA, bufG, lane, c.L, d, -1.0);
+    double* sG = bufG + 5 * nQ;
+    Epilogue ep{Epilogue::kStore, true, -g.invJ, sG, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    nodal_to_modal(c, T, bufA, bufG, lane, ep);
+    double* dW = bufDW + d * 5 * nQ;
+    modal_to_nodal(c, T, sG, dW, bufG, lane);
+    write_traces(c, T, s, dW, c.Vt, 1.0, lane, 3, (int64_t)d * 5 * n2);
+    __syncthreads();
+  }
+  // total contravariant flux G_l = sum_d M[l][d] (F_e - F_v)_d
+  for (int q = lane; q < nQ; q += blockDim.x) {
+    double U[5], W[5], gr[15];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = bufU[v * nQ + q];
+#pragma unroll
+    for (int t = 0; t < 15; ++t) gr[t] = bufDW[t * nQ + q];
+    primitive(U, gm1, W);
+    double Fv[3][5];
+    viscous_flux(W, gr, c.mu, c.kappa, Fv);
+    double M[3][3];
+    point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+    const double u = W[1], v = W[2], w = W[3], p = W[4], Ep = U[4] + p;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double Vl = M[l][0] * u + M[l][1] * v + M[l][2] * w;
+      double* G = bufG + l * 5 * nQ + q;
+      G[0] = Vl * U[0];
+      G[nQ] = Vl * U[1] + p * M[l][0] - (M[l][0] * Fv[0][1] + M[l][1] * Fv[1][1] + M[l][2] * Fv[2][1]);
+      G[2 * nQ] = Vl * U[2] + p * M[l][1] - (M[l][0] * Fv[0][2] + M[l][1] * Fv[1][2] + M[l][2] * Fv[2][2]);
+      G[3 * nQ] = Vl * U[3] + p * M[l][2] - (M[l][0] * Fv[0][3] + M[l][1] * Fv[1][3] + M[l][2] * Fv[2][3]);
+      G[4 * nQ] = Vl * Ep - (M[l][0] * Fv[0][4] + M[l][1] * Fv[1][4] + M[l][2] * Fv[2][4]);
+    }
+  }
+  __syncthreads();
+  {
+    double* H = c.H + c.slot_hoff[s];
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      const double* G0 = bufG + jk;
+      const double* G1 = bufG + 5 * nQ + i * n2 + k;
+      const double* G2 = bufG + 10 * nQ + i * n2 + j * n;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[i * n + m], G0 + m * n2, nQ, acc);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[j * n + m], G1 + m * n, nQ, acc);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[k * n + m], G2 + m, nQ, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) H[v * nQ + o] = acc[v];
+    }
+  }
+  __syncthreads();
+}
+
 // One element at slot s.  smem per warp: bufA [5 nQmax], bufG [15 nQmax].
 template <int MODE>
 __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& io, int64_t s, double* bufA,
@@ -655,6 +843,10 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
   const TypeTab& T = c.tabs[c.slot_tab[s]];
   const int nM = T.nM, nQ = T.nQ;
   const int64_t qoff = c.slot_qoff[s];
+  if (MODE == kNsVolume) {
+    element_ns_volume(c, T, s, bufA, lane);
+    return;
+  }
   if (MODE == kFwd) {
     const double* Q = io.Qin + qoff;
     for (int w = lane; w < 5 * nM; w += blockDim.x) bufG[w] = Q[w];
@@ -906,6 +1098,113 @@ __global__ void face_kernel(Ctx c) {
   }
 }
 
+// Navier-Stokes face phases.  KIND 0 (BR1 lifting): per owner point p,
+// W* = (W(U-) + W(U+))/2 with U+ the neighbour trace mapped to the owner's
+// points, and L = w S W* (owner side) / Map^T (w S W*) (neighbour side); the
+// element multiplies by its own outward normal.  KIND 1 (flux): the inviscid
+// Riemann flux minus the central viscous flux (F_v(U-, g-) + F_v(U+, g+)).n/2,
+// g the lifted gradient traces, times w S, written over the traces as in the
+// Euler face kernel.
+template <int KIND>
+__global__ void face_ns_kernel(Ctx c) {
+  extern __shared__ double sF[];
+  const FaceBlock fb = c.fblocks[blockIdx.x];
+  const int n = fb.n, n2 = n * n, items = fb.count * n2;
+  const double gamma = c.gamma, gm1 = gamma - 1.0;
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, p = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    const double* T0 = c.T + R.toff;
+    const double* T1 = T0 + 5 * n2;
+    double UL[5], UR[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) UL[v] = T0[v * n2 + p];
+    if (R.map >= 0) {
+      int j = c.perms[(size_t)R.map + p];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) UR[v] = T1[v * n2 + j];
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int j = 0; j < n2; ++j) acc = fma(D[j], T1[v * n2 + j], acc);
+        UR[v] = acc;
+      }
+    }
+    const TypeTab& T = c.tabs[R.owner_tab];
+    const double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    double Fs[5];
+    if (KIND == 0) {
+      double WL[5], WR[5];
+      primitive(UL, gm1, WL);
+      primitive(UR, gm1, WR);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (WL[v] + WR[v]);
+    } else {
+      const double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+      if (c.flux == 0) flux_lf(UL, UR, nrm, gamma, Fs);
+      else flux_roe(UL, UR, nrm, gamma, Fs);
+      const double* V0 = c.Vt + 3 * R.toff;
+      const double* V1 = V0 + 15 * n2;
+      double g[15], W[5], Fv[3][5];
+#pragma unroll
+      for (int t = 0; t < 15; ++t) g[t] = V0[t * n2 + p];
+      primitive(UL, gm1, W);
+      viscous_flux(W, g, c.mu, c.kappa, Fv);
+      double Fvn[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fvn[v] = nrm[0] * Fv[0][v] + nrm[1] * Fv[1][v] + nrm[2] * Fv[2][v];
+      if (R.map >= 0) {
+        int j = c.perms[(size_t)R.map + p];
+#pragma unroll
+        for (int t = 0; t < 15; ++t) g[t] = V1[t * n2 + j];
+      } else {
+        const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
+        for (int t = 0; t < 15; ++t) {
+          double acc = 0.0;
+          for (int j = 0; j < n2; ++j) acc = fma(D[j], V1[t * n2 + j], acc);
+          g[t] = acc;
+        }
+      }
+      primitive(UR, gm1, W);
+      viscous_flux(W, g, c.mu, c.kappa, Fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        Fvn[v] += nrm[0] * Fv[0][v] + nrm[1] * Fv[1][v] + nrm[2] * Fv[2][v];
+        Fs[v] -= 0.5 * Fvn[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+  }
+  __syncthreads();
+  double* out = KIND == 0 ? c.L : c.T;
+  const double nb_sign = KIND == 0 ? 1.0 : -1.0;
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, q = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    double* O0 = out + R.toff;
+    double* O1 = O0 + 5 * n2;
+    const double* F = sF + fl * 5 * n2;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) O0[v * n2 + q] = F[v * n2 + q];
+    if (R.map >= 0) {
+      int p = c.perms[(size_t)R.map + n2 + q];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) O1[v * n2 + q] = nb_sign * F[v * n2 + p];
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) + q;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int p = 0; p < n2; ++p) acc = fma(D[(size_t)p * n2], F[v * n2 + p], acc);
+        O1[v * n2 + q] = nb_sign * acc;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ adjoint kernels
 
 __global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va, int phase) {
@@ -1073,6 +1372,19 @@ void launch_mode(const Ctx& c, const StageArgs& a, const Sched& s, bool balanced
 }
 }  // namespace
 
+int element_smem_bytes_ns(int nQmax) { return 40 * nQmax * (int)sizeof(double); }
+
+cudaError_t element_kernel_attributes_ns(int nQmax, int wpb, int* blocks_per_sm) {
+  const int bytes = element_smem_bytes_ns(nQmax);
+  cudaError_t e;
+  if ((e = set_mode<kNsVolume>(bytes)) != cudaSuccess) return e;
+  const int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
+  if ((e = set_smem(face_ns_kernel<0>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_kernel<1>, fbytes)) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kNsVolume>, 32 * wpb,
+                                                       bytes);
+}
+
 cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   int bytes = element_smem_bytes(nQmax, wpb);
   cudaError_t e;
@@ -1090,8 +1402,9 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
 
 void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb,
                     cudaStream_t st) {
-  int bytes = element_smem_bytes(c.nQmax, wpb);
+  int bytes = mode == kNsVolume ? element_smem_bytes_ns(c.nQmax) : element_smem_bytes(c.nQmax, wpb);
   switch (mode) {
+    case kNsVolume: launch_mode<kNsVolume>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kFwd: launch_mode<kFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kBwdRhs: launch_mode<kBwdRhs>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kBwdRk: launch_mode<kBwdRk>(c, a, s, balanced, grid, wpb, bytes, st); break;
@@ -1110,6 +1423,13 @@ void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
   if (nblocks <= 0) return;
   int bytes = 2 * 32 * 5 * n * n * (int)sizeof(double);
   face_vjp_kernel<<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+}
+
+void launch_faces_ns(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  int bytes = 32 * 5 * n * n * (int)sizeof(double);
+  if (kind == 0) face_ns_kernel<0><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  else face_ns_kernel<1><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
 }
 
 void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {

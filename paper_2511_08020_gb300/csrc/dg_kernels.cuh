@@ -30,7 +30,8 @@ enum ElemMode : int {
   kBwdRkFwd = 3,   // backward + LSERK update + forward of the new state
   kProject = 4,    // Algorithm 1 projection of point values
   kGather = 5,     // copy caller layout -> storage layout
-  kScatter = 6     // copy storage layout -> caller layout
+  kScatter = 6,    // copy storage layout -> caller layout
+  kNsVolume = 7    // Navier-Stokes: BR1 lifting, gradient traces, volume residual H
 };
 
 struct Ctx {
@@ -59,6 +60,13 @@ struct Ctx {
   double gamma;
   int flux;                    // 0 LF, 1 Roe
   int nQmax;
+  // Navier-Stokes (BR1) state; ns == 0 for the Euler equations
+  int ns;
+  double mu, kappa;            // viscosity, heat conductivity mu gamma / ((gamma - 1) Pr)
+  const double* fnrm;          // [slot][6][3] outward unit normal per local face
+  double* Unod;                // [slot][5][nQ] nodal state (slot_hoff offsets)
+  double* L;                   // lifting face values, layout of T
+  double* Vt;                  // gradient traces [face][2][3][5][n^2] (3x the offsets of T)
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
@@ -91,12 +99,17 @@ struct Sched {
 void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid,
                     int warps_per_block, cudaStream_t st);
 void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
+// Navier-Stokes face phases: kind 0 = BR1 lifting values (T -> L), kind 1 =
+// inviscid + central viscous flux (T, Vt -> T).
+void launch_faces_ns(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st);
+int element_smem_bytes_ns(int nQmax);
 void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int warps_per_block, cudaStream_t st);
 void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st);
 int element_smem_bytes(int nQmax, int warps_per_block);
 int face_block_threads(int n);
 cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm);
+cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm);
 cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops);
 
 }  // namespace dgk
