@@ -75,6 +75,33 @@ def element_flops(t, N):
 
 FACE_POINT_FLOPS = {"lf": 101, "roe": 214}
 
+
+def ns_element_flops(t, N):
+    """Algorithmic FP64 flops of one element for one Navier-Stokes stage:
+    the fused backward + forward launch (no volume term there) and the BR1
+    volume launch (per direction: lifting volume term, face lift, V^T, V and
+    gradient traces; then the total flux and the volume residual)."""
+    n = N + 1
+    nM = n_modes(t, N)
+    T = n * (n + 1) // 2
+    ncols = n * n if t in (0, 2) else T
+    bsum = n * n * (n * n if t in (0, 2) else T)
+    fwd = n * nM + bsum + n ** 4
+    bwd = n ** 4 + ncols * n * n + nM * n
+    nf = (6, 5, 5, 4)[t]
+    metric = (9, 15, 21, 27)[t]
+    nQ = n ** 3
+    fused = 2 * 5 * (fwd + bwd + 2 * nf * n ** 3) + 5 * nM * 7
+    per_dir = 2 * 5 * (3 * n ** 4 + 2 * nf * n ** 3 + bwd + fwd) + nQ * (15 + 13)
+    volume = 3 * per_dir + 2 * 5 * 3 * n ** 4 + nQ * (61 + metric + 13 + 66 + 72)
+    return fused + volume
+
+
+# per face point: lifting values (two primitive conversions and the mean) and
+# the Navier-Stokes flux (inviscid Riemann flux plus two viscous fluxes and
+# their normal components)
+FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 214 + 2 * (13 + 66 + 30) + 10}
+
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused element launch
 # (backward + LSERK + forward) of this workload, from the ncu capture
 # summarised in profiles/element_kernel_16cube_N4.md; set to None whenever
@@ -171,6 +198,34 @@ def tgv_dt(box, mesh_xyz, N, m=MESH_M):
     return CFL * h_min(m) / ((2 * N + 1) * tgv_smax(mesh_xyz))
 
 
+def dist_helpers(ws, dev):
+    """barrier() and max_over_ranks(x) of the replica run (torch.distributed
+    already initialised when ws > 1; CPU tensors on the gloo backend)."""
+    import torch
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def replica_value(ws, dof, steps, ms):
+    """Whole-job DOF-updates/s: every rank advanced its own copy of `dof`
+    modal coefficients per variable for `steps` LSERK steps (5 stages), and
+    `ms` is the slowest rank's time."""
+    return ws * dof * 5 * steps / (ms * 1e-3)
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -189,34 +244,33 @@ def run_reference(args):
     from oracle.dg import Oracle
     from oracle.mesh import from_box
     box = build_workload()
-    if True:
-        o = Oracle(from_box(box, N_DEG), flux=args.flux)
-        rng = np.random.default_rng(0)
-        sample = np.sort(rng.choice(box.n_elems, size=args.ref_sample, replace=False))
-        Q = np.zeros(o.mesh.n_dof())
-        # TGV projected on the sampled elements and their face neighbours
-        touched = set(sample.tolist())
-        for e in sample:
-            for f, _ in o.mesh.elem_faces[e]:
-                e0, _, e1, _ = o.mesh.faces[f]
-                touched.update((e0, e1))
-        for e in touched:
-            op = o.ops[o.mesh.etype[e]]
-            q = di.tgv_state(o.quad_points(e))
-            r = o.mesh.J[e] * (q * op.w) @ op.V
-            Q[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
-        dof = int(sum(o.mesh.nM[e] for e in sample))
+    o = Oracle(from_box(box, N_DEG), flux=args.flux)
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(box.n_elems, size=args.ref_sample, replace=False))
+    Q = np.zeros(o.mesh.n_dof())
+    # TGV projected on the sampled elements and their face neighbours
+    touched = set(sample.tolist())
+    for e in sample:
+        for f, _ in o.mesh.elem_faces[e]:
+            e0, _, e1, _ = o.mesh.faces[f]
+            touched.update((e0, e1))
+    for e in touched:
+        op = o.ops[o.mesh.etype[e]]
+        q = di.tgv_state(o.quad_points(e))
+        r = o.mesh.J[e] * (q * op.w) @ op.V
+        Q[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
+    dof = int(sum(o.mesh.nM[e] for e in sample))
 
-        def step():
-            for _ in range(5):
-                o.rhs(Q, elems=sample)
+    def step():
+        for _ in range(5):
+            o.rhs(Q, elems=sample)
 
-        for _ in range(args.warmup):
-            step()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step()
-        dt = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
     value = dof * 5 * args.steps / dt
     sample_txt = f"{args.ref_sample} of {box.n_elems} elements (seeded), 5 residual evaluations per step"
     line = {"metric": "FP64 RHS DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
@@ -282,18 +336,7 @@ def run_ours(args):
     dof = int(sum(n_modes(int(t), N_DEG) for t in box.etype))
     counts = mesh.type_counts
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = dist_helpers(ws, dev)
 
     def timed_steps(m, Q, K, steps, warmup, profile=False):
         m.set_profiling(profile)
@@ -326,7 +369,11 @@ def run_ours(args):
     tuned = {}
     for sched in ("naive", "static", "balanced"):
         mesh.set_scheduler(sched)
-        tuned[sched] = mesh.autotune(Q0, dt)
+        if args.warps:
+            mesh.set_element_warps(args.warps)
+            tuned[sched] = (args.warps, np.zeros(4))
+        else:
+            tuned[sched] = mesh.autotune(Q0, dt)
     tuned_ms = {k: [round(x, 3) for x in v[1].tolist()] for k, v in tuned.items()}
 
     # main measurement: balanced scheduler, LF
@@ -337,7 +384,7 @@ def run_ours(args):
     ms, _ = timed_steps(mesh, Q, K, args.steps, args.warmup)
     clk = clocks.stop()
     mesh.sync()
-    value = ws * dof * 5 * args.steps / (ms * 1e-3)
+    value = replica_value(ws, dof, args.steps, ms)
 
     # kernel split (events inside the replayed graph), same workload
     Qp = Q0.clone()
@@ -352,6 +399,17 @@ def run_ours(args):
     elem_tflops = el_flops_stage * 5 * steps_p / (elem_ms * 1e-3) / 1e12
     face_tflops = face_flops_stage * 5 * steps_p / (face_ms * 1e-3) / 1e12
     total_tflops = (el_flops_stage + face_flops_stage) * 5 * args.steps / (ms * 1e-3) / 1e12 / ws
+
+    if args.only_main:
+        # profiling aid: the main measurement (and the Navier-Stokes leg) only
+        line = {"metric": "FP64 RHS DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
+                "ms_per_step": ms / args.steps, "element_ms_per_step": elem_ms / steps_p,
+                "face_ms_per_step": face_ms / steps_p, "element_tflops": elem_tflops, "only_main": True}
+        if args.ns_steps > 0:
+            line["navier_stokes"] = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     dfma, dmma = dg.probe_fp64_peak()
     nominal = 1.25
@@ -483,6 +541,8 @@ def run_ours(args):
     }
     if args.batch_steps > 0:
         line["batch"] = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
+    if args.ns_steps > 0:
+        line["navier_stokes"] = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -491,6 +551,79 @@ def run_ours(args):
 BATCH_WORKLOAD = ("64 independent periodic mixed hex/prism/pyramid boxes, m uniform on 4..20 cubes per "
                   "direction, N uniform on {2,3,4,5} (dg_inputs.batch_workload seed 5), Euler TGV, LF, one "
                   "dt (CFL 0.5 of the finest instance), FP64")
+
+
+NS_WORKLOAD = ("24^3-cube periodic box, mixed hex/prism/pyramid (prism columns 1/4, pyramid cubes 1/9 of hex "
+               "columns, seed 4), N=4, Navier-Stokes TGV Re=1600 (mu=1/1600, Pr=0.72, BR1), LF, CFL 0.5, FP64")
+
+
+def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
+    """Viscous TGV: one handle in Navier-Stokes mode, balanced and naive."""
+    import torch
+    m, N = 24, 4
+    box = di.box_mesh(m, "mixed", seed=4, p_prism=0.25, p_pyr=1.0 / 9.0)
+    mesh = dg.Mesh(box, N, flux=args.flux, scheduler="balanced")
+    mesh.set_physics("navier_stokes", 1.0 / 1600.0, 0.72)
+    n = N + 1
+    xyz = mesh.quad_points()
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Q0 = mesh.project(torch.from_numpy(vals).to(dev))
+    dt = tgv_dt(box, xyz, N, m)
+    del vals, xyz
+    dof = int(sum(n_modes(int(t), N) for t in box.etype))
+    steps = args.ns_steps
+
+    def timed(Q, K, profile=False):
+        mesh.set_profiling(profile)
+        for _ in range(args.warmup):
+            mesh.rk_step(Q, K, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el = fa = 0.0
+        e0.record(stream)
+        for _ in range(steps):
+            mesh.rk_step(Q, K, dt, 1)
+            if profile:
+                a, b, _, _ = mesh.phase_times()
+                el += a
+                fa += b
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        mesh.set_profiling(False)
+        return max_over_ranks(e0.elapsed_time(e1)), el, fa
+
+    out = {"workload": NS_WORKLOAD, "elements": box.n_elems, "faces": mesh.n_faces, "dof_per_var": dof,
+           "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), mesh.type_counts)), "steps": steps, "dt": dt,
+           "unit": "DOF-updates/s"}
+    res = {}
+    for sched in (("balanced",) if args.only_main else ("naive", "balanced")):
+        mesh.set_scheduler(sched)
+        if args.warps:
+            mesh.set_element_warps(args.warps)
+            warps = args.warps
+        else:
+            warps, _ = mesh.autotune(Q0, dt)
+        Q = Q0.clone()
+        ms, _, _ = timed(Q, torch.empty_like(Q))
+        res[sched] = Q
+        out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps}
+    Qp = Q0.clone()
+    _, el_ms, fa_ms = timed(Qp, torch.empty_like(Qp), profile=True)
+    el_flops = sum(ns_element_flops(int(t), N) for t in box.etype) * 5 * steps
+    fa_flops = mesh.n_faces * n * n * (FACE_POINT_FLOPS_NS["lift"] + FACE_POINT_FLOPS_NS[args.flux]) * 5 * steps
+    out["element_kernels_tflops"] = el_flops / (el_ms * 1e-3) / 1e12
+    out["face_kernels_tflops"] = fa_flops / (fa_ms * 1e-3) / 1e12
+    out["element_ms_per_step"] = el_ms / steps
+    out["face_ms_per_step"] = fa_ms / steps
+    if "naive" in out:
+        out["balanced_over_naive"] = out["balanced"]["value"] / out["naive"]["value"]
+        out["schedulers_bitwise_equal"] = bool(torch.equal(res["naive"], res["balanced"]))
+    mesh.sync()
+    mesh.close()
+    return out
 
 
 def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
@@ -574,6 +707,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10,
                     help="steps of the 64-instance batch leg (0 skips it)")
+    ap.add_argument("--warps", type=int, default=0,
+                    help="warps per element for every scheduler instead of the autotuner (0: autotune)")
+    ap.add_argument("--only-main", action="store_true",
+                    help="profiling aid: run the main measurement and the Navier-Stokes leg only")
+    ap.add_argument("--ns-steps", type=int, default=200,
+                    help="steps of the 24^3 Navier-Stokes TGV leg (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
