@@ -94,7 +94,8 @@ def rk_vjp(o, Q0, dt, nsteps, QKbar):
         Kbar = np.zeros_like(Qbar)
         for s in reversed(range(5)):
             Kbar = Kbar + LSERK_B[s] * Qbar
-            Qbar = Qbar + dt * rhs_vjp(o, stages[5 * step + s], Kbar)
+            Qs = stages[5 * step + s]
+            Qbar = Qbar + dt * (o.rhs_vjp(Qs, Kbar) if hasattr(o, "rhs_vjp") else rhs_vjp(o, Qs, Kbar))
             Kbar = LSERK_A[s] * Kbar
     return Qbar
 

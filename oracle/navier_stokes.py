@@ -28,9 +28,18 @@ discretisation; the reading taken here is the first Bassi-Rebay scheme
 Works on real or complex arrays (complex-step differentiation).  With mu = 0
 the residual is the Euler residual.
 
+Adjoint (rhs_vjp): the plain transpose of every step above, in reverse
+order -- projection, volume flux (inviscid and viscous, with the viscous
+flux's dependence on both U and the lifted gradient), face flux (Riemann and
+central viscous parts), then the lifting (mass solve, volume and face terms)
+and the face values W*; the pointwise Jacobians come from complex steps
+through the functions of this module and oracle.euler.
+
 Parity: pinned by exact lifting of linear W, exact residuals of polynomial
 states against a symbolic strong-form residual, reduction to Euler at mu = 0,
-free-stream preservation and conservation (tests/test_oracle_ns.py).
+free-stream preservation and conservation; the adjoint by the dense Jacobian
+from complex steps through rhs (brute force) and the dot-product test
+(tests/test_oracle_ns.py).
 """
 from __future__ import annotations
 
@@ -38,6 +47,20 @@ import numpy as np
 
 from .dg import Oracle
 from .euler import physical_flux, riemann
+
+H_CS = 1e-30
+
+
+def _cs(fun, X):
+    """Jacobian of fun at X by complex steps: X [*shape_in, P] -> [*shape_out, *shape_in, P]."""
+    shape_in = X.shape[:-1]
+    cols = []
+    for idx in np.ndindex(*shape_in):
+        dX = np.zeros(X.shape, dtype=complex)
+        dX[idx] = 1.0
+        cols.append(fun(X + 1j * H_CS * dX).imag / H_CS)
+    out = np.stack(cols, axis=-2)                                 # [*out, prod(in), P]
+    return out.reshape(out.shape[:-2] + shape_in + out.shape[-1:])
 
 
 def primitive(U, gamma):
@@ -135,6 +158,76 @@ class NSOracle(Oracle):
             r = self.ns_volume_term(Q, e, G) - self.surface_term(Q, e, fluxes)
             R[m.dof_off[e]:m.dof_off[e + 1]] = self.apply_minv(e, r).ravel()
         return R
+
+    def rhs_vjp(self, Q, Rbar):
+        """Qbar = (dR/dQ)^T Rbar (caller layout), every step transposed."""
+        m = self.mesh
+        gam, mu, Pr = self.gamma, self.mu, self.Pr
+        Q = np.asarray(Q, dtype=float)
+        Qbar = np.zeros_like(Q)
+        E, F = m.n_elems, len(m.faces)
+        wstar = {f: self.face_wstar(Q, f) for f in range(F)}
+        G = {e: self.lifting(Q, e, wstar) for e in range(E)}
+        rbar = {e: self.apply_minv(e, m.block(Rbar, e)) for e in range(E)}
+        Gbar = {e: np.zeros((3, 5, m.nM[e])) for e in range(E)}
+        Wsbar = {f: np.zeros_like(wstar[f]) for f in range(F)}
+
+        def add(e, vals):
+            Qbar[m.dof_off[e]:m.dof_off[e + 1]] += vals.ravel()
+
+        def vf_u(g):
+            return lambda X: viscous_flux(X, g, gam, mu, Pr)
+
+        def vf_g(U):
+            return lambda Y: viscous_flux(U, Y, gam, mu, Pr)
+
+        # volume: total flux F_e(U) - F_v(U, grad W)
+        for e in range(E):
+            op = self.ops[m.etype[e]]
+            U = m.block(Q, e) @ op.V.T
+            gW = G[e] @ op.V.T
+            Fbar = m.J[e] * op.w * np.einsum("kd,kqi,vi->dvq", m.dxi_dx[e], op.G, rbar[e])
+            JU = _cs(lambda X: physical_flux(X, gam), U) - _cs(vf_u(gW), U)     # [3, 5, 5, nQ]
+            JG = _cs(vf_g(U), gW)                                               # [3, 5, 3, 5, nQ]
+            add(e, np.einsum("dvuq,dvq->uq", JU, Fbar) @ op.V)
+            Gbar[e] += -np.einsum("dvxyq,dvq->xyq", JG, Fbar) @ op.V
+        # faces: Riemann flux minus the central viscous flux
+        for f, (e0, _, e1, _) in enumerate(m.faces):
+            phi0, phi1, wS, nrm = self.face_data(f)
+            UL, UR = m.block(Q, e0) @ phi0.T, m.block(Q, e1) @ phi1.T
+            gL, gR = G[e0] @ phi0.T, G[e1] @ phi1.T
+            Fsbar = wS * (-(rbar[e0] @ phi0.T) + rbar[e1] @ phi1.T)
+            JL = _cs(lambda X: riemann(self.flux, X, UR, nrm, gam), UL)
+            JR = _cs(lambda X: riemann(self.flux, UL, X, nrm, gam), UR)
+            Fvbar = -0.5 * nrm[:, None, None] * Fsbar[None]                    # [3, 5, P]
+            ULbar = np.einsum("vup,vp->up", JL, Fsbar) + np.einsum("dvup,dvp->up", _cs(vf_u(gL), UL), Fvbar)
+            URbar = np.einsum("vup,vp->up", JR, Fsbar) + np.einsum("dvup,dvp->up", _cs(vf_u(gR), UR), Fvbar)
+            add(e0, ULbar @ phi0)
+            add(e1, URbar @ phi1)
+            Gbar[e0] += np.einsum("dvxyp,dvp->xyp", _cs(vf_g(UL), gL), Fvbar) @ phi0
+            Gbar[e1] += np.einsum("dvxyp,dvp->xyp", _cs(vf_g(UR), gR), Fvbar) @ phi1
+        # lifting: G_d = M^{-1}(surf_d - vol_d)
+        for e in range(E):
+            op = self.ops[m.etype[e]]
+            U = m.block(Q, e) @ op.V.T
+            sbar = np.stack([self.apply_minv(e, Gbar[e][d]) for d in range(3)])
+            gx = np.einsum("kd,kqi->dqi", m.dxi_dx[e], op.G)
+            Wbar = -m.J[e] * op.w * np.einsum("dqi,dvi->vq", gx, sbar)
+            JW = _cs(lambda X: primitive(X, gam), U)                            # [5, 5, nQ]
+            add(e, np.einsum("wuq,wq->uq", JW, Wbar) @ op.V)
+            for f, side in m.elem_faces[e]:
+                phi0, phi1, _, nrm = self.face_data(f)
+                phi, sgn = (phi0, 1.0) if side == 0 else (phi1, -1.0)
+                for d in range(3):
+                    Wsbar[f] += sgn * nrm[d] * (sbar[d] @ phi.T)
+        # face values W* = w S (W(U-) + W(U+)) / 2
+        for f, (e0, _, e1, _) in enumerate(m.faces):
+            phi0, phi1, wS, _ = self.face_data(f)
+            UL, UR = m.block(Q, e0) @ phi0.T, m.block(Q, e1) @ phi1.T
+            a = 0.5 * wS * Wsbar[f]
+            add(e0, np.einsum("wup,wp->up", _cs(lambda X: primitive(X, gam), UL), a) @ phi0)
+            add(e1, np.einsum("wup,wp->up", _cs(lambda X: primitive(X, gam), UR), a) @ phi1)
+        return Qbar
 
     def lifted_gradient(self, Q, elems=None):
         """{e: G_e [3, 5, nM]} for the given elements (all by default)."""

@@ -245,3 +245,48 @@ def test_ns_conservation(kind, m, N, flux):
     total = sum(o.integrate(R, e) for e in range(o.mesh.n_elems))
     scale = sum(np.abs(o.integrate(R, e)) for e in range(o.mesh.n_elems))
     assert np.all(np.abs(total) < 1e-12 * scale), (total, scale)
+
+
+# ---------------------------------------------------------------- adjoint
+def ns_jvp(o, Q, V):
+    """J(Q) V by one complex step through the NS residual (brute force route)."""
+    h = 1e-30
+    return o.rhs(np.asarray(Q, dtype=float) + 1j * h * np.asarray(V)).imag / h
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder", [("hex", 2, 1, "lf", None), ("prism", 2, 1, "roe", 3)])
+def test_ns_vjp_dense_jacobian(kind, m, N, flux, reorder):
+    """Transpose of the Jacobian assembled column by column with complex steps."""
+    o = make(kind, m, N, flux=flux, reorder=reorder)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=5, amp=0.05))
+    n = len(Q)
+    J = np.stack([ns_jvp(o, Q, np.eye(n)[j]) for j in range(n)], axis=1)
+    w = di.random_vector(n, seed=9)
+    ref = J.T @ w
+    got = o.rhs_vjp(Q, w)
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder", [("mixed", 2, 3, "lf", None), ("kuhn", 2, 2, "roe", 7),
+                                                    ("mixed", 2, 2, "lf", 5)])
+def test_ns_vjp_dot(kind, m, N, flux, reorder):
+    o = make(kind, m, N, flux=flux, reorder=reorder)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=6, amp=0.05))
+    w = di.random_vector(len(Q), seed=10)
+    vjp = o.rhs_vjp(Q, w)
+    for s in range(3):
+        v = di.random_vector(len(Q), seed=20 + s)
+        a, b = np.dot(w, ns_jvp(o, Q, v)), np.dot(vjp, v)
+        assert abs(a - b) < 1e-11 * (np.abs(w).sum() * np.abs(ns_jvp(o, Q, v)).max()), (a, b)
+
+
+def test_ns_rk_vjp_dot():
+    from oracle.adjoint import rk_jvp, rk_vjp
+    o = make("mixed", 2, 2)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=7, amp=0.05))
+    w = di.random_vector(len(Q), seed=11)
+    v = di.random_vector(len(Q), seed=12)
+    dt, K = 2e-3, 2
+    a = np.dot(w, rk_jvp(o, Q, dt, K, v))
+    b = np.dot(rk_vjp(o, Q, dt, K, w), v)
+    assert abs(a - b) < 1e-11 * abs(a), (a, b)
