@@ -221,8 +221,10 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
  * (lifting values) and one element phase (gradient, traces, volume term).
  * Allocates the workspace (nodal state, lifting values, gradient traces: 5
  * times the face buffer plus the nodal residual) on first use; DG_ERR_OOM if
- * that fails.  mu and Pr are ignored for DG_EULER.  The adjoint entry points
- * return DG_ERR_UNSUPPORTED while Navier-Stokes is selected. */
+ * that fails.  mu and Pr are ignored for DG_EULER.  dg_rhs_vjp and dg_rk_vjp
+ * differentiate whichever equations are selected (the viscous adjoint
+ * allocates the nodal gradient and gradient-trace cotangents on first use);
+ * dg_rhs_vjp_noalloc returns DG_ERR_UNSUPPORTED under Navier-Stokes. */
 dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr);
 
 /* Scheduler of the element kernels: DG_SCHED_BALANCED (one persistent launch

@@ -65,6 +65,8 @@ struct dg_mesh {
   int ns = 0, blocks_per_sm_ns = 1;
   double mu = 0.0, Pr = 0.72;
   double *d_Unod = nullptr, *d_L = nullptr, *d_Vt = nullptr, *d_fnrm = nullptr;
+  double *d_DW = nullptr, *d_Vtb = nullptr;   // Navier-Stokes adjoint workspace
+  bool store_dw = false;                      // the volume phase keeps the nodal gradient (adjoint)
   // device data
   double* d_dpool = nullptr;
   int* d_ipool = nullptr;
@@ -169,6 +171,8 @@ struct dg_mesh {
     c.Unod = d_Unod;
     c.L = d_L;
     c.Vt = d_Vt;
+    c.DW = store_dw ? d_DW : nullptr;
+    c.Vtb = d_Vtb;
     c.H = d_H;
     c.T = d_T;
     c.Tv = d_Tv;
@@ -283,6 +287,12 @@ struct dg_mesh {
   // Adjoint workspace (allocated on first use).
   cudaError_t ensure_adjoint(size_t ckpt_needed) {
     cudaError_t e = cudaSuccess;
+    if (ns) {
+      const size_t hb = sizeof(double) * (size_t)std::max<int64_t>(1, h.h_total);
+      const size_t tb = sizeof(double) * (size_t)std::max<int64_t>(1, h.t_total);
+      if (!d_DW && (e = cudaMalloc(&d_DW, 3 * hb)) != cudaSuccess) return e;
+      if (!d_Vtb && (e = cudaMalloc(&d_Vtb, 3 * tb)) != cudaSuccess) return e;
+    }
     if (!d_Tv && (e = cudaMalloc(&d_Tv, sizeof(double) * std::max<int64_t>(1, h.t_total))) != cudaSuccess) return e;
     if (!d_Kbar && (e = cudaMalloc(&d_Kbar, sizeof(double) * std::max<int64_t>(1, h.n_dof))) != cudaSuccess) return e;
     if (ckpt_needed > ckpt_doubles) {
@@ -297,6 +307,24 @@ struct dg_mesh {
 
   // One RHS VJP (rk == 0) or one reverse LSERK stage (rk == 1) at state Q.
   void enqueue_vjp(const dgk::VjpArgs& va, cudaStream_t st) {
+    if (ns) {
+      // forward state at Q (traces, nodal state, lifting values, gradient
+      // traces and the nodal gradient), then the transposed phases
+      const int64_t nb = (int64_t)h.face_blocks.size();
+      dgk::StageArgs fa{va.Q, nullptr, nullptr, 0.0, 0.0, 0.0};
+      store_dw = true;
+      element_phase(dgk::kFwd, fa, st);
+      dgk::launch_faces_ns(ctx(), nb, h.n, 0, st);
+      element_phase(dgk::kNsVolume, fa, st);
+      dgk::Ctx c = ctx();
+      store_dw = false;
+      dgk::launch_vjp(c, 10, va, h.n_elems, wpb, st);
+      dgk::launch_faces_ns_vjp(c, nb, h.n, 1, st);
+      dgk::launch_vjp(c, 11, va, h.n_elems, wpb, st);
+      dgk::launch_faces_ns_vjp(c, nb, h.n, 0, st);
+      dgk::launch_vjp(c, 2, va, h.n_elems, wpb, st);
+      return;
+    }
     dgk::Ctx c = ctx();
     dgk::launch_vjp(c, 0, va, h.n_elems, wpb, st);
     dgk::launch_faces_vjp(c, (int64_t)h.face_blocks.size(), h.n, st);
@@ -346,7 +374,7 @@ struct dg_mesh {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
-                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm};
+                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -628,7 +656,6 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the Euler equations only (dg_set_physics)");
   DG_CUDA(mesh->ensure_adjoint(0));
   dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
   mesh->enqueue_vjp(va, stream);
@@ -673,7 +700,9 @@ extern "C" {
 dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
                              cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the Euler equations only (dg_set_physics)");
+  if (mesh->ns)
+    return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp_noalloc covers the Euler equations (the viscous adjoint needs "
+                                    "workspace that dg_rhs_vjp allocates); use dg_rhs_vjp");
   const size_t need = (size_t)std::max<int64_t>(1, mesh->h.t_total);
   if (need > kNoAllocScratchDoubles)
     return fail(DG_ERR_ARG, "dg_rhs_vjp_noalloc: the mesh needs " + std::to_string(need) +
@@ -704,7 +733,6 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream) {
   if (!mesh || !Q0_store || !QKbar || !Q0bar) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the Euler equations only (dg_set_physics)");
   if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;

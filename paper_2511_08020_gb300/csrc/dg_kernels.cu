@@ -136,6 +136,57 @@ __device__ __forceinline__ void viscous_flux(const double* W, const double* g, d
   }
 }
 
+// Reverse mode of viscous_flux: Fb[d][v] cotangent of F_v[d][v]; adds the
+// cotangents of W (5) to Wb and of the gradient (15) to gb.
+__device__ __forceinline__ void viscous_flux_vjp(const double* W, const double* g, double mu, double kappa,
+                                                 const double Fb[3][5], double* Wb, double* gb) {
+  const double div = g[1] + g[5 + 2] + g[10 + 3];
+  const double rinv = 1.0 / W[0], Tr = W[4] * rinv;
+  const double lam = (2.0 / 3.0) * mu * div;
+  double lamb = 0.0, rinvb = 0.0, Trb = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double e = Fb[d][4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double tau = mu * (g[d * 5 + 1 + i] + g[i * 5 + 1 + d]) - (i == d ? lam : 0.0);
+      const double taub = Fb[d][1 + i] + W[1 + i] * e;
+      Wb[1 + i] += tau * e;
+      gb[d * 5 + 1 + i] += mu * taub;
+      gb[i * 5 + 1 + d] += mu * taub;
+      if (i == d) lamb -= taub;
+    }
+    const double dTb = kappa * e;
+    gb[d * 5 + 4] += dTb * rinv;
+    gb[d * 5] -= Tr * rinv * dTb;
+    Trb -= g[d * 5] * rinv * dTb;
+    rinvb += (g[d * 5 + 4] - Tr * g[d * 5]) * dTb;
+  }
+  Wb[4] += rinv * Trb;
+  rinvb += W[4] * Trb;
+  Wb[0] -= rinv * rinv * rinvb;
+  const double divb = (2.0 / 3.0) * mu * lamb;
+  gb[1] += divb;
+  gb[5 + 2] += divb;
+  gb[10 + 3] += divb;
+}
+
+// Reverse mode of primitive: adds the cotangent of U to Ub.
+__device__ __forceinline__ void primitive_vjp(const double* U, double gm1, const double* Wb, double* Ub) {
+  const double r = 1.0 / U[0];
+  const double hp = 0.5 * gm1 * Wb[4];
+  double rb = 0.0;
+  Ub[4] += gm1 * Wb[4];
+#pragma unroll
+  for (int i = 1; i <= 3; ++i) {
+    const double Wi = U[i] * r;
+    const double Wib = Wb[i] - hp * U[i];
+    Ub[i] += r * Wib - hp * Wi;
+    rb += U[i] * Wib;
+  }
+  Ub[0] += Wb[0] - r * r * rb;
+}
+
 // ------------------------------------------------------------------ adjoint physics
 // Hand-written reverse mode of the functions above.  Readings at the kinks:
 // d|x|/dx = sign(x) with sign(0) = 0; max(aL, aR) passes its cotangent to the
@@ -791,6 +842,10 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
     double* dW = bufDW + d * 5 * nQ;
     modal_to_nodal(c, T, sG, dW, bufG, lane);
     write_traces(c, T, s, dW, c.Vt, 1.0, lane, 3, (int64_t)d * 5 * n2);
+    if (c.DW) {
+      double* out = c.DW + 3 * c.slot_hoff[s] + d * 5 * nQ;
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) out[w] = dW[w];
+    }
     __syncthreads();
   }
   // total contravariant flux G_l = sum_d M[l][d] (F_e - F_v)_d
@@ -974,6 +1029,224 @@ __device__ __noinline__ void element_vjp_c(const Ctx& c, const VjpArgs& va, int6
   Epilogue ep{va.rk ? Epilogue::kAxpy : Epilogue::kStore, false, va.rk ? va.dt : 1.0, va.Qbar + c.slot_qoff[s],
               nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
   nodal_to_modal(c, T, bufA, bufG, lane, ep);
+}
+
+// ------------------------------------------------------------------ Navier-Stokes adjoint element phases
+//
+// The forward state at Q is recomputed first (traces T, nodal state Unod,
+// lifting values, gradient traces Vt and the nodal gradient DW).  Then:
+//   A: Ybar = V diag(M_ref^-1 / J) Rbar, seeds -E_f Ybar (Tv), Fbar_l = D_l Ybar;
+//      per point the transposed total flux F_e(U) - F_v(U, DW): Ubar -> H,
+//      gradient cotangent -> DW (in place);
+//   face flux adjoint: trace cotangents (Tv) and gradient-trace cotangents (Vtb);
+//   B: DWbar_d = DW + sum_f E_f^T Vtb_f,d; Bbar_d = V (-1/J) M_ref^-1 V^T DWbar_d;
+//      Lbar_f = -sum_d n_d(f) E_f Bbar_d (own side of L);
+//      Wbar = sum_d sum_l M[l][d] D_l Bbar_d, Ubar += (dW/dU)^T Wbar (H);
+//   lifting-value adjoint: trace cotangents += (dW/dU)^T of the face means (Tv);
+//   C (shared with Euler): Qbar = V^T (Ubar + sum_f E_f^T Tbar_f).
+
+// bufA += sum_f coef_f E_f^T faces_f, face values at (ft_mult ft[lf] + ft_add)
+// (staged through bufS).
+__device__ __noinline__ void lift_add(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufS, int lane,
+                                      const double* faces, int ft_mult, int64_t ft_add, const double* coef) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
+  const double* dp = c.dpool;
+  const int64_t* ft = c.slot_ftoff + s * 6;
+  {
+    const int per = 5 * n2;
+    for (int w = lane; w < nf * per; w += blockDim.x) {
+      int lf = w / per, r = w - lf * per;
+      bufS[w] = faces[ft_mult * ft[lf] + ft_add + r];
+    }
+  }
+  __syncthreads();
+  for (int o = lane; o < nQ; o += blockDim.x) {
+    int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+    double h[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) h[v] = bufA[v * nQ + o];
+    for (int lf = 0; lf < nf; ++lf) {
+      const FaceDesc fd = T.faces[lf];
+      int m = sel3(i, j, k, fd.fixed);
+      int p = sel3(i, j, k, fd.alpha) + n * sel3(i, j, k, fd.beta);
+      DG_FMA5(coef[lf] * dp[T.ext + fd.end * n + m], bufS + lf * 5 * n2 + p, n2, h);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = h[v];
+  }
+  __syncthreads();
+}
+
+// Phase A (Navier-Stokes).  smem: bufY [5 nQ] | bufG [15 nQ] | bufS [5 nQ].
+__device__ __noinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, int64_t s, double* smem, int lane) {
+  const TypeTab& T = c.tabs[c.slot_tab[s]];
+  const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
+  const int nQm = c.nQmax;
+  double* bufY = smem;
+  double* bufG = smem + 5 * nQm;
+  double* bufS = smem + 20 * nQm;
+  const double* dp = c.dpool;
+  const int64_t qoff = c.slot_qoff[s];
+  const double invJ = c.geo[s].invJ;
+  for (int w = lane; w < 5 * nM; w += blockDim.x) {
+    const int m = w % nM;
+    double rb;
+    if (va.rk) {
+      rb = va.Kbar[qoff + w] + va.b * va.Qbar[qoff + w];
+      va.Kbar[qoff + w] = va.a * rb;
+    } else {
+      rb = va.Rbar[qoff + w];
+    }
+    bufS[w] = rb * dp[T.minv + m] * invJ;
+  }
+  __syncthreads();
+  modal_to_nodal(c, T, bufS, bufY, bufG, lane);
+  write_traces(c, T, s, bufY, c.Tv, -1.0, lane);
+  {
+    const double* Dt = dp + T.Dt;
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + i], bufY + m * n2 + jk, nQ, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[v * nQ + o] = acc[v];
+      double acc1[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + j], bufY + i * n2 + m * n + k, nQ, acc1);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[(5 + v) * nQ + o] = acc1[v];
+      double acc2[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + k], bufY + i * n2 + j * n + m, nQ, acc2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[(10 + v) * nQ + o] = acc2[v];
+    }
+  }
+  __syncthreads();
+  {
+    const ElemGeo& g = c.geo[s];
+    double Jg[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+    const double gm1 = c.gamma - 1.0;
+    const double* Un = c.Unod + c.slot_hoff[s];
+    double* DWs = c.DW + 3 * c.slot_hoff[s];
+    double* Hb = c.H + c.slot_hoff[s];
+    for (int q = lane; q < nQ; q += blockDim.x) {
+      double U[5], W[5], gr[15], Gb[3][5], Ub[5], Wb[5] = {0, 0, 0, 0, 0}, gb[15];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = Un[v * nQ + q];
+#pragma unroll
+      for (int t = 0; t < 15; ++t) {
+        gr[t] = DWs[t * nQ + q];
+        gb[t] = 0.0;
+      }
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Gb[l][v] = bufG[(l * 5 + v) * nQ + q];
+      double M[3][3];
+      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      contravariant_vjp(U, M, c.gamma, Gb, Ub);
+      // G_l -= sum_d M[l][d] F_v[d]  =>  Fvbar[d] = -sum_l M[l][d] Gbar_l
+      double Fvb[3][5];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fvb[d][v] = -(M[0][d] * Gb[0][v] + M[1][d] * Gb[1][v] + M[2][d] * Gb[2][v]);
+      primitive(U, gm1, W);
+      viscous_flux_vjp(W, gr, c.mu, c.kappa, Fvb, Wb, gb);
+      primitive_vjp(U, gm1, Wb, Ub);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Hb[v * nQ + q] = Ub[v];
+#pragma unroll
+      for (int t = 0; t < 15; ++t) DWs[t * nQ + q] = gb[t];
+    }
+  }
+  __syncthreads();
+}
+
+// Phase B (Navier-Stokes lifting transpose).
+// smem: bufD [15 nQ] | bufB [5 nQ] | bufX [5 nQ] | bufW [5 nQ] | bufL [15 nQ].
+__device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* smem, int lane) {
+  const TypeTab& T = c.tabs[c.slot_tab[s]];
+  const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
+  const int nQm = c.nQmax;
+  double* bufD = smem;
+  double* bufB = smem + 15 * nQm;
+  double* bufX = smem + 20 * nQm;
+  double* bufW = smem + 25 * nQm;
+  double* bufL = smem + 30 * nQm;
+  const double* dp = c.dpool;
+  const double* Dt = dp + T.Dt;
+  const int64_t* ft = c.slot_ftoff + s * 6;
+  const ElemGeo& g = c.geo[s];
+  {
+    const double* DWs = c.DW + 3 * c.slot_hoff[s];
+    for (int w = lane; w < 15 * nQ; w += blockDim.x) bufD[w] = DWs[w];
+  }
+  __syncthreads();
+  const double ones[6] = {1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+  for (int d = 0; d < 3; ++d) lift_add(c, T, s, bufD + d * 5 * nQ, bufL, lane, c.Vtb, 3, (int64_t)d * 5 * n2, ones);
+  for (int w = lane; w < 5 * nQ; w += blockDim.x) bufW[w] = 0.0;
+  for (int w = lane; w < nf * 5 * n2; w += blockDim.x) bufL[w] = 0.0;
+  __syncthreads();
+  double Jg[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+  for (int d = 0; d < 3; ++d) {
+    Epilogue ep{Epilogue::kStore, true, -g.invJ, bufX, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    nodal_to_modal(c, T, bufD + d * 5 * nQ, bufX, lane, ep);
+    modal_to_nodal(c, T, bufX, bufB, bufX, lane);     // Bbar_d in bufB
+    // Lbar_f -= n_d(f) E_f Bbar_d on the own face points
+    for (int w = lane; w < nf * n2; w += blockDim.x) {
+      int lf = w / n2, p = w - lf * n2;
+      int ia = p % n, ib = p / n;
+      const FaceDesc fd = T.faces[lf];
+      int sa = fd.alpha == 0 ? n2 : (fd.alpha == 1 ? n : 1);
+      int sb = fd.beta == 0 ? n2 : (fd.beta == 1 ? n : 1);
+      int sf = fd.fixed == 0 ? n2 : (fd.fixed == 1 ? n : 1);
+      const double* e = dp + T.ext + fd.end * n;
+      const double* Bs = bufB + ia * sa + ib * sb;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(e[m], Bs + m * sf, nQ, acc);
+      const double nd = c.fnrm[(s * 6 + lf) * 3 + d];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufL[(lf * 5 + v) * n2 + p] -= nd * acc[v];
+    }
+    // Wbar += sum_l M[l][d] D_l Bbar_d
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      double a0[5] = {0, 0, 0, 0, 0}, a1[5] = {0, 0, 0, 0, 0}, a2[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + i], bufB + m * n2 + jk, nQ, a0);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + j], bufB + i * n2 + m * n + k, nQ, a1);
+      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + k], bufB + i * n2 + j * n + m, nQ, a2);
+      double M[3][3];
+      point_metric(T.type, dp + T.wA + o * 9, Jg, M);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufW[v * nQ + o] += M[0][d] * a0[v] + M[1][d] * a1[v] + M[2][d] * a2[v];
+    }
+    __syncthreads();
+  }
+  {
+    const double gm1 = c.gamma - 1.0;
+    const double* Un = c.Unod + c.slot_hoff[s];
+    double* Hb = c.H + c.slot_hoff[s];
+    for (int q = lane; q < nQ; q += blockDim.x) {
+      double U[5], Wb[5], Ub[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        U[v] = Un[v * nQ + q];
+        Wb[v] = bufW[v * nQ + q];
+      }
+      primitive_vjp(U, gm1, Wb, Ub);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Hb[v * nQ + q] += Ub[v];
+    }
+    for (int w = lane; w < nf * 5 * n2; w += blockDim.x) {
+      int lf = w / (5 * n2), r = w - lf * 5 * n2;
+      c.L[ft[lf] + r] = bufL[w];
+    }
+  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------ kernels
@@ -1214,6 +1487,8 @@ __global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va, int ph
   double* bufG = bufA + 5 * c.nQmax;
   double* bufC = bufG + 15 * c.nQmax;
   if (phase == 0) element_vjp_a(c, va, s, bufA, bufG, bufC, threadIdx.x);
+  else if (phase == 10) element_vjp_a_ns(c, va, s, smem, threadIdx.x);
+  else if (phase == 11) element_vjp_b_ns(c, s, smem, threadIdx.x);
   else element_vjp_c(c, va, s, bufA, bufG, threadIdx.x);
 }
 
@@ -1301,6 +1576,162 @@ __global__ void face_vjp_kernel(Ctx c) {
   }
 }
 
+// Navier-Stokes face adjoints.
+// KIND 1 (flux): g = wS (seed_own - Map seed_nb) is the cotangent of the
+//   unscaled flux F* = Riemann(U-, U+) - (F_v(U-, g-) + F_v(U+, g+)).n/2;
+//   trace cotangents Tv (own side: Ubar-, neighbour: Map^T Ubar+) and
+//   gradient-trace cotangents Vtb (likewise).  The neighbour's gradient
+//   cotangent at the owner's points is parked in the owner half of Vt (read
+//   only by the same thread) before the transposed map.
+// KIND 0 (lifting values): Wbar = wS (Lbar_own + Map Lbar_nb) / 2 for both
+//   means' arguments; Tv += (dW/dU)^T Wbar (own), Map^T (neighbour).
+template <int KIND>
+__global__ void face_ns_vjp_kernel(Ctx c) {
+  extern __shared__ double sF[];
+  const FaceBlock fb = c.fblocks[blockIdx.x];
+  const int n = fb.n, n2 = n * n, items = fb.count * n2;
+  double* sR = sF + 32 * 5 * n2;
+  const double gamma = c.gamma, gm1 = gamma - 1.0;
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, p = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    const double* T0 = c.T + R.toff;
+    const double* T1 = T0 + 5 * n2;
+    const double* S0 = (KIND == 1 ? c.Tv : c.L) + R.toff;
+    const double* S1 = S0 + 5 * n2;
+    double UL[5], UR[5], gs[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      UL[v] = T0[v * n2 + p];
+      gs[v] = S0[v * n2 + p];
+    }
+    const double sgn = KIND == 1 ? -1.0 : 1.0;
+    if (R.map >= 0) {
+      int j = c.perms[(size_t)R.map + p];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        UR[v] = T1[v * n2 + j];
+        gs[v] += sgn * S1[v * n2 + j];
+      }
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < n2; ++j) {
+          a = fma(D[j], T1[v * n2 + j], a);
+          b = fma(D[j], S1[v * n2 + j], b);
+        }
+        UR[v] = a;
+        gs[v] += sgn * b;
+      }
+    }
+    const TypeTab& T = c.tabs[R.owner_tab];
+    const double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    double UbL[5] = {0, 0, 0, 0, 0}, UbR[5] = {0, 0, 0, 0, 0};
+    if (KIND == 0) {
+      double Wb[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Wb[v] = 0.5 * wS * gs[v];
+      primitive_vjp(UL, gm1, Wb, UbL);
+      primitive_vjp(UR, gm1, Wb, UbR);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) gs[v] *= wS;
+      const double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+      if (c.flux == 0) flux_lf_vjp(UL, UR, nrm, gamma, gs, UbL, UbR);
+      else flux_roe_vjp(UL, UR, nrm, gamma, gs, UbL, UbR);
+      double Fvb[3][5];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fvb[d][v] = -0.5 * nrm[d] * gs[v];
+      double* V0 = c.Vt + 3 * R.toff;
+      const double* V1 = V0 + 15 * n2;
+      double gr[15], gb[15], W[5], Wb[5];
+      // owner side
+#pragma unroll
+      for (int t = 0; t < 15; ++t) {
+        gr[t] = V0[t * n2 + p];
+        gb[t] = 0.0;
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Wb[v] = 0.0;
+      primitive(UL, gm1, W);
+      viscous_flux_vjp(W, gr, c.mu, c.kappa, Fvb, Wb, gb);
+      primitive_vjp(UL, gm1, Wb, UbL);
+      double* B0 = c.Vtb + 3 * R.toff;
+#pragma unroll
+      for (int t = 0; t < 15; ++t) B0[t * n2 + p] = gb[t];
+      // neighbour side at the owner's points
+      if (R.map >= 0) {
+        int j = c.perms[(size_t)R.map + p];
+#pragma unroll
+        for (int t = 0; t < 15; ++t) gr[t] = V1[t * n2 + j];
+      } else {
+        const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
+        for (int t = 0; t < 15; ++t) {
+          double acc = 0.0;
+          for (int j = 0; j < n2; ++j) acc = fma(D[j], V1[t * n2 + j], acc);
+          gr[t] = acc;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 15; ++t) gb[t] = 0.0;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Wb[v] = 0.0;
+      primitive(UR, gm1, W);
+      viscous_flux_vjp(W, gr, c.mu, c.kappa, Fvb, Wb, gb);
+      primitive_vjp(UR, gm1, Wb, UbR);
+#pragma unroll
+      for (int t = 0; t < 15; ++t) V0[t * n2 + p] = gb[t];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      sF[(fl * 5 + v) * n2 + p] = UbL[v];
+      sR[(fl * 5 + v) * n2 + p] = UbR[v];
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int fl = w / n2, q = w - fl * n2;
+    const FaceRec& R = c.faces[fb.first + fl];
+    double* S0 = c.Tv + R.toff;
+    double* S1 = S0 + 5 * n2;
+    const double* Fl = sF + fl * 5 * n2;
+    const double* Fr = sR + fl * 5 * n2;
+    const double keep = KIND == 0 ? 1.0 : 0.0;     // lifting values add to the flux cotangents
+#pragma unroll
+    for (int v = 0; v < 5; ++v) S0[v * n2 + q] = keep * S0[v * n2 + q] + Fl[v * n2 + q];
+    const double* P0 = c.Vt + 3 * R.toff;          // parked neighbour gradient cotangents
+    double* B1 = c.Vtb + 3 * R.toff + 15 * n2;
+    if (R.map >= 0) {
+      int p = c.perms[(size_t)R.map + n2 + q];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) S1[v * n2 + q] = keep * S1[v * n2 + q] + Fr[v * n2 + p];
+      if (KIND == 1) {
+#pragma unroll
+        for (int t = 0; t < 15; ++t) B1[t * n2 + q] = P0[t * n2 + p];
+      }
+    } else {
+      const double* D = c.dense + (size_t)(-1 - R.map) + q;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int p = 0; p < n2; ++p) acc = fma(D[(size_t)p * n2], Fr[v * n2 + p], acc);
+        S1[v * n2 + q] = keep * S1[v * n2 + q] + acc;
+      }
+      if (KIND == 1) {
+        for (int t = 0; t < 15; ++t) {
+          double acc = 0.0;
+          for (int p = 0; p < n2; ++p) acc = fma(D[(size_t)p * n2], P0[t * n2 + p], acc);
+          B1[t * n2 + q] = acc;
+        }
+      }
+    }
+  }
+}
+
 // Storage <-> caller layout copies (warp per element).
 __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __restrict__ dst, int64_t E, int to_storage) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1374,30 +1805,37 @@ void launch_mode(const Ctx& c, const StageArgs& a, const Sched& s, bool balanced
 
 int element_smem_bytes_ns(int nQmax) { return 40 * nQmax * (int)sizeof(double); }
 
+// The shared-memory limits are per kernel function and process-wide, so they
+// are set for the largest element any mesh may hold (N = kMaxN); the
+// occupancy query uses this mesh's own launch size.
+constexpr int kMaxnQ = kMaxn * kMaxn * kMaxn;
+
 cudaError_t element_kernel_attributes_ns(int nQmax, int wpb, int* blocks_per_sm) {
-  const int bytes = element_smem_bytes_ns(nQmax);
   cudaError_t e;
-  if ((e = set_mode<kNsVolume>(bytes)) != cudaSuccess) return e;
+  if ((e = set_mode<kNsVolume>(element_smem_bytes_ns(kMaxnQ))) != cudaSuccess) return e;
   const int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_ns_kernel<0>, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_ns_kernel<1>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_vjp_kernel<0>, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_vjp_kernel<1>, 2 * fbytes)) != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kNsVolume>, 32 * wpb,
-                                                       bytes);
+                                                       element_smem_bytes_ns(nQmax));
 }
 
 cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
-  int bytes = element_smem_bytes(nQmax, wpb);
+  const int bmax = element_smem_bytes(kMaxnQ, wpb);
   cudaError_t e;
-  if ((e = set_mode<kFwd>(bytes)) != cudaSuccess) return e;
-  if ((e = set_mode<kBwdRhs>(bytes)) != cudaSuccess) return e;
-  if ((e = set_mode<kBwdRk>(bytes)) != cudaSuccess) return e;
-  if ((e = set_mode<kBwdRkFwd>(bytes)) != cudaSuccess) return e;
-  if ((e = set_mode<kProject>(bytes)) != cudaSuccess) return e;
+  if ((e = set_mode<kFwd>(bmax)) != cudaSuccess) return e;
+  if ((e = set_mode<kBwdRhs>(bmax)) != cudaSuccess) return e;
+  if ((e = set_mode<kBwdRk>(bmax)) != cudaSuccess) return e;
+  if ((e = set_mode<kBwdRkFwd>(bmax)) != cudaSuccess) return e;
+  if ((e = set_mode<kProject>(bmax)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_vjp_kernel, 2 * fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(elem_vjp_kernel, 25 * nQmax * (int)sizeof(double))) != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd>, 32 * wpb, bytes);
+  if ((e = set_smem(elem_vjp_kernel, 45 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd>, 32 * wpb,
+                                                       element_smem_bytes(nQmax, wpb));
 }
 
 void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb,
@@ -1413,9 +1851,17 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
   }
 }
 
+void launch_faces_ns_vjp(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  int bytes = 2 * 32 * 5 * n * n * (int)sizeof(double);
+  if (kind == 0) face_ns_vjp_kernel<0><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  else face_ns_vjp_kernel<1><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+}
+
 void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int wpb, cudaStream_t st) {
   if (nelem <= 0) return;
-  const int bytes = (phase == 0 ? 25 : 20) * c.nQmax * (int)sizeof(double);
+  const int per = phase == 0 || phase == 10 ? 25 : (phase == 11 ? 45 : 20);
+  const int bytes = per * c.nQmax * (int)sizeof(double);
   elem_vjp_kernel<<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va, phase);
 }
 

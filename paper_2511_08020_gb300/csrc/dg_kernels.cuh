@@ -67,6 +67,8 @@ struct Ctx {
   double* Unod;                // [slot][5][nQ] nodal state (slot_hoff offsets)
   double* L;                   // lifting face values, layout of T
   double* Vt;                  // gradient traces [face][2][3][5][n^2] (3x the offsets of T)
+  double* DW;                  // adjoint: nodal lifted gradient [slot][3][5][nQ] (3x slot_hoff), or null
+  double* Vtb;                 // adjoint: gradient-trace cotangents, layout of Vt
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
@@ -103,7 +105,12 @@ void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
 // inviscid + central viscous flux (T, Vt -> T).
 void launch_faces_ns(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st);
 int element_smem_bytes_ns(int nQmax);
+// phase 0: adjoint phase A (Euler), 2: phase C; Navier-Stokes adds 10: phase A
+// (inviscid + viscous flux transposes), 11: phase B (lifting transpose).
 void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int warps_per_block, cudaStream_t st);
+// Navier-Stokes face adjoints: kind 1 = flux (before phase B), kind 0 =
+// lifting values (after phase B).
+void launch_faces_ns_vjp(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st);
 void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st);
 int element_smem_bytes(int nQmax, int warps_per_block);

@@ -136,12 +136,111 @@ def test_ns_batch_equals_instances(dg):
         np.testing.assert_array_equal(b.instance(R, i), Ri)
 
 
-def test_ns_adjoint_unsupported(dg):
+# ---------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("kind,m,N,flux,reorder", [("mixed", 2, 2, "lf", None), ("kuhn", 2, 2, "roe", 7),
+                                                    ("mixed", 2, 3, "lf", 5), ("hex", 2, 1, "roe", 3),
+                                                    ("prism", 2, 3, "lf", None)])
+def test_ns_rhs_vjp_parity(dg, kind, m, N, flux, reorder):
+    box, o, mesh = setup(dg, kind, m, N, flux, reorder)
+    Q = state(o)
+    w = di.random_vector(Q.size, seed=11)
+    Qb = mesh.get_state(mesh.rhs_vjp(mesh.set_state(Q), mesh.set_state(w)))
+    ref = o.rhs_vjp(Q, w)
+    assert rel_err(Qb, ref, var_index(o.mesh.nM)) < TOL
+
+
+def test_ns_rhs_vjp_dot_product(dg):
+    """<J v, w> (oracle complex-step JVP through the NS residual) = <v, J^T w> (GPU)."""
+    box, o, mesh = setup(dg, "mixed", 3, 3, "roe", 4)
+    Q = state(o)
+    Qs = mesh.set_state(Q)
+    for k in range(3):
+        v = di.random_vector(Q.size, seed=20 + k)
+        w = di.random_vector(Q.size, seed=30 + k)
+        jv = o.rhs(Q + 1e-30j * v).imag / 1e-30
+        a = w @ jv
+        b = v @ mesh.get_state(mesh.rhs_vjp(Qs, mesh.set_state(w)))
+        assert abs(a - b) < 1e-11 * np.abs(w).sum() * np.abs(jv).max()
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder,nsteps,ckpt", [("mixed", 2, 2, "lf", 5, 2, 1),
+                                                                ("kuhn", 2, 2, "roe", 7, 3, 2)])
+def test_ns_rk_vjp_parity(dg, kind, m, N, flux, reorder, nsteps, ckpt):
+    from oracle.adjoint import rk_vjp
+    box, o, mesh = setup(dg, kind, m, N, flux, reorder)
+    Q0 = state(o)
+    w = di.random_vector(Q0.size, seed=13)
+    dt = 2e-3
+    Q0b = mesh.get_state(mesh.rk_vjp(mesh.set_state(Q0), dt, nsteps, ckpt, mesh.set_state(w)))
+    ref = rk_vjp(o, Q0, dt, nsteps, w)
+    assert rel_err(Q0b, ref, var_index(o.mesh.nM)) < TOL
+
+
+def test_ns_rk_vjp_checkpoint_invariance(dg):
+    box, o, mesh = setup(dg, "mixed", 3, 2, "lf", 8)
+    Q0 = state(o)
+    Qs = mesh.set_state(Q0)
+    Ws = mesh.set_state(di.random_vector(Q0.size, seed=5))
+    outs = [mesh.rk_vjp(Qs, 1e-3, 4, c, Ws).clone() for c in (1, 2, 4)]
+    for x in outs[1:]:
+        assert torch.equal(x, outs[0])
+
+
+def test_ns_noalloc_unsupported(dg):
+    import ctypes
     box, o, mesh = setup(dg, "hex", 2, 2)
     Q = mesh.empty().fill_(1.0)
-    with pytest.raises(dg.DGError) as ei:
-        mesh.rhs_vjp(Q, Q)
-    assert ei.value.status == -7
+    st = dg.load().dg_rhs_vjp_noalloc(mesh.handle, dg._ptr(Q), dg._ptr(Q), dg._ptr(mesh.empty()),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == -7
+
+
+def test_ns_kinetic_energy_adjoint_central_differences(dg):
+    """Adjoint of the final kinetic energy through K = 20 Navier-Stokes steps
+    (checkpoints every 5) on a 6^3 mixed box at N = 3, Re = 1600: the
+    directional derivative <dE_k/dQ0, v> by dg_rk_vjp against central
+    differences of E_k(Q_K(Q0 +- h v)).  E_k = sum over volume points of
+    w J |m|^2 / (2 rho), evaluated from the states on the host."""
+    from oracle.mesh import from_box
+    from oracle.navier_stokes import NSOracle
+    box = di.box_mesh(6, "mixed", seed=4, p_prism=0.25, p_pyr=1.0 / 9.0)
+    N = 3
+    o = NSOracle(from_box(box, N), flux="lf", mu=1.0 / 1600, Pr=PR)
+    mesh = dg.Mesh(box, N)
+    mesh.set_physics("navier_stokes", 1.0 / 1600, PR)
+    Q0 = o.project(lambda x: di.perturbed_tgv_state(x, seed=9, amp=1e-2))
+    dt, K = 2e-3, 20
+
+    def ek_and_grad(Q):
+        """E_k and dE_k/dQ (caller layout) by the oracle's quadrature."""
+        val, grad = 0.0, np.zeros_like(Q)
+        for e in range(o.mesh.n_elems):
+            op = o.ops[o.mesh.etype[e]]
+            U = o.mesh.block(Q, e) @ op.V.T
+            wq = o.mesh.J[e] * op.w
+            m2 = U[1] ** 2 + U[2] ** 2 + U[3] ** 2
+            val += np.sum(wq * 0.5 * m2 / U[0])
+            dU = np.stack([-0.5 * m2 / U[0] ** 2, U[1] / U[0], U[2] / U[0], U[3] / U[0], 0 * U[0]]) * wq
+            grad[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = (dU @ op.V).ravel()
+        return val, grad
+
+    def run(Q):
+        Qs = mesh.set_state(Q)
+        mesh.rk_step(Qs, mesh.empty(), dt, K)
+        return mesh.get_state(Qs)
+
+    _, gK = ek_and_grad(run(Q0))
+    g0 = mesh.get_state(mesh.rk_vjp(mesh.set_state(Q0), dt, K, 5, mesh.set_state(gK)))
+    # perturbation scaled per variable, small enough not to cross the kinks of max
+    v = di.random_vector(Q0.size, seed=41)
+    for idx in var_index(o.mesh.nM):
+        v[idx] *= np.abs(Q0[idx]).max()
+    h = 1e-7
+    ep, _ = ek_and_grad(run(Q0 + h * v))
+    em, _ = ek_and_grad(run(Q0 - h * v))
+    fd = (ep - em) / (2 * h)
+    ad = g0 @ v
+    assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
 
 
 def test_ns_sampled_12cube_N4(dg):
