@@ -836,11 +836,19 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
     }
     __syncthreads();
     lift_scaled(c, T, s, bufA, bufG, lane, c.L, d, -1.0);
-    double* sG = bufG + 5 * nQ;
-    Epilogue ep{Epilogue::kStore, true, -g.invJ, sG, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
-    nodal_to_modal(c, T, bufA, bufG, lane, ep);
     double* dW = bufDW + d * 5 * nQ;
-    modal_to_nodal(c, T, sG, dW, bufG, lane);
+    if (T.type == HEX) {
+      // V is square for the hexahedron, so V M_ref^{-1} V^T = W^{-1}: the
+      // projection onto the modal space is the identity at the nodes
+      const double* wq = dp + T.W;
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) dW[w] = -g.invJ * bufA[w] / wq[w % nQ];
+      __syncthreads();
+    } else {
+      double* sG = bufG + 5 * nQ;
+      Epilogue ep{Epilogue::kStore, true, -g.invJ, sG, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+      nodal_to_modal(c, T, bufA, bufG, lane, ep);
+      modal_to_nodal(c, T, sG, dW, bufG, lane);
+    }
     write_traces(c, T, s, dW, c.Vt, 1.0, lane, 3, (int64_t)d * 5 * n2);
     if (c.DW) {
       double* out = c.DW + 3 * c.slot_hoff[s] + d * 5 * nQ;
@@ -1193,9 +1201,17 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
 #pragma unroll
   for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
   for (int d = 0; d < 3; ++d) {
-    Epilogue ep{Epilogue::kStore, true, -g.invJ, bufX, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
-    nodal_to_modal(c, T, bufD + d * 5 * nQ, bufX, lane, ep);
-    modal_to_nodal(c, T, bufX, bufB, bufX, lane);     // Bbar_d in bufB
+    if (T.type == HEX) {
+      // V M_ref^{-1} V^T = W^{-1} (square V): pointwise
+      const double* wq = dp + T.W;
+      const double* Dd = bufD + d * 5 * nQ;
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufB[w] = -g.invJ * Dd[w] / wq[w % nQ];
+      __syncthreads();
+    } else {
+      Epilogue ep{Epilogue::kStore, true, -g.invJ, bufX, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+      nodal_to_modal(c, T, bufD + d * 5 * nQ, bufX, lane, ep);
+      modal_to_nodal(c, T, bufX, bufB, bufX, lane);   // Bbar_d in bufB
+    }
     // Lbar_f -= n_d(f) E_f Bbar_d on the own face points
     for (int w = lane; w < nf * n2; w += blockDim.x) {
       int lf = w / n2, p = w - lf * n2;
