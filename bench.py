@@ -476,6 +476,9 @@ def run_ours(args):
     fwd_ms = device_ms(lambda: mesh.rk_step(Qa, Ka, dt, Kadj))
     adj5_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, 5, wbar))
     adjK_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, Kadj, wbar))
+    mesh.set_adjoint_storage(False)
+    adj5r_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, 5, wbar))
+    mesh.set_adjoint_storage(True)
     rhs_ms = device_ms(lambda: mesh.rhs(Q0), reps=5)
     vjp_ms = device_ms(lambda: mesh.rhs_vjp(Q0, wbar), reps=5)
     mesh.sync()
@@ -547,6 +550,7 @@ def run_ours(args):
         "adjoint_over_forward": adj5_ms / fwd_ms,
         "adjoint": {"steps": Kadj, "forward_ms": fwd_ms, "rk_vjp_ckpt5_ms": adj5_ms, "rk_vjp_one_segment_ms": adjK_ms,
                     "ratio_ckpt5": adj5_ms / fwd_ms, "ratio_one_segment": adjK_ms / fwd_ms,
+                    "rk_vjp_ckpt5_recompute_ms": adj5r_ms, "ratio_ckpt5_recompute": adj5r_ms / fwd_ms,
                     "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms, "rhs_vjp_over_rhs": vjp_ms / rhs_ms},
     }
     if args.batch_steps > 0:

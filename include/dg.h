@@ -207,6 +207,16 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream);
 
+/* Memory/time trade-off of dg_rk_vjp.  keep_stages = 1 (default): the forward
+ * pass of each checkpoint segment keeps, per stage, the nodal state and the
+ * own-side traces (Euler: (H + F) doubles per stage, H = 5 sum_e n^3 and
+ * F = the face buffer, 10 n^2 per face; Navier-Stokes: 4 (H + F), adding
+ * the gradient traces and the nodal gradient), 5 ckpt_every stages at a time,
+ * so the reverse stages do not recompute them.  If that memory cannot be
+ * allocated dg_rk_vjp silently recomputes.  keep_stages = 0: always recompute
+ * (and free the store).  Results are bitwise identical either way. */
+dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages);
+
 /* Governing equations of dg_rhs / dg_rk_step (a new mesh solves the Euler
  * equations).  DG_NAVIER_STOKES: the Navier-Stokes-Fourier equations that
  * the paper's solver integrates (Sec. 2; Eq. 1 with a flux F(q, grad q); the

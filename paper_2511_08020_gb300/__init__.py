@@ -57,6 +57,7 @@ _SIGS = {
     "dg_rk_vjp": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "dg_set_scheduler": [_P, ctypes.c_int],
     "dg_set_physics": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
+    "dg_set_adjoint_storage": [_P, ctypes.c_int],
     "dg_cost_table": [_P, _P, _P, _P],
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
     "dg_sync": [_P, _P],
@@ -255,6 +256,10 @@ class Mesh:
         _check(load().dg_rk_vjp(self.handle, _ptr(Q0_store), float(dt), int(nsteps), int(ckpt_every),
                                 _ptr(QKbar), _ptr(Q0bar), _stream(stream)))
         return Q0bar
+
+    def set_adjoint_storage(self, keep_stages=True):
+        """dg_rk_vjp keeps per-stage forward data (True) or recomputes it (False)."""
+        _check(load().dg_set_adjoint_storage(self.handle, int(bool(keep_stages))))
 
     # ---------------------------------------------------------------- physics
     def set_physics(self, physics="euler", mu=0.0, Pr=0.72):

@@ -67,6 +67,47 @@ struct dg_mesh {
   double *d_Unod = nullptr, *d_L = nullptr, *d_Vt = nullptr, *d_fnrm = nullptr;
   double *d_DW = nullptr, *d_Vtb = nullptr;   // Navier-Stokes adjoint workspace
   bool store_dw = false;                      // the volume phase keeps the nodal gradient (adjoint)
+  bool keep_stages = true;                    // dg_rk_vjp keeps stage data (dg_set_adjoint_storage)
+  // Stage data kept by the forward pass of dg_rk_vjp for one segment (5 per
+  // step): the nodal state and the own-side traces, plus for Navier-Stokes
+  // the gradient traces and the nodal gradient.  The reverse stages then skip
+  // the forward recomputation.
+  double* d_sstore = nullptr;
+  size_t sstore_doubles = 0;
+  double *ov_T = nullptr, *ov_Unod = nullptr, *ov_Vt = nullptr, *ov_DW = nullptr, *ov_Usave = nullptr;
+  struct StagePtrs {
+    double *U, *T, *Vt, *DW;
+  };
+  size_t stage_doubles() const {
+    const size_t hh = (size_t)std::max<int64_t>(1, h.h_total), tt = (size_t)std::max<int64_t>(1, h.t_total);
+    return ns ? 4 * (hh + tt) : hh + tt;
+  }
+  StagePtrs stage_ptrs(int g) const {
+    const size_t hh = (size_t)std::max<int64_t>(1, h.h_total), tt = (size_t)std::max<int64_t>(1, h.t_total);
+    double* b = d_sstore + (size_t)g * stage_doubles();
+    StagePtrs P{b, b + hh, nullptr, nullptr};
+    if (ns) {
+      P.Vt = P.T + tt;
+      P.DW = P.Vt + 3 * tt;
+    }
+    return P;
+  }
+  void clear_overrides() { ov_T = ov_Unod = ov_Vt = ov_DW = ov_Usave = nullptr; }
+  // false when the store cannot be allocated: the caller recomputes instead
+  bool ensure_stage_store(int nstages) {
+    const size_t need = (size_t)nstages * stage_doubles();
+    if (need <= sstore_doubles) return true;
+    if (d_sstore) cudaFree(d_sstore);
+    d_sstore = nullptr;
+    sstore_doubles = 0;
+    if (cudaMalloc(&d_sstore, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();  // clear the allocation error; fall back to recomputation
+      d_sstore = nullptr;
+      return false;
+    }
+    sstore_doubles = need;
+    return true;
+  }
   // device data
   double* d_dpool = nullptr;
   int* d_ipool = nullptr;
@@ -168,13 +209,14 @@ struct dg_mesh {
     c.mu = mu;
     c.kappa = ns ? mu * gamma / ((gamma - 1.0) * Pr) : 0.0;
     c.fnrm = d_fnrm;
-    c.Unod = d_Unod;
+    c.Unod = ov_Unod ? ov_Unod : d_Unod;
     c.L = d_L;
-    c.Vt = d_Vt;
-    c.DW = store_dw ? d_DW : nullptr;
+    c.Vt = ov_Vt ? ov_Vt : d_Vt;
+    c.DW = ov_DW ? ov_DW : (store_dw ? d_DW : nullptr);
+    c.Usave = ov_Usave;
     c.Vtb = d_Vtb;
     c.H = d_H;
-    c.T = d_T;
+    c.T = ov_T ? ov_T : d_T;
     c.Tv = d_Tv;
     c.faces = d_faces;
     c.fblocks = d_fblocks;
@@ -306,16 +348,28 @@ struct dg_mesh {
   }
 
   // One RHS VJP (rk == 0) or one reverse LSERK stage (rk == 1) at state Q.
-  void enqueue_vjp(const dgk::VjpArgs& va, cudaStream_t st) {
+  // stage >= 0: the forward data of that stage of the store are used instead
+  // of recomputing them from va.Q.
+  void enqueue_vjp(dgk::VjpArgs va, cudaStream_t st, int stage = -1) {
+    if (stage >= 0) {
+      const StagePtrs P = stage_ptrs(stage);
+      ov_T = P.T;
+      ov_Unod = P.U;
+      ov_Vt = P.Vt;
+      ov_DW = P.DW;
+      va.stored = 1;
+    }
+    const int64_t nb = (int64_t)h.face_blocks.size();
     if (ns) {
-      // forward state at Q (traces, nodal state, lifting values, gradient
-      // traces and the nodal gradient), then the transposed phases
-      const int64_t nb = (int64_t)h.face_blocks.size();
-      dgk::StageArgs fa{va.Q, nullptr, nullptr, 0.0, 0.0, 0.0};
-      store_dw = true;
-      element_phase(dgk::kFwd, fa, st);
-      dgk::launch_faces_ns(ctx(), nb, h.n, 0, st);
-      element_phase(dgk::kNsVolume, fa, st);
+      if (stage < 0) {
+        // forward state at Q (traces, nodal state, lifting values, gradient
+        // traces and the nodal gradient), then the transposed phases
+        dgk::StageArgs fa{va.Q, nullptr, nullptr, 0.0, 0.0, 0.0};
+        store_dw = true;
+        element_phase(dgk::kFwd, fa, st);
+        dgk::launch_faces_ns(ctx(), nb, h.n, 0, st);
+        element_phase(dgk::kNsVolume, fa, st);
+      }
       dgk::Ctx c = ctx();
       store_dw = false;
       dgk::launch_vjp(c, 10, va, h.n_elems, wpb, st);
@@ -323,30 +377,55 @@ struct dg_mesh {
       dgk::launch_vjp(c, 11, va, h.n_elems, wpb, st);
       dgk::launch_faces_ns_vjp(c, nb, h.n, 0, st);
       dgk::launch_vjp(c, 2, va, h.n_elems, wpb, st);
+      clear_overrides();
       return;
     }
     dgk::Ctx c = ctx();
     dgk::launch_vjp(c, 0, va, h.n_elems, wpb, st);
-    dgk::launch_faces_vjp(c, (int64_t)h.face_blocks.size(), h.n, st);
+    dgk::launch_faces_vjp(c, nb, h.n, st);
     dgk::launch_vjp(c, 2, va, h.n_elems, wpb, st);
+    clear_overrides();
   }
 
   // Forward LSERK steps from Q (in place) with the stage inputs copied to
   // `stages` (5 per step) when non-null.  Non-captured launches.
-  void enqueue_rk_stages(double* Q, double* K, double dt, int nsteps, double* stages, cudaStream_t st) {
+  // keep: fill the stage store (stage g = 5 step + s) for enqueue_vjp.
+  void enqueue_rk_stages(double* Q, double* K, double dt, int nsteps, double* stages, cudaStream_t st,
+                         bool keep = false) {
     const size_t bytes = sizeof(double) * h.n_dof;
+    const size_t tbytes = sizeof(double) * (size_t)std::max<int64_t>(1, h.t_total);
+    auto keep_forward = [&](int g) {
+      if (!keep) return;
+      if (ns) ov_Unod = stage_ptrs(g).U;
+      else ov_Usave = stage_ptrs(g).U;
+    };
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
     parity = 0;
     dgk::StageArgs a{Q, Q, K, 0.0, 0.0, dt};
+    keep_forward(0);
     element_phase(dgk::kFwd, a, st);
+    clear_overrides();
     for (int step = 0; step < nsteps; ++step)
       for (int s = 0; s < 5; ++s) {
-        if (stages) cudaMemcpyAsync(stages + (size_t)(5 * step + s) * h.n_dof, Q, bytes, cudaMemcpyDeviceToDevice, st);
+        const int g = 5 * step + s;
+        if (stages) cudaMemcpyAsync(stages + (size_t)g * h.n_dof, Q, bytes, cudaMemcpyDeviceToDevice, st);
+        if (keep) {
+          const StagePtrs P = stage_ptrs(g);
+          cudaMemcpyAsync(P.T, d_T, tbytes, cudaMemcpyDeviceToDevice, st);
+          if (ns) {
+            ov_Unod = P.U;
+            ov_Vt = P.Vt;
+            ov_DW = P.DW;
+          }
+        }
         face_phase(st);
+        clear_overrides();
         bool last = step == nsteps - 1 && s == 4;
         a.a = kLsA[s];
         a.b = kLsB[s];
+        if (!last) keep_forward(g + 1);
         element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, st);
+        clear_overrides();
       }
   }
 
@@ -374,7 +453,7 @@ struct dg_mesh {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
-                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb};
+                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -657,7 +736,7 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
   DG_CUDA(mesh->ensure_adjoint(0));
-  dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
+  dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0, 0};
   mesh->enqueue_vjp(va, stream);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -717,7 +796,7 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
   dgk::Ctx c = mesh->ctx();
   c.Tv = scratch;  // every face side slot is written (seed) before it is read
-  dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0};
+  dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0, 0};
   dgk::launch_vjp(c, 0, va, mesh->h.n_elems, mesh->wpb, stream);
   dgk::launch_faces_vjp(c, (int64_t)mesh->h.face_blocks.size(), mesh->h.n, stream);
   dgk::launch_vjp(c, 2, va, mesh->h.n_elems, mesh->wpb, stream);
@@ -745,6 +824,9 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   double* Kw = Qw + n;
   double* ck = Kw + n;
   double* stages = ck + (size_t)nseg * n;
+  // forward data of one segment's stages kept for the reverse pass when the
+  // device has room (else each reverse stage recomputes them)
+  const bool keep = mesh->keep_stages && mesh->ensure_stage_store(5 * c);
   DG_CUDA(cudaMemcpyAsync(Qw, Q0_store, bytes, cudaMemcpyDeviceToDevice, stream));
   for (int seg = 0; seg < nseg - 1; ++seg) {
     DG_CUDA(cudaMemcpyAsync(ck + (size_t)seg * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
@@ -755,14 +837,27 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int steps = std::min(c, nsteps - seg * c);
     DG_CUDA(cudaMemcpyAsync(Qw, ck + (size_t)seg * n, bytes, cudaMemcpyDeviceToDevice, stream));
-    mesh->enqueue_rk_stages(Qw, Kw, dt, steps, stages, stream);
+    mesh->enqueue_rk_stages(Qw, Kw, dt, steps, keep ? nullptr : stages, stream, keep);
     for (int step = steps - 1; step >= 0; --step)
       for (int s = 4; s >= 0; --s) {
-        dgk::VjpArgs va{stages + (size_t)(5 * step + s) * n, nullptr, mesh->d_Kbar, Q0bar, kLsA[s], kLsB[s], dt, 1};
-        mesh->enqueue_vjp(va, stream);
+        const int g = 5 * step + s;
+        dgk::VjpArgs va{keep ? nullptr : stages + (size_t)g * n, nullptr, mesh->d_Kbar, Q0bar, kLsA[s], kLsB[s], dt,
+                        1, 0};
+        mesh->enqueue_vjp(va, stream, keep ? g : -1);
       }
   }
   DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  mesh->keep_stages = keep_stages != 0;
+  if (!mesh->keep_stages && mesh->d_sstore) {
+    DG_CUDA(cudaFree(mesh->d_sstore));
+    mesh->d_sstore = nullptr;
+    mesh->sstore_doubles = 0;
+  }
   return DG_OK;
 }
 

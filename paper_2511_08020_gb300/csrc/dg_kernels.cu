@@ -653,6 +653,11 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
   const double* dp = c.dpool;
   modal_to_nodal(c, T, bufG, bufA, bufG, lane);
   write_traces(c, T, s, bufA, c.T, 1.0, lane);
+  if (c.Usave) {
+    // kept for the adjoint (reverse LSERK with stored stage data)
+    double* Un = c.Usave + c.slot_hoff[s];
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) Un[w] = bufA[w];
+  }
   if (c.ns) {
     // Navier-Stokes: the volume residual needs the lifted gradient, which
     // needs the neighbours' traces; keep the nodal state for that phase.
@@ -962,11 +967,18 @@ __device__ __noinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int6
   const double* dp = c.dpool;
   const int64_t qoff = c.slot_qoff[s];
   const int nQm = c.nQmax;
-  // forward nodal state and its traces (read by the face phase)
-  for (int w = lane; w < 5 * nM; w += blockDim.x) bufC[w] = va.Q[qoff + w];
-  __syncthreads();
-  modal_to_nodal(c, T, bufC, bufA, bufG, lane);
-  write_traces(c, T, s, bufA, c.T, 1.0, lane);
+  // forward nodal state and its traces (read by the face phase): kept by the
+  // forward pass, or recomputed from Q
+  if (va.stored) {
+    const double* Un = c.Unod + c.slot_hoff[s];
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = Un[w];
+    __syncthreads();
+  } else {
+    for (int w = lane; w < 5 * nM; w += blockDim.x) bufC[w] = va.Q[qoff + w];
+    __syncthreads();
+    modal_to_nodal(c, T, bufC, bufA, bufG, lane);
+    write_traces(c, T, s, bufA, c.T, 1.0, lane);
+  }
   // scaled cotangent of the modal residual
   const double invJ = c.geo[s].invJ;
   for (int w = lane; w < 5 * nM; w += blockDim.x) {
@@ -1496,15 +1508,17 @@ __global__ void face_ns_kernel(Ctx c) {
 
 // ------------------------------------------------------------------ adjoint kernels
 
-__global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va, int phase) {
+// One kernel per phase, so that each gets its own register allocation.
+template <int PHASE>
+__global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va) {
   extern __shared__ double smem[];
   const int64_t s = blockIdx.x;
   double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
   double* bufC = bufG + 15 * c.nQmax;
-  if (phase == 0) element_vjp_a(c, va, s, bufA, bufG, bufC, threadIdx.x);
-  else if (phase == 10) element_vjp_a_ns(c, va, s, smem, threadIdx.x);
-  else if (phase == 11) element_vjp_b_ns(c, s, smem, threadIdx.x);
+  if (PHASE == 0) element_vjp_a(c, va, s, bufA, bufG, bufC, threadIdx.x);
+  else if (PHASE == 10) element_vjp_a_ns(c, va, s, smem, threadIdx.x);
+  else if (PHASE == 11) element_vjp_b_ns(c, s, smem, threadIdx.x);
   else element_vjp_c(c, va, s, bufA, bufG, threadIdx.x);
 }
 
@@ -1849,7 +1863,10 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_vjp_kernel, 2 * fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(elem_vjp_kernel, 45 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<0>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<2>, 20 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<10>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<11>, 45 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd>, 32 * wpb,
                                                        element_smem_bytes(nQmax, wpb));
 }
@@ -1878,7 +1895,12 @@ void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int w
   if (nelem <= 0) return;
   const int per = phase == 0 || phase == 10 ? 25 : (phase == 11 ? 45 : 20);
   const int bytes = per * c.nQmax * (int)sizeof(double);
-  elem_vjp_kernel<<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va, phase);
+  switch (phase) {
+    case 0: elem_vjp_kernel<0><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
+    case 10: elem_vjp_kernel<10><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
+    case 11: elem_vjp_kernel<11><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
+    default: elem_vjp_kernel<2><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
+  }
 }
 
 void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {

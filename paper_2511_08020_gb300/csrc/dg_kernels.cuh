@@ -68,6 +68,7 @@ struct Ctx {
   double* L;                   // lifting face values, layout of T
   double* Vt;                  // gradient traces [face][2][3][5][n^2] (3x the offsets of T)
   double* DW;                  // adjoint: nodal lifted gradient [slot][3][5][nQ] (3x slot_hoff), or null
+  double* Usave;               // Euler forward: also keep the nodal state here (slot_hoff), or null
   double* Vtb;                 // adjoint: gradient-trace cotangents, layout of Vt
 };
 
@@ -81,6 +82,7 @@ struct VjpArgs {
   double* Qbar;
   double a, b, dt;
   int rk;
+  int stored;   // 1: the forward nodal state (Unod) and traces (T) of Q were kept by the forward pass
 };
 
 struct StageArgs {

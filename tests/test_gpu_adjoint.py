@@ -80,6 +80,21 @@ def test_rk_vjp_parity(dg, kind, m, N, flux, reorder, nsteps, ckpt):
     assert rel_err(Q0b, ref, var_index(o.mesh.nM)) < TOL
 
 
+@pytest.mark.parametrize("flux", ["lf", "roe"])
+def test_rk_vjp_stored_equals_recomputed(dg, flux):
+    """dg_rk_vjp with the per-stage forward data kept (default) and with every
+    reverse stage recomputing it from the stage state: bitwise equal."""
+    box, o, mesh = setup(dg, "mixed", 3, 3, flux, 6)
+    Q0 = state(o)
+    Qs = mesh.set_state(Q0)
+    Ws = mesh.set_state(di.random_vector(Q0.size, seed=7))
+    kept = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    mesh.set_adjoint_storage(False)
+    recomputed = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    mesh.set_adjoint_storage(True)
+    assert torch.equal(kept, recomputed)
+
+
 def test_rk_vjp_checkpoint_invariance(dg):
     box, o, mesh = setup(dg, "mixed", 3, 2, "lf", 8)
     Q0 = state(o)

@@ -186,6 +186,17 @@ def test_ns_rk_vjp_checkpoint_invariance(dg):
         assert torch.equal(x, outs[0])
 
 
+def test_ns_rk_vjp_stored_equals_recomputed(dg):
+    box, o, mesh = setup(dg, "mixed", 3, 3, "roe", 6)
+    Q0 = state(o)
+    Qs = mesh.set_state(Q0)
+    Ws = mesh.set_state(di.random_vector(Q0.size, seed=7))
+    kept = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    mesh.set_adjoint_storage(False)
+    recomputed = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    assert torch.equal(kept, recomputed)
+
+
 def test_ns_noalloc_unsupported(dg):
     import ctypes
     box, o, mesh = setup(dg, "hex", 2, 2)
