@@ -95,8 +95,13 @@ def ns_element_flops(t, N):
     # per direction: lifting volume term, face lift, projection V M^-1 V^T
     # (pointwise 1/w for the hexahedron, whose V is square) and gradient traces
     proj = 5 * nQ if t == 0 else 2 * 5 * (bwd + fwd)
-    per_dir = 2 * 5 * (3 * n ** 4 + 2 * nf * n ** 3) + proj + nQ * (15 + 13)
-    volume = 3 * per_dir + 2 * 5 * 3 * n ** 4 + nQ * (61 + metric + 13 + 66 + 72)
+    per_dir = 2 * 5 * (2 * nf * n ** 3) + proj
+    # lifting volume terms through the reference directions: one directional
+    # pass per structurally nonzero entry of d(a,b,c)/dxi (3/4/5/6 for
+    # hex/prism/pyramid/tet), then the 3x3 metric combination per point
+    nz = (3, 4, 5, 6)[t]
+    lift_volume = 2 * 5 * nz * n ** 4 + nQ * (13 + 5 * nz + 2 * 5 * 9)
+    volume = lift_volume + 3 * per_dir + 2 * 5 * 3 * n ** 4 + nQ * (61 + metric + 13 + 66 + 72)
     return fused + volume
 
 

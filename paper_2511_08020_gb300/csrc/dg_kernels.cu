@@ -603,6 +603,11 @@ __device__ __forceinline__ void write_traces(const Ctx& c, const TypeTab& T, int
   }
 }
 
+// Structurally nonzero entries of d(a,b,c)_l / d(xi)_k per type: bit l*3+k.
+// hex: diagonal; prism: a(xi, eta); pyramid: a(xi, zeta), b(eta, zeta);
+// tet: a(xi, eta, zeta), b(eta, zeta); c = zeta for all.
+__constant__ unsigned kMetricMask[4] = {0x111u, 0x113u, 0x135u, 0x137u};
+
 // M = (w_q d(a,b,c)/d(xi)) (J dxi/dx) at volume point q, using each
 // collapse's sparsity (hex: diagonal; prism, pyramid, tet: triangular).
 __device__ __forceinline__ void point_metric(int type, const double* wa, const double* Jg, double M[3][3]) {
@@ -812,32 +817,63 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
     for (int w = lane; w < 5 * nQ; w += blockDim.x) bufU[w] = Un[w];
   }
   __syncthreads();
-  for (int d = 0; d < 3; ++d) {
-    // G_l = (w da_l/dxi J dxi/dx_d) W at the volume points
+  // Lifting volume terms through the reference directions: with
+  // M[l][d] = sum_k wA[l][k] Jg[k][d] (wA = w da_l/dxi_k, structurally sparse
+  // per type), Hd = sum_l D_l^T (M[l][d] W) = sum_k Jg[k][d] P_k with
+  // P_k = sum_{l: wA[l][k] != 0} D_l^T (wA[l][k] W): 3 (hex) to 6 (tet)
+  // directional passes instead of 9.  H_0..H_2 accumulate in bufDW.
+  for (int q = lane; q < nQ; q += blockDim.x) {
+    double U[5], W[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = bufU[v * nQ + q];
+    primitive(U, gm1, W);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bufA[v * nQ + q] = W[v];
+  }
+  __syncthreads();
+  const unsigned nz = kMetricMask[T.type];
+  for (int kr = 0; kr < 3; ++kr) {
+    const bool u0 = (nz >> (0 * 3 + kr)) & 1u, u1 = (nz >> (1 * 3 + kr)) & 1u, u2 = (nz >> (2 * 3 + kr)) & 1u;
     for (int q = lane; q < nQ; q += blockDim.x) {
-      double U[5], W[5];
+      const double* wa = dp + T.wA + q * 9;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) U[v] = bufU[v * nQ + q];
-      primitive(U, gm1, W);
-      double M[3][3];
-      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      for (int l = 0; l < 3; ++l) {
+        if (!((nz >> (l * 3 + kr)) & 1u)) continue;
+        const double f = wa[l * 3 + kr];
 #pragma unroll
-      for (int l = 0; l < 3; ++l)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) bufG[(l * 5 + v) * nQ + q] = M[l][d] * W[v];
+        for (int v = 0; v < 5; ++v) bufG[(l * 5 + v) * nQ + q] = f * bufA[v * nQ + q];
+      }
     }
     __syncthreads();
     for (int o = lane; o < nQ; o += blockDim.x) {
       int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
-      const double* G0 = bufG + jk;
-      const double* G1 = bufG + 5 * nQ + i * n2 + k;
-      const double* G2 = bufG + 10 * nQ + i * n2 + j * n;
       double acc[5] = {0, 0, 0, 0, 0};
-      for (int m = 0; m < n; ++m) DG_FMA5(Dt[i * n + m], G0 + m * n2, nQ, acc);
-      for (int m = 0; m < n; ++m) DG_FMA5(Dt[j * n + m], G1 + m * n, nQ, acc);
-      for (int m = 0; m < n; ++m) DG_FMA5(Dt[k * n + m], G2 + m, nQ, acc);
+      if (u0) {
+        const double* G0 = bufG + jk;
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[i * n + m], G0 + m * n2, nQ, acc);
+      }
+      if (u1) {
+        const double* G1 = bufG + 5 * nQ + i * n2 + k;
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[j * n + m], G1 + m * n, nQ, acc);
+      }
+      if (u2) {
+        const double* G2 = bufG + 10 * nQ + i * n2 + j * n;
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[k * n + m], G2 + m, nQ, acc);
+      }
 #pragma unroll
-      for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = acc[v];
+      for (int d = 0; d < 3; ++d) {
+        double* Hd = bufDW + d * 5 * nQ + o;
+        const double jkd = Jg[kr * 3 + d];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Hd[v * nQ] = kr == 0 ? jkd * acc[v] : fma(jkd, acc[v], Hd[v * nQ]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int d = 0; d < 3; ++d) {
+    {
+      const double* Hd = bufDW + d * 5 * nQ;
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = Hd[w];
     }
     __syncthreads();
     lift_scaled(c, T, s, bufA, bufG, lane, c.L, d, -1.0);
@@ -1213,16 +1249,16 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
 #pragma unroll
   for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
   for (int d = 0; d < 3; ++d) {
+    double* Bd = bufD + d * 5 * nQ;     // DWbar_d, replaced by Bbar_d
     if (T.type == HEX) {
       // V M_ref^{-1} V^T = W^{-1} (square V): pointwise
       const double* wq = dp + T.W;
-      const double* Dd = bufD + d * 5 * nQ;
-      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufB[w] = -g.invJ * Dd[w] / wq[w % nQ];
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) Bd[w] = -g.invJ * Bd[w] / wq[w % nQ];
       __syncthreads();
     } else {
       Epilogue ep{Epilogue::kStore, true, -g.invJ, bufX, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
-      nodal_to_modal(c, T, bufD + d * 5 * nQ, bufX, lane, ep);
-      modal_to_nodal(c, T, bufX, bufB, bufX, lane);   // Bbar_d in bufB
+      nodal_to_modal(c, T, Bd, bufX, lane, ep);
+      modal_to_nodal(c, T, bufX, Bd, bufX, lane);
     }
     // Lbar_f -= n_d(f) E_f Bbar_d on the own face points
     for (int w = lane; w < nf * n2; w += blockDim.x) {
@@ -1233,27 +1269,56 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
       int sb = fd.beta == 0 ? n2 : (fd.beta == 1 ? n : 1);
       int sf = fd.fixed == 0 ? n2 : (fd.fixed == 1 ? n : 1);
       const double* e = dp + T.ext + fd.end * n;
-      const double* Bs = bufB + ia * sa + ib * sb;
+      const double* Bs = Bd + ia * sa + ib * sb;
       double acc[5] = {0, 0, 0, 0, 0};
       for (int m = 0; m < n; ++m) DG_FMA5(e[m], Bs + m * sf, nQ, acc);
       const double nd = c.fnrm[(s * 6 + lf) * 3 + d];
 #pragma unroll
       for (int v = 0; v < 5; ++v) bufL[(lf * 5 + v) * n2 + p] -= nd * acc[v];
     }
-    // Wbar += sum_l M[l][d] D_l Bbar_d
-    for (int o = lane; o < nQ; o += blockDim.x) {
-      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
-      double a0[5] = {0, 0, 0, 0, 0}, a1[5] = {0, 0, 0, 0, 0}, a2[5] = {0, 0, 0, 0, 0};
-      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + i], bufB + m * n2 + jk, nQ, a0);
-      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + j], bufB + i * n2 + m * n + k, nQ, a1);
-      for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + k], bufB + i * n2 + j * n + m, nQ, a2);
-      double M[3][3];
-      point_metric(T.type, dp + T.wA + o * 9, Jg, M);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) bufW[v * nQ + o] += M[0][d] * a0[v] + M[1][d] * a1[v] + M[2][d] * a2[v];
-    }
     __syncthreads();
   }
+  // Wbar = sum_d sum_l M[l][d] D_l Bbar_d = sum_k sum_{l: wA[l][k] != 0} wA[l][k] D_l C_k
+  // with C_k = sum_d Jg[k][d] Bbar_d (in place of the Bbar_d)
+  for (int w = lane; w < 5 * nQ; w += blockDim.x) {
+    const double b0 = bufD[w], b1 = bufD[5 * nQ + w], b2 = bufD[10 * nQ + w];
+#pragma unroll
+    for (int kr = 0; kr < 3; ++kr)
+      bufD[kr * 5 * nQ + w] = Jg[kr * 3] * b0 + Jg[kr * 3 + 1] * b1 + Jg[kr * 3 + 2] * b2;
+  }
+  __syncthreads();
+  {
+    const unsigned nz = kMetricMask[T.type];
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      const double* wa = dp + T.wA + o * 9;
+      double wb[5] = {0, 0, 0, 0, 0};
+      for (int kr = 0; kr < 3; ++kr) {
+        const double* C = bufD + kr * 5 * nQ;
+        if ((nz >> kr) & 1u) {
+          double a[5] = {0, 0, 0, 0, 0};
+          for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + i], C + m * n2 + jk, nQ, a);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) wb[v] = fma(wa[kr], a[v], wb[v]);
+        }
+        if ((nz >> (3 + kr)) & 1u) {
+          double a[5] = {0, 0, 0, 0, 0};
+          for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + j], C + i * n2 + m * n + k, nQ, a);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) wb[v] = fma(wa[3 + kr], a[v], wb[v]);
+        }
+        if ((nz >> (6 + kr)) & 1u) {
+          double a[5] = {0, 0, 0, 0, 0};
+          for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + k], C + i * n2 + j * n + m, nQ, a);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) wb[v] = fma(wa[6 + kr], a[v], wb[v]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufW[v * nQ + o] = wb[v];
+    }
+  }
+  __syncthreads();
   {
     const double gm1 = c.gamma - 1.0;
     const double* Un = c.Unod + c.slot_hoff[s];
