@@ -65,7 +65,7 @@ def test_hilbert_order_is_local(dg):
     assert np.mean(d < 1.01 * h) > 0.99
 
 
-@pytest.mark.parametrize("bad", ["nonaffine", "unmatched", "type", "degree"])
+@pytest.mark.parametrize("bad", ["nonaffine", "unmatched", "type", "degree", "degree0", "empty", "vertex"])
 def test_bad_mesh_rejected(dg, bad):
     box = di.box_mesh(3, "hex", seed=1)
     N = 2
@@ -83,8 +83,19 @@ def test_bad_mesh_rejected(dg, bad):
         et[0] = 7
         box = di.BoxMesh(box.xyz, et, box.elem_vert_off, box.elem_verts, box.period, 3, "hex", 1)
         status = -1
-    else:
+    elif bad == "degree":
         N = 9
+        status = -1
+    elif bad == "degree0":
+        N = 0
+        status = -1
+    elif bad == "empty":
+        box = di.BoxMesh(box.xyz, box.etype[:0], box.elem_vert_off[:1], box.elem_verts[:0], box.period, 3, "hex", 1)
+        status = -1
+    else:
+        ev = box.elem_verts.copy()
+        ev[3] = len(box.xyz) + 5                     # vertex index out of range
+        box = di.BoxMesh(box.xyz, box.etype, box.elem_vert_off, ev, box.period, 3, "hex", 1)
         status = -1
     with pytest.raises(dg.DGError) as ei:
         dg.check_mesh(box, N)

@@ -35,7 +35,8 @@ def state(o, seed=3, amp=0.05):
 
 
 CASES = [("mixed", 2, 3, "lf", 5), ("mixed", 2, 3, "roe", 5), ("kuhn", 2, 3, "lf", 7), ("kuhn", 2, 2, "roe", 7),
-         ("hex", 2, 4, "lf", 3), ("mixed", 3, 2, "lf", None), ("prism", 2, 5, "roe", 2)]
+         ("hex", 2, 4, "lf", 3), ("mixed", 3, 2, "lf", None), ("prism", 2, 5, "roe", 2),
+         ("mixed", 2, 6, "lf", 4)]                                            # N = 6 = DG_MAX_N
 
 
 @pytest.mark.parametrize("kind,m,N,flux,reorder", CASES)
@@ -93,6 +94,14 @@ def test_rk_vjp_stored_equals_recomputed(dg, flux):
     recomputed = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
     mesh.set_adjoint_storage(True)
     assert torch.equal(kept, recomputed)
+
+
+def test_rk_vjp_zero_steps_is_identity(dg):
+    box, o, mesh = setup(dg, "mixed", 2, 2, "lf")
+    Q0 = state(o)
+    Ws = mesh.set_state(di.random_vector(Q0.size, seed=3))
+    out = mesh.rk_vjp(mesh.set_state(Q0), 1e-3, 0, 1, Ws)
+    assert torch.equal(out, Ws)
 
 
 def test_rk_vjp_checkpoint_invariance(dg):

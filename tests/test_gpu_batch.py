@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 # (kind, m, N, vertex reordering seed)
 INSTANCES = [("mixed", 3, 2, None), ("kuhn", 2, 3, 7), ("hex", 2, 4, None), ("mixed", 2, 1, 5),
-             ("pyramid", 2, 3, None), ("prism", 2, 5, 3)]
+             ("pyramid", 2, 3, None), ("prism", 2, 5, 3), ("mixed", 2, 6, 9)]
 
 
 @pytest.fixture(scope="module")

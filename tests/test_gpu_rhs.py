@@ -38,7 +38,8 @@ def state(o, seed=3, amp=0.05):
 CASES = [("mixed", 4, 3, "lf", None), ("mixed", 4, 3, "roe", None), ("kuhn", 2, 3, "lf", 7),
          ("kuhn", 2, 2, "roe", 7), ("mixed", 3, 2, "lf", 5), ("mixed", 2, 4, "roe", 5),
          ("hex", 2, 5, "lf", 3), ("prism", 2, 5, "roe", 3), ("pyramid", 2, 1, "lf", None),
-         ("kuhn", 2, 5, "lf", 11), ("mixed", 3, 1, "roe", 2)]
+         ("kuhn", 2, 5, "lf", 11), ("mixed", 3, 1, "roe", 2),
+         ("mixed", 2, 6, "roe", 3), ("kuhn", 2, 6, "lf", None)]      # N = 6 = DG_MAX_N
 
 
 @pytest.mark.parametrize("kind,m,N,flux,reorder", CASES)
@@ -68,6 +69,16 @@ def test_rk_step_parity(dg, kind, m, N, flux, reorder, nsteps):
     assert err < 1e-10, err
     assert rel_err(Qg, Qref, var_index(o.mesh.nM)) < TOL
     mesh.sync()
+
+
+def test_zero_steps_is_identity(dg):
+    box, o, mesh = setup(dg, "mixed", 2, 3, "lf", None)
+    Q = state(o)
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    before = Qs.clone()
+    mesh.rk_step(Qs, mesh.empty(), 1e-3, 0)
+    mesh.sync()
+    assert torch.equal(Qs, before)
 
 
 @pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 4, 3, None), ("kuhn", 2, 4, 7), ("hex", 2, 2, 1)])
