@@ -484,6 +484,12 @@ def run_ours(args):
     mesh.set_adjoint_storage(False)
     adj5r_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, 5, wbar))
     mesh.set_adjoint_storage(True)
+    # autograd split: the forward keeps the segment-start checkpoints, the
+    # backward recomputes the segments from them
+    Qc = Q0.clone()
+    ck = mesh.rk_step_checkpointed(Qc, Ka, dt, Kadj, 5)
+    fwdc_ms = device_ms(lambda: mesh.rk_step_checkpointed(Qc, Ka, dt, Kadj, 5, ck))
+    adjc_ms = device_ms(lambda: mesh.rk_vjp_checkpointed(ck, dt, Kadj, 5, wbar))
     rhs_ms = device_ms(lambda: mesh.rhs(Q0), reps=5)
     vjp_ms = device_ms(lambda: mesh.rhs_vjp(Q0, wbar), reps=5)
     mesh.sync()
@@ -556,6 +562,8 @@ def run_ours(args):
         "adjoint": {"steps": Kadj, "forward_ms": fwd_ms, "rk_vjp_ckpt5_ms": adj5_ms, "rk_vjp_one_segment_ms": adjK_ms,
                     "ratio_ckpt5": adj5_ms / fwd_ms, "ratio_one_segment": adjK_ms / fwd_ms,
                     "rk_vjp_ckpt5_recompute_ms": adj5r_ms, "ratio_ckpt5_recompute": adj5r_ms / fwd_ms,
+                    "forward_checkpointed_ms": fwdc_ms, "rk_vjp_checkpointed_ms": adjc_ms,
+                    "ratio_backward_given_forward_checkpoints": adjc_ms / fwdc_ms,
                     "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms, "rhs_vjp_over_rhs": vjp_ms / rhs_ms},
     }
     if args.batch_steps > 0:
@@ -660,8 +668,20 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
         e2.record(stream)
         torch.cuda.synchronize()
         fwd_ms, adj_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        ck = mesh.rk_step_checkpointed(Qa, Kr, dt, Ka, 5)
+        mesh.rk_vjp_checkpointed(ck, dt, Ka, 5, seed)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mesh.rk_step_checkpointed(Qa, Kr, dt, Ka, 5, ck)
+        e1.record(stream)
+        mesh.rk_vjp_checkpointed(ck, dt, Ka, 5, seed)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fwdc_ms, adjc_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
         out["adjoint"] = {"steps": Ka, "ckpt_every": 5, "forward_ms": fwd_ms, "rk_vjp_ms": adj_ms,
-                          "adjoint_over_forward": adj_ms / fwd_ms}
+                          "adjoint_over_forward": adj_ms / fwd_ms, "forward_checkpointed_ms": fwdc_ms,
+                          "rk_vjp_checkpointed_ms": adjc_ms,
+                          "backward_given_forward_checkpoints_over_forward": adjc_ms / fwdc_ms}
     mesh.sync()
     mesh.close()
     return out

@@ -207,6 +207,20 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream);
 
+/* The same split at the checkpoints, for callers that run the forward steps
+ * themselves (an autograd forward): dg_rk_step_checkpointed advances Q_store
+ * by nsteps steps exactly as dg_rk_step and writes Q at the start of every
+ * segment of ckpt_every steps to ckpt_store (device, caller-owned,
+ * [ceil(nsteps / ckpt_every)][n_dof] in the storage layout);
+ * dg_rk_vjp_checkpointed then computes Q0bar from those checkpoints without
+ * the forward pass that dg_rk_vjp runs to place them (bitwise the same result
+ * as dg_rk_vjp from the same Q0).  QKbar and Q0bar may alias.
+ * Asynchronous. */
+dg_status dg_rk_step_checkpointed(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps,
+                                  int ckpt_every, double* ckpt_store, cudaStream_t stream);
+dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double dt, int nsteps, int ckpt_every,
+                                 const double* QKbar, double* Q0bar, cudaStream_t stream);
+
 /* Memory/time trade-off of dg_rk_vjp.  keep_stages = 1 (default): the forward
  * pass of each checkpoint segment keeps, per stage, the nodal state and the
  * own-side traces (Euler: (H + F) doubles per stage, H = 5 sum_e n^3 and

@@ -55,6 +55,8 @@ _SIGS = {
     "dg_rk_step": [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P],
     "dg_rhs_vjp": [_P, _P, _P, _P, _P],
     "dg_rk_vjp": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
+    "dg_rk_step_checkpointed": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P],
+    "dg_rk_vjp_checkpointed": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "dg_set_scheduler": [_P, ctypes.c_int],
     "dg_set_physics": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
     "dg_set_adjoint_storage": [_P, ctypes.c_int],
@@ -266,6 +268,24 @@ class Mesh:
         """'euler' or 'navier_stokes' (BR1 lifting, constant mu, Prandtl number Pr)."""
         _check(load().dg_set_physics(self.handle, PHYSICS[physics] if isinstance(physics, str) else int(physics),
                                      float(mu), float(Pr)))
+
+    def rk_step_checkpointed(self, Q_store, K_store, dt, nsteps, ckpt_every, ckpt=None, stream=None):
+        """dg_rk_step that also writes the segment-start checkpoints; returns them
+        ([ceil(nsteps / ckpt_every), n_dof] CUDA tensor)."""
+        import torch
+        nseg = max(1, -(-int(nsteps) // max(1, min(int(ckpt_every), max(1, int(nsteps))))))
+        if ckpt is None:
+            ckpt = torch.empty((nseg, self.n_dof), dtype=torch.float64, device=Q_store.device)
+        _check(load().dg_rk_step_checkpointed(self.handle, _ptr(Q_store), _ptr(K_store), float(dt), int(nsteps),
+                                              int(ckpt_every), _ptr(ckpt), _stream(stream)))
+        return ckpt
+
+    def rk_vjp_checkpointed(self, ckpt, dt, nsteps, ckpt_every, QKbar, Q0bar=None, stream=None):
+        if Q0bar is None:
+            Q0bar = self.empty()
+        _check(load().dg_rk_vjp_checkpointed(self.handle, _ptr(ckpt), float(dt), int(nsteps), int(ckpt_every),
+                                             _ptr(QKbar), _ptr(Q0bar), _stream(stream)))
+        return Q0bar
 
     # ---------------------------------------------------------------- scheduler
     def set_scheduler(self, kind):

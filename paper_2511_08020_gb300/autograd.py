@@ -2,8 +2,10 @@
 
 Forward and backward both run in libdg.so: DGRHS.forward is dg_rhs and its
 backward dg_rhs_vjp (the hand-written adjoint of Eq. 1's residual); DGRK
-advances K LSERK(5,4) steps with dg_rk_step and its backward is dg_rk_vjp
-(reverse LSERK with checkpointed recomputation).  Tensors are float64 CUDA
+advances K LSERK(5,4) steps with dg_rk_step_checkpointed (keeping the state
+at the start of every segment of ckpt_every steps) and its backward is
+dg_rk_vjp_checkpointed (reverse LSERK recomputing each segment from its
+checkpoint).  Tensors are float64 CUDA
 tensors in the library's storage layout.
 """
 from __future__ import annotations
@@ -34,15 +36,15 @@ class DGRK(torch.autograd.Function):
     def forward(ctx, Q0, mesh, dt, nsteps, ckpt_every=5):
         Q0 = Q0.contiguous()
         ctx.mesh, ctx.dt, ctx.nsteps, ctx.ckpt = mesh, float(dt), int(nsteps), int(ckpt_every)
-        ctx.save_for_backward(Q0)
         Q = Q0.clone()
-        mesh.rk_step(Q, torch.empty_like(Q), dt, nsteps)
+        ckpts = mesh.rk_step_checkpointed(Q, torch.empty_like(Q), dt, nsteps, ckpt_every)
+        ctx.save_for_backward(ckpts)
         return Q
 
     @staticmethod
     def backward(ctx, QKbar):
-        (Q0,) = ctx.saved_tensors
-        Q0bar = ctx.mesh.rk_vjp(Q0, ctx.dt, ctx.nsteps, ctx.ckpt, QKbar.contiguous())
+        (ckpts,) = ctx.saved_tensors
+        Q0bar = ctx.mesh.rk_vjp_checkpointed(ckpts, ctx.dt, ctx.nsteps, ctx.ckpt, QKbar.contiguous())
         return Q0bar, None, None, None, None
 
 

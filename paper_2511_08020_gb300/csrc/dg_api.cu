@@ -74,6 +74,8 @@ struct dg_mesh {
   // the forward recomputation.
   double* d_sstore = nullptr;
   size_t sstore_doubles = 0;
+  double* d_ckpt_q = nullptr;                 // dg_rk_vjp's own checkpoints (+ work state)
+  size_t ckpt_q_doubles = 0;
   double *ov_T = nullptr, *ov_Unod = nullptr, *ov_Vt = nullptr, *ov_DW = nullptr, *ov_Usave = nullptr;
   struct StagePtrs {
     double *U, *T, *Vt, *DW;
@@ -453,7 +455,7 @@ struct dg_mesh {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
-                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore};
+                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -809,30 +811,22 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 //   Kbar <- Kbar + B_s Qbar;  Qbar <- Qbar + dt J(Q_{s-1})^T Kbar;  Kbar <- A_s Kbar.
 // Stage inputs are recomputed segment by segment from checkpoints of Q taken
 // every ckpt_every steps (the last segment's forward pass is not needed).
-dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
-                    const double* QKbar, double* Q0bar, cudaStream_t stream) {
-  if (!mesh || !Q0_store || !QKbar || !Q0bar) return fail(DG_ERR_ARG, "null argument");
-  if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
-  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
+}  // extern "C"
+
+namespace {
+// Reverse sweep of dg_rk_vjp over the checkpoints ck[seg] (Q at the start of
+// segment seg of c steps); Q0bar already holds QKbar.
+dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps, int c, double* Q0bar,
+                         cudaStream_t stream) {
   const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
-  if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
-  if (nsteps == 0) return DG_OK;
-  const int c = std::min(ckpt_every, nsteps);
   const int nseg = (nsteps + c - 1) / c;
-  DG_CUDA(mesh->ensure_adjoint((size_t)(2 + nseg + 5 * c) * n));
+  DG_CUDA(mesh->ensure_adjoint((size_t)(2 + 5 * c) * n));
   double* Qw = mesh->d_ckpt;
   double* Kw = Qw + n;
-  double* ck = Kw + n;
-  double* stages = ck + (size_t)nseg * n;
+  double* stages = Kw + n;
   // forward data of one segment's stages kept for the reverse pass when the
   // device has room (else each reverse stage recomputes them)
   const bool keep = mesh->keep_stages && mesh->ensure_stage_store(5 * c);
-  DG_CUDA(cudaMemcpyAsync(Qw, Q0_store, bytes, cudaMemcpyDeviceToDevice, stream));
-  for (int seg = 0; seg < nseg - 1; ++seg) {
-    DG_CUDA(cudaMemcpyAsync(ck + (size_t)seg * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
-    mesh->enqueue_rk_stages(Qw, Kw, dt, c, nullptr, stream);
-  }
-  DG_CUDA(cudaMemcpyAsync(ck + (size_t)(nseg - 1) * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
   DG_CUDA(cudaMemsetAsync(mesh->d_Kbar, 0, bytes, stream));
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int steps = std::min(c, nsteps - seg * c);
@@ -849,6 +843,81 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
+
+dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
+                      double dt) {
+  if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
+  if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
+  return DG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+// Reverse LSERK through nsteps steps (2N storage, K = 0 at every step start),
+// per stage s = 5..1 at the stage input state Q_{s-1}:
+//   Kbar <- Kbar + B_s Qbar;  Qbar <- Qbar + dt J(Q_{s-1})^T Kbar;  Kbar <- A_s Kbar.
+// Stage inputs are recomputed segment by segment from checkpoints of Q taken
+// every ckpt_every steps (placed by a first forward pass here, or by
+// dg_rk_step_checkpointed for dg_rk_vjp_checkpointed).
+dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
+                    const double* QKbar, double* Q0bar, cudaStream_t stream) {
+  dg_status st = rk_vjp_args(mesh, Q0_store, QKbar, Q0bar, nsteps, ckpt_every, dt);
+  if (st != DG_OK) return st;
+  const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
+  if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
+  if (nsteps == 0) return DG_OK;
+  const int c = std::min(ckpt_every, nsteps);
+  const int nseg = (nsteps + c - 1) / c;
+  if (!mesh->d_ckpt_q || mesh->ckpt_q_doubles < (size_t)(nseg + 2) * n) {
+    if (mesh->d_ckpt_q) cudaFree(mesh->d_ckpt_q);
+    mesh->d_ckpt_q = nullptr;
+    mesh->ckpt_q_doubles = 0;
+    DG_CUDA(cudaMalloc(&mesh->d_ckpt_q, sizeof(double) * (size_t)(nseg + 2) * n));
+    mesh->ckpt_q_doubles = (size_t)(nseg + 2) * n;
+  }
+  double* Qw = mesh->d_ckpt_q;
+  double* Kw = Qw + n;
+  double* ck = Kw + n;
+  DG_CUDA(cudaMemcpyAsync(Qw, Q0_store, bytes, cudaMemcpyDeviceToDevice, stream));
+  for (int seg = 0; seg < nseg - 1; ++seg) {
+    DG_CUDA(cudaMemcpyAsync(ck + (size_t)seg * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
+    mesh->enqueue_rk_stages(Qw, Kw, dt, c, nullptr, stream);
+  }
+  DG_CUDA(cudaMemcpyAsync(ck + (size_t)(nseg - 1) * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
+  return rk_vjp_reverse(mesh, ck, dt, nsteps, c, Q0bar, stream);
+}
+
+dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double dt, int nsteps, int ckpt_every,
+                                 const double* QKbar, double* Q0bar, cudaStream_t stream) {
+  dg_status st = rk_vjp_args(mesh, ckpt_store, QKbar, Q0bar, nsteps, ckpt_every, dt);
+  if (st != DG_OK) return st;
+  const size_t bytes = sizeof(double) * (size_t)mesh->h.n_dof;
+  if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
+  if (nsteps == 0) return DG_OK;
+  return rk_vjp_reverse(mesh, ckpt_store, dt, nsteps, std::min(ckpt_every, nsteps), Q0bar, stream);
+}
+
+dg_status dg_rk_step_checkpointed(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps,
+                                  int ckpt_every, double* ckpt_store, cudaStream_t stream) {
+  if (!mesh || !Q_store || !K_store || !ckpt_store) return fail(DG_ERR_ARG, "null argument");
+  if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
+  const size_t bytes = sizeof(double) * (size_t)mesh->h.n_dof;
+  const int c = std::max(1, std::min(ckpt_every, nsteps));
+  for (int seg = 0, done = 0; done < nsteps; ++seg, done += c) {
+    DG_CUDA(cudaMemcpyAsync(ckpt_store + (size_t)seg * mesh->h.n_dof, Q_store, bytes, cudaMemcpyDeviceToDevice,
+                            stream));
+    dg_status r = dg_rk_step(mesh, Q_store, K_store, dt, std::min(c, nsteps - done), stream);
+    if (r != DG_OK) return r;
+  }
+  return DG_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");

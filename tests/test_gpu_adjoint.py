@@ -96,6 +96,25 @@ def test_rk_vjp_stored_equals_recomputed(dg, flux):
     assert torch.equal(kept, recomputed)
 
 
+@pytest.mark.parametrize("nsteps,ckpt", [(4, 2), (5, 2), (3, 5)])
+def test_rk_checkpointed_split(dg, nsteps, ckpt):
+    """dg_rk_step_checkpointed == dg_rk_step and dg_rk_vjp_checkpointed ==
+    dg_rk_vjp, bitwise (including a shorter last segment)."""
+    box, o, mesh = setup(dg, "mixed", 2, 3, "roe", 6)
+    Q0 = state(o)
+    Qa = mesh.set_state(Q0)
+    Qb = Qa.clone()
+    Q0s = Qa.clone()
+    mesh.rk_step(Qa, mesh.empty(), 1e-3, nsteps)
+    ck = mesh.rk_step_checkpointed(Qb, mesh.empty(), 1e-3, nsteps, ckpt)
+    assert torch.equal(Qa, Qb)
+    assert torch.equal(ck[0], Q0s)
+    Ws = mesh.set_state(di.random_vector(Q0.size, seed=8))
+    ref = mesh.rk_vjp(Q0s, 1e-3, nsteps, ckpt, Ws).clone()
+    got = mesh.rk_vjp_checkpointed(ck, 1e-3, nsteps, ckpt, Ws)
+    assert torch.equal(ref, got)
+
+
 def test_rk_vjp_zero_steps_is_identity(dg):
     box, o, mesh = setup(dg, "mixed", 2, 2, "lf")
     Q0 = state(o)

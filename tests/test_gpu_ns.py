@@ -198,6 +198,17 @@ def test_ns_rk_vjp_stored_equals_recomputed(dg):
     assert torch.equal(kept, recomputed)
 
 
+def test_ns_rk_checkpointed_split(dg):
+    box, o, mesh = setup(dg, "mixed", 2, 3, "lf", 6)
+    Q0 = state(o)
+    Q0s = mesh.set_state(Q0)
+    Qb = Q0s.clone()
+    ck = mesh.rk_step_checkpointed(Qb, mesh.empty(), 1e-3, 5, 2)
+    Ws = mesh.set_state(di.random_vector(Q0.size, seed=8))
+    ref = mesh.rk_vjp(Q0s, 1e-3, 5, 2, Ws).clone()
+    assert torch.equal(ref, mesh.rk_vjp_checkpointed(ck, 1e-3, 5, 2, Ws))
+
+
 def test_ns_noalloc_unsupported(dg):
     import ctypes
     box, o, mesh = setup(dg, "hex", 2, 2)
