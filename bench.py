@@ -420,6 +420,7 @@ def run_ours(args):
         return
 
     dfma, dmma = dg.probe_fp64_peak()
+    fp64_mixed = dg.probe_fp64_mixed()
     # ALU roofline: FP64 peak from unit counts and clocks -- every SM retires
     # 2 DFMA per clock (the sm__inst_executed_pipe_fp64 peak ncu reports for
     # this part), 2 flops each, at the maximum SM clock seen during the run
@@ -549,7 +550,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_stage": el_bytes_stage, "algorithmic_flops_per_stage": el_flops_stage,
                      "element_ms_per_step": elem_ms / steps_p, "face_ms_per_step": face_ms / steps_p,
                      "face_kernel_tflops": face_tflops, "whole_step_tflops": total_tflops,
-                     "dmma_peak_measured": dmma},
+                     "dmma_peak_measured": dmma, "dfma_plus_dmma_concurrent_measured": fp64_mixed},
         "cost_table_ns_per_elem": dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns_type])),
         "sm_load_imbalance": imb,
         "clocks": clk,

@@ -313,6 +313,11 @@ const char* dg_last_error(void);
  * m8n8k4), TFLOP/s, from a ~50 ms probe launch.  Synchronises. */
 dg_status dg_probe_fp64_peak(double* dfma_tflops, double* dmma_tflops);
 
+/* Combined FP64 throughput (TFLOP/s) when half of every block's warps run
+ * DFMA chains and the other half mma.sync f64 at the same time: equal to the
+ * single-path rates if the two share one FP64 throughput limit.  Synchronises. */
+dg_status dg_probe_fp64_mixed(double* total_tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "FLUX", "SCHED", "PHYSICS", "load"]
+__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "probe_fp64_mixed", "FLUX", "SCHED", "PHYSICS", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
 SCHED = {"balanced": 0, "naive": 1, "static": 2}
@@ -64,6 +64,7 @@ _SIGS = {
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
     "dg_sync": [_P, _P],
     "dg_probe_fp64_peak": [_P, _P],
+    "dg_probe_fp64_mixed": [_P],
     "dg_set_profiling": [_P, ctypes.c_int],
     "dg_set_stage_fusion": [_P, ctypes.c_int],
     "dg_set_element_warps": [_P, ctypes.c_int],
@@ -150,6 +151,13 @@ def probe_fp64_peak():
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().dg_probe_fp64_peak(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def probe_fp64_mixed():
+    """Combined DFMA + mma.sync f64 throughput with both running at once (TFLOP/s)."""
+    a = ctypes.c_double()
+    _check(load().dg_probe_fp64_mixed(ctypes.byref(a)))
+    return a.value
 
 
 class Mesh:

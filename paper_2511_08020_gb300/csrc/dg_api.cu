@@ -1190,6 +1190,13 @@ dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream) {
   return DG_OK;
 }
 
+dg_status dg_probe_fp64_mixed(double* total_tflops) {
+  if (!total_tflops) return fail(DG_ERR_ARG, "null argument");
+  cudaError_t e = dgk::probe_fp64_mixed(total_tflops);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 probe");
+  return DG_OK;
+}
+
 dg_status dg_probe_fp64_peak(double* dfma_tflops, double* dmma_tflops) {
   if (!dfma_tflops || !dmma_tflops) return fail(DG_ERR_ARG, "null argument");
   cudaError_t e = dgk::probe_fp64(dfma_tflops, dmma_tflops);

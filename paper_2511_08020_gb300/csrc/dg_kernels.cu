@@ -1680,8 +1680,10 @@ __global__ void face_vjp_kernel(Ctx c) {
 //   only by the same thread) before the transposed map.
 // KIND 0 (lifting values): Wbar = wS (Lbar_own + Map Lbar_nb) / 2 for both
 //   means' arguments; Tv += (dW/dU)^T Wbar (own), Map^T (neighbour).
+// At most 7 warps (n <= 7) per block; two resident blocks at the largest n
+// (three at n = 5) instead of the two that 168 registers allow.
 template <int KIND>
-__global__ void face_ns_vjp_kernel(Ctx c) {
+__global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
   extern __shared__ double sF[];
   const FaceBlock fb = c.fblocks[blockIdx.x];
   const int n = fb.n, n2 = n * n, items = fb.count * n2;
@@ -1869,7 +1871,66 @@ __global__ void dmma_probe_kernel(double* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
+// Half the warps of a block run DFMA chains, the other half mma.sync f64:
+// shows whether the two share one FP64 throughput limit.
+__global__ void fp64_mixed_probe_kernel(double* out, int it_f, int it_m) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double t = 0;
+  if (warp < nw / 2) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
+    for (int i = 0; i < it_f; ++i) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fma(a[k], 1.0000001, 1e-7);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += a[k];
+  } else {
+    double a = 1e-3 * (threadIdx.x & 7), b = 1e-3 * ((threadIdx.x >> 3) & 3);
+    double c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
+    for (int i = 0; i < it_m; ++i) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                     : "+d"(c0[k]), "+d"(c1[k])
+                     : "d"(a), "d"(b));
+    }
+    for (int k = 0; k < 4; ++k) t += c0[k] + c1[k];
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 }  // namespace
+
+cudaError_t probe_fp64_mixed(double* total_tflops) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 4, threads = 256, itf = 4000, itm = 4000;
+  double* out = nullptr;
+  e = cudaMalloc(&out, sizeof(double) * blocks * threads);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fp64_mixed_probe_kernel<<<blocks, threads>>>(out, 10, 10);
+  cudaEventRecord(e0);
+  fp64_mixed_probe_kernel<<<blocks, threads>>>(out, itf, itm);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  const double fl = 2.0 * 8 * itf * (double)blocks * (threads / 2) + 2.0 * 8 * 8 * 4 * 4 * itm * (double)blocks * (threads / 64);
+  *total_tflops = fl / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e = cudaGetLastError();
+  cudaFree(out);
+  return e;
+}
 
 int element_smem_bytes(int nQmax, int) { return 20 * nQmax * (int)sizeof(double); }
 int face_block_threads(int n) { return 32 * n; }

@@ -120,5 +120,6 @@ int face_block_threads(int n);
 cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm);
 cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm);
 cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops);
+cudaError_t probe_fp64_mixed(double* total_tflops);
 
 }  // namespace dgk
