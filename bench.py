@@ -737,12 +737,16 @@ def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
     res = {}
     for sched in ("naive", "balanced"):
         b.set_scheduler(sched)
-        warps, _ = b.autotune(Q0, dt)
+        warps, tms = b.autotune(Q0, dt)
         Q = Q0.clone()
         K = torch.empty_like(Q)
         ms, _ = timed(Q, K)
         res[sched] = Q
-        out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps}
+        out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps,
+                      "autotune_ms_per_step": [round(x, 3) for x in tms.tolist()]}
+        if sched == "balanced":
+            names = ("hex", "prism", "pyramid", "tet")
+            out[sched]["tile_shapes"] = {f"{names[t]}/N{N}": w for t, N, w in b.tile_shapes()}
     Qp = Q0.clone()
     _, el_ms = timed(Qp, torch.empty_like(Qp), profile=True)
     out["unit"] = "DOF-updates/s"

@@ -260,20 +260,33 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr);
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler);
 
 /* Tile shape of the element kernels: the number of warps (1..4) that work
- * together on one element (one element per thread block).  The default is
- * 2 for N <= 4 and 1 above; dg_autotune picks the fastest.  Rebuilds the
- * chunk tables; results are bitwise identical for every choice. */
+ * together on one element (one element per thread block), for every (type,
+ * N) table at once.  The default is 2 for N <= 4 and 1 above; dg_autotune
+ * picks the fastest.  Rebuilds the chunk tables; results are bitwise
+ * identical for every choice. */
 dg_status dg_set_element_warps(dg_mesh* mesh, int warps);
 
-/* Autotuner: times one dg_rk_step of size dt for every element tile shape
+/* Tile shape of one (type, N) table (balanced scheduler): tables that share
+ * N and warps form one persistent launch per phase, sized for that N.
+ * DG_ERR_ARG if the mesh (or batch) holds no element of that type and N. */
+dg_status dg_set_table_warps(dg_mesh* mesh, int type, int N, int warps);
+
+/* The tables present and their tile shapes: *n_tables receives the count;
+ * type, N, warps (host, [max], may be NULL) the first max entries. */
+dg_status dg_tile_shapes(const dg_mesh* mesh, int max, int* n_tables, int* type, int* N, int* warps);
+
+/* Autotuner: times dg_rk_step of size dt for every uniform tile shape
  * (1..4 warps per element) on a scratch copy of Q_store (device, storage
- * layout; library-allocated scratch of 2 n_dof doubles, freed on return) and
- * keeps the fastest for this mesh's scheduler and flux.  With the environment
- * variable DG_AUTOTUNE_CACHE naming a file, results are read from and
- * appended to it, keyed by device name, N, element counts, scheduler and
- * flux.  best_warps (may be NULL) receives the choice, ms_per_step (host [4],
- * may be NULL) the measured times (zeros when taken from the cache).
- * Synchronises `stream`. */
+ * layout; library-allocated scratch of 2 n_dof doubles, freed on return),
+ * reads each table's time per element from the in-kernel cost probe, and
+ * keeps the fastest uniform shape unless per-table shapes (each table at its
+ * best resident-blocks-per-time ratio; balanced scheduler only) make the step
+ * faster still.  With the environment variable DG_AUTOTUNE_CACHE naming a
+ * file, results are read from and appended to it, keyed by device name, N,
+ * element counts, scheduler and flux.  best_warps (may be NULL) receives the
+ * uniform choice, ms_per_step (host [5], may be NULL) the times of the four
+ * uniform shapes and of the per-table shapes (0 when not tried; all zeros
+ * when taken from the cache).  Synchronises `stream`. */
 dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best_warps, double* ms_per_step,
                       cudaStream_t stream);
 

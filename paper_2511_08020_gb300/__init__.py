@@ -59,6 +59,8 @@ _SIGS = {
     "dg_rk_vjp_checkpointed": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "dg_set_scheduler": [_P, ctypes.c_int],
     "dg_set_physics": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
+    "dg_set_table_warps": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "dg_tile_shapes": [_P, ctypes.c_int, _P, _P, _P, _P],
     "dg_set_adjoint_storage": [_P, ctypes.c_int],
     "dg_cost_table": [_P, _P, _P, _P],
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
@@ -315,12 +317,25 @@ class Mesh:
         _check(load().dg_set_element_warps(self.handle, int(warps)))
 
     def autotune(self, Q_store, dt, stream=None):
-        """Pick the fastest warps-per-element for this mesh; returns (warps, ms per step [4])."""
+        """Pick the fastest tile shapes; returns (uniform warps, ms per step [5]: the four
+        uniform shapes and the per-table shapes, 0 when not tried)."""
         import numpy as np
         best = ctypes.c_int()
-        ms = np.zeros(4)
+        ms = np.zeros(5)
         _check(load().dg_autotune(self.handle, _ptr(Q_store), float(dt), ctypes.byref(best), _ptr(ms), _stream(stream)))
         return best.value, ms
+
+    def set_table_warps(self, etype, N, warps):
+        _check(load().dg_set_table_warps(self.handle, int(etype), int(N), int(warps)))
+
+    def tile_shapes(self):
+        """[(type, N, warps)] of the tables present."""
+        import numpy as np
+        k = ctypes.c_int()
+        _check(load().dg_tile_shapes(self.handle, 0, ctypes.byref(k), None, None, None))
+        t, n, w = (np.zeros(max(1, k.value), dtype=np.int32) for _ in range(3))
+        _check(load().dg_tile_shapes(self.handle, k.value, ctypes.byref(k), _ptr(t), _ptr(n), _ptr(w)))
+        return [(int(a), int(b), int(c)) for a, b, c in zip(t[:k.value], n[:k.value], w[:k.value])]
 
     def set_stage_fusion(self, fused=True):
         _check(load().dg_set_stage_fusion(self.handle, int(bool(fused))))

@@ -134,11 +134,8 @@ struct dg_mesh {
   unsigned long long* d_smns = nullptr;
   unsigned* d_counters = nullptr;
   int64_t* d_type_slots[4] = {nullptr, nullptr, nullptr, nullptr};
-  int64_t* d_chunks = nullptr;
-  int64_t nchunks = 0;
   int64_t* d_chunks_static = nullptr;
   int64_t nchunks_static = 0;
-  int64_t* d_chunk_list = nullptr;
   bool fused = true;  // backward of stage s and forward of stage s+1 in one launch
   double weight[dgk::kMaxTabs] = {};  // chunk weights in use per (type, N) table (ns or modelled)
 
@@ -236,49 +233,110 @@ struct dg_mesh {
   int grid_balanced() const { return num_sms * blocks_per_sm; }
   int grid_ns() const { return num_sms * blocks_per_sm_ns; }
 
-  // Balanced work list: the Hilbert order grouped by (type, N) table (every
-  // group's elements stay in Hilbert order), groups in decreasing cost per
-  // element, cut into contiguous chunks by guided self-scheduling on the
-  // measured (or modelled) cost: each chunk takes a fixed fraction of the
-  // work still unassigned, so chunks are large at first and single elements
-  // at the end, where they set the length of the tail.  A chunk never spans
-  // two groups, so at any moment most blocks run one group's code.
-  cudaError_t build_chunks(const double* tab_weight) {
-    const int64_t E = h.n_elems;
-    const int ntab = (int)h.tables.tabs.size();
-    for (int t = 0; t < dgk::kMaxTabs; ++t) weight[t] = tab_weight[t];
-    std::vector<int> order(ntab);
-    for (int t = 0; t < ntab; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tab_weight[x] > tab_weight[y]; });
-    std::vector<int64_t> list;
-    list.reserve(E);
-    for (int oi = 0; oi < ntab; ++oi)
-      for (int64_t s = 0; s < E; ++s)
-        if (h.slot_tab[s] == order[oi]) list.push_back(s);
-    double remaining = 0.0;
-    for (int64_t s = 0; s < E; ++s) remaining += tab_weight[h.slot_tab[s]];
-    const double blocks = (double)std::max(1, grid_balanced());
-    std::vector<int64_t> starts;
-    starts.push_back(0);
-    double acc = 0.0, target = remaining / (2.0 * blocks);
-    for (int64_t i = 0; i < E; ++i) {
-      const double w = tab_weight[h.slot_tab[list[i]]];
-      acc += w;
-      remaining -= w;
-      bool type_end = i + 1 < E && h.slot_tab[list[i + 1]] != h.slot_tab[list[i]];
-      if (i + 1 < E && (acc >= target || type_end)) {
-        starts.push_back(i + 1);
-        acc = 0.0;
-        target = remaining / (2.0 * blocks);
+  // Launch groups of the balanced scheduler: the (type, N) tables present in
+  // the mesh, grouped by (n, warps per element).  Every group is one
+  // persistent launch per phase with its own block size, shared memory
+  // (n^3-sized buffers) and grid, so the tile shape can differ per table
+  // (dg_autotune chooses it per table).
+  struct Group {
+    int n = 0, wpb = 1, bpsm = 1, bpsm_ns = 1;
+    std::vector<int> tabs;
+    int64_t* d_chunks = nullptr;
+    int64_t* d_list = nullptr;
+    int64_t nchunks = 0;
+  };
+  std::vector<Group> groups;
+  int tab_wpb[dgk::kMaxTabs] = {};
+
+  void free_groups() {
+    for (auto& G : groups) {
+      if (G.d_chunks) cudaFree(G.d_chunks);
+      if (G.d_list) cudaFree(G.d_list);
+    }
+    groups.clear();
+  }
+
+  cudaError_t build_groups() {
+    free_groups();
+    std::vector<int64_t> count(h.tables.tabs.size(), 0);
+    for (int64_t s = 0; s < h.n_elems; ++s) ++count[h.slot_tab[s]];
+    for (size_t t = 0; t < h.tables.tabs.size(); ++t) {
+      if (!count[t]) continue;
+      const int n = h.tables.tabs[t].n, w = tab_wpb[t];
+      auto it = std::find_if(groups.begin(), groups.end(), [&](const Group& G) { return G.n == n && G.wpb == w; });
+      if (it == groups.end()) {
+        Group G;
+        G.n = n;
+        G.wpb = w;
+        groups.push_back(G);
+        it = groups.end() - 1;
+      }
+      it->tabs.push_back((int)t);
+    }
+    for (auto& G : groups) {
+      cudaError_t e = dgk::element_kernel_attributes(G.n * G.n * G.n, G.wpb, &G.bpsm);
+      if (e != cudaSuccess) return e;
+      if (G.bpsm < 1) G.bpsm = 1;
+      if (ns) {
+        e = dgk::element_kernel_attributes_ns(G.n * G.n * G.n, G.wpb, &G.bpsm_ns);
+        if (e != cudaSuccess) return e;
+        if (G.bpsm_ns < 1) G.bpsm_ns = 1;
       }
     }
-    starts.push_back(E);
-    nchunks = (int64_t)starts.size() - 1;
-    if (d_chunks) cudaFree(d_chunks);
-    if (d_chunk_list) cudaFree(d_chunk_list);
-    cudaError_t e = upload(&d_chunks, starts);
+    // restore the mesh-wide attributes used by the static and naive launches
+    cudaError_t e = dgk::element_kernel_attributes(nQmax, wpb, &blocks_per_sm);
     if (e != cudaSuccess) return e;
-    return upload(&d_chunk_list, list);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    std::vector<double> w(weight, weight + dgk::kMaxTabs);
+    return build_chunks(w.data());
+  }
+
+  // Balanced work list of every group: the Hilbert order grouped by (type,
+  // N) table (every table's elements stay in Hilbert order), tables in
+  // decreasing cost per element, cut into contiguous chunks by guided
+  // self-scheduling on the measured (or modelled) cost: each chunk takes a
+  // fixed fraction of the group's work still unassigned, so chunks are large
+  // at first and single elements at the end, where they set the length of
+  // the tail.  A chunk never spans two tables.
+  cudaError_t build_chunks(const double* tab_weight) {
+    const int64_t E = h.n_elems;
+    for (int t = 0; t < dgk::kMaxTabs; ++t) weight[t] = tab_weight[t];
+    for (auto& G : groups) {
+      std::vector<int> order = G.tabs;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tab_weight[x] > tab_weight[y]; });
+      std::vector<int64_t> list;
+      for (int t : order)
+        for (int64_t s = 0; s < E; ++s)
+          if (h.slot_tab[s] == t) list.push_back(s);
+      const int64_t L = (int64_t)list.size();
+      double remaining = 0.0;
+      for (int64_t s : list) remaining += tab_weight[h.slot_tab[s]];
+      const double blocks = (double)std::max(1, num_sms * G.bpsm);
+      std::vector<int64_t> starts;
+      starts.push_back(0);
+      double acc = 0.0, target = remaining / (2.0 * blocks);
+      for (int64_t i = 0; i < L; ++i) {
+        const double w = tab_weight[h.slot_tab[list[i]]];
+        acc += w;
+        remaining -= w;
+        bool tab_end = i + 1 < L && h.slot_tab[list[i + 1]] != h.slot_tab[list[i]];
+        if (i + 1 < L && (acc >= target || tab_end)) {
+          starts.push_back(i + 1);
+          acc = 0.0;
+          target = remaining / (2.0 * blocks);
+        }
+      }
+      starts.push_back(L);
+      G.nchunks = (int64_t)starts.size() - 1;
+      if (G.d_chunks) cudaFree(G.d_chunks);
+      if (G.d_list) cudaFree(G.d_list);
+      G.d_chunks = G.d_list = nullptr;
+      cudaError_t e = upload(&G.d_chunks, starts);
+      if (e != cudaSuccess) return e;
+      e = upload(&G.d_list, list);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
 
   // Static partition: one contiguous Hilbert segment of equal element count
@@ -296,10 +354,17 @@ struct dg_mesh {
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
     dgk::Ctx c = ctx();
     timed(true, st, [&] {
-      if ((scheduler == DG_SCHED_BALANCED || scheduler == DG_SCHED_STATIC) && mode != dgk::kProject) {
-        const bool stat = scheduler == DG_SCHED_STATIC;
-        dgk::Sched s{stat ? nullptr : d_chunk_list, stat ? nchunks_static : nchunks, stat ? d_chunks_static : d_chunks,
-                     d_counters + parity, d_counters + (parity ^ 1)};
+      if (scheduler == DG_SCHED_BALANCED && mode != dgk::kProject) {
+        for (const auto& G : groups) {
+          dgk::Ctx cg = c;
+          cg.nQmax = G.n * G.n * G.n;
+          dgk::Sched s{G.d_list, G.nchunks, G.d_chunks, d_counters + parity, d_counters + (parity ^ 1)};
+          dgk::launch_element(cg, mode, a, s, true, num_sms * (mode == dgk::kNsVolume ? G.bpsm_ns : G.bpsm), G.wpb,
+                              st);
+          parity ^= 1;
+        }
+      } else if (scheduler == DG_SCHED_STATIC && mode != dgk::kProject) {
+        dgk::Sched s{nullptr, nchunks_static, d_chunks_static, d_counters + parity, d_counters + (parity ^ 1)};
         dgk::launch_element(c, mode, a, s, true, mode == dgk::kNsVolume ? grid_ns() : grid_balanced(), wpb, st);
         parity ^= 1;
       } else {
@@ -454,12 +519,13 @@ struct dg_mesh {
   void release() {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
-                    d_cost, d_smns, d_counters, d_chunks, d_chunks_static, d_chunk_list, d_stage,
+                    d_cost, d_smns, d_counters, d_chunks_static, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
       if (p) cudaFree(p);
+    free_groups();
     for (auto& pl : ev_pool)
       for (auto e : pl) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -597,7 +663,14 @@ dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t 
   cudaMemset(m->d_counters, 0, 2 * sizeof(unsigned));
   cudaMemset(m->d_cost, 0, 2 * dgk::kMaxTabs * sizeof(unsigned long long));
   cudaMemset(m->d_smns, 0, (size_t)m->num_sms * sizeof(unsigned long long));
-  if ((e = m->build_chunks(m->static_weights().data())) != cudaSuccess) return fail_cuda(e, "chunk table");
+  {
+    const std::vector<double> w0 = m->static_weights();
+    for (int t = 0; t < dgk::kMaxTabs; ++t) {
+      m->weight[t] = w0[t];
+      m->tab_wpb[t] = m->wpb;
+    }
+  }
+  if ((e = m->build_groups()) != cudaSuccess) return fail_cuda(e, "chunk table");
   if ((e = m->build_static_chunks()) != cudaSuccess) return fail_cuda(e, "chunk table");
   if ((e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking)) != cudaSuccess) return fail_cuda(e, "stream");
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail_cuda(e, "synchronise");
@@ -947,6 +1020,7 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
     mesh->Pr = Pr;
   }
   mesh->ns = physics == DG_NAVIER_STOKES;
+  DG_CUDA(mesh->build_groups());
   if (mesh->gexec) {
     cudaGraphExecDestroy(mesh->gexec);
     mesh->gexec = nullptr;
@@ -1035,14 +1109,12 @@ dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (warps < 1 || warps > 4) return fail(DG_ERR_ARG, "warps per element must be 1..4");
   mesh->wpb = warps;
-  DG_CUDA(dgk::element_kernel_attributes(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm));
-  if (mesh->blocks_per_sm < 1) mesh->blocks_per_sm = 1;
+  for (int t = 0; t < dgk::kMaxTabs; ++t) mesh->tab_wpb[t] = warps;
   if (mesh->ns) {
     DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns));
     if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;
   }
-  std::vector<double> w(mesh->weight, mesh->weight + dgk::kMaxTabs);
-  DG_CUDA(mesh->build_chunks(w.data()));
+  DG_CUDA(mesh->build_groups());
   DG_CUDA(mesh->build_static_chunks());
   if (mesh->gexec) {
     cudaGraphExecDestroy(mesh->gexec);
@@ -1066,42 +1138,82 @@ std::string autotune_key(const dg_mesh* m) {
   return k;
 }
 
-int autotune_lookup(const char* path, const std::string& key) {
+// Cache line: "<key> <uniform warps> <warps of table 0>,<table 1>,...".
+bool autotune_lookup(const char* path, const std::string& key, int* uniform, std::vector<int>* per_table) {
   FILE* f = path ? std::fopen(path, "r") : nullptr;
-  if (!f) return 0;
-  char line[512];
-  int found = 0;
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
   while (std::fgets(line, sizeof line, f)) {
-    char k[480];
+    char k[480], list[480];
     int w = 0;
-    if (std::sscanf(line, "%479s %d", k, &w) == 2 && key == k) found = w;
+    if (std::sscanf(line, "%479s %d %479s", k, &w, list) == 3 && key == k && w >= 1 && w <= 4) {
+      std::vector<int> v;
+      for (char* p = std::strtok(list, ","); p; p = std::strtok(nullptr, ",")) v.push_back(std::atoi(p));
+      *uniform = w;
+      *per_table = v;
+      found = true;
+    }
   }
   std::fclose(f);
   return found;
 }
 
-void autotune_store(const char* path, const std::string& key, int warps) {
+void autotune_store(const char* path, const std::string& key, int warps, const int* tab_wpb, int ntab) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d\n", key.c_str(), warps);
+  std::fprintf(f, "%s %d ", key.c_str(), warps);
+  for (int t = 0; t < ntab; ++t) std::fprintf(f, "%s%d", t ? "," : "", tab_wpb[t]);
+  std::fprintf(f, "\n");
   std::fclose(f);
+}
+
+// Apply per-table warps (values outside 1..4 keep the uniform choice).
+dg_status apply_table_warps(dg_mesh* mesh, int uniform, const std::vector<int>& per_table) {
+  dg_status s = dg_set_element_warps(mesh, uniform);
+  if (s != DG_OK) return s;
+  bool differs = false;
+  for (size_t t = 0; t < per_table.size() && t < (size_t)dgk::kMaxTabs; ++t)
+    if (per_table[t] >= 1 && per_table[t] <= 4 && per_table[t] != uniform) {
+      mesh->tab_wpb[t] = per_table[t];
+      differs = true;
+    }
+  if (differs) {
+    cudaError_t e = mesh->build_groups();
+    if (e != cudaSuccess) return cuda_fail(e, "launch groups");
+    if (mesh->gexec) {
+      cudaGraphExecDestroy(mesh->gexec);
+      mesh->gexec = nullptr;
+    }
+  }
+  return DG_OK;
 }
 
 }  // namespace
 
+// Tile shape per (type, N) table.  For every uniform choice of warps per
+// element (1..4) a few steps are timed, and the in-kernel cost probe gives
+// each table's time per element at that shape; a table's throughput is its
+// resident blocks per SM over that time.  The uniform shape with the fastest
+// step is kept unless the per-table best shapes (balanced scheduler only,
+// one persistent launch per (N, warps) group) make the step faster still.
 dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best_warps, double* ms_per_step,
                       cudaStream_t stream) {
   if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
   const char* cache = std::getenv("DG_AUTOTUNE_CACHE");
   const std::string key = autotune_key(mesh);
-  int cached = autotune_lookup(cache, key);
-  if (cached >= 1 && cached <= 4) {
-    dg_status s = dg_set_element_warps(mesh, cached);
-    if (s != DG_OK) return s;
-    if (best_warps) *best_warps = cached;
-    if (ms_per_step) for (int g = 0; g < 4; ++g) ms_per_step[g] = 0.0;
-    return DG_OK;
+  const int ntab = (int)mesh->h.tables.tabs.size();
+  {
+    int cached = 0;
+    std::vector<int> per;
+    if (autotune_lookup(cache, key, &cached, &per)) {
+      dg_status s = apply_table_warps(mesh, cached, per);
+      if (s != DG_OK) return s;
+      if (best_warps) *best_warps = cached;
+      if (ms_per_step) for (int g = 0; g < 5; ++g) ms_per_step[g] = 0.0;
+      return DG_OK;
+    }
   }
   double *Qs = nullptr, *Ks = nullptr;
   const size_t bytes = sizeof(double) * mesh->h.n_dof;
@@ -1113,38 +1225,104 @@ dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  double best = 1e300;
-  int bestg = mesh->wpb;
-  dg_status st = DG_OK;
-  for (int g = 1; g <= 4 && st == DG_OK; ++g) {
-    st = dg_set_element_warps(mesh, g);
-    if (st != DG_OK) break;
+  const int reps = 3;
+  auto time_steps = [&](double* per) -> dg_status {
     cudaMemcpyAsync(Qs, Q_store, bytes, cudaMemcpyDeviceToDevice, stream);
-    st = dg_rk_step(mesh, Qs, Ks, dt, 1, stream);  // captures this shape's graph
-    if (st != DG_OK) break;
-    const int reps = 3;
+    dg_status st = dg_rk_step(mesh, Qs, Ks, dt, 1, stream);  // captures this shape's graph
+    if (st != DG_OK) return st;
+    cudaMemsetAsync(mesh->d_cost, 0, 2 * dgk::kMaxTabs * sizeof(unsigned long long), stream);
     cudaEventRecord(e0, stream);
     for (int r = 0; r < reps && st == DG_OK; ++r) st = dg_rk_step(mesh, Qs, Ks, dt, 1, stream);
     cudaEventRecord(e1, stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    const double per = ms / reps;
+    *per = ms / reps;
+    return st;
+  };
+  double best = 1e300;
+  int bestg = mesh->wpb;
+  std::vector<std::vector<double>> score(5, std::vector<double>(ntab, 0.0));
+  dg_status st = DG_OK;
+  for (int g = 1; g <= 4 && st == DG_OK; ++g) {
+    st = dg_set_element_warps(mesh, g);
+    if (st != DG_OK) break;
+    double per = 0.0;
+    st = time_steps(&per);
+    if (st != DG_OK) break;
     if (ms_per_step) ms_per_step[g - 1] = per;
     if (per < best) {
       best = per;
       bestg = g;
     }
+    unsigned long long cost[2 * dgk::kMaxTabs];
+    if (cudaMemcpy(cost, mesh->d_cost, sizeof(cost), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(DG_ERR_CUDA, "cost table");
+      break;
+    }
+    for (const auto& G : mesh->groups)
+      for (int t : G.tabs)
+        if (cost[2 * t + 1] && cost[2 * t]) score[g][t] = (double)G.bpsm * (double)cost[2 * t + 1] / (double)cost[2 * t];
   }
+  std::vector<int> per_table(ntab, bestg);
+  double mixed = 0.0;
+  if (st == DG_OK && mesh->scheduler == DG_SCHED_BALANCED) {
+    bool differs = false;
+    for (int t = 0; t < ntab; ++t) {
+      int bw = bestg;
+      for (int g = 1; g <= 4; ++g)
+        if (score[g][t] > score[bw][t] * 1.02) bw = g;
+      per_table[t] = bw;
+      differs |= bw != bestg;
+    }
+    if (differs) {
+      st = apply_table_warps(mesh, bestg, per_table);
+      if (st == DG_OK) st = time_steps(&mixed);
+      if (st == DG_OK && !(mixed < best)) {
+        per_table.assign(ntab, bestg);   // keep the uniform shape
+      }
+    }
+  }
+  if (ms_per_step) ms_per_step[4] = mixed;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(Qs);
   cudaFree(Ks);
   if (st != DG_OK) return st;
-  dg_status s = dg_set_element_warps(mesh, bestg);
+  dg_status s = apply_table_warps(mesh, bestg, per_table);
   if (s != DG_OK) return s;
-  autotune_store(cache, key, bestg);
+  autotune_store(cache, key, bestg, per_table.data(), ntab);
   if (best_warps) *best_warps = bestg;
+  return DG_OK;
+}
+
+dg_status dg_tile_shapes(const dg_mesh* mesh, int max, int* n_tables, int* type, int* N, int* warps) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  int k = 0;
+  for (const auto& G : mesh->groups)
+    for (int t : G.tabs) {
+      if (k < max) {
+        if (type) type[k] = mesh->h.tables.tabs[t].type;
+        if (N) N[k] = mesh->h.tables.tabs[t].N;
+        if (warps) warps[k] = G.wpb;
+      }
+      ++k;
+    }
+  if (n_tables) *n_tables = k;
+  return DG_OK;
+}
+
+dg_status dg_set_table_warps(dg_mesh* mesh, int type, int N, int warps) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (warps < 1 || warps > 4) return fail(DG_ERR_ARG, "warps per element must be 1..4");
+  const int t = mesh->h.tables.find(type, N);
+  if (t < 0) return fail(DG_ERR_ARG, "no such (type, N) table in the mesh");
+  mesh->tab_wpb[t] = warps;
+  DG_CUDA(mesh->build_groups());
+  if (mesh->gexec) {
+    cudaGraphExecDestroy(mesh->gexec);
+    mesh->gexec = nullptr;
+  }
   return DG_OK;
 }
 

@@ -157,3 +157,29 @@ def test_batch_rejects_mixed_flux(dg, parts):
     descs = (dg.MeshDesc * 2)(d0, d1)
     h = ctypes.c_void_p()
     assert dg.load().dg_batch_create(descs, 2, None, ctypes.byref(h)) == -1
+
+
+def test_batch_per_table_tile_shapes(dg, parts):
+    """Per-(type, N) tile shapes: tables sharing (N, warps) form one launch
+    group each; results are bitwise independent of the shapes, and the
+    autotuner's choice (per table or uniform) keeps them."""
+    b = make_batch(dg, parts)
+    Q = np.concatenate([p[3] for p in parts])
+    Qs = b.set_state(torch.from_numpy(Q).cuda())
+    R0 = b.get_state(b.rhs(Qs))
+    shapes = b.tile_shapes()
+    assert sorted((t, N) for t, N, _ in shapes) == sorted({(int(t), p[1]) for p in parts for t in set(p[0].etype)})
+    for t, N, _ in shapes:
+        b.set_table_warps(t, N, 1 if N <= 2 else (2 if N <= 4 else 4))
+    assert {(t, N): w for t, N, w in b.tile_shapes()}[(shapes[0][0], shapes[0][1])] in (1, 2, 4)
+    np.testing.assert_array_equal(b.get_state(b.rhs(Qs)), R0)
+    Q2a = Qs.clone()
+    b.rk_step(Q2a, b.empty(), 1e-4, 1)
+    warps, ms = b.autotune(Qs, 1e-4)
+    assert 1 <= warps <= 4 and len(ms) == 5
+    np.testing.assert_array_equal(b.get_state(b.rhs(Qs)), R0)
+    Q2b = Qs.clone()
+    b.rk_step(Q2b, b.empty(), 1e-4, 1)
+    assert torch.equal(Q2a, Q2b)
+    with pytest.raises(dg.DGError):
+        b.set_table_warps(3, 6, 2)                  # no tet at N = 6 in this batch
