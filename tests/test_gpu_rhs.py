@@ -229,3 +229,23 @@ def test_full_size_sampled_parity(dg):
     Q3 = naive.set_state(Q)
     naive.rk_step(Q3, naive.empty(), 1e-3, 1)
     assert np.array_equal(naive.get_state(Q3), Qafter)
+
+
+@pytest.mark.parametrize("physics", ["euler", "navier_stokes"])
+def test_nonfinite_state_is_reported(dg, physics):
+    """A NaN in the state propagates into the LSERK update; the kernel flags it
+    and dg_sync reports DG_ERR_NONFINITE once (the flag is then cleared)."""
+    box, o, mesh = setup(dg, "mixed", 2, 2, "lf", None)
+    if physics == "navier_stokes":
+        mesh.set_physics("navier_stokes", 0.05, 0.72)
+    Q = state(o)
+    Q[7] = float("nan")
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    mesh.rk_step(Qs, mesh.empty(), 1e-3, 1)
+    with pytest.raises(dg.DGError) as ei:
+        mesh.sync()
+    assert ei.value.status == -6
+    mesh.sync()
+    Qs = mesh.set_state(torch.from_numpy(state(o)).cuda())
+    mesh.rk_step(Qs, mesh.empty(), 1e-3, 1)
+    mesh.sync()
