@@ -164,6 +164,12 @@ dg_status dg_quad_points(const dg_mesh* mesh, double* xyz_out);
  * Q_store.  Asynchronous. */
 dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cudaStream_t stream);
 
+/* The inverse direction: the modal expansion of Q_store evaluated at the
+ * volume quadrature points, U = V Q (the first step of Eq. 1's residual and
+ * of Algorithm 1's nodal form), written to u_points (device, caller order,
+ * the layout dg_project reads).  Asynchronous. */
+dg_status dg_eval_nodal(dg_mesh* mesh, const double* Q_store, double* u_points, cudaStream_t stream);
+
 /* R = M^{-1}(vol - surf) of Eq. 1 for the state Q_store; R_store (device,
  * storage layout) is overwritten.  Asynchronous. */
 dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStream_t stream);

@@ -51,6 +51,7 @@ _SIGS = {
     "dg_get_state": [_P, _P, _P, ctypes.c_int, _P],
     "dg_quad_points": [_P, _P],
     "dg_project": [_P, _P, _P, _P],
+    "dg_eval_nodal": [_P, _P, _P, _P],
     "dg_rhs": [_P, _P, _P, _P],
     "dg_rk_step": [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P],
     "dg_rhs_vjp": [_P, _P, _P, _P, _P],
@@ -244,6 +245,14 @@ class Mesh:
             Q_store = self.empty()
         _check(load().dg_project(self.handle, _ptr(q_points), _ptr(Q_store), _stream(stream)))
         return Q_store
+
+    def eval_nodal(self, Q_store, out=None, stream=None):
+        """dg_eval_nodal: U = V Q at the volume points, per caller element [5, n^3] (CUDA tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty(int(self.points_per_elem.sum()) * 5, dtype=torch.float64, device=Q_store.device)
+        _check(load().dg_eval_nodal(self.handle, _ptr(Q_store), _ptr(out), _stream(stream)))
+        return out
 
     # ---------------------------------------------------------------- hot path
     def rhs(self, Q_store, R_store=None, stream=None):

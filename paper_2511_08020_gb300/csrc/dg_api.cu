@@ -354,7 +354,8 @@ struct dg_mesh {
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
     dgk::Ctx c = ctx();
     timed(true, st, [&] {
-      if (scheduler == DG_SCHED_BALANCED && mode != dgk::kProject) {
+      const bool per_elem = mode == dgk::kProject || mode == dgk::kEval;   // one-shot maps: per-type launches
+      if (scheduler == DG_SCHED_BALANCED && !per_elem) {
         for (const auto& G : groups) {
           dgk::Ctx cg = c;
           cg.nQmax = G.n * G.n * G.n;
@@ -363,7 +364,7 @@ struct dg_mesh {
                               st);
           parity ^= 1;
         }
-      } else if (scheduler == DG_SCHED_STATIC && mode != dgk::kProject) {
+      } else if (scheduler == DG_SCHED_STATIC && !per_elem) {
         dgk::Sched s{nullptr, nchunks_static, d_chunks_static, d_counters + parity, d_counters + (parity ^ 1)};
         dgk::launch_element(c, mode, a, s, true, mode == dgk::kNsVolume ? grid_ns() : grid_balanced(), wpb, st);
         parity ^= 1;
@@ -758,6 +759,14 @@ dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cud
   if (!mesh || !q_points || !Q_store) return fail(DG_ERR_ARG, "null argument");
   dgk::StageArgs a{q_points, Q_store, nullptr, 0.0, 0.0, 0.0};
   mesh->element_phase(dgk::kProject, a, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_eval_nodal(dg_mesh* mesh, const double* Q_store, double* u_points, cudaStream_t stream) {
+  if (!mesh || !Q_store || !u_points) return fail(DG_ERR_ARG, "null argument");
+  dgk::StageArgs a{Q_store, u_points, nullptr, 0.0, 0.0, 0.0};
+  mesh->element_phase(dgk::kEval, a, stream);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

@@ -958,6 +958,16 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     element_forward(c, T, s, bufA, bufG, lane);
     return;
   }
+  if (MODE == kEval) {
+    const double* Q = io.Qin + qoff;
+    for (int w = lane; w < 5 * nM; w += blockDim.x) bufG[w] = Q[w];
+    __syncthreads();
+    modal_to_nodal(c, T, bufG, bufA, bufG, lane);
+    double* out = io.Qout + c.elem_voff[c.elem_of_slot[s]];
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) out[w] = bufA[w];
+    __syncthreads();
+    return;
+  }
   if (MODE == kProject) {
     const int64_t e = c.elem_of_slot[s];
     const double* vals = io.Qin + c.elem_voff[e];
@@ -1986,6 +1996,7 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   if ((e = set_mode<kBwdRk>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kBwdRkFwd>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kProject>(bmax)) != cudaSuccess) return e;
+  if ((e = set_mode<kEval>(bmax)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_vjp_kernel, 2 * fbytes)) != cudaSuccess) return e;
@@ -2007,6 +2018,7 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
     case kBwdRk: launch_mode<kBwdRk>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kBwdRkFwd: launch_mode<kBwdRkFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kProject: launch_mode<kProject>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kEval: launch_mode<kEval>(c, a, s, balanced, grid, wpb, bytes, st); break;
   }
 }
 

@@ -31,7 +31,8 @@ enum ElemMode : int {
   kProject = 4,    // Algorithm 1 projection of point values
   kGather = 5,     // copy caller layout -> storage layout
   kScatter = 6,    // copy storage layout -> caller layout
-  kNsVolume = 7    // Navier-Stokes: BR1 lifting, gradient traces, volume residual H
+  kNsVolume = 7,   // Navier-Stokes: BR1 lifting, gradient traces, volume residual H
+  kEval = 8        // modal -> nodal values at the volume points (caller element order)
 };
 
 struct Ctx {

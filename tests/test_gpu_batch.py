@@ -172,7 +172,10 @@ def test_batch_per_table_tile_shapes(dg, parts):
     for t, N, _ in shapes:
         b.set_table_warps(t, N, 1 if N <= 2 else (2 if N <= 4 else 4))
     assert {(t, N): w for t, N, w in b.tile_shapes()}[(shapes[0][0], shapes[0][1])] in (1, 2, 4)
-    np.testing.assert_array_equal(b.get_state(b.rhs(Qs)), R0)
+    R1 = b.empty().fill_(float("nan"))                  # every element written by some group
+    b.rhs(Qs, R1)
+    assert bool(torch.isfinite(R1).all())
+    np.testing.assert_array_equal(b.get_state(R1), R0)
     Q2a = Qs.clone()
     b.rk_step(Q2a, b.empty(), 1e-4, 1)
     warps, ms = b.autotune(Qs, 1e-4)

@@ -249,3 +249,42 @@ def test_nonfinite_state_is_reported(dg, physics):
     Qs = mesh.set_state(torch.from_numpy(state(o)).cuda())
     mesh.rk_step(Qs, mesh.empty(), 1e-3, 1)
     mesh.sync()
+
+
+@pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 3, 3, None), ("kuhn", 2, 4, 7), ("prism", 2, 2, 3)])
+def test_eval_nodal_parity(dg, kind, m, N, reorder):
+    """dg_eval_nodal (U = V Q at the volume points) against the oracle's own
+    basis evaluated at the library's quadrature points; and projecting the
+    values back (Algorithm 1) returns Q."""
+    from oracle.elements import eval_basis
+    box, o, mesh = setup(dg, kind, m, N, "lf", reorder)
+    Q = state(o)
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    U = mesh.eval_nodal(Qs).cpu().numpy()
+    xyz = mesh.quad_points()
+    n3 = (N + 1) ** 3
+    worst = 0.0
+    for e in range(o.mesh.n_elems):
+        ref = o.mesh.to_reference(e, xyz[e * n3:(e + 1) * n3])
+        Ue = o.mesh.block(Q, e) @ eval_basis(o.mesh.etype[e], N, ref).T
+        worst = max(worst, np.abs(U[e * 5 * n3:(e + 1) * 5 * n3] - Ue.ravel()).max() / np.abs(Ue).max())
+    assert worst < 1e-12, worst
+    Qb = mesh.get_state(mesh.project(torch.from_numpy(U).cuda()))
+    assert rel_err(Qb, Q, var_index(o.mesh.nM)) < 1e-12
+
+
+@pytest.mark.parametrize("scheduler", ["balanced", "static", "naive"])
+def test_every_element_written(dg, scheduler):
+    """Outputs prefilled with NaN: after dg_rhs every entry is finite (each
+    element is processed exactly once by each scheduler) and equal to the
+    naive scheduler's result."""
+    box, o, mesh = setup(dg, "mixed", 4, 3, "lf", 5, scheduler=scheduler)
+    Q = state(o)
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    R = mesh.empty().fill_(float("nan"))
+    mesh.rhs(Qs, R)
+    assert bool(torch.isfinite(R).all())
+    ref = dg.Mesh(box, 3, scheduler="naive")
+    Rn = ref.empty().fill_(float("nan"))
+    ref.rhs(ref.set_state(torch.from_numpy(Q).cuda()), Rn)
+    assert torch.equal(R, Rn)
