@@ -14,6 +14,12 @@ Mesh recipe (periodic box [-pi, pi]^3 of m^3 cubes of side 2*pi/m):
   * 'kuhn'   - every cube split into the 6 Kuhn tetrahedra that share the
                v000-v111 diagonal (same orientation in every cube, so the mesh
                is conforming across cubes and across the periodic boundary).
+  * 'four'   - all four types in one conforming mesh: the x-slab of cubes
+               i < w (w = max(1, m // 4)) is split into Kuhn tetrahedra; the
+               two neighbouring slabs (i = w and i = m - 1) are pyramid cubes
+               whose pyramid facing the tet slab is split along the base
+               diagonal the Kuhn split puts on that cube face (two tets); the
+               remaining cubes follow the 'mixed' recipe (needs m >= 4).
   * 'hex', 'prism', 'pyramid' - all cubes of one kind (test meshes).
 The hash is splitmix64(seed ^ id) compared with p * 2^64 (a decision is taken
 when the hash is below the threshold).  Column ids are i + m*j; cube ids are
@@ -100,7 +106,23 @@ def box_mesh(m: int, kind: str = "mixed", seed: int = 1, p_prism: float = 0.5,
                     for dy in (0, 1):
                         for dx in (0, 1):
                             v[(dx, dy, dz)] = vid(i + dx, j + dy, k + dz)
-                if kind == "mixed":
+                split_face = None   # (axis, side) of a pyramid cube's face split into two tets
+                if kind == "four":
+                    if m < 4:
+                        raise ValueError("'four' meshes need m >= 4")
+                    w = max(1, m // 4)
+                    if i < w:
+                        sub = "kuhn"
+                    elif i == w:
+                        sub, split_face = "pyramid", (0, 0)
+                    elif i == m - 1:
+                        sub, split_face = "pyramid", (0, 1)
+                    elif _decide(seed, i + m * j, p_prism):
+                        sub = "prism"
+                    else:
+                        cube_id = i + m * (j + m * k) + (1 << 32)
+                        sub = "pyramid" if _decide(seed, cube_id, p_pyr) else "hex"
+                elif kind == "mixed":
                     is_prism_col = _decide(seed, i + m * j, p_prism)
                     if is_prism_col:
                         sub = "prism"
@@ -134,8 +156,15 @@ def box_mesh(m: int, kind: str = "mixed", seed: int = 1, p_prism: float = 0.5,
                                     d = [0, 0, 0]
                                     d[axis], d[u], d[w] = side, bu, bw
                                     base.append(v[tuple(d)])
-                            types.append(PYR)
-                            conn.append(base + [c_id])
+                            if split_face == (axis, side):
+                                # the Kuhn split of the neighbouring cube puts the
+                                # diagonal base[0]-base[3] on this face
+                                for tri in ((0, 1, 3), (0, 2, 3)):
+                                    types.append(TET)
+                                    conn.append([base[t] for t in tri] + [c_id])
+                            else:
+                                types.append(PYR)
+                                conn.append(base + [c_id])
                 elif sub == "kuhn":
                     for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
                         d = [0, 0, 0]

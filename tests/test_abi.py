@@ -36,7 +36,8 @@ def test_library_exports_every_declared_symbol(dg):
 
 @pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 4, 3, False), ("kuhn", 2, 3, True),
                                               ("mixed", 3, 2, True), ("hex", 2, 5, True),
-                                              ("pyramid", 2, 1, False), ("prism", 3, 4, True)])
+                                              ("pyramid", 2, 1, False), ("prism", 3, 4, True),
+                                              ("four", 4, 3, True)])
 def test_host_setup_matches_oracle(dg, kind, m, N, reorder):
     from oracle.dg import Oracle
     from oracle.mesh import from_box
@@ -51,6 +52,13 @@ def test_host_setup_matches_oracle(dg, kind, m, N, reorder):
     oq = np.concatenate([o.quad_points(e) for e in range(box.n_elems)])
     assert np.abs(qp - oq).max() < 1e-13
     assert sorted(slots.tolist()) == list(range(box.n_elems))
+
+
+def test_four_type_mesh_recipe():
+    """The 'four' recipe holds all four element types in one conforming mesh."""
+    box = di.box_mesh(5, "four", seed=3)
+    counts = box.type_counts()
+    assert all(counts[t] > 0 for t in ("hex", "prism", "pyramid", "tet")), counts
 
 
 def test_hilbert_order_is_local(dg):

@@ -36,7 +36,8 @@ def state(o, seed=3, amp=0.05):
 
 CASES = [("mixed", 2, 3, "lf", 5), ("mixed", 2, 3, "roe", 5), ("kuhn", 2, 3, "lf", 7), ("kuhn", 2, 2, "roe", 7),
          ("hex", 2, 4, "lf", 3), ("mixed", 3, 2, "lf", None), ("prism", 2, 5, "roe", 2),
-         ("mixed", 2, 6, "lf", 4)]                                            # N = 6 = DG_MAX_N
+         ("mixed", 2, 6, "lf", 4),                                            # N = 6 = DG_MAX_N
+         ("four", 4, 2, "roe", 6)]                                            # all four types
 
 
 @pytest.mark.parametrize("kind,m,N,flux,reorder", CASES)

@@ -42,7 +42,8 @@ def state(o, seed=3, amp=0.05):
 CASES = [("mixed", 3, 3, "lf", None, MU), ("kuhn", 2, 3, "roe", 7, MU), ("mixed", 2, 4, "lf", 5, MU),
          ("hex", 2, 2, "roe", 3, MU), ("pyramid", 2, 3, "lf", None, MU), ("prism", 2, 5, "lf", 3, MU),
          ("kuhn", 2, 2, "lf", 11, MU), ("mixed", 3, 1, "roe", 2, MU), ("mixed", 3, 4, "lf", None, 1.0 / 1600),
-         ("mixed", 2, 6, "lf", 4, MU)]                                        # N = 6 = DG_MAX_N
+         ("mixed", 2, 6, "lf", 4, MU),                                        # N = 6 = DG_MAX_N
+         ("four", 4, 2, "roe", 3, MU)]                                        # all four types
 
 
 @pytest.mark.parametrize("kind,m,N,flux,reorder,mu", CASES)
@@ -140,7 +141,8 @@ def test_ns_batch_equals_instances(dg):
 # ---------------------------------------------------------------- adjoint
 @pytest.mark.parametrize("kind,m,N,flux,reorder", [("mixed", 2, 2, "lf", None), ("kuhn", 2, 2, "roe", 7),
                                                     ("mixed", 2, 3, "lf", 5), ("hex", 2, 1, "roe", 3),
-                                                    ("prism", 2, 3, "lf", None), ("hex", 2, 6, "roe", 5)])
+                                                    ("prism", 2, 3, "lf", None), ("hex", 2, 6, "roe", 5),
+                                                    ("four", 4, 1, "lf", 7)])
 def test_ns_rhs_vjp_parity(dg, kind, m, N, flux, reorder):
     box, o, mesh = setup(dg, kind, m, N, flux, reorder)
     Q = state(o)

@@ -39,7 +39,8 @@ CASES = [("mixed", 4, 3, "lf", None), ("mixed", 4, 3, "roe", None), ("kuhn", 2, 
          ("kuhn", 2, 2, "roe", 7), ("mixed", 3, 2, "lf", 5), ("mixed", 2, 4, "roe", 5),
          ("hex", 2, 5, "lf", 3), ("prism", 2, 5, "roe", 3), ("pyramid", 2, 1, "lf", None),
          ("kuhn", 2, 5, "lf", 11), ("mixed", 3, 1, "roe", 2),
-         ("mixed", 2, 6, "roe", 3), ("kuhn", 2, 6, "lf", None)]      # N = 6 = DG_MAX_N
+         ("mixed", 2, 6, "roe", 3), ("kuhn", 2, 6, "lf", None),     # N = 6 = DG_MAX_N
+         ("four", 4, 3, "lf", None), ("four", 5, 2, "roe", 5)]       # all four types in one mesh
 
 
 @pytest.mark.parametrize("kind,m,N,flux,reorder", CASES)

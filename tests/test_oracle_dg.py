@@ -35,7 +35,7 @@ def const_state(o, U0):
     return o.project(lambda x: np.tile(np.asarray(U0)[:, None], (1, x.shape[0])))
 
 
-@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("kuhn", 2, 3), ("hex", 2, 4), ("mixed", 2, 4)])
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("kuhn", 2, 3), ("hex", 2, 4), ("mixed", 2, 4), ("four", 4, 2)])
 @pytest.mark.parametrize("flux", ["lf", "roe"])
 def test_free_stream(kind, m, N, flux):
     o = make(kind, m, N, flux=flux)
@@ -52,7 +52,7 @@ def test_free_stream(kind, m, N, flux):
     assert worst < 1e-13
 
 
-@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("kuhn", 2, 2), ("mixed", 2, 4)])
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("kuhn", 2, 2), ("mixed", 2, 4), ("four", 4, 2)])
 @pytest.mark.parametrize("flux", ["lf", "roe"])
 def test_conservation(kind, m, N, flux):
     o = make(kind, m, N, flux=flux)
@@ -134,7 +134,7 @@ def nodal_residual(o, Q, e):
     return (vol - surf) @ op.V
 
 
-@pytest.mark.parametrize("kind,m,N", [("mixed", 2, 3), ("kuhn", 2, 2), ("mixed", 3, 2)])
+@pytest.mark.parametrize("kind,m,N", [("mixed", 2, 3), ("kuhn", 2, 2), ("mixed", 3, 2), ("four", 4, 2)])
 def test_algorithm1_nodal_equivalence(kind, m, N):
     o = make(kind, m, N)
     Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
