@@ -383,6 +383,7 @@ def run_ours(args):
         else:
             tuned[sched] = mesh.autotune(Q0, dt)
     tuned_ms = {k: [round(x, 3) for x in v[1].tolist()] for k, v in tuned.items()}
+    shapes_main = mesh.tile_shapes()      # the balanced configuration the main leg times
 
     # main measurement: balanced scheduler, LF
     Q = Q0.clone()
@@ -519,7 +520,10 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = ws * dof * 5 * args.steps / e2e_s
 
-    gpu_launches = args.steps * (1 + 5 * 2)  # per step: forward prime + 5 x (face + element)
+    # per step: a forward prime and 5 element phases per launch group
+    # (tables sharing N and tile shape), and 5 face phases
+    n_groups = len({(N, w) for _, N, w in shapes_main})
+    gpu_launches = args.steps * (6 * n_groups + 5)
 
     if rank != 0:
         return
@@ -556,8 +560,9 @@ def run_ours(args):
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 8 * mesh.n_dof,
                 "d2h_bytes_per_step": 8 * mesh.n_dof},
-        "gpu_launches": gpu_launches,
+        "gpu_launches": gpu_launches, "launch_groups": n_groups,
         "autotune_warps_per_element": {k: v[0] for k, v in tuned.items()},
+        "tile_shapes": {f"{('hex', 'prism', 'pyramid', 'tet')[t]}/N{N}": w for t, N, w in shapes_main},
         "autotune_ms_per_step_by_warps": tuned_ms,
         "adjoint_over_forward": adj5_ms / fwd_ms,
         "adjoint": {"steps": Kadj, "forward_ms": fwd_ms, "rk_vjp_ckpt5_ms": adj5_ms, "rk_vjp_one_segment_ms": adjK_ms,
