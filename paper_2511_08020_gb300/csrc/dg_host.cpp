@@ -403,7 +403,7 @@ int Tables::add(int type, int N, std::string* err) {
         double al = x[ia], be = x[ib];
         double s = d.tri ? 0.5 * (1 + al) * (1 - be) - 1 : al;
         double tt = be;
-        double xi[3], abc[3];
+        double xi[3], abc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < 3; ++k) xi[k] = c0[k] + 0.5 * (s + 1) * (c1[k] - c0[k]) + 0.5 * (tt + 1) * (c2[k] - c0[k]);
         collapse(type, xi, abc);
         double expect[3];
@@ -693,7 +693,8 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
         for (int d = 0; d < 3; ++d) c[d] += P[d] / fk.nv;
       }
       fk.c = reduce(c, in.period);
-      std::sort(fk.v, fk.v + fk.nv);
+      for (int i = 1; i < fk.nv; ++i)      // insertion sort of the (at most 4) vertex keys
+        for (int j = i; j > 0 && fk.v[j] < fk.v[j - 1]; --j) std::swap(fk.v[j], fk.v[j - 1]);
       table[fk].push_back({e, lf});
     }
   }

@@ -7,8 +7,6 @@ namespace dgk {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
 __device__ __forceinline__ int sel3(int i, int j, int k, int w) { return w == 0 ? i : (w == 1 ? j : k); }
 
 __device__ __forceinline__ bool finite_bits(double x) {
@@ -1236,8 +1234,7 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
   const TypeTab& T = c.tabs[c.slot_tab[s]];
   const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
   const int nQm = c.nQmax;
-  double* bufD = smem;
-  double* bufB = smem + 15 * nQm;
+  double* bufD = smem;                 // smem + 15 nQm .. 20 nQm is unused
   double* bufX = smem + 20 * nQm;
   double* bufW = smem + 25 * nQm;
   double* bufL = smem + 30 * nQm;
