@@ -458,8 +458,11 @@ struct dg_mesh {
   // Forward LSERK steps from Q (in place) with the stage inputs copied to
   // `stages` (5 per step) when non-null.  Non-captured launches.
   // keep: fill the stage store (stage g = 5 step + s) for enqueue_vjp.
+  // final_update = false: the state after the last stage is not needed (a
+  // segment pass of the reverse sweep), so the last stage stops once its
+  // stage data exist.
   void enqueue_rk_stages(double* Q, double* K, double dt, int nsteps, double* stages, cudaStream_t st,
-                         bool keep = false) {
+                         bool keep = false, bool final_update = true) {
     const size_t bytes = sizeof(double) * h.n_dof;
     const size_t tbytes = sizeof(double) * (size_t)std::max<int64_t>(1, h.t_total);
     auto keep_forward = [&](int g) {
@@ -486,9 +489,20 @@ struct dg_mesh {
             ov_DW = P.DW;
           }
         }
+        bool last = step == nsteps - 1 && s == 4;
+        if (last && !final_update) {
+          // only the Navier-Stokes stage data of the volume phase are still
+          // missing (with kept stage data); nothing else is read later
+          if (ns && keep) {
+            timed(false, st, [&] { dgk::launch_faces_ns(ctx(), (int64_t)h.face_blocks.size(), h.n, 0, st); });
+            dgk::StageArgs none{nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+            element_phase(dgk::kNsVolume, none, st);
+          }
+          clear_overrides();
+          return;
+        }
         face_phase(st);
         clear_overrides();
-        bool last = step == nsteps - 1 && s == 4;
         a.a = kLsA[s];
         a.b = kLsB[s];
         if (!last) keep_forward(g + 1);
@@ -913,7 +927,7 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int steps = std::min(c, nsteps - seg * c);
     DG_CUDA(cudaMemcpyAsync(Qw, ck + (size_t)seg * n, bytes, cudaMemcpyDeviceToDevice, stream));
-    mesh->enqueue_rk_stages(Qw, Kw, dt, steps, keep ? nullptr : stages, stream, keep);
+    mesh->enqueue_rk_stages(Qw, Kw, dt, steps, keep ? nullptr : stages, stream, keep, false);
     for (int step = steps - 1; step >= 0; --step)
       for (int s = 4; s >= 0; --s) {
         const int g = 5 * step + s;
