@@ -1443,23 +1443,33 @@ __global__ void face_kernel(Ctx c) {
     else flux_roe(UL, UR, nrm, gamma, Fs);
     const TypeTab& T = c.tabs[R.owner_tab];
     double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    if (R.map >= 0) {
+      // permutation map: this thread alone read T0[p] and T1[perm[p]], so it
+      // writes both results in place at once
+      const int j = c.perms[(size_t)R.map + p];
+      double* W0 = c.T + R.toff;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+      for (int v = 0; v < 5; ++v) {
+        W0[v * n2 + p] = wS * Fs[v];
+        W0[(5 + v) * n2 + j] = -wS * Fs[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+    }
   }
   __syncthreads();
+  // interpolating maps: the neighbour's share needs every owner point first
   for (int w = threadIdx.x; w < items; w += blockDim.x) {
     int fl = w / n2, q = w - fl * n2;
     const FaceRec& R = c.faces[fb.first + fl];
+    if (R.map >= 0) continue;
     double* T0 = c.T + R.toff;
     double* T1 = T0 + 5 * n2;
     const double* F = sF + fl * 5 * n2;
 #pragma unroll
     for (int v = 0; v < 5; ++v) T0[v * n2 + q] = F[v * n2 + q];
-    if (R.map >= 0) {
-      int p = c.perms[(size_t)R.map + n2 + q];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) T1[v * n2 + q] = -F[v * n2 + p];
-    } else {
+    {
       const double* D = c.dense + (size_t)(-1 - R.map) + q;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -1548,8 +1558,21 @@ __global__ void face_ns_kernel(Ctx c) {
         Fs[v] -= 0.5 * Fvn[v];
       }
     }
+    if (R.map >= 0) {
+      // permutation map: direct writes (this thread alone read the inputs at
+      // p and perm[p]; the flux kind overwrites them in place)
+      const int j = c.perms[(size_t)R.map + p];
+      double* O0 = (KIND == 0 ? c.L : c.T) + R.toff;
+      const double nb = KIND == 0 ? 1.0 : -1.0;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+      for (int v = 0; v < 5; ++v) {
+        O0[v * n2 + p] = wS * Fs[v];
+        O0[(5 + v) * n2 + j] = nb * wS * Fs[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+    }
   }
   __syncthreads();
   double* out = KIND == 0 ? c.L : c.T;
@@ -1557,16 +1580,13 @@ __global__ void face_ns_kernel(Ctx c) {
   for (int w = threadIdx.x; w < items; w += blockDim.x) {
     int fl = w / n2, q = w - fl * n2;
     const FaceRec& R = c.faces[fb.first + fl];
+    if (R.map >= 0) continue;
     double* O0 = out + R.toff;
     double* O1 = O0 + 5 * n2;
     const double* F = sF + fl * 5 * n2;
 #pragma unroll
     for (int v = 0; v < 5; ++v) O0[v * n2 + q] = F[v * n2 + q];
-    if (R.map >= 0) {
-      int p = c.perms[(size_t)R.map + n2 + q];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) O1[v * n2 + q] = nb_sign * F[v * n2 + p];
-    } else {
+    {
       const double* D = c.dense + (size_t)(-1 - R.map) + q;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -1646,27 +1666,35 @@ __global__ void face_vjp_kernel(Ctx c) {
     double UbL[5] = {0, 0, 0, 0, 0}, UbR[5] = {0, 0, 0, 0, 0};
     if (c.flux == 0) flux_lf_vjp(UL, UR, nrm, gamma, g, UbL, UbR);
     else flux_roe_vjp(UL, UR, nrm, gamma, g, UbL, UbR);
+    if (R.map >= 0) {
+      // permutation map: this thread alone read the seeds at p and perm[p]
+      const int j = c.perms[(size_t)R.map + p];
+      double* W0 = c.Tv + R.toff;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      sF[(fl * 5 + v) * n2 + p] = UbL[v];
-      sR[(fl * 5 + v) * n2 + p] = UbR[v];
+      for (int v = 0; v < 5; ++v) {
+        W0[v * n2 + p] = UbL[v];
+        W0[(5 + v) * n2 + j] = UbR[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        sF[(fl * 5 + v) * n2 + p] = UbL[v];
+        sR[(fl * 5 + v) * n2 + p] = UbR[v];
+      }
     }
   }
   __syncthreads();
   for (int w = threadIdx.x; w < items; w += blockDim.x) {
     int fl = w / n2, q = w - fl * n2;
     const FaceRec& R = c.faces[fb.first + fl];
+    if (R.map >= 0) continue;
     double* S0 = c.Tv + R.toff;
     double* S1 = S0 + 5 * n2;
     const double* Fl = sF + fl * 5 * n2;
     const double* Fr = sR + fl * 5 * n2;
 #pragma unroll
     for (int v = 0; v < 5; ++v) S0[v * n2 + q] = Fl[v * n2 + q];
-    if (R.map >= 0) {
-      int p = c.perms[(size_t)R.map + n2 + q];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) S1[v * n2 + q] = Fr[v * n2 + p];
-    } else {
+    {
       const double* D = c.dense + (size_t)(-1 - R.map) + q;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -1682,9 +1710,11 @@ __global__ void face_vjp_kernel(Ctx c) {
 // KIND 1 (flux): g = wS (seed_own - Map seed_nb) is the cotangent of the
 //   unscaled flux F* = Riemann(U-, U+) - (F_v(U-, g-) + F_v(U+, g+)).n/2;
 //   trace cotangents Tv (own side: Ubar-, neighbour: Map^T Ubar+) and
-//   gradient-trace cotangents Vtb (likewise).  The neighbour's gradient
+//   gradient-trace cotangents Vtb (likewise).  Faces with a permutation map
+//   are finished by the thread that owns the point (it alone read the inputs
+//   at p and perm[p]); on interpolating faces the neighbour's gradient
 //   cotangent at the owner's points is parked in the owner half of Vt (read
-//   only by the same thread) before the transposed map.
+//   only by the same thread) and the transposed map runs after a barrier.
 // KIND 0 (lifting values): Wbar = wS (Lbar_own + Map Lbar_nb) / 2 for both
 //   means' arguments; Tv += (dW/dU)^T Wbar (own), Map^T (neighbour).
 // At most 7 warps (n <= 7) per block; two resident blocks at the largest n
@@ -1787,19 +1817,43 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
       primitive(UR, gm1, W);
       viscous_flux_vjp(W, gr, c.mu, c.kappa, Fvb, Wb, gb);
       primitive_vjp(UR, gm1, Wb, UbR);
+      if (R.map >= 0) {
+        const int j = c.perms[(size_t)R.map + p];
+        double* B1 = B0 + 15 * n2;
 #pragma unroll
-      for (int t = 0; t < 15; ++t) V0[t * n2 + p] = gb[t];
+        for (int t = 0; t < 15; ++t) B1[t * n2 + j] = gb[t];
+      } else {
+#pragma unroll
+        for (int t = 0; t < 15; ++t) V0[t * n2 + p] = gb[t];
+      }
     }
+    if (R.map >= 0) {
+      // permutation map: this thread alone read the inputs at p and perm[p]
+      const int j = c.perms[(size_t)R.map + p];
+      double* W0 = c.Tv + R.toff;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      sF[(fl * 5 + v) * n2 + p] = UbL[v];
-      sR[(fl * 5 + v) * n2 + p] = UbR[v];
+      for (int v = 0; v < 5; ++v) {
+        if (KIND == 0) {
+          W0[v * n2 + p] += UbL[v];
+          W0[(5 + v) * n2 + j] += UbR[v];
+        } else {
+          W0[v * n2 + p] = UbL[v];
+          W0[(5 + v) * n2 + j] = UbR[v];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        sF[(fl * 5 + v) * n2 + p] = UbL[v];
+        sR[(fl * 5 + v) * n2 + p] = UbR[v];
+      }
     }
   }
   __syncthreads();
   for (int w = threadIdx.x; w < items; w += blockDim.x) {
     int fl = w / n2, q = w - fl * n2;
     const FaceRec& R = c.faces[fb.first + fl];
+    if (R.map >= 0) continue;
     double* S0 = c.Tv + R.toff;
     double* S1 = S0 + 5 * n2;
     const double* Fl = sF + fl * 5 * n2;
@@ -1809,15 +1863,7 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
     for (int v = 0; v < 5; ++v) S0[v * n2 + q] = keep * S0[v * n2 + q] + Fl[v * n2 + q];
     const double* P0 = c.Vt + 3 * R.toff;          // parked neighbour gradient cotangents
     double* B1 = c.Vtb + 3 * R.toff + 15 * n2;
-    if (R.map >= 0) {
-      int p = c.perms[(size_t)R.map + n2 + q];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) S1[v * n2 + q] = keep * S1[v * n2 + q] + Fr[v * n2 + p];
-      if (KIND == 1) {
-#pragma unroll
-        for (int t = 0; t < 15; ++t) B1[t * n2 + q] = P0[t * n2 + p];
-      }
-    } else {
+    {
       const double* D = c.dense + (size_t)(-1 - R.map) + q;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
