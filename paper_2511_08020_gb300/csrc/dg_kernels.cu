@@ -938,7 +938,8 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
   __syncthreads();
 }
 
-// One element at slot s.  smem per warp: bufA [5 nQmax], bufG [15 nQmax].
+// One element at slot s.  smem per block: bufA [5 nQmax], bufG [15 nQmax]
+// (40 nQmax for the Navier-Stokes volume phase).
 template <int MODE>
 __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& io, int64_t s, double* bufA,
                                                 double* bufG, int lane) {

@@ -13,8 +13,11 @@
 //            transposed passes, times the diagonal M_ref^{-1} and 1/J, and the
 //            fused LSERK update K <- a K + dt R, Q <- Q + b K.
 // The backward phase of stage s is fused with the forward phase of stage s+1.
-// One warp owns one element at a time; all work inside an element is spread
-// over (variable, output) pairs so the 32 lanes stay busy for every N.
+// One thread block (1 to 4 warps, the tile shape chosen per (type, N)) owns
+// one element at a time; all work inside an element is spread over
+// (variable, output) pairs so the lanes stay busy for every N.  The
+// Navier-Stokes path adds a lifting face phase and a volume phase per stage
+// (BR1), and every phase has a hand-written adjoint.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
