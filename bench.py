@@ -681,10 +681,19 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
         e2.record(stream)
         torch.cuda.synchronize()
         fwdc_ms, adjc_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        # automatic segment length (as long as half the free memory allows)
+        mesh.rk_vjp(Q0, dt, Ka, 0, seed)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mesh.rk_vjp(Q0, dt, Ka, 0, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        auto_ms = e0.elapsed_time(e1)
         out["adjoint"] = {"steps": Ka, "ckpt_every": 5, "forward_ms": fwd_ms, "rk_vjp_ms": adj_ms,
                           "adjoint_over_forward": adj_ms / fwd_ms, "forward_checkpointed_ms": fwdc_ms,
                           "rk_vjp_checkpointed_ms": adjc_ms,
-                          "backward_given_forward_checkpoints_over_forward": adjc_ms / fwdc_ms}
+                          "backward_given_forward_checkpoints_over_forward": adjc_ms / fwdc_ms,
+                          "rk_vjp_auto_segment_ms": auto_ms, "auto_segment_over_forward": auto_ms / fwd_ms}
     mesh.sync()
     mesh.close()
     return out

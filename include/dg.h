@@ -209,7 +209,10 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 
 /* Q0bar = (dQ_K/dQ_0)^T QKbar for nsteps LSERK steps of size dt from Q0_store.
  * Stage states are recomputed from checkpoints of Q stored every ckpt_every
- * steps in library memory.  No counterpart in the paper.  Asynchronous. */
+ * steps in library memory; ckpt_every = 0 picks the longest segment whose
+ * kept stage data fit in half of the free device memory (fewest forward
+ * passes; see dg_set_adjoint_storage).  The result does not depend on the
+ * segment length.  No counterpart in the paper.  Asynchronous. */
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream);
 

@@ -916,13 +916,14 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
                          cudaStream_t stream) {
   const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
   const int nseg = (nsteps + c - 1) / c;
-  DG_CUDA(mesh->ensure_adjoint((size_t)(2 + 5 * c) * n));
+  // forward data of one segment's stages kept for the reverse pass when the
+  // device has room (else each reverse stage recomputes them from copies of
+  // the stage states)
+  const bool keep = mesh->keep_stages && mesh->ensure_stage_store(5 * c);
+  DG_CUDA(mesh->ensure_adjoint((size_t)(keep ? 2 : 2 + 5 * c) * n));
   double* Qw = mesh->d_ckpt;
   double* Kw = Qw + n;
   double* stages = Kw + n;
-  // forward data of one segment's stages kept for the reverse pass when the
-  // device has room (else each reverse stage recomputes them)
-  const bool keep = mesh->keep_stages && mesh->ensure_stage_store(5 * c);
   DG_CUDA(cudaMemsetAsync(mesh->d_Kbar, 0, bytes, stream));
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int steps = std::min(c, nsteps - seg * c);
@@ -943,9 +944,22 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
 dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
                       double dt) {
   if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
-  if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+  if (nsteps < 0 || ckpt_every < 0) return fail(DG_ERR_ARG, "nsteps and ckpt_every must be >= 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   return DG_OK;
+}
+
+// ckpt_every == 0: the longest segment whose kept stage data (5 stages per
+// step) fit in half of the device memory that is free now, at least 1 step.
+int auto_ckpt(const dg_mesh* mesh, int nsteps) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const double per_step = 5.0 * sizeof(double) * (double)mesh->stage_doubles();
+  const double fit = 0.5 * (double)free_b / per_step;
+  return (int)std::max(1.0, std::min((double)nsteps, std::floor(fit)));
 }
 }  // namespace
 
@@ -964,7 +978,7 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
   if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
   if (nsteps == 0) return DG_OK;
-  const int c = std::min(ckpt_every, nsteps);
+  const int c = ckpt_every == 0 ? auto_ckpt(mesh, nsteps) : std::min(ckpt_every, nsteps);
   const int nseg = (nsteps + c - 1) / c;
   if (!mesh->d_ckpt_q || mesh->ckpt_q_doubles < (size_t)(nseg + 2) * n) {
     if (mesh->d_ckpt_q) cudaFree(mesh->d_ckpt_q);
@@ -989,6 +1003,7 @@ dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double
                                  const double* QKbar, double* Q0bar, cudaStream_t stream) {
   dg_status st = rk_vjp_args(mesh, ckpt_store, QKbar, Q0bar, nsteps, ckpt_every, dt);
   if (st != DG_OK) return st;
+  if (ckpt_every < 1) return fail(DG_ERR_ARG, "ckpt_every must be >= 1 (the checkpoints' spacing)");
   const size_t bytes = sizeof(double) * (size_t)mesh->h.n_dof;
   if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
   if (nsteps == 0) return DG_OK;
