@@ -550,6 +550,10 @@ def run_ours(args):
     n_groups = len({(N, w) for _, N, w in shapes_main})
     gpu_launches = args.steps * (6 * n_groups + 5)
 
+    # the batch and Navier-Stokes legs time every rank's replica (barriers and
+    # the max over ranks inside), so every rank runs them
+    batch = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.batch_steps > 0 else None
+    nsl = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.ns_steps > 0 else None
     if rank != 0:
         return
     line = {
@@ -598,10 +602,10 @@ def run_ours(args):
                     "ratio_backward_given_forward_checkpoints": adjc_ms / fwdc_ms,
                     "rhs_ms": rhs_ms, "rhs_vjp_ms": vjp_ms, "rhs_vjp_over_rhs": vjp_ms / rhs_ms},
     }
-    if args.batch_steps > 0:
-        line["batch"] = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
-    if args.ns_steps > 0:
-        line["navier_stokes"] = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
+    if batch is not None:
+        line["batch"] = batch
+    if nsl is not None:
+        line["navier_stokes"] = nsl
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
     print(json.dumps(line), flush=True)
