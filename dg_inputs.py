@@ -21,6 +21,7 @@ Mesh recipe (periodic box [-pi, pi]^3 of m^3 cubes of side 2*pi/m):
                diagonal the Kuhn split puts on that cube face (two tets); the
                remaining cubes follow the 'mixed' recipe (needs m >= 4).
   * 'hex', 'prism', 'pyramid' - all cubes of one kind (test meshes).
+perturb_vertices() moves the vertices of any of these (curved geometry).
 The hash is splitmix64(seed ^ id) compared with p * 2^64 (a decision is taken
 when the hash is below the threshold).  Column ids are i + m*j; cube ids are
 i + m*(j + m*k) + 2^32 so the two hash streams never share an input.
@@ -247,6 +248,45 @@ def reorder_vertices(box: BoxMesh, seed: int) -> BoxMesh:
         verts[lo:hi] = box.elem_verts[lo:hi][m]
     return BoxMesh(xyz=box.xyz, etype=box.etype, elem_vert_off=box.elem_vert_off, elem_verts=verts,
                    period=box.period, m=box.m, kind=box.kind + "+reordered", seed=box.seed)
+
+
+def perturb_vertices(box: BoxMesh, amp: float, seed: int = 11, smooth: bool = False) -> BoxMesh:
+    """Curved-geometry variant of a box mesh: every vertex is moved, so hex,
+    prism and pyramid elements are no longer affine images of their reference
+    elements (tetrahedra stay affine).  Periodic images of a lattice vertex
+    move together, so the mesh stays conforming and periodic.
+
+      smooth = False: lattice vertex (i, j, k) moves by amp * h * (u0, u1, u2),
+        u_d uniform on [-1, 1) from splitmix64(seed ^ (3 v + d)) with
+        v = (i mod m) + m ((j mod m) + m (k mod m)); a cube centre (pyramid
+        apex) by the same rule with v = m^3 + cube id.
+      smooth = True: every vertex x moves by amp * (sin y sin z, sin z sin x,
+        sin x sin y) (a fixed smooth periodic deformation of the box, so the
+        elements become affine as the mesh is refined)."""
+    m = box.m
+    h = float(box.period[0]) / m
+    n1 = m + 1
+    xyz = box.xyz.copy()
+    n_grid = n1 ** 3
+    if smooth:
+        X = box.xyz
+        d = np.stack([np.sin(X[:, 1]) * np.sin(X[:, 2]), np.sin(X[:, 2]) * np.sin(X[:, 0]),
+                      np.sin(X[:, 0]) * np.sin(X[:, 1])], axis=1)
+        xyz = X + amp * d
+    else:
+        origin = float(box.xyz[0, 0])
+        for v in range(box.xyz.shape[0]):
+            if v < n_grid:
+                i, j, k = v % n1, (v // n1) % n1, v // (n1 * n1)
+                key = (i % m) + m * ((j % m) + m * (k % m))
+            else:
+                c = np.rint((box.xyz[v] - origin) / h - 0.5).astype(np.int64)
+                key = m ** 3 + int(c[0] + m * (c[1] + m * c[2]))
+            for dd in range(3):
+                u = splitmix64((seed ^ (3 * key + dd)) & MASK64) / 2.0 ** 64
+                xyz[v, dd] += amp * h * (2.0 * u - 1.0)
+    return BoxMesh(xyz=xyz, etype=box.etype, elem_vert_off=box.elem_vert_off, elem_verts=box.elem_verts,
+                   period=box.period, m=box.m, kind=box.kind + ("+smooth" if smooth else "+jitter"), seed=box.seed)
 
 
 # --------------------------------------------------------------------------

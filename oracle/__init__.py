@@ -13,7 +13,8 @@ is the seeded input generator (dg_inputs), which holds none of the method's
 arithmetic.
 
 Parity status per function (see each module's header):
-  basis / quadrature / mesh / rhs / lserk / adjoint: pinned by the tests in
+  basis / quadrature / mesh / rhs / lserk / adjoint / curved elements
+  (oracle.curved): pinned by the tests in
   tests/test_oracle_*.py (closed forms, invariants, brute force).  The choice
   of modal space, quadrature and flux where the paper is silent is a reading,
   listed in the design notes; those readings are pinned for internal

@@ -1,0 +1,233 @@
+"""Curved (non-affine) elements for the oracle: pointwise J in Eq. 1 and in
+the projection of Algorithm 1.
+
+Sec. 2 writes the weak form on elements mapped by x = chi(xi) with a
+pointwise Jacobian J and contravariant metric terms, and notes with
+Algorithm 1 that the projection M^{-1} V^T W J cannot be formed once per
+element type when J varies.  The affine oracle (oracle.mesh, oracle.dg) covers
+the case J = const per element; this module drops that restriction.
+
+Element maps (a reading: the paper names no geometry representation beyond
+x = chi(xi)).  Each element is the vertex interpolant of its reference element,
+x = sum_v N_v(xi) X_v, with
+  hex      N_v = prod_d (1 + r_vd xi_d) / 2            (trilinear; r_v = reference vertex)
+  prism    N_i = l_i(xi, eta) (1 - zeta)/2,  N_{i+3} = l_i(xi, eta) (1 + zeta)/2,
+           l_0 = -(xi + eta)/2, l_1 = (1 + xi)/2, l_2 = (1 + eta)/2
+  pyramid  N_v = (1 + r_v0 a)/2 (1 + r_v1 b)/2 (1 - c)/2 for the base, N_4 = (1 + c)/2,
+           in the collapsed coordinates (a, b, c) of the pyramid
+  tet      barycentric (affine)
+so quadrilateral faces are bilinear and triangular faces planar, and two
+elements that share a face's vertices share the face exactly.  d x / d xi is
+taken by complex-step differentiation of the map (exact to rounding).
+
+Per volume point q of element e: J_q = |det dx/dxi| and dxi/dx = (dx/dxi)^{-1};
+the volume term is sum_q w_q J_q sum_d (d phi_i / d x_d)(xi_q) F_d(U_q), the
+mass matrix M_e = V^T diag(w_q J_q) V (dense for every type), and the
+projection Q = M_e^{-1} V^T W J q (Algorithm 1, J pointwise).
+
+Faces: the owner's face points as in the affine case; at each point the area
+vector is w_p |t_s x t_t| |det F| F^{-T} N (Nanson's formula with the
+reference outward unit normal N and reference tangents t_s, t_t of the face
+parametrisation, F = dx/dxi at the point); (w S)_p is its length and the
+normal its direction.  The neighbour's reference coordinates of each owner
+face point are found by Newton's method on the neighbour's map.
+
+Parity: pinned by reduction to the affine oracle on affine meshes, the
+divergence theorem on every element, the total volume of the box, free-stream
+preservation, conservation, reproduction of the element maps by the
+projection, and convergence of order about N+1 under a smooth deformation
+(tests/test_oracle_curved.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import cho_factor, cho_solve
+
+from .dg import Oracle
+from .elements import FACES, HEX, PRISM, PYR, REF_VERTS, TET, eval_basis, n_modes
+from .euler import physical_flux
+from .mesh import OracleMesh
+from .quadrature import face_rule
+
+H_CS = 1e-30
+
+
+def shape_functions(etype, pts):
+    """N_v at reference points pts [P, 3] (real or complex): [P, nv]."""
+    xi, eta, zeta = pts[:, 0], pts[:, 1], pts[:, 2]
+    R = REF_VERTS[etype]
+    if etype == HEX:
+        return np.stack([(1 + R[v, 0] * xi) * (1 + R[v, 1] * eta) * (1 + R[v, 2] * zeta) / 8
+                         for v in range(8)], axis=1)
+    if etype == PRISM:
+        lam = [-(xi + eta) / 2, (1 + xi) / 2, (1 + eta) / 2]
+        return np.stack([lam[i] * (1 - zeta) / 2 for i in range(3)] +
+                        [lam[i] * (1 + zeta) / 2 for i in range(3)], axis=1)
+    if etype == TET:
+        return np.stack([-(1 + xi + eta + zeta) / 2, (1 + xi) / 2, (1 + eta) / 2, (1 + zeta) / 2], axis=1)
+    if etype == PYR:
+        a = 2 * (1 + xi) / (1 - zeta) - 1
+        b = 2 * (1 + eta) / (1 - zeta) - 1
+        base = [(1 + R[v, 0] * a) / 2 * (1 + R[v, 1] * b) / 2 * (1 - zeta) / 2 for v in range(4)]
+        return np.stack(base + [(1 + zeta) / 2], axis=1)
+    raise ValueError(etype)
+
+
+class CurvedOracleMesh(OracleMesh):
+    """OracleMesh without the affine restriction (element maps as above)."""
+
+    def __init__(self, xyz, etype, elem_vert_off, elem_verts, period, N):
+        self.xyz = np.asarray(xyz, dtype=float)
+        self.etype = np.asarray(etype, dtype=np.int64)
+        self.N = int(N)
+        self.period = None if period is None else np.asarray(period, dtype=float)
+        off = np.asarray(elem_vert_off)
+        ev = np.asarray(elem_verts)
+        E = self.etype.size
+        self.n_elems = E
+        self.verts = [ev[off[e]:off[e + 1]] for e in range(E)]
+        for e in range(E):
+            if self.verts[e].size != REF_VERTS[self.etype[e]].shape[0]:
+                raise ValueError(f"element {e}: wrong vertex count")
+        self.nM = np.array([n_modes(t, N) for t in self.etype])
+        self.dof_off = np.zeros(E + 1, dtype=np.int64)
+        self.dof_off[1:] = np.cumsum(5 * self.nM)
+        self.centroid = np.array([self.xyz[v].mean(0) for v in self.verts])
+        self._match_faces()
+
+    # ------------------------------------------------------------ maps
+    def _rel(self, e):
+        """Vertex positions relative to the element's first vertex."""
+        X = self.xyz[self.verts[e]]
+        return X - X[0]
+
+    def to_physical_rel(self, e, ref):
+        """chi_e(ref) - X_{v0}: [P, 3] (real or complex ref)."""
+        ref = np.atleast_2d(ref)
+        return shape_functions(self.etype[e], ref) @ self._rel(e)
+
+    def to_physical(self, e, ref):
+        return self.xyz[self.verts[e][0]] + self.to_physical_rel(e, ref)
+
+    def jacobian(self, e, ref):
+        """F = dx/dxi at reference points: [P, 3(x_d), 3(xi_k)]."""
+        ref = np.atleast_2d(np.asarray(ref, dtype=float))
+        cols = []
+        for k in range(3):
+            d = np.zeros(3, dtype=complex)
+            d[k] = 1j * H_CS
+            cols.append(self.to_physical_rel(e, ref + d).imag / H_CS)
+        return np.stack(cols, axis=2)
+
+    def volume_geometry(self, e, pts):
+        """J_q = |det F| and dxi/dx = F^{-1} at the volume points."""
+        F = self.jacobian(e, pts)
+        det = np.linalg.det(F)
+        if not (np.all(det > 0) or np.all(det < 0)):
+            raise ValueError(f"element {e} is inverted or degenerate at a quadrature point")
+        return np.abs(det), np.linalg.inv(F)
+
+    def to_reference(self, e, x_rel, guess):
+        """Newton's method for chi_e(xi) - X_{v0} = x_rel, per row."""
+        xi = np.array(guess, dtype=float)
+        for _ in range(60):
+            r = self.to_physical_rel(e, xi) - x_rel
+            F = self.jacobian(e, xi)
+            step = np.linalg.solve(F, r[..., None])[..., 0]
+            xi = xi - step
+            if np.abs(step).max() < 1e-15:
+                break
+        return xi
+
+    def face_geometry(self, f):
+        """Owner reference points, neighbour reference points of the same
+        physical points, (w S)_p and outward unit normals [3, P]."""
+        e0, l0, e1, l1 = self.faces[f]
+        t0 = self.etype[e0]
+        ref0, w, ts, tt = face_rule(t0, l0, self.N)
+        # reference outward unit normal of the face
+        nr = np.cross(ts, tt)
+        nr = nr / np.linalg.norm(nr)
+        cen = REF_VERTS[t0][FACES[t0][l0]].mean(0) - REF_VERTS[t0].mean(0)
+        if np.dot(nr, cen) < 0:
+            nr = -nr
+        F = self.jacobian(e0, ref0)
+        det = np.abs(np.linalg.det(F))
+        area = (w * np.linalg.norm(np.cross(ts, tt)) * det)[:, None] * \
+            np.einsum("pkd,k->pd", np.linalg.inv(F), nr)        # |det F| F^{-T} N, scaled
+        wS = np.linalg.norm(area, axis=1)
+        nrm = (area / wS[:, None]).T
+        shift = np.zeros(3)
+        if self.period is not None:
+            d = self.face_centroid(e0, l0) - self.face_centroid(e1, l1)
+            shift = np.rint(d / self.period) * self.period
+        x_rel = (self.xyz[self.verts[e0][0]] - shift - self.xyz[self.verts[e1][0]]) + \
+            self.to_physical_rel(e0, ref0)
+        t1 = self.etype[e1]
+        guess = np.tile(REF_VERTS[t1][FACES[t1][l1]].mean(0), (ref0.shape[0], 1))
+        ref1 = self.to_reference(e1, x_rel, guess)
+        return ref0, ref1, wS, nrm
+
+
+def curved_from_box(box, N):
+    return CurvedOracleMesh(box.xyz, box.etype, box.elem_vert_off, box.elem_verts, box.period, N)
+
+
+class CurvedOracle(Oracle):
+    """Oracle (Eq. 1, Algorithm 1, LSERK) on a CurvedOracleMesh."""
+
+    def __init__(self, mesh, flux="lf", gamma=1.4):
+        super().__init__(mesh, flux=flux, gamma=gamma)
+        self.Jq, self.dxi_dx, self.chol = [], [], []
+        for e in range(mesh.n_elems):
+            op = self.ops[mesh.etype[e]]
+            Jq, G = mesh.volume_geometry(e, op.pts)
+            self.Jq.append(Jq)
+            self.dxi_dx.append(G)                       # [nQ, 3(xi_k), 3(x_d)]
+            Me = op.V.T @ ((op.w * Jq)[:, None] * op.V)
+            self.chol.append(cho_factor(Me))
+
+    def face_data(self, f):
+        if f not in self._face_cache:
+            m = self.mesh
+            e0, l0, e1, l1 = m.faces[f]
+            ref0, ref1, wS, nrm = m.face_geometry(f)
+            phi0 = eval_basis(m.etype[e0], m.N, ref0)
+            phi1 = eval_basis(m.etype[e1], m.N, ref1)
+            self._face_cache[f] = (phi0, phi1, wS, nrm)
+        return self._face_cache[f]
+
+    def volume_term(self, Q, e):
+        m = self.mesh
+        op = self.ops[m.etype[e]]
+        U = m.block(Q, e) @ op.V.T                       # [5, nQ]
+        F = physical_flux(U, self.gamma)                 # [3(d), 5, nQ]
+        Fc = np.einsum("qkd,dvq->kvq", self.dxi_dx[e], F)
+        return np.einsum("kqi,kvq->vi", op.G, (op.w * self.Jq[e]) * Fc)
+
+    def apply_minv(self, e, r):
+        c = self.chol[e]
+        if np.iscomplexobj(r):
+            return cho_solve(c, r.real.T).T + 1j * cho_solve(c, r.imag.T).T
+        return cho_solve(c, r.T).T
+
+    def project(self, values_at_points):
+        m = self.mesh
+        Q = np.zeros(m.n_dof())
+        for e in range(m.n_elems):
+            op = self.ops[m.etype[e]]
+            q = values_at_points(self.quad_points(e))
+            r = (q * (op.w * self.Jq[e])) @ op.V
+            Q[m.dof_off[e]:m.dof_off[e + 1]] = self.apply_minv(e, r).ravel()
+        return Q
+
+    def integrate(self, Q, e):
+        op = self.ops[self.mesh.etype[e]]
+        return (self.mesh.block(Q, e) @ op.V.T) @ (op.w * self.Jq[e])
+
+    def volume(self, e):
+        op = self.ops[self.mesh.etype[e]]
+        return float(op.w @ self.Jq[e])
+
+
+__all__ = ["CurvedOracle", "CurvedOracleMesh", "curved_from_box", "shape_functions", "HEX", "PRISM", "PYR", "TET"]
