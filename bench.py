@@ -76,6 +76,32 @@ def element_flops(t, N):
 FACE_POINT_FLOPS = {"lf": 101, "roe": 214}
 
 
+def curved_element_flops(t, N):
+    """element_flops of a curved element: the pointwise metric is read
+    instead of formed (no metric flops), a hexahedron scales its nodal
+    residual by 1/J_q (5 n^3), a prism or pyramid applies its dense inverse
+    mass matrix (2 * 5 nM^2) instead of the diagonal one; tetrahedra stay
+    affine."""
+    if t == 3:
+        return element_flops(t, N)
+    n = N + 1
+    nM = n_modes(t, N)
+    metric = (9, 15, 21, 27)[t]
+    base = element_flops(t, N) - n ** 3 * metric
+    return base + (5 * n ** 3 if t == 0 else 2 * 5 * nM * nM)
+
+
+def curved_element_bytes(t, N):
+    """element_bytes plus the curved element's pointwise geometry: metric,
+    J and 1/J per volume point, and for prism / pyramid the dense inverse
+    mass matrix."""
+    if t == 3:
+        return element_bytes(t, N)
+    n = N + 1
+    nM = n_modes(t, N)
+    return element_bytes(t, N) - 8 * 10 + 8 * (9 * n ** 3 + (n ** 3 if t == 0 else nM * nM))
+
+
 def ns_element_flops(t, N):
     """Algorithmic FP64 flops of one element for one Navier-Stokes stage:
     the fused backward + forward launch (no volume term there) and the BR1
@@ -413,6 +439,8 @@ def run_ours(args):
                 "face_ms_per_step": face_ms / steps_p, "element_tflops": elem_tflops, "only_main": True}
         if args.ns_steps > 0:
             line["navier_stokes"] = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws)
+        if args.curved_steps > 0:
+            line["curved"] = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, value)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
@@ -554,6 +582,7 @@ def run_ours(args):
     # the max over ranks inside), so every rank runs them
     batch = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.batch_steps > 0 else None
     nsl = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.ns_steps > 0 else None
+    cvl = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, value) if args.curved_steps > 0 else None
     if rank != 0:
         return
     line = {
@@ -606,6 +635,8 @@ def run_ours(args):
         line["batch"] = batch
     if nsl is not None:
         line["navier_stokes"] = nsl
+    if cvl is not None:
+        line["curved"] = cvl
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -732,6 +763,82 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
     return out
 
 
+CURVED_WORKLOAD = ("16^3-cube periodic box, mixed hex/prism/pyramid (seed 2) with every vertex moved by up to "
+                   "0.1 h per coordinate (dg_inputs.perturb_vertices, seed 11): trilinear hexahedra, prisms and "
+                   "pyramids with pointwise J and dense per-element M^-1; N=4, Euler TGV, LF, FP64")
+
+
+def curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, affine_value):
+    """Curved (non-affine) geometry: the main workload's mesh with perturbed
+    vertices, so the projection of Algorithm 1 differs per element (a dense
+    M_e^-1 for every prism and pyramid, 1/J_q for every hexahedron)."""
+    import torch
+    box = di.perturb_vertices(di.box_mesh(MESH_M, "mixed", seed=MESH_SEED), 0.1, seed=11)
+    mesh = dg.Mesh(box, N_DEG, flux=args.flux, scheduler="balanced", geometry="vertex")
+    n = N_DEG + 1
+    xyz = mesh.quad_points()
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Q0 = mesh.project(torch.from_numpy(vals).to(dev))
+    dt = 0.8 * tgv_dt(box, xyz, N_DEG)
+    dof = int(sum(n_modes(int(t), N_DEG) for t in box.etype))
+    steps = args.curved_steps
+    out = {"workload": CURVED_WORKLOAD, "elements": box.n_elems, "curved_elements": mesh.n_curved,
+           "curved_faces": mesh.n_curved_faces, "geometry_mb": mesh.geometry_doubles * 8 / 1e6,
+           "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), mesh.type_counts)), "dof_per_var": dof,
+           "steps": steps, "dt": dt, "unit": "DOF-updates/s"}
+
+    def timed(Q, K, profile=False):
+        mesh.set_profiling(profile)
+        for _ in range(args.warmup):
+            mesh.rk_step(Q, K, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el = fa = 0.0
+        e0.record(stream)
+        for _ in range(steps):
+            mesh.rk_step(Q, K, dt, 1)
+            if profile:
+                a, b_, _, _ = mesh.phase_times()
+                el += a
+                fa += b_
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        mesh.set_profiling(False)
+        return max_over_ranks(e0.elapsed_time(e1)), el, fa
+
+    res = {}
+    for sched in ("naive", "balanced"):
+        mesh.set_scheduler(sched)
+        warps, tms = mesh.autotune(Q0, dt)
+        Q = Q0.clone()
+        ms, _, _ = timed(Q, torch.empty_like(Q))
+        res[sched] = Q
+        out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps}
+    Qp = Q0.clone()
+    _, el_ms, fa_ms = timed(Qp, torch.empty_like(Qp), profile=True)
+    el_flops = sum(curved_element_flops(int(t), N_DEG) for t in box.etype)
+    el_bytes = sum(curved_element_bytes(int(t), N_DEG) for t in box.etype)
+    out["balanced_over_naive"] = out["balanced"]["value"] / out["naive"]["value"]
+    out["schedulers_bitwise_equal"] = bool(torch.equal(res["naive"], res["balanced"]))
+    out["curved_over_affine"] = out["balanced"]["value"] / affine_value
+    out["element_ms_per_step"] = el_ms / steps
+    out["face_ms_per_step"] = fa_ms / steps
+    out["element_kernel_tflops"] = el_flops * 5 * steps / (el_ms * 1e-3) / 1e12
+    out["element_kernel_gbs"] = el_bytes * 5 * steps / (el_ms * 1e-3) / 1e9
+    out["algorithmic_flops_per_stage"] = el_flops
+    out["algorithmic_bytes_per_stage"] = el_bytes
+    ns, imb = mesh.cost_table()
+    out["cost_table_ns_per_elem"] = dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns]))
+    out["sm_load_imbalance"] = imb
+    out["finite"] = bool(torch.isfinite(res["balanced"]).all())
+    mesh.sync()
+    mesh.close()
+    return out
+
+
 def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
     """Serving-style batch: all instances advance in one handle (one persistent
     element launch and one face launch per phase, one CUDA graph per step)."""
@@ -825,6 +932,8 @@ def main():
                     help="steps of the 24^3 Navier-Stokes TGV leg (0 skips it)")
     ap.add_argument("--ns-adj-steps", type=int, default=20,
                     help="steps of the Navier-Stokes adjoint timing (0 skips it)")
+    ap.add_argument("--curved-steps", type=int, default=100,
+                    help="steps of the curved-geometry leg (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -3,7 +3,8 @@
  *
  * The library evaluates the right-hand side of the modal discontinuous
  * Galerkin discretisation of the compressible Euler equations on periodic
- * affine meshes that mix hexahedra, prisms, pyramids and tetrahedra, and
+ * meshes (affine, or curved with vertex-interpolated element maps) that mix
+ * hexahedra, prisms, pyramids and tetrahedra, and
  * advances it with a low-storage Runge-Kutta scheme, as described in
  * "In-Memory Load Balancing for Discontinuous Galerkin Methods on Polytopal
  * Meshes" (Kopper, Schwarz, Keim, Beck):
@@ -62,7 +63,7 @@ typedef enum { DG_HEX = 0, DG_PRISM = 1, DG_PYR = 2, DG_TET = 3 } dg_elem_type;
 typedef enum {
   DG_OK = 0,
   DG_ERR_ARG = -1,         /* invalid argument (null pointer, size, enum)       */
-  DG_ERR_MESH = -2,        /* non-affine element, unmatched or ambiguous face   */
+  DG_ERR_MESH = -2,        /* non-affine (or inverted) element, unmatched face  */
   DG_ERR_CUDA = -3,        /* a CUDA runtime call failed (no device, launch...) */
   DG_ERR_OOM = -4,         /* device or host allocation failed                  */
   DG_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up           */
@@ -74,8 +75,31 @@ typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1 } dg_flux;
 typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1, DG_SCHED_STATIC = 2 } dg_scheduler;
 typedef enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 } dg_physics;
 
+/* Element geometry (Sec. 2: x = chi(xi) with a pointwise Jacobian J; with
+ * Algorithm 1 the projection M^{-1} V^T W J then differs per element).
+ *   DG_GEOM_AFFINE  every element must be an affine image of its reference
+ *                   element (DG_ERR_MESH otherwise).
+ *   DG_GEOM_VERTEX  elements that are not affine are curved: their map is the
+ *                   vertex interpolant of the reference element (trilinear
+ *                   hex; prism linear on the triangle times linear in zeta;
+ *                   pyramid (1 +- a)(1 +- b)(1 - c)/8 on the base vertices
+ *                   and (1 + c)/2 on the apex in its collapsed coordinates
+ *                   a, b, c; tetrahedra are always affine), so quadrilateral
+ *                   faces are bilinear.  A curved element keeps J, the
+ *                   contravariant metric and, for prisms and pyramids, the
+ *                   dense inverse mass matrix (V^T diag(w J) V)^{-1} of
+ *                   Algorithm 1 per quadrature point in device memory; a
+ *                   curved hexahedron applies M^{-1} V^T as V^T diag(1/J)
+ *                   (exact: its V is square with V^T W V = I).  Affine
+ *                   elements of such a mesh take the affine path.  Curved
+ *                   meshes support the Euler equations, dg_project,
+ *                   dg_eval_nodal, dg_rhs and dg_rk_step; the other calls
+ *                   return DG_ERR_UNSUPPORTED on them. */
+typedef enum { DG_GEOM_AFFINE = 0, DG_GEOM_VERTEX = 1 } dg_geometry;
+
 /* Mesh description, caller-owned, read only during dg_mesh_create.
- * Elements are affine images of the reference elements; the local vertex
+ * Elements are affine images of the reference elements (or curved, see
+ * dg_geometry); the local vertex
  * order of element e (elem_verts[elem_vert_off[e] .. elem_vert_off[e+1]-1])
  * follows the reference vertex order:
  *   hex     (-1,-1,-1) (1,-1,-1) (-1,1,-1) (1,1,-1) then the same at zeta=+1
@@ -98,6 +122,7 @@ typedef struct {
   double gamma;                 /* ratio of specific heats (1.4)                  */
   int scheduler;                /* dg_scheduler                                   */
   double imbalance_threshold;   /* rebalance when max/mean SM load - 1 exceeds it */
+  int geometry;                 /* dg_geometry (0 = affine elements only)         */
 } dg_mesh_desc;
 
 #define DG_MAX_N 6
@@ -124,6 +149,11 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
  * instance report its index in dg_last_error().  Synchronises `stream`;
  * free with dg_mesh_destroy. */
 dg_status dg_batch_create(const dg_mesh_desc* descs, int n_instances, cudaStream_t stream, dg_mesh** out);
+
+/* Curved-geometry summary (host-only): number of curved elements, of faces
+ * whose owner is curved (per-point normals and w S), and the doubles of
+ * pointwise geometry the mesh holds in device memory.  Pointers may be NULL. */
+dg_status dg_mesh_geometry(const dg_mesh* mesh, int64_t* n_curved_elems, int64_t* n_curved_faces, int64_t* geometry_doubles);
 
 /* Instance offsets of a handle from dg_batch_create (a plain mesh is a batch
  * of one).  instance_elem_off, instance_dof_off (host, [n_instances + 1],

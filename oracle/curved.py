@@ -173,19 +173,38 @@ def curved_from_box(box, N):
     return CurvedOracleMesh(box.xyz, box.etype, box.elem_vert_off, box.elem_verts, box.period, N)
 
 
+class _PerElement:
+    """e -> field(e), computed on first use (large meshes are checked on
+    sampled elements only)."""
+
+    def __init__(self, fill):
+        self._fill = fill
+        self._vals = {}
+
+    def __getitem__(self, e):
+        e = int(e)
+        if e not in self._vals:
+            self._fill(e)
+        return self._vals[e]
+
+
 class CurvedOracle(Oracle):
-    """Oracle (Eq. 1, Algorithm 1, LSERK) on a CurvedOracleMesh."""
+    """Oracle (Eq. 1, Algorithm 1, LSERK) on a CurvedOracleMesh.  Per
+    element: Jq [nQ], dxi_dx [nQ, 3(xi_k), 3(x_d)] and the Cholesky factor of
+    M_e = V^T diag(w J) V."""
 
     def __init__(self, mesh, flux="lf", gamma=1.4):
         super().__init__(mesh, flux=flux, gamma=gamma)
-        self.Jq, self.dxi_dx, self.chol = [], [], []
-        for e in range(mesh.n_elems):
-            op = self.ops[mesh.etype[e]]
-            Jq, G = mesh.volume_geometry(e, op.pts)
-            self.Jq.append(Jq)
-            self.dxi_dx.append(G)                       # [nQ, 3(xi_k), 3(x_d)]
-            Me = op.V.T @ ((op.w * Jq)[:, None] * op.V)
-            self.chol.append(cho_factor(Me))
+        self.Jq = _PerElement(self._element_geometry)
+        self.dxi_dx = _PerElement(self._element_geometry)
+        self.chol = _PerElement(self._element_geometry)
+
+    def _element_geometry(self, e):
+        op = self.ops[self.mesh.etype[e]]
+        Jq, G = self.mesh.volume_geometry(e, op.pts)
+        self.Jq._vals[e] = Jq
+        self.dxi_dx._vals[e] = G
+        self.chol._vals[e] = cho_factor(op.V.T @ ((op.w * Jq)[:, None] * op.V))
 
     def face_data(self, f):
         if f not in self._face_cache:

@@ -13,11 +13,13 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "probe_fp64_mixed", "FLUX", "SCHED", "PHYSICS", "load"]
+__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "probe_fp64_mixed", "FLUX", "SCHED",
+           "PHYSICS", "GEOMETRY", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
 SCHED = {"balanced": 0, "naive": 1, "static": 2}
 PHYSICS = {"euler": 0, "navier_stokes": 1}
+GEOMETRY = {"affine": 0, "vertex": 1}
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_OOM",
           -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_UNSUPPORTED"}
 
@@ -34,7 +36,7 @@ class MeshDesc(ctypes.Structure):
                 ("elem_vert_off", ctypes.c_void_p), ("elem_verts", ctypes.c_void_p),
                 ("period", ctypes.c_void_p), ("N", ctypes.c_int), ("flux", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("scheduler", ctypes.c_int),
-                ("imbalance_threshold", ctypes.c_double)]
+                ("imbalance_threshold", ctypes.c_double), ("geometry", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -44,6 +46,7 @@ _SIGS = {
     "dg_mesh_create": [ctypes.POINTER(MeshDesc), _P, ctypes.POINTER(_P)],
     "dg_batch_create": [ctypes.POINTER(MeshDesc), ctypes.c_int, _P, ctypes.POINTER(_P)],
     "dg_batch_layout": [_P, _P, _P],
+    "dg_mesh_geometry": [_P, _P, _P, _P],
     "dg_mesh_destroy": [_P],
     "dg_mesh_check": [ctypes.POINTER(MeshDesc), _P, _P, _P],
     "dg_mesh_layout": [_P, _P, _P, _P],
@@ -123,7 +126,7 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def _desc(box_or_arrays, N, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1):
+def _desc(box_or_arrays, N, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, geometry="affine"):
     import numpy as np
     b = box_or_arrays
     keep = dict(xyz=np.ascontiguousarray(b.xyz, dtype=np.float64),
@@ -134,14 +137,15 @@ def _desc(box_or_arrays, N, flux="lf", gamma=1.4, scheduler="balanced", imbalanc
     d = MeshDesc(keep["xyz"].shape[0], keep["xyz"].ctypes.data, keep["etype"].shape[0], keep["etype"].ctypes.data,
                  keep["off"].ctypes.data, keep["verts"].ctypes.data, keep["period"].ctypes.data, int(N),
                  FLUX[flux] if isinstance(flux, str) else int(flux), float(gamma),
-                 SCHED[scheduler] if isinstance(scheduler, str) else int(scheduler), float(imbalance_threshold))
+                 SCHED[scheduler] if isinstance(scheduler, str) else int(scheduler), float(imbalance_threshold),
+                 GEOMETRY[geometry] if isinstance(geometry, str) else int(geometry))
     return d, keep
 
 
-def check_mesh(box, N):
+def check_mesh(box, N, geometry="affine"):
     """dg_mesh_check: host-only set-up; returns (counts[8], quad points [E*n^3, 3], slot_of_elem)."""
     import numpy as np
-    d, keep = _desc(box, N)
+    d, keep = _desc(box, N, geometry=geometry)
     n = N + 1
     counts = np.zeros(8, dtype=np.int64)
     qp = np.zeros((len(keep["etype"]) * n ** 3, 3))
@@ -167,11 +171,15 @@ class Mesh:
     """Owns a dg_mesh handle.  State tensors are float64 CUDA tensors of n_dof
     entries in the storage layout (see dg_set_state / dg_get_state)."""
 
-    def __init__(self, box, N, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None):
+    def __init__(self, box, N, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None,
+                 geometry="affine"):
+        """geometry: "affine" (every element an affine image of its reference
+        element) or "vertex" (non-affine elements are curved, with
+        vertex-interpolated maps; see dg_geometry in include/dg.h)."""
         import numpy as np
         self.N = int(N)
         self.flux = flux
-        d, keep = _desc(box, N, flux, gamma, scheduler, imbalance_threshold)
+        d, keep = _desc(box, N, flux, gamma, scheduler, imbalance_threshold, geometry)
         h = ctypes.c_void_p()
         _check(load().dg_mesh_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
         self._adopt(h, keep["etype"].copy())
@@ -188,6 +196,9 @@ class Mesh:
         self.n_elems, self.n_faces = int(counts[0]), int(counts[1])
         self.type_counts = counts[2:].tolist()
         self.etype = etype
+        nc, nf, gd = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().dg_mesh_geometry(h, ctypes.byref(nc), ctypes.byref(nf), ctypes.byref(gd)))
+        self.n_curved, self.n_curved_faces, self.geometry_doubles = nc.value, nf.value, gd.value
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -371,7 +382,8 @@ class Batch(Mesh):
     entries dof_off[i]:dof_off[i+1] (in both the caller and the storage
     layout).  All instances share flux and gamma."""
 
-    def __init__(self, boxes, Ns, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None):
+    def __init__(self, boxes, Ns, flux="lf", gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None,
+                 geometry="affine"):
         import numpy as np
         if len(boxes) != len(Ns) or not boxes:
             raise ValueError("one N per mesh, at least one mesh")
@@ -379,7 +391,7 @@ class Batch(Mesh):
         descs = (MeshDesc * k)()
         self._keep = []
         for i, (b, N) in enumerate(zip(boxes, Ns)):
-            d, keep = _desc(b, N, flux, gamma, scheduler, imbalance_threshold)
+            d, keep = _desc(b, N, flux, gamma, scheduler, imbalance_threshold, geometry)
             descs[i] = d
             self._keep.append(keep)
         self.Ns = [int(N) for N in Ns]

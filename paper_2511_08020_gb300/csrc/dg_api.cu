@@ -119,6 +119,8 @@ struct dg_mesh {
   int64_t *d_slot_qoff = nullptr, *d_slot_hoff = nullptr, *d_slot_ftoff = nullptr;
   int64_t *d_elem_of_slot = nullptr, *d_elem_qoff = nullptr, *d_elem_voff = nullptr;
   dgk::ElemGeo* d_geo = nullptr;
+  int64_t* d_slot_coff = nullptr;
+  double *d_cpool = nullptr, *d_fgeo = nullptr;
   double* d_H = nullptr;
   double* d_T = nullptr;
   double* d_Tv = nullptr;       // adjoint face buffer
@@ -204,6 +206,9 @@ struct dg_mesh {
     c.elem_qoff = d_elem_qoff;
     c.elem_voff = d_elem_voff;
     c.geo = d_geo;
+    c.slot_coff = h.n_curved ? d_slot_coff : nullptr;
+    c.cpool = d_cpool;
+    c.fgeo = d_fgeo;
     c.ns = ns;
     c.mu = mu;
     c.kappa = ns ? mu * gamma / ((gamma - 1.0) * Pr) : 0.0;
@@ -535,7 +540,8 @@ struct dg_mesh {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks_static, d_stage,
-                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q};
+                    d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
+                    d_slot_coff, d_cpool, d_fgeo};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -564,7 +570,8 @@ dg_status check_desc(const dg_mesh_desc* desc) {
 }
 
 dgh::MeshInput input_of(const dg_mesh_desc* d) {
-  return dgh::MeshInput{d->n_vertices, d->xyz, d->n_elems, d->type, d->elem_vert_off, d->elem_verts, d->period, d->N};
+  return dgh::MeshInput{d->n_vertices, d->xyz, d->n_elems, d->type, d->elem_vert_off, d->elem_verts, d->period, d->N,
+                        d->geometry};
 }
 
 dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out);
@@ -617,6 +624,14 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_instances, cudaStream
   return create_device_mesh(m, descs, stream, out);
 }
 
+dg_status dg_mesh_geometry(const dg_mesh* mesh, int64_t* n_curved_elems, int64_t* n_curved_faces, int64_t* geometry_doubles) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (n_curved_elems) *n_curved_elems = mesh->h.n_curved;
+  if (n_curved_faces) *n_curved_faces = mesh->h.n_curved_faces;
+  if (geometry_doubles) *geometry_doubles = (int64_t)(mesh->h.cpool.size() + mesh->h.fgeo.size());
+  return DG_OK;
+}
+
 dg_status dg_batch_layout(const dg_mesh* mesh, int64_t* instance_elem_off, int64_t* instance_dof_off) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   const size_t k = mesh->h.inst_elem_off.size();
@@ -660,6 +675,11 @@ dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t 
   if ((e = upload(&m->d_elem_qoff, h.elem_qoff)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_elem_voff, h.elem_voff)) != cudaSuccess) return fail_cuda(e, "upload slots");
   if ((e = upload(&m->d_geo, h.slot_geo)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+  if (h.n_curved) {
+    if ((e = upload(&m->d_slot_coff, h.slot_coff)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+    if ((e = upload(&m->d_cpool, h.cpool)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+    if ((e = upload(&m->d_fgeo, h.fgeo)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+  }
   if ((e = upload(&m->d_fnrm, h.slot_fnrm)) != cudaSuccess) return fail_cuda(e, "upload geometry");
   if ((e = upload(&m->d_faces, h.faces)) != cudaSuccess) return fail_cuda(e, "upload faces");
   if ((e = upload(&m->d_fblocks, h.face_blocks)) != cudaSuccess) return fail_cuda(e, "upload faces");
@@ -701,8 +721,7 @@ extern "C" {
 dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_xyz, int64_t* slot_of_elem) {
   if (!desc) return fail(DG_ERR_ARG, "null argument");
   dgh::HostMesh h;
-  dgh::MeshInput in{desc->n_vertices, desc->xyz, desc->n_elems, desc->type, desc->elem_vert_off, desc->elem_verts,
-                    desc->period, desc->N};
+  dgh::MeshInput in = input_of(desc);
   std::string err;
   int r = dgh::build_mesh(in, &h, &err);
   if (r != 0) return fail((dg_status)r, err);
@@ -833,6 +852,7 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available on curved meshes");
   DG_CUDA(mesh->ensure_adjoint(0));
   dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0, 0};
   mesh->enqueue_vjp(va, stream);
@@ -877,6 +897,7 @@ extern "C" {
 dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
                              cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available on curved meshes");
   if (mesh->ns)
     return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp_noalloc covers the Euler equations (the viscous adjoint needs "
                                     "workspace that dg_rhs_vjp allocates); use dg_rhs_vjp");
@@ -944,6 +965,7 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
 dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
                       double dt) {
   if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available on curved meshes");
   if (nsteps < 0 || ckpt_every < 0) return fail(DG_ERR_ARG, "nsteps and ckpt_every must be >= 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   return DG_OK;
@@ -1045,6 +1067,7 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
   if (physics == DG_NAVIER_STOKES) {
+    if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes path is not available on curved meshes");
     if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(DG_ERR_ARG, "mu must be finite and >= 0");
     if (!(Pr > 0.0) || !std::isfinite(Pr)) return fail(DG_ERR_ARG, "Pr must be finite and > 0");
     const size_t hb = sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.h_total);

@@ -53,7 +53,8 @@ struct TypeTab {
 };
 
 // Per-element geometry (affine): Jg = J * dxi/dx (row k = xi_k, column d = x_d)
-// and 1/J, J = |det dx/dxi|.
+// and 1/J, J = |det dx/dxi|.  Curved elements keep their pointwise geometry
+// in a separate pool (HostMesh::cpool) and leave this record zero.
 struct ElemGeo {
   double Jg[9];
   double invJ;
@@ -70,9 +71,9 @@ struct FaceRec {
   int map;
   int owner_tab;    // type table of the owner (reference face weights)
   int owner_lf;     // owner's local face
-  int pad;
+  int cgeo;         // curved owner: double offset of the face's per-point normals and w S ([4][n^2]); -1 otherwise
   double nrm[3];
-  double S;         // area scale |dx/ds x dx/dt|
+  double S;         // area scale |dx/ds x dx/dt| (affine owner)
 };
 
 struct FaceBlock {

@@ -14,6 +14,8 @@
 #include <map>
 #include <tuple>
 #include <unordered_map>
+#include <atomic>
+#include <thread>
 
 namespace dgh {
 
@@ -531,6 +533,197 @@ void inv3(const double A[3][3], double Ai[3][3]) {
 // reference vertices spanning the affine map (images of the reference axes)
 const int kAxisVert[4][3] = {{1, 2, 4}, {1, 2, 3}, {1, 2, 4}, {1, 2, 3}};
 
+// ---- curved elements: vertex-interpolated maps x = sum_v N_v(xi) X_v
+//   hex      N_v = prod_d (1 + r_vd xi_d)/2                     (trilinear)
+//   prism    l_i(xi, eta) (1 -+ zeta)/2, l = (-(xi+eta)/2, (1+xi)/2, (1+eta)/2)
+//   pyramid  (1 + r_v0 a)/2 (1 + r_v1 b)/2 (1 - c)/2 (base), (1 + c)/2 (apex),
+//            in the pyramid's collapsed coordinates (a, b, c)
+//   tet      barycentric
+// Values N[v] and gradients dN[v][k] = d N_v / d xi_k at the collapsed point
+// (a, b, c).
+void shape_grad(int type, double a, double b, double c, double* N, double (*dN)[3]) {
+  double xi[3];
+  uncollapse(type, a, b, c, xi);
+  switch (type) {
+    case dgk::HEX:
+      for (int v = 0; v < 8; ++v) {
+        const double* r = kRefVerts[0][v];
+        double f[3];
+        for (int d = 0; d < 3; ++d) f[d] = 0.5 * (1.0 + r[d] * xi[d]);
+        N[v] = f[0] * f[1] * f[2];
+        dN[v][0] = 0.5 * r[0] * f[1] * f[2];
+        dN[v][1] = 0.5 * r[1] * f[0] * f[2];
+        dN[v][2] = 0.5 * r[2] * f[0] * f[1];
+      }
+      break;
+    case dgk::PRISM: {
+      const double lam[3] = {-0.5 * (xi[0] + xi[1]), 0.5 * (1.0 + xi[0]), 0.5 * (1.0 + xi[1])};
+      const double dl[3][2] = {{-0.5, -0.5}, {0.5, 0.0}, {0.0, 0.5}};
+      const double zl = 0.5 * (1.0 - xi[2]), zu = 0.5 * (1.0 + xi[2]);
+      for (int i = 0; i < 3; ++i) {
+        N[i] = lam[i] * zl;
+        N[i + 3] = lam[i] * zu;
+        dN[i][0] = dl[i][0] * zl;
+        dN[i][1] = dl[i][1] * zl;
+        dN[i][2] = -0.5 * lam[i];
+        dN[i + 3][0] = dl[i][0] * zu;
+        dN[i + 3][1] = dl[i][1] * zu;
+        dN[i + 3][2] = 0.5 * lam[i];
+      }
+      break;
+    }
+    case dgk::TET: {
+      N[0] = -0.5 * (1.0 + xi[0] + xi[1] + xi[2]);
+      N[1] = 0.5 * (1.0 + xi[0]);
+      N[2] = 0.5 * (1.0 + xi[1]);
+      N[3] = 0.5 * (1.0 + xi[2]);
+      const double g[4][3] = {{-0.5, -0.5, -0.5}, {0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}};
+      for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < 3; ++k) dN[v][k] = g[v][k];
+      break;
+    }
+    case dgk::PYR: {
+      double cm[3][3];  // d(a,b,c)_l / d xi_k
+      collapse_metric(dgk::PYR, a, b, c, cm);
+      for (int v = 0; v < 5; ++v) {
+        double g[3];
+        if (v < 4) {
+          const double* r = kRefVerts[2][v];
+          double fa = 0.5 * (1.0 + r[0] * a), fb = 0.5 * (1.0 + r[1] * b), fc = 0.5 * (1.0 - c);
+          N[v] = fa * fb * fc;
+          g[0] = 0.5 * r[0] * fb * fc;
+          g[1] = 0.5 * r[1] * fa * fc;
+          g[2] = -0.5 * fa * fb;
+        } else {
+          N[v] = 0.5 * (1.0 + c);
+          g[0] = g[1] = 0.0;
+          g[2] = 0.5;
+        }
+        for (int k = 0; k < 3; ++k) dN[v][k] = g[0] * cm[0][k] + g[1] * cm[1][k] + g[2] * cm[2][k];
+      }
+      break;
+    }
+  }
+}
+
+// dx/dxi (F[d][k]) and x - X_0 at the collapsed point from the element's
+// vertex positions relative to its first vertex (Xrel [nv][3]).
+void element_map(int type, const double* Xrel, double a, double b, double c, double F[3][3], double* xrel) {
+  double N[8], dN[8][3];
+  shape_grad(type, a, b, c, N, dN);
+  for (int d = 0; d < 3; ++d) {
+    xrel[d] = 0.0;
+    for (int k = 0; k < 3; ++k) F[d][k] = 0.0;
+  }
+  for (int v = 0; v < kNumVerts[type]; ++v)
+    for (int d = 0; d < 3; ++d) {
+      xrel[d] += N[v] * Xrel[3 * v + d];
+      for (int k = 0; k < 3; ++k) F[d][k] += Xrel[3 * v + d] * dN[v][k];
+    }
+}
+
+// Generalized Vandermonde matrix V[q][mode] on the collapsed GL grid.
+std::vector<double> vandermonde(int type, int N, const double* x) {
+  const int n = N + 1, nQ = n * n * n, nM = n_modes(type, N);
+  std::vector<double> V((size_t)nQ * nM);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        int q = (i * n + j) * n + k, mode = 0;
+        for (int p = 0; p < n; ++p)
+          for (int qq = 0; qq < q_count(type, N, p); ++qq)
+            for (int r = 0; r < r_count(type, N, p, qq); ++r, ++mode)
+              V[(size_t)q * nM + mode] = factor_A(type, p, x[i]) * factor_B(type, p, qq, x[j]) * factor_C(type, p, qq, r, x[k]);
+      }
+  return V;
+}
+
+// Inverse of a symmetric positive definite matrix (row-major, n x n) by a
+// Cholesky factorisation A = L L^T and two triangular solves per column.
+bool spd_inverse(int n, const double* A, double* Ainv) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = s / ljj;
+    }
+  }
+  std::vector<double> y(n);
+  for (int col = 0; col < n; ++col) {
+    for (int i = 0; i < n; ++i) {  // L y = e_col
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * y[k];
+      y[i] = s / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * Ainv[(size_t)k * n + col];
+      Ainv[(size_t)i * n + col] = s / L[(size_t)i * n + i];
+    }
+  }
+  return true;
+}
+
+// Pointwise geometry block of one curved element (layout of HostMesh::cpool).
+// Returns false if det(dx/dxi) changes sign or vanishes at a volume point, or
+// the mass matrix is not positive definite.
+bool curved_block(const TypeTab& T, const std::vector<double>& dpool, const double* x, const double* Xrel,
+                  const double* V, double* out) {
+  const int n = T.n, nQ = T.nQ, nM = T.nM, type = T.type;
+  const double* wq = dpool.data() + T.W;
+  int sign = 0;
+  std::vector<double> wJ(nQ);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        const int q = (i * n + j) * n + k;
+        double F[3][3], xr[3];
+        element_map(type, Xrel, x[i], x[j], x[k], F, xr);
+        const double det = det3(F);
+        const int sg = det > 0 ? 1 : (det < 0 ? -1 : 0);
+        if (sg == 0 || (sign != 0 && sg != sign)) return false;
+        sign = sg;
+        const double J = std::fabs(det);
+        double Fi[3][3];
+        inv3(F, Fi);
+        double cm[3][3];
+        collapse_metric(type, x[i], x[j], x[k], cm);
+        for (int l = 0; l < 3; ++l)
+          for (int d = 0; d < 3; ++d) {
+            double m = 0.0;
+            for (int kk = 0; kk < 3; ++kk) m += cm[l][kk] * J * Fi[kk][d];
+            out[(size_t)(l * 3 + d) * nQ + q] = wq[q] * m;
+          }
+        out[(size_t)9 * nQ + q] = J;
+        out[(size_t)10 * nQ + q] = 1.0 / J;
+        wJ[q] = wq[q] * J;
+      }
+  if (type == dgk::PRISM || type == dgk::PYR) {
+    std::vector<double> Me((size_t)nM * nM, 0.0);
+    for (int q = 0; q < nQ; ++q) {
+      const double* vq = V + (size_t)q * nM;
+      for (int a = 0; a < nM; ++a) {
+        const double s = wJ[q] * vq[a];
+        for (int b2 = 0; b2 <= a; ++b2) Me[(size_t)a * nM + b2] += s * vq[b2];
+      }
+    }
+    for (int a = 0; a < nM; ++a)
+      for (int b2 = a + 1; b2 < nM; ++b2) Me[(size_t)a * nM + b2] = Me[(size_t)b2 * nM + a];
+    if (!spd_inverse(nM, Me.data(), out + (size_t)11 * nQ)) return false;
+  }
+  return true;
+}
+
+int64_t curved_block_size(const TypeTab& T) {
+  return 11 * (int64_t)T.nQ + ((T.type == dgk::PRISM || T.type == dgk::PYR) ? (int64_t)T.nM * T.nM : 0);
+}
+
 }  // namespace
 
 int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
@@ -567,6 +760,8 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   std::vector<dgk::ElemGeo> geo(E);
   std::vector<std::array<double, 12>> affine(E);  // X0, A columns
   std::vector<std::array<double, 3>> centroid(E);
+  std::vector<char> curved(E, 0);
+  if (in.geometry != 0 && in.geometry != 1) { *err = "unknown geometry kind"; return -1; }
   for (int64_t e = 0; e < E; ++e) {
     int t = in.type[e];
     const int64_t* V = in.verts + in.off[e];
@@ -579,13 +774,27 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
     double scale = 0.0;
     for (int k = 0; k < 3; ++k)
       for (int d = 0; d < 3; ++d) scale = std::max(scale, std::fabs(A[d][k]));
+    bool is_affine = true;
     for (int m = 0; m < kNumVerts[t]; ++m) {
       const double* Xm = in.xyz + 3 * V[m];
       for (int d = 0; d < 3; ++d) {
         double pred = X0[d];
         for (int k = 0; k < 3; ++k) pred += A[d][k] * 0.5 * (kRefVerts[t][m][k] + 1.0);
-        if (std::fabs(pred - Xm[d]) > 1e-10 * scale) { *err = "element is not an affine image of its reference element"; return -2; }
+        if (std::fabs(pred - Xm[d]) > 1e-10 * scale) is_affine = false;
       }
+    }
+    {
+      double c[3] = {0, 0, 0};
+      for (int m = 0; m < kNumVerts[t]; ++m)
+        for (int d = 0; d < 3; ++d) c[d] += in.xyz[3 * V[m] + d] / kNumVerts[t];
+      for (int d = 0; d < 3; ++d) centroid[e][d] = c[d];
+    }
+    if (!is_affine) {
+      if (in.geometry != 1) { *err = "element is not an affine image of its reference element"; return -2; }
+      curved[e] = 1;   // pointwise geometry below; the affine record stays zero
+      std::memset(&geo[e], 0, sizeof(geo[e]));
+      for (int d = 0; d < 12; ++d) affine[e][d] = 0.0;
+      continue;
     }
     double det = det3(A);
     if (!(std::fabs(det) > 1e-300)) { *err = "degenerate element"; return -2; }
@@ -599,10 +808,6 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
       affine[e][d] = X0[d];
       for (int k = 0; k < 3; ++k) affine[e][3 + 3 * k + d] = A[d][k];
     }
-    double c[3] = {0, 0, 0};
-    for (int m = 0; m < kNumVerts[t]; ++m)
-      for (int d = 0; d < 3; ++d) c[d] += in.xyz[3 * V[m] + d] / kNumVerts[t];
-    for (int d = 0; d < 3; ++d) centroid[e][d] = c[d];
   }
 
   // ---- Hilbert order of the centroids (ties: caller index)
@@ -664,6 +869,54 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   for (int t = 0; t < 4; ++t) M.type_slots[t].clear();
   for (int64_t e = 0; e < E; ++e) M.type_slots[(int)in.type[e]].push_back(M.slot_of_elem[e]);
 
+  // ---- curved elements: pointwise metric, J, 1/J and (prism, pyramid) the
+  // dense inverse mass matrix of Algorithm 1, per slot
+  M.slot_coff.assign(E, -1);
+  M.cpool.clear();
+  M.n_curved = 0;
+  {
+    int64_t csize = 0;
+    for (int64_t s = 0; s < E; ++s)
+      if (curved[M.elem_of_slot[s]]) {
+        M.slot_coff[s] = csize;
+        csize += curved_block_size(M.tables.tabs[M.slot_tab[s]]);
+        M.n_curved++;
+      }
+    if (M.n_curved) {
+      M.cpool.assign((size_t)csize, 0.0);
+      std::vector<double> Vt[4];
+      for (int t = 0; t < 4; ++t)
+        if (tab_of_type[t] >= 0 && (t == dgk::PRISM || t == dgk::PYR)) Vt[t] = vandermonde(t, N, M.x1d.data());
+      std::vector<int64_t> todo;
+      for (int64_t s = 0; s < E; ++s)
+        if (M.slot_coff[s] >= 0) todo.push_back(s);
+      std::atomic<int64_t> next(0);
+      std::atomic<int> bad(0);
+      auto work = [&]() {
+        std::vector<double> Xrel(24);
+        for (;;) {
+          const int64_t i = next.fetch_add(1);
+          if (i >= (int64_t)todo.size() || bad.load()) break;
+          const int64_t s = todo[i], e = M.elem_of_slot[s];
+          const int t = in.type[e];
+          const int64_t* V = in.verts + in.off[e];
+          for (int v = 0; v < kNumVerts[t]; ++v)
+            for (int d = 0; d < 3; ++d) Xrel[3 * v + d] = in.xyz[3 * V[v] + d] - in.xyz[3 * V[0] + d];
+          const TypeTab& T = M.tables.tabs[M.slot_tab[s]];
+          if (!curved_block(T, M.tables.dpool, M.x1d.data(), Xrel.data(), Vt[t].data(), M.cpool.data() + M.slot_coff[s]))
+            bad.store(1);
+        }
+      };
+      unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+      nth = (unsigned)std::min<int64_t>(nth, (int64_t)todo.size());
+      std::vector<std::thread> pool;
+      for (unsigned i = 1; i < nth; ++i) pool.emplace_back(work);
+      work();
+      for (auto& th : pool) th.join();
+      if (bad.load()) { *err = "curved element is inverted or degenerate at a quadrature point"; return -2; }
+    }
+  }
+
   // ---- canonical (periodically reduced) vertex ids
   std::vector<int64_t> canon(in.n_vertices);
   {
@@ -720,6 +973,8 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   M.slot_fnrm.assign((size_t)E * 18, 0.0);
   M.perms.clear();
   M.dense.clear();
+  M.fgeo.clear();
+  M.n_curved_faces = 0;
   std::map<std::vector<int16_t>, int> perm_ids;
   std::map<std::vector<int>, int> dense_ids;  // key: (nb type, nb lf, sigma, owner tri)
   const double* x = M.x1d.data();
@@ -749,9 +1004,63 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
     R.toff = f * 2 * 5 * (int64_t)n2;
     R.owner_tab = tab_of_type[t0];
     R.owner_lf = ft.l0;
-    R.pad = 0;
-    // owner geometry: normal and area scale
-    {
+    R.cgeo = -1;
+    if (curved[ft.e0]) {
+      // curved owner: per face point p = ia + n ib (the owner's face grid)
+      // the area vector (dx/dxi t_s) x (dx/dxi t_t), t_s, t_t the reference
+      // tangents of the face parameters, oriented outward: sign(det dx/dxi)
+      // times the orientation of t_s x t_t against the reference outward side
+      const int* fv = kFaceVerts[t0][ft.l0];
+      const double* c0r = kRefVerts[t0][fv[0]];
+      const double* c1r = kRefVerts[t0][fv[1]];
+      const double* c2r = kRefVerts[t0][fv[2]];
+      double tsr[3], ttr[3], nref[3], out_ref[3] = {0, 0, 0}, cen[3] = {0, 0, 0};
+      for (int k = 0; k < 3; ++k) {
+        tsr[k] = 0.5 * (c1r[k] - c0r[k]);
+        ttr[k] = 0.5 * (c2r[k] - c0r[k]);
+      }
+      cross(tsr, ttr, nref);
+      for (int v = 0; v < kNumVerts[t0]; ++v)
+        for (int k = 0; k < 3; ++k) cen[k] += kRefVerts[t0][v][k] / kNumVerts[t0];
+      for (int i = 0; i < nv; ++i)
+        for (int k = 0; k < 3; ++k) out_ref[k] += kRefVerts[t0][fv[i]][k] / nv - cen[k] / nv;
+      const double orient = (nref[0] * out_ref[0] + nref[1] * out_ref[1] + nref[2] * out_ref[2]) > 0 ? 1.0 : -1.0;
+      double Xrel[24];
+      for (int v = 0; v < kNumVerts[t0]; ++v)
+        for (int d = 0; d < 3; ++d) Xrel[3 * v + d] = in.xyz[3 * V0[v] + d] - in.xyz[3 * V0[0] + d];
+      const TypeTab& T0 = M.tables.tabs[tab_of_type[t0]];
+      const FaceDesc fd = T0.faces[ft.l0];
+      const double* fw = M.tables.dpool.data() + T0.fw + (size_t)ft.l0 * n2;
+      const size_t base = M.fgeo.size();
+      M.fgeo.resize(base + (size_t)4 * n2);
+      for (int ib = 0; ib < n; ++ib)
+        for (int ia = 0; ia < n; ++ia) {
+          const int p = ia + n * ib;
+          double abc[3];
+          abc[fd.fixed] = fd.end ? 1.0 : -1.0;
+          abc[fd.alpha] = x[ia];
+          abc[fd.beta] = x[ib];
+          double F[3][3], xr[3], ts[3], tt[3], cr[3];
+          element_map(t0, Xrel, abc[0], abc[1], abc[2], F, xr);
+          for (int d = 0; d < 3; ++d) {
+            ts[d] = F[d][0] * tsr[0] + F[d][1] * tsr[1] + F[d][2] * tsr[2];
+            tt[d] = F[d][0] * ttr[0] + F[d][1] * ttr[1] + F[d][2] * ttr[2];
+          }
+          cross(ts, tt, cr);
+          const double S = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+          const double sg = (det3(F) > 0 ? 1.0 : -1.0) * orient;
+          for (int d = 0; d < 3; ++d) M.fgeo[base + (size_t)d * n2 + p] = sg * cr[d] / S;
+          M.fgeo[base + (size_t)3 * n2 + p] = fw[p] * S;
+          if (p == 0) {
+            for (int d = 0; d < 3; ++d) R.nrm[d] = sg * cr[d] / S;
+          }
+        }
+      R.S = 0.0;
+      if (base >= ((size_t)1 << 31)) { *err = "too many curved faces for 32-bit face-geometry offsets"; return -7; }
+      R.cgeo = (int)base;
+      M.n_curved_faces++;
+    } else {
+      // owner geometry: normal and area scale
       const auto& af = affine[ft.e0];
       const int* fv = kFaceVerts[t0][ft.l0];
       double ts[3], tt[3];
@@ -885,6 +1194,22 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   for (int64_t e = 0; e < E; ++e) {
     int t = in.type[e];
     const auto& af = affine[e];
+    if (curved[e]) {
+      const int64_t* V = in.verts + in.off[e];
+      const double* X0 = in.xyz + 3 * V[0];
+      double Xrel[24];
+      for (int v = 0; v < kNumVerts[t]; ++v)
+        for (int d = 0; d < 3; ++d) Xrel[3 * v + d] = in.xyz[3 * V[v] + d] - X0[d];
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k) {
+            double F[3][3], xr[3];
+            element_map(t, Xrel, x[i], x[j], x[k], F, xr);
+            size_t q = (size_t)e * n * n * n + (size_t)(i * n + j) * n + k;
+            for (int d = 0; d < 3; ++d) M.quad_xyz[3 * q + d] = X0[d] + xr[d];
+          }
+      continue;
+    }
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j)
         for (int k = 0; k < n; ++k) {
@@ -919,6 +1244,7 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
     M.tables = std::move(Mi.tables);
     const int64_t E = Mi.n_elems;
     const int64_t p_off = (int64_t)M.perms.size(), d_off = (int64_t)M.dense.size();
+    const int64_t c_off = (int64_t)M.cpool.size(), g_off = (int64_t)M.fgeo.size();
     for (int64_t s = 0; s < E; ++s) {
       M.elem_of_slot.push_back(Mi.elem_of_slot[s] + e_off);
       M.slot_tab.push_back(Mi.slot_tab[s]);
@@ -926,6 +1252,7 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
       M.slot_qoff.push_back(Mi.slot_qoff[s] + q_off);
       M.slot_hoff.push_back(Mi.slot_hoff[s] + h_off);
       M.slot_geo.push_back(Mi.slot_geo[s]);
+      M.slot_coff.push_back(Mi.slot_coff[s] >= 0 ? Mi.slot_coff[s] + c_off : -1);
       for (int lf = 0; lf < 6; ++lf) {
         int64_t t = Mi.slot_ftoff[(size_t)s * 6 + lf];
         M.slot_ftoff.push_back(t >= 0 ? t + t_off : -1);
@@ -939,8 +1266,13 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
     }
     M.perms.insert(M.perms.end(), Mi.perms.begin(), Mi.perms.end());
     M.dense.insert(M.dense.end(), Mi.dense.begin(), Mi.dense.end());
+    M.cpool.insert(M.cpool.end(), Mi.cpool.begin(), Mi.cpool.end());
+    M.fgeo.insert(M.fgeo.end(), Mi.fgeo.begin(), Mi.fgeo.end());
+    M.n_curved += Mi.n_curved;
+    M.n_curved_faces += Mi.n_curved_faces;
     for (dgk::FaceRec R : Mi.faces) {
       R.toff += t_off;
+      if (R.cgeo >= 0) R.cgeo += (int)g_off;
       R.map = R.map >= 0 ? (int)(R.map + p_off) : (int)(-1 - ((-1 - R.map) + d_off));
       M.faces.push_back(R);
     }
@@ -971,7 +1303,8 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
   M.h_total = h_off;
   M.t_total = t_off;
   M.n_faces = f_off;
-  if (f_off >= (int64_t)1 << 31 || (int64_t)M.perms.size() >= (int64_t)1 << 31 || (int64_t)M.dense.size() >= (int64_t)1 << 31) {
+  if (f_off >= (int64_t)1 << 31 || (int64_t)M.perms.size() >= (int64_t)1 << 31 || (int64_t)M.dense.size() >= (int64_t)1 << 31 ||
+      (int64_t)M.fgeo.size() >= (int64_t)1 << 31) {
     *err = "batch too large for 32-bit face indices";
     return -7;
   }

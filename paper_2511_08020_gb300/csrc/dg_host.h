@@ -47,6 +47,7 @@ struct MeshInput {
   const int64_t* verts;
   const double* period;
   int N;
+  int geometry = 0;   // 0: affine elements only; 1: vertex-interpolated (curved) maps allowed
 };
 
 struct HostMesh {
@@ -60,6 +61,18 @@ struct HostMesh {
   std::vector<int8_t> slot_type;
   std::vector<int64_t> slot_qoff, slot_hoff; // double offsets
   std::vector<dgk::ElemGeo> slot_geo;
+  // curved (non-affine) elements: per slot the offset of its block in cpool,
+  // -1 for an affine element.  Block: [9][nQ] weighted contravariant metric
+  // w_q (d(a,b,c)/dxi)(J dxi/dx), [nQ] J_q, [nQ] 1/J_q, and for prism and
+  // pyramid the dense inverse mass matrix (V^T diag(w J) V)^{-1} [nM][nM].
+  std::vector<int64_t> slot_coff;
+  std::vector<double> cpool;
+  int64_t n_curved = 0;
+  // face-point geometry of faces whose owner is curved (per face [4][n^2]:
+  // outward unit normal x, y, z and w S per owner point); FaceRec::cgeo is
+  // the double offset of a face's block
+  std::vector<double> fgeo;
+  int64_t n_curved_faces = 0;
   std::vector<int64_t> slot_ftoff;           // [slot][6] trace offset of (face, own side)
   std::vector<double> slot_fnrm;             // [slot][6][3] outward unit normal of each local face
                                              // (the owner's normal, negated on the neighbour side)

@@ -508,12 +508,44 @@ struct Epilogue {
   double* K;
   double* sQ;
   double a, b, dt;
+  // curved prism / pyramid: r = Md (V^T bufA) with the element's dense
+  // inverse mass matrix Md [nM][nM] (symmetric) instead of minv and scale;
+  // rbuf [5][nM] is shared scratch that no other argument aliases
+  const double* Md = nullptr;
+  double* rbuf = nullptr;
 };
+
+// The epilogue of one mode given r_v (5 values).  Returns true if a
+// non-finite state value was produced.
+__device__ __forceinline__ bool epilogue_mode(const Epilogue& ep, int nM, int mode, const double* r) {
+  bool bad = false;
+  if (ep.kind == Epilogue::kStore) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] = r[v];
+  } else if (ep.kind == Epilogue::kAxpy) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] += r[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int idx = v * nM + mode;
+      const double R = r[v];
+      const double k = (ep.a == 0.0) ? ep.dt * R : fma(ep.a, ep.K[idx], ep.dt * R);
+      const double qn = fma(ep.b, k, ep.Qi[idx]);
+      ep.K[idx] = k;
+      ep.Qo[idx] = qn;
+      if (ep.sQ) ep.sQ[idx] = qn;
+      bad |= !finite_bits(qn);
+    }
+  }
+  return bad;
+}
 
 // Nodal -> modal transpose: bufA [5][nQ] -> modal coefficients through `ep`;
 // bufB is scratch.  Returns true if a non-finite state value was produced.
-__device__ __noinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane,
-                                            const Epilogue& ep) {
+template <bool DENSE>
+__device__ __noinline__ bool nodal_to_modal_t(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane,
+                                              const Epilogue& ep) {
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int* ip = c.ipool;
@@ -550,29 +582,36 @@ __device__ __noinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, doub
     const double* X = bufA + col * n;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < n; ++k) DG_FMA5(C[k], X + k, nQ, acc);
+    if (DENSE) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ep.rbuf[v * nM + mode] = acc[v];
+      continue;
+    }
     const double mi = ep.minv ? dp[T.minv + mode] * ep.scale : ep.scale;
-    if (ep.kind == Epilogue::kStore) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] = acc[v] * mi;
-    } else if (ep.kind == Epilogue::kAxpy) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) ep.out[v * nM + mode] += acc[v] * mi;
-    } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const int idx = v * nM + mode;
-        const double R = acc[v] * mi;
-        const double k = (ep.a == 0.0) ? ep.dt * R : fma(ep.a, ep.K[idx], ep.dt * R);
-        const double qn = fma(ep.b, k, ep.Qi[idx]);
-        ep.K[idx] = k;
-        ep.Qo[idx] = qn;
-        if (ep.sQ) ep.sQ[idx] = qn;
-        bad |= !finite_bits(qn);
-      }
+    for (int v = 0; v < 5; ++v) acc[v] *= mi;
+    bad |= epilogue_mode(ep, nM, mode, acc);
+  }
+  if (DENSE) {
+    // dense inverse mass matrix of a curved element (Algorithm 1 with a
+    // pointwise J): lanes run over output modes, so the column reads of the
+    // symmetric Md are coalesced and every load feeds 5 FMAs
+    __syncthreads();
+    for (int mode = lane; mode < nM; mode += blockDim.x) {
+      const double* Mc = ep.Md + mode;
+      double acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+      for (int j = 0; j < nM; ++j) DG_FMA5(Mc[(size_t)j * nM], ep.rbuf + j, nM, acc);
+      bad |= epilogue_mode(ep, nM, mode, acc);
     }
   }
   __syncthreads();
   return bad;
+}
+
+__device__ __forceinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane,
+                                               const Epilogue& ep) {
+  return ep.Md ? nodal_to_modal_t<true>(c, T, bufA, bufB, lane, ep) : nodal_to_modal_t<false>(c, T, bufA, bufB, lane, ep);
 }
 
 // Values of the nodal field `src` [5][nQ] on the element's own face points,
@@ -650,8 +689,9 @@ __device__ __forceinline__ void point_metric(int type, const double* wa, const d
 
 // Forward phase of the element at slot s: nodal state, own-face traces and
 // the nodal volume residual H.  sQ lives at the start of bufG.
-__device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
-                                                int lane) {
+template <bool CURVED>
+__device__ __noinline__ void element_forward_t(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
+                                                  int lane) {
   const int n = T.n, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   modal_to_nodal(c, T, bufG, bufA, bufG, lane);
@@ -674,13 +714,22 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
   double Jg[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+  // a curved element reads its pointwise metric w (da/dxi)(J dxi/dx) instead
+  const double* cm = CURVED ? c.cpool + c.slot_coff[s] : nullptr;
   const double gm1 = c.gamma - 1.0;
   for (int q = lane; q < nQ; q += blockDim.x) {
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v] = bufA[v * nQ + q];
     double M[3][3];
-    point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+    if (CURVED) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) M[l][d] = cm[(l * 3 + d) * nQ + q];
+    } else {
+      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+    }
     double rinv = 1.0 / U[0];
     double u = U[1] * rinv, v = U[2] * rinv, w = U[3] * rinv;
     double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
@@ -717,12 +766,19 @@ __device__ __noinline__ void element_forward(const Ctx& c, const TypeTab& T, int
   __syncthreads();
 }
 
+__device__ __forceinline__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
+                                                int lane) {
+  if (c.slot_coff && c.slot_coff[s] >= 0) element_forward_t<true>(c, T, s, bufA, bufG, lane);
+  else element_forward_t<false>(c, T, s, bufA, bufG, lane);
+}
+
 // Backward phase, first half: bufA = H + sign sum_faces E_f^T F_f with the
 // face values F_f read from `faces` (the lifted fluxes with sign -1; the
 // adjoint's trace cotangents with sign +1).  They are staged into bufG with
 // coalesced loads first.
-__device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
-                                          int lane, const double* faces, double sign) {
+template <bool PSCALE>
+__device__ __noinline__ void element_lift_t(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
+                                            int lane, const double* faces, double sign, const double* pscale) {
   const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
   const double* dp = c.dpool;
   const int64_t* ft = c.slot_ftoff + s * 6;
@@ -746,10 +802,23 @@ __device__ __noinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_
       int p = sel3(i, j, k, d.alpha) + n * sel3(i, j, k, d.beta);
       DG_FMA5(sign * dp[T.ext + d.end * n + m], bufG + lf * 5 * n2 + p, n2, h);
     }
+    if (PSCALE) {
+      // curved hexahedron: M^{-1} V^T = V^T diag(1/J) (V square, V^T W V = I)
+      const double sc = pscale[o];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) h[v] *= sc;
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) bufA[v * nQ + o] = h[v];
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
+                                             int lane, const double* faces, double sign,
+                                             const double* pscale = nullptr) {
+  if (pscale) element_lift_t<true>(c, T, s, bufA, bufG, lane, faces, sign, pscale);
+  else element_lift_t<false>(c, T, s, bufA, bufG, lane, faces, sign, nullptr);
 }
 
 // BR1 lifting face term: bufA += sum_f coef_f E_f^T L_f with coef_f =
@@ -967,25 +1036,49 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     __syncthreads();
     return;
   }
+  // Curved element: pointwise J (cpool block [9][nQ] metric, [nQ] J, [nQ] 1/J,
+  // then for prism / pyramid the dense M_e^{-1}); the affine scale 1/J_e and
+  // the diagonal M_ref^{-1} are replaced by diag(1/J_q) before V^T (hex) or by
+  // M_e^{-1} after it (prism, pyramid).  Tetrahedra are always affine.
+  const int64_t coff = c.slot_coff ? c.slot_coff[s] : -1;
+  const double* cblk = coff >= 0 ? c.cpool + coff : nullptr;
+  const bool dense = cblk && T.type != HEX;
   if (MODE == kProject) {
     const int64_t e = c.elem_of_slot[s];
     const double* vals = io.Qin + c.elem_voff[e];
     const double* W = c.dpool + T.W;
-    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * vals[w];
+    if (dense) {
+      const double* Jq = cblk + 9 * nQ;
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * Jq[w % nQ] * vals[w];
+    } else {
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * vals[w];
+    }
     __syncthreads();
     Epilogue ep{Epilogue::kStore, true, 1.0, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    if (dense) {
+      ep.Md = cblk + 11 * nQ;
+      ep.rbuf = bufG + 5 * nQ;
+    }
     nodal_to_modal(c, T, bufA, bufG, lane, ep);
     return;
   }
-  element_lift(c, T, s, bufA, bufG, lane, c.T, -1.0);
-  const double invJ = c.geo[s].invJ;
+  element_lift(c, T, s, bufA, bufG, lane, c.T, -1.0, (cblk && T.type == HEX) ? cblk + 10 * nQ : nullptr);
+  const double invJ = cblk ? 1.0 : c.geo[s].invJ;
   if (MODE == kBwdRhs) {
     Epilogue ep{Epilogue::kStore, true, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    if (dense) {
+      ep.Md = cblk + 11 * nQ;
+      ep.rbuf = bufG + 5 * nQ;
+    }
     nodal_to_modal(c, T, bufA, bufG, lane, ep);
     return;
   }
   Epilogue ep{Epilogue::kRk, true, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
               MODE == kBwdRkFwd ? bufG : nullptr, io.a, io.b, io.dt};
+  if (dense) {
+    ep.Md = cblk + 11 * nQ;
+    ep.rbuf = bufG + 5 * nQ;
+  }
   const bool bad = __syncthreads_or(nodal_to_modal(c, T, bufA, bufG, lane, ep));
   if (bad && lane == 0) atomicOr(c.status, 1u);
   if (MODE == kBwdRkFwd) element_forward(c, T, s, bufA, bufG, lane);
@@ -1412,6 +1505,7 @@ __global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io,
   }
 }
 
+template <bool CURVED>
 __global__ void face_kernel(Ctx c) {
   extern __shared__ double sF[];
   const FaceBlock fb = c.fblocks[blockIdx.x];
@@ -1439,11 +1533,18 @@ __global__ void face_kernel(Ctx c) {
       }
     }
     double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+    const bool cg = CURVED && R.cgeo >= 0;
+    if (cg) {
+      // curved owner: the normal at this point
+      const double* G = c.fgeo + R.cgeo;
+      nrm[0] = G[p];
+      nrm[1] = G[n2 + p];
+      nrm[2] = G[2 * n2 + p];
+    }
     double Fs[5];
     if (c.flux == 0) flux_lf(UL, UR, nrm, gamma, Fs);
     else flux_roe(UL, UR, nrm, gamma, Fs);
-    const TypeTab& T = c.tabs[R.owner_tab];
-    double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    const double wS = cg ? c.fgeo[R.cgeo + 3 * n2 + p] : c.dpool[c.tabs[R.owner_tab].fw + R.owner_lf * n2 + p] * R.S;
     if (R.map >= 0) {
       // permutation map: this thread alone read T0[p] and T1[perm[p]], so it
       // writes both results in place at once
@@ -2042,7 +2143,8 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   if ((e = set_mode<kProject>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kEval>(bmax)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
-  if ((e = set_smem(face_kernel, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_kernel<false>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_kernel<true>, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_vjp_kernel, 2 * fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(elem_vjp_kernel<0>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem(elem_vjp_kernel<2>, 20 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
@@ -2101,7 +2203,8 @@ void launch_faces_ns(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_
 void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
   if (nblocks <= 0) return;
   int bytes = 32 * 5 * n * n * (int)sizeof(double);
-  face_kernel<<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  if (c.fgeo) face_kernel<true><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  else face_kernel<false><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
 }
 
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st) {

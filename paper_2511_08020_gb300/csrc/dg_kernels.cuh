@@ -74,6 +74,10 @@ struct Ctx {
   double* DW;                  // adjoint: nodal lifted gradient [slot][3][5][nQ] (3x slot_hoff), or null
   double* Usave;               // Euler forward: also keep the nodal state here (slot_hoff), or null
   double* Vtb;                 // adjoint: gradient-trace cotangents, layout of Vt
+  // curved (non-affine) elements; null / -1 entries for an affine mesh or element
+  const int64_t* slot_coff;    // [slot] offset into cpool, -1 for an affine element
+  const double* cpool;         // per curved slot: [9][nQ] metric, [nQ] J, [nQ] 1/J, (prism, pyramid) [nM][nM] M_e^{-1}
+  const double* fgeo;          // per curved-owner face: [4][n^2] normal x, y, z and w S (FaceRec::cgeo)
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.

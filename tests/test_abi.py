@@ -137,3 +137,44 @@ def test_batch_argument_checks_without_gpu(dg):
     with pytest.raises(dg.DGError) as ei:
         dg.Batch([b0, b1], [2, 3], stream=0)
     assert ei.value.status == -3
+
+
+@pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 3, 3, False), ("four", 4, 2, True), ("hex", 2, 4, True),
+                                              ("pyramid", 2, 2, True), ("prism", 2, 3, False)])
+def test_curved_host_setup_matches_oracle(dg, kind, m, N, reorder):
+    """Curved (vertex-interpolated) element maps: the host's quadrature points
+    equal the curved oracle's, and a perturbed mesh is rejected unless the
+    curved geometry is requested."""
+    from oracle.curved import CurvedOracle, curved_from_box
+    box = di.perturb_vertices(di.box_mesh(m, kind, seed=1), 0.1)
+    if reorder:
+        box = di.reorder_vertices(box, seed=9)
+    with pytest.raises(dg.DGError) as ei:
+        dg.check_mesh(box, N)
+    assert ei.value.status == -2
+    counts, qp, slots = dg.check_mesh(box, N, geometry="vertex")
+    o = CurvedOracle(curved_from_box(box, N))
+    assert counts[1] == len(o.mesh.faces)
+    oq = np.concatenate([o.quad_points(e) for e in range(box.n_elems)])
+    assert np.abs(qp - oq).max() < 1e-13
+    assert sorted(slots.tolist()) == list(range(box.n_elems))
+
+
+def test_curved_inverted_element_rejected(dg):
+    """A vertex moved through the opposite face makes the trilinear map change
+    orientation inside the element: DG_ERR_MESH."""
+    box = di.box_mesh(3, "hex", seed=1)
+    xyz = box.xyz.copy()
+    v = box.verts_of(4)
+    xyz[v[7]] = xyz[v[0]] - 0.3 * (xyz[v[7]] - xyz[v[0]])
+    bad = di.BoxMesh(xyz, box.etype, box.elem_vert_off, box.elem_verts, box.period, 3, "hex", 1)
+    with pytest.raises(dg.DGError) as ei:
+        dg.check_mesh(bad, 2, geometry="vertex")
+    assert ei.value.status == -2
+
+
+def test_affine_mesh_is_unchanged_by_the_curved_flag(dg):
+    box = di.box_mesh(3, "mixed", seed=2)
+    c0, q0, s0 = dg.check_mesh(box, 3)
+    c1, q1, s1 = dg.check_mesh(box, 3, geometry="vertex")
+    assert np.array_equal(c0, c1) and np.array_equal(q0, q1) and np.array_equal(s0, s1)

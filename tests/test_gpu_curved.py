@@ -1,0 +1,189 @@
+"""GPU parity on curved meshes (vertex-interpolated element maps, pointwise J
+in Eq. 1 and in the Algorithm 1 projection) against the curved oracle,
+through the C ABI: dg_rhs, dg_rk_step, dg_project, dg_eval_nodal, the
+quadrature points, free-stream preservation, scheduler and batch
+equivalence, the affine limit, the calls curved meshes do not support, and a
+sampled check of the 16^3 mixed N = 4 perturbed mesh in the launch
+configuration the benchmark times.  Tolerance: relative L-infinity per
+variable <= 1e-11."""
+import numpy as np
+import pytest
+
+import dg_inputs as di
+from gpu_util import TOL, rel_err, var_index
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_08020_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def curved_box(kind, m, seed=1, reorder=None, amp=0.1):
+    box = di.perturb_vertices(di.box_mesh(m, kind, seed=seed), amp)
+    if reorder is not None:
+        box = di.reorder_vertices(box, seed=reorder)
+    return box
+
+
+def setup(dg, kind, m, N, flux="lf", reorder=None, scheduler="balanced"):
+    from oracle.curved import CurvedOracle, curved_from_box
+    box = curved_box(kind, m, reorder=reorder)
+    o = CurvedOracle(curved_from_box(box, N), flux=flux)
+    mesh = dg.Mesh(box, N, flux=flux, scheduler=scheduler, geometry="vertex")
+    return box, o, mesh
+
+
+def state(o, seed=3, amp=0.05):
+    return o.project(lambda x: di.perturbed_tgv_state(x, seed=seed, amp=amp))
+
+
+CASES = [("mixed", 3, 3, "lf", None), ("mixed", 3, 3, "roe", 5), ("hex", 2, 4, "lf", 3),
+         ("prism", 2, 5, "roe", 3), ("pyramid", 2, 2, "lf", 7), ("pyramid", 2, 1, "roe", None),
+         ("mixed", 2, 6, "lf", 3), ("four", 4, 2, "lf", 5), ("kuhn", 2, 3, "roe", 7),
+         ("mixed", 2, 1, "lf", None), ("prism", 2, 6, "lf", None)]
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder", CASES)
+def test_curved_rhs_parity(dg, kind, m, N, flux, reorder):
+    box, o, mesh = setup(dg, kind, m, N, flux, reorder)
+    if kind != "kuhn":
+        assert mesh.n_curved > 0
+    Q = state(o)
+    R = mesh.get_state(mesh.rhs(mesh.set_state(torch.from_numpy(Q).cuda())))
+    err = rel_err(R, o.rhs(Q), var_index(o.mesh.nM))
+    assert err < TOL, err
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("four", 4, 2), ("prism", 2, 4)])
+def test_curved_project_eval_and_points(dg, kind, m, N):
+    box, o, mesh = setup(dg, kind, m, N)
+    n = N + 1
+    xyz = mesh.quad_points()
+    oq = np.concatenate([o.quad_points(e) for e in range(box.n_elems)])
+    assert np.abs(xyz - oq).max() < 1e-13
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).reshape(-1)
+    Q = mesh.get_state(mesh.project(torch.from_numpy(vals).cuda()))
+    Qref = o.project(di.tgv_state)
+    assert rel_err(Q, Qref, var_index(o.mesh.nM)) < TOL
+    U = mesh.eval_nodal(mesh.set_state(torch.from_numpy(Qref).cuda())).cpu().numpy()
+    Uref = np.concatenate([(o.mesh.block(Qref, e) @ o.ops[o.mesh.etype[e]].V.T).ravel()
+                           for e in range(box.n_elems)])
+    assert np.abs(U - Uref).max() < 1e-12 * np.abs(Uref).max()
+
+
+@pytest.mark.parametrize("kind,m,N,flux,nsteps", [("mixed", 3, 3, "lf", 2), ("four", 4, 2, "roe", 1)])
+def test_curved_rk_step_parity(dg, kind, m, N, flux, nsteps):
+    box, o, mesh = setup(dg, kind, m, N, flux)
+    Q = state(o)
+    dt = 1e-3
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    mesh.rk_step(Qs, mesh.empty(), dt, nsteps)
+    Qg = mesh.get_state(Qs)
+    Qref = o.run(Q, dt, nsteps)
+    assert rel_err(Qg - Q, Qref - Q, var_index(o.mesh.nM)) < 1e-10
+    assert rel_err(Qg, Qref, var_index(o.mesh.nM)) < TOL
+    mesh.sync()
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("four", 4, 2), ("pyramid", 2, 1)])
+def test_curved_free_stream(dg, kind, m, N):
+    box, o, mesh = setup(dg, kind, m, N)
+    U0 = np.array([1.2, 0.3, -0.2, 0.1, 3.0])
+    n = N + 1
+    vals = np.tile(U0[None, :, None], (box.n_elems, 1, n ** 3)).reshape(-1)
+    Qs = mesh.project(torch.from_numpy(vals).cuda())
+    R = mesh.get_state(mesh.rhs(Qs))
+    # flux scale: |F| ~ p + rho u^2 ~ 1; R = M^{-1}(vol - surf) ~ |F| / h
+    assert np.abs(R).max() < 1e-12
+
+
+@pytest.mark.parametrize("scheduler", ["naive", "static"])
+def test_curved_schedulers_agree(dg, scheduler):
+    box, o, mesh = setup(dg, "mixed", 3, 3)
+    other = dg.Mesh(box, 3, scheduler=scheduler, geometry="vertex")
+    Q = torch.from_numpy(state(o)).cuda()
+    R0 = mesh.get_state(mesh.rhs(mesh.set_state(Q)))
+    R1 = other.get_state(other.rhs(other.set_state(Q)))
+    np.testing.assert_array_equal(R0, R1)
+
+
+def test_affine_mesh_same_with_curved_flag(dg):
+    box = di.box_mesh(3, "mixed", seed=2)
+    a = dg.Mesh(box, 3)
+    b = dg.Mesh(box, 3, geometry="vertex")
+    assert b.n_curved == 0 and b.geometry_doubles == 0
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    Q = torch.from_numpy(state(Oracle(from_box(box, 3)))).cuda()
+    np.testing.assert_array_equal(a.get_state(a.rhs(a.set_state(Q))), b.get_state(b.rhs(b.set_state(Q))))
+
+
+def test_curved_batch_equals_instances(dg):
+    from oracle.curved import CurvedOracle, curved_from_box
+    parts = [(curved_box("mixed", 3, seed=1), 3), (curved_box("four", 4, seed=2, reorder=4), 2),
+             (di.box_mesh(2, "hex", seed=3), 4), (curved_box("prism", 2, seed=4), 5)]
+    b = dg.Batch([p[0] for p in parts], [p[1] for p in parts], geometry="vertex")
+    Qs, singles = [], []
+    for i, (box, N) in enumerate(parts):
+        o = CurvedOracle(curved_from_box(box, N))
+        Qs.append(state(o, seed=10 + i))
+        singles.append((dg.Mesh(box, N, geometry="vertex"), o))
+    R = b.get_state(b.rhs(b.set_state(torch.from_numpy(np.concatenate(Qs)).cuda())))
+    for i, (s, o) in enumerate(singles):
+        Ri = s.get_state(s.rhs(s.set_state(torch.from_numpy(Qs[i]).cuda())))
+        np.testing.assert_array_equal(b.instance(R, i), Ri)
+        assert rel_err(Ri, o.rhs(Qs[i]), var_index(o.mesh.nM)) < TOL
+
+
+def test_curved_unsupported_calls(dg):
+    box, o, mesh = setup(dg, "mixed", 2, 2)
+    Qs = mesh.set_state(torch.from_numpy(state(o)).cuda())
+    with pytest.raises(dg.DGError) as ei:
+        mesh.rhs_vjp(Qs, Qs.clone())
+    assert ei.value.status == -7
+    with pytest.raises(dg.DGError) as ei:
+        mesh.rk_vjp(Qs, 1e-3, 2, 1, Qs.clone())
+    assert ei.value.status == -7
+    with pytest.raises(dg.DGError) as ei:
+        mesh.set_physics("navier_stokes", 1e-3, 0.72)
+    assert ei.value.status == -7
+    # the mesh stays usable
+    R = mesh.get_state(mesh.rhs(Qs))
+    assert np.isfinite(R).all()
+
+
+def test_curved_16cube_N4_sampled(dg):
+    """The benchmark's curved workload (16^3 mixed, vertices moved by up to
+    0.1 h per coordinate, N = 4) after autotuning: sampled elements against
+    the oracle evaluated on those elements only, each variable's error
+    measured against the larger of its residual and volume-term magnitude."""
+    from oracle.curved import CurvedOracle, curved_from_box
+    box = di.perturb_vertices(di.box_mesh(16, "mixed", seed=2), 0.1)
+    N = 4
+    mesh = dg.Mesh(box, N, geometry="vertex")
+    n = N + 1
+    vals = di.perturbed_tgv_state(mesh.quad_points(), seed=3).reshape(5, box.n_elems, n ** 3)
+    Qs = mesh.project(torch.from_numpy(vals.transpose(1, 0, 2).reshape(-1)).cuda())
+    mesh.autotune(Qs, 1e-4)
+    R = mesh.get_state(mesh.rhs(Qs))
+    Q = mesh.get_state(Qs)
+    elems = np.sort(np.random.default_rng(7).choice(box.n_elems, 24, replace=False))
+    o = CurvedOracle(curved_from_box(box, N))
+    mask = np.zeros(len(Q), dtype=bool)
+    vol = np.zeros(len(Q))
+    for e in elems:
+        sl = slice(o.mesh.dof_off[e], o.mesh.dof_off[e + 1])
+        mask[sl] = True
+        vol[sl] = o.apply_minv(e, o.volume_term(Q, e)).ravel()
+    Rref = o.rhs(Q, elems)
+    for v, idx in enumerate(var_index(o.mesh.nM)):
+        i = idx[mask[idx]]
+        scale = max(np.abs(Rref[i]).max(), np.abs(vol[i]).max())
+        assert np.abs(R[i] - Rref[i]).max() < TOL * scale, (v, np.abs(R[i] - Rref[i]).max(), scale)
