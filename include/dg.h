@@ -92,9 +92,10 @@ typedef enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 } dg_physics;
  *                   curved hexahedron applies M^{-1} V^T as V^T diag(1/J)
  *                   (exact: its V is square with V^T W V = I).  Affine
  *                   elements of such a mesh take the affine path.  Curved
- *                   meshes support the Euler equations, dg_project,
- *                   dg_eval_nodal, dg_rhs and dg_rk_step; the other calls
- *                   return DG_ERR_UNSUPPORTED on them. */
+ *                   meshes support every call for the Euler equations
+ *                   (residual, time stepping, projection and adjoints);
+ *                   dg_set_physics(DG_NAVIER_STOKES) returns
+ *                   DG_ERR_UNSUPPORTED on them. */
 typedef enum { DG_GEOM_AFFINE = 0, DG_GEOM_VERTEX = 1 } dg_geometry;
 
 /* Mesh description, caller-owned, read only during dg_mesh_create.

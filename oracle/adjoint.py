@@ -58,7 +58,15 @@ def rhs_vjp(o, Q, Rbar):
         JF = cs_jacobian(lambda X: physical_flux(X, o.gamma), U)     # [3, 5(v), 5(u), nQ]
         Ubar = np.einsum("dvuq,dvq->uq", JF, Fbar)
         Qbar[m.dof_off[e]:m.dof_off[e + 1]] += (Ubar @ op.V).ravel()
-    # faces
+    face_vjp(o, Q, rbar, Qbar)
+    return Qbar
+
+
+def face_vjp(o, Q, rbar, Qbar):
+    """Face part of the transpose: adds to Qbar the cotangents of both
+    traces of every face, given rbar_e = M_e^{-1} Rbar_e per element.  The
+    face weights w S and the normals may be per point (curved owners)."""
+    m = o.mesh
     for f, (e0, _, e1, _) in enumerate(m.faces):
         phi0, phi1, wS, nrm = o.face_data(f)
         UL = m.block(Q, e0) @ phi0.T
@@ -70,7 +78,6 @@ def rhs_vjp(o, Q, Rbar):
         URbar = np.einsum("vup,vp->up", JR, Fs_bar)
         Qbar[m.dof_off[e0]:m.dof_off[e0 + 1]] += (ULbar @ phi0).ravel()
         Qbar[m.dof_off[e1]:m.dof_off[e1 + 1]] += (URbar @ phi1).ravel()
-    return Qbar
 
 
 def rhs_jvp(o, Q, V):

@@ -32,10 +32,14 @@ parametrisation, F = dx/dxi at the point); (w S)_p is its length and the
 normal its direction.  The neighbour's reference coordinates of each owner
 face point are found by Newton's method on the neighbour's map.
 
+The adjoint (rhs_vjp) is the transpose of each of these steps.
+
 Parity: pinned by reduction to the affine oracle on affine meshes, the
 divergence theorem on every element, the total volume of the box, free-stream
 preservation, conservation, reproduction of the element maps by the
-projection, and convergence of order about N+1 under a smooth deformation
+projection, convergence of order about N+1 under a smooth deformation, and
+for the adjoint the dot-product test against complex-step directional
+derivatives of the residual and of K LSERK steps
 (tests/test_oracle_curved.py).
 """
 from __future__ import annotations
@@ -243,6 +247,28 @@ class CurvedOracle(Oracle):
     def integrate(self, Q, e):
         op = self.ops[self.mesh.etype[e]]
         return (self.mesh.block(Q, e) @ op.V.T) @ (op.w * self.Jq[e])
+
+    def rhs_vjp(self, Q, Rbar):
+        """(dR/dQ)^T Rbar: the transpose of every step of rhs on curved
+        elements, with the pointwise metric in the volume term:
+          rbar_e = M_e^{-1} Rbar_e (M_e symmetric)
+          Fbar_d[v, q] = w_q J_q sum_k (dxi_k/dx_d)(q) sum_i (dphi_i/dxi_k)(q) rbar[v, i]
+          Ubar[:, q] = sum_d (dF_d/dU)^T Fbar_d[:, q];  Qbar_e += Ubar V
+        and the face part of oracle.adjoint with per-point w S and normals."""
+        from .adjoint import cs_jacobian, face_vjp
+        m = self.mesh
+        Q = np.asarray(Q, dtype=float)
+        Qbar = np.zeros_like(Q)
+        rbar = {e: self.apply_minv(e, m.block(Rbar, e)) for e in range(m.n_elems)}
+        for e in range(m.n_elems):
+            op = self.ops[m.etype[e]]
+            U = m.block(Q, e) @ op.V.T
+            Fbar = (op.w * self.Jq[e]) * np.einsum("qkd,kqi,vi->dvq", self.dxi_dx[e], op.G, rbar[e])
+            JF = cs_jacobian(lambda X: physical_flux(X, self.gamma), U)
+            Ubar = np.einsum("dvuq,dvq->uq", JF, Fbar)
+            Qbar[m.dof_off[e]:m.dof_off[e + 1]] += (Ubar @ op.V).ravel()
+        face_vjp(self, Q, rbar, Qbar)
+        return Qbar
 
     def volume(self, e):
         op = self.ops[self.mesh.etype[e]]

@@ -852,7 +852,6 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available on curved meshes");
   DG_CUDA(mesh->ensure_adjoint(0));
   dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0, 0};
   mesh->enqueue_vjp(va, stream);
@@ -897,7 +896,6 @@ extern "C" {
 dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
                              cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available on curved meshes");
   if (mesh->ns)
     return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp_noalloc covers the Euler equations (the viscous adjoint needs "
                                     "workspace that dg_rhs_vjp allocates); use dg_rhs_vjp");
@@ -965,7 +963,6 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
 dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
                       double dt) {
   if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the adjoint is not available on curved meshes");
   if (nsteps < 0 || ckpt_every < 0) return fail(DG_ERR_ARG, "nsteps and ckpt_every must be >= 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   return DG_OK;

@@ -1098,9 +1098,14 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
 // Phase A.  rk == 0: Rbar given.  rk == 1 (one reverse LSERK stage):
 // Kbar <- Kbar + b Qbar is the Rbar of this stage and Kbar <- a (Kbar + b Qbar)
 // is written back.
-__device__ __noinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
-                                           double* bufC, int lane) {
+template <bool CURVED>
+__device__ __noinline__ void element_vjp_a_t(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
+                                             double* bufC, int lane) {
   const TypeTab& T = c.tabs[c.slot_tab[s]];
+  // curved element: pointwise metric, 1/J_q (hex) or the dense M_e^{-1}
+  // (prism, pyramid) in place of the affine 1/J and diagonal M_ref^{-1}
+  const double* cblk = CURVED ? c.cpool + c.slot_coff[s] : nullptr;
+  const bool dense = CURVED && T.type != HEX;
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int64_t qoff = c.slot_qoff[s];
@@ -1117,8 +1122,9 @@ __device__ __noinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int6
     modal_to_nodal(c, T, bufC, bufA, bufG, lane);
     write_traces(c, T, s, bufA, c.T, 1.0, lane);
   }
-  // scaled cotangent of the modal residual
-  const double invJ = c.geo[s].invJ;
+  // scaled cotangent of the modal residual, rbar = M_e^{-1} Rbar (M_e symmetric)
+  const double invJ = CURVED ? 1.0 : c.geo[s].invJ;
+  double* rdst = dense ? bufC : bufG;   // bufC is free here (Q consumed above)
   for (int w = lane; w < 5 * nM; w += blockDim.x) {
     const int m = w % nM;
     double rb;
@@ -1128,10 +1134,27 @@ __device__ __noinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int6
     } else {
       rb = va.Rbar[qoff + w];
     }
-    bufG[w] = rb * dp[T.minv + m] * invJ;
+    rdst[w] = dense ? rb : rb * dp[T.minv + m] * invJ;
   }
   __syncthreads();
+  if (dense) {
+    const double* Md = cblk + 11 * nQ;
+    for (int m = lane; m < nM; m += blockDim.x) {
+      double acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+      for (int j = 0; j < nM; ++j) DG_FMA5(Md[(size_t)j * nM + m], bufC + j, nM, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufG[v * nM + m] = acc[v];
+    }
+    __syncthreads();
+  }
   modal_to_nodal(c, T, bufG, bufC, bufG + 5 * nQm, lane);  // Ybar in bufC
+  if (CURVED && !dense) {
+    // curved hexahedron: the forward's diag(1/J_q) before V^T, transposed
+    const double* iJ = cblk + 10 * nQ;
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufC[w] *= iJ[w % nQ];
+    __syncthreads();
+  }
   write_traces(c, T, s, bufC, c.Tv, -1.0, lane);           // seeds
   // Gbar_l = D_l Ybar (collocation derivative), D[i][i'] = Dt[i'][i]
   {
@@ -1169,13 +1192,26 @@ __device__ __noinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int6
 #pragma unroll
         for (int v = 0; v < 5; ++v) Gb[l][v] = bufG[(l * 5 + v) * nQ + q];
       double M[3][3];
-      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      if (CURVED) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) M[l][d] = cblk[(l * 3 + d) * nQ + q];
+      } else {
+        point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      }
       contravariant_vjp(U, M, c.gamma, Gb, Ub);
 #pragma unroll
       for (int v = 0; v < 5; ++v) Hb[v * nQ + q] = Ub[v];
     }
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
+                                              double* bufC, int lane) {
+  if (c.slot_coff && c.slot_coff[s] >= 0) element_vjp_a_t<true>(c, va, s, bufA, bufG, bufC, lane);
+  else element_vjp_a_t<false>(c, va, s, bufA, bufG, bufC, lane);
 }
 
 // Phase C: Qbar = V^T (Ubar + sum_f E_f^T Tbar_f); stored (rk == 0) or added
@@ -1721,6 +1757,7 @@ __global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va) {
 //   g(p) = wS_p (seed_own(p) - (Map seed_nb)(p))     (cotangent of F*)
 //   (Tbar-, Tbar+) = (dF*/dU-, dF*/dU+)^T g
 //   Tbar_own = Tbar-,  Tbar_nb = Map^T Tbar+        (written over the seeds)
+template <bool CURVED>
 __global__ void face_vjp_kernel(Ctx c) {
   extern __shared__ double sF[];
   const FaceBlock fb = c.fblocks[blockIdx.x];
@@ -1760,11 +1797,18 @@ __global__ void face_vjp_kernel(Ctx c) {
         g[v] -= b;
       }
     }
-    const TypeTab& T = c.tabs[R.owner_tab];
-    const double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    const bool cg = CURVED && R.cgeo >= 0;
+    const double wS = cg ? c.fgeo[R.cgeo + 3 * n2 + p]
+                         : c.dpool[c.tabs[R.owner_tab].fw + R.owner_lf * n2 + p] * R.S;
 #pragma unroll
     for (int v = 0; v < 5; ++v) g[v] *= wS;
     double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+    if (cg) {
+      const double* G = c.fgeo + R.cgeo;
+      nrm[0] = G[p];
+      nrm[1] = G[n2 + p];
+      nrm[2] = G[2 * n2 + p];
+    }
     double UbL[5] = {0, 0, 0, 0, 0}, UbR[5] = {0, 0, 0, 0, 0};
     if (c.flux == 0) flux_lf_vjp(UL, UR, nrm, gamma, g, UbL, UbR);
     else flux_roe_vjp(UL, UR, nrm, gamma, g, UbL, UbR);
@@ -2145,7 +2189,8 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel<false>, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_kernel<true>, fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(face_vjp_kernel, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_vjp_kernel<false>, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_vjp_kernel<true>, 2 * fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(elem_vjp_kernel<0>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem(elem_vjp_kernel<2>, 20 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
   if ((e = set_smem(elem_vjp_kernel<10>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
@@ -2190,7 +2235,8 @@ void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int w
 void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
   if (nblocks <= 0) return;
   int bytes = 2 * 32 * 5 * n * n * (int)sizeof(double);
-  face_vjp_kernel<<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  if (c.fgeo) face_vjp_kernel<true><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  else face_vjp_kernel<false><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
 }
 
 void launch_faces_ns(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st) {

@@ -221,3 +221,29 @@ def test_perturbed_meshes_are_curved():
         spread[t] = max(spread.get(t, 0.0), np.ptp(o.Jq[e]) / o.Jq[e].mean())
     assert spread[0] > 1e-2 and spread[1] > 1e-2 and spread[2] > 1e-2
     assert spread[3] < 1e-13
+
+
+@pytest.mark.parametrize("kind,m,N,flux", [("mixed", 2, 2, "lf"), ("four", 4, 1, "lf"), ("pyramid", 2, 2, "roe")])
+def test_adjoint_dot_product(kind, m, N, flux):
+    """<J v, w> = <v, J^T w> with J v by a complex step through the curved
+    residual (exact to rounding) and J^T w from rhs_vjp."""
+    from oracle.adjoint import rhs_jvp
+    o = curved(kind, m, N, flux=flux)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
+    scale = np.abs(Q).max()
+    v = di.random_vector(Q.size, seed=21) * scale
+    w = di.random_vector(Q.size, seed=22)
+    lhs = rhs_jvp(o, Q, v) @ w
+    rhs = v @ o.rhs_vjp(Q, w)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+def test_rk_adjoint_dot_product():
+    from oracle.adjoint import rk_jvp, rk_vjp
+    o = curved("mixed", 2, 2)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
+    v = di.random_vector(Q.size, seed=23) * np.abs(Q).max()
+    w = di.random_vector(Q.size, seed=24)
+    lhs = rk_jvp(o, Q, 1e-3, 2, v) @ w
+    rhs = v @ rk_vjp(o, Q, 1e-3, 2, w)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
