@@ -33,6 +33,8 @@ normal its direction.  The neighbour's reference coordinates of each owner
 face point are found by Newton's method on the neighbour's map.
 
 The adjoint (rhs_vjp) is the transpose of each of these steps.
+CurvedNSOracle carries the Navier-Stokes residual with BR1 lifting of
+oracle.navier_stokes onto curved elements (pointwise metric and normals).
 
 Parity: pinned by reduction to the affine oracle on affine meshes, the
 divergence theorem on every element, the total volume of the box, free-stream
@@ -49,8 +51,9 @@ from scipy.linalg import cho_factor, cho_solve
 
 from .dg import Oracle
 from .elements import FACES, HEX, PRISM, PYR, REF_VERTS, TET, eval_basis, n_modes
-from .euler import physical_flux
+from .euler import physical_flux, riemann
 from .mesh import OracleMesh
+from .navier_stokes import NSOracle, _cs, primitive, viscous_flux
 from .quadrature import face_rule
 
 H_CS = 1e-30
@@ -275,4 +278,116 @@ class CurvedOracle(Oracle):
         return float(op.w @ self.Jq[e])
 
 
-__all__ = ["CurvedOracle", "CurvedOracleMesh", "curved_from_box", "shape_functions", "HEX", "PRISM", "PYR", "TET"]
+class CurvedNSOracle(NSOracle, CurvedOracle):
+    """Navier-Stokes residual with BR1 lifting (oracle.navier_stokes) on a
+    CurvedOracleMesh: the lifting's volume term and the total flux use the
+    pointwise metric, w_q J_q as the volume weight, and the face terms the
+    per-point normals (the lifting face term multiplies W* by the normal at
+    each face point before testing, the central viscous flux takes its normal
+    component per point); M_e^{-1} is the curved element's dense inverse."""
+
+    def lifting(self, Q, e, wstar):
+        m = self.mesh
+        op = self.ops[m.etype[e]]
+        W = primitive(m.block(Q, e) @ op.V.T, self.gamma)               # [5, nQ]
+        gx = np.einsum("qkd,kqi->dqi", self.dxi_dx[e], op.G)             # d phi_i / d x_d at q
+        vol = np.einsum("dqi,vq->dvi", gx, (op.w * self.Jq[e]) * W)
+        surf = np.zeros_like(vol)
+        for f, side in m.elem_faces[e]:
+            phi0, phi1, _, nrm = self.face_data(f)
+            phi, sgn = (phi0, 1.0) if side == 0 else (phi1, -1.0)
+            for d in range(3):
+                surf[d] = surf[d] + sgn * ((nrm[d] * wstar[f]) @ phi)
+        return np.stack([self.apply_minv(e, surf[d] - vol[d]) for d in range(3)])
+
+    def ns_face_flux(self, Q, f, G):
+        m = self.mesh
+        e0, _, e1, _ = m.faces[f]
+        phi0, phi1, wS, nrm = self.face_data(f)
+        UL = m.block(Q, e0) @ phi0.T
+        UR = m.block(Q, e1) @ phi1.T
+        gL = G[e0] @ phi0.T
+        gR = G[e1] @ phi1.T
+        Fv = 0.5 * (viscous_flux(UL, gL, self.gamma, self.mu, self.Pr)
+                    + viscous_flux(UR, gR, self.gamma, self.mu, self.Pr))
+        Fvn = np.einsum("dp,dvp->vp", nrm, Fv)
+        return wS * (riemann(self.flux, UL, UR, nrm, self.gamma) - Fvn)
+
+    def ns_volume_term(self, Q, e, G):
+        m = self.mesh
+        op = self.ops[m.etype[e]]
+        U = m.block(Q, e) @ op.V.T
+        gradW = G[e] @ op.V.T
+        F = physical_flux(U, self.gamma) - viscous_flux(U, gradW, self.gamma, self.mu, self.Pr)
+        Fc = np.einsum("qkd,dvq->kvq", self.dxi_dx[e], F)
+        return np.einsum("kqi,kvq->vi", op.G, (op.w * self.Jq[e]) * Fc)
+
+    def rhs_vjp(self, Q, Rbar):
+        """Qbar = (dR/dQ)^T Rbar: the steps of NSOracle.rhs_vjp with the
+        pointwise metric and per-point normals."""
+        m = self.mesh
+        gam, mu, Pr = self.gamma, self.mu, self.Pr
+        Q = np.asarray(Q, dtype=float)
+        Qbar = np.zeros_like(Q)
+        E, F = m.n_elems, len(m.faces)
+        wstar = {f: self.face_wstar(Q, f) for f in range(F)}
+        G = {e: self.lifting(Q, e, wstar) for e in range(E)}
+        rbar = {e: self.apply_minv(e, m.block(Rbar, e)) for e in range(E)}
+        Gbar = {e: np.zeros((3, 5, m.nM[e])) for e in range(E)}
+        Wsbar = {f: np.zeros_like(wstar[f]) for f in range(F)}
+
+        def add(e, vals):
+            Qbar[m.dof_off[e]:m.dof_off[e + 1]] += vals.ravel()
+
+        def vf_u(g):
+            return lambda X: viscous_flux(X, g, gam, mu, Pr)
+
+        def vf_g(U):
+            return lambda Y: viscous_flux(U, Y, gam, mu, Pr)
+
+        for e in range(E):
+            op = self.ops[m.etype[e]]
+            U = m.block(Q, e) @ op.V.T
+            gW = G[e] @ op.V.T
+            Fbar = (op.w * self.Jq[e]) * np.einsum("qkd,kqi,vi->dvq", self.dxi_dx[e], op.G, rbar[e])
+            JU = _cs(lambda X: physical_flux(X, gam), U) - _cs(vf_u(gW), U)
+            JG = _cs(vf_g(U), gW)
+            add(e, np.einsum("dvuq,dvq->uq", JU, Fbar) @ op.V)
+            Gbar[e] += -np.einsum("dvxyq,dvq->xyq", JG, Fbar) @ op.V
+        for f, (e0, _, e1, _) in enumerate(m.faces):
+            phi0, phi1, wS, nrm = self.face_data(f)
+            UL, UR = m.block(Q, e0) @ phi0.T, m.block(Q, e1) @ phi1.T
+            gL, gR = G[e0] @ phi0.T, G[e1] @ phi1.T
+            Fsbar = wS * (-(rbar[e0] @ phi0.T) + rbar[e1] @ phi1.T)
+            JL = _cs(lambda X: riemann(self.flux, X, UR, nrm, gam), UL)
+            JR = _cs(lambda X: riemann(self.flux, UL, X, nrm, gam), UR)
+            Fvbar = -0.5 * nrm[:, None, :] * Fsbar[None]                         # [3, 5, P]
+            ULbar = np.einsum("vup,vp->up", JL, Fsbar) + np.einsum("dvup,dvp->up", _cs(vf_u(gL), UL), Fvbar)
+            URbar = np.einsum("vup,vp->up", JR, Fsbar) + np.einsum("dvup,dvp->up", _cs(vf_u(gR), UR), Fvbar)
+            add(e0, ULbar @ phi0)
+            add(e1, URbar @ phi1)
+            Gbar[e0] += np.einsum("dvxyp,dvp->xyp", _cs(vf_g(UL), gL), Fvbar) @ phi0
+            Gbar[e1] += np.einsum("dvxyp,dvp->xyp", _cs(vf_g(UR), gR), Fvbar) @ phi1
+        for e in range(E):
+            op = self.ops[m.etype[e]]
+            U = m.block(Q, e) @ op.V.T
+            sbar = np.stack([self.apply_minv(e, Gbar[e][d]) for d in range(3)])
+            gx = np.einsum("qkd,kqi->dqi", self.dxi_dx[e], op.G)
+            Wbar = -(op.w * self.Jq[e]) * np.einsum("dqi,dvi->vq", gx, sbar)
+            JW = _cs(lambda X: primitive(X, gam), U)
+            add(e, np.einsum("wuq,wq->uq", JW, Wbar) @ op.V)
+            for f, side in m.elem_faces[e]:
+                phi0, phi1, _, nrm = self.face_data(f)
+                phi, sgn = (phi0, 1.0) if side == 0 else (phi1, -1.0)
+                for d in range(3):
+                    Wsbar[f] += sgn * nrm[d] * (sbar[d] @ phi.T)
+        for f, (e0, _, e1, _) in enumerate(m.faces):
+            phi0, phi1, wS, _ = self.face_data(f)
+            UL, UR = m.block(Q, e0) @ phi0.T, m.block(Q, e1) @ phi1.T
+            a = 0.5 * wS * Wsbar[f]
+            add(e0, np.einsum("wup,wp->up", _cs(lambda X: primitive(X, gam), UL), a) @ phi0)
+            add(e1, np.einsum("wup,wp->up", _cs(lambda X: primitive(X, gam), UR), a) @ phi1)
+        return Qbar
+
+
+__all__ = ["CurvedOracle", "CurvedNSOracle", "CurvedOracleMesh", "curved_from_box", "shape_functions", "HEX", "PRISM", "PYR", "TET"]

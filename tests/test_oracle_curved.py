@@ -247,3 +247,96 @@ def test_rk_adjoint_dot_product():
     lhs = rk_jvp(o, Q, 1e-3, 2, v) @ w
     rhs = v @ rk_vjp(o, Q, 1e-3, 2, w)
     assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+# ---------------------------------------------------------------- Navier-Stokes on curved elements
+NS_MU, NS_PR = 0.05, 0.72
+
+
+def curved_ns(kind, m, N, amp=0.1, mu=NS_MU, flux="lf", reorder=None):
+    from oracle.curved import CurvedNSOracle
+    box = di.perturb_vertices(di.box_mesh(m, kind, seed=1), amp)
+    if reorder is not None:
+        box = di.reorder_vertices(box, seed=reorder)
+    return CurvedNSOracle(curved_from_box(box, N), flux=flux, mu=mu, Pr=NS_PR)
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("four", 4, 2)])
+def test_ns_affine_limit(kind, m, N):
+    from oracle.curved import CurvedNSOracle
+    from oracle.navier_stokes import NSOracle
+    box = di.box_mesh(m, kind, seed=1)
+    oc = CurvedNSOracle(curved_from_box(box, N), mu=NS_MU, Pr=NS_PR)
+    oa = NSOracle(from_box(box, N), mu=NS_MU, Pr=NS_PR)
+    Q = oa.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
+    R, Rc = oa.rhs(Q), oc.rhs(Q)
+    G = oa.lifted_gradient(Q)
+    for e in range(0, oa.mesh.n_elems, 2):
+        vol = oa.apply_minv(e, oa.ns_volume_term(Q, e, G))
+        sl = slice(oa.mesh.dof_off[e], oa.mesh.dof_off[e + 1])
+        assert np.abs(Rc[sl] - R[sl]).max() < 1e-13 * np.abs(vol).max()
+
+
+def test_ns_mu_zero_is_curved_euler():
+    o = curved_ns("mixed", 3, 3, mu=0.0)
+    oe = curved("mixed", 3, 3)
+    Q = oe.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
+    assert np.abs(o.rhs(Q) - oe.rhs(Q)).max() <= 1e-14 * np.abs(oe.rhs(Q)).max()
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("four", 4, 2), ("pyramid", 2, 2)])
+def test_ns_free_stream_and_conservation(kind, m, N):
+    o = curved_ns(kind, m, N)
+    Qf = o.project(lambda x: np.tile(U_CONST[:, None], (1, x.shape[0])))
+    assert np.abs(o.rhs(Qf)).max() < 1e-12
+    R = o.rhs(o.project(di.tgv_state))
+    tot = sum(o.integrate(R, e) for e in range(o.mesh.n_elems))
+    scale = max(np.abs(o.integrate(np.abs(R), e)).max() for e in range(o.mesh.n_elems))
+    assert np.abs(tot).max() < 1e-13 * scale * o.mesh.n_elems
+
+
+# a primitive state linear in x (rho, u, v, w, p) and its constant gradient
+LIN = np.array([[1.0, 0.10, -0.05, 0.02],
+                [0.3, 0.20, 0.10, -0.10],
+                [-0.2, 0.05, 0.15, 0.07],
+                [0.1, -0.12, 0.04, 0.09],
+                [70.0, 1.0, -2.0, 0.5]])
+
+
+def lin_state(x, gamma=1.4):
+    rho, u, v, w, p = LIN[:, :1] + LIN[:, 1:] @ x.T
+    return np.stack([rho, rho * u, rho * v, rho * w, p / (gamma - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+@pytest.mark.parametrize("kind,N", [("hex", 3), ("mixed", 3), ("prism", 3), ("pyramid", 3)])
+def test_ns_lifting_exact_for_linear_W(kind, N):
+    """The curved element maps lie in every type's modal space, so at N = 3
+    the conservative state of a W linear in x (cubic in x) is represented
+    exactly; BR1 lifting then returns grad W on elements away from the
+    periodic seam (where the non-periodic W jumps)."""
+    m = 4
+    o = curved_ns(kind, m, N)
+    Q = o.project(lin_state)
+    h = 2 * np.pi / m
+    idx = np.floor((o.mesh.centroid + np.pi) / h).astype(int)
+    elems = np.nonzero(np.all((idx >= 1) & (idx <= m - 2), axis=1))[0]
+    assert len(elems) > 0
+    G = o.lifted_gradient(Q, elems)
+    exact = LIN[:, 1:].T
+    wmax = np.abs(LIN[:, 0]) + np.pi * np.abs(LIN[:, 1:]).sum(axis=1)
+    for e in elems:
+        gq = G[e] @ o.ops[o.mesh.etype[e]].V.T
+        err = np.abs(gq - exact[:, :, None]).max(axis=(0, 2))
+        assert np.all(err < 5e-12 * wmax), (e, err)
+
+
+@pytest.mark.parametrize("kind,m,N,flux", [("mixed", 2, 2, "lf"), ("four", 4, 1, "roe")])
+def test_ns_adjoint_dot_product(kind, m, N, flux):
+    from oracle.adjoint import rhs_jvp
+    o = curved_ns(kind, m, N, flux=flux)
+    Q = o.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.05))
+    v = di.random_vector(Q.size, seed=25) * np.abs(Q).max()
+    w = di.random_vector(Q.size, seed=26)
+    lhs = rhs_jvp(o, Q, v) @ w
+    rhs = v @ o.rhs_vjp(Q, w)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
