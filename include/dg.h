@@ -91,11 +91,12 @@ typedef enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 } dg_physics;
  *                   Algorithm 1 per quadrature point in device memory; a
  *                   curved hexahedron applies M^{-1} V^T as V^T diag(1/J)
  *                   (exact: its V is square with V^T W V = I).  Affine
- *                   elements of such a mesh take the affine path.  Curved
- *                   meshes support every call for the Euler equations
- *                   (residual, time stepping, projection and adjoints);
- *                   dg_set_physics(DG_NAVIER_STOKES) returns
- *                   DG_ERR_UNSUPPORTED on them. */
+ *                   elements of such a mesh take the affine path.  Every
+ *                   call supports curved meshes, for the Euler and the
+ *                   Navier-Stokes equations (the BR1 lifting then uses the
+ *                   pointwise metric and the normals at each face point).
+ *                   All instances of a batch must request the same
+ *                   geometry kind (DG_ERR_ARG otherwise). */
 typedef enum { DG_GEOM_AFFINE = 0, DG_GEOM_VERTEX = 1 } dg_geometry;
 
 /* Mesh description, caller-owned, read only during dg_mesh_create.

@@ -120,7 +120,7 @@ struct dg_mesh {
   int64_t *d_elem_of_slot = nullptr, *d_elem_qoff = nullptr, *d_elem_voff = nullptr;
   dgk::ElemGeo* d_geo = nullptr;
   int64_t* d_slot_coff = nullptr;
-  double *d_cpool = nullptr, *d_fgeo = nullptr;
+  double *d_cpool = nullptr, *d_fgeo = nullptr, *d_snrm = nullptr;
   double* d_H = nullptr;
   double* d_T = nullptr;
   double* d_Tv = nullptr;       // adjoint face buffer
@@ -209,6 +209,7 @@ struct dg_mesh {
     c.slot_coff = h.n_curved ? d_slot_coff : nullptr;
     c.cpool = d_cpool;
     c.fgeo = d_fgeo;
+    c.snrm = d_snrm;
     c.ns = ns;
     c.mu = mu;
     c.kappa = ns ? mu * gamma / ((gamma - 1.0) * Pr) : 0.0;
@@ -279,17 +280,17 @@ struct dg_mesh {
       it->tabs.push_back((int)t);
     }
     for (auto& G : groups) {
-      cudaError_t e = dgk::element_kernel_attributes(G.n * G.n * G.n, G.wpb, &G.bpsm);
+      cudaError_t e = dgk::element_kernel_attributes(G.n * G.n * G.n, G.wpb, &G.bpsm, h.n_curved > 0);
       if (e != cudaSuccess) return e;
       if (G.bpsm < 1) G.bpsm = 1;
       if (ns) {
-        e = dgk::element_kernel_attributes_ns(G.n * G.n * G.n, G.wpb, &G.bpsm_ns);
+        e = dgk::element_kernel_attributes_ns(G.n * G.n * G.n, G.wpb, &G.bpsm_ns, h.n_curved > 0);
         if (e != cudaSuccess) return e;
         if (G.bpsm_ns < 1) G.bpsm_ns = 1;
       }
     }
     // restore the mesh-wide attributes used by the static and naive launches
-    cudaError_t e = dgk::element_kernel_attributes(nQmax, wpb, &blocks_per_sm);
+    cudaError_t e = dgk::element_kernel_attributes(nQmax, wpb, &blocks_per_sm, h.n_curved > 0);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     std::vector<double> w(weight, weight + dgk::kMaxTabs);
@@ -541,7 +542,7 @@ struct dg_mesh {
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks_static, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
-                    d_slot_coff, d_cpool, d_fgeo};
+                    d_slot_coff, d_cpool, d_fgeo, d_snrm};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -660,7 +661,7 @@ dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t 
     return cuda_fail(e, what);
   };
   cudaError_t e;
-  if ((e = dgk::element_kernel_attributes(m->nQmax, m->wpb, &m->blocks_per_sm)) != cudaSuccess) return fail_cuda(e, "kernel attributes");
+  if ((e = dgk::element_kernel_attributes(m->nQmax, m->wpb, &m->blocks_per_sm, m->h.n_curved > 0)) != cudaSuccess) return fail_cuda(e, "kernel attributes");
   if (m->blocks_per_sm < 1) m->blocks_per_sm = 1;
   std::vector<int> slot_tab(h.slot_tab);
   if ((e = upload(&m->d_dpool, h.tables.dpool)) != cudaSuccess) return fail_cuda(e, "upload tables");
@@ -679,6 +680,7 @@ dg_status create_device_mesh(dg_mesh* m, const dg_mesh_desc* desc, cudaStream_t 
     if ((e = upload(&m->d_slot_coff, h.slot_coff)) != cudaSuccess) return fail_cuda(e, "upload geometry");
     if ((e = upload(&m->d_cpool, h.cpool)) != cudaSuccess) return fail_cuda(e, "upload geometry");
     if ((e = upload(&m->d_fgeo, h.fgeo)) != cudaSuccess) return fail_cuda(e, "upload geometry");
+    if ((e = upload(&m->d_snrm, h.snrm)) != cudaSuccess) return fail_cuda(e, "upload geometry");
   }
   if ((e = upload(&m->d_fnrm, h.slot_fnrm)) != cudaSuccess) return fail_cuda(e, "upload geometry");
   if ((e = upload(&m->d_faces, h.faces)) != cudaSuccess) return fail_cuda(e, "upload faces");
@@ -1064,7 +1066,6 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
   if (physics == DG_NAVIER_STOKES) {
-    if (mesh->h.n_curved) return fail(DG_ERR_UNSUPPORTED, "the Navier-Stokes path is not available on curved meshes");
     if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(DG_ERR_ARG, "mu must be finite and >= 0");
     if (!(Pr > 0.0) || !std::isfinite(Pr)) return fail(DG_ERR_ARG, "Pr must be finite and > 0");
     const size_t hb = sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.h_total);
@@ -1072,7 +1073,7 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
     if (!mesh->d_Unod && cudaMalloc(&mesh->d_Unod, hb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     if (!mesh->d_L && cudaMalloc(&mesh->d_L, tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     if (!mesh->d_Vt && cudaMalloc(&mesh->d_Vt, 3 * tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
-    DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns));
+    DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns, mesh->h.n_curved > 0));
     if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;
     mesh->mu = mu;
     mesh->Pr = Pr;
@@ -1169,7 +1170,7 @@ dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
   mesh->wpb = warps;
   for (int t = 0; t < dgk::kMaxTabs; ++t) mesh->tab_wpb[t] = warps;
   if (mesh->ns) {
-    DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns));
+    DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns, mesh->h.n_curved > 0));
     if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;
   }
   DG_CUDA(mesh->build_groups());

@@ -1175,6 +1175,26 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   M.n_perm = (int)perm_ids.size();
   M.n_dense = (int)dense_ids.size();
   M.t_total = F * 2 * 5 * (int64_t)n2;
+  // per-side normals at the side's own points (curved geometry requested):
+  // the owner's normal at its points; the neighbour's is the negated owner
+  // normal at the matching owner point (a permutation), or the constant
+  // negated normal of a planar triangle (interpolating maps)
+  M.snrm.clear();
+  if (in.geometry == 1) {
+    M.snrm.assign((size_t)(3 * (M.t_total / 5)), 0.0);
+    for (int64_t f = 0; f < F; ++f) {
+      const dgk::FaceRec& R = M.faces[f];
+      double* N0 = M.snrm.data() + 3 * (R.toff / 5);
+      double* N1 = M.snrm.data() + 3 * ((R.toff + 5 * (int64_t)n2) / 5);
+      for (int p = 0; p < n2; ++p)
+        for (int d = 0; d < 3; ++d)
+          N0[d * n2 + p] = R.cgeo >= 0 ? M.fgeo[(size_t)R.cgeo + (size_t)d * n2 + p] : R.nrm[d];
+      for (int p = 0; p < n2; ++p) {
+        const int q = R.map >= 0 ? M.perms[(size_t)R.map + p] : p;
+        for (int d = 0; d < 3; ++d) N1[d * n2 + q] = R.map >= 0 ? -N0[d * n2 + p] : -N0[d * n2];
+      }
+    }
+  }
   for (int64_t s = 0; s < E; ++s)
     for (int lf = 0; lf < kNumFaces[M.slot_type[s]]; ++lf)
       if (M.slot_ftoff[(size_t)s * 6 + lf] < 0) { *err = "internal: unassigned face"; return -1; }
@@ -1268,6 +1288,11 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
     M.dense.insert(M.dense.end(), Mi.dense.begin(), Mi.dense.end());
     M.cpool.insert(M.cpool.end(), Mi.cpool.begin(), Mi.cpool.end());
     M.fgeo.insert(M.fgeo.end(), Mi.fgeo.begin(), Mi.fgeo.end());
+    if (Mi.snrm.empty() != (i == 0 ? Mi.snrm.empty() : M.snrm.empty())) {
+      *err = "all instances of a batch must request the same geometry kind";
+      return -1;
+    }
+    M.snrm.insert(M.snrm.end(), Mi.snrm.begin(), Mi.snrm.end());
     M.n_curved += Mi.n_curved;
     M.n_curved_faces += Mi.n_curved_faces;
     for (dgk::FaceRec R : Mi.faces) {

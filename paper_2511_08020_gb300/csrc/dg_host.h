@@ -73,6 +73,10 @@ struct HostMesh {
   // the double offset of a face's block
   std::vector<double> fgeo;
   int64_t n_curved_faces = 0;
+  // meshes built with the curved geometry: every face side's outward unit
+  // normal at its own face points, [3][n^2] at 3 * (side trace offset / 5)
+  // (the Navier-Stokes lifting multiplies W* by it point by point)
+  std::vector<double> snrm;
   std::vector<int64_t> slot_ftoff;           // [slot][6] trace offset of (face, own side)
   std::vector<double> slot_fnrm;             // [slot][6][3] outward unit normal of each local face
                                              // (the owner's normal, negated on the neighbour side)

@@ -602,6 +602,8 @@ __device__ __noinline__ bool nodal_to_modal_t(const Ctx& c, const TypeTab& T, do
       double acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll 4
       for (int j = 0; j < nM; ++j) DG_FMA5(Mc[(size_t)j * nM], ep.rbuf + j, nM, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] *= ep.scale;
       bad |= epilogue_mode(ep, nM, mode, acc);
     }
   }
@@ -609,9 +611,13 @@ __device__ __noinline__ bool nodal_to_modal_t(const Ctx& c, const TypeTab& T, do
   return bad;
 }
 
+// ANY: the launch may meet curved elements (their variants are compiled into
+// the kernel only then, so affine launches keep the affine register budget).
+template <bool ANY>
 __device__ __forceinline__ bool nodal_to_modal(const Ctx& c, const TypeTab& T, double* bufA, double* bufB, int lane,
                                                const Epilogue& ep) {
-  return ep.Md ? nodal_to_modal_t<true>(c, T, bufA, bufB, lane, ep) : nodal_to_modal_t<false>(c, T, bufA, bufB, lane, ep);
+  return (ANY && ep.Md) ? nodal_to_modal_t<true>(c, T, bufA, bufB, lane, ep)
+                        : nodal_to_modal_t<false>(c, T, bufA, bufB, lane, ep);
 }
 
 // Values of the nodal field `src` [5][nQ] on the element's own face points,
@@ -766,9 +772,10 @@ __device__ __noinline__ void element_forward_t(const Ctx& c, const TypeTab& T, i
   __syncthreads();
 }
 
+template <bool ANY>
 __device__ __forceinline__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
                                                 int lane) {
-  if (c.slot_coff && c.slot_coff[s] >= 0) element_forward_t<true>(c, T, s, bufA, bufG, lane);
+  if (ANY && c.slot_coff[s] >= 0) element_forward_t<true>(c, T, s, bufA, bufG, lane);
   else element_forward_t<false>(c, T, s, bufA, bufG, lane);
 }
 
@@ -814,32 +821,38 @@ __device__ __noinline__ void element_lift_t(const Ctx& c, const TypeTab& T, int6
   __syncthreads();
 }
 
+template <bool ANY>
 __device__ __forceinline__ void element_lift(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
                                              int lane, const double* faces, double sign,
                                              const double* pscale = nullptr) {
-  if (pscale) element_lift_t<true>(c, T, s, bufA, bufG, lane, faces, sign, pscale);
+  if (ANY && pscale) element_lift_t<true>(c, T, s, bufA, bufG, lane, faces, sign, pscale);
   else element_lift_t<false>(c, T, s, bufA, bufG, lane, faces, sign, nullptr);
 }
 
 // BR1 lifting face term: bufA += sum_f coef_f E_f^T L_f with coef_f =
 // sign n_d(f), n(f) the element's outward unit normal of local face f and
 // L_f the face values at its own points (staged through bufS).
-__device__ __noinline__ void lift_scaled(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufS,
-                                         int lane, const double* faces, int d, double sign) {
+template <bool CURVED>
+__device__ __noinline__ void lift_scaled_t(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufS,
+                                           int lane, const double* faces, int d, double sign) {
   const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
   const double* dp = c.dpool;
   const int64_t* ft = c.slot_ftoff + s * 6;
   {
+    // curved: the normal varies over the face; it multiplies the staged
+    // face values point by point (c.snrm holds each side's own normals)
     const int per = 5 * n2;
     for (int w = lane; w < nf * per; w += blockDim.x) {
       int lf = w / per, r = w - lf * per;
-      bufS[w] = faces[ft[lf] + r];
+      double v = faces[ft[lf] + r];
+      if (CURVED) v *= sign * c.snrm[3 * (ft[lf] / 5) + d * n2 + r % n2];
+      bufS[w] = v;
     }
   }
   __syncthreads();
   double coef[6];
 #pragma unroll
-  for (int lf = 0; lf < 6; ++lf) coef[lf] = lf < nf ? sign * c.fnrm[(s * 6 + lf) * 3 + d] : 0.0;
+  for (int lf = 0; lf < 6; ++lf) coef[lf] = lf < nf ? (CURVED ? 1.0 : sign * c.fnrm[(s * 6 + lf) * 3 + d]) : 0.0;
   for (int o = lane; o < nQ; o += blockDim.x) {
     int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
     double h[5];
@@ -865,8 +878,11 @@ __device__ __noinline__ void lift_scaled(const Ctx& c, const TypeTab& T, int64_t
 // then the total flux F_e(U) - F_v(U, grad W) at the volume points and
 // H = sum_l D_l^T G_l(F) as in the Euler forward phase.
 // smem: bufU [5 nQ] | bufDW [3][5][nQ] | bufG [15 nQ] | bufA [5 nQ].
-__device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, int64_t s, double* smem, int lane) {
+template <bool CURVED>
+__device__ __noinline__ void element_ns_volume_t(const Ctx& c, const TypeTab& T, int64_t s, double* smem, int lane) {
   const int n = T.n, nQ = T.nQ, n2 = n * n;
+  // curved element: pointwise metric [9][nQ], J, 1/J, (prism, pyramid) dense M_e^{-1}
+  const double* cblk = CURVED ? c.cpool + c.slot_coff[s] : nullptr;
   const int nQm = c.nQmax;
   double* bufU = smem;
   double* bufDW = smem + 5 * nQm;
@@ -898,8 +914,37 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
     for (int v = 0; v < 5; ++v) bufA[v * nQ + q] = W[v];
   }
   __syncthreads();
+  if (CURVED) {
+    // pointwise metric: Hd = sum_l D_l^T (M_q[l][d] W), one full set of
+    // directional passes per direction d
+    for (int d = 0; d < 3; ++d) {
+      for (int q = lane; q < nQ; q += blockDim.x) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          const double f = cblk[(l * 3 + d) * nQ + q];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) bufG[(l * 5 + v) * nQ + q] = f * bufA[v * nQ + q];
+        }
+      }
+      __syncthreads();
+      for (int o = lane; o < nQ; o += blockDim.x) {
+        int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+        const double* G0 = bufG + jk;
+        const double* G1 = bufG + 5 * nQ + i * n2 + k;
+        const double* G2 = bufG + 10 * nQ + i * n2 + j * n;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[i * n + m], G0 + m * n2, nQ, acc);
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[j * n + m], G1 + m * n, nQ, acc);
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[k * n + m], G2 + m, nQ, acc);
+        double* Hd = bufDW + d * 5 * nQ + o;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Hd[v * nQ] = acc[v];
+      }
+      __syncthreads();
+    }
+  }
   const unsigned nz = kMetricMask[T.type];
-  for (int kr = 0; kr < 3; ++kr) {
+  for (int kr = 0; kr < (CURVED ? 0 : 3); ++kr) {
     const bool u0 = (nz >> (0 * 3 + kr)) & 1u, u1 = (nz >> (1 * 3 + kr)) & 1u, u2 = (nz >> (2 * 3 + kr)) & 1u;
     for (int q = lane; q < nQ; q += blockDim.x) {
       const double* wa = dp + T.wA + q * 9;
@@ -943,18 +988,27 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
       for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = Hd[w];
     }
     __syncthreads();
-    lift_scaled(c, T, s, bufA, bufG, lane, c.L, d, -1.0);
+    lift_scaled_t<CURVED>(c, T, s, bufA, bufG, lane, c.L, d, -1.0);
     double* dW = bufDW + d * 5 * nQ;
     if (T.type == HEX) {
-      // V is square for the hexahedron, so V M_ref^{-1} V^T = W^{-1}: the
+      // V is square for the hexahedron, so V M^{-1} V^T = (W J)^{-1}: the
       // projection onto the modal space is the identity at the nodes
       const double* wq = dp + T.W;
-      for (int w = lane; w < 5 * nQ; w += blockDim.x) dW[w] = -g.invJ * bufA[w] / wq[w % nQ];
+      if (CURVED) {
+        const double* iJ = cblk + 10 * nQ;
+        for (int w = lane; w < 5 * nQ; w += blockDim.x) dW[w] = -iJ[w % nQ] * bufA[w] / wq[w % nQ];
+      } else {
+        for (int w = lane; w < 5 * nQ; w += blockDim.x) dW[w] = -g.invJ * bufA[w] / wq[w % nQ];
+      }
       __syncthreads();
     } else {
       double* sG = bufG + 5 * nQ;
-      Epilogue ep{Epilogue::kStore, true, -g.invJ, sG, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
-      nodal_to_modal(c, T, bufA, bufG, lane, ep);
+      Epilogue ep{Epilogue::kStore, true, CURVED ? -1.0 : -g.invJ, sG, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+      if (CURVED) {
+        ep.Md = cblk + 11 * nQ;
+        ep.rbuf = bufG + 10 * nQ;
+      }
+      nodal_to_modal<CURVED>(c, T, bufA, bufG, lane, ep);
       modal_to_nodal(c, T, sG, dW, bufG, lane);
     }
     write_traces(c, T, s, dW, c.Vt, 1.0, lane, 3, (int64_t)d * 5 * n2);
@@ -975,7 +1029,14 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
     double Fv[3][5];
     viscous_flux(W, gr, c.mu, c.kappa, Fv);
     double M[3][3];
-    point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+    if (CURVED) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd) M[l][dd] = cblk[(l * 3 + dd) * nQ + q];
+    } else {
+      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+    }
     const double u = W[1], v = W[2], w = W[3], p = W[4], Ep = U[4] + p;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
@@ -1007,23 +1068,29 @@ __device__ __noinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, i
   __syncthreads();
 }
 
+template <bool ANY>
+__device__ __forceinline__ void element_ns_volume(const Ctx& c, const TypeTab& T, int64_t s, double* smem, int lane) {
+  if (ANY && c.slot_coff[s] >= 0) element_ns_volume_t<true>(c, T, s, smem, lane);
+  else element_ns_volume_t<false>(c, T, s, smem, lane);
+}
+
 // One element at slot s.  smem per block: bufA [5 nQmax], bufG [15 nQmax]
 // (40 nQmax for the Navier-Stokes volume phase).
-template <int MODE>
+template <int MODE, bool ANY>
 __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& io, int64_t s, double* bufA,
                                                 double* bufG, int lane) {
   const TypeTab& T = c.tabs[c.slot_tab[s]];
   const int nM = T.nM, nQ = T.nQ;
   const int64_t qoff = c.slot_qoff[s];
   if (MODE == kNsVolume) {
-    element_ns_volume(c, T, s, bufA, lane);
+    element_ns_volume<ANY>(c, T, s, bufA, lane);
     return;
   }
   if (MODE == kFwd) {
     const double* Q = io.Qin + qoff;
     for (int w = lane; w < 5 * nM; w += blockDim.x) bufG[w] = Q[w];
     __syncthreads();
-    element_forward(c, T, s, bufA, bufG, lane);
+    element_forward<ANY>(c, T, s, bufA, bufG, lane);
     return;
   }
   if (MODE == kEval) {
@@ -1040,7 +1107,7 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
   // then for prism / pyramid the dense M_e^{-1}); the affine scale 1/J_e and
   // the diagonal M_ref^{-1} are replaced by diag(1/J_q) before V^T (hex) or by
   // M_e^{-1} after it (prism, pyramid).  Tetrahedra are always affine.
-  const int64_t coff = c.slot_coff ? c.slot_coff[s] : -1;
+  const int64_t coff = ANY ? c.slot_coff[s] : -1;
   const double* cblk = coff >= 0 ? c.cpool + coff : nullptr;
   const bool dense = cblk && T.type != HEX;
   if (MODE == kProject) {
@@ -1059,10 +1126,10 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
       ep.Md = cblk + 11 * nQ;
       ep.rbuf = bufG + 5 * nQ;
     }
-    nodal_to_modal(c, T, bufA, bufG, lane, ep);
+    nodal_to_modal<ANY>(c, T, bufA, bufG, lane, ep);
     return;
   }
-  element_lift(c, T, s, bufA, bufG, lane, c.T, -1.0, (cblk && T.type == HEX) ? cblk + 10 * nQ : nullptr);
+  element_lift<ANY>(c, T, s, bufA, bufG, lane, c.T, -1.0, (cblk && T.type == HEX) ? cblk + 10 * nQ : nullptr);
   const double invJ = cblk ? 1.0 : c.geo[s].invJ;
   if (MODE == kBwdRhs) {
     Epilogue ep{Epilogue::kStore, true, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
@@ -1070,7 +1137,7 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
       ep.Md = cblk + 11 * nQ;
       ep.rbuf = bufG + 5 * nQ;
     }
-    nodal_to_modal(c, T, bufA, bufG, lane, ep);
+    nodal_to_modal<ANY>(c, T, bufA, bufG, lane, ep);
     return;
   }
   Epilogue ep{Epilogue::kRk, true, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
@@ -1079,9 +1146,9 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     ep.Md = cblk + 11 * nQ;
     ep.rbuf = bufG + 5 * nQ;
   }
-  const bool bad = __syncthreads_or(nodal_to_modal(c, T, bufA, bufG, lane, ep));
+  const bool bad = __syncthreads_or(nodal_to_modal<ANY>(c, T, bufA, bufG, lane, ep));
   if (bad && lane == 0) atomicOr(c.status, 1u);
-  if (MODE == kBwdRkFwd) element_forward(c, T, s, bufA, bufG, lane);
+  if (MODE == kBwdRkFwd) element_forward<ANY>(c, T, s, bufA, bufG, lane);
 }
 
 // ------------------------------------------------------------------ adjoint element phases
@@ -1208,9 +1275,10 @@ __device__ __noinline__ void element_vjp_a_t(const Ctx& c, const VjpArgs& va, in
   __syncthreads();
 }
 
+template <bool ANY>
 __device__ __forceinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
                                               double* bufC, int lane) {
-  if (c.slot_coff && c.slot_coff[s] >= 0) element_vjp_a_t<true>(c, va, s, bufA, bufG, bufC, lane);
+  if (ANY && c.slot_coff[s] >= 0) element_vjp_a_t<true>(c, va, s, bufA, bufG, bufC, lane);
   else element_vjp_a_t<false>(c, va, s, bufA, bufG, bufC, lane);
 }
 
@@ -1219,10 +1287,10 @@ __device__ __forceinline__ void element_vjp_a(const Ctx& c, const VjpArgs& va, i
 __device__ __noinline__ void element_vjp_c(const Ctx& c, const VjpArgs& va, int64_t s, double* bufA, double* bufG,
                                            int lane) {
   const TypeTab& T = c.tabs[c.slot_tab[s]];
-  element_lift(c, T, s, bufA, bufG, lane, c.Tv, 1.0);
+  element_lift<false>(c, T, s, bufA, bufG, lane, c.Tv, 1.0);
   Epilogue ep{va.rk ? Epilogue::kAxpy : Epilogue::kStore, false, va.rk ? va.dt : 1.0, va.Qbar + c.slot_qoff[s],
               nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
-  nodal_to_modal(c, T, bufA, bufG, lane, ep);
+  nodal_to_modal<false>(c, T, bufA, bufG, lane, ep);
 }
 
 // ------------------------------------------------------------------ Navier-Stokes adjoint element phases
@@ -1272,7 +1340,8 @@ __device__ __noinline__ void lift_add(const Ctx& c, const TypeTab& T, int64_t s,
 }
 
 // Phase A (Navier-Stokes).  smem: bufY [5 nQ] | bufG [15 nQ] | bufS [5 nQ].
-__device__ __noinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, int64_t s, double* smem, int lane) {
+template <bool CURVED>
+__device__ __noinline__ void element_vjp_a_ns_t(const Ctx& c, const VjpArgs& va, int64_t s, double* smem, int lane) {
   const TypeTab& T = c.tabs[c.slot_tab[s]];
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const int nQm = c.nQmax;
@@ -1281,7 +1350,11 @@ __device__ __noinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, i
   double* bufS = smem + 20 * nQm;
   const double* dp = c.dpool;
   const int64_t qoff = c.slot_qoff[s];
-  const double invJ = c.geo[s].invJ;
+  // curved element: dense M_e^{-1} (prism, pyramid) or 1/J_q (hex), pointwise metric
+  const double* cblk = CURVED ? c.cpool + c.slot_coff[s] : nullptr;
+  const bool dense = CURVED && T.type != HEX;
+  const double invJ = CURVED ? 1.0 : c.geo[s].invJ;
+  double* rdst = dense ? bufY : bufS;   // bufY is free until the modal -> nodal pass
   for (int w = lane; w < 5 * nM; w += blockDim.x) {
     const int m = w % nM;
     double rb;
@@ -1291,10 +1364,26 @@ __device__ __noinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, i
     } else {
       rb = va.Rbar[qoff + w];
     }
-    bufS[w] = rb * dp[T.minv + m] * invJ;
+    rdst[w] = dense ? rb : rb * dp[T.minv + m] * invJ;
   }
   __syncthreads();
+  if (dense) {
+    const double* Md = cblk + 11 * nQ;
+    for (int m = lane; m < nM; m += blockDim.x) {
+      double acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+      for (int j = 0; j < nM; ++j) DG_FMA5(Md[(size_t)j * nM + m], bufY + j, nM, acc);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufS[v * nM + m] = acc[v];
+    }
+    __syncthreads();
+  }
   modal_to_nodal(c, T, bufS, bufY, bufG, lane);
+  if (CURVED && !dense) {
+    const double* iJ = cblk + 10 * nQ;
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufY[w] *= iJ[w % nQ];
+    __syncthreads();
+  }
   write_traces(c, T, s, bufY, c.Tv, -1.0, lane);
   {
     const double* Dt = dp + T.Dt;
@@ -1338,7 +1427,14 @@ __device__ __noinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, i
 #pragma unroll
         for (int v = 0; v < 5; ++v) Gb[l][v] = bufG[(l * 5 + v) * nQ + q];
       double M[3][3];
-      point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      if (CURVED) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) M[l][d] = cblk[(l * 3 + d) * nQ + q];
+      } else {
+        point_metric(T.type, dp + T.wA + q * 9, Jg, M);
+      }
       contravariant_vjp(U, M, c.gamma, Gb, Ub);
       // G_l -= sum_d M[l][d] F_v[d]  =>  Fvbar[d] = -sum_l M[l][d] Gbar_l
       double Fvb[3][5];
@@ -1360,8 +1456,10 @@ __device__ __noinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, i
 
 // Phase B (Navier-Stokes lifting transpose).
 // smem: bufD [15 nQ] | bufB [5 nQ] | bufX [5 nQ] | bufW [5 nQ] | bufL [15 nQ].
-__device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* smem, int lane) {
+template <bool CURVED>
+__device__ __noinline__ void element_vjp_b_ns_t(const Ctx& c, int64_t s, double* smem, int lane) {
   const TypeTab& T = c.tabs[c.slot_tab[s]];
+  const double* cblk = CURVED ? c.cpool + c.slot_coff[s] : nullptr;
   const int n = T.n, nQ = T.nQ, n2 = n * n, nf = T.nfaces;
   const int nQm = c.nQmax;
   double* bufD = smem;                 // smem + 15 nQm .. 20 nQm is unused
@@ -1388,13 +1486,22 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
   for (int d = 0; d < 3; ++d) {
     double* Bd = bufD + d * 5 * nQ;     // DWbar_d, replaced by Bbar_d
     if (T.type == HEX) {
-      // V M_ref^{-1} V^T = W^{-1} (square V): pointwise
+      // V M^{-1} V^T = (W J)^{-1} (square V): pointwise
       const double* wq = dp + T.W;
-      for (int w = lane; w < 5 * nQ; w += blockDim.x) Bd[w] = -g.invJ * Bd[w] / wq[w % nQ];
+      if (CURVED) {
+        const double* iJ = cblk + 10 * nQ;
+        for (int w = lane; w < 5 * nQ; w += blockDim.x) Bd[w] = -iJ[w % nQ] * Bd[w] / wq[w % nQ];
+      } else {
+        for (int w = lane; w < 5 * nQ; w += blockDim.x) Bd[w] = -g.invJ * Bd[w] / wq[w % nQ];
+      }
       __syncthreads();
     } else {
-      Epilogue ep{Epilogue::kStore, true, -g.invJ, bufX, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
-      nodal_to_modal(c, T, Bd, bufX, lane, ep);
+      Epilogue ep{Epilogue::kStore, true, CURVED ? -1.0 : -g.invJ, bufX, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+      if (CURVED) {
+        ep.Md = cblk + 11 * nQ;        // symmetric: its own transpose
+        ep.rbuf = smem + 15 * nQm;
+      }
+      nodal_to_modal<CURVED>(c, T, Bd, bufX, lane, ep);
       modal_to_nodal(c, T, bufX, Bd, bufX, lane);
     }
     // Lbar_f -= n_d(f) E_f Bbar_d on the own face points
@@ -1409,22 +1516,42 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
       const double* Bs = Bd + ia * sa + ib * sb;
       double acc[5] = {0, 0, 0, 0, 0};
       for (int m = 0; m < n; ++m) DG_FMA5(e[m], Bs + m * sf, nQ, acc);
-      const double nd = c.fnrm[(s * 6 + lf) * 3 + d];
+      const double nd = CURVED ? c.snrm[3 * (ft[lf] / 5) + d * n2 + p] : c.fnrm[(s * 6 + lf) * 3 + d];
 #pragma unroll
       for (int v = 0; v < 5; ++v) bufL[(lf * 5 + v) * n2 + p] -= nd * acc[v];
     }
     __syncthreads();
   }
   // Wbar = sum_d sum_l M[l][d] D_l Bbar_d = sum_k sum_{l: wA[l][k] != 0} wA[l][k] D_l C_k
-  // with C_k = sum_d Jg[k][d] Bbar_d (in place of the Bbar_d)
-  for (int w = lane; w < 5 * nQ; w += blockDim.x) {
+  // with C_k = sum_d Jg[k][d] Bbar_d (in place of the Bbar_d); a curved
+  // element takes the first form with its pointwise metric
+  if (CURVED) {
+    for (int o = lane; o < nQ; o += blockDim.x) {
+      int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
+      double wb[5] = {0, 0, 0, 0, 0};
+      for (int d = 0; d < 3; ++d) {
+        const double* B = bufD + d * 5 * nQ;
+        double a0[5] = {0, 0, 0, 0, 0}, a1[5] = {0, 0, 0, 0, 0}, a2[5] = {0, 0, 0, 0, 0};
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + i], B + m * n2 + jk, nQ, a0);
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + j], B + i * n2 + m * n + k, nQ, a1);
+        for (int m = 0; m < n; ++m) DG_FMA5(Dt[m * n + k], B + i * n2 + j * n + m, nQ, a2);
+        const double m0 = cblk[(0 * 3 + d) * nQ + o], m1 = cblk[(1 * 3 + d) * nQ + o], m2 = cblk[(2 * 3 + d) * nQ + o];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) wb[v] += m0 * a0[v] + m1 * a1[v] + m2 * a2[v];
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bufW[v * nQ + o] = wb[v];
+    }
+    __syncthreads();
+  }
+  for (int w = lane; w < (CURVED ? 0 : 5 * nQ); w += blockDim.x) {
     const double b0 = bufD[w], b1 = bufD[5 * nQ + w], b2 = bufD[10 * nQ + w];
 #pragma unroll
     for (int kr = 0; kr < 3; ++kr)
       bufD[kr * 5 * nQ + w] = Jg[kr * 3] * b0 + Jg[kr * 3 + 1] * b1 + Jg[kr * 3 + 2] * b2;
   }
   __syncthreads();
-  {
+  if (!CURVED) {
     const unsigned nz = kMetricMask[T.type];
     for (int o = lane; o < nQ; o += blockDim.x) {
       int i = o / n2, jk = o - i * n2, j = jk / n, k = jk - j * n;
@@ -1479,12 +1606,24 @@ __device__ __noinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* s
   __syncthreads();
 }
 
+template <bool ANY>
+__device__ __forceinline__ void element_vjp_a_ns(const Ctx& c, const VjpArgs& va, int64_t s, double* smem, int lane) {
+  if (ANY && c.slot_coff[s] >= 0) element_vjp_a_ns_t<true>(c, va, s, smem, lane);
+  else element_vjp_a_ns_t<false>(c, va, s, smem, lane);
+}
+
+template <bool ANY>
+__device__ __forceinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double* smem, int lane) {
+  if (ANY && c.slot_coff[s] >= 0) element_vjp_b_ns_t<true>(c, s, smem, lane);
+  else element_vjp_b_ns_t<false>(c, s, smem, lane);
+}
+
 // ------------------------------------------------------------------ kernels
 //
 // One block (1 to 4 warps) works on one element at a time; its threads share
 // the element's shared-memory workspace bufA [5 nQmax] + bufG [15 nQmax].
 
-template <int MODE>
+template <int MODE, bool ANY>
 __global__ void __launch_bounds__(128) elem_naive_kernel(Ctx c, StageArgs io, const int64_t* __restrict__ list,
                                                          int64_t count) {
   extern __shared__ double smem[];
@@ -1492,10 +1631,10 @@ __global__ void __launch_bounds__(128) elem_naive_kernel(Ctx c, StageArgs io, co
   if (idx >= count) return;
   double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
-  process_element<MODE>(c, io, list ? list[idx] : idx, bufA, bufG, threadIdx.x);
+  process_element<MODE, ANY>(c, io, list ? list[idx] : idx, bufA, bufG, threadIdx.x);
 }
 
-template <int MODE>
+template <int MODE, bool ANY>
 __global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io, const int64_t* __restrict__ list,
                                                             const int64_t* __restrict__ chunk_start, int64_t nchunks,
                                                             unsigned int* counter, unsigned int* next_counter) {
@@ -1520,7 +1659,7 @@ __global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io,
     for (int64_t i = chunk_start[ch]; i < chunk_start[ch + 1]; ++i) {
       const int64_t s = list ? list[i] : i;
       uint64_t t0 = global_ns();
-      process_element<MODE>(c, io, s, bufA, bufG, lane);
+      process_element<MODE, ANY>(c, io, s, bufA, bufG, lane);
       __syncthreads();
       uint64_t dtn = global_ns() - t0;
       if (lane == 0) {
@@ -1626,7 +1765,7 @@ __global__ void face_kernel(Ctx c) {
 // Riemann flux minus the central viscous flux (F_v(U-, g-) + F_v(U+, g+)).n/2,
 // g the lifted gradient traces, times w S, written over the traces as in the
 // Euler face kernel.
-template <int KIND>
+template <int KIND, bool CURVED>
 __global__ void face_ns_kernel(Ctx c) {
   extern __shared__ double sF[];
   const FaceBlock fb = c.fblocks[blockIdx.x];
@@ -1653,8 +1792,8 @@ __global__ void face_ns_kernel(Ctx c) {
         UR[v] = acc;
       }
     }
-    const TypeTab& T = c.tabs[R.owner_tab];
-    const double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    const bool cg = CURVED && R.cgeo >= 0;   // curved owner: per-point normal and w S
+    const double wS = cg ? c.fgeo[R.cgeo + 3 * n2 + p] : c.dpool[c.tabs[R.owner_tab].fw + R.owner_lf * n2 + p] * R.S;
     double Fs[5];
     if (KIND == 0) {
       double WL[5], WR[5];
@@ -1663,7 +1802,12 @@ __global__ void face_ns_kernel(Ctx c) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (WL[v] + WR[v]);
     } else {
-      const double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+      double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+      if (cg) {
+        nrm[0] = c.fgeo[R.cgeo + p];
+        nrm[1] = c.fgeo[R.cgeo + n2 + p];
+        nrm[2] = c.fgeo[R.cgeo + 2 * n2 + p];
+      }
       if (c.flux == 0) flux_lf(UL, UR, nrm, gamma, Fs);
       else flux_roe(UL, UR, nrm, gamma, Fs);
       const double* V0 = c.Vt + 3 * R.toff;
@@ -1739,16 +1883,16 @@ __global__ void face_ns_kernel(Ctx c) {
 // ------------------------------------------------------------------ adjoint kernels
 
 // One kernel per phase, so that each gets its own register allocation.
-template <int PHASE>
+template <int PHASE, bool ANY>
 __global__ void __launch_bounds__(128) elem_vjp_kernel(Ctx c, VjpArgs va) {
   extern __shared__ double smem[];
   const int64_t s = blockIdx.x;
   double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
   double* bufC = bufG + 15 * c.nQmax;
-  if (PHASE == 0) element_vjp_a(c, va, s, bufA, bufG, bufC, threadIdx.x);
-  else if (PHASE == 10) element_vjp_a_ns(c, va, s, smem, threadIdx.x);
-  else if (PHASE == 11) element_vjp_b_ns(c, s, smem, threadIdx.x);
+  if (PHASE == 0) element_vjp_a<ANY>(c, va, s, bufA, bufG, bufC, threadIdx.x);
+  else if (PHASE == 10) element_vjp_a_ns<ANY>(c, va, s, smem, threadIdx.x);
+  else if (PHASE == 11) element_vjp_b_ns<ANY>(c, s, smem, threadIdx.x);
   else element_vjp_c(c, va, s, bufA, bufG, threadIdx.x);
 }
 
@@ -1865,7 +2009,7 @@ __global__ void face_vjp_kernel(Ctx c) {
 //   means' arguments; Tv += (dW/dU)^T Wbar (own), Map^T (neighbour).
 // At most 7 warps (n <= 7) per block; two resident blocks at the largest n
 // (three at n = 5) instead of the two that 168 registers allow.
-template <int KIND>
+template <int KIND, bool CURVED>
 __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
   extern __shared__ double sF[];
   const FaceBlock fb = c.fblocks[blockIdx.x];
@@ -1906,8 +2050,8 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
         gs[v] += sgn * b;
       }
     }
-    const TypeTab& T = c.tabs[R.owner_tab];
-    const double wS = c.dpool[T.fw + R.owner_lf * n2 + p] * R.S;
+    const bool cg = CURVED && R.cgeo >= 0;   // curved owner: per-point normal and w S
+    const double wS = cg ? c.fgeo[R.cgeo + 3 * n2 + p] : c.dpool[c.tabs[R.owner_tab].fw + R.owner_lf * n2 + p] * R.S;
     double UbL[5] = {0, 0, 0, 0, 0}, UbR[5] = {0, 0, 0, 0, 0};
     if (KIND == 0) {
       double Wb[5];
@@ -1918,7 +2062,12 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) gs[v] *= wS;
-      const double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+      double nrm[3] = {R.nrm[0], R.nrm[1], R.nrm[2]};
+      if (cg) {
+        nrm[0] = c.fgeo[R.cgeo + p];
+        nrm[1] = c.fgeo[R.cgeo + n2 + p];
+        nrm[2] = c.fgeo[R.cgeo + 2 * n2 + p];
+      }
       if (c.flux == 0) flux_lf_vjp(UL, UR, nrm, gamma, gs, UbL, UbR);
       else flux_roe_vjp(UL, UR, nrm, gamma, gs, UbL, UbR);
       double Fvb[3][5];
@@ -2141,20 +2290,28 @@ cudaError_t set_smem(K kernel, int bytes) {
 }
 template <int MODE>
 cudaError_t set_mode(int bytes) {
-  cudaError_t e = set_smem(elem_naive_kernel<MODE>, bytes);
-  if (e != cudaSuccess) return e;
-  return set_smem(elem_balanced_kernel<MODE>, bytes);
+  cudaError_t e;
+  if ((e = set_smem(elem_naive_kernel<MODE, false>, bytes)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_naive_kernel<MODE, true>, bytes)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_balanced_kernel<MODE, false>, bytes)) != cudaSuccess) return e;
+  return set_smem(elem_balanced_kernel<MODE, true>, bytes);
+}
+template <int MODE, bool ANY>
+void launch_mode_t(const Ctx& c, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb, int bytes,
+                   cudaStream_t st) {
+  if (balanced) {
+    elem_balanced_kernel<MODE, ANY><<<grid, 32 * wpb, bytes, st>>>(c, a, s.list, s.chunk_start, s.count, s.counter,
+                                                                   s.next_counter);
+  } else {
+    if (s.count <= 0) return;
+    elem_naive_kernel<MODE, ANY><<<(unsigned)s.count, 32 * wpb, bytes, st>>>(c, a, s.list, s.count);
+  }
 }
 template <int MODE>
 void launch_mode(const Ctx& c, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb, int bytes,
                  cudaStream_t st) {
-  if (balanced) {
-    elem_balanced_kernel<MODE><<<grid, 32 * wpb, bytes, st>>>(c, a, s.list, s.chunk_start, s.count, s.counter,
-                                                              s.next_counter);
-  } else {
-    if (s.count <= 0) return;
-    elem_naive_kernel<MODE><<<(unsigned)s.count, 32 * wpb, bytes, st>>>(c, a, s.list, s.count);
-  }
+  if (c.slot_coff) launch_mode_t<MODE, true>(c, a, s, balanced, grid, wpb, bytes, st);
+  else launch_mode_t<MODE, false>(c, a, s, balanced, grid, wpb, bytes, st);
 }
 }  // namespace
 
@@ -2165,19 +2322,26 @@ int element_smem_bytes_ns(int nQmax) { return 40 * nQmax * (int)sizeof(double); 
 // occupancy query uses this mesh's own launch size.
 constexpr int kMaxnQ = kMaxn * kMaxn * kMaxn;
 
-cudaError_t element_kernel_attributes_ns(int nQmax, int wpb, int* blocks_per_sm) {
+cudaError_t element_kernel_attributes_ns(int nQmax, int wpb, int* blocks_per_sm, bool curved) {
   cudaError_t e;
   if ((e = set_mode<kNsVolume>(element_smem_bytes_ns(kMaxnQ))) != cudaSuccess) return e;
   const int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
-  if ((e = set_smem(face_ns_kernel<0>, fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(face_ns_kernel<1>, fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(face_ns_vjp_kernel<0>, 2 * fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(face_ns_vjp_kernel<1>, 2 * fbytes)) != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kNsVolume>, 32 * wpb,
+  if ((e = set_smem(face_ns_kernel<0, false>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_kernel<1, false>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_kernel<0, true>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_kernel<1, true>, fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_vjp_kernel<0, false>, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_vjp_kernel<1, false>, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_vjp_kernel<0, true>, 2 * fbytes)) != cudaSuccess) return e;
+  if ((e = set_smem(face_ns_vjp_kernel<1, true>, 2 * fbytes)) != cudaSuccess) return e;
+  if (curved)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kNsVolume, true>, 32 * wpb,
+                                                         element_smem_bytes_ns(nQmax));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kNsVolume, false>, 32 * wpb,
                                                        element_smem_bytes_ns(nQmax));
 }
 
-cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
+cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm, bool curved) {
   const int bmax = element_smem_bytes(kMaxnQ, wpb);
   cudaError_t e;
   if ((e = set_mode<kFwd>(bmax)) != cudaSuccess) return e;
@@ -2191,11 +2355,19 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm) {
   if ((e = set_smem(face_kernel<true>, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_vjp_kernel<false>, 2 * fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_vjp_kernel<true>, 2 * fbytes)) != cudaSuccess) return e;
-  if ((e = set_smem(elem_vjp_kernel<0>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem(elem_vjp_kernel<2>, 20 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem(elem_vjp_kernel<10>, 25 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem(elem_vjp_kernel<11>, 45 * kMaxnQ * (int)sizeof(double))) != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd>, 32 * wpb,
+  const int vb = (int)sizeof(double) * kMaxnQ;
+  if ((e = set_smem(elem_vjp_kernel<0, false>, 25 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<2, false>, 20 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<10, false>, 25 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<11, false>, 45 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<0, true>, 25 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<2, true>, 20 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<10, true>, 25 * vb)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_vjp_kernel<11, true>, 45 * vb)) != cudaSuccess) return e;
+  if (curved)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd, true>, 32 * wpb,
+                                                         element_smem_bytes(nQmax, wpb));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd, false>, 32 * wpb,
                                                        element_smem_bytes(nQmax, wpb));
 }
 
@@ -2216,19 +2388,35 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
 void launch_faces_ns_vjp(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st) {
   if (nblocks <= 0) return;
   int bytes = 2 * 32 * 5 * n * n * (int)sizeof(double);
-  if (kind == 0) face_ns_vjp_kernel<0><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
-  else face_ns_vjp_kernel<1><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  const unsigned nb = (unsigned)nblocks, nt = face_block_threads(n);
+  if (c.fgeo) {
+    if (kind == 0) face_ns_vjp_kernel<0, true><<<nb, nt, bytes, st>>>(c);
+    else face_ns_vjp_kernel<1, true><<<nb, nt, bytes, st>>>(c);
+  } else {
+    if (kind == 0) face_ns_vjp_kernel<0, false><<<nb, nt, bytes, st>>>(c);
+    else face_ns_vjp_kernel<1, false><<<nb, nt, bytes, st>>>(c);
+  }
 }
 
 void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int wpb, cudaStream_t st) {
   if (nelem <= 0) return;
   const int per = phase == 0 || phase == 10 ? 25 : (phase == 11 ? 45 : 20);
   const int bytes = per * c.nQmax * (int)sizeof(double);
-  switch (phase) {
-    case 0: elem_vjp_kernel<0><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
-    case 10: elem_vjp_kernel<10><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
-    case 11: elem_vjp_kernel<11><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
-    default: elem_vjp_kernel<2><<<(unsigned)nelem, 32 * wpb, bytes, st>>>(c, va); break;
+  const unsigned nb = (unsigned)nelem, nt = 32 * wpb;
+  if (c.slot_coff) {
+    switch (phase) {
+      case 0: elem_vjp_kernel<0, true><<<nb, nt, bytes, st>>>(c, va); break;
+      case 10: elem_vjp_kernel<10, true><<<nb, nt, bytes, st>>>(c, va); break;
+      case 11: elem_vjp_kernel<11, true><<<nb, nt, bytes, st>>>(c, va); break;
+      default: elem_vjp_kernel<2, false><<<nb, nt, bytes, st>>>(c, va); break;   // phase C has no geometry
+    }
+  } else {
+    switch (phase) {
+      case 0: elem_vjp_kernel<0, false><<<nb, nt, bytes, st>>>(c, va); break;
+      case 10: elem_vjp_kernel<10, false><<<nb, nt, bytes, st>>>(c, va); break;
+      case 11: elem_vjp_kernel<11, false><<<nb, nt, bytes, st>>>(c, va); break;
+      default: elem_vjp_kernel<2, false><<<nb, nt, bytes, st>>>(c, va); break;
+    }
   }
 }
 
@@ -2242,8 +2430,14 @@ void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
 void launch_faces_ns(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st) {
   if (nblocks <= 0) return;
   int bytes = 32 * 5 * n * n * (int)sizeof(double);
-  if (kind == 0) face_ns_kernel<0><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
-  else face_ns_kernel<1><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+  const unsigned nb = (unsigned)nblocks, nt = face_block_threads(n);
+  if (c.fgeo) {
+    if (kind == 0) face_ns_kernel<0, true><<<nb, nt, bytes, st>>>(c);
+    else face_ns_kernel<1, true><<<nb, nt, bytes, st>>>(c);
+  } else {
+    if (kind == 0) face_ns_kernel<0, false><<<nb, nt, bytes, st>>>(c);
+    else face_ns_kernel<1, false><<<nb, nt, bytes, st>>>(c);
+  }
 }
 
 void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {

@@ -78,6 +78,7 @@ struct Ctx {
   const int64_t* slot_coff;    // [slot] offset into cpool, -1 for an affine element
   const double* cpool;         // per curved slot: [9][nQ] metric, [nQ] J, [nQ] 1/J, (prism, pyramid) [nM][nM] M_e^{-1}
   const double* fgeo;          // per curved-owner face: [4][n^2] normal x, y, z and w S (FaceRec::cgeo)
+  const double* snrm;          // curved meshes: per face side [3][n^2] outward normal at 3 * (side offset / 5)
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
@@ -125,8 +126,9 @@ void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st);
 int element_smem_bytes(int nQmax, int warps_per_block);
 int face_block_threads(int n);
-cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm);
-cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm);
+// curved: the mesh holds curved elements (occupancy of the kernel variants that handle them)
+cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false);
+cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false);
 cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops);
 cudaError_t probe_fp64_mixed(double* total_tflops);
 

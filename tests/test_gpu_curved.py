@@ -3,7 +3,8 @@ in Eq. 1 and in the Algorithm 1 projection) against the curved oracle,
 through the C ABI: dg_rhs, dg_rk_step, dg_project, dg_eval_nodal, the
 quadrature points, free-stream preservation, scheduler and batch
 equivalence, the affine limit, dg_rhs_vjp and dg_rk_vjp (oracle parity and
-central differences), the call curved meshes do not support, and a
+central differences), the Navier-Stokes residual, steps and adjoint (BR1 with
+pointwise metric and normals, a 12^3 Re 1600 sampled check), and a
 sampled check of the 16^3 mixed N = 4 perturbed mesh in the launch
 configuration the benchmark times.  Tolerance: relative L-infinity per
 variable <= 1e-11."""
@@ -197,15 +198,101 @@ def test_curved_rk_vjp_central_differences(dg):
     assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
 
 
-def test_curved_unsupported_calls(dg):
-    box, o, mesh = setup(dg, "mixed", 2, 2)
-    Qs = mesh.set_state(torch.from_numpy(state(o)).cuda())
-    with pytest.raises(dg.DGError) as ei:
-        mesh.set_physics("navier_stokes", 1e-3, 0.72)
-    assert ei.value.status == -7
-    # the mesh stays usable
+# ---------------------------------------------------------------- Navier-Stokes (BR1) on curved meshes
+NS_CASES = [("mixed", 2, 2, "lf", None), ("four", 4, 2, "roe", 5), ("prism", 2, 3, "lf", 3),
+            ("hex", 2, 4, "roe", None), ("pyramid", 2, 3, "lf", 7), ("mixed", 3, 3, "lf", None)]
+
+
+def setup_ns(dg, kind, m, N, flux="lf", reorder=None, mu=0.05, Pr=0.72):
+    from oracle.curved import CurvedNSOracle, curved_from_box
+    box = curved_box(kind, m, reorder=reorder)
+    o = CurvedNSOracle(curved_from_box(box, N), flux=flux, mu=mu, Pr=Pr)
+    mesh = dg.Mesh(box, N, flux=flux, geometry="vertex")
+    mesh.set_physics("navier_stokes", mu, Pr)
+    return box, o, mesh
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder", NS_CASES)
+def test_curved_ns_rhs_parity(dg, kind, m, N, flux, reorder):
+    box, o, mesh = setup_ns(dg, kind, m, N, flux, reorder)
+    Q = state(o)
+    R = mesh.get_state(mesh.rhs(mesh.set_state(torch.from_numpy(Q).cuda())))
+    err = rel_err(R, o.rhs(Q), var_index(o.mesh.nM))
+    assert err < TOL, err
+
+
+def test_curved_ns_rk_step_and_free_stream(dg):
+    box, o, mesh = setup_ns(dg, "mixed", 2, 3)
+    Q = state(o)
+    dt = 1e-3
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    mesh.rk_step(Qs, mesh.empty(), dt, 2)
+    Qg = mesh.get_state(Qs)
+    Qref = o.run(Q, dt, 2)
+    assert rel_err(Qg - Q, Qref - Q, var_index(o.mesh.nM)) < 1e-10
+    n = 4
+    U0 = np.array([1.2, 0.3, -0.2, 0.1, 3.0])
+    vals = np.tile(U0[None, :, None], (box.n_elems, 1, n ** 3)).reshape(-1)
+    R = mesh.get_state(mesh.rhs(mesh.project(torch.from_numpy(vals).cuda())))
+    assert np.abs(R).max() < 1e-12
+    mesh.sync()
+
+
+@pytest.mark.parametrize("kind,m,N,flux,reorder", [("mixed", 2, 2, "lf", None), ("four", 4, 1, "roe", 5),
+                                                    ("pyramid", 2, 2, "lf", 7), ("hex", 2, 3, "lf", 3)])
+def test_curved_ns_rhs_vjp_parity(dg, kind, m, N, flux, reorder):
+    box, o, mesh = setup_ns(dg, kind, m, N, flux, reorder)
+    Q = state(o)
+    w = di.random_vector(Q.size, seed=33)
+    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+    G = mesh.get_state(mesh.rhs_vjp(Qs, mesh.set_state(torch.from_numpy(w).cuda())))
+    err = rel_err(G, o.rhs_vjp(Q, w), var_index(o.mesh.nM))
+    assert err < TOL, err
+
+
+def test_curved_ns_rk_vjp_parity(dg):
+    from oracle.adjoint import rk_vjp
+    box, o, mesh = setup_ns(dg, "mixed", 2, 2)
+    Q = state(o)
+    w = di.random_vector(Q.size, seed=34)
+    dt, K = 1e-3, 2
+    Q0 = mesh.set_state(torch.from_numpy(Q).cuda())
+    for ckpt in (1, 2):
+        G = mesh.get_state(mesh.rk_vjp(Q0, dt, K, ckpt, mesh.set_state(torch.from_numpy(w).cuda())))
+        err = rel_err(G, rk_vjp(o, Q, dt, K, w), var_index(o.mesh.nM))
+        assert err < TOL, (ckpt, err)
+
+
+def test_curved_ns_12cube_N4_sampled(dg):
+    """Viscous TGV at Re 1600 on the 12^3 mixed box with moved vertices, N = 4,
+    autotuned balanced launches: sampled elements against the oracle, each
+    variable's error measured against the larger of its residual and its
+    volume-term magnitude."""
+    from oracle.curved import CurvedNSOracle, curved_from_box
+    box = di.perturb_vertices(di.box_mesh(12, "mixed", seed=4, p_prism=0.25, p_pyr=1.0 / 9.0), 0.1)
+    N, mu, Pr = 4, 1.0 / 1600, 0.72
+    mesh = dg.Mesh(box, N, geometry="vertex")
+    mesh.set_physics("navier_stokes", mu, Pr)
+    n = N + 1
+    vals = di.perturbed_tgv_state(mesh.quad_points(), seed=8).reshape(5, box.n_elems, n ** 3)
+    Qs = mesh.project(torch.from_numpy(vals.transpose(1, 0, 2).reshape(-1)).cuda())
+    mesh.autotune(Qs, 1e-4)
     R = mesh.get_state(mesh.rhs(Qs))
-    assert np.isfinite(R).all()
+    Q = mesh.get_state(Qs)
+    o = CurvedNSOracle(curved_from_box(box, N), flux="lf", mu=mu, Pr=Pr)
+    elems = np.sort(np.random.default_rng(9).choice(box.n_elems, 16, replace=False))
+    G = o.lifted_gradient(Q, elems)
+    mask = np.zeros(len(Q), dtype=bool)
+    vol = np.zeros(len(Q))
+    for e in elems:
+        sl = slice(o.mesh.dof_off[e], o.mesh.dof_off[e + 1])
+        mask[sl] = True
+        vol[sl] = o.apply_minv(e, o.ns_volume_term(Q, e, G)).ravel()
+    Rref = o.rhs(Q, elems)
+    for v, idx in enumerate(var_index(o.mesh.nM)):
+        i = idx[mask[idx]]
+        scale = max(np.abs(Rref[i]).max(), np.abs(vol[i]).max())
+        assert np.abs(R[i] - Rref[i]).max() < TOL * scale, (v, np.abs(R[i] - Rref[i]).max(), scale)
 
 
 def test_curved_16cube_N4_sampled(dg):
