@@ -846,6 +846,60 @@ def curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, affine_value)
     out["cost_table_ns_per_elem"] = dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns]))
     out["sm_load_imbalance"] = imb
     out["finite"] = bool(torch.isfinite(res["balanced"]).all())
+
+    def device_ms(fn, reps=2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # adjoint / forward on the curved mesh: dg_rk_vjp through K steps,
+    # checkpoints every 5, against K forward steps
+    Kadj = 10
+    Qa, Ka = Q0.clone(), torch.empty_like(Q0)
+    wbar = torch.ones_like(Qa)
+    mesh.rk_step(Qa, Ka, dt, Kadj)
+    mesh.rk_vjp(Q0, dt, Kadj, 5, wbar)
+    torch.cuda.synchronize()
+    fwd_ms = device_ms(lambda: mesh.rk_step(Qa, Ka, dt, Kadj))
+    adj_ms = device_ms(lambda: mesh.rk_vjp(Q0, dt, Kadj, 5, wbar))
+    out["adjoint"] = {"steps": Kadj, "forward_ms": fwd_ms, "rk_vjp_ckpt5_ms": adj_ms, "ratio_ckpt5": adj_ms / fwd_ms}
+
+    # Navier-Stokes (BR1, Re 1600) on the same curved mesh and on its affine
+    # original, balanced, tile shapes from the autotuner
+    nsteps = max(2, steps // 5)
+    ns_out = {"steps": nsteps, "mu": 1.0 / 1600, "Pr": 0.72}
+    for name, m in (("curved", mesh),
+                    ("affine", dg.Mesh(di.box_mesh(MESH_M, "mixed", seed=MESH_SEED), N_DEG, flux=args.flux))):
+        m.set_scheduler("balanced")
+        m.set_physics("navier_stokes", 1.0 / 1600, 0.72)
+        if name == "affine":
+            xa = m.quad_points()
+            va = di.tgv_state(xa).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+            Qn0 = m.project(torch.from_numpy(va).to(dev))
+        else:
+            Qn0 = Q0
+        if args.warps:
+            m.set_element_warps(args.warps)
+        else:
+            m.autotune(Qn0, dt)
+        Qn = Qn0.clone()
+        Kn = torch.empty_like(Qn)
+        for _ in range(args.warmup):
+            m.rk_step(Qn, Kn, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        ms_ns = max_over_ranks(device_ms(lambda: m.rk_step(Qn, Kn, dt, nsteps), reps=1))
+        ns_out[name] = {"value": ws * dof * 5 * nsteps / (ms_ns * 1e-3), "ms_per_step": ms_ns / nsteps}
+        if name == "affine":
+            m.sync()
+            m.close()
+    ns_out["curved_over_affine"] = ns_out["curved"]["value"] / ns_out["affine"]["value"]
+    out["navier_stokes"] = ns_out
     mesh.sync()
     mesh.close()
     return out
