@@ -295,6 +295,39 @@ def test_curved_ns_12cube_N4_sampled(dg):
         assert np.abs(R[i] - Rref[i]).max() < TOL * scale, (v, np.abs(R[i] - Rref[i]).max(), scale)
 
 
+def test_curved_autograd(dg):
+    """torch.autograd through the curved residual and K steps: gradients of a
+    scalar loss equal dg_rhs_vjp / dg_rk_vjp of its seed."""
+    from paper_2511_08020_gb300 import autograd as dga
+    box, o, mesh = setup(dg, "mixed", 2, 3)
+    Q0 = mesh.set_state(torch.from_numpy(state(o)).cuda())
+    w = mesh.set_state(torch.from_numpy(di.random_vector(mesh.n_dof, seed=35)).cuda())
+    Q = Q0.clone().requires_grad_(True)
+    (dga.rhs(Q, mesh) * w).sum().backward()
+    assert torch.equal(Q.grad, mesh.rhs_vjp(Q0, w))
+    Q = Q0.clone().requires_grad_(True)
+    (dga.rk(Q, mesh, 1e-3, 4, 2) * w).sum().backward()
+    ref = mesh.rk_vjp(Q0, 1e-3, 4, 2, w)
+    assert rel_err(Q.grad.cpu().numpy(), ref.cpu().numpy(), var_index(o.mesh.nM)) < TOL
+
+
+def test_curved_ns_batch_equals_instances(dg):
+    parts = [(curved_box("mixed", 2, seed=1), 2), (curved_box("four", 4, seed=2), 2), (curved_box("prism", 2, seed=3), 3)]
+    b = dg.Batch([p[0] for p in parts], [p[1] for p in parts], geometry="vertex")
+    b.set_physics("navier_stokes", 0.05, 0.72)
+    from oracle.curved import CurvedOracle, curved_from_box
+    Qs, singles = [], []
+    for i, (box, N) in enumerate(parts):
+        Qs.append(state(CurvedOracle(curved_from_box(box, N)), seed=20 + i))
+        s = dg.Mesh(box, N, geometry="vertex")
+        s.set_physics("navier_stokes", 0.05, 0.72)
+        singles.append(s)
+    R = b.get_state(b.rhs(b.set_state(torch.from_numpy(np.concatenate(Qs)).cuda())))
+    for i, s in enumerate(singles):
+        Ri = s.get_state(s.rhs(s.set_state(torch.from_numpy(Qs[i]).cuda())))
+        np.testing.assert_array_equal(b.instance(R, i), Ri)
+
+
 def test_curved_16cube_N4_sampled(dg):
     """The benchmark's curved workload (16^3 mixed, vertices moved by up to
     0.1 h per coordinate, N = 4) after autotuning: sampled elements against

@@ -55,6 +55,22 @@ def test_noalloc_matches_rhs_vjp_twice(dg, flux):
     mesh.sync()
 
 
+def test_noalloc_on_a_curved_mesh(dg):
+    from oracle.elements import n_modes
+    box = di.perturb_vertices(make_box("four", 4, seed=1), 0.1)
+    N = 2
+    mesh = dg.Mesh(box, N, geometry="vertex")
+    assert mesh.n_curved > 0
+    nM = [n_modes(int(t), N) for t in box.etype]
+    Q = mesh.set_state(di.random_modal_state(nM, seed=2, amp=1e-2))
+    W = mesh.set_state(di.random_vector(mesh.n_dof, seed=33))
+    ref = mesh.get_state(mesh.rhs_vjp(Q, W))
+    out = torch.full_like(Q, float("nan"))
+    assert noalloc(dg, mesh, Q, W, out) == 0, dg.load().dg_last_error().decode()
+    np.testing.assert_array_equal(mesh.get_state(out), ref)
+    mesh.sync()
+
+
 def test_noalloc_rejects_meshes_beyond_the_fixed_scratch(dg):
     box = make_box("mixed", 20, seed=2)   # ~58k faces x 2 x 5 x 25 doubles > 8 Mi doubles
     mesh = dg.Mesh(box, 4)
