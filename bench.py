@@ -724,8 +724,8 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
         out["balanced_over_naive"] = out["balanced"]["value"] / out["naive"]["value"]
         out["schedulers_bitwise_equal"] = bool(torch.equal(res["naive"], res["balanced"]))
     if args.ns_adj_steps > 0:
-        # adjoint of the final kinetic energy seed through K steps
-        # (checkpoints every 5 steps) against K forward steps
+        # adjoint through K steps (checkpoints every 5 steps) against K
+        # forward steps; the seed is all ones (the cost does not depend on it)
         Ka = args.ns_adj_steps
         Qa = Q0.clone()
         Kr = torch.empty_like(Qa)
