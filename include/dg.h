@@ -72,7 +72,17 @@ typedef enum {
 } dg_status;
 
 typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1 } dg_flux;
-typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1, DG_SCHED_STATIC = 2 } dg_scheduler;
+/* Element scheduling (Sec. 3's load balancing on one GPU; results are
+ * bitwise identical for all four):
+ *   BALANCED  persistent launches whose blocks pop cost-weighted chunks of the
+ *             Hilbert order from an atomic queue (guided self-scheduling);
+ *   NAIVE     one launch per element type and phase in caller order;
+ *   STATIC    one contiguous Hilbert segment of equal element count per
+ *             resident block (the paper's partition without balancing);
+ *   WEIGHTED  one contiguous Hilbert segment of equal weight per resident
+ *             block, with the per-(type, N) weights of the timers once
+ *             dg_rebalance has read them (the paper's balanced partition). */
+typedef enum { DG_SCHED_BALANCED = 0, DG_SCHED_NAIVE = 1, DG_SCHED_STATIC = 2, DG_SCHED_WEIGHTED = 3 } dg_scheduler;
 typedef enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 } dg_physics;
 
 /* Element geometry (Sec. 2: x = chi(xi) with a pointwise Jacobian J; with
@@ -292,12 +302,15 @@ dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages);
  * dg_rhs_vjp_noalloc returns DG_ERR_UNSUPPORTED under Navier-Stokes. */
 dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr);
 
-/* Scheduler of the element kernels: DG_SCHED_BALANCED (one persistent launch
- * per phase, warps take cost-weighted Hilbert-contiguous element chunks from
- * an atomic queue), DG_SCHED_NAIVE (one launch per element type and phase,
- * caller element order) or DG_SCHED_STATIC (one persistent launch, every warp
- * owns one contiguous Hilbert segment of equal element count: the SFC
- * partition without load balancing of Sec. 3).  Results are bitwise identical. */
+/* Scheduler of the element kernels (dg_scheduler above): DG_SCHED_BALANCED
+ * (one persistent launch per phase, blocks take cost-weighted
+ * Hilbert-contiguous element chunks from an atomic queue), DG_SCHED_NAIVE
+ * (one launch per element type and phase, caller element order),
+ * DG_SCHED_STATIC (one persistent launch, every block owns one contiguous
+ * Hilbert segment of equal element count: the SFC partition without load
+ * balancing of Sec. 3) or DG_SCHED_WEIGHTED (the same with segments of equal
+ * weight: the load-balanced SFC partition of Sec. 3).  Results are bitwise
+ * identical. */
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler);
 
 /* Tile shape of the element kernels: the number of warps (1..4) that work
@@ -343,9 +356,10 @@ dg_status dg_set_stage_fusion(dg_mesh* mesh, int fused);
  * current per-SM load imbalance (max/mean - 1).  Synchronises `stream`. */
 dg_status dg_cost_table(dg_mesh* mesh, double* ns_per_elem, double* imbalance, cudaStream_t stream);
 
-/* Rebuild the weighted chunk table from the measured costs when the measured
- * imbalance exceeds the threshold (or always, if force != 0); resets the
- * counters.  *rebuilt (may be NULL) tells whether it did.  Synchronises. */
+/* Rebuild the weighted chunk table and the equal-weight partition of
+ * DG_SCHED_WEIGHTED from the measured costs when the measured imbalance
+ * exceeds the threshold (or always, if force != 0); resets the counters.
+ * *rebuilt (may be NULL) tells whether it did.  Synchronises. */
 dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stream);
 
 /* Phase timing: with profiling on, dg_rhs and the dg_rk_step graph record

@@ -17,7 +17,7 @@ __all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "
            "PHYSICS", "GEOMETRY", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
-SCHED = {"balanced": 0, "naive": 1, "static": 2}
+SCHED = {"balanced": 0, "naive": 1, "static": 2, "weighted": 3}
 PHYSICS = {"euler": 0, "navier_stokes": 1}
 GEOMETRY = {"affine": 0, "vertex": 1}
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_CUDA", -4: "DG_ERR_OOM",

@@ -138,6 +138,8 @@ struct dg_mesh {
   int64_t* d_type_slots[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t* d_chunks_static = nullptr;
   int64_t nchunks_static = 0;
+  int64_t* d_chunks_weighted = nullptr;   // equal-weight Hilbert segments (DG_SCHED_WEIGHTED)
+  int64_t nchunks_weighted = 0;
   bool fused = true;  // backward of stage s and forward of stage s+1 in one launch
   double weight[dgk::kMaxTabs] = {};  // chunk weights in use per (type, N) table (ns or modelled)
 
@@ -342,11 +344,14 @@ struct dg_mesh {
       e = upload(&G.d_list, list);
       if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return build_static_chunks();
   }
 
-  // Static partition: one contiguous Hilbert segment of equal element count
-  // per resident warp (the paper's partition without load balancing).
+  // Static partitions, one contiguous Hilbert segment per resident block:
+  // of equal element count (the paper's partition without load balancing,
+  // DG_SCHED_STATIC), and of equal weight with the current per-(type, N)
+  // weights (the paper's load-balanced partition, Sec. 3: weights from the
+  // timers once dg_rebalance has read them, DG_SCHED_WEIGHTED).
   cudaError_t build_static_chunks() {
     const int64_t E = h.n_elems;
     int64_t W = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)grid_balanced()));
@@ -354,7 +359,23 @@ struct dg_mesh {
     for (int64_t w = 0; w <= W; ++w) starts[w] = w * E / W;
     nchunks_static = W;
     if (d_chunks_static) cudaFree(d_chunks_static);
-    return upload(&d_chunks_static, starts);
+    d_chunks_static = nullptr;
+    cudaError_t e = upload(&d_chunks_static, starts);
+    if (e != cudaSuccess) return e;
+    // equal-weight cuts of the prefix sum of the slots' weights
+    double total = 0.0;
+    for (int64_t s = 0; s < E; ++s) total += weight[h.slot_tab[s]];
+    std::vector<int64_t> ws(1, 0);
+    double acc = 0.0;
+    for (int64_t s = 0; s < E && (int64_t)ws.size() < W; ++s) {
+      acc += weight[h.slot_tab[s]];
+      if (acc >= total * (double)ws.size() / (double)W) ws.push_back(s + 1);
+    }
+    ws.push_back(E);
+    nchunks_weighted = (int64_t)ws.size() - 1;
+    if (d_chunks_weighted) cudaFree(d_chunks_weighted);
+    d_chunks_weighted = nullptr;
+    return upload(&d_chunks_weighted, ws);
   }
 
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
@@ -370,8 +391,10 @@ struct dg_mesh {
                               st);
           parity ^= 1;
         }
-      } else if (scheduler == DG_SCHED_STATIC && !per_elem) {
-        dgk::Sched s{nullptr, nchunks_static, d_chunks_static, d_counters + parity, d_counters + (parity ^ 1)};
+      } else if ((scheduler == DG_SCHED_STATIC || scheduler == DG_SCHED_WEIGHTED) && !per_elem) {
+        const bool wt = scheduler == DG_SCHED_WEIGHTED;
+        dgk::Sched s{nullptr, wt ? nchunks_weighted : nchunks_static, wt ? d_chunks_weighted : d_chunks_static,
+                     d_counters + parity, d_counters + (parity ^ 1)};
         dgk::launch_element(c, mode, a, s, true, mode == dgk::kNsVolume ? grid_ns() : grid_balanced(), wpb, st);
         parity ^= 1;
       } else {
@@ -540,7 +563,7 @@ struct dg_mesh {
   void release() {
     void* ptrs[] = {d_dpool, d_ipool, d_tabs, d_slot_tab, d_slot_type, d_slot_qoff, d_slot_hoff, d_slot_ftoff,
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
-                    d_cost, d_smns, d_counters, d_chunks_static, d_stage,
+                    d_cost, d_smns, d_counters, d_chunks_static, d_chunks_weighted, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
                     d_slot_coff, d_cpool, d_fgeo, d_snrm};
     for (void* p : ptrs)
@@ -565,7 +588,7 @@ namespace {
 
 dg_status check_desc(const dg_mesh_desc* desc) {
   if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE) return fail(DG_ERR_ARG, "unknown flux");
-  if (desc->scheduler < DG_SCHED_BALANCED || desc->scheduler > DG_SCHED_STATIC) return fail(DG_ERR_ARG, "unknown scheduler");
+  if (desc->scheduler < DG_SCHED_BALANCED || desc->scheduler > DG_SCHED_WEIGHTED) return fail(DG_ERR_ARG, "unknown scheduler");
   if (!(desc->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
   return DG_OK;
 }
@@ -1089,7 +1112,7 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
 
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
-  if (scheduler < DG_SCHED_BALANCED || scheduler > DG_SCHED_STATIC) return fail(DG_ERR_ARG, "unknown scheduler");
+  if (scheduler < DG_SCHED_BALANCED || scheduler > DG_SCHED_WEIGHTED) return fail(DG_ERR_ARG, "unknown scheduler");
   mesh->scheduler = scheduler;
   return DG_OK;
 }

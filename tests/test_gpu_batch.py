@@ -64,7 +64,7 @@ def test_batch_layout(dg, parts):
 
 
 @pytest.mark.parametrize("flux", ["lf", "roe"])
-@pytest.mark.parametrize("scheduler", ["balanced", "naive", "static"])
+@pytest.mark.parametrize("scheduler", ["balanced", "naive", "static", "weighted"])
 def test_batch_rhs_equals_instances(dg, parts, flux, scheduler):
     b = make_batch(dg, parts, flux=flux, scheduler=scheduler)
     Q = np.concatenate([p[3] for p in parts])

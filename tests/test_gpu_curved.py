@@ -106,7 +106,7 @@ def test_curved_free_stream(dg, kind, m, N):
     assert np.abs(R).max() < 1e-12
 
 
-@pytest.mark.parametrize("scheduler", ["naive", "static"])
+@pytest.mark.parametrize("scheduler", ["naive", "static", "weighted"])
 def test_curved_schedulers_agree(dg, scheduler):
     box, o, mesh = setup(dg, "mixed", 3, 3)
     other = dg.Mesh(box, 3, scheduler=scheduler, geometry="vertex")

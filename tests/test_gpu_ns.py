@@ -102,13 +102,14 @@ def test_ns_schedulers_bitwise_equal(dg):
     box, o, mesh = setup(dg, "mixed", 4, 3, "lf", None)
     Q = state(o)
     out = {}
-    for sched in ("balanced", "naive", "static"):
+    for sched in ("balanced", "naive", "static", "weighted"):
         mesh.set_scheduler(sched)
         Qs = mesh.set_state(torch.from_numpy(Q).cuda())
         mesh.rk_step(Qs, mesh.empty(), 1e-3, 2)
         out[sched] = mesh.get_state(Qs)
     np.testing.assert_array_equal(out["balanced"], out["naive"])
     np.testing.assert_array_equal(out["balanced"], out["static"])
+    np.testing.assert_array_equal(out["balanced"], out["weighted"])
 
 
 def test_ns_free_stream(dg):

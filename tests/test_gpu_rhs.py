@@ -274,7 +274,7 @@ def test_eval_nodal_parity(dg, kind, m, N, reorder):
     assert rel_err(Qb, Q, var_index(o.mesh.nM)) < 1e-12
 
 
-@pytest.mark.parametrize("scheduler", ["balanced", "static", "naive"])
+@pytest.mark.parametrize("scheduler", ["balanced", "static", "naive", "weighted"])
 def test_every_element_written(dg, scheduler):
     """Outputs prefilled with NaN: after dg_rhs every entry is finite (each
     element is processed exactly once by each scheduler) and equal to the
@@ -289,3 +289,29 @@ def test_every_element_written(dg, scheduler):
     Rn = ref.empty().fill_(float("nan"))
     ref.rhs(ref.set_state(torch.from_numpy(Q).cuda()), Rn)
     assert torch.equal(R, Rn)
+
+
+def test_weighted_partition_after_rebalance(dg):
+    """DG_SCHED_WEIGHTED with the measured per-type weights (read by
+    dg_rebalance): every element is still processed once, results equal the
+    naive scheduler's, and the measured imbalance of the weighted partition
+    is no worse than twice that of the equal-count partition."""
+    box, o, mesh = setup(dg, "mixed", 6, 4, "lf", None, scheduler="static")
+    Q = state(o)
+    Q0 = mesh.set_state(torch.from_numpy(Q).cuda())
+    mesh.set_profiling(True)
+    Qs = Q0.clone()
+    mesh.rk_step(Qs, mesh.empty(), 1e-4, 2)
+    _, imb_static = mesh.cost_table()
+    assert mesh.rebalance(force=True)
+    mesh.set_scheduler("weighted")
+    Qw = Q0.clone()
+    mesh.rk_step(Qw, mesh.empty(), 1e-4, 2)
+    _, imb_weighted = mesh.cost_table()
+    mesh.set_profiling(False)
+    assert torch.equal(Qs, Qw)
+    R = mesh.empty().fill_(float("nan"))
+    mesh.rhs(Q0, R)
+    ref = dg.Mesh(box, 4, scheduler="naive")
+    assert torch.equal(R, ref.rhs(ref.set_state(torch.from_numpy(Q).cuda())))
+    assert imb_weighted <= 2 * imb_static + 0.05, (imb_static, imb_weighted)
