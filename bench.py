@@ -780,6 +780,56 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
                           "rk_vjp_checkpointed_ms": adjc_ms,
                           "backward_given_forward_checkpoints_over_forward": adjc_ms / fwdc_ms,
                           "rk_vjp_auto_segment_ms": auto_ms, "auto_segment_over_forward": auto_ms / fwd_ms}
+    if args.ns_ke_adjoint:
+        # the adjoint of the final kinetic energy with respect to the initial
+        # modal state through all the leg's steps (checkpoints every 5 steps,
+        # segments recomputed): seed = dE_k/dQ_K = V^T W J (dke/dU)(U_K)
+        mesh.set_scheduler("balanced")
+        Qf = Q0.clone()
+        Kf = torch.empty_like(Qf)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mesh.rk_step(Qf, Kf, dt, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_full = e0.elapsed_time(e1)
+        U = mesh.eval_nodal(Qf).view(box.n_elems, 5, n ** 3)
+        rho, mom = U[:, 0], U[:, 1:4]
+        g = torch.zeros_like(U)
+        g[:, 0] = -0.5 * (mom * mom).sum(1) / (rho * rho)
+        g[:, 1:4] = mom / rho[:, None]
+        seed = mesh.load_vector(g.reshape(-1))
+        del U, g
+        e0.record(stream)
+        grad = mesh.rk_vjp(Q0, dt, steps, 5, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        adj_full = e0.elapsed_time(e1)
+        # the autograd split: the forward keeps Q at every segment start, the
+        # backward recomputes the segments from them
+        Qc = Q0.clone()
+        e0.record(stream)
+        ck = mesh.rk_step_checkpointed(Qc, Kf, dt, steps, 5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwdc_full = e0.elapsed_time(e1)
+        e0.record(stream)
+        gradc = mesh.rk_vjp_checkpointed(ck, dt, steps, 5, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        adjc_full = e0.elapsed_time(e1)
+        del ck
+        out["ke_adjoint"] = {"steps": steps, "ckpt_every": 5, "forward_ms": fwd_full, "rk_vjp_ms": adj_full,
+                             "adjoint_over_forward": adj_full / fwd_full,
+                             "forward_checkpointed_ms": fwdc_full, "rk_vjp_checkpointed_ms": adjc_full,
+                             "backward_given_forward_checkpoints_over_forward": adjc_full / fwdc_full,
+                             "gradients_equal": bool(torch.equal(grad, gradc)),
+                             "gradient_finite": bool(torch.isfinite(grad).all()),
+                             "what": "d E_k(Q_K) / d Q_0 through all steps: dg_rk_vjp from Q_0 (its own forward pass "
+                                     "places the checkpoints, segments are recomputed with kept stage data), and "
+                                     "the split where the forward keeps the checkpoints"}
     mesh.sync()
     mesh.close()
     return out
@@ -1016,6 +1066,8 @@ def main():
                     help="steps of the 24^3 Navier-Stokes TGV leg (0 skips it)")
     ap.add_argument("--ns-adj-steps", type=int, default=20,
                     help="steps of the Navier-Stokes adjoint timing (0 skips it)")
+    ap.add_argument("--ns-ke-adjoint", type=int, default=1,
+                    help="time the adjoint of the final kinetic energy through all NS steps (0 skips it)")
     ap.add_argument("--curved-steps", type=int, default=100,
                     help="steps of the curved-geometry leg (0 skips it)")
     ap.add_argument("--curved-only", action="store_true",

@@ -206,6 +206,15 @@ dg_status dg_quad_points(const dg_mesh* mesh, double* xyz_out);
  * Q_store.  Asynchronous. */
 dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cudaStream_t stream);
 
+/* The right-hand side of that projection, b = V^T W J q per element:
+ * b_i = the volume-rule integral of q times phi_i (with the pointwise J of a
+ * curved element), for point values q laid out as dg_project reads them,
+ * written to b_store (device, storage layout); dg_project is M^{-1} b.  It is
+ * also the gradient of a functional sum_q w_q J_q f(U_q) with respect to the
+ * modal state when q = df/dU at the points (the seed of an adjoint).
+ * Asynchronous. */
+dg_status dg_load_vector(dg_mesh* mesh, const double* q_points, double* b_store, cudaStream_t stream);
+
 /* The inverse direction: the modal expansion of Q_store evaluated at the
  * volume quadrature points, U = V Q (the first step of Eq. 1's residual and
  * of Algorithm 1's nodal form), written to u_points (device, caller order,

@@ -55,6 +55,7 @@ _SIGS = {
     "dg_quad_points": [_P, _P],
     "dg_project": [_P, _P, _P, _P],
     "dg_eval_nodal": [_P, _P, _P, _P],
+    "dg_load_vector": [_P, _P, _P, _P],
     "dg_rhs": [_P, _P, _P, _P],
     "dg_rk_step": [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P],
     "dg_rhs_vjp": [_P, _P, _P, _P, _P],
@@ -256,6 +257,13 @@ class Mesh:
             Q_store = self.empty()
         _check(load().dg_project(self.handle, _ptr(q_points), _ptr(Q_store), _stream(stream)))
         return Q_store
+
+    def load_vector(self, q_points, b_store=None, stream=None):
+        """dg_load_vector: b = V^T W J q (storage layout) for point values q (CUDA tensor)."""
+        if b_store is None:
+            b_store = self.empty()
+        _check(load().dg_load_vector(self.handle, _ptr(q_points), _ptr(b_store), _stream(stream)))
+        return b_store
 
     def eval_nodal(self, Q_store, out=None, stream=None):
         """dg_eval_nodal: U = V Q at the volume points, per caller element [5, n^3] (CUDA tensor)."""

@@ -381,7 +381,7 @@ struct dg_mesh {
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
     dgk::Ctx c = ctx();
     timed(true, st, [&] {
-      const bool per_elem = mode == dgk::kProject || mode == dgk::kEval;   // one-shot maps: per-type launches
+      const bool per_elem = mode == dgk::kProject || mode == dgk::kEval || mode == dgk::kLoad;   // one-shot maps
       if (scheduler == DG_SCHED_BALANCED && !per_elem) {
         for (const auto& G : groups) {
           dgk::Ctx cg = c;
@@ -821,6 +821,14 @@ dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cud
   return DG_OK;
 }
 
+dg_status dg_load_vector(dg_mesh* mesh, const double* q_points, double* b_store, cudaStream_t stream) {
+  if (!mesh || !q_points || !b_store) return fail(DG_ERR_ARG, "null argument");
+  dgk::StageArgs a{q_points, b_store, nullptr, 0.0, 0.0, 0.0};
+  mesh->element_phase(dgk::kLoad, a, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 dg_status dg_eval_nodal(dg_mesh* mesh, const double* Q_store, double* u_points, cudaStream_t stream) {
   if (!mesh || !Q_store || !u_points) return fail(DG_ERR_ARG, "null argument");
   dgk::StageArgs a{Q_store, u_points, nullptr, 0.0, 0.0, 0.0};
@@ -956,8 +964,12 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 namespace {
 // Reverse sweep of dg_rk_vjp over the checkpoints ck[seg] (Q at the start of
 // segment seg of c steps); Q0bar already holds QKbar.
+// Segments starting at or after step `tail0` (a multiple of c) already have
+// their stage data in the stage store, stage g = 5 (step - tail0) + s (kept by
+// dg_rk_vjp's own forward pass); earlier segments are recomputed from their
+// checkpoints ck[seg].
 dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps, int c, double* Q0bar,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, int tail0) {
   const size_t n = (size_t)mesh->h.n_dof, bytes = sizeof(double) * n;
   const int nseg = (nsteps + c - 1) / c;
   // forward data of one segment's stages kept for the reverse pass when the
@@ -971,11 +983,15 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
   DG_CUDA(cudaMemsetAsync(mesh->d_Kbar, 0, bytes, stream));
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int steps = std::min(c, nsteps - seg * c);
-    DG_CUDA(cudaMemcpyAsync(Qw, ck + (size_t)seg * n, bytes, cudaMemcpyDeviceToDevice, stream));
-    mesh->enqueue_rk_stages(Qw, Kw, dt, steps, keep ? nullptr : stages, stream, keep, false);
+    const bool kept = keep && seg * c >= tail0;
+    const int g0 = kept ? 5 * (seg * c - tail0) : 0;
+    if (!kept) {
+      DG_CUDA(cudaMemcpyAsync(Qw, ck + (size_t)seg * n, bytes, cudaMemcpyDeviceToDevice, stream));
+      mesh->enqueue_rk_stages(Qw, Kw, dt, steps, keep ? nullptr : stages, stream, keep, false);
+    }
     for (int step = steps - 1; step >= 0; --step)
       for (int s = 4; s >= 0; --s) {
-        const int g = 5 * step + s;
+        const int g = g0 + 5 * step + s;
         dgk::VjpArgs va{keep ? nullptr : stages + (size_t)g * n, nullptr, mesh->d_Kbar, Q0bar, kLsA[s], kLsB[s], dt,
                         1, 0};
         mesh->enqueue_vjp(va, stream, keep ? g : -1);
@@ -994,7 +1010,8 @@ dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c
 }
 
 // ckpt_every == 0: the longest segment whose kept stage data (5 stages per
-// step) fit in half of the device memory that is free now, at least 1 step.
+// step) fit in half of the device memory that is free now (the mesh's own
+// stage store counting as free: it is reused or replaced), at least 1 step.
 int auto_ckpt(const dg_mesh* mesh, int nsteps) {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -1002,7 +1019,8 @@ int auto_ckpt(const dg_mesh* mesh, int nsteps) {
     return 1;
   }
   const double per_step = 5.0 * sizeof(double) * (double)mesh->stage_doubles();
-  const double fit = 0.5 * (double)free_b / per_step;
+  const double avail = (double)free_b + sizeof(double) * (double)mesh->sstore_doubles;
+  const double fit = 0.5 * avail / per_step;
   return (int)std::max(1.0, std::min((double)nsteps, std::floor(fit)));
 }
 }  // namespace
@@ -1024,6 +1042,18 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   if (nsteps == 0) return DG_OK;
   const int c = ckpt_every == 0 ? auto_ckpt(mesh, nsteps) : std::min(ckpt_every, nsteps);
   const int nseg = (nsteps + c - 1) / c;
+  // The forward pass keeps the stage data of the final steps itself, as many
+  // whole segments as fit in half of the free device memory: those segments
+  // are reversed without being recomputed.  The steps before tail0 only
+  // place checkpoints.
+  int tail0 = nsteps;
+  if (mesh->keep_stages) {
+    const int fit = auto_ckpt(mesh, nsteps);
+    int t0 = std::max(0, nsteps - fit);
+    t0 = ((t0 + c - 1) / c) * c;
+    if (t0 < nsteps && mesh->ensure_stage_store(5 * std::max(c, nsteps - t0))) tail0 = t0;
+  }
+  const int nseg0 = (tail0 + c - 1) / c;   // segments that get checkpoints
   if (!mesh->d_ckpt_q || mesh->ckpt_q_doubles < (size_t)(nseg + 2) * n) {
     if (mesh->d_ckpt_q) cudaFree(mesh->d_ckpt_q);
     mesh->d_ckpt_q = nullptr;
@@ -1035,12 +1065,13 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   double* Kw = Qw + n;
   double* ck = Kw + n;
   DG_CUDA(cudaMemcpyAsync(Qw, Q0_store, bytes, cudaMemcpyDeviceToDevice, stream));
-  for (int seg = 0; seg < nseg - 1; ++seg) {
+  for (int seg = 0; seg < nseg0; ++seg) {
     DG_CUDA(cudaMemcpyAsync(ck + (size_t)seg * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
-    mesh->enqueue_rk_stages(Qw, Kw, dt, c, nullptr, stream);
+    const int steps = std::min(c, tail0 - seg * c);
+    if (seg < nseg0 - 1 || tail0 < nsteps) mesh->enqueue_rk_stages(Qw, Kw, dt, steps, nullptr, stream);
   }
-  DG_CUDA(cudaMemcpyAsync(ck + (size_t)(nseg - 1) * n, Qw, bytes, cudaMemcpyDeviceToDevice, stream));
-  return rk_vjp_reverse(mesh, ck, dt, nsteps, c, Q0bar, stream);
+  if (tail0 < nsteps) mesh->enqueue_rk_stages(Qw, Kw, dt, nsteps - tail0, nullptr, stream, true, false);
+  return rk_vjp_reverse(mesh, ck, dt, nsteps, c, Q0bar, stream, tail0);
 }
 
 dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double dt, int nsteps, int ckpt_every,
@@ -1051,7 +1082,7 @@ dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double
   const size_t bytes = sizeof(double) * (size_t)mesh->h.n_dof;
   if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
   if (nsteps == 0) return DG_OK;
-  return rk_vjp_reverse(mesh, ckpt_store, dt, nsteps, std::min(ckpt_every, nsteps), Q0bar, stream);
+  return rk_vjp_reverse(mesh, ckpt_store, dt, nsteps, std::min(ckpt_every, nsteps), Q0bar, stream, nsteps);
 }
 
 dg_status dg_rk_step_checkpointed(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps,

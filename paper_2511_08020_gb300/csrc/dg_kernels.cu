@@ -1110,6 +1110,23 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
   const int64_t coff = ANY ? c.slot_coff[s] : -1;
   const double* cblk = coff >= 0 ? c.cpool + coff : nullptr;
   const bool dense = cblk && T.type != HEX;
+  if (MODE == kLoad) {
+    // b = V^T W J q: pointwise J_q (curved) or the element's constant J
+    const int64_t e = c.elem_of_slot[s];
+    const double* vals = io.Qin + c.elem_voff[e];
+    const double* W = c.dpool + T.W;
+    if (cblk) {
+      const double* Jq = cblk + 9 * nQ;
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * Jq[w % nQ] * vals[w];
+    } else {
+      for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = W[w % nQ] * vals[w];
+    }
+    __syncthreads();
+    Epilogue ep{Epilogue::kStore, false, cblk ? 1.0 : 1.0 / c.geo[s].invJ, io.Qout + qoff, nullptr, nullptr, nullptr,
+                nullptr, 0.0, 0.0, 0.0};
+    nodal_to_modal<false>(c, T, bufA, bufG, lane, ep);
+    return;
+  }
   if (MODE == kProject) {
     const int64_t e = c.elem_of_slot[s];
     const double* vals = io.Qin + c.elem_voff[e];
@@ -2350,6 +2367,7 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm, bo
   if ((e = set_mode<kBwdRkFwd>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kProject>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kEval>(bmax)) != cudaSuccess) return e;
+  if ((e = set_mode<kLoad>(bmax)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel<false>, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_kernel<true>, fbytes)) != cudaSuccess) return e;
@@ -2382,6 +2400,7 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
     case kBwdRkFwd: launch_mode<kBwdRkFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kProject: launch_mode<kProject>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kEval: launch_mode<kEval>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kLoad: launch_mode<kLoad>(c, a, s, balanced, grid, wpb, bytes, st); break;
   }
 }
 

@@ -35,7 +35,8 @@ enum ElemMode : int {
   kGather = 5,     // copy caller layout -> storage layout
   kScatter = 6,    // copy storage layout -> caller layout
   kNsVolume = 7,   // Navier-Stokes: BR1 lifting, gradient traces, volume residual H
-  kEval = 8        // modal -> nodal values at the volume points (caller element order)
+  kEval = 8,       // modal -> nodal values at the volume points (caller element order)
+  kLoad = 9        // load vector V^T W J q of point values (Algorithm 1's projection without M^{-1})
 };
 
 struct Ctx {

@@ -80,6 +80,16 @@ def test_curved_project_eval_and_points(dg, kind, m, N):
     assert np.abs(U - Uref).max() < 1e-12 * np.abs(Uref).max()
 
 
+def test_curved_load_vector(dg):
+    box, o, mesh = setup(dg, "four", 4, 3)
+    n = 4
+    vals = di.tgv_state(mesh.quad_points()).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2)
+    b = mesh.get_state(mesh.load_vector(torch.from_numpy(vals.reshape(-1).copy()).cuda()))
+    ref = np.concatenate([((vals[e] * (o.ops[o.mesh.etype[e]].w * o.Jq[e])) @ o.ops[o.mesh.etype[e]].V).ravel()
+                          for e in range(box.n_elems)])
+    assert rel_err(b, ref, var_index(o.mesh.nM)) < TOL
+
+
 @pytest.mark.parametrize("kind,m,N,flux,nsteps", [("mixed", 3, 3, "lf", 2), ("four", 4, 2, "roe", 1)])
 def test_curved_rk_step_parity(dg, kind, m, N, flux, nsteps):
     box, o, mesh = setup(dg, kind, m, N, flux)

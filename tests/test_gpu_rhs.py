@@ -315,3 +315,21 @@ def test_weighted_partition_after_rebalance(dg):
     ref = dg.Mesh(box, 4, scheduler="naive")
     assert torch.equal(R, ref.rhs(ref.set_state(torch.from_numpy(Q).cuda())))
     assert imb_weighted <= 2 * imb_static + 0.05, (imb_static, imb_weighted)
+
+
+@pytest.mark.parametrize("kind,m,N", [("mixed", 3, 3), ("four", 4, 2)])
+def test_load_vector_parity(dg, kind, m, N):
+    """dg_load_vector = V^T W J q per element (the right-hand side of the
+    Algorithm 1 projection), against the oracle's rule; dg_project of the
+    same values is its M^{-1}."""
+    box, o, mesh = setup(dg, kind, m, N, "lf", 5)
+    n = N + 1
+    vals = di.tgv_state(mesh.quad_points()).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).reshape(-1)
+    b = mesh.get_state(mesh.load_vector(torch.from_numpy(vals).cuda()))
+    pv = vals.reshape(box.n_elems, 5, n ** 3)
+    ref = np.concatenate([((pv[e] * (o.ops[o.mesh.etype[e]].w * o.mesh.J[e])) @ o.ops[o.mesh.etype[e]].V).ravel()
+                          for e in range(box.n_elems)])
+    assert rel_err(b, ref, var_index(o.mesh.nM)) < TOL
+    Qp = mesh.get_state(mesh.project(torch.from_numpy(vals).cuda()))
+    back = np.concatenate([o.apply_minv(e, o.mesh.block(ref, e)).ravel() for e in range(box.n_elems)])
+    assert rel_err(Qp, back, var_index(o.mesh.nM)) < TOL
