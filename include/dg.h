@@ -259,11 +259,13 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
                              cudaStream_t stream);
 
 /* Q0bar = (dQ_K/dQ_0)^T QKbar for nsteps LSERK steps of size dt from Q0_store.
- * Stage states are recomputed from checkpoints of Q stored every ckpt_every
- * steps in library memory; ckpt_every = 0 picks the longest segment whose
- * kept stage data fit in half of the free device memory (fewest forward
- * passes; see dg_set_adjoint_storage).  The result does not depend on the
- * segment length.  No counterpart in the paper.  Asynchronous. */
+ * A forward pass from Q0 keeps the stage data of as many final segments of
+ * ckpt_every steps as fit in half of the free device memory (see
+ * dg_set_adjoint_storage) and stores Q at the start of every earlier
+ * segment; the reverse sweep uses the kept data directly and recomputes the
+ * earlier segments from their checkpoints.  ckpt_every = 0 picks the longest
+ * segment whose stage data fit in that memory.  The result does not depend on
+ * the segment length.  No counterpart in the paper.  Asynchronous. */
 dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps, int ckpt_every,
                     const double* QKbar, double* Q0bar, cudaStream_t stream);
 
@@ -281,14 +283,16 @@ dg_status dg_rk_step_checkpointed(dg_mesh* mesh, double* Q_store, double* K_stor
 dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double dt, int nsteps, int ckpt_every,
                                  const double* QKbar, double* Q0bar, cudaStream_t stream);
 
-/* Memory/time trade-off of dg_rk_vjp.  keep_stages = 1 (default): the forward
- * pass of each checkpoint segment keeps, per stage, the nodal state and the
- * own-side traces (Euler: (H + F) doubles per stage, H = 5 sum_e n^3 and
- * F = the face buffer, 10 n^2 per face; Navier-Stokes: 4 (H + F), adding
- * the gradient traces and the nodal gradient), 5 ckpt_every stages at a time,
- * so the reverse stages do not recompute them.  If that memory cannot be
- * allocated dg_rk_vjp silently recomputes.  keep_stages = 0: always recompute
- * (and free the store).  Results are bitwise identical either way. */
+/* Memory/time trade-off of dg_rk_vjp.  keep_stages = 1 (default): forward
+ * passes keep, per stage, the nodal state and the own-side traces (Euler:
+ * (H + F) doubles per stage, H = 5 sum_e n^3 and F = the face buffer,
+ * 10 n^2 per face; Navier-Stokes: 4 (H + F), adding the gradient traces and
+ * the nodal gradient) -- dg_rk_vjp's first pass for its final segments (up to
+ * half of the free device memory), each segment recomputation for its own
+ * 5 ckpt_every stages -- so the reverse stages do not recompute them.  The
+ * store stays allocated with the mesh.  If that memory cannot be allocated
+ * dg_rk_vjp silently recomputes.  keep_stages = 0: always recompute (and free
+ * the store).  Results are bitwise identical either way. */
 dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages);
 
 /* Governing equations of dg_rhs / dg_rk_step (a new mesh solves the Euler
