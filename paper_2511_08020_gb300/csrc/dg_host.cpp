@@ -313,8 +313,8 @@ int Tables::add(int type, int N, std::string* err) {
     if (mode != t.nM) { *err = "internal: mode count mismatch"; return -1; }
     std::vector<int> order(t.ncols);
     for (int col = 0; col < t.ncols; ++col) order[col] = col;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-      return ipool[t.col_len + x] > ipool[t.col_len + y];
+    std::stable_sort(order.begin(), order.end(), [&](int ca, int cb) {
+      return ipool[t.col_len + ca] > ipool[t.col_len + cb];
     });
     t.col_order = ialloc(t.ncols);
     for (int r = 0; r < t.ncols; ++r) ipool[t.col_order + r] = order[r];
@@ -1040,15 +1040,15 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
           abc[fd.fixed] = fd.end ? 1.0 : -1.0;
           abc[fd.alpha] = x[ia];
           abc[fd.beta] = x[ib];
-          double F[3][3], xr[3], ts[3], tt[3], cr[3];
-          element_map(t0, Xrel, abc[0], abc[1], abc[2], F, xr);
+          double Fp[3][3], xr[3], ts[3], tt[3], cr[3];
+          element_map(t0, Xrel, abc[0], abc[1], abc[2], Fp, xr);
           for (int d = 0; d < 3; ++d) {
-            ts[d] = F[d][0] * tsr[0] + F[d][1] * tsr[1] + F[d][2] * tsr[2];
-            tt[d] = F[d][0] * ttr[0] + F[d][1] * ttr[1] + F[d][2] * ttr[2];
+            ts[d] = Fp[d][0] * tsr[0] + Fp[d][1] * tsr[1] + Fp[d][2] * tsr[2];
+            tt[d] = Fp[d][0] * ttr[0] + Fp[d][1] * ttr[1] + Fp[d][2] * ttr[2];
           }
           cross(ts, tt, cr);
           const double S = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-          const double sg = (det3(F) > 0 ? 1.0 : -1.0) * orient;
+          const double sg = (det3(Fp) > 0 ? 1.0 : -1.0) * orient;
           for (int d = 0; d < 3; ++d) M.fgeo[base + (size_t)d * n2 + p] = sg * cr[d] / S;
           M.fgeo[base + (size_t)3 * n2 + p] = fw[p] * S;
           if (p == 0) {
@@ -1223,8 +1223,8 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
       for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j)
           for (int k = 0; k < n; ++k) {
-            double F[3][3], xr[3];
-            element_map(t, Xrel, x[i], x[j], x[k], F, xr);
+            double Fq[3][3], xr[3];
+            element_map(t, Xrel, x[i], x[j], x[k], Fq, xr);
             size_t q = (size_t)e * n * n * n + (size_t)(i * n + j) * n + k;
             for (int d = 0; d < 3; ++d) M.quad_xyz[3 * q + d] = X0[d] + xr[d];
           }
