@@ -182,6 +182,22 @@ dg_status dg_batch_layout(const dg_mesh* mesh, int64_t* instance_elem_off, int64
  * slot_of_elem (host, [n_elems], may be NULL) receives the Hilbert slots. */
 dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_xyz, int64_t* slot_of_elem);
 
+/* Host-only (no GPU): the space-filling-curve partition of Sec. 3 for nparts
+ * ranks and the halo each rank needs -- the bookkeeping of a multi-GPU
+ * decomposition of one mesh (this library runs one GPU per mesh; the plan is
+ * what a partitioned run, or a redistribution after the imbalance trigger,
+ * would exchange).  Parts are contiguous runs of the Hilbert order of
+ * (nearly) equal weight, an element weighing type_weight[its dg_elem_type]
+ * (host [4], e.g. the per-type costs of dg_cost_table; NULL: 1 each).
+ * part_of_elem (host, [n_elems]) receives each caller element's part;
+ * halo_off (host, [nparts + 1]) the offsets of every part's halo list in
+ * halo_elems (host, [halo_off[nparts]], may be NULL to query the sizes): the
+ * caller indices, ascending, of the elements of other parts that share a face
+ * with the part's elements (the states a rank must receive to evaluate Eq. 1
+ * on its own elements).  1 <= nparts <= n_elems. */
+dg_status dg_partition_plan(const dg_mesh_desc* desc, int nparts, const double* type_weight, int64_t* part_of_elem,
+                            int64_t* halo_off, int64_t* halo_elems);
+
 /* n_dof = 5 * sum_e nM(type_e, N).  slot_of_elem (host, [n_elems], may be
  * NULL) receives the Hilbert slot of every caller element.  counts (host,
  * [6], may be NULL) receives n_elems, n_faces, and the number of hex, prism,

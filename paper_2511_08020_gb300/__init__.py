@@ -13,7 +13,7 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "probe_fp64_peak", "probe_fp64_mixed", "FLUX", "SCHED",
+__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "partition_plan", "probe_fp64_peak", "probe_fp64_mixed", "FLUX", "SCHED",
            "PHYSICS", "GEOMETRY", "load"]
 
 FLUX = {"lf": 0, "roe": 1}
@@ -49,6 +49,7 @@ _SIGS = {
     "dg_mesh_geometry": [_P, _P, _P, _P],
     "dg_mesh_destroy": [_P],
     "dg_mesh_check": [ctypes.POINTER(MeshDesc), _P, _P, _P],
+    "dg_partition_plan": [ctypes.POINTER(MeshDesc), ctypes.c_int, _P, _P, _P, _P],
     "dg_mesh_layout": [_P, _P, _P, _P],
     "dg_set_state": [_P, _P, ctypes.c_int, _P, _P],
     "dg_get_state": [_P, _P, _P, ctypes.c_int, _P],
@@ -153,6 +154,21 @@ def check_mesh(box, N, geometry="affine"):
     slots = np.zeros(len(keep["etype"]), dtype=np.int64)
     _check(load().dg_mesh_check(ctypes.byref(d), _ptr(counts), _ptr(qp), _ptr(slots)))
     return counts, qp, slots
+
+
+def partition_plan(box, N, nparts, type_weight=None, geometry="affine"):
+    """dg_partition_plan (host-only): (part_of_elem [E], halo_off [nparts+1], halo_elems)."""
+    import numpy as np
+    d, keep = _desc(box, N, geometry=geometry)
+    E = len(keep["etype"])
+    part = np.zeros(E, dtype=np.int64)
+    off = np.zeros(nparts + 1, dtype=np.int64)
+    tw = None if type_weight is None else np.ascontiguousarray(type_weight, dtype=np.float64)
+    twp = ctypes.c_void_p(0) if tw is None else _ptr(tw)
+    _check(load().dg_partition_plan(ctypes.byref(d), int(nparts), twp, _ptr(part), _ptr(off), ctypes.c_void_p(0)))
+    halo = np.zeros(max(1, int(off[-1])), dtype=np.int64)
+    _check(load().dg_partition_plan(ctypes.byref(d), int(nparts), twp, _ptr(part), _ptr(off), _ptr(halo)))
+    return part, off, halo[:int(off[-1])]
 
 
 def probe_fp64_peak():

@@ -762,6 +762,22 @@ dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_
   return DG_OK;
 }
 
+dg_status dg_partition_plan(const dg_mesh_desc* desc, int nparts, const double* type_weight, int64_t* part_of_elem,
+                            int64_t* halo_off, int64_t* halo_elems) {
+  if (!desc || !part_of_elem || !halo_off) return fail(DG_ERR_ARG, "null argument");
+  dgh::HostMesh h;
+  std::string err;
+  int r = dgh::build_mesh(input_of(desc), &h, &err);
+  if (r != 0) return fail((dg_status)r, err);
+  std::vector<int64_t> part, off, halo;
+  r = dgh::partition_plan(h, nparts, type_weight, &part, &off, &halo, &err);
+  if (r != 0) return fail((dg_status)r, err);
+  std::memcpy(part_of_elem, part.data(), sizeof(int64_t) * part.size());
+  std::memcpy(halo_off, off.data(), sizeof(int64_t) * off.size());
+  if (halo_elems) std::memcpy(halo_elems, halo.data(), sizeof(int64_t) * halo.size());
+  return DG_OK;
+}
+
 dg_status dg_mesh_destroy(dg_mesh* mesh) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   cudaDeviceSynchronize();

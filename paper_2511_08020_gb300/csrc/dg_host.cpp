@@ -1246,6 +1246,63 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   return 0;
 }
 
+int partition_plan(const HostMesh& M, int nparts, const double* type_weight, std::vector<int64_t>* part_of_elem,
+                   std::vector<int64_t>* halo_off, std::vector<int64_t>* halo_elems, std::string* err) {
+  const int64_t E = M.n_elems;
+  if (nparts < 1 || nparts > E) { *err = "nparts must be between 1 and the number of elements"; return -1; }
+  if (M.inst_elem_off.size() != 2) { *err = "partition plans are for single meshes"; return -7; }
+  // equal-weight cuts of the prefix sum along the Hilbert order
+  std::vector<double> w(E);
+  double total = 0.0;
+  for (int64_t s = 0; s < E; ++s) {
+    const double ws = type_weight ? type_weight[(int)M.slot_type[s]] : 1.0;
+    if (!(ws > 0.0) || !std::isfinite(ws)) { *err = "element weights must be finite and positive"; return -1; }
+    w[s] = ws;
+    total += ws;
+  }
+  part_of_elem->assign(E, -1);
+  {
+    double acc = 0.0;
+    int p = 0;
+    for (int64_t s = 0; s < E; ++s) {
+      // part p takes the slots whose weight midpoint lies in [p W / P, (p+1) W / P)
+      const double mid = acc + 0.5 * w[s];
+      while (p + 1 < nparts && mid >= total * (double)(p + 1) / (double)nparts) ++p;
+      (*part_of_elem)[M.elem_of_slot[s]] = p;
+      acc += w[s];
+    }
+  }
+  // faces -> the two slots: trace offsets are f (2 sides) (5 n^2), side 1 at + 5 n^2
+  const int64_t side = 5 * (int64_t)M.n * M.n;
+  std::vector<int64_t> face_slot(2 * (size_t)M.n_faces, -1);
+  for (int64_t s = 0; s < E; ++s)
+    for (int lf = 0; lf < 6; ++lf) {
+      const int64_t t = M.slot_ftoff[(size_t)s * 6 + lf];
+      if (t < 0) continue;
+      face_slot[(size_t)(t / side)] = s;   // index 2 f + side
+    }
+  std::vector<std::vector<int64_t>> halo(nparts);
+  for (int64_t f = 0; f < M.n_faces; ++f) {
+    const int64_t a = face_slot[2 * f], b = face_slot[2 * f + 1];
+    if (a < 0 || b < 0) { *err = "internal: face without two sides"; return -1; }
+    const int64_t ea = M.elem_of_slot[a], eb = M.elem_of_slot[b];
+    const int64_t pa = (*part_of_elem)[ea], pb = (*part_of_elem)[eb];
+    if (pa != pb) {
+      halo[pa].push_back(eb);
+      halo[pb].push_back(ea);
+    }
+  }
+  halo_off->assign(nparts + 1, 0);
+  halo_elems->clear();
+  for (int p = 0; p < nparts; ++p) {
+    std::sort(halo[p].begin(), halo[p].end());
+    halo[p].erase(std::unique(halo[p].begin(), halo[p].end()), halo[p].end());
+    halo_elems->insert(halo_elems->end(), halo[p].begin(), halo[p].end());
+    (*halo_off)[p + 1] = (int64_t)halo_elems->size();
+  }
+  return 0;
+}
+
 int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* err) {
   if (ins.empty()) { *err = "empty batch"; return -1; }
   HostMesh& M = *out;

@@ -108,6 +108,15 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
 
 uint64_t hilbert_key3(uint32_t x, uint32_t y, uint32_t z, int bits);
 
+// Space-filling-curve partition of Sec. 3 for nparts ranks: contiguous runs
+// of the Hilbert order of (nearly) equal weight, the weight of an element
+// type_weight[its type] (1 each when null); part_of_elem [n_elems] in caller
+// order.  Halo of every part: the elements of other parts that share a face
+// with one of its elements, ascending caller indices, part p's list at
+// halo_elems[halo_off[p] .. halo_off[p+1]).  Plain meshes only.
+int partition_plan(const HostMesh& M, int nparts, const double* type_weight, std::vector<int64_t>* part_of_elem,
+                   std::vector<int64_t>* halo_off, std::vector<int64_t>* halo_elems, std::string* err);
+
 // Static per-element FP64 work estimate of one stage (initial chunk weights).
 double static_cost(const dgk::TypeTab& t);
 
