@@ -391,6 +391,19 @@ dg_status dg_cost_table(dg_mesh* mesh, double* ns_per_elem, double* imbalance, c
  * *rebuilt (may be NULL) tells whether it did.  Synchronises. */
 dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stream);
 
+/* The imbalance trigger inside the time loop (Sec. 3: the paper checks the
+ * measured imbalance during the run and redistributes when it exceeds the
+ * threshold): with nsteps > 0, dg_rk_step runs dg_rebalance(force = 0) once
+ * at least nsteps steps have been enqueued since the last check (that call
+ * synchronises `stream`, so it must not run inside a stream capture).
+ * nsteps = 0 (default) turns it off.  Results do not depend on it (every
+ * schedule is bitwise identical). */
+dg_status dg_set_rebalance_interval(dg_mesh* mesh, int nsteps);
+
+/* Host [1] counters of the automatic trigger: checks made, tables rebuilt
+ * (either may be NULL). */
+dg_status dg_rebalance_stats(const dg_mesh* mesh, int64_t* checks, int64_t* rebalances);
+
 /* Phase timing: with profiling on, dg_rhs and the dg_rk_step graph record
  * CUDA events around every element-kernel and face-kernel phase (events
  * inside the captured graph; a few microseconds of overhead per phase).

@@ -70,6 +70,8 @@ _SIGS = {
     "dg_set_adjoint_storage": [_P, ctypes.c_int],
     "dg_cost_table": [_P, _P, _P, _P],
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
+    "dg_set_rebalance_interval": [_P, ctypes.c_int],
+    "dg_rebalance_stats": [_P, _P, _P],
     "dg_sync": [_P, _P],
     "dg_probe_fp64_peak": [_P, _P],
     "dg_probe_fp64_mixed": [_P],
@@ -356,6 +358,15 @@ class Mesh:
         r = ctypes.c_int()
         _check(load().dg_rebalance(self.handle, int(bool(force)), ctypes.byref(r), _stream(stream)))
         return bool(r.value)
+
+    def set_rebalance_interval(self, nsteps):
+        """dg_set_rebalance_interval: check the imbalance every nsteps steps of rk_step (0: off)."""
+        _check(load().dg_set_rebalance_interval(self.handle, int(nsteps)))
+
+    def rebalance_stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().dg_rebalance_stats(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def set_element_warps(self, warps):
         _check(load().dg_set_element_warps(self.handle, int(warps)))

@@ -141,6 +141,9 @@ struct dg_mesh {
   int64_t* d_chunks_weighted = nullptr;   // equal-weight Hilbert segments (DG_SCHED_WEIGHTED)
   int64_t nchunks_weighted = 0;
   bool fused = true;  // backward of stage s and forward of stage s+1 in one launch
+  // automatic imbalance trigger of dg_rk_step (dg_set_rebalance_interval)
+  int rebalance_every = 0, steps_since_check = 0;
+  int64_t rebalances = 0, checks = 0;
   double weight[dgk::kMaxTabs] = {};  // chunk weights in use per (type, N) table (ns or modelled)
 
   std::vector<double> static_weights() const {
@@ -896,6 +899,35 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
   }
   mesh->last_pool = 0;
   DG_CUDA(cudaGraphLaunch(mesh->gexec, stream));
+  if (mesh->rebalance_every > 0) {
+    // the imbalance trigger of Sec. 3 in the time loop: every
+    // rebalance_every steps compare the measured SM load imbalance with the
+    // threshold and rebuild the chunk tables from the measured costs
+    mesh->steps_since_check += nsteps;
+    if (mesh->steps_since_check >= mesh->rebalance_every) {
+      mesh->steps_since_check = 0;
+      int rebuilt = 0;
+      dg_status st = dg_rebalance(mesh, 0, &rebuilt, stream);
+      if (st != DG_OK) return st;
+      mesh->checks++;
+      mesh->rebalances += rebuilt;
+    }
+  }
+  return DG_OK;
+}
+
+dg_status dg_set_rebalance_interval(dg_mesh* mesh, int nsteps) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (nsteps < 0) return fail(DG_ERR_ARG, "the interval must be >= 0");
+  mesh->rebalance_every = nsteps;
+  mesh->steps_since_check = 0;
+  return DG_OK;
+}
+
+dg_status dg_rebalance_stats(const dg_mesh* mesh, int64_t* checks, int64_t* rebalances) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (checks) *checks = mesh->checks;
+  if (rebalances) *rebalances = mesh->rebalances;
   return DG_OK;
 }
 

@@ -333,3 +333,29 @@ def test_load_vector_parity(dg, kind, m, N):
     Qp = mesh.get_state(mesh.project(torch.from_numpy(vals).cuda()))
     back = np.concatenate([o.apply_minv(e, o.mesh.block(ref, e)).ravel() for e in range(box.n_elems)])
     assert rel_err(Qp, back, var_index(o.mesh.nM)) < TOL
+
+
+def test_automatic_rebalance_trigger(dg):
+    """dg_set_rebalance_interval: dg_rk_step checks the measured imbalance
+    every 2 steps; with a zero threshold every check rebuilds the chunk
+    tables from the measured costs, and the state stays bitwise equal to a
+    run without the trigger."""
+    box = make_box("mixed", 4, seed=1)
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    o = Oracle(from_box(box, 3))
+    Q = torch.from_numpy(state(o)).cuda()
+    a = dg.Mesh(box, 3, imbalance_threshold=1e-12)
+    b = dg.Mesh(box, 3)
+    a.set_rebalance_interval(2)
+    Qa, Qb = a.set_state(Q), b.set_state(Q)
+    Ka, Kb = a.empty(), b.empty()
+    for _ in range(5):
+        a.rk_step(Qa, Ka, 1e-3, 1)
+        b.rk_step(Qb, Kb, 1e-3, 1)
+    checks, rebuilt = a.rebalance_stats()
+    assert checks == 2 and rebuilt == 2
+    assert torch.equal(Qa, Qb)
+    a.set_rebalance_interval(0)
+    a.rk_step(Qa, Ka, 1e-3, 2)
+    assert a.rebalance_stats() == (2, 2)
