@@ -1843,6 +1843,7 @@ __global__ void face_ns_kernel(Ctx c) {
         for (int t = 0; t < 15; ++t) g[t] = V1[t * n2 + j];
       } else {
         const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
+#pragma unroll
         for (int t = 0; t < 15; ++t) {
           double acc = 0.0;
           for (int j = 0; j < n2; ++j) acc = fma(D[j], V1[t * n2 + j], acc);
@@ -2116,6 +2117,7 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
         for (int t = 0; t < 15; ++t) gr[t] = V1[t * n2 + j];
       } else {
         const double* D = c.dense + (size_t)(-1 - R.map) + (size_t)p * n2;
+#pragma unroll
         for (int t = 0; t < 15; ++t) {
           double acc = 0.0;
           for (int j = 0; j < n2; ++j) acc = fma(D[j], V1[t * n2 + j], acc);
