@@ -140,7 +140,7 @@ FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 2
 # (backward + LSERK + forward) of this workload, from the ncu capture
 # summarised in profiles/element_kernel_16cube_N4.md; set to None whenever
 # the element kernel changes until it is captured again.
-NCU_TRAFFIC_FUSED_LAUNCH = (154.120448 + 142.546432) * 1e6
+NCU_TRAFFIC_FUSED_LAUNCH = (154.148864 + 146.578432) * 1e6
 
 
 def element_bytes(t, N):
