@@ -43,6 +43,16 @@ import dg_inputs as di  # noqa: E402
 MESH_M, MESH_SEED, N_DEG, CFL = 16, 2, 4, 0.5
 GAMMA = 1.4
 WORKLOAD = "16^3-cube periodic box, mixed hex/prism/pyramid (seed 2), N=4, Euler TGV (Ma 0.1), LF, CFL 0.5, FP64"
+METRIC = "FP64 RHS DOF-updates/s per RK stage (balanced vs naive); adjoint/forward cost"
+
+
+def workload_config(box, faces, dof, dt, flux, ws):
+    """The workload part of the JSON line's config (the same for both arms)."""
+    counts = [int((box.etype == t).sum()) for t in range(4)]
+    return {"workload": WORKLOAD, "elements": box.n_elems,
+            "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), counts)), "faces": faces,
+            "dof_per_var": dof, "dt": dt, "flux": flux,
+            "l2": "working set ~180 MB > 129 MB L2 (no flush)", "parallelism": f"replicas x{ws}"}
 
 
 # ----------------------------------------------------------------------------- model
@@ -277,8 +287,12 @@ class OracleSample:
         from oracle.dg import Oracle
         from oracle.mesh import from_box
         box = build_workload()
+        self.box = box
         self.n_elems = box.n_elems
         self.o = o = Oracle(from_box(box, N_DEG), flux=flux)
+        self.dof_total = int(o.mesh.nM.sum())
+        xyz = np.concatenate([o.quad_points(e) for e in range(box.n_elems)])
+        self.dt = tgv_dt(box, xyz, N_DEG)
         rng = np.random.default_rng(0)
         self.sample = np.sort(rng.choice(box.n_elems, size=size, replace=False))
         self.Q = np.zeros(o.mesh.n_dof())
@@ -316,11 +330,13 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = smp.dof * 5 * args.steps / dt
     sample_txt = smp.describe()
-    line = {"metric": "FP64 RHS DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
+    cfg = workload_config(smp.box, len(smp.o.mesh.faces), smp.dof_total, smp.dt, args.flux, ws)
+    cfg["sample"] = sample_txt
+    line = {"metric": METRIC, "value": value, "unit": "DOF-updates/s",
             "impl": "reference", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "flux": args.flux, "sample": sample_txt},
+            "config": cfg,
             "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample_txt},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -442,7 +458,7 @@ def run_ours(args):
 
     if args.only_main:
         # profiling aid: the main measurement (and the Navier-Stokes and curved legs) only
-        line = {"metric": "FP64 RHS DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
+        line = {"metric": METRIC, "value": value, "unit": "DOF-updates/s",
                 "ms_per_step": ms / args.steps, "element_ms_per_step": elem_ms / steps_p,
                 "face_ms_per_step": face_ms / steps_p, "element_tflops": elem_tflops, "only_main": True}
         if args.ns_steps > 0:
@@ -604,13 +620,11 @@ def run_ours(args):
     if rank != 0:
         return
     line = {
-        "metric": "FP64 RHS DOF-updates/s per RK stage (balanced vs naive); adjoint/forward cost",
+        "metric": METRIC,
         "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "elements": box.n_elems, "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), counts)),
-                   "faces": mesh.n_faces, "dof_per_var": dof, "dt": dt, "flux": args.flux, "scheduler": "balanced",
-                   "l2": "working set ~180 MB > 129 MB L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "config": dict(workload_config(box, mesh.n_faces, dof, dt, args.flux, ws), scheduler="balanced"),
         "naive": {"value": naive_value, "ms_per_step": ms_naive / args.steps},
         "static": {"value": static_value, "ms_per_step": ms_static / args.steps, "sm_load_imbalance": imb_static},
         "static_weighted": {"value": weighted_value, "ms_per_step": ms_weighted / args.steps,
