@@ -4,8 +4,8 @@ elements (the oracle evaluates only the sampled elements and what they read):
   * the 24^3 viscous TGV mesh (Navier-Stokes, Re 1600, N = 4);
   * the 64-instance serving batch (N from 2 to 5, sizes 4^3 to 20^3), three
     instances (the smallest, a middle one, the largest) checked;
-  * the 12^3 Kuhn tetrahedral mesh at N = 5 (residual, and the adjoint of 20
-    steps with checkpoints every 5 against central differences).
+  * the 12^3 Kuhn tetrahedral mesh at N = 3 and N = 5 (residual, and the
+    adjoint of 20 steps with checkpoints every 5 against central differences).
 
 Each runs in the launch configuration of bench.py: balanced scheduler with
 the autotuner's tile shapes.  As in the 16^3 Euler check, each variable's
@@ -97,11 +97,11 @@ def test_batch_64_instances_sampled(dg):
         check_sample(o, Qi, Ri, elems, lambda e: o.volume_term(Qi, e))
 
 
-def test_kuhn_12cube_N5_sampled(dg):
+@pytest.mark.parametrize("N", [3, 5])
+def test_kuhn_12cube_sampled(dg, N):
     from oracle.dg import Oracle
     from oracle.mesh import from_box
     box = di.box_mesh(12, "kuhn", seed=3)
-    N = 5
     mesh = dg.Mesh(box, N)
     vals = point_values(mesh.quad_points(), box.n_elems, N, lambda x: di.perturbed_tgv_state(x, seed=3))
     Qs = mesh.project(torch.from_numpy(vals).cuda())
@@ -113,16 +113,16 @@ def test_kuhn_12cube_N5_sampled(dg):
     check_sample(o, Q, R, elems, lambda e: o.volume_term(Q, e))
 
 
-def test_kuhn_12cube_N5_adjoint_central_differences(dg):
+@pytest.mark.parametrize("N", [3, 5])
+def test_kuhn_12cube_adjoint_central_differences(dg, N):
     """<Q_K(Q0 + h v) - Q_K(Q0 - h v), w>/(2h) against <v, dg_rk_vjp(w)>
-    through K = 20 steps, checkpoints every 5, at N = 5."""
+    through K = 20 steps, checkpoints every 5, at N = 3 and N = 5."""
     box = di.box_mesh(12, "kuhn", seed=3)
-    N = 5
     mesh = dg.Mesh(box, N)
     vals = point_values(mesh.quad_points(), box.n_elems, N, lambda x: di.perturbed_tgv_state(x, seed=3))
     Q0 = mesh.project(torch.from_numpy(vals).cuda())
     Qh = mesh.get_state(Q0)
-    nM = 56
+    nM = (N + 1) * (N + 2) * (N + 3) // 6
     scale = np.abs(Qh.reshape(-1, 5, nM)).max(axis=(0, 2))
     v = (di.random_vector(Qh.size, seed=41).reshape(-1, 5, nM) * scale[None, :, None]).reshape(-1)
     w = di.random_vector(Qh.size, seed=42)
