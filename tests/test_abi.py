@@ -73,7 +73,7 @@ def test_hilbert_order_is_local(dg):
     assert np.mean(d < 1.01 * h) > 0.99
 
 
-@pytest.mark.parametrize("bad", ["nonaffine", "unmatched", "type", "degree", "degree0", "empty", "vertex"])
+@pytest.mark.parametrize("bad", ["nonaffine", "unmatched", "type", "degree", "degree0", "empty", "vertex", "onecube"])
 def test_bad_mesh_rejected(dg, bad):
     box = di.box_mesh(3, "hex", seed=1)
     N = 2
@@ -100,6 +100,11 @@ def test_bad_mesh_rejected(dg, bad):
     elif bad == "empty":
         box = di.BoxMesh(box.xyz, box.etype[:0], box.elem_vert_off[:1], box.elem_verts[:0], box.period, 3, "hex", 1)
         status = -1
+    elif bad == "onecube":
+        # one cube per period: every face would be its own periodic image,
+        # the owner rule has no neighbour to pick
+        box = di.box_mesh(1, "hex", seed=1)
+        status = -2
     else:
         ev = box.elem_verts.copy()
         ev[3] = len(box.xyz) + 5                     # vertex index out of range
