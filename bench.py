@@ -637,6 +637,10 @@ def run_ours(args):
         "weighted_over_static": weighted_value / static_value,
         "roe": {"balanced": roe_value, "naive": roe_naive_value, "balanced_over_naive": roe_value / roe_naive_value},
         "pid_ns_per_dof_stage": 1e9 / (value / ws),
+        # the same rate in the other usual units: all five variables, and
+        # volume quadrature points (n^3 per element, the nodal DGSEM count)
+        "dof_updates_all_variables": 5 * value,
+        "quad_point_updates": value * box.n_elems * (N_DEG + 1) ** 3 / dof,
         "roofline": {"bound": "alu", "kernel": "element kernel (balanced, fused backward+LSERK+forward)",
                      "achieved": elem_tflops, "peak": peak_derived, "unit": "TFLOP/s",
                      "frac": elem_tflops / peak_derived,
