@@ -967,6 +967,7 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
     return x.l0 < y.l0;
   });
   const int64_t F = (int64_t)ftmp.size();
+  if (F >= ((int64_t)1 << 31)) { *err = "too many faces for 32-bit face-block indices"; return -7; }
   M.n_faces = F;
   M.faces.resize(F);
   M.slot_ftoff.assign((size_t)E * 6, -1);
