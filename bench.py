@@ -67,20 +67,35 @@ def element_flops(t, N):
     modal->nodal and nodal->modal sum-factorised passes, collocation volume
     derivative (3 n^4 per variable), face traces and lifts (n^3 per face and
     variable each), contravariant flux per volume point, diagonal mass
-    projection and the LSERK update."""
+    projection and the LSERK update.  A hexahedron is stored in scaled nodal
+    values, so its two transforms are pointwise scales (one multiply per
+    point and variable each) instead of sum-factorised passes."""
     n = N + 1
     nM = n_modes(t, N)
-    T = n * (n + 1) // 2
-    ncols = n * n if t in (0, 2) else T
-    bsum = n * n * (n * n if t in (0, 2) else T)          # sum_p blen(p) n^2
-    fwd = n * nM + bsum + n ** 4                            # c, b, a passes
-    bwd = n ** 4 + ncols * n * n + nM * n                   # a^T, b^T, c^T
+    fwd, bwd = transform_macs(t, N)
     nf = (6, 5, 5, 4)[t]
     macs_per_var = fwd + bwd + 3 * n ** 4 + 2 * nf * n ** 3
     metric = (9, 15, 21, 27)[t]
-    pointwise = n ** 3 * (61 + metric)
+    pointwise = n ** 3 * (61 + metric) + (2 * 5 * n ** 3 if t == 0 else 0)
     epilogue = 5 * nM * (2 + 5)
     return 2 * 5 * macs_per_var + pointwise + epilogue
+
+
+def transform_macs(t, N):
+    """MACs per variable of the storage -> nodal and nodal -> storage
+    transforms: the c, b, a passes and their transposes for prism, pyramid
+    and tetrahedron (modal storage); none for the hexahedron, whose storage
+    W^{1/2} V Q turns both into pointwise scales."""
+    if t == 0:
+        return 0, 0
+    n = N + 1
+    nM = n_modes(t, N)
+    T = n * (n + 1) // 2
+    ncols = n * n if t == 2 else T
+    bsum = n * n * (n * n if t == 2 else T)               # sum_p blen(p) n^2
+    fwd = n * nM + bsum + n ** 4                            # c, b, a passes
+    bwd = n ** 4 + ncols * n * n + nM * n                   # a^T, b^T, c^T
+    return fwd, bwd
 
 
 FACE_POINT_FLOPS = {"lf": 101, "roe": 214}
@@ -119,15 +134,11 @@ def ns_element_flops(t, N):
     gradient traces; then the total flux and the volume residual)."""
     n = N + 1
     nM = n_modes(t, N)
-    T = n * (n + 1) // 2
-    ncols = n * n if t in (0, 2) else T
-    bsum = n * n * (n * n if t in (0, 2) else T)
-    fwd = n * nM + bsum + n ** 4
-    bwd = n ** 4 + ncols * n * n + nM * n
+    fwd, bwd = transform_macs(t, N)
     nf = (6, 5, 5, 4)[t]
     metric = (9, 15, 21, 27)[t]
     nQ = n ** 3
-    fused = 2 * 5 * (fwd + bwd + 2 * nf * n ** 3) + 5 * nM * 7
+    fused = 2 * 5 * (fwd + bwd + 2 * nf * n ** 3) + 5 * nM * 7 + (2 * 5 * nQ if t == 0 else 0)
     # per direction: lifting volume term, face lift, projection V M^-1 V^T
     # (pointwise 1/w for the hexahedron, whose V is square) and gradient traces
     proj = 5 * nQ if t == 0 else 2 * 5 * (bwd + fwd)
@@ -150,7 +161,7 @@ FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 2
 # (backward + LSERK + forward) of this workload, from the ncu capture
 # summarised in profiles/element_kernel_16cube_N4.md; set to None whenever
 # the element kernel changes until it is captured again.
-NCU_TRAFFIC_FUSED_LAUNCH = (154.148864 + 146.578432) * 1e6
+NCU_TRAFFIC_FUSED_LAUNCH = None
 
 
 def element_bytes(t, N):

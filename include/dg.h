@@ -25,12 +25,20 @@
  * Conventions shared by all calls
  *   - Pointers named *_store are DEVICE pointers to FP64 arrays of n_dof
  *     doubles in the library's storage layout (per element in Hilbert order,
- *     5 blocks of nM modal coefficients: [slot][var][mode]).  They are owned
- *     by the caller, must be 8-byte aligned, and must stay valid until the
- *     work queued on the stream has finished.
- *   - The external (caller) layout is the same [element][var][mode] blocks in
- *     the caller's element order.  dg_set_state / dg_get_state are the only
- *     permutations between the two.
+ *     5 blocks of nM values: [slot][var][mode]).  Prisms, pyramids and
+ *     tetrahedra hold their modal coefficients there; a hexahedron holds
+ *     the scaled nodal values s = W^{1/2} V Q at its n^3 volume points
+ *     (point order, nM = n^3), an orthogonal change of basis (V^T W V = I for
+ *     the hexahedron), so the hexahedra are time-stepped in nodal values as
+ *     in the nodal DGSEM, and inner products, adjoints and cotangents are
+ *     the same in both bases.  They are owned by the caller, must be 8-byte
+ *     aligned, and must stay valid until the work queued on the stream has
+ *     finished.
+ *   - The external (caller) layout is [element][var][mode] blocks of modal
+ *     coefficients for every type, in the caller's element order.
+ *     dg_set_state / dg_get_state are the only conversions between the two
+ *     (a permutation, and for hexahedra the change of basis); they apply to
+ *     states and cotangents alike.
  *   - Modes are ordered lexicographically in (p, q, r), r fastest, over the
  *     type's index set (hex p,q,r<=N; prism p+q<=N, r<=N; pyramid p,q<=N,
  *     r<=N-max(p,q); tet p+q+r<=N).  Variables are (rho, rho u, rho v, rho w, E).
@@ -204,8 +212,10 @@ dg_status dg_partition_plan(const dg_mesh_desc* desc, int nparts, const double* 
  * pyramid and tet elements. */
 dg_status dg_mesh_layout(const dg_mesh* mesh, int64_t* n_dof, int64_t* slot_of_elem, int64_t* counts);
 
-/* Copy a state between the caller layout Q_ext and the storage layout.
- * is_device = 1: Q_ext is a device pointer and the call is asynchronous;
+/* Convert a state (or a cotangent) between the caller layout Q_ext and the
+ * storage layout: element blocks permuted, hexahedra's modal coefficients Q
+ * mapped to W^{1/2} V Q and back by V^T W^{1/2}.  Q_ext and Q_store must not
+ * overlap.  is_device = 1: Q_ext is a device pointer and the call is asynchronous;
  * is_device = 0: Q_ext is host memory (pinned or pageable) and the call
  * synchronises `stream` before returning. */
 dg_status dg_set_state(dg_mesh* mesh, const double* Q_ext, int is_device, double* Q_store, cudaStream_t stream);

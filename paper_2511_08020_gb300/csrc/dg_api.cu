@@ -381,6 +381,17 @@ struct dg_mesh {
     return upload(&d_chunks_weighted, ws);
   }
 
+  // Hexahedra are stored as scaled nodal values W^{1/2} V Q (an orthogonal
+  // change of basis; the other types hold their modal coefficients): after
+  // the permutation of every element block, kGather / kScatter rewrite the
+  // hexahedra's blocks with the converted values.
+  void convert_hex(int mode, const double* src, double* dst, cudaStream_t st) const {
+    if (h.type_slots[dgk::HEX].empty()) return;
+    dgk::StageArgs a{src, dst, nullptr, 0.0, 0.0, 0.0};
+    dgk::Sched s{d_type_slots[dgk::HEX], (int64_t)h.type_slots[dgk::HEX].size(), nullptr, nullptr, nullptr};
+    dgk::launch_element(ctx(), mode, a, s, false, 0, wpb, st);
+  }
+
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
     dgk::Ctx c = ctx();
     timed(true, st, [&] {
@@ -809,6 +820,7 @@ dg_status dg_set_state(dg_mesh* mesh, const double* Q_ext, int is_device, double
     src = mesh->d_stage;
   }
   dgk::launch_permute(mesh->ctx(), src, Q_store, mesh->h.n_elems, 1, stream);
+  mesh->convert_hex(dgk::kGather, src, Q_store, stream);
   DG_CUDA(cudaGetLastError());
   if (!is_device) DG_CUDA(cudaStreamSynchronize(stream));
   return DG_OK;
@@ -818,6 +830,7 @@ dg_status dg_get_state(const dg_mesh* mesh, const double* Q_store, double* Q_ext
   if (!mesh || !Q_ext || !Q_store) return fail(DG_ERR_ARG, "null argument");
   double* dst = is_device ? Q_ext : mesh->d_stage;
   dgk::launch_permute(mesh->ctx(), Q_store, dst, mesh->h.n_elems, 0, stream);
+  mesh->convert_hex(dgk::kScatter, Q_store, dst, stream);
   DG_CUDA(cudaGetLastError());
   if (!is_device) {
     DG_CUDA(cudaMemcpyAsync(Q_ext, mesh->d_stage, sizeof(double) * mesh->h.n_dof, cudaMemcpyDeviceToHost, stream));

@@ -43,6 +43,7 @@ struct TypeTab {
   int W;        // [nQ]                   w_q (Gauss-Legendre weights times the Duffy Jacobian)
   int wA;       // [nQ][3][3]             w_q d(a,b,c)_l / d(xi,eta,zeta)_k
   int minv;     // [nM]                   1 / (V^T W V)_ii   (the mass matrix is diagonal)
+  int sqw;      // hexahedron: [nQ] sqrt(w_q), then [nQ] 1 / sqrt(w_q) (scaled nodal storage); -1 otherwise
   int fw;       // [nfaces][n*n]          reference face weights at the face points
   // int pool
   int col_moff, col_len, col_coff, col_p;   // [ncols]

@@ -389,7 +389,25 @@ int Tables::add(int type, int N, std::string* err) {
         else maxoff = std::max(maxoff, std::fabs(s));
       }
     if (maxoff > 1e-12 * maxd) { *err = "mass matrix is not diagonal for this (type, N)"; return -7; }
-    for (int a = 0; a < t.nM; ++a) dput(1.0 / diag[a]);
+    // hexahedron: the n-point rule integrates every product of two modes
+    // exactly, so V^T W V is the identity (its computed diagonal differs
+    // from 1 by rounding only)
+    for (int a = 0; a < t.nM; ++a) dput(type == dgk::HEX ? 1.0 : 1.0 / diag[a]);
+  }
+  // Hexahedron: V is square and V^T W V = I, so W^{1/2} V is orthogonal and
+  // the state is stored as the scaled nodal values s = W^{1/2} V Q.  Then
+  // V Q = W^{-1/2} s and, for the projected residual, W^{1/2} V M^{-1} V^T h =
+  // W^{-1/2} h: both transforms become pointwise scales (the hexahedron is
+  // time-stepped in nodal values, as in the nodal DGSEM of Sec. 2, while the
+  // other types stay modal -- the extra Vandermonde work of Sec. 2 falls on
+  // them alone), and an orthogonal change of basis leaves inner products (so
+  // every adjoint and cotangent) unchanged.  dg_set_state / dg_get_state
+  // convert between the caller's modal coefficients and this storage.
+  t.sqw = -1;
+  if (type == dgk::HEX) {
+    t.sqw = (int)dpool.size();
+    for (int q = 0; q < t.nQ; ++q) dput(std::sqrt(wq[q]));
+    for (int q = 0; q < t.nQ; ++q) dput(1.0 / std::sqrt(wq[q]));
   }
   // face descriptors + numerical check that the face rule points lie on the grid
   t.fw = (int)dpool.size();

@@ -443,9 +443,10 @@ __device__ __forceinline__ void contravariant_vjp(const double* U, const double 
     acc[4] = fma(_c, _s[4 * (stride)], acc[4]);  \
   } while (0)
 
-// Modal -> nodal: sQ [5][nM] -> U in bufA [5][nQ]; bufB is scratch.
-__device__ __noinline__ void modal_to_nodal(const Ctx& c, const TypeTab& T, const double* sQ, double* bufA,
-                                               double* bufB, int lane) {
+// Modal -> nodal by the sum-factorised passes: sQ [5][nM] (modal
+// coefficients) -> U in bufA [5][nQ]; bufB is scratch.
+__device__ __forceinline__ void modal_to_nodal_passes(const Ctx& c, const TypeTab& T, const double* sQ, double* bufA,
+                                                         double* bufB, int lane) {
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int* ip = c.ipool;
@@ -491,6 +492,21 @@ __device__ __noinline__ void modal_to_nodal(const Ctx& c, const TypeTab& T, cons
   __syncthreads();
 }
 
+// Storage -> nodal: U = V Q in bufA [5][nQ] from a stored element block sQ.
+// A hexahedron is stored as s = W^{1/2} V Q, so U = W^{-1/2} s pointwise;
+// the other types hold modal coefficients.  sQ may alias bufB.
+__device__ __noinline__ void modal_to_nodal(const Ctx& c, const TypeTab& T, const double* sQ, double* bufA,
+                                            double* bufB, int lane) {
+  if (T.type == HEX) {
+    const int nQ = T.nQ;
+    const double* rs = c.dpool + T.sqw + nQ;
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = sQ[w] * rs[w % nQ];
+    __syncthreads();
+    return;
+  }
+  modal_to_nodal_passes(c, T, sQ, bufA, bufB, lane);
+}
+
 // What the nodal->modal pass does with r = M_ref^{-1} V^T bufA of a mode
 // (r = V^T bufA without the mass matrix when minv == false):
 //   kStore: out[v nM + m] = scale r_v
@@ -513,6 +529,9 @@ struct Epilogue {
   // rbuf [5][nM] is shared scratch that no other argument aliases
   const double* Md = nullptr;
   double* rbuf = nullptr;
+  // true: r is the modal result for a hexahedron too (the conversion to the
+  // caller's layout); false: a hexahedron's r is in its scaled nodal storage
+  bool modal = false;
 };
 
 // The epilogue of one mode given r_v (5 values).  Returns true if a
@@ -549,6 +568,20 @@ __device__ __noinline__ bool nodal_to_modal_t(const Ctx& c, const TypeTab& T, do
   const int n = T.n, nM = T.nM, nQ = T.nQ, n2 = n * n;
   const double* dp = c.dpool;
   const int* ip = c.ipool;
+  if (!DENSE && T.type == HEX && !ep.modal) {
+    // scaled nodal storage: W^{1/2} V M^{-1} V^T h = W^{-1/2} h (M = I)
+    const double* rs = dp + T.sqw + nQ;
+    bool bad = false;
+    for (int q = lane; q < nQ; q += blockDim.x) {
+      double acc[5];
+      const double f = rs[q] * ep.scale;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] = bufA[v * nQ + q] * f;
+      bad |= epilogue_mode(ep, nM, q, acc);
+    }
+    __syncthreads();
+    return bad;
+  }
   for (int o = lane; o < nQ; o += blockDim.x) {
     int p = o / n2, jk = o - p * n2;
     const double* A = dp + T.A + p * n;
@@ -1084,6 +1117,30 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
   const int64_t qoff = c.slot_qoff[s];
   if (MODE == kNsVolume) {
     element_ns_volume<ANY>(c, T, s, bufA, lane);
+    return;
+  }
+  if (MODE == kGather) {
+    // hexahedra only: caller modal coefficients Q -> storage s = W^{1/2} V Q
+    const double* Q = io.Qin + c.elem_qoff[c.elem_of_slot[s]];
+    for (int w = lane; w < 5 * nM; w += blockDim.x) bufG[w] = Q[w];
+    __syncthreads();
+    modal_to_nodal_passes(c, T, bufG, bufA, bufG, lane);
+    const double* sq = c.dpool + T.sqw;
+    double* out = io.Qout + qoff;
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) out[w] = bufA[w] * sq[w % nQ];
+    __syncthreads();
+    return;
+  }
+  if (MODE == kScatter) {
+    // hexahedra only: storage s -> caller modal coefficients V^T W^{1/2} s
+    const double* S = io.Qin + qoff;
+    const double* sq = c.dpool + T.sqw;
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = S[w] * sq[w % nQ];
+    __syncthreads();
+    Epilogue ep{Epilogue::kStore, false, 1.0, io.Qout + c.elem_qoff[c.elem_of_slot[s]], nullptr, nullptr, nullptr,
+                nullptr, 0.0, 0.0, 0.0};
+    ep.modal = true;
+    nodal_to_modal_t<false>(c, T, bufA, bufG, lane, ep);
     return;
   }
   if (MODE == kFwd) {
@@ -2370,6 +2427,8 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm, bo
   if ((e = set_mode<kProject>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kEval>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kLoad>(bmax)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_naive_kernel<kGather, false>, bmax)) != cudaSuccess) return e;
+  if ((e = set_smem(elem_naive_kernel<kScatter, false>, bmax)) != cudaSuccess) return e;
   int fbytes = 32 * 5 * kMaxn * kMaxn * (int)sizeof(double);
   if ((e = set_smem(face_kernel<false>, fbytes)) != cudaSuccess) return e;
   if ((e = set_smem(face_kernel<true>, fbytes)) != cudaSuccess) return e;
@@ -2403,6 +2462,12 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
     case kProject: launch_mode<kProject>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kEval: launch_mode<kEval>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kLoad: launch_mode<kLoad>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kGather:   // one block per listed hexahedron
+      if (s.count > 0) elem_naive_kernel<kGather, false><<<(unsigned)s.count, 32 * wpb, bytes, st>>>(c, a, s.list, s.count);
+      break;
+    case kScatter:
+      if (s.count > 0) elem_naive_kernel<kScatter, false><<<(unsigned)s.count, 32 * wpb, bytes, st>>>(c, a, s.list, s.count);
+      break;
   }
 }
 

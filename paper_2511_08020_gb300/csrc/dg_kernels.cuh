@@ -32,8 +32,8 @@ enum ElemMode : int {
   kBwdRk = 2,      // backward + LSERK update
   kBwdRkFwd = 3,   // backward + LSERK update + forward of the new state
   kProject = 4,    // Algorithm 1 projection of point values
-  kGather = 5,     // copy caller layout -> storage layout
-  kScatter = 6,    // copy storage layout -> caller layout
+  kGather = 5,     // hexahedra: caller modal coefficients -> scaled nodal storage
+  kScatter = 6,    // hexahedra: scaled nodal storage -> caller modal coefficients
   kNsVolume = 7,   // Navier-Stokes: BR1 lifting, gradient traces, volume residual H
   kEval = 8,       // modal -> nodal values at the volume points (caller element order)
   kLoad = 9        // load vector V^T W J q of point values (Algorithm 1's projection without M^{-1})

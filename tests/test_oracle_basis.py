@@ -36,6 +36,27 @@ def test_orthonormal_exact_rule(etype, N):
     assert np.abs(M - np.eye(M.shape[0])).max() < 1e-13
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_hex_scaled_nodal_basis_is_orthogonal(N):
+    """On the hexahedron the n-point rule (n = N + 1) integrates every product
+    of two modes exactly and V is square, so O = W^{1/2} V is an orthogonal
+    matrix: storing W^{1/2} V Q instead of Q is an exact change of basis
+    whose inverse is its transpose (what lets the hexahedra be stored in
+    nodal values with cotangents transforming like states).  A prism has
+    fewer modes than points, so no such square transform exists there."""
+    pts, w = volume_rule(HEX, N)
+    V = eval_basis(HEX, N, pts)
+    assert V.shape == (len(w), len(w))
+    O = np.sqrt(w)[:, None] * V
+    eye = np.eye(len(w))
+    assert np.abs(O.T @ O - eye).max() < 1e-13
+    assert np.abs(O @ O.T - eye).max() < 1e-13
+    # V M^{-1} V^T = W^{-1}: the projected residual is a pointwise scale
+    assert np.abs(V @ V.T - np.diag(1.0 / w)).max() < 1e-12 * (1.0 / w).max()
+    pts_p, w_p = volume_rule(PRISM, N)
+    assert eval_basis(PRISM, N, pts_p).shape[1] < len(w_p)
+
+
 def space_monomials(etype, N):
     for a, b, c in itertools.product(range(N + 1), repeat=3):
         if etype == HEX or (etype == PRISM and a + b <= N) or (etype in (TET, PYR) and a + b + c <= N):
