@@ -161,7 +161,7 @@ FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 2
 # (backward + LSERK + forward) of this workload, from the ncu capture
 # summarised in profiles/element_kernel_16cube_N4.md; set to None whenever
 # the element kernel changes until it is captured again.
-NCU_TRAFFIC_FUSED_LAUNCH = None
+NCU_TRAFFIC_FUSED_LAUNCH = (186.212096 + 145.397760) * 1e6
 
 
 def element_bytes(t, N):
