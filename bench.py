@@ -98,7 +98,29 @@ def transform_macs(t, N):
     return fwd, bwd
 
 
-FACE_POINT_FLOPS = {"lf": 101, "roe": 214}
+with open(os.path.join(ROOT, "alg_counts.json")) as _f:
+    ALG = json.load(_f)["per_point_flops"]
+# w S times the Riemann flux per face point, as the face kernel evaluates it
+# (derived by counting in tests/test_alg_counts.py)
+FACE_POINT_FLOPS = {"lf": ALG["kernel_lf_per_face_point"], "roe": ALG["kernel_roe_per_face_point"]}
+
+
+def survey_element_flops(t, N, flux):
+    """The per-element, per-stage flop model written before the kernels
+    existed: modal <-> quadrature transforms counted as five C_V passes per
+    variable (the forward transform, the projection and three volume-integral
+    derivative passes), trace and lift (nM + 2 n^3) MACs per face side each,
+    f_F per volume point, the Riemann flux f_R per face point once per face
+    (half per element side), and 20 nM for the LSERK update, with f_F and f_R
+    counted from the oracle's formulas (alg_counts.json)."""
+    n = N + 1
+    nM = n_modes(t, N)
+    T = n * (n + 1) // 2
+    cv = (3 * n ** 4, n ** 4 + 2 * n * n * T, 2 * n ** 4 + n * nM, n ** 4 + n * n * T + n * nM)[t]
+    nf = (6, 5, 5, 4)[t]
+    fR = ALG["oracle_lf_per_face_point" if flux == "lf" else "oracle_roe_per_face_point"]
+    return (2 * 5 * (5 * cv + nf * 2 * (nM + 2 * n ** 3)) + n ** 3 * ALG["f_F_per_point"]
+            + n * n * nf / 2 * fR + 20 * nM)
 
 
 def curved_element_flops(t, N):
@@ -158,10 +180,27 @@ def ns_element_flops(t, N):
 FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 214 + 2 * (13 + 66 + 30) + 10}
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused element launch
-# (backward + LSERK + forward) of this workload, from the ncu capture
-# summarised in profiles/element_kernel_16cube_N4.md; set to None whenever
+# (backward + LSERK + forward) of this workload, from the committed ncu
+# capture of the element kernel on the 16^3 N = 4 mesh; set to None whenever
 # the element kernel changes until it is captured again.
 NCU_TRAFFIC_FUSED_LAUNCH = (186.212096 + 145.397760) * 1e6
+
+
+def fp64_probes():
+    """Measured FP64 rates of this device from the benchmark's probe library
+    (libfp64probe.so, built beside libdg.so): DFMA loop, mma.sync f64 loop,
+    and both at once, TFLOP/s."""
+    import ctypes
+
+    from paper_2511_08020_gb300.build import PROBE_LIB, build_probe
+    if not os.path.exists(PROBE_LIB):
+        build_probe()
+    lib = ctypes.CDLL(PROBE_LIB)
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    for rc in (lib.fp64_probe_peak(ctypes.byref(a), ctypes.byref(b)), lib.fp64_probe_mixed(ctypes.byref(c))):
+        if rc != 0:
+            raise RuntimeError(f"FP64 probe failed with CUDA error {rc}")
+    return a.value, b.value, c.value
 
 
 def element_bytes(t, N):
@@ -176,12 +215,18 @@ def element_bytes(t, N):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms for the whole
+    run; every timed region marks its host-time window (after the
+    synchronisation that opens it, before the one that closes it is left),
+    and the summary keeps the samples that fall inside the windows."""
     FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index=0):
         self.index = index
         self.rows = []
+        self.windows = []
         self.proc = None
         self.thread = None
 
@@ -198,31 +243,89 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.monotonic(), [x.strip() for x in line.split(",")]))
 
-    def stop(self):
+    def mark(self, name, t0, t1):
+        self.windows.append((name, t0, t1))
+
+    def summary(self, names=None):
+        """Median SM clock, maximum clock, throttle reasons seen and sample
+        counts over the windows (all, or those whose name is in `names`)."""
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        if self.thread:
-            self.thread.join(timeout=2)
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        wins = [(a, b) for n, a, b in self.windows if names is None or n in names]
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for t, r in list(self.rows):
+            if not any(a <= t <= b for a, b in wins):
+                continue
             try:
                 sm.append(float(r[0]))
                 mx.append(float(r[1]))
             except (ValueError, IndexError):
                 continue
-            for name, val in zip(names, r[4:8]):
+            for name, val in zip(self.REASONS, r[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "timed_seconds": round(sum(b - a for a, b in wins), 3)}
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+
+# the run's sampler (started by run_ours; the legs mark their timed windows)
+CLOCKS = ClockSampler()
+
+
+class timed_window:
+    """Marks a timed region's host-time window in CLOCKS."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        self.t0 = time.monotonic()
+        return self
+
+    def __exit__(self, *exc):
+        CLOCKS.mark(self.name, self.t0, time.monotonic())
+        return False
+
+
+def interleaved_repeats(configs, timed_fn, reps):
+    """Scheduler comparison with a spread: `reps` rounds, in each of which
+    every configuration (name, set-up callable) is set up and timed once by
+    timed_fn() -> ms per step; the order rotates every round.  Returns per
+    name the repeats' ms per step with their median and quartiles."""
+    times = {name: [] for name, _ in configs}
+    for r in range(reps):
+        k = r % len(configs)
+        for name, setup in configs[k:] + configs[:k]:
+            setup()
+            times[name].append(timed_fn())
+    out = {}
+    for name, v in times.items():
+        q1, med, q3 = np.percentile(v, [25, 50, 75])
+        out[name] = {"median_ms_per_step": float(med), "q1_ms_per_step": float(q1), "q3_ms_per_step": float(q3),
+                     "repeats": len(v), "ms_per_step": [round(x, 4) for x in v]}
+    return out
+
+
+def compare_to(stats, a, b):
+    """Median ratio time(b)/time(a) (> 1: a is faster) and whether the two
+    interquartile ranges are disjoint."""
+    sa, sb = stats[a], stats[b]
+    return {"speedup_median": sb["median_ms_per_step"] / sa["median_ms_per_step"],
+            "iqr_disjoint": bool(sa["q3_ms_per_step"] < sb["q1_ms_per_step"]
+                                 or sb["q3_ms_per_step"] < sa["q1_ms_per_step"])}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -289,82 +392,163 @@ def dist_info():
 
 
 # ----------------------------------------------------------------------------- reference arm
-class OracleSample:
-    """The CPU oracle on a fixed seeded sample of elements of the workload
-    (the TGV projected on the sample and its face neighbours): one 'step' is 5
-    residual evaluations of the sample (one LSERK step's worth)."""
+def _oracle_worker(conn, flux, elems):
+    """A spawned process that owns a fixed part of the element list (so its
+    oracle's face tables stay warm): receives states, returns the residual
+    blocks of its elements, until it receives None."""
+    from oracle.dg import Oracle
+    from oracle.mesh import from_box
+    o = Oracle(from_box(build_workload(), N_DEG), flux=flux)
+    off = o.mesh.dof_off
+    conn.send("ready")
+    while True:
+        Q = conn.recv()
+        if Q is None:
+            break
+        R = o.rhs(Q, elems=elems)
+        conn.send(np.concatenate([R[off[e]:off[e + 1]] for e in elems]))
+    conn.close()
 
-    def __init__(self, flux, size):
-        from oracle.dg import Oracle
+
+class OracleRun:
+    """The CPU oracle on the benchmark workload, timed in full LSERK steps:
+    the residual of `elems` (every element, or a seeded sample whose
+    neighbours stay frozen) is evaluated by `cores` spawned worker processes,
+    each with its own oracle and one BLAS thread and always the same equal
+    part of the element list; the stage updates run in this process.  Initial
+    state: the TGV projected with the oracle (Algorithm 1)."""
+
+    def __init__(self, flux, cores, n_sample=None):
+        import multiprocessing as mp
+
+        from oracle.dg import LSERK_A, LSERK_B, Oracle
         from oracle.mesh import from_box
+        self.A, self.B = LSERK_A, LSERK_B
         box = build_workload()
         self.box = box
-        self.n_elems = box.n_elems
         self.o = o = Oracle(from_box(box, N_DEG), flux=flux)
+        E = box.n_elems
         self.dof_total = int(o.mesh.nM.sum())
-        xyz = np.concatenate([o.quad_points(e) for e in range(box.n_elems)])
-        self.dt = tgv_dt(box, xyz, N_DEG)
-        rng = np.random.default_rng(0)
-        self.sample = np.sort(rng.choice(box.n_elems, size=size, replace=False))
+        if n_sample is None or n_sample >= E:
+            self.elems = np.arange(E)
+            touched = self.elems
+        else:
+            self.elems = np.sort(np.random.default_rng(0).choice(E, size=n_sample, replace=False))
+            t = set(self.elems.tolist())
+            for e in self.elems:
+                for f, _ in o.mesh.elem_faces[e]:
+                    t.update((o.mesh.faces[f][0], o.mesh.faces[f][2]))
+            touched = sorted(t)
         self.Q = np.zeros(o.mesh.n_dof())
-        touched = set(self.sample.tolist())
-        for e in self.sample:
-            for f, _ in o.mesh.elem_faces[e]:
-                e0, _, e1, _ = o.mesh.faces[f]
-                touched.update((e0, e1))
+        xyz = []
         for e in touched:
             op = o.ops[o.mesh.etype[e]]
-            q = di.tgv_state(o.quad_points(e))
-            r = o.mesh.J[e] * (q * op.w) @ op.V
+            x = o.quad_points(e)
+            xyz.append(x)
+            r = o.mesh.J[e] * (di.tgv_state(x) * op.w) @ op.V
             self.Q[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, r).ravel()
-        self.dof = int(sum(o.mesh.nM[e] for e in self.sample))
+        self.dt = tgv_dt(box, np.concatenate(xyz), N_DEG)
+        self.dof = int(sum(o.mesh.nM[e] for e in self.elems))
+        self.parts = [p for p in np.array_split(self.elems, cores) if len(p)]
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for part in self.parts:
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, flux, part), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def rhs(self, Q):
+        R = np.zeros_like(Q)
+        off = self.o.mesh.dof_off
+        for c in self.conns:
+            c.send(Q)
+        for c, part in zip(self.conns, self.parts):
+            blocks = c.recv()
+            k = 0
+            for e in part:
+                n = off[e + 1] - off[e]
+                R[off[e]:off[e + 1]] = blocks[k:k + n]
+                k += n
+        return R
 
     def step(self):
-        for _ in range(5):
-            self.o.rhs(self.Q, elems=self.sample)
+        K = np.zeros_like(self.Q)
+        for s in range(5):
+            K = self.A[s] * K + self.dt * self.rhs(self.Q)
+            self.Q = self.Q + self.B[s] * K
 
     def describe(self):
-        return f"{len(self.sample)} of {self.n_elems} elements (seeded), 5 residual evaluations per step, 1 thread"
+        what = "all" if len(self.elems) == self.box.n_elems else f"a seeded sample of {len(self.elems)} of the"
+        return (f"{what} {self.box.n_elems} elements, full LSERK steps (5 residual evaluations and stage "
+                f"updates), {len(self.parts)} worker process(es), one BLAS thread each")
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for pr in self.procs:
+            pr.join(timeout=30)
 
 
 def run_reference(args):
-    """The CPU oracle timed on this host on a bounded sample of the workload."""
+    """The CPU oracle timed on this host's cores: full LSERK steps of the
+    workload on every core (a seeded sample of 1024 elements per core when
+    the host has too few cores for whole steps within a few minutes)."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    smp = OracleSample(args.flux, args.ref_sample)
+    cores = os.cpu_count() or 1
+    run = OracleRun(args.flux, cores, n_sample=1024 * cores)
+    run.rhs(run.Q)                      # warm-up: builds the workers' face tables
     for _ in range(args.warmup):
-        smp.step()
+        run.step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        smp.step()
+        run.step()
     dt = time.perf_counter() - t0
-    value = smp.dof * 5 * args.steps / dt
-    sample_txt = smp.describe()
-    cfg = workload_config(smp.box, len(smp.o.mesh.faces), smp.dof_total, smp.dt, args.flux, ws)
+    run.close()
+    value = run.dof * 5 * args.steps / dt
+    sample_txt = run.describe()
+    cfg = workload_config(run.box, len(run.o.mesh.faces), run.dof_total, run.dt, args.flux, ws)
     cfg["sample"] = sample_txt
     line = {"metric": METRIC, "value": value, "unit": "DOF-updates/s",
             "impl": "reference", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": cfg,
-            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample_txt},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": len(run.parts), "kind": "oracle",
+                             "sample": sample_txt},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(flux, seconds=12.0, size=48):
-    """Oracle throughput on the same bounded sample as the reference arm
-    (one warm-up step, then steps for about `seconds` of CPU work)."""
-    smp = OracleSample(flux, size)
-    smp.step()
-    steps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        smp.step()
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": smp.dof * 5 * steps / dt, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{smp.describe()}, {steps} steps in {dt:.1f} s"}
+def cpu_baseline(flux, one_core_sample=256, min_seconds=10.0):
+    """The oracle timed on this host, after one warm-up residual evaluation
+    (which builds the oracle's face tables): full LSERK steps of the whole
+    benchmark mesh on every core (os.cpu_count() worker processes), and on
+    one core full LSERK steps of a seeded sample of elements (a whole-mesh
+    step on one core needs minutes of face-table set-up alone); in each case
+    steps until min_seconds have passed (at least one)."""
+    out = {"unit": "DOF-updates/s", "kind": "oracle", "nproc": os.cpu_count()}
+    for label, cores, sample in (("all_cores", os.cpu_count() or 1, None), ("one_core", 1, one_core_sample)):
+        run = OracleRun(flux, cores, n_sample=sample)
+        run.rhs(run.Q)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            run.step()
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds:
+                break
+        out[label] = {"value": run.dof * 5 * steps / el, "cores": len(run.parts), "steps": steps,
+                      "seconds": round(el, 2), "sample": run.describe()}
+        run.close()
+    for k in ("value", "cores", "sample"):
+        out[k] = out["all_cores"][k]
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -381,6 +565,15 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     barrier, max_over_ranks = dist_helpers(ws, dev)
+    CLOCKS.index = local
+    CLOCKS.start()
+    try:
+        run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, max_over_ranks)
+    finally:
+        CLOCKS.stop()
+
+
+def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, max_over_ranks):
     if args.curved_only:
         # profiling aid: the curved-geometry leg alone (its affine ratio is omitted)
         cv = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, None)
@@ -404,7 +597,7 @@ def run_ours(args):
     counts = mesh.type_counts
 
 
-    def timed_steps(m, Q, K, steps, warmup, profile=False):
+    def timed_steps(m, Q, K, steps, warmup, profile=False, window="main legs"):
         m.set_profiling(profile)
         for _ in range(warmup):
             m.rk_step(Q, K, dt, 1)
@@ -415,17 +608,18 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         elem_ms = face_ms = 0.0
         nel = nfa = 0
-        e0.record(stream)
-        for _ in range(steps):
-            m.rk_step(Q, K, dt, 1)
-            if profile:
-                a, b, c, d = m.phase_times()
-                elem_ms += a
-                face_ms += b
-                nel += c
-                nfa += d
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with timed_window(window):
+            e0.record(stream)
+            for _ in range(steps):
+                m.rk_step(Q, K, dt, 1)
+                if profile:
+                    a, b, c, d = m.phase_times()
+                    elem_ms += a
+                    face_ms += b
+                    nel += c
+                    nfa += d
+            e1.record(stream)
+            torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1))
@@ -446,10 +640,8 @@ def run_ours(args):
     # main measurement: balanced scheduler, LF
     Q = Q0.clone()
     K = torch.empty_like(Q)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms, _ = timed_steps(mesh, Q, K, args.steps, args.warmup)
-    clk = clocks.stop()
+    ms, _ = timed_steps(mesh, Q, K, args.steps, args.warmup, window="main")
+    clk = CLOCKS.summary(["main"])
     mesh.sync()
     value = replica_value(ws, dof, args.steps, ms)
 
@@ -466,6 +658,8 @@ def run_ours(args):
     elem_tflops = el_flops_stage * 5 * steps_p / (elem_ms * 1e-3) / 1e12
     face_tflops = face_flops_stage * 5 * steps_p / (face_ms * 1e-3) / 1e12
     total_tflops = (el_flops_stage + face_flops_stage) * 5 * args.steps / (ms * 1e-3) / 1e12 / ws
+    survey_flops_stage = sum(survey_element_flops(int(t), N_DEG, args.flux) for t in box.etype)
+    survey_tflops = survey_flops_stage * 5 * args.steps / (ms * 1e-3) / 1e12 / ws
 
     if args.only_main:
         # profiling aid: the main measurement (and the Navier-Stokes and curved legs) only
@@ -480,8 +674,7 @@ def run_ours(args):
             print(json.dumps(line), flush=True)
         return
 
-    dfma, dmma = dg.probe_fp64_peak()
-    fp64_mixed = dg.probe_fp64_mixed()
+    dfma, dmma, fp64_mixed = fp64_probes()
     # ALU roofline: FP64 peak from unit counts and clocks -- every SM retires
     # 2 DFMA per clock (the sm__inst_executed_pipe_fp64 peak ncu reports for
     # this part), 2 flops each, at the maximum SM clock seen during the run
@@ -489,25 +682,34 @@ def run_ours(args):
     sm_max_ghz = (clk.get("sm_max_mhz") or 2070.0) / 1e3
     peak_derived = props.multi_processor_count * 2 * 2 * sm_max_ghz / 1e3
 
-    # naive scheduler and Roe flux, same workload and state
-    mesh.set_scheduler("naive")
-    mesh.set_element_warps(tuned["naive"][0])
+    # scheduler comparison on the same workload and state: one timed run per
+    # scheduler (its final state for the bitwise comparison), then
+    # interleaved repeats for the spread
+    def use(sched):
+        def setup():
+            mesh.set_scheduler(sched)
+            if sched == "balanced" and not args.warps:
+                for t, N, w in shapes_main:      # the autotuned per-table tile shapes of the main leg
+                    mesh.set_table_warps(t, N, w)
+            else:
+                mesh.set_element_warps(tuned["static" if sched == "weighted" else sched][0])
+        return setup
+
+    use("naive")()
     Qn = Q0.clone()
     ms_naive, _ = timed_steps(mesh, Qn, K, args.steps, args.warmup)
-    mesh.set_scheduler("static")
-    mesh.set_element_warps(tuned["static"][0])
+    use("static")()
     Qst = Q0.clone()
     ms_static, _ = timed_steps(mesh, Qst, K, args.steps, args.warmup)
     # the paper's balanced partition: equal-weight Hilbert segments with the
     # per-type weights the in-kernel timers measured (dg_rebalance reads them)
     _, imb_static = mesh.cost_table()
     mesh.rebalance(force=True)
-    mesh.set_scheduler("weighted")
+    use("weighted")()
     Qwt = Q0.clone()
     ms_weighted, _ = timed_steps(mesh, Qwt, K, args.steps, args.warmup)
     _, imb_weighted = mesh.cost_table()
-    mesh.set_scheduler("balanced")
-    mesh.set_element_warps(tuned["balanced"][0])
+    use("balanced")()
     mesh.set_stage_fusion(False)
     Qsp = Q0.clone()
     ms_split, _ = timed_steps(mesh, Qsp, K, args.steps, args.warmup)
@@ -518,6 +720,21 @@ def run_ours(args):
     weighted_value = ws * dof * 5 * args.steps / (ms_weighted * 1e-3)
     same_bits = (bool(torch.equal(Qn, Q)) and bool(torch.equal(Qst, Q)) and bool(torch.equal(Qsp, Q))
                  and bool(torch.equal(Qwt, Q)))
+    rep_steps = max(5, args.steps // 4)
+    Qr, Kr = Q0.clone(), torch.empty_like(Q0)
+
+    def timed_rep():
+        Qr.copy_(Q0)
+        ms_r, _ = timed_steps(mesh, Qr, Kr, rep_steps, 1, window="scheduler repeats")
+        return ms_r / rep_steps
+
+    sched_stats = interleaved_repeats([(sd, use(sd)) for sd in ("naive", "static", "weighted", "balanced")],
+                                      timed_rep, args.sched_repeats)
+    use("balanced")()
+    sched_cmp = {"steps_per_repeat": rep_steps, "stats": sched_stats,
+                 "balanced_vs_naive": compare_to(sched_stats, "balanced", "naive"),
+                 "balanced_vs_static": compare_to(sched_stats, "balanced", "static"),
+                 "weighted_vs_static": compare_to(sched_stats, "weighted", "static")}
 
     roe_mesh, Q0r, _ = make("roe", "naive")
     roe_mesh.autotune(Q0r, dt)
@@ -643,6 +860,7 @@ def run_ours(args):
                             "what": "equal-weight Hilbert segments, measured per-type weights (the paper's partition)"},
         "balanced_unfused_stages": {"value": split_value, "ms_per_step": ms_split / args.steps},
         "schedulers_bitwise_equal": same_bits,
+        "scheduler_repeats": sched_cmp,
         "balanced_over_naive": value / naive_value,
         "balanced_over_static": value / static_value,
         "weighted_over_static": weighted_value / static_value,
@@ -659,10 +877,19 @@ def run_ours(args):
                                   f"{sm_max_ghz:.3f} GHz (max SM clock of the run)",
                      "dfma_loop_measured": dfma, "frac_of_dfma_loop": elem_tflops / dfma,
                      "traffic": NCU_TRAFFIC_FUSED_LAUNCH,
-                     "traffic_source": "dram read+write of one fused element launch, profiles/element_kernel_16cube_N4.md",
+                     "traffic_source": "ncu dram read+write of one fused element launch (16^3 mixed, N = 4)",
                      "algorithmic_bytes_per_stage": el_bytes_stage, "algorithmic_flops_per_stage": el_flops_stage,
                      "element_ms_per_step": elem_ms / steps_p, "face_ms_per_step": face_ms / steps_p,
                      "face_kernel_tflops": face_tflops, "whole_step_tflops": total_tflops,
+                     "flop_models": {
+                         "schedule": {"flops_per_stage": el_flops_stage + face_flops_stage,
+                                      "whole_step_tflops": total_tflops, "frac": total_tflops / peak_derived,
+                                      "what": "the sum-factorised schedule the kernels run (element + face kernel)"},
+                         "survey": {"flops_per_stage": survey_flops_stage, "whole_step_tflops": survey_tflops,
+                                    "frac": survey_tflops / peak_derived,
+                                    "what": "five C_V passes per variable, trace/lift per face side, f_F and f_R "
+                                            "from the oracle's formulas (alg_counts.json); above 1 where the "
+                                            "schedule removes work the model counts (hexahedral transforms)"}},
                      "dmma_peak_measured": dmma, "dfma_plus_dmma_concurrent_measured": fp64_mixed},
         "cost_table_ns_per_elem": dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns_type])),
         "sm_load_imbalance": imb,
@@ -689,7 +916,7 @@ def run_ours(args):
     if cvl is not None:
         line["curved"] = cvl
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_one_core_sample)
     print(json.dumps(line), flush=True)
 
 
@@ -718,9 +945,9 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
     dof = int(sum(n_modes(int(t), N) for t in box.etype))
     steps = args.ns_steps
 
-    def timed(Q, K, profile=False):
+    def timed(Q, K, profile=False, nsteps=steps, warmup=args.warmup):
         mesh.set_profiling(profile)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             mesh.rk_step(Q, K, dt, 1)
         torch.cuda.synchronize()
         barrier()
@@ -831,11 +1058,20 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
         g[:, 1:4] = mom / rho[:, None]
         seed = mesh.load_vector(g.reshape(-1))
         del U, g
+        # the adjoint of the whole trajectory may keep stage data in most of
+        # the free memory (fewer segments recomputed); freed after the leg
+        mesh.set_adjoint_memory(args.ke_adjoint_memory)
+        grad = torch.empty_like(seed)
+        mesh.rk_vjp(Q0, dt, steps, 5, seed, grad)     # allocates the stage store (untimed)
+        torch.cuda.synchronize()
         e0.record(stream)
-        grad = mesh.rk_vjp(Q0, dt, steps, 5, seed)
+        mesh.rk_vjp(Q0, dt, steps, 5, seed, grad)
         e1.record(stream)
         torch.cuda.synchronize()
         adj_full = e0.elapsed_time(e1)
+        mesh.set_adjoint_storage(False)
+        mesh.set_adjoint_storage(True)
+        mesh.set_adjoint_memory(0.5)
         # the autograd split: the forward keeps Q at every segment start, the
         # backward recomputes the segments from them
         Qc = Q0.clone()
@@ -851,6 +1087,7 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
         adjc_full = e0.elapsed_time(e1)
         del ck
         out["ke_adjoint"] = {"steps": steps, "ckpt_every": 5, "forward_ms": fwd_full, "rk_vjp_ms": adj_full,
+                             "stage_store_share_of_free_memory": args.ke_adjoint_memory,
                              "adjoint_over_forward": adj_full / fwd_full,
                              "forward_checkpointed_ms": fwdc_full, "rk_vjp_checkpointed_ms": adjc_full,
                              "backward_given_forward_checkpoints_over_forward": adjc_full / fwdc_full,
@@ -888,29 +1125,30 @@ def curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, affine_value)
            "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), mesh.type_counts)), "dof_per_var": dof,
            "steps": steps, "dt": dt, "unit": "DOF-updates/s"}
 
-    def timed(Q, K, profile=False):
+    def timed(Q, K, profile=False, nsteps=steps, warmup=args.warmup):
         mesh.set_profiling(profile)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             mesh.rk_step(Q, K, dt, 1)
         torch.cuda.synchronize()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         el = fa = 0.0
-        e0.record(stream)
-        for _ in range(steps):
-            mesh.rk_step(Q, K, dt, 1)
-            if profile:
-                a, b_, _, _ = mesh.phase_times()
-                el += a
-                fa += b_
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with timed_window("curved"):
+            e0.record(stream)
+            for _ in range(nsteps):
+                mesh.rk_step(Q, K, dt, 1)
+                if profile:
+                    a, b_, _, _ = mesh.phase_times()
+                    el += a
+                    fa += b_
+            e1.record(stream)
+            torch.cuda.synchronize()
         barrier()
         mesh.set_profiling(False)
         return max_over_ranks(e0.elapsed_time(e1)), el, fa
 
-    res = {}
+    res, wsched = {}, {}
     for sched in ("naive", "static", "weighted", "balanced"):
         if sched == "weighted":
             mesh.rebalance(force=True)          # per-type weights measured by the in-kernel timers
@@ -920,10 +1158,36 @@ def curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, affine_value)
             warps = args.warps
         else:
             warps, _ = mesh.autotune(Q0, dt)
+        wsched[sched] = warps
         Q = Q0.clone()
         ms, _, _ = timed(Q, torch.empty_like(Q))
         res[sched] = Q
         out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps}
+
+    shapes_cv = mesh.tile_shapes()      # balanced was tuned last: its per-table shapes
+
+    def use(sched):
+        def setup():
+            mesh.set_scheduler(sched)
+            if sched == "balanced" and not args.warps:
+                for t, N, w in shapes_cv:
+                    mesh.set_table_warps(t, N, w)
+            else:
+                mesh.set_element_warps(wsched[sched])
+        return setup
+    rep_steps = max(5, steps // 4)
+    Qr, Kr = Q0.clone(), torch.empty_like(Q0)
+
+    def timed_rep():
+        Qr.copy_(Q0)
+        return timed(Qr, Kr, nsteps=rep_steps, warmup=1)[0] / rep_steps
+    stats = interleaved_repeats([(sd, use(sd)) for sd in ("naive", "static", "weighted", "balanced")], timed_rep,
+                                args.sched_repeats)
+    use("balanced")()
+    out["scheduler_repeats"] = {"steps_per_repeat": rep_steps, "stats": stats,
+                                "balanced_vs_naive": compare_to(stats, "balanced", "naive"),
+                                "balanced_vs_static": compare_to(stats, "balanced", "static"),
+                                "weighted_vs_static": compare_to(stats, "weighted", "static")}
     Qp = Q0.clone()
     _, el_ms, fa_ms = timed(Qp, torch.empty_like(Qp), profile=True)
     el_flops = sum(curved_element_flops(int(t), N_DEG) for t in box.etype)
@@ -1025,25 +1289,29 @@ def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
     el_flops_stage = sum(sum(element_flops(int(t), N) for t in box.etype) for box, N in zip(boxes, Ns))
     steps = args.batch_steps
 
-    def timed(Q, K, profile=False):
+    def timed(Q, K, profile=False, nsteps=steps, warmup=args.warmup):
         b.set_profiling(profile)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             b.rk_step(Q, K, dt, 1)
         torch.cuda.synchronize()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         el = 0.0
-        e0.record(stream)
-        for _ in range(steps):
-            b.rk_step(Q, K, dt, 1)
-            if profile:
-                el += b.phase_times()[0]
-        e1.record(stream)
-        torch.cuda.synchronize()
+        nl = 0
+        with timed_window("batch"):
+            e0.record(stream)
+            for _ in range(nsteps):
+                b.rk_step(Q, K, dt, 1)
+                if profile:
+                    pt = b.phase_times()
+                    el += pt[0]
+                    nl = pt[2]
+            e1.record(stream)
+            torch.cuda.synchronize()
         barrier()
         b.set_profiling(False)
-        return max_over_ranks(e0.elapsed_time(e1)), el
+        return max_over_ranks(e0.elapsed_time(e1)), el, nl
 
     out = {"workload": BATCH_WORKLOAD, "instances": len(work), "elements": b.n_elems, "faces": b.n_faces,
            "dof_per_var": dof, "degrees": {str(k): Ns.count(k) for k in sorted(set(Ns))},
@@ -1054,15 +1322,42 @@ def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
         warps, tms = b.autotune(Q0, dt)
         Q = Q0.clone()
         K = torch.empty_like(Q)
-        ms, _ = timed(Q, K)
+        ms, _, _ = timed(Q, K)
         res[sched] = Q
         out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps,
                       "autotune_ms_per_step": [round(x, 3) for x in tms.tolist()]}
         if sched == "balanced":
             names = ("hex", "prism", "pyramid", "tet")
             out[sched]["tile_shapes"] = {f"{names[t]}/N{N}": w for t, N, w in b.tile_shapes()}
+    shapes = b.tile_shapes()
+
+    def use(sched):
+        def setup():
+            b.set_scheduler(sched)
+            if sched == "naive":
+                b.set_element_warps(out["naive"]["warps"])
+            else:
+                for t, N, w in shapes:
+                    b.set_table_warps(t, N, w)
+        return setup
+    rep_steps = max(2, steps // 2)
+    Qr, Kr = Q0.clone(), torch.empty_like(Q0)
+
+    def timed_rep():
+        Qr.copy_(Q0)
+        return timed(Qr, Kr, nsteps=rep_steps, warmup=1)[0] / rep_steps
+    stats = interleaved_repeats([(sd, use(sd)) for sd in ("naive", "balanced")], timed_rep, args.sched_repeats)
+    use("balanced")()
+    out["scheduler_repeats"] = {"steps_per_repeat": rep_steps, "stats": stats,
+                                "balanced_vs_naive": compare_to(stats, "balanced", "naive")}
     Qp = Q0.clone()
-    _, el_ms = timed(Qp, torch.empty_like(Qp), profile=True)
+    _, el_ms, nl = timed(Qp, torch.empty_like(Qp), profile=True)
+    # every element phase of the balanced scheduler is one launch per launch
+    # group (tables sharing N and tile shape); a step has nl element phases
+    # (the forward prime and one per stage) and 5 face launches
+    out["launch_groups"] = len({(N, w) for _, N, w in shapes})
+    out["element_launches_per_stage"] = out["launch_groups"]
+    out["element_phases_per_step"] = nl
     out["unit"] = "DOF-updates/s"
     out["balanced_over_naive"] = out["balanced"]["value"] / out["naive"]["value"]
     out["schedulers_bitwise_equal"] = bool(torch.equal(res["naive"], res["balanced"]))
@@ -1082,8 +1377,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flux", default="lf", choices=["lf", "roe"])
-    ap.add_argument("--ref-sample", type=int, default=48)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--sched-repeats", type=int, default=10,
+                    help="interleaved repeats per scheduler in the scheduler comparisons")
+    ap.add_argument("--cpu-one-core-sample", type=int, default=256,
+                    help="seeded sample of elements whose full LSERK steps the one-core oracle timing runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10,
                     help="steps of the 64-instance batch leg (0 skips it)")
@@ -1097,6 +1394,8 @@ def main():
                     help="steps of the Navier-Stokes adjoint timing (0 skips it)")
     ap.add_argument("--ns-ke-adjoint", type=int, default=1,
                     help="time the adjoint of the final kinetic energy through all NS steps (0 skips it)")
+    ap.add_argument("--ke-adjoint-memory", type=float, default=0.9,
+                    help="share of the free device memory the kinetic-energy adjoint may keep stage data in")
     ap.add_argument("--curved-steps", type=int, default=100,
                     help="steps of the curved-geometry leg (0 skips it)")
     ap.add_argument("--curved-only", action="store_true",

@@ -50,9 +50,15 @@
  *     thread-local message for the last failure.  Device-side conditions
  *     (non-finite residual) are sticky in the mesh and reported by dg_sync.
  *     No call aborts the process or throws across the ABI.
- *   - A mesh object may be used from one host thread at a time.  Calls on the
- *     same mesh that overlap on the GPU (different streams without ordering)
- *     race on the library's workspace.
+ *   - A mesh object may be used from one host thread at a time.  All calls
+ *     on one mesh share its workspace on the device -- nodal residual, face
+ *     buffer, the balanced scheduler's queue counters (each launch zeroes
+ *     the counter of the next), the cost bins and dg_rk_step's parameter
+ *     block -- so they must be ordered on the GPU: one stream, or streams
+ *     ordered by events.  Calls on the same mesh that overlap on the GPU
+ *     race on that workspace and give wrong results.  Distinct meshes share
+ *     nothing (except dg_rhs_vjp_noalloc's scratch array) and may run
+ *     concurrently.
  */
 #ifndef DG_H_
 #define DG_H_
@@ -79,7 +85,14 @@ typedef enum {
   DG_ERR_UNSUPPORTED = -7  /* option outside what the build supports            */
 } dg_status;
 
-typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1 } dg_flux;
+/* Numerical surface flux (F.n)* of Eq. 1.  DG_FLUX_EC is Chandrashekar's
+ * entropy-conservative two-point flux F#(U-, U+).n with no dissipation (the
+ * interface flux under which the split form of dg_set_volume_form conserves
+ * entropy); the adjoint entry points and Navier-Stokes take LF or Roe. */
+typedef enum { DG_FLUX_LF = 0, DG_FLUX_ROE = 1, DG_FLUX_EC = 2 } dg_flux;
+
+/* Volume term of the hexahedra (dg_set_volume_form). */
+typedef enum { DG_VOLUME_WEAK = 0, DG_VOLUME_SPLIT = 1 } dg_volume_form;
 /* Element scheduling (Sec. 3's load balancing on one GPU; results are
  * bitwise identical for all four):
  *   BALANCED  persistent launches whose blocks pop cost-weighted chunks of the
@@ -251,11 +264,23 @@ dg_status dg_eval_nodal(dg_mesh* mesh, const double* Q_store, double* u_points, 
  * storage layout) is overwritten.  Asynchronous. */
 dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStream_t stream);
 
-/* nsteps LSERK(5,4) steps (Carpenter-Kennedy 2N storage) of size dt, in
- * place on Q_store; K_store is the second register (its input value is
- * ignored, K = 0 at every step start).  The stage loop is replayed from a
- * captured CUDA graph.  Asynchronous. */
+/* nsteps LSERK(5,4) steps (Carpenter-Kennedy 2N storage, Sec. 2) of size
+ * dt, in place on Q_store; K_store is the second register (its input value
+ * is ignored, K = 0 at every step start).  The stage loop is replayed from
+ * CUDA graphs captured on the first call: one that primes a step, one per
+ * step and one for the last step, whose element launches read Q_store,
+ * K_store and dt from a device parameter block that the first graph's head
+ * node writes.  A new state or register pointer, dt or step count only
+ * changes that node's arguments (no capture, no instantiation); a change of
+ * scheduler, stage fusion, launch groups, chunk tables or physics captures
+ * the graphs again.  With profiling on (dg_set_profiling) the call is one
+ * graph with event nodes, captured again whenever an argument changes.
+ * Asynchronous. */
 dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps, cudaStream_t stream);
+
+/* Host [1]: how many times dg_rk_step has captured (and instantiated) its
+ * graphs on this mesh. */
+dg_status dg_graph_captures(const dg_mesh* mesh, int64_t* captures);
 
 /* Qbar = (dR/dQ)^T Rbar at Q_store (all device, storage layout); Qbar is
  * overwritten.  No counterpart in the paper.  Asynchronous. */
@@ -274,9 +299,11 @@ dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, d
  *   - The mesh's face buffer must fit: meshes needing more than 8 Mi doubles
  *     of face scratch (2 * 5 * (N+1)^2 per face) get DG_ERR_ARG with a
  *     message; use dg_rhs_vjp for those.
- *   - The mesh's device must be the current device.  The first call on a
- *     device looks up the array's device address (cudaGetSymbolAddress) and
- *     caches it; make that first call before any stream capture.
+ *   - The mesh's device must be the current device.  Every call looks up
+ *     the array's device address with cudaGetSymbolAddress (which allocates
+ *     nothing); the first call on a device can make the runtime load the
+ *     library's device code there, so make that first call before any
+ *     stream capture.
  *   - All calls on a device share the one array and it keeps the last
  *     call's contents (nothing in it has to start at zero: every slot is
  *     written before it is read).  Calls that overlap on the GPU (different
@@ -286,8 +313,8 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
 
 /* Q0bar = (dQ_K/dQ_0)^T QKbar for nsteps LSERK steps of size dt from Q0_store.
  * A forward pass from Q0 keeps the stage data of as many final segments of
- * ckpt_every steps as fit in half of the free device memory (see
- * dg_set_adjoint_storage) and stores Q at the start of every earlier
+ * ckpt_every steps as fit in the mesh's share of the free device memory
+ * (half by default; see dg_set_adjoint_storage, dg_set_adjoint_memory) and stores Q at the start of every earlier
  * segment; the reverse sweep uses the kept data directly and recomputes the
  * earlier segments from their checkpoints.  ckpt_every = 0 picks the longest
  * segment whose stage data fit in that memory.  The result does not depend on
@@ -320,6 +347,31 @@ dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double
  * dg_rk_vjp silently recomputes.  keep_stages = 0: always recompute (and free
  * the store).  Results are bitwise identical either way. */
 dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages);
+
+/* Share of the device memory that is free at the call (the mesh's own stage
+ * store counted as free) that dg_rk_vjp may fill with kept stage data:
+ * 0 < fraction <= 0.95, default 0.5.  A larger share lets the forward pass
+ * keep more final steps, so fewer segments are run twice (the self-contained
+ * adjoint of a long trajectory); the store stays allocated until
+ * dg_set_adjoint_storage(mesh, 0) or dg_mesh_destroy.  Results are bitwise
+ * identical for every share. */
+dg_status dg_set_adjoint_memory(dg_mesh* mesh, double fraction);
+
+/* Volume term of the hexahedra.  DG_VOLUME_WEAK (default): the weak form of
+ * Eq. 1.  DG_VOLUME_SPLIT: the entropy-stable split form that Sec. 2 uses for
+ * stabilisation -- Chandrashekar's two-point flux F# in flux-differencing
+ * form on the hexahedron's Gauss-Legendre nodes, with the hybridised
+ * summation-by-parts operator of Gauss collocation along every coordinate
+ * line (antisymmetric part of W D between nodes, coupling of every node to
+ * the line's two face states), and entropy-projected traces u(E v(u)) (the
+ * entropy variables extrapolated to the face points) on which the surface
+ * flux is taken.  Prisms, pyramids and tetrahedra keep the weak form.  With
+ * DG_FLUX_EC the semi-discrete entropy of an all-hexahedral periodic mesh is
+ * conserved; with DG_FLUX_LF it decays.  Euler equations and affine meshes
+ * only (DG_ERR_UNSUPPORTED otherwise, and from the adjoint entry points while
+ * it is set).  Synchronous set-up (launch configuration); captured graphs are
+ * rebuilt on the next dg_rk_step. */
+dg_status dg_set_volume_form(dg_mesh* mesh, int form);
 
 /* Governing equations of dg_rhs / dg_rk_step (a new mesh solves the Euler
  * equations).  DG_NAVIER_STOKES: the Navier-Stokes-Fourier equations that
@@ -428,15 +480,6 @@ dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream);
 
 /* Thread-local description of the last error. */
 const char* dg_last_error(void);
-
-/* Measured FP64 throughput of this device (DFMA chains and mma.sync f64
- * m8n8k4), TFLOP/s, from a ~50 ms probe launch.  Synchronises. */
-dg_status dg_probe_fp64_peak(double* dfma_tflops, double* dmma_tflops);
-
-/* Combined FP64 throughput (TFLOP/s) when half of every block's warps run
- * DFMA chains and the other half mma.sync f64 at the same time: equal to the
- * single-path rates if the two share one FP64 throughput limit.  Synchronises. */
-dg_status dg_probe_fp64_mixed(double* total_tflops);
 
 #ifdef __cplusplus
 }

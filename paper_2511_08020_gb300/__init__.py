@@ -13,10 +13,11 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "partition_plan", "probe_fp64_peak", "probe_fp64_mixed", "FLUX", "SCHED",
+__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "partition_plan", "FLUX", "SCHED",
            "PHYSICS", "GEOMETRY", "load"]
 
-FLUX = {"lf": 0, "roe": 1}
+FLUX = {"lf": 0, "roe": 1, "ec": 2}
+VOLUME = {"weak": 0, "split": 1}
 SCHED = {"balanced": 0, "naive": 1, "static": 2, "weighted": 3}
 PHYSICS = {"euler": 0, "navier_stokes": 1}
 GEOMETRY = {"affine": 0, "vertex": 1}
@@ -65,6 +66,8 @@ _SIGS = {
     "dg_rk_vjp_checkpointed": [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "dg_set_scheduler": [_P, ctypes.c_int],
     "dg_set_physics": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
+    "dg_set_volume_form": [_P, ctypes.c_int],
+    "dg_set_adjoint_memory": [_P, ctypes.c_double],
     "dg_set_table_warps": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "dg_tile_shapes": [_P, ctypes.c_int, _P, _P, _P, _P],
     "dg_set_adjoint_storage": [_P, ctypes.c_int],
@@ -72,9 +75,8 @@ _SIGS = {
     "dg_rebalance": [_P, ctypes.c_int, _P, _P],
     "dg_set_rebalance_interval": [_P, ctypes.c_int],
     "dg_rebalance_stats": [_P, _P, _P],
+    "dg_graph_captures": [_P, _P],
     "dg_sync": [_P, _P],
-    "dg_probe_fp64_peak": [_P, _P],
-    "dg_probe_fp64_mixed": [_P],
     "dg_set_profiling": [_P, ctypes.c_int],
     "dg_set_stage_fusion": [_P, ctypes.c_int],
     "dg_set_element_warps": [_P, ctypes.c_int],
@@ -171,19 +173,6 @@ def partition_plan(box, N, nparts, type_weight=None, geometry="affine"):
     halo = np.zeros(max(1, int(off[-1])), dtype=np.int64)
     _check(load().dg_partition_plan(ctypes.byref(d), int(nparts), twp, _ptr(part), _ptr(off), _ptr(halo)))
     return part, off, halo[:int(off[-1])]
-
-
-def probe_fp64_peak():
-    a, b = ctypes.c_double(), ctypes.c_double()
-    _check(load().dg_probe_fp64_peak(ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
-
-
-def probe_fp64_mixed():
-    """Combined DFMA + mma.sync f64 throughput with both running at once (TFLOP/s)."""
-    a = ctypes.c_double()
-    _check(load().dg_probe_fp64_mixed(ctypes.byref(a)))
-    return a.value
 
 
 class Mesh:
@@ -320,6 +309,14 @@ class Mesh:
         _check(load().dg_set_adjoint_storage(self.handle, int(bool(keep_stages))))
 
     # ---------------------------------------------------------------- physics
+    def set_adjoint_memory(self, fraction=0.5):
+        """Share of the free device memory dg_rk_vjp may keep stage data in."""
+        _check(load().dg_set_adjoint_memory(self.handle, float(fraction)))
+
+    def set_volume_form(self, form="weak"):
+        """'weak' (Eq. 1) or 'split' (the entropy-stable split form on the hexahedra)."""
+        _check(load().dg_set_volume_form(self.handle, VOLUME[form] if isinstance(form, str) else int(form)))
+
     def set_physics(self, physics="euler", mu=0.0, Pr=0.72):
         """'euler' or 'navier_stokes' (BR1 lifting, constant mu, Prandtl number Pr)."""
         _check(load().dg_set_physics(self.handle, PHYSICS[physics] if isinstance(physics, str) else int(physics),
@@ -367,6 +364,12 @@ class Mesh:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load().dg_rebalance_stats(self.handle, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def graph_captures(self):
+        """How many times dg_rk_step captured its graphs on this mesh."""
+        n = ctypes.c_int64()
+        _check(load().dg_graph_captures(self.handle, ctypes.byref(n)))
+        return n.value
 
     def set_element_warps(self, warps):
         _check(load().dg_set_element_warps(self.handle, int(warps)))

@@ -1,7 +1,10 @@
 """Build libdg.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 The three translation units compile in parallel and link into
-paper_2511_08020_gb300/_lib/libdg.so.  Nothing is installed elsewhere.
+paper_2511_08020_gb300/_lib/libdg.so.  The FP64 throughput probes of the
+benchmark (fp64_probe.cu) link into a library of their own,
+_lib/libfp64probe.so, so that libdg.so carries only the hot path.  Nothing is
+installed elsewhere.
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdg.so")
 SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_api.cu"]
+PROBE_SRC = "fp64_probe.cu"
+PROBE_LIB = os.path.join(LIBDIR, "libfp64probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -35,6 +40,21 @@ def _compile(src: str, obj: str) -> None:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compiling {src} failed:\n{r.stdout}\n{r.stderr}")
+
+
+def build_probe(force: bool = False) -> str:
+    """The benchmark's FP64 throughput probes (libfp64probe.so)."""
+    os.makedirs(LIBDIR, exist_ok=True)
+    src = os.path.join(CSRC, PROBE_SRC)
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(src) <= os.path.getmtime(PROBE_LIB):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", "-cudart", "shared", "-o", tmp, src]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"building libfp64probe.so failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -61,3 +81,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)
+    build_probe(force="--force" in sys.argv)

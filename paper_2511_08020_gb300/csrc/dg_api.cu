@@ -8,7 +8,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -57,6 +56,7 @@ struct dg_mesh {
   int device = 0;
   dgh::HostMesh h;
   int flux = 0;
+  int split = 0;      // DG_VOLUME_SPLIT: entropy-stable split form on the hexahedra
   double gamma = 1.4;
   int scheduler = DG_SCHED_BALANCED;
   double threshold = 0.1;
@@ -68,6 +68,7 @@ struct dg_mesh {
   double *d_DW = nullptr, *d_Vtb = nullptr;   // Navier-Stokes adjoint workspace
   bool store_dw = false;                      // the volume phase keeps the nodal gradient (adjoint)
   bool keep_stages = true;                    // dg_rk_vjp keeps stage data (dg_set_adjoint_storage)
+  double adj_mem_frac = 0.5;                  // share of the free device memory dg_rk_vjp may keep stage data in
   // Stage data kept by the forward pass of dg_rk_vjp for one segment (5 per
   // step): the nodal state and the own-side traces, plus for Navier-Stokes
   // the gradient traces and the nodal gradient.  The reverse stages then skip
@@ -153,13 +154,111 @@ struct dg_mesh {
     return w;
   }
   double* d_stage = nullptr;
-  // graph cache for dg_rk_step
+  // graph cache for dg_rk_step.  Without profiling: three graphs captured
+  // once and replayed for any state, register, dt and step count -- prime
+  // (parameter node, forward of stage 1), step (five stages ending in the
+  // next step's forward) and last (five stages) -- whose element launches
+  // read (Q, K, dt) from d_rkdyn; only the parameter node's arguments change
+  // between calls.  With profiling: one graph of the whole call (its event
+  // nodes time the phases), captured again when an argument changes.
   cudaStream_t cap = nullptr;
+  dgk::RkDyn* d_rkdyn = nullptr;
+  struct Captured {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+  };
+  Captured gr_prime, gr_step, gr_last;
+  cudaGraphNode_t gr_param_node = nullptr;
+  int64_t graph_captures = 0;
   cudaGraphExec_t gexec = nullptr;
   const double* g_Q = nullptr;
   const double* g_K = nullptr;
   double g_dt = 0.0;
-  int g_nsteps = -1, g_sched = -1, g_prof = -1, g_fused = -1;
+  int g_nsteps = -1, g_sched = -1, g_fused = -1;
+  int r_sched = -1, r_fused = -1;   // configuration of the three replayed graphs
+
+  void drop_graphs() {
+    for (Captured* c : {&gr_prime, &gr_step, &gr_last}) {
+      if (c->x) cudaGraphExecDestroy(c->x);
+      if (c->g) cudaGraphDestroy(c->g);
+      c->x = nullptr;
+      c->g = nullptr;
+    }
+    gr_param_node = nullptr;
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
+
+  template <class F>
+  cudaError_t capture(Captured& c, F&& body) {
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    body(cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&c.x, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return e;
+    }
+    c.g = g;   // kept: the parameter node handle refers to it
+    return cudaSuccess;
+  }
+
+  // The three replayed graphs of dg_rk_step (profiling off).
+  cudaError_t capture_stage_graphs() {
+    drop_graphs();
+    dgk::StageArgs a{nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, d_rkdyn};
+    auto stages = [&](cudaStream_t st, bool last_step) {
+      cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
+      parity = 0;
+      for (int s = 0; s < 5; ++s) {
+        face_phase(st);
+        const bool last = last_step && s == 4;
+        a.a = kLsA[s];
+        a.b = kLsB[s];
+        if (fused) {
+          element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, st);
+        } else {
+          element_phase(dgk::kBwdRk, a, st);
+          if (!last) element_phase(dgk::kFwd, a, st);
+        }
+      }
+    };
+    cudaError_t e = capture(gr_prime, [&](cudaStream_t st) {
+      dgk::launch_rk_params(d_rkdyn, nullptr, nullptr, 0.0, st);
+      cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
+      parity = 0;
+      element_phase(dgk::kFwd, a, st);
+    });
+    if (e == cudaSuccess) e = capture(gr_step, [&](cudaStream_t st) { stages(st, false); });
+    if (e == cudaSuccess) e = capture(gr_last, [&](cudaStream_t st) { stages(st, true); });
+    if (e != cudaSuccess) {
+      drop_graphs();
+      return e;
+    }
+    size_t n = 0;
+    e = cudaGraphGetNodes(gr_prime.g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(gr_prime.g, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n && !gr_param_node; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp{};
+      if (cudaGraphKernelNodeGetParams(nodes[i], &kp) == cudaSuccess && dgk::is_rk_params_kernel(kp.func))
+        gr_param_node = nodes[i];
+    }
+    if (e == cudaSuccess && !gr_param_node) e = cudaErrorGraphExecUpdateFailure;
+    if (e != cudaSuccess) {
+      drop_graphs();
+      return e;
+    }
+    r_sched = scheduler;
+    r_fused = (int)fused;
+    ++graph_captures;
+    return cudaSuccess;
+  }
   int parity = 0;
   // phase timing events: pool 0 for captured graphs, pool 1 for direct calls
   bool profiling = false;
@@ -237,6 +336,7 @@ struct dg_mesh {
     c.sm_ns = d_smns;
     c.gamma = gamma;
     c.flux = flux;
+    c.split = split;
     c.nQmax = nQmax;
     return c;
   }
@@ -285,7 +385,7 @@ struct dg_mesh {
       it->tabs.push_back((int)t);
     }
     for (auto& G : groups) {
-      cudaError_t e = dgk::element_kernel_attributes(G.n * G.n * G.n, G.wpb, &G.bpsm, h.n_curved > 0);
+      cudaError_t e = dgk::element_kernel_attributes(G.n * G.n * G.n, G.wpb, &G.bpsm, h.n_curved > 0, split != 0);
       if (e != cudaSuccess) return e;
       if (G.bpsm < 1) G.bpsm = 1;
       if (ns) {
@@ -295,7 +395,7 @@ struct dg_mesh {
       }
     }
     // restore the mesh-wide attributes used by the static and naive launches
-    cudaError_t e = dgk::element_kernel_attributes(nQmax, wpb, &blocks_per_sm, h.n_curved > 0);
+    cudaError_t e = dgk::element_kernel_attributes(nQmax, wpb, &blocks_per_sm, h.n_curved > 0, split != 0);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     std::vector<double> w(weight, weight + dgk::kMaxTabs);
@@ -587,7 +687,8 @@ struct dg_mesh {
     free_groups();
     for (auto& pl : ev_pool)
       for (auto e : pl) cudaEventDestroy(e);
-    if (gexec) cudaGraphExecDestroy(gexec);
+    drop_graphs();
+    if (d_rkdyn) cudaFree(d_rkdyn);
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -601,7 +702,8 @@ const char* dg_last_error(void) { return g_err.c_str(); }
 namespace {
 
 dg_status check_desc(const dg_mesh_desc* desc) {
-  if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE) return fail(DG_ERR_ARG, "unknown flux");
+  if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE && desc->flux != DG_FLUX_EC)
+    return fail(DG_ERR_ARG, "unknown flux");
   if (desc->scheduler < DG_SCHED_BALANCED || desc->scheduler > DG_SCHED_WEIGHTED) return fail(DG_ERR_ARG, "unknown scheduler");
   if (!(desc->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must exceed 1");
   return DG_OK;
@@ -887,31 +989,55 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
   if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return DG_OK;
   if (!(std::isfinite(dt))) return fail(DG_ERR_ARG, "dt must be finite");
-  if (!mesh->gexec || mesh->g_Q != Q_store || mesh->g_K != K_store || mesh->g_dt != dt || mesh->g_nsteps != nsteps ||
-      mesh->g_sched != mesh->scheduler || mesh->g_prof != (int)mesh->profiling || mesh->g_fused != (int)mesh->fused) {
-    if (mesh->gexec) {
-      cudaGraphExecDestroy(mesh->gexec);
-      mesh->gexec = nullptr;
+  if (!mesh->profiling) {
+    // replay the three captured graphs; a new state, register, dt or step
+    // count only changes the arguments of the parameter node
+    if (!mesh->gr_prime.x || mesh->r_sched != mesh->scheduler || mesh->r_fused != (int)mesh->fused) {
+      if (!mesh->d_rkdyn && cudaMalloc(&mesh->d_rkdyn, sizeof(dgk::RkDyn)) != cudaSuccess)
+        return fail(DG_ERR_OOM, "step parameter block");
+      mesh->begin_timing(0);
+      cudaError_t e = mesh->capture_stage_graphs();
+      if (e != cudaSuccess) return cuda_fail(e, "stage graph capture");
     }
-    cudaGraph_t g;
-    mesh->begin_timing(0);
-    DG_CUDA(cudaStreamBeginCapture(mesh->cap, cudaStreamCaptureModeThreadLocal));
-    mesh->enqueue_rk(Q_store, K_store, dt, nsteps, mesh->cap);
-    cudaError_t e = cudaStreamEndCapture(mesh->cap, &g);
-    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    e = cudaGraphInstantiate(&mesh->gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-    mesh->g_Q = Q_store;
-    mesh->g_K = K_store;
-    mesh->g_dt = dt;
-    mesh->g_nsteps = nsteps;
-    mesh->g_sched = mesh->scheduler;
-    mesh->g_prof = (int)mesh->profiling;
-    mesh->g_fused = (int)mesh->fused;
+    dgk::RkDyn* d = mesh->d_rkdyn;
+    double* Qp = Q_store;
+    double* Kp = K_store;
+    double dtv = dt;
+    void* args[] = {&d, &Qp, &Kp, &dtv};
+    cudaKernelNodeParams kp{};
+    dgk::rk_params_node(&kp, args);
+    DG_CUDA(cudaGraphExecKernelNodeSetParams(mesh->gr_prime.x, mesh->gr_param_node, &kp));
+    mesh->last_pool = 0;
+    DG_CUDA(cudaGraphLaunch(mesh->gr_prime.x, stream));
+    for (int k = 0; k + 1 < nsteps; ++k) DG_CUDA(cudaGraphLaunch(mesh->gr_step.x, stream));
+    DG_CUDA(cudaGraphLaunch(mesh->gr_last.x, stream));
+  } else {
+    if (!mesh->gexec || mesh->g_Q != Q_store || mesh->g_K != K_store || mesh->g_dt != dt ||
+        mesh->g_nsteps != nsteps || mesh->g_sched != mesh->scheduler || mesh->g_fused != (int)mesh->fused) {
+      if (mesh->gexec) {
+        cudaGraphExecDestroy(mesh->gexec);
+        mesh->gexec = nullptr;
+      }
+      cudaGraph_t g;
+      mesh->begin_timing(0);
+      DG_CUDA(cudaStreamBeginCapture(mesh->cap, cudaStreamCaptureModeThreadLocal));
+      mesh->enqueue_rk(Q_store, K_store, dt, nsteps, mesh->cap);
+      cudaError_t e = cudaStreamEndCapture(mesh->cap, &g);
+      if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+      e = cudaGraphInstantiate(&mesh->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+      mesh->g_Q = Q_store;
+      mesh->g_K = K_store;
+      mesh->g_dt = dt;
+      mesh->g_nsteps = nsteps;
+      mesh->g_sched = mesh->scheduler;
+      mesh->g_fused = (int)mesh->fused;
+      ++mesh->graph_captures;
+    }
+    mesh->last_pool = 0;
+    DG_CUDA(cudaGraphLaunch(mesh->gexec, stream));
   }
-  mesh->last_pool = 0;
-  DG_CUDA(cudaGraphLaunch(mesh->gexec, stream));
   if (mesh->rebalance_every > 0) {
     // the imbalance trigger of Sec. 3 in the time loop: every
     // rebalance_every steps compare the measured SM load imbalance with the
@@ -926,6 +1052,12 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
       mesh->rebalances += rebuilt;
     }
   }
+  return DG_OK;
+}
+
+dg_status dg_graph_captures(const dg_mesh* mesh, int64_t* captures) {
+  if (!mesh || !captures) return fail(DG_ERR_ARG, "null argument");
+  *captures = mesh->graph_captures;
   return DG_OK;
 }
 
@@ -946,6 +1078,8 @@ dg_status dg_rebalance_stats(const dg_mesh* mesh, int64_t* checks, int64_t* reba
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->split || mesh->flux == DG_FLUX_EC)
+    return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
   DG_CUDA(mesh->ensure_adjoint(0));
   dgk::VjpArgs va{Q_store, Rbar, nullptr, Qbar, 0.0, 0.0, 0.0, 0, 0};
   mesh->enqueue_vjp(va, stream);
@@ -966,20 +1100,16 @@ constexpr size_t kNoAllocScratchDoubles = size_t(8) << 20;  // 64 MiB of FP64 pe
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 constexpr int kNoAllocMaxDevices = 64;
-double* g_noalloc_addr[kNoAllocMaxDevices] = {};
-std::mutex g_noalloc_mutex;
 
-// Device address of the scratch array for the current device (resolved once
-// per device; in host code the symbol itself is only a host-side stand-in).
-cudaError_t noalloc_scratch(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_addr[dev];
+// Device address of the scratch array for the current device, looked up on
+// every call (cheap, allocates nothing, and stays right if the device's
+// primary context was reset and the module loaded again); in host code the
+// symbol itself is only a host-side stand-in, never a device address.
+cudaError_t noalloc_scratch(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -990,6 +1120,8 @@ extern "C" {
 dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
                              cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->split || mesh->flux == DG_FLUX_EC)
+    return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
   if (mesh->ns)
     return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp_noalloc covers the Euler equations (the viscous adjoint needs "
                                     "workspace that dg_rhs_vjp allocates); use dg_rhs_vjp");
@@ -1003,7 +1135,7 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
   if (dev != mesh->device) return fail(DG_ERR_ARG, "dg_rhs_vjp_noalloc: the mesh's device is not the current device");
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(DG_ERR_UNSUPPORTED, "device ordinal beyond 63");
   double* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(dev, &scratch);
+  cudaError_t e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
   dgk::Ctx c = mesh->ctx();
   c.Tv = scratch;  // every face side slot is written (seed) before it is read
@@ -1065,14 +1197,17 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
 dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
                       double dt) {
   if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->split || mesh->flux == DG_FLUX_EC)
+    return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
   if (nsteps < 0 || ckpt_every < 0) return fail(DG_ERR_ARG, "nsteps and ckpt_every must be >= 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   return DG_OK;
 }
 
 // ckpt_every == 0: the longest segment whose kept stage data (5 stages per
-// step) fit in half of the device memory that is free now (the mesh's own
-// stage store counting as free: it is reused or replaced), at least 1 step.
+// step) fit in the mesh's share (dg_set_adjoint_memory, half by default) of
+// the device memory that is free now (the mesh's own stage store counting as
+// free: it is reused or replaced), at least 1 step.
 int auto_ckpt(const dg_mesh* mesh, int nsteps) {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -1081,7 +1216,7 @@ int auto_ckpt(const dg_mesh* mesh, int nsteps) {
   }
   const double per_step = 5.0 * sizeof(double) * (double)mesh->stage_doubles();
   const double avail = (double)free_b + sizeof(double) * (double)mesh->sstore_doubles;
-  const double fit = 0.5 * avail / per_step;
+  const double fit = mesh->adj_mem_frac * avail / per_step;
   return (int)std::max(1.0, std::min((double)nsteps, std::floor(fit)));
 }
 }  // namespace
@@ -1177,9 +1312,33 @@ dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages) {
   return DG_OK;
 }
 
+dg_status dg_set_adjoint_memory(dg_mesh* mesh, double fraction) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (!(fraction > 0.0 && fraction <= 0.95)) return fail(DG_ERR_ARG, "the memory fraction must lie in (0, 0.95]");
+  mesh->adj_mem_frac = fraction;
+  return DG_OK;
+}
+
+dg_status dg_set_volume_form(dg_mesh* mesh, int form) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (form != DG_VOLUME_WEAK && form != DG_VOLUME_SPLIT) return fail(DG_ERR_ARG, "unknown volume form");
+  if (form == DG_VOLUME_SPLIT) {
+    if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the split form covers the Euler equations");
+    if (mesh->h.n_curved > 0) return fail(DG_ERR_UNSUPPORTED, "the split form covers affine meshes");
+  }
+  mesh->split = form == DG_VOLUME_SPLIT;
+  if (mesh->split && mesh->wpb < 1) mesh->wpb = 1;
+  DG_CUDA(mesh->build_groups());
+  DG_CUDA(mesh->build_static_chunks());
+  mesh->drop_graphs();
+  return DG_OK;
+}
+
 dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
+  if (physics == DG_NAVIER_STOKES && (mesh->split || mesh->flux == DG_FLUX_EC))
+    return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes runs with the weak form and the LF or Roe flux");
   if (physics == DG_NAVIER_STOKES) {
     if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(DG_ERR_ARG, "mu must be finite and >= 0");
     if (!(Pr > 0.0) || !std::isfinite(Pr)) return fail(DG_ERR_ARG, "Pr must be finite and > 0");
@@ -1195,10 +1354,7 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   }
   mesh->ns = physics == DG_NAVIER_STOKES;
   DG_CUDA(mesh->build_groups());
-  if (mesh->gexec) {
-    cudaGraphExecDestroy(mesh->gexec);
-    mesh->gexec = nullptr;
-  }
+  mesh->drop_graphs();
   return DG_OK;
 }
 
@@ -1269,13 +1425,11 @@ dg_status dg_rebalance(dg_mesh* mesh, int force, int* rebuilt, cudaStream_t stre
     if (measured && complete)
       for (size_t t = 0; t < tabs.size(); ++t) w[t] = (double)cost[2 * t] / (double)cost[2 * t + 1];
     DG_CUDA(mesh->build_chunks(w.data()));
-    if (mesh->gexec) {
-      cudaGraphExecDestroy(mesh->gexec);
-      mesh->gexec = nullptr;
-    }
+    mesh->drop_graphs();
   }
-  DG_CUDA(cudaMemset(mesh->d_cost, 0, 2 * dgk::kMaxTabs * sizeof(unsigned long long)));
-  DG_CUDA(cudaMemset(mesh->d_smns, 0, (size_t)mesh->num_sms * sizeof(unsigned long long)));
+  // on the caller's stream: the next launch there is ordered after the reset
+  DG_CUDA(cudaMemsetAsync(mesh->d_cost, 0, 2 * dgk::kMaxTabs * sizeof(unsigned long long), stream));
+  DG_CUDA(cudaMemsetAsync(mesh->d_smns, 0, (size_t)mesh->num_sms * sizeof(unsigned long long), stream));
   return DG_OK;
 }
 
@@ -1290,10 +1444,7 @@ dg_status dg_set_element_warps(dg_mesh* mesh, int warps) {
   }
   DG_CUDA(mesh->build_groups());
   DG_CUDA(mesh->build_static_chunks());
-  if (mesh->gexec) {
-    cudaGraphExecDestroy(mesh->gexec);
-    mesh->gexec = nullptr;
-  }
+  mesh->drop_graphs();
   return DG_OK;
 }
 
@@ -1356,10 +1507,7 @@ dg_status apply_table_warps(dg_mesh* mesh, int uniform, const std::vector<int>& 
   if (differs) {
     cudaError_t e = mesh->build_groups();
     if (e != cudaSuccess) return cuda_fail(e, "launch groups");
-    if (mesh->gexec) {
-      cudaGraphExecDestroy(mesh->gexec);
-      mesh->gexec = nullptr;
-    }
+    mesh->drop_graphs();
   }
   return DG_OK;
 }
@@ -1493,10 +1641,7 @@ dg_status dg_set_table_warps(dg_mesh* mesh, int type, int N, int warps) {
   if (t < 0) return fail(DG_ERR_ARG, "no such (type, N) table in the mesh");
   mesh->tab_wpb[t] = warps;
   DG_CUDA(mesh->build_groups());
-  if (mesh->gexec) {
-    cudaGraphExecDestroy(mesh->gexec);
-    mesh->gexec = nullptr;
-  }
+  mesh->drop_graphs();
   return DG_OK;
 }
 
@@ -1539,20 +1684,6 @@ dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream) {
     cudaMemset(mesh->d_status, 0, sizeof(unsigned));
     return fail(DG_ERR_NONFINITE, "a non-finite state value was produced");
   }
-  return DG_OK;
-}
-
-dg_status dg_probe_fp64_mixed(double* total_tflops) {
-  if (!total_tflops) return fail(DG_ERR_ARG, "null argument");
-  cudaError_t e = dgk::probe_fp64_mixed(total_tflops);
-  if (e != cudaSuccess) return cuda_fail(e, "fp64 probe");
-  return DG_OK;
-}
-
-dg_status dg_probe_fp64_peak(double* dfma_tflops, double* dmma_tflops) {
-  if (!dfma_tflops || !dmma_tflops) return fail(DG_ERR_ARG, "null argument");
-  cudaError_t e = dgk::probe_fp64(dfma_tflops, dmma_tflops);
-  if (e != cudaSuccess) return cuda_fail(e, "fp64 probe");
   return DG_OK;
 }
 

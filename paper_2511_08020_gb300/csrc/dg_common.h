@@ -45,6 +45,9 @@ struct TypeTab {
   int minv;     // [nM]                   1 / (V^T W V)_ii   (the mass matrix is diagonal)
   int sqw;      // hexahedron: [nQ] sqrt(w_q), then [nQ] 1 / sqrt(w_q) (scaled nodal storage); -1 otherwise
   int fw;       // [nfaces][n*n]          reference face weights at the face points
+  int sbp;      // hexahedron: [n][n] S_ij = w_i D_ij - w_j D_ji (D_ij = l'_j(x_i)), the antisymmetric
+                //   part of the 1D collocation operator W D (split form); -1 otherwise
+  int w1;       // hexahedron: [n] 1D Gauss-Legendre weights; -1 otherwise
   // int pool
   int col_moff, col_len, col_coff, col_p;   // [ncols]
   int col_order;                            // [ncols] columns by decreasing length (uniform trip counts per warp)

@@ -321,12 +321,12 @@ int Tables::add(int type, int N, std::string* err) {
   }
   // collocation derivative Dt[i'][i] = l'_{i'}(x_i) (barycentric formula)
   t.Dt = (int)dpool.size();
+  std::vector<double> D(n * n, 0.0);  // D[i][j] = l'_j(x_i)
   {
     std::vector<double> lam(n, 1.0);
     for (int j = 0; j < n; ++j)
       for (int k = 0; k < n; ++k)
         if (k != j) lam[j] /= (x[j] - x[k]);
-    std::vector<double> D(n * n, 0.0);  // D[i][j] = l'_j(x_i)
     for (int i = 0; i < n; ++i) {
       double diag = 0.0;
       for (int j = 0; j < n; ++j) {
@@ -338,6 +338,17 @@ int Tables::add(int type, int N, std::string* err) {
     }
     for (int ip = 0; ip < n; ++ip)
       for (int i = 0; i < n; ++i) dput(D[i * n + ip]);
+  }
+  // hexahedra, entropy-stable split form: the antisymmetric part S = Q - Q^T
+  // of the 1D Gauss collocation operator Q = W D, and the 1D weights
+  t.sbp = -1;
+  t.w1 = -1;
+  if (type == dgk::HEX) {
+    t.sbp = (int)dpool.size();
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) dput(w[i] * D[i * n + j] - w[j] * D[j * n + i]);
+    t.w1 = (int)dpool.size();
+    for (int i = 0; i < n; ++i) dput(w[i]);
   }
   // extrapolation to the ends
   t.ext = (int)dpool.size();

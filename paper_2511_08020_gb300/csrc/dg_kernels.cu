@@ -58,6 +58,43 @@ __device__ __forceinline__ void flux_lf(const double* UL, const double* UR, cons
   for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (L.F[v] + R.F[v]) - 0.5 * lam * (UR[v] - UL[v]);
 }
 
+// The Lax-Friedrichs flux above, already multiplied by the face weight
+// wS = w S of the point, arranged for few FP64 instructions: with the scaled
+// normal s = (wS/2) n,
+//   wS F* = F_s(U-) + F_s(U+) + lam_s (U- - U+),
+//   F_s(U) = (m.s, m (m.s)/rho + p s, (E + p)(m.s)/rho),
+//   lam_s = max(|m-.s|/rho- + (wS/2) c-, |m+.s|/rho+ + (wS/2) c+),
+// so rho F_0 = m.n needs no multiply, one reciprocal and one square root per
+// side serve the flux and the wave speed, and the 1/2 and wS scales fold into
+// the normal.
+__device__ __forceinline__ void lf_side(const double* U, const double* s, double h, double gm1, double gamma,
+                                        double* F, double& lam) {
+  const double r = 1.0 / U[0];
+  const double ms = fma(U[1], s[0], fma(U[2], s[1], U[3] * s[2]));
+  const double us = ms * r;
+  const double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
+  const double p = gm1 * fma(-0.5 * r, m2, U[4]);
+  F[0] = ms;
+  F[1] = fma(U[1], us, p * s[0]);
+  F[2] = fma(U[2], us, p * s[1]);
+  F[3] = fma(U[3], us, p * s[2]);
+  F[4] = (U[4] + p) * us;
+  lam = fma(h, sqrt(gamma * p * r), fabs(us));
+}
+
+__device__ __forceinline__ void flux_lf_scaled(const double* UL, const double* UR, const double* n, double wS,
+                                               double gamma, double* Fs) {
+  const double h = 0.5 * wS;
+  const double s[3] = {h * n[0], h * n[1], h * n[2]};
+  const double gm1 = gamma - 1.0;
+  double FL[5], FR[5], lamL, lamR;
+  lf_side(UL, s, h, gm1, gamma, FL, lamL);
+  lf_side(UR, s, h, gm1, gamma, FR, lamR);
+  const double lam = fmax(lamL, lamR);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Fs[v] = fma(lam, UL[v] - UR[v], FL[v] + FR[v]);
+}
+
 // Roe: F* = (F- + F+)/2 - sum_k |lambda_k| alpha_k r_k / 2 with
 // sqrt(rho)-weighted averages of u and H, no entropy fix.
 __device__ __forceinline__ void flux_roe(const double* UL, const double* UR, const double* n, double gamma, double* Fs) {
@@ -96,6 +133,136 @@ __device__ __forceinline__ void flux_roe(const double* UL, const double* UR, con
   D[4] = l1 * (H - c * un) + l5 * (H + c * un) + l2 * (a2 * 0.5 * q2 + rho * udut);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (L.F[v] + R.F[v]) - 0.5 * D[v];
+}
+
+// ------------------------------------------------------------------ two-point flux (split form)
+//
+// Entropy-stable split form (Sec. 2: entropy-stable DGSEM with a
+// summation-by-parts property and Chandrashekar's two-point flux) for the
+// entropy U = -rho s/(gamma-1), s = ln(p rho^-gamma).  A state enters the
+// two-point flux through kTP = 8 quantities: rho, u, v, w, beta = rho/(2p),
+// ln rho, ln beta, |u|^2.
+constexpr int kTP = 8;
+constexpr double kLn2 = 0.69314718055994530942;
+
+__device__ __forceinline__ void two_point_state(const double* U, double gm1, double* P) {
+  const double r = U[0], ri = 1.0 / r;
+  const double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
+  const double q2 = fma(u, u, fma(v, v, w * w));
+  const double p = gm1 * fma(-0.5 * r, q2, U[4]);
+  const double b = 0.5 * r / p;
+  P[0] = r;
+  P[1] = u;
+  P[2] = v;
+  P[3] = w;
+  P[4] = b;
+  P[5] = log(r);
+  P[6] = log(b);
+  P[7] = q2;
+}
+
+// Logarithmic mean (a - b)/(ln a - ln b) from the values and their logs.
+// With f = (a - b)/(a + b) and u = f^2: for u < 1e-2 it is
+// ((a + b)/2) f/artanh(f), the ratio from its Taylor series in u through u^7
+// (f/artanh(f) = 1/(1 + u/3 + u^2/5 + ...); truncation below 2e-18), else the
+// quotient of the differences (whose denominator is then at least 0.2).
+__device__ __forceinline__ double ln_mean(double a, double b, double la, double lb) {
+  const double d = a - b, sm = a + b;
+  if (d * d < 1e-2 * sm * sm) {
+    const double f = d / sm, u = f * f;
+    double g = -5472607916.0 / 488462349375.0;
+    g = fma(g, u, -25865068.0 / 1915538625.0);
+    g = fma(g, u, -10719068.0 / 638512875.0);
+    g = fma(g, u, -10196.0 / 467775.0);
+    g = fma(g, u, -428.0 / 14175.0);
+    g = fma(g, u, -44.0 / 945.0);
+    g = fma(g, u, -4.0 / 45.0);
+    g = fma(g, u, -1.0 / 3.0);
+    g = fma(g, u, 1.0);
+    return 0.5 * sm * g;
+  }
+  return d / (la - lb);
+}
+
+// 1 / ln_mean(a, b): (2/(a + b)) artanh(f)/f = (2/(a + b)) sum_k u^k/(2k+1)
+// for u < 1e-2 (through u^7), else (ln a - ln b)/(a - b).
+__device__ __forceinline__ double inv_ln_mean(double a, double b, double la, double lb) {
+  const double d = a - b, sm = a + b;
+  if (d * d < 1e-2 * sm * sm) {
+    const double is = 1.0 / sm, f = d * is, u = f * f;
+    double h = 1.0 / 15.0;
+    h = fma(h, u, 1.0 / 13.0);
+    h = fma(h, u, 1.0 / 11.0);
+    h = fma(h, u, 1.0 / 9.0);
+    h = fma(h, u, 1.0 / 7.0);
+    h = fma(h, u, 1.0 / 5.0);
+    h = fma(h, u, 1.0 / 3.0);
+    h = fma(h, u, 1.0);
+    return 2.0 * is * h;
+  }
+  return (la - lb) / d;
+}
+
+// Chandrashekar's two-point flux F#(L, R) contracted with m:
+//   F_rho = rho_ln (u_bar . m),  F_mom = p_hat m + u_bar F_rho,
+//   F_E = (1/(2 (gamma-1) beta_ln) - |u|^2_bar/2) F_rho + u_bar . F_mom,
+// bars arithmetic means, _ln logarithmic means, p_hat = rho_bar/(2 beta_bar).
+__device__ __forceinline__ void two_point_flux(const double* L, int sl, const double* R, int sr, const double* m,
+                                               double igm1, double* F) {
+  const double rho_ln = ln_mean(L[0], R[0], L[5 * sl], R[5 * sr]);
+  const double ib_ln = inv_ln_mean(L[4 * sl], R[4 * sr], L[6 * sl], R[6 * sr]);
+  const double u = 0.5 * (L[sl] + R[sr]), v = 0.5 * (L[2 * sl] + R[2 * sr]), w = 0.5 * (L[3 * sl] + R[3 * sr]);
+  const double p_hat = 0.5 * (L[0] + R[0]) / (L[4 * sl] + R[4 * sr]);
+  const double q2 = 0.5 * (L[7 * sl] + R[7 * sr]);
+  const double F0 = rho_ln * fma(u, m[0], fma(v, m[1], w * m[2]));
+  F[0] = F0;
+  F[1] = fma(p_hat, m[0], u * F0);
+  F[2] = fma(p_hat, m[1], v * F0);
+  F[3] = fma(p_hat, m[2], w * F0);
+  F[4] = fma(fma(0.5 * igm1, ib_ln, -0.5 * q2), F0, fma(u, F[1], fma(v, F[2], w * F[3])));
+}
+
+// Entropy variables v = ((gamma - s)/(gamma - 1) - beta |u|^2, 2 beta u, -2 beta)
+// from the two-point quantities (s = ln p - gamma ln rho, ln p = ln rho - ln(2 beta)).
+__device__ __forceinline__ void entropy_variables(const double* P, int sp, double gamma, double* v) {
+  const double igm1 = 1.0 / (gamma - 1.0);
+  const double lnp = P[5 * sp] - kLn2 - P[6 * sp];
+  const double s = lnp - gamma * P[5 * sp];
+  const double b2 = 2.0 * P[4 * sp];
+  v[0] = fma(gamma - s, igm1, -P[4 * sp] * P[7 * sp]);
+  v[1] = b2 * P[sp];
+  v[2] = b2 * P[2 * sp];
+  v[3] = b2 * P[3 * sp];
+  v[4] = -b2;
+}
+
+// The inverse: conservative state U and its two-point quantities P from
+// entropy variables: beta = -v4/2, u = -v_{1..3}/v4,
+// s = gamma - (gamma - 1)(v0 + beta |u|^2), ln rho = -(s + ln(2 beta))/(gamma - 1).
+__device__ __forceinline__ void from_entropy_variables(const double* v, double gamma, double* U, double* P) {
+  const double igm1 = 1.0 / (gamma - 1.0);
+  const double b = -0.5 * v[4];
+  const double iv4 = 1.0 / v[4];
+  const double u = -v[1] * iv4, vv = -v[2] * iv4, w = -v[3] * iv4;
+  const double q2 = fma(u, u, fma(vv, vv, w * w));
+  const double s = gamma - (gamma - 1.0) * fma(b, q2, v[0]);
+  const double lb = log(b);
+  const double lr = -(s + kLn2 + lb) * igm1;
+  const double r = exp(lr);
+  const double p = 0.5 * r / b;
+  U[0] = r;
+  U[1] = r * u;
+  U[2] = r * vv;
+  U[3] = r * w;
+  U[4] = fma(p, igm1, 0.5 * r * q2);
+  P[0] = r;
+  P[1] = u;
+  P[2] = vv;
+  P[3] = w;
+  P[4] = b;
+  P[5] = lr;
+  P[6] = lb;
+  P[7] = q2;
 }
 
 // ------------------------------------------------------------------ viscous physics
@@ -726,6 +893,144 @@ __device__ __forceinline__ void point_metric(int type, const double* wa, const d
   }
 }
 
+// Forward phase of an affine hexahedron in the entropy-stable split form
+// (hybridised Gauss SBP operator along every coordinate line):
+//   r_i = - sum_j S_ij F#(u_i, u_j) - sum_f s_f E_f,i F#(u_i, u~_f)
+//         + sum_f s_f E_f,i sum_j E_f,j F#(u~_f, u_j),
+// S = W D - (W D)^T, E_f the extrapolation to the line's end f (s_- = -1,
+// s_+ = +1), F# contracted with the line direction's metric J dxi_l/dx, u~_f
+// the entropy-projected face state u(E_f v(u)); H_q = sum_l w_perp r_q^(l)
+// with w_perp the product of the two other directions' weights.  For a
+// central F# this is the weak form's H (sum_l D_l^T G_l).  The face states
+// u~ are this element's traces (the face kernel takes the Riemann flux on
+// them).  sQ lives at the start of bufG; workspace: bufA [5 nQ] (nodal state,
+// then entropy variables), bufG: [kTP][nQ] two-point quantities, [kTP][6 n^2]
+// of the face states, [3][n^2][2][5] face sums.
+__device__ __noinline__ void element_forward_split(const Ctx& c, const TypeTab& T, int64_t s, double* bufA,
+                                                   double* bufG, int lane) {
+  const int n = T.n, nQ = T.nQ, n2 = n * n, nF = 6 * n2;
+  const double* dp = c.dpool;
+  const double gamma = c.gamma, gm1 = gamma - 1.0, igm1 = 1.0 / gm1;
+  modal_to_nodal(c, T, bufG, bufA, bufG, lane);
+  double* P = bufG;
+  double* Pf = P + kTP * nQ;
+  double* Gs = Pf + kTP * nF;
+  // nodal two-point quantities; the entropy variables overwrite U in place
+  for (int q = lane; q < nQ; q += blockDim.x) {
+    double U[5], Pq[kTP], v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k] = bufA[k * nQ + q];
+    two_point_state(U, gm1, Pq);
+#pragma unroll
+    for (int k = 0; k < kTP; ++k) P[k * nQ + q] = Pq[k];
+    entropy_variables(Pq, 1, gamma, v);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) bufA[k * nQ + q] = v[k];
+  }
+  __syncthreads();
+  // entropy-projected face states: extrapolate v along the face-normal
+  // coordinate, map back; they are the element's traces
+  const int64_t* ft = c.slot_ftoff + s * 6;
+  for (int w = lane; w < nF; w += blockDim.x) {
+    const int lf = w / n2, p = w - lf * n2;
+    const int ia = p % n, ib = p / n;
+    const FaceDesc d = T.faces[lf];
+    const int sa = d.alpha == 0 ? n2 : (d.alpha == 1 ? n : 1);
+    const int sb = d.beta == 0 ? n2 : (d.beta == 1 ? n : 1);
+    const int sf = d.fixed == 0 ? n2 : (d.fixed == 1 ? n : 1);
+    const double* e = dp + T.ext + d.end * n;
+    const double* V = bufA + ia * sa + ib * sb;
+    double vt[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < n; ++m) DG_FMA5(e[m], V + m * sf, nQ, vt);
+    double U[5], Pp[kTP];
+    from_entropy_variables(vt, gamma, U, Pp);
+    double* out = c.T + ft[lf] + p;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k * n2] = U[k];
+#pragma unroll
+    for (int k = 0; k < kTP; ++k) Pf[k * nF + w] = Pp[k];
+  }
+  __syncthreads();
+  const ElemGeo& g = c.geo[s];
+  const double* S = dp + T.sbp;
+  const double* w1 = dp + T.w1;
+  const double* E = dp + T.ext;
+  // the local face at the end `end` of coordinate l, and the index of a face
+  // point from the two other coordinates' indices (x1 < x2 by coordinate)
+  auto face_of = [&](int l, int end) {
+    int lf = 0;
+    for (int k = 0; k < 6; ++k)
+      if (T.faces[k].fixed == l && T.faces[k].end == end) lf = k;
+    return lf;
+  };
+  auto face_point = [&](int lf, int l, int x1, int x2) {
+    const FaceDesc d = T.faces[lf];
+    const int o1 = l == 0 ? 1 : 0;
+    const int ia = d.alpha == o1 ? x1 : x2, ib = d.beta == o1 ? x1 : x2;
+    return lf * n2 + ia + ib * n;
+  };
+  // face sums G[l][line][end] = sum_j E_end,j F#_l(u~_end, u_j)
+  for (int t = lane; t < 6 * n2; t += blockDim.x) {
+    const int l = t / (2 * n2), rem = t - l * 2 * n2, line = rem >> 1, end = rem & 1;
+    const int x1 = line / n, x2 = line - x1 * n;
+    const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;
+    const int st[3] = {n2, n, 1};
+    const int base = x1 * st[o1] + x2 * st[o2];
+    const int fp = face_point(face_of(l, end), l, x1, x2);
+    const double m[3] = {g.Jg[3 * l], g.Jg[3 * l + 1], g.Jg[3 * l + 2]};
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < n; ++j) {
+      double F[5];
+      two_point_flux(Pf + fp, nF, P + base + j * st[l], nQ, m, igm1, F);
+      const double ej = E[end * n + j];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] = fma(ej, F[k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Gs[t * 5 + k] = acc[k];
+  }
+  __syncthreads();
+  // per node: the three directions' line terms
+  double* H = c.H + c.slot_hoff[s];
+  for (int q = lane; q < nQ; q += blockDim.x) {
+    const int idx[3] = {q / n2, (q / n) % n, q % n};
+    const int st[3] = {n2, n, 1};
+    double h[5] = {0, 0, 0, 0, 0};
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+      const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;
+      const int x1 = idx[o1], x2 = idx[o2], ii = idx[l];
+      const int line = x1 * n + x2;
+      const int base = q - ii * st[l];
+      const double m[3] = {g.Jg[3 * l], g.Jg[3 * l + 1], g.Jg[3 * l + 2]};
+      double r[5] = {0, 0, 0, 0, 0};
+      for (int j = 0; j < n; ++j) {
+        if (j == ii) continue;
+        double F[5];
+        two_point_flux(P + q, nQ, P + base + j * st[l], nQ, m, igm1, F);
+        const double sij = -S[ii * n + j];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = fma(sij, F[k], r[k]);
+      }
+#pragma unroll
+      for (int end = 0; end < 2; ++end) {
+        const double se = (end ? 1.0 : -1.0) * E[end * n + ii];
+        double F[5];
+        two_point_flux(P + q, nQ, Pf + face_point(face_of(l, end), l, x1, x2), nF, m, igm1, F);
+        const double* Gl = Gs + ((l * n2 + line) * 2 + end) * 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = fma(se, Gl[k] - F[k], r[k]);
+      }
+      const double wp = w1[x1] * w1[x2];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) h[k] = fma(wp, r[k], h[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) H[k * nQ + q] = h[k];
+  }
+  __syncthreads();
+}
+
 // Forward phase of the element at slot s: nodal state, own-face traces and
 // the nodal volume residual H.  sQ lives at the start of bufG.
 template <bool CURVED>
@@ -809,6 +1114,7 @@ template <bool ANY>
 __device__ __forceinline__ void element_forward(const Ctx& c, const TypeTab& T, int64_t s, double* bufA, double* bufG,
                                                 int lane) {
   if (ANY && c.slot_coff[s] >= 0) element_forward_t<true>(c, T, s, bufA, bufG, lane);
+  else if (c.split && T.type == HEX) element_forward_split(c, T, s, bufA, bufG, lane);
   else element_forward_t<false>(c, T, s, bufA, bufG, lane);
 }
 
@@ -1697,23 +2003,39 @@ __device__ __forceinline__ void element_vjp_b_ns(const Ctx& c, int64_t s, double
 // One block (1 to 4 warps) works on one element at a time; its threads share
 // the element's shared-memory workspace bufA [5 nQmax] + bufG [15 nQmax].
 
+// The launch's stage arguments with the state, register and time step taken
+// from the device parameter block when the launch has one.
+__device__ __forceinline__ StageArgs resolve_args(const StageArgs& a) {
+  StageArgs r = a;
+  if (a.dyn) {
+    const RkDyn d = *a.dyn;
+    r.Qin = d.Q;
+    r.Qout = d.Q;
+    r.K = d.K;
+    r.dt = d.dt;
+  }
+  return r;
+}
+
 template <int MODE, bool ANY>
-__global__ void __launch_bounds__(128) elem_naive_kernel(Ctx c, StageArgs io, const int64_t* __restrict__ list,
+__global__ void __launch_bounds__(128) elem_naive_kernel(Ctx c, StageArgs io0, const int64_t* __restrict__ list,
                                                          int64_t count) {
   extern __shared__ double smem[];
   const int64_t idx = blockIdx.x;
   if (idx >= count) return;
+  const StageArgs io = resolve_args(io0);
   double* bufA = smem;
   double* bufG = bufA + 5 * c.nQmax;
   process_element<MODE, ANY>(c, io, list ? list[idx] : idx, bufA, bufG, threadIdx.x);
 }
 
 template <int MODE, bool ANY>
-__global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io, const int64_t* __restrict__ list,
+__global__ void __launch_bounds__(128) elem_balanced_kernel(Ctx c, StageArgs io0, const int64_t* __restrict__ list,
                                                             const int64_t* __restrict__ chunk_start, int64_t nchunks,
                                                             unsigned int* counter, unsigned int* next_counter) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_chunk;
+  const StageArgs io = resolve_args(io0);
   // The previous launch on this stream used next_counter and has finished.
   if (blockIdx.x == 0 && threadIdx.x == 0 && next_counter) *next_counter = 0u;
   const int lane = threadIdx.x;
@@ -1790,10 +2112,22 @@ __global__ void face_kernel(Ctx c) {
       nrm[1] = G[n2 + p];
       nrm[2] = G[2 * n2 + p];
     }
-    double Fs[5];
-    if (c.flux == 0) flux_lf(UL, UR, nrm, gamma, Fs);
-    else flux_roe(UL, UR, nrm, gamma, Fs);
     const double wS = cg ? c.fgeo[R.cgeo + 3 * n2 + p] : c.dpool[c.tabs[R.owner_tab].fw + R.owner_lf * n2 + p] * R.S;
+    double Fs[5];
+    if (c.flux == 0) {
+      flux_lf_scaled(UL, UR, nrm, wS, gamma, Fs);   // wS F*
+    } else if (c.flux == 2) {
+      // entropy-conservative: Chandrashekar's F# contracted with wS n
+      double PL[kTP], PR[kTP];
+      two_point_state(UL, gamma - 1.0, PL);
+      two_point_state(UR, gamma - 1.0, PR);
+      const double m[3] = {wS * nrm[0], wS * nrm[1], wS * nrm[2]};
+      two_point_flux(PL, 1, PR, 1, m, 1.0 / (gamma - 1.0), Fs);
+    } else {
+      flux_roe(UL, UR, nrm, gamma, Fs);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fs[v] *= wS;
+    }
     if (R.map >= 0) {
       // permutation map: this thread alone read T0[p] and T1[perm[p]], so it
       // writes both results in place at once
@@ -1801,12 +2135,12 @@ __global__ void face_kernel(Ctx c) {
       double* W0 = c.T + R.toff;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        W0[v * n2 + p] = wS * Fs[v];
-        W0[(5 + v) * n2 + j] = -wS * Fs[v];
+        W0[v * n2 + p] = Fs[v];
+        W0[(5 + v) * n2 + j] = -Fs[v];
       }
     } else {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = wS * Fs[v];
+      for (int v = 0; v < 5; ++v) sF[(fl * 5 + v) * n2 + p] = Fs[v];
     }
   }
   __syncthreads();
@@ -2254,6 +2588,12 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
 }
 
 // Storage <-> caller layout copies (warp per element).
+__global__ void rk_params_kernel(RkDyn* d, double* Q, double* K, double dt) {
+  d->Q = Q;
+  d->K = K;
+  d->dt = dt;
+}
+
 __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __restrict__ dst, int64_t E, int to_storage) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -2265,98 +2605,19 @@ __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __
   for (int w = lane; w < 5 * nM; w += 32) b[w] = a[w];
 }
 
-// FP64 throughput probes.
-__global__ void dfma_probe_kernel(double* out, int iters, double s) {
-  double a[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
-  for (int i = 0; i < iters; ++i) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], s, 1e-7);
-  }
-  double t = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) t += a[k];
-  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
-}
-
-__global__ void dmma_probe_kernel(double* out, int iters) {
-  double a = 1e-3 * (threadIdx.x & 7), b = 1e-3 * (threadIdx.x >> 3);
-  double c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
-  for (int i = 0; i < iters; ++i) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                   : "+d"(c0[k]), "+d"(c1[k])
-                   : "d"(a), "d"(b));
-  }
-  double t = 0;
-  for (int k = 0; k < 4; ++k) t += c0[k] + c1[k];
-  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
-}
-
-// Half the warps of a block run DFMA chains, the other half mma.sync f64:
-// shows whether the two share one FP64 throughput limit.
-__global__ void fp64_mixed_probe_kernel(double* out, int it_f, int it_m) {
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double t = 0;
-  if (warp < nw / 2) {
-    double a[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
-    for (int i = 0; i < it_f; ++i) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) a[k] = fma(a[k], 1.0000001, 1e-7);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) t += a[k];
-  } else {
-    double a = 1e-3 * (threadIdx.x & 7), b = 1e-3 * ((threadIdx.x >> 3) & 3);
-    double c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
-    for (int i = 0; i < it_m; ++i) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                     : "+d"(c0[k]), "+d"(c1[k])
-                     : "d"(a), "d"(b));
-    }
-    for (int k = 0; k < 4; ++k) t += c0[k] + c1[k];
-  }
-  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
-}
-
 }  // namespace
 
-cudaError_t probe_fp64_mixed(double* total_tflops) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = sms * 4, threads = 256, itf = 4000, itm = 4000;
-  double* out = nullptr;
-  e = cudaMalloc(&out, sizeof(double) * blocks * threads);
-  if (e != cudaSuccess) return e;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  fp64_mixed_probe_kernel<<<blocks, threads>>>(out, 10, 10);
-  cudaEventRecord(e0);
-  fp64_mixed_probe_kernel<<<blocks, threads>>>(out, itf, itm);
-  cudaEventRecord(e1);
-  cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  const double fl = 2.0 * 8 * itf * (double)blocks * (threads / 2) + 2.0 * 8 * 8 * 4 * 4 * itm * (double)blocks * (threads / 64);
-  *total_tflops = fl / (ms * 1e-3) / 1e12;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  e = cudaGetLastError();
-  cudaFree(out);
-  return e;
-}
-
 int element_smem_bytes(int nQmax, int) { return 20 * nQmax * (int)sizeof(double); }
+
+int element_launch_smem_bytes(int nQmax, int wpb, bool split) {
+  int b = element_smem_bytes(nQmax, wpb);
+  if (!split) return b;
+  int n = 1;
+  while (n * n * n < nQmax) ++n;
+  // bufA [5 nQ] + two-point quantities [kTP][nQ] + face states [kTP][6 n^2] + face sums [3][n^2][2][5]
+  const int sb = (5 * nQmax + kTP * nQmax + kTP * 6 * n * n + 30 * n * n) * (int)sizeof(double);
+  return b > sb ? b : sb;
+}
 int face_block_threads(int n) { return 32 * n; }
 
 namespace {
@@ -2417,8 +2678,8 @@ cudaError_t element_kernel_attributes_ns(int nQmax, int wpb, int* blocks_per_sm,
                                                        element_smem_bytes_ns(nQmax));
 }
 
-cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm, bool curved) {
-  const int bmax = element_smem_bytes(kMaxnQ, wpb);
+cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm, bool curved, bool split) {
+  const int bmax = element_launch_smem_bytes(kMaxnQ, wpb, true);
   cudaError_t e;
   if ((e = set_mode<kFwd>(bmax)) != cudaSuccess) return e;
   if ((e = set_mode<kBwdRhs>(bmax)) != cudaSuccess) return e;
@@ -2447,12 +2708,12 @@ cudaError_t element_kernel_attributes(int nQmax, int wpb, int* blocks_per_sm, bo
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd, true>, 32 * wpb,
                                                          element_smem_bytes(nQmax, wpb));
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elem_balanced_kernel<kBwdRkFwd, false>, 32 * wpb,
-                                                       element_smem_bytes(nQmax, wpb));
+                                                       element_launch_smem_bytes(nQmax, wpb, split));
 }
 
 void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, bool balanced, int grid, int wpb,
                     cudaStream_t st) {
-  int bytes = mode == kNsVolume ? element_smem_bytes_ns(c.nQmax) : element_smem_bytes(c.nQmax, wpb);
+  int bytes = mode == kNsVolume ? element_smem_bytes_ns(c.nQmax) : element_launch_smem_bytes(c.nQmax, wpb, c.split != 0);
   switch (mode) {
     case kNsVolume: launch_mode<kNsVolume>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kFwd: launch_mode<kFwd>(c, a, s, balanced, grid, wpb, bytes, st); break;
@@ -2533,46 +2794,26 @@ void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
   else face_kernel<false><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
 }
 
+void launch_rk_params(RkDyn* d, double* Q, double* K, double dt, cudaStream_t st) {
+  rk_params_kernel<<<1, 1, 0, st>>>(d, Q, K, dt);
+}
+
+void rk_params_node(cudaKernelNodeParams* p, void** args) {
+  p->func = (void*)rk_params_kernel;
+  p->gridDim = dim3(1, 1, 1);
+  p->blockDim = dim3(1, 1, 1);
+  p->sharedMemBytes = 0;
+  p->kernelParams = args;
+  p->extra = nullptr;
+}
+
+bool is_rk_params_kernel(const void* func) { return func == (const void*)rk_params_kernel; }
+
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st) {
   const int wpb = 4;
   int64_t blocks = (E + wpb - 1) / wpb;
   permute_kernel<<<(unsigned)blocks, 32 * wpb, 0, st>>>(c, src, dst, E, to_storage);
 }
 
-cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = sms * 4, threads = 128;
-  double* out = nullptr;
-  e = cudaMalloc(&out, sizeof(double) * blocks * threads);
-  if (e != cudaSuccess) return e;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float ms = 0.f;
-  const int it1 = 4000, it2 = 1000;
-  dfma_probe_kernel<<<blocks, threads>>>(out, 10, 1.0000001);
-  cudaEventRecord(e0);
-  dfma_probe_kernel<<<blocks, threads>>>(out, it1, 1.0000001);
-  cudaEventRecord(e1);
-  cudaEventSynchronize(e1);
-  cudaEventElapsedTime(&ms, e0, e1);
-  *dfma_tflops = 2.0 * 8 * it1 * (double)blocks * threads / (ms * 1e-3) / 1e12;
-  dmma_probe_kernel<<<blocks, threads>>>(out, 10);
-  cudaEventRecord(e0);
-  dmma_probe_kernel<<<blocks, threads>>>(out, it2);
-  cudaEventRecord(e1);
-  cudaEventSynchronize(e1);
-  cudaEventElapsedTime(&ms, e0, e1);
-  *dmma_tflops = 2.0 * 8 * 8 * 4 * 4 * it2 * (double)blocks * (threads / 32) / (ms * 1e-3) / 1e12;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  e = cudaGetLastError();
-  cudaFree(out);
-  return e;
-}
 
 }  // namespace dgk

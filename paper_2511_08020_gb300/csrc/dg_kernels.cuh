@@ -63,7 +63,8 @@ struct Ctx {
   unsigned long long* cost;    // [kMaxTabs tables][2]: ns, count
   unsigned long long* sm_ns;   // [num SMs]
   double gamma;
-  int flux;                    // 0 LF, 1 Roe
+  int flux;                    // 0 LF, 1 Roe, 2 entropy-conservative (Chandrashekar F#.n, no dissipation)
+  int split;                   // 1: hexahedra evaluate the entropy-stable split form of the volume term
   int nQmax;
   // Navier-Stokes (BR1) state; ns == 0 for the Euler equations
   int ns;
@@ -95,11 +96,22 @@ struct VjpArgs {
   int stored;   // 1: the forward nodal state (Unod) and traces (T) of Q were kept by the forward pass
 };
 
+// State, register and time step of dg_rk_step, read by the element kernels
+// from device memory so that one captured stage graph serves every call (the
+// graph's first node, rk_params_kernel, writes them).
+struct RkDyn {
+  double* Q;
+  double* K;
+  double dt;
+  double pad;
+};
+
 struct StageArgs {
   const double* Qin;   // state (storage layout) or point values / ext state
   double* Qout;        // updated state (may alias Qin) or R / storage output
   double* K;           // LSERK register
   double a, b, dt;     // K <- a K + dt R (a == 0: K <- dt R), Q <- Q + b K
+  const RkDyn* dyn = nullptr;   // non-null: Qin = Qout = dyn->Q, K = dyn->K, dt = dyn->dt
 };
 
 struct Sched {
@@ -125,12 +137,21 @@ void launch_vjp(const Ctx& c, int phase, const VjpArgs& va, int64_t nelem, int w
 void launch_faces_ns_vjp(const Ctx& c, int64_t nblocks, int n, int kind, cudaStream_t st);
 void launch_faces_vjp(const Ctx& c, int64_t nblocks, int n, cudaStream_t st);
 void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int to_storage, cudaStream_t st);
+// One-thread kernel that writes (Q, K, dt) into *d; the head node of the
+// captured stage graphs.  rk_params_node fills the kernel-node parameters of
+// that node for cudaGraphExecKernelNodeSetParams (args: &d, &Q, &K, &dt), and
+// is_rk_params_kernel recognises the node's function in a captured graph.
+void launch_rk_params(RkDyn* d, double* Q, double* K, double dt, cudaStream_t st);
+void rk_params_node(cudaKernelNodeParams* p, void** args);
+bool is_rk_params_kernel(const void* func);
 int element_smem_bytes(int nQmax, int warps_per_block);
+// shared memory of an element launch: element_smem_bytes, or the split form's
+// larger workspace when c.split is set
+int element_launch_smem_bytes(int nQmax, int warps_per_block, bool split);
 int face_block_threads(int n);
 // curved: the mesh holds curved elements (occupancy of the kernel variants that handle them)
-cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false);
+cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false,
+                                      bool split = false);
 cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false);
-cudaError_t probe_fp64(double* dfma_tflops, double* dmma_tflops);
-cudaError_t probe_fp64_mixed(double* total_tflops);
 
 }  // namespace dgk

@@ -39,7 +39,7 @@ def _worker(rank, ws, port, outdir):
     ran = None
     if rank != 0:
         import argparse
-        ran = bench.run_reference(argparse.Namespace(flux="lf", ref_sample=4, steps=1, warmup=0))
+        ran = bench.run_reference(argparse.Namespace(flux="lf", steps=1, warmup=0))
     barrier()
     dist.destroy_process_group()
     with open(os.path.join(outdir, f"rank{rank}.json"), "w") as f:

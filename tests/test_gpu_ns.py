@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import dg_inputs as di
-from gpu_util import TOL, make_box, rel_err, var_index
+from gpu_util import FULL_SIZE_AMP, TOL, assert_sampled_parity, make_box, rel_err, var_index
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -271,7 +271,8 @@ def test_ns_kinetic_energy_adjoint_central_differences(dg):
 
 def test_ns_sampled_12cube_N4(dg):
     """12^3 mixed box (the 40/30/30 recipe of the viscous TGV workload), N = 4,
-    Re = 1600 viscosity: sampled elements against the oracle."""
+    Re = 1600 viscosity, TGV perturbed at amplitude 0.1: sampled elements
+    against the oracle, plain per-variable metric at 1e-11."""
     from oracle.mesh import from_box
     from oracle.navier_stokes import NSOracle
     box = di.box_mesh(12, "mixed", seed=4, p_prism=0.25, p_pyr=1.0 / 9.0)
@@ -281,7 +282,8 @@ def test_ns_sampled_12cube_N4(dg):
     mesh.set_physics("navier_stokes", 1.0 / 1600, PR)
     xyz = mesh.quad_points()
     n = N + 1
-    vals = di.perturbed_tgv_state(xyz, seed=8, amp=1e-2).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    vals = di.perturbed_tgv_state(xyz, seed=8, amp=FULL_SIZE_AMP)
+    vals = vals.reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
     Qs = mesh.project(torch.from_numpy(vals).cuda())
     Q = mesh.get_state(Qs)
     R = mesh.get_state(mesh.rhs(Qs))
@@ -291,15 +293,11 @@ def test_ns_sampled_12cube_N4(dg):
     mask = np.zeros(len(Q), dtype=bool)
     for e in elems:
         mask[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = True
-    vidx = var_index(o.mesh.nM)
-    # Each variable's error is measured against the larger of its residual and
-    # its volume-term magnitude (in residual units): at this resolution the
-    # residual is a cancellation of terms up to 100x larger.
     G = o.lifted_gradient(Q, elems)
-    vol = np.zeros(mesh.n_dof)
-    for e in elems:
-        vol[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, o.ns_volume_term(Q, e, G)).ravel()
-    for v in range(5):
-        i = vidx[v][mask[vidx[v]]]
-        scale = max(np.abs(Rref[i]).max(), np.abs(vol[i]).max())
-        assert np.abs(R[i] - Rref[i]).max() < TOL * scale, (v, np.abs(R[i] - Rref[i]).max(), scale)
+
+    def volume():
+        vol = np.zeros(mesh.n_dof)
+        for e in elems:
+            vol[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, o.ns_volume_term(Q, e, G)).ravel()
+        return vol
+    assert_sampled_parity(R, Rref, var_index(o.mesh.nM), mask, volume=volume, label="NS 12^3")

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import dg_inputs as di
-from gpu_util import TOL, make_box, rel_err, var_index
+from gpu_util import FULL_SIZE_AMP, TOL, assert_sampled_parity, make_box, rel_err, var_index
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -70,6 +70,39 @@ def test_rk_step_parity(dg, kind, m, N, flux, reorder, nsteps):
     assert err < 1e-10, err
     assert rel_err(Qg, Qref, var_index(o.mesh.nM)) < TOL
     mesh.sync()
+
+
+def test_rk_step_graphs_replayed_for_new_buffers_dt_and_step_counts(dg):
+    """50 dg_rk_step calls alternating two state / register buffer pairs, with
+    dt and the step count changing every call, capture the stage graphs once.
+    The states equal bit for bit the same calls on a second mesh in profiling
+    mode (one graph per call, captured again whenever an argument changes)
+    and the oracle's LSERK steps to 1e-11."""
+    box, o, mesh = setup(dg, "mixed", 3, 3, "lf", None)
+    ref = dg.Mesh(box, 3, flux="lf")
+    ref.set_profiling(True)
+    QA, QB = state(o, seed=3), state(o, seed=4)
+    A, B = mesh.set_state(torch.from_numpy(QA).cuda()), mesh.set_state(torch.from_numpy(QB).cuda())
+    RA, RB = A.clone(), B.clone()
+    KA, KB, KR = mesh.empty(), mesh.empty(), ref.empty()
+    for i in range(50):
+        dt = 1e-3 * (1.0 + 0.25 * np.sin(i))
+        nsteps = 1 + i % 3
+        X, K, Y = (A, KA, RA) if i % 2 == 0 else (B, KB, RB)
+        mesh.rk_step(X, K, dt, nsteps)
+        ref.rk_step(Y, KR, dt, nsteps)
+        if i % 2 == 0:
+            QA = o.run(QA, dt, nsteps)
+        else:
+            QB = o.run(QB, dt, nsteps)
+    mesh.sync()
+    ref.sync()
+    assert mesh.graph_captures() == 1
+    assert ref.graph_captures() == 50
+    assert torch.equal(A, RA) and torch.equal(B, RB)
+    vidx = var_index(o.mesh.nM)
+    assert rel_err(mesh.get_state(A), QA, vidx) < TOL
+    assert rel_err(mesh.get_state(B), QB, vidx) < TOL
 
 
 def test_zero_steps_is_identity(dg):
@@ -184,8 +217,9 @@ def test_conservation_gpu(dg):
 def test_full_size_sampled_parity(dg):
     """16^3 mixed hex/prism/pyramid mesh at N = 4 (the benchmark workload),
     balanced scheduler: dg_rhs on every element, checked against the oracle on
-    a seeded sample of elements; plus conservation of one graph-replayed
-    LSERK step, and bitwise equality with the naive scheduler."""
+    a seeded sample of elements with the plain per-variable metric at 1e-11;
+    plus conservation of one graph-replayed LSERK step, and bitwise equality
+    with the naive scheduler."""
     from oracle.dg import Oracle
     from oracle.mesh import from_box
     box = make_box("mixed", 16, seed=2)
@@ -200,8 +234,9 @@ def test_full_size_sampled_parity(dg):
     # The TGV velocity is divergence-free, so its density residual is pure
     # truncation error (~1e-5) and a normwise relative error on it measures
     # rounding against ~0; the residual check uses the seeded perturbation of
-    # the TGV (amplitude 1e-2, 4 lowest Fourier modes) instead.
-    pvals = di.perturbed_tgv_state(xyz, seed=3).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    # the TGV (4 lowest Fourier modes) instead.
+    pvals = di.perturbed_tgv_state(xyz, seed=3, amp=FULL_SIZE_AMP)
+    pvals = pvals.reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
     Ps = mesh.project(torch.from_numpy(pvals).cuda())
     P = mesh.get_state(Ps)
     R = mesh.get_state(mesh.rhs(Ps))
@@ -212,18 +247,7 @@ def test_full_size_sampled_parity(dg):
     for e in sample:
         mask[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = True
     vidx = var_index(o.mesh.nM)
-    # At this size the residual is a cancellation of terms up to 100x larger
-    # (p0 = 71 at Ma 0.1 and small elements): a 1-ulp perturbation of the
-    # input alone moves the exact density residual by 2.6e-11 of its maximum.
-    # Each variable's error is therefore measured against the larger of its
-    # residual and its volume-term magnitude (in residual units), at 1e-11.
-    vol = np.zeros(mesh.n_dof)
-    for e in sample:
-        vol[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, o.volume_term(P, e)).ravel()
-    for v in range(5):
-        i = vidx[v][mask[vidx[v]]]
-        scale = max(np.abs(Rref[i]).max(), np.abs(vol[i]).max())
-        assert np.abs(R[i] - Rref[i]).max() < TOL * scale, v
+    assert_sampled_parity(R, Rref, vidx, mask, volume=lambda: volume_magnitude(o, P, sample), label="16^3 N=4")
     # the same inputs projected by the oracle agree with dg_project
     Qo = np.zeros_like(Q)
     for e in sample[:8]:
@@ -248,6 +272,14 @@ def test_full_size_sampled_parity(dg):
     Q3 = Qs.clone()           # the same stored state (same Hilbert order)
     naive.rk_step(Q3, naive.empty(), 1e-3, 1)
     assert torch.equal(Q3, Q2)
+
+
+def volume_magnitude(o, Q, elems):
+    """The oracle's volume term M^{-1} vol of the sampled elements (residual units)."""
+    vol = np.zeros(len(Q))
+    for e in elems:
+        vol[o.mesh.dof_off[e]:o.mesh.dof_off[e + 1]] = o.apply_minv(e, o.volume_term(Q, e)).ravel()
+    return vol
 
 
 @pytest.mark.parametrize("physics", ["euler", "navier_stokes"])

@@ -4,8 +4,10 @@ is a fixed 64 MiB array in the library image instead of a cudaMalloc'd
 buffer.  Called through the C ABI; checked against dg_rhs_vjp on two calls
 in a row with different cotangents (the second call must not depend on what
 the first left in the shared array), and a mesh whose face scratch exceeds
-the fixed size must be rejected with DG_ERR_ARG.  This file is collected
-last so that a run stopping at the first failure has run everything else."""
+the fixed size must be rejected with DG_ERR_ARG; free device memory must not
+change across a call on a mesh that never ran dg_rhs_vjp.  This file is
+collected last so that a run stopping at the first failure has run everything
+else."""
 import ctypes
 
 import numpy as np
@@ -80,3 +82,37 @@ def test_noalloc_rejects_meshes_beyond_the_fixed_scratch(dg):
     status = noalloc(dg, mesh, Q, W, out)
     assert status == -1
     assert "64 MiB" in dg.load().dg_last_error().decode()
+
+
+def test_noalloc_allocates_no_device_memory(dg):
+    """Free device memory is the same before and after a call on a fresh mesh
+    that has never run dg_rhs_vjp (whose first call cudaMallocs the face
+    scratch); the same measurement does see that allocation afterwards."""
+    from oracle.elements import n_modes
+    N = 4
+    # load the entry point's device code and kernels first (a module load
+    # allocates device memory once per process)
+    warm = dg.Mesh(make_box("mixed", 3, seed=1), N)
+    Qw = warm.empty().fill_(0.0)
+    assert noalloc(dg, warm, Qw, Qw, warm.empty()) == 0, dg.load().dg_last_error().decode()
+    torch.cuda.synchronize()
+    box = make_box("mixed", 10, seed=3)   # ~1.9 Mi doubles of face scratch (15 MB)
+    mesh = dg.Mesh(box, N)
+    nM = [n_modes(int(t), N) for t in box.etype]
+    Q = mesh.set_state(di.random_modal_state(nM, seed=2, amp=1e-2))
+    W = mesh.set_state(di.random_vector(mesh.n_dof, seed=34))
+    out = torch.full_like(Q, float("nan"))
+    ref = mesh.empty()
+    mesh.rhs(Q)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert noalloc(dg, mesh, Q, W, out) == 0, dg.load().dg_last_error().decode()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    mesh.rhs_vjp(Q, W, ref)   # allocates the mesh's own face scratch
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free0 - free2 >= 8 << 20, (free0, free2)
+    assert rel_err(mesh.get_state(out), mesh.get_state(ref), var_index(nM)) < TOL
+    mesh.sync()
