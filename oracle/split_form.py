@@ -131,6 +131,19 @@ def central(UL, UR, m, gamma):
     return 0.5 * sum((FL[d] + FR[d]) * m[d] for d in range(3))
 
 
+def lagrange_values(x, pts):
+    """l_j(pts) for the Lagrange basis on the nodes x, from the product form:
+    [len(pts), n]."""
+    pts = np.asarray(pts, dtype=float)
+    n = len(x)
+    L = np.ones((pts.size, n))
+    for j in range(n):
+        for k in range(n):
+            if k != j:
+                L[:, j] *= (pts - x[k]) / (x[j] - x[k])
+    return L
+
+
 def lagrange_1d(x):
     """Derivative matrix D_ij = l_j'(x_i) and end values E[-], E[+] (rows
     l_j(-1), l_j(+1)) of the Lagrange basis on the nodes x, from the product
@@ -171,13 +184,13 @@ class SplitFormOracle(Oracle):
         self.x1, self.w1 = x, w
         self.D1, self.E1 = lagrange_1d(x)
         self.Q1 = w[:, None] * self.D1
+        self._ref_cache = {}
         if HEX in self.ops:
             op = self.ops[HEX]
             # the oracle's hexahedral volume points are (xi_i, eta_j, zeta_k),
             # k fastest: check, so the tensor lines below are the right ones
             grid = np.stack(np.meshgrid(x, x, x, indexing="ij"), axis=-1).reshape(-1, 3)
             assert np.abs(op.pts - grid).max() < 1e-14
-            self.Vinv_hex = op.V.T * op.w[None, :]     # V^{-1} = V^T W (V^T W V = I)
 
     # ------------------------------------------------------------ hexahedra
     def nodal_state(self, Q, e):
@@ -223,18 +236,29 @@ class SplitFormOracle(Oracle):
         # modal test functions: phi_i = sum_q phi_i(x_q) l_q, so vol = V^T H
         return self.split_volume_nodal(Q, e) @ self.ops[HEX].V
 
-    def trace(self, Q, e, phi):
-        """The element's state at face points whose basis values are phi [P, nM]."""
+    def trace(self, Q, e, phi, ref):
+        """The element's state at face points with reference coordinates ref
+        [P, 3] and basis values phi [P, nM].  A split-form hexahedron gives
+        u(v~), v~ the interpolant of the nodal entropy variables at the
+        points, evaluated in its Lagrange form sum_q l_q(x) v_q (tensor
+        products of 1D Lagrange polynomials on the Gauss nodes)."""
         if self.mesh.etype[e] != HEX or not self.project_traces:
             return self.mesh.block(Q, e) @ phi.T
-        v = entropy_variables(self.nodal_state(Q, e), self.gamma)
-        return conservative_from_entropy((v @ self.Vinv_hex.T) @ phi.T, self.gamma)
+        v = entropy_variables(self.nodal_state(Q, e), self.gamma)           # [5, n^3]
+        n = self.mesh.N + 1
+        La, Lb, Lc = (lagrange_values(self.x1, ref[:, d]) for d in range(3))
+        ell = np.einsum("pi,pj,pk->pijk", La, Lb, Lc).reshape(len(ref), n ** 3)
+        return conservative_from_entropy(v @ ell.T, self.gamma)
 
     def face_flux(self, Q, f):
         m = self.mesh
         e0, _, e1, _ = m.faces[f]
         phi0, phi1, wS, nrm = self.face_data(f)
-        UL, UR = self.trace(Q, e0, phi0), self.trace(Q, e1, phi1)
+        if f not in self._ref_cache:
+            ref0, ref1, _, _ = m.face_geometry(f)
+            self._ref_cache[f] = (ref0, ref1)
+        ref0, ref1 = self._ref_cache[f]
+        UL, UR = self.trace(Q, e0, phi0, ref0), self.trace(Q, e1, phi1, ref1)
         if self.iflux == "ec":
             return wS * chandrashekar(UL, UR, nrm, self.gamma)
         return wS * riemann(self.flux, UL, UR, nrm, self.gamma)
