@@ -123,6 +123,23 @@ def survey_element_flops(t, N, flux):
             + n * n * nf / 2 * fR + 20 * nM)
 
 
+def split_hex_flops(N):
+    """Algorithmic flops of one hexahedron for one stage in the entropy-stable
+    split form (alg_counts.json, model split_hex): the weak-form element
+    without its collocation derivative and contravariant flux, plus every
+    unordered node pair of every coordinate line once, every (face state,
+    node) pair once, the nodal two-point states and entropy variables, and
+    the extrapolated and converted face states."""
+    n = N + 1
+    f2 = ALG["split_two_point_flux"]
+    base = element_flops(0, N) - 2 * 5 * 3 * n ** 4 - n ** 3 * (61 + 9)
+    pairs = 3 * n * n * (n * (n - 1) // 2) * (f2 + 2 * 2 * 5)
+    face_pairs = 3 * n * n * 2 * n * (f2 + 2 * 2 * 5)
+    nodes = n ** 3 * (ALG["split_two_point_state"] + ALG["split_entropy_variables"])
+    face_states = 6 * n * n * (2 * 5 * n + ALG["split_from_entropy_variables"])
+    return base + pairs + face_pairs + nodes + face_states
+
+
 def curved_element_flops(t, N):
     """element_flops of a curved element: the pointwise metric is read
     instead of formed (no metric flops), a hexahedron scales its nodal
@@ -183,7 +200,7 @@ FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 2
 # (backward + LSERK + forward) of this workload, from the committed ncu
 # capture of the element kernel on the 16^3 N = 4 mesh; set to None whenever
 # the element kernel changes until it is captured again.
-NCU_TRAFFIC_FUSED_LAUNCH = (186.212096 + 145.397760) * 1e6
+NCU_TRAFFIC_FUSED_LAUNCH = (153.895424 + 132.812032) * 1e6
 
 
 def fp64_probes():
@@ -574,6 +591,13 @@ def run_ours(args):
 
 
 def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, max_over_ranks):
+    if args.split_only:
+        sp = split_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, None)
+        if rank == 0:
+            print(json.dumps({"metric": "FP64 RHS DOF-updates/s per RK stage (split form on hexahedra)",
+                              "value": sp["value"], "unit": "DOF-updates/s", "split_form": sp,
+                              "split_only": True}), flush=True)
+        return
     if args.curved_only:
         # profiling aid: the curved-geometry leg alone (its affine ratio is omitted)
         cv = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, None)
@@ -845,6 +869,9 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
     batch = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.batch_steps > 0 else None
     nsl = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.ns_steps > 0 else None
     cvl = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, value) if args.curved_steps > 0 else None
+    spl = split_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, value) if args.split_steps > 0 else None
+    prt = (partitioned_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, rank)
+           if args.partition_steps > 0 else None)
     if rank != 0:
         return
     line = {
@@ -915,6 +942,11 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
         line["navier_stokes"] = nsl
     if cvl is not None:
         line["curved"] = cvl
+    if spl is not None:
+        line["split_form"] = spl
+    if prt is not None:
+        prt["over_whole_mesh"] = prt["value"] / value if prt["value"] and ws == 1 else None
+        line["partitioned"] = prt
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.flux, args.cpu_one_core_sample)
     print(json.dumps(line), flush=True)
@@ -1266,6 +1298,185 @@ def curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, affine_value)
     return out
 
 
+def partitioned_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, rank):
+    """The benchmark mesh partitioned along the Hilbert curve (Sec. 3,
+    dg_partition_plan, equal element weights): one part per rank under
+    torchrun, the halo traces exchanged every stage by NCCL send/recv; on one
+    rank, args.parts parts in this process on this GPU with the exchange by
+    device copies.  Steps through dg_rk_prime / dg_rk_stage."""
+    import torch
+    box = build_workload()
+    N = N_DEG
+    nparts = ws if ws > 1 else args.parts
+    plan = dg.partition_plan(box, N, nparts)[0]
+    mine = [rank] if ws > 1 else list(range(nparts))
+    parts = [dg.Part(box, N, plan, nparts, p, flux=args.flux) for p in mine]
+    n = N + 1
+    Qs, Ks = [], []
+    for P in parts:
+        xyz = P.quad_points()
+        vals = di.tgv_state(xyz).reshape(5, P.n_elems, n ** 3).transpose(1, 0, 2).copy()
+        Qs.append(P.project(torch.from_numpy(vals).to(dev)))
+        Ks.append(torch.empty_like(Qs[-1]))
+    dt = tgv_dt(box, dg.check_mesh(box, N)[1], N)
+    per = parts[0].doubles_per_face
+    bufs = [P.halo_buffers() for P in parts]
+
+    def seg(counts, k):
+        a = int(counts[:k].sum()) * per
+        return slice(a, a + int(counts[k]) * per)
+
+    if ws > 1:
+        import torch.distributed as dist
+        P, (send, recv) = parts[0], bufs[0]
+
+        def exchange():
+            P.halo_pack(send)
+            ops = []
+            for q in range(nparts):
+                if P.send_faces[q]:
+                    ops.append(dist.P2POp(dist.isend, send[seg(P.send_faces, q)], q))
+                if P.recv_faces[q]:
+                    ops.append(dist.P2POp(dist.irecv, recv[seg(P.recv_faces, q)], q))
+            if ops:
+                for r in dist.batch_isend_irecv(ops):
+                    r.wait()
+            P.halo_unpack(recv)
+    else:
+        def exchange():
+            for Pp, (snd, _) in zip(parts, bufs):
+                Pp.halo_pack(snd)
+            for p in range(nparts):
+                for q in range(nparts):
+                    if parts[p].send_faces[q]:
+                        bufs[q][1][seg(parts[q].recv_faces, p)].copy_(bufs[p][0][seg(parts[p].send_faces, q)])
+            for Pp, (_, rcv) in zip(parts, bufs):
+                Pp.halo_unpack(rcv)
+
+    owned = [int((P.is_ghost == 0).sum()) for P in parts]
+    dof_owned = sum(int(sum(n_modes(int(box.etype[g]), N) for g, gh in zip(P.global_of_local, P.is_ghost) if not gh))
+                    for P in parts)
+    steps = args.partition_steps
+    dg.step_parts(parts, Qs, Ks, dt, args.warmup, exchange)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with timed_window("partitioned"):
+        e0.record(stream)
+        dg.step_parts(parts, Qs, Ks, dt, steps, exchange)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    total_dof = dof_owned * (ws if ws > 1 else 1)    # each rank owns a different part: the job's DOF
+    out = {"parts": nparts, "ranks": ws, "parts_per_gpu": len(parts), "steps": steps, "ms_per_step": ms / steps,
+           "value": total_dof * 5 * steps / (ms * 1e-3) if ws == 1 else None, "unit": "DOF-updates/s",
+           "owned_elements": owned, "halo_faces_sent": [int(P.send_faces.sum()) for P in parts],
+           "exchange": "NCCL send/recv per stage" if ws > 1 else "device copies between parts on one GPU",
+           "finite": all(bool(torch.isfinite(Q).all()) for Q in Qs)}
+    if ws > 1:
+        # every rank owns a disjoint part: the job's rate is the sum of the parts' DOF over the slowest rank's time
+        t = torch.tensor([float(dof_owned)], device=dev)
+        import torch.distributed as dist
+        dist.all_reduce(t)
+        out["value"] = float(t.item()) * 5 * steps / (ms * 1e-3)
+        out["scaling"] = "strong"
+    for P in parts:
+        P.sync()
+        P.close()
+    return out
+
+
+SPLIT_WORKLOAD = ("16^3-cube periodic box, mixed hex/prism/pyramid (seed 2), N=4, Euler TGV (Ma 0.1), LF, CFL 0.5, "
+                  "FP64; hexahedra in the entropy-stable split form (Chandrashekar two-point flux, hybridised Gauss "
+                  "SBP lines, entropy-projected traces), prisms and pyramids in the weak form")
+
+
+def split_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, weak_value):
+    """The benchmark mesh with the hexahedra in the entropy-stable split form
+    (dg_set_volume_form): balanced and naive, the element kernel's rate
+    against the split-form flop model, and the cost per element type."""
+    import torch
+    box = build_workload()
+    mesh = dg.Mesh(box, N_DEG, flux=args.flux, scheduler="balanced")
+    mesh.set_volume_form("split")
+    n = N_DEG + 1
+    xyz = mesh.quad_points()
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Q0 = mesh.project(torch.from_numpy(vals).to(dev))
+    dt = tgv_dt(box, xyz, N_DEG)
+    del vals, xyz
+    dof = int(sum(n_modes(int(t), N_DEG) for t in box.etype))
+    steps = args.split_steps
+    out = {"workload": SPLIT_WORKLOAD, "steps": steps, "dt": dt, "unit": "DOF-updates/s",
+           "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), mesh.type_counts))}
+
+    def timed(Q, K, profile=False, nsteps=steps, warmup=args.warmup):
+        mesh.set_profiling(profile)
+        for _ in range(warmup):
+            mesh.rk_step(Q, K, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el = fa = 0.0
+        with timed_window("split form"):
+            e0.record(stream)
+            for _ in range(nsteps):
+                mesh.rk_step(Q, K, dt, 1)
+                if profile:
+                    a, b_, _, _ = mesh.phase_times()
+                    el += a
+                    fa += b_
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        mesh.set_profiling(False)
+        return max_over_ranks(e0.elapsed_time(e1)), el, fa
+
+    res = {}
+    for sched in ("naive", "balanced"):
+        mesh.set_scheduler(sched)
+        if args.warps:
+            mesh.set_element_warps(args.warps)
+            warps = args.warps
+        else:
+            warps, _ = mesh.autotune(Q0, dt)
+        Q = Q0.clone()
+        ms, _, _ = timed(Q, torch.empty_like(Q))
+        res[sched] = Q
+        out[sched] = {"value": ws * dof * 5 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "warps": warps}
+    out["tile_shapes"] = {f"{('hex', 'prism', 'pyramid', 'tet')[t]}/N{N}": w for t, N, w in mesh.tile_shapes()}
+    Qp = Q0.clone()
+    _, el_ms, fa_ms = timed(Qp, torch.empty_like(Qp), profile=True)
+    el_flops = sum(split_hex_flops(N_DEG) if int(t) == 0 else element_flops(int(t), N_DEG) for t in box.etype)
+    el_bytes = sum(element_bytes(int(t), N_DEG) for t in box.etype)
+    props = torch.cuda.get_device_properties(dev)
+    clk = CLOCKS.summary(["split form"])
+    peak = props.multi_processor_count * 2 * 2 * (clk.get("sm_max_mhz") or 2070.0) / 1e6
+    tflops = el_flops * 5 * steps / (el_ms * 1e-3) / 1e12
+    out["value"] = out["balanced"]["value"]
+    out["balanced_over_naive"] = out["balanced"]["value"] / out["naive"]["value"]
+    out["split_over_weak"] = out["balanced"]["value"] / weak_value if weak_value else None
+    out["schedulers_bitwise_equal"] = bool(torch.equal(res["naive"], res["balanced"]))
+    out["finite"] = bool(torch.isfinite(res["balanced"]).all())
+    out["element_ms_per_step"] = el_ms / steps
+    out["face_ms_per_step"] = fa_ms / steps
+    out["roofline"] = {"bound": "alu", "kernel": "element kernel (balanced, fused), hexahedra in the split form",
+                       "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                       "algorithmic_flops_per_stage": el_flops, "algorithmic_bytes_per_stage": el_bytes,
+                       "hex_flops_split": split_hex_flops(N_DEG), "hex_flops_weak": element_flops(0, N_DEG),
+                       "model": "alg_counts.json split_hex (every unordered node pair and every (face state, "
+                                "node) pair of a line once, as the kernel evaluates them)"}
+    ns, imb = mesh.cost_table()
+    out["cost_table_ns_per_elem"] = dict(zip(("hex", "prism", "pyramid", "tet"), [round(x, 1) for x in ns]))
+    out["sm_load_imbalance"] = imb
+    mesh.sync()
+    mesh.close()
+    return out
+
+
 def batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
     """Serving-style batch: all instances advance in one handle (one persistent
     element launch and one face launch per phase, one CUDA graph per step)."""
@@ -1398,6 +1609,14 @@ def main():
                     help="share of the free device memory the kinetic-energy adjoint may keep stage data in")
     ap.add_argument("--curved-steps", type=int, default=100,
                     help="steps of the curved-geometry leg (0 skips it)")
+    ap.add_argument("--partition-steps", type=int, default=20,
+                    help="steps of the partitioned leg (0 skips it)")
+    ap.add_argument("--parts", type=int, default=2,
+                    help="parts of the partitioned leg when one rank runs them all on its GPU")
+    ap.add_argument("--split-steps", type=int, default=50,
+                    help="steps of the split-form leg (0 skips it)")
+    ap.add_argument("--split-only", action="store_true",
+                    help="profiling aid: run the split-form leg only")
     ap.add_argument("--curved-only", action="store_true",
                     help="profiling aid: run the curved-geometry leg only")
     args = ap.parse_args()

@@ -219,6 +219,69 @@ dg_status dg_mesh_check(const dg_mesh_desc* desc, int64_t* counts, double* quad_
 dg_status dg_partition_plan(const dg_mesh_desc* desc, int nparts, const double* type_weight, int64_t* part_of_elem,
                             int64_t* halo_off, int64_t* halo_elems);
 
+/* One part of a partitioned mesh (Sec. 3: each rank owns a contiguous
+ * space-filling-curve segment of the elements and exchanges the traces on
+ * the faces it shares with other ranks every stage).  desc describes the
+ * whole mesh; part_of_elem (host, [n_elems], e.g. from dg_partition_plan)
+ * assigns every caller element to one of nparts parts.  The part mesh holds
+ * the elements of `part` and, as ghosts, every element of another part that
+ * shares a face with one of them; its caller element order is ascending
+ * global caller index (dg_part_elements), so the owner rule and every face
+ * computation match the whole mesh's, and a partitioned run reproduces the
+ * whole mesh's residual and steps bit for bit on the owned elements.  No
+ * element work runs on ghosts: their face traces arrive by the halo exchange
+ * (dg_halo_pack / dg_halo_unpack).  A partition mesh runs the Euler equations
+ * with the balanced or naive scheduler and steps stage by stage
+ * (dg_rk_prime / dg_rk_stage); whole-residual calls (dg_rhs, dg_rk_step,
+ * dg_autotune, the adjoint) return DG_ERR_UNSUPPORTED.  Synchronous. */
+dg_status dg_mesh_create_part(const dg_mesh_desc* desc, const int64_t* part_of_elem, int nparts, int part,
+                              cudaStream_t stream, dg_mesh** out);
+
+/* Host-only (no GPU): the halo plan of part `part` that dg_mesh_create_part
+ * builds -- send_faces / recv_faces (host [nparts]) as dg_halo_counts, and
+ * (host, may be NULL) the faces' global keys, 8 * (global owner element) +
+ * (owner's local face), in send and in receive order (peers ascending, keys
+ * ascending within a peer).  Part q's send keys for part p equal part p's
+ * receive keys from part q, in the same order: the contract that lets ranks
+ * exchange packed blocks without further bookkeeping. */
+dg_status dg_halo_plan(const dg_mesh_desc* desc, const int64_t* part_of_elem, int nparts, int part,
+                       int64_t* send_faces, int64_t* recv_faces, int64_t* send_keys, int64_t* recv_keys);
+
+/* The part's elements: *n_local (host) and, when not NULL, their global
+ * caller indices (host [n_local], ascending) and ghost flags (host
+ * [n_local], 1 for a ghost).  The part's state layouts (dg_set_state etc.)
+ * hold every local element; only owned elements are computed. */
+dg_status dg_part_elements(const dg_mesh* mesh, int64_t* n_local, int64_t* global_of_local, int8_t* is_ghost);
+
+/* Halo sizes: send_faces / recv_faces (host [nparts], may be NULL) the number
+ * of face traces this part sends to / receives from each part, and
+ * *doubles_per_face (may be NULL) = 5 (N+1)^2.  The send buffer holds the
+ * blocks for part 0, then part 1, ...; within a peer the faces are ordered by
+ * their global key (owner element, owner's local face), the order in which
+ * the peer's receive buffer expects them. */
+dg_status dg_halo_counts(const dg_mesh* mesh, int64_t* send_faces, int64_t* recv_faces, int64_t* doubles_per_face);
+
+/* Pack this part's face traces that other parts need into send (device,
+ * [sum send_faces][5 (N+1)^2]); unpack the traces received from other parts
+ * (device, [sum recv_faces][5 (N+1)^2], same peer grouping) into the ghost
+ * side of the shared faces.  Between them the caller moves the blocks (NCCL
+ * send/recv, peer copies, or a device copy when two parts share a GPU).
+ * Asynchronous. */
+dg_status dg_halo_pack(dg_mesh* mesh, double* send, cudaStream_t stream);
+dg_status dg_halo_unpack(dg_mesh* mesh, const double* recv, cudaStream_t stream);
+
+/* Stage-wise LSERK(5,4) for partitioned runs (Sec. 2, Sec. 3).  dg_rk_prime
+ * runs the forward phase of the first stage (state at the points, the
+ * element's face traces, the volume term) on Q_store.  dg_rk_stage(stage =
+ * 0..4) runs the face phase and the backward phase of that stage with the
+ * LSERK update of Q_store and K_store, and -- unless last != 0 -- the forward
+ * phase of the next stage on the new state (the next step's first stage
+ * after stage 4).  One step: prime (first step only), then for every stage:
+ * halo exchange, dg_rk_stage.  Works on any mesh.  Asynchronous. */
+dg_status dg_rk_prime(dg_mesh* mesh, const double* Q_store, cudaStream_t stream);
+dg_status dg_rk_stage(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int stage, int last,
+                      cudaStream_t stream);
+
 /* n_dof = 5 * sum_e nM(type_e, N).  slot_of_elem (host, [n_elems], may be
  * NULL) receives the Hilbert slot of every caller element.  counts (host,
  * [6], may be NULL) receives n_elems, n_faces, and the number of hex, prism,

@@ -13,7 +13,7 @@ import os
 
 from .build import LIB, build as _build
 
-__all__ = ["lib", "DGError", "Mesh", "Batch", "check_mesh", "partition_plan", "FLUX", "SCHED",
+__all__ = ["lib", "DGError", "Mesh", "Batch", "Part", "step_parts", "halo_plan", "check_mesh", "partition_plan", "FLUX", "SCHED",
            "PHYSICS", "GEOMETRY", "load"]
 
 FLUX = {"lf": 0, "roe": 1, "ec": 2}
@@ -67,6 +67,14 @@ _SIGS = {
     "dg_set_scheduler": [_P, ctypes.c_int],
     "dg_set_physics": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
     "dg_set_volume_form": [_P, ctypes.c_int],
+    "dg_mesh_create_part": [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P],
+    "dg_halo_plan": [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P],
+    "dg_part_elements": [_P, _P, _P, _P],
+    "dg_halo_counts": [_P, _P, _P, _P],
+    "dg_halo_pack": [_P, _P, _P],
+    "dg_halo_unpack": [_P, _P, _P],
+    "dg_rk_prime": [_P, _P, _P],
+    "dg_rk_stage": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P],
     "dg_set_adjoint_memory": [_P, ctypes.c_double],
     "dg_set_table_warps": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "dg_tile_shapes": [_P, ctypes.c_int, _P, _P, _P, _P],
@@ -158,6 +166,20 @@ def check_mesh(box, N, geometry="affine"):
     slots = np.zeros(len(keep["etype"]), dtype=np.int64)
     _check(load().dg_mesh_check(ctypes.byref(d), _ptr(counts), _ptr(qp), _ptr(slots)))
     return counts, qp, slots
+
+
+def halo_plan(box, N, part_of_elem, nparts, part, geometry="affine"):
+    """dg_halo_plan (host-only): (send_faces [nparts], recv_faces [nparts],
+    send_keys, recv_keys) of one part."""
+    import numpy as np
+    d, keep = _desc(box, N, geometry=geometry)
+    poe = np.ascontiguousarray(part_of_elem, dtype=np.int64)
+    sf, rf = np.zeros(nparts, dtype=np.int64), np.zeros(nparts, dtype=np.int64)
+    _check(load().dg_halo_plan(ctypes.byref(d), _ptr(poe), int(nparts), int(part), _ptr(sf), _ptr(rf), None, None))
+    sk, rk = np.zeros(max(1, int(sf.sum())), dtype=np.int64), np.zeros(max(1, int(rf.sum())), dtype=np.int64)
+    _check(load().dg_halo_plan(ctypes.byref(d), _ptr(poe), int(nparts), int(part), _ptr(sf), _ptr(rf), _ptr(sk),
+                               _ptr(rk)))
+    return sf, rf, sk[:int(sf.sum())], rk[:int(rf.sum())]
 
 
 def partition_plan(box, N, nparts, type_weight=None, geometry="affine"):
@@ -410,6 +432,72 @@ class Mesh:
 
     def sync(self, stream=None):
         _check(load().dg_sync(self.handle, _stream(stream)))
+
+
+class Part(Mesh):
+    """One part of a partitioned mesh (dg_mesh_create_part): the elements of
+    `part` under part_of_elem plus their ghosts, in ascending global caller
+    index (global_of_local); steps with rk_prime / rk_stage and the halo
+    exchange (halo_pack / halo_unpack)."""
+
+    def __init__(self, box, N, part_of_elem, nparts, part, flux="lf", gamma=1.4, scheduler="balanced",
+                 stream=None, geometry="affine"):
+        import numpy as np
+        self.N = int(N)
+        self.flux = flux
+        self.nparts, self.part = int(nparts), int(part)
+        d, keep = _desc(box, N, flux, gamma, scheduler, 0.1, geometry)
+        poe = np.ascontiguousarray(part_of_elem, dtype=np.int64)
+        h = ctypes.c_void_p()
+        _check(load().dg_mesh_create_part(ctypes.byref(d), _ptr(poe), self.nparts, self.part, _stream(stream),
+                                          ctypes.byref(h)))
+        n = ctypes.c_int64()
+        _check(load().dg_part_elements(h, ctypes.byref(n), None, None))
+        self.global_of_local = np.zeros(n.value, dtype=np.int64)
+        self.is_ghost = np.zeros(n.value, dtype=np.int8)
+        _check(load().dg_part_elements(h, ctypes.byref(n), _ptr(self.global_of_local), _ptr(self.is_ghost)))
+        self._adopt(h, keep["etype"][self.global_of_local].copy())
+        self.points_per_elem = np.full(self.n_elems, (self.N + 1) ** 3, dtype=np.int64)
+        self.send_faces = np.zeros(self.nparts, dtype=np.int64)
+        self.recv_faces = np.zeros(self.nparts, dtype=np.int64)
+        per = ctypes.c_int64()
+        _check(load().dg_halo_counts(h, _ptr(self.send_faces), _ptr(self.recv_faces), ctypes.byref(per)))
+        self.doubles_per_face = per.value
+
+    def halo_buffers(self):
+        """Device send and receive buffers of the halo exchange."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        return (torch.empty(max(1, int(self.send_faces.sum())) * self.doubles_per_face, dtype=torch.float64, device=dev),
+                torch.empty(max(1, int(self.recv_faces.sum())) * self.doubles_per_face, dtype=torch.float64, device=dev))
+
+    def halo_pack(self, send, stream=None):
+        _check(load().dg_halo_pack(self.handle, _ptr(send), _stream(stream)))
+
+    def halo_unpack(self, recv, stream=None):
+        _check(load().dg_halo_unpack(self.handle, _ptr(recv), _stream(stream)))
+
+    def rk_prime(self, Q_store, stream=None):
+        _check(load().dg_rk_prime(self.handle, _ptr(Q_store), _stream(stream)))
+
+    def rk_stage(self, Q_store, K_store, dt, stage, last, stream=None):
+        _check(load().dg_rk_stage(self.handle, _ptr(Q_store), _ptr(K_store), float(dt), int(stage), int(bool(last)),
+                                  _stream(stream)))
+
+
+def step_parts(parts, Qs, Ks, dt, nsteps, exchange):
+    """nsteps LSERK steps of a partitioned mesh: parts[i] advances Qs[i]
+    (storage layout) with register Ks[i]; exchange() moves every part's packed
+    halo blocks into its peers' receive buffers between the forward phase and
+    the face phase of every stage (pack and unpack are done here)."""
+    for step in range(nsteps):
+        if step == 0:
+            for P, Q in zip(parts, Qs):
+                P.rk_prime(Q)
+        for s in range(5):
+            exchange()
+            for P, Q, K in zip(parts, Qs, Ks):
+                P.rk_stage(Q, K, dt, s, last=(s == 4 and step == nsteps - 1))
 
 
 class Batch(Mesh):

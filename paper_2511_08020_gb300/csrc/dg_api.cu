@@ -57,6 +57,15 @@ struct dg_mesh {
   dgh::HostMesh h;
   int flux = 0;
   int split = 0;      // DG_VOLUME_SPLIT: entropy-stable split form on the hexahedra
+  // partition meshes (dg_mesh_create_part): the part's elements (owned and
+  // ghosts, ascending global caller index) and the halo lists: per peer part,
+  // the face-buffer offsets of the owned traces to send and of the ghost
+  // slots to fill, both in the order of the faces' global keys
+  int nparts = 0, part = -1;
+  std::vector<int64_t> global_of_local;
+  std::vector<int64_t> send_count, recv_count, send_off, recv_off;
+  int64_t* d_send_off = nullptr;
+  int64_t* d_recv_off = nullptr;
   double gamma = 1.4;
   int scheduler = DG_SCHED_BALANCED;
   double threshold = 0.1;
@@ -149,8 +158,13 @@ struct dg_mesh {
 
   std::vector<double> static_weights() const {
     std::vector<double> w(dgk::kMaxTabs, 1.0);
-    for (size_t i = 0; i < h.tables.tabs.size() && i < (size_t)dgk::kMaxTabs; ++i)
-      w[i] = dgh::static_cost(h.tables.tabs[i]);
+    for (size_t i = 0; i < h.tables.tabs.size() && i < (size_t)dgk::kMaxTabs; ++i) {
+      const dgk::TypeTab& t = h.tables.tabs[i];
+      w[i] = dgh::static_cost(t);
+      // split form: every coordinate line's node pairs and face pairs, each
+      // a two-point flux of about 100 FP64 operations
+      if (split && t.type == dgk::HEX) w[i] += 3.0 * t.n * t.n * (t.n * (t.n - 1) + 4.0 * t.n) * 100.0;
+    }
     return w;
   }
   double* d_stage = nullptr;
@@ -341,6 +355,8 @@ struct dg_mesh {
     return c;
   }
 
+  bool ghost_slot(int64_t s) const { return !h.slot_ghost.empty() && h.slot_ghost[s]; }
+
   int grid_balanced() const { return num_sms * blocks_per_sm; }
   int grid_ns() const { return num_sms * blocks_per_sm_ns; }
 
@@ -370,7 +386,8 @@ struct dg_mesh {
   cudaError_t build_groups() {
     free_groups();
     std::vector<int64_t> count(h.tables.tabs.size(), 0);
-    for (int64_t s = 0; s < h.n_elems; ++s) ++count[h.slot_tab[s]];
+    for (int64_t s = 0; s < h.n_elems; ++s)
+      if (!ghost_slot(s)) ++count[h.slot_tab[s]];
     for (size_t t = 0; t < h.tables.tabs.size(); ++t) {
       if (!count[t]) continue;
       const int n = h.tables.tabs[t].n, w = tab_wpb[t];
@@ -418,7 +435,7 @@ struct dg_mesh {
       std::vector<int64_t> list;
       for (int t : order)
         for (int64_t s = 0; s < E; ++s)
-          if (h.slot_tab[s] == t) list.push_back(s);
+          if (h.slot_tab[s] == t && !ghost_slot(s)) list.push_back(s);
       const int64_t L = (int64_t)list.size();
       double remaining = 0.0;
       for (int64_t s : list) remaining += tab_weight[h.slot_tab[s]];
@@ -689,6 +706,8 @@ struct dg_mesh {
       for (auto e : pl) cudaEventDestroy(e);
     drop_graphs();
     if (d_rkdyn) cudaFree(d_rkdyn);
+    if (d_send_off) cudaFree(d_send_off);
+    if (d_recv_off) cudaFree(d_recv_off);
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -700,6 +719,10 @@ const char* dg_last_error(void) { return g_err.c_str(); }
 }  // extern "C"
 
 namespace {
+
+// Calls that evaluate a whole residual in one go cannot run on a partition
+// mesh (its ghost traces need the halo exchange between phases).
+bool part_mesh(const dg_mesh* m) { return m && m->nparts > 0; }
 
 dg_status check_desc(const dg_mesh_desc* desc) {
   if (desc->flux != DG_FLUX_LF && desc->flux != DG_FLUX_ROE && desc->flux != DG_FLUX_EC)
@@ -894,6 +917,235 @@ dg_status dg_partition_plan(const dg_mesh_desc* desc, int nparts, const double* 
   return DG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The part mesh of `part` (owned elements and their ghosts, ascending
+// global caller index) and its halo lists, on the host.  A face with one
+// ghost side is sent (the owned side's trace) to, and received (the ghost
+// side's slot) from, the ghost's part; both lists are ordered by (peer,
+// global owner element, owner's local face), an order the peer's lists of
+// the same faces share.
+struct PartPlan {
+  dgh::HostMesh h;
+  std::vector<int64_t> glob, send_count, recv_count, send_off, recv_off, send_key, recv_key;
+};
+
+dg_status plan_part(const dg_mesh_desc* desc, const int64_t* part_of_elem, int nparts, int part, PartPlan* P) {
+  if (!desc || !part_of_elem) return fail(DG_ERR_ARG, "null argument");
+  if (nparts < 1 || part < 0 || part >= nparts) return fail(DG_ERR_ARG, "part must lie in [0, nparts)");
+  dg_status st = check_desc(desc);
+  if (st != DG_OK) return st;
+  const int64_t E = desc->n_elems;
+  for (int64_t e = 0; e < E; ++e)
+    if (part_of_elem[e] < 0 || part_of_elem[e] >= nparts) return fail(DG_ERR_ARG, "part_of_elem out of range");
+  // the whole mesh's faces give the ghosts: every element of another part
+  // that shares a face with an element of this part
+  std::string err;
+  dgh::HostMesh G;
+  int r = dgh::build_mesh(input_of(desc), &G, &err);
+  if (r != 0) return fail((dg_status)r, err);
+  std::vector<uint8_t> keep(E, 0);
+  for (int64_t e = 0; e < E; ++e) keep[e] = part_of_elem[e] == part ? 1 : 0;
+  for (int64_t f = 0; f < G.n_faces; ++f) {
+    const int64_t a = G.face_e0[f], b = G.face_e1[f];
+    if (part_of_elem[a] == part && part_of_elem[b] != part) keep[b] = 2;
+    if (part_of_elem[b] == part && part_of_elem[a] != part) keep[a] = 2;
+  }
+  std::vector<int8_t> type;
+  std::vector<int64_t> off(1, 0), verts;
+  std::vector<uint8_t> ghost;
+  P->glob.clear();
+  for (int64_t e = 0; e < E; ++e) {
+    if (!keep[e]) continue;
+    P->glob.push_back(e);
+    type.push_back(desc->type[e]);
+    for (int64_t k = desc->elem_vert_off[e]; k < desc->elem_vert_off[e + 1]; ++k) verts.push_back(desc->elem_verts[k]);
+    off.push_back((int64_t)verts.size());
+    ghost.push_back(keep[e] == 2 ? 1 : 0);
+  }
+  if (P->glob.empty() || std::find(ghost.begin(), ghost.end(), 0) == ghost.end())
+    return fail(DG_ERR_ARG, "the part owns no element");
+  dgh::MeshInput in = input_of(desc);
+  in.n_elems = (int64_t)P->glob.size();
+  in.type = type.data();
+  in.off = off.data();
+  in.verts = verts.data();
+  in.ghost = ghost.data();
+  r = dgh::build_mesh(in, &P->h, &err);
+  if (r != 0) return fail((dg_status)r, err);
+  const dgh::HostMesh& h = P->h;
+  const int64_t per = 5 * (int64_t)h.n * h.n;
+  struct Entry { int64_t peer, key0, key1, off; };
+  std::vector<Entry> snd, rcv;
+  for (int64_t f = 0; f < h.n_faces; ++f) {
+    const int64_t a = h.face_e0[f], b = h.face_e1[f];
+    const bool ga = ghost[a] != 0, gb = ghost[b] != 0;
+    if (ga == gb) continue;
+    const int own_side = ga ? 1 : 0;
+    const int64_t peer = part_of_elem[P->glob[ga ? a : b]];
+    const int64_t toff = h.faces[f].toff;
+    snd.push_back({peer, P->glob[a], h.face_l0[f], toff + own_side * per});
+    rcv.push_back({peer, P->glob[a], h.face_l0[f], toff + (1 - own_side) * per});
+  }
+  auto by_key = [](const Entry& x, const Entry& y) { return std::tie(x.peer, x.key0, x.key1) < std::tie(y.peer, y.key0, y.key1); };
+  std::sort(snd.begin(), snd.end(), by_key);
+  std::sort(rcv.begin(), rcv.end(), by_key);
+  P->send_count.assign(nparts, 0);
+  P->recv_count.assign(nparts, 0);
+  P->send_off.clear();
+  P->recv_off.clear();
+  P->send_key.clear();
+  P->recv_key.clear();
+  for (const auto& x : snd) {
+    P->send_count[x.peer]++;
+    P->send_off.push_back(x.off);
+    P->send_key.push_back(x.key0 * 8 + x.key1);
+  }
+  for (const auto& x : rcv) {
+    P->recv_count[x.peer]++;
+    P->recv_off.push_back(x.off);
+    P->recv_key.push_back(x.key0 * 8 + x.key1);
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_halo_plan(const dg_mesh_desc* desc, const int64_t* part_of_elem, int nparts, int part,
+                       int64_t* send_faces, int64_t* recv_faces, int64_t* send_keys, int64_t* recv_keys) {
+  if (!send_faces || !recv_faces) return fail(DG_ERR_ARG, "null argument");
+  PartPlan P;
+  dg_status st = plan_part(desc, part_of_elem, nparts, part, &P);
+  if (st != DG_OK) return st;
+  for (int q = 0; q < nparts; ++q) {
+    send_faces[q] = P.send_count[q];
+    recv_faces[q] = P.recv_count[q];
+  }
+  if (send_keys) std::memcpy(send_keys, P.send_key.data(), sizeof(int64_t) * P.send_key.size());
+  if (recv_keys) std::memcpy(recv_keys, P.recv_key.data(), sizeof(int64_t) * P.recv_key.size());
+  return DG_OK;
+}
+
+dg_status dg_mesh_create_part(const dg_mesh_desc* desc, const int64_t* part_of_elem, int nparts, int part,
+                              cudaStream_t stream, dg_mesh** out) {
+  if (!out) return fail(DG_ERR_ARG, "null argument");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) return fail(DG_ERR_CUDA, "no CUDA device available (the library has no CPU path)");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  {
+    PartPlan P;
+    dg_status st = plan_part(desc, part_of_elem, nparts, part, &P);
+    if (st != DG_OK) {
+      delete m;
+      return st;
+    }
+    m->h = std::move(P.h);
+    m->global_of_local = std::move(P.glob);
+    m->send_count = std::move(P.send_count);
+    m->recv_count = std::move(P.recv_count);
+    m->send_off = std::move(P.send_off);
+    m->recv_off = std::move(P.recv_off);
+  }
+  m->nparts = nparts;
+  m->part = part;
+  dg_mesh* made = nullptr;
+  dg_status st = create_device_mesh(m, desc, stream, &made);
+  if (st != DG_OK) return st;
+  if (!made->send_off.empty()) {
+    cudaError_t e = upload(&made->d_send_off, made->send_off);
+    if (e == cudaSuccess) e = upload(&made->d_recv_off, made->recv_off);
+    if (e != cudaSuccess) {
+      made->release();
+      delete made;
+      return cuda_fail(e, "upload halo lists");
+    }
+  }
+  *out = made;
+  return DG_OK;
+}
+
+dg_status dg_part_elements(const dg_mesh* mesh, int64_t* n_local, int64_t* global_of_local, int8_t* is_ghost) {
+  if (!mesh || !n_local) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->nparts == 0) return fail(DG_ERR_ARG, "not a partition mesh");
+  *n_local = (int64_t)mesh->global_of_local.size();
+  for (int64_t e = 0; e < *n_local; ++e) {
+    if (global_of_local) global_of_local[e] = mesh->global_of_local[e];
+    if (is_ghost) is_ghost[e] = (int8_t)mesh->h.slot_ghost[mesh->h.slot_of_elem[e]];
+  }
+  return DG_OK;
+}
+
+dg_status dg_halo_counts(const dg_mesh* mesh, int64_t* send_faces, int64_t* recv_faces, int64_t* doubles_per_face) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (mesh->nparts == 0) return fail(DG_ERR_ARG, "not a partition mesh");
+  for (int p = 0; p < mesh->nparts; ++p) {
+    if (send_faces) send_faces[p] = mesh->send_count[p];
+    if (recv_faces) recv_faces[p] = mesh->recv_count[p];
+  }
+  if (doubles_per_face) *doubles_per_face = 5 * (int64_t)mesh->h.n * mesh->h.n;
+  return DG_OK;
+}
+
+dg_status dg_halo_pack(dg_mesh* mesh, double* send, cudaStream_t stream) {
+  if (!mesh || (!send && !mesh->send_off.empty())) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->nparts == 0) return fail(DG_ERR_ARG, "not a partition mesh");
+  if (mesh->send_off.empty()) return DG_OK;
+  dgk::launch_halo_copy(mesh->d_T, send, mesh->d_send_off, (int64_t)mesh->send_off.size(),
+                        5 * mesh->h.n * mesh->h.n, true, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_halo_unpack(dg_mesh* mesh, const double* recv, cudaStream_t stream) {
+  if (!mesh || (!recv && !mesh->recv_off.empty())) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->nparts == 0) return fail(DG_ERR_ARG, "not a partition mesh");
+  if (mesh->recv_off.empty()) return DG_OK;
+  dgk::launch_halo_copy(recv, mesh->d_T, mesh->d_recv_off, (int64_t)mesh->recv_off.size(),
+                        5 * mesh->h.n * mesh->h.n, false, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_rk_prime(dg_mesh* mesh, const double* Q_store, cudaStream_t stream) {
+  if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "stage-wise stepping covers the Euler equations");
+  DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
+  mesh->parity = 0;
+  mesh->begin_timing(1);
+  dgk::StageArgs a{Q_store, const_cast<double*>(Q_store), nullptr, 0.0, 0.0, 0.0};
+  mesh->element_phase(dgk::kFwd, a, stream);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_rk_stage(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int stage, int last,
+                      cudaStream_t stream) {
+  if (!mesh || !Q_store || !K_store) return fail(DG_ERR_ARG, "null argument");
+  if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must lie in 0..4");
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
+  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "stage-wise stepping covers the Euler equations");
+  DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
+  mesh->parity = 0;
+  mesh->begin_timing(1);
+  mesh->face_phase(stream);
+  dgk::StageArgs a{Q_store, Q_store, K_store, kLsA[stage], kLsB[stage], dt};
+  if (mesh->fused) {
+    mesh->element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, stream);
+  } else {
+    mesh->element_phase(dgk::kBwdRk, a, stream);
+    if (!last) mesh->element_phase(dgk::kFwd, a, stream);
+  }
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 dg_status dg_mesh_destroy(dg_mesh* mesh) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   cudaDeviceSynchronize();
@@ -973,6 +1225,7 @@ dg_status dg_eval_nodal(dg_mesh* mesh, const double* Q_store, double* u_points, 
 
 dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStream_t stream) {
   if (!mesh || !Q_store || !R_store) return fail(DG_ERR_ARG, "null argument");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "a partition mesh steps with dg_rk_prime / dg_rk_stage and the halo exchange");
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
   mesh->begin_timing(1);
@@ -986,6 +1239,7 @@ dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStre
 
 dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps, cudaStream_t stream) {
   if (!mesh || !Q_store || !K_store) return fail(DG_ERR_ARG, "null argument");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "a partition mesh steps with dg_rk_prime / dg_rk_stage and the halo exchange");
   if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return DG_OK;
   if (!(std::isfinite(dt))) return fail(DG_ERR_ARG, "dt must be finite");
@@ -1078,6 +1332,7 @@ dg_status dg_rebalance_stats(const dg_mesh* mesh, int64_t* checks, int64_t* reba
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers whole meshes");
   if (mesh->split || mesh->flux == DG_FLUX_EC)
     return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
   DG_CUDA(mesh->ensure_adjoint(0));
@@ -1122,6 +1377,7 @@ dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double*
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
   if (mesh->split || mesh->flux == DG_FLUX_EC)
     return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers whole meshes");
   if (mesh->ns)
     return fail(DG_ERR_UNSUPPORTED, "dg_rhs_vjp_noalloc covers the Euler equations (the viscous adjoint needs "
                                     "workspace that dg_rhs_vjp allocates); use dg_rhs_vjp");
@@ -1197,6 +1453,7 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
 dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
                       double dt) {
   if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers whole meshes");
   if (mesh->split || mesh->flux == DG_FLUX_EC)
     return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
   if (nsteps < 0 || ckpt_every < 0) return fail(DG_ERR_ARG, "nsteps and ckpt_every must be >= 0");
@@ -1284,6 +1541,7 @@ dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double
 dg_status dg_rk_step_checkpointed(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps,
                                   int ckpt_every, double* ckpt_store, cudaStream_t stream) {
   if (!mesh || !Q_store || !K_store || !ckpt_store) return fail(DG_ERR_ARG, "null argument");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "a partition mesh steps with dg_rk_prime / dg_rk_stage and the halo exchange");
   if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   const size_t bytes = sizeof(double) * (size_t)mesh->h.n_dof;
@@ -1327,7 +1585,12 @@ dg_status dg_set_volume_form(dg_mesh* mesh, int form) {
     if (mesh->h.n_curved > 0) return fail(DG_ERR_UNSUPPORTED, "the split form covers affine meshes");
   }
   mesh->split = form == DG_VOLUME_SPLIT;
-  if (mesh->split && mesh->wpb < 1) mesh->wpb = 1;
+  {
+    // the modelled chunk weights of the new volume form (dg_rebalance
+    // replaces them with measured ones)
+    const std::vector<double> w0 = mesh->static_weights();
+    for (int t = 0; t < dgk::kMaxTabs; ++t) mesh->weight[t] = w0[t];
+  }
   DG_CUDA(mesh->build_groups());
   DG_CUDA(mesh->build_static_chunks());
   mesh->drop_graphs();
@@ -1337,6 +1600,8 @@ dg_status dg_set_volume_form(dg_mesh* mesh, int form) {
 dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
+  if (physics == DG_NAVIER_STOKES && part_mesh(mesh))
+    return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes needs a second halo exchange per stage; partition meshes run Euler");
   if (physics == DG_NAVIER_STOKES && (mesh->split || mesh->flux == DG_FLUX_EC))
     return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes runs with the weak form and the LF or Roe flux");
   if (physics == DG_NAVIER_STOKES) {
@@ -1361,6 +1626,8 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
 dg_status dg_set_scheduler(dg_mesh* mesh, int scheduler) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (scheduler < DG_SCHED_BALANCED || scheduler > DG_SCHED_WEIGHTED) return fail(DG_ERR_ARG, "unknown scheduler");
+  if (part_mesh(mesh) && (scheduler == DG_SCHED_STATIC || scheduler == DG_SCHED_WEIGHTED))
+    return fail(DG_ERR_UNSUPPORTED, "a partition mesh runs the balanced or naive scheduler");
   mesh->scheduler = scheduler;
   return DG_OK;
 }
@@ -1523,6 +1790,7 @@ dg_status apply_table_warps(dg_mesh* mesh, int uniform, const std::vector<int>& 
 dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best_warps, double* ms_per_step,
                       cudaStream_t stream) {
   if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the autotuner times dg_rk_step, which a partition mesh cannot run");
   const char* cache = std::getenv("DG_AUTOTUNE_CACHE");
   const std::string key = autotune_key(mesh);
   const int ntab = (int)mesh->h.tables.tabs.size();

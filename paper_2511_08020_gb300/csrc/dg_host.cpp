@@ -896,7 +896,17 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
     M.h_total = hs;
   }
   for (int t = 0; t < 4; ++t) M.type_slots[t].clear();
-  for (int64_t e = 0; e < E; ++e) M.type_slots[(int)in.type[e]].push_back(M.slot_of_elem[e]);
+  M.slot_ghost.assign(E, 0);
+  M.n_ghost = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    if (in.ghost && in.ghost[e]) {
+      M.slot_ghost[M.slot_of_elem[e]] = 1;
+      M.n_ghost++;
+      continue;
+    }
+    M.type_slots[(int)in.type[e]].push_back(M.slot_of_elem[e]);
+  }
+  if (M.n_ghost == E) { *err = "a partition mesh needs at least one owned element"; return -1; }
 
   // ---- curved elements: pointwise metric, J, 1/J and (prism, pyramid) the
   // dense inverse mass matrix of Algorithm 1, per slot
@@ -983,9 +993,12 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   struct FaceTmp { int64_t e0, e1; int l0, l1; };
   std::vector<FaceTmp> ftmp;
   ftmp.reserve(table.size());
+  auto is_ghost = [&](int64_t e) { return in.ghost != nullptr && in.ghost[e] != 0; };
   for (auto& kv : table) {
+    if (kv.second.size() == 1 && is_ghost(kv.second[0].e)) continue;     // a ghost's face towards other parts
     if (kv.second.size() != 2) { *err = "a face does not have exactly one partner (mesh must be conforming and periodic)"; return -2; }
     Side a = kv.second[0], b = kv.second[1];
+    if (is_ghost(a.e) && is_ghost(b.e)) continue;                         // between two ghosts: not needed
     if (std::tie(b.e, b.lf) < std::tie(a.e, a.lf)) std::swap(a, b);  // owner: smaller caller index
     ftmp.push_back({a.e, b.e, a.lf, b.lf});
   }
@@ -999,6 +1012,16 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
   if (F >= ((int64_t)1 << 31)) { *err = "too many faces for 32-bit face-block indices"; return -7; }
   M.n_faces = F;
   M.faces.resize(F);
+  M.face_e0.resize(F);
+  M.face_e1.resize(F);
+  M.face_l0.resize(F);
+  M.face_l1.resize(F);
+  for (int64_t f = 0; f < F; ++f) {
+    M.face_e0[f] = ftmp[f].e0;
+    M.face_e1[f] = ftmp[f].e1;
+    M.face_l0[f] = (int8_t)ftmp[f].l0;
+    M.face_l1[f] = (int8_t)ftmp[f].l1;
+  }
   M.slot_ftoff.assign((size_t)E * 6, -1);
   M.slot_fnrm.assign((size_t)E * 18, 0.0);
   M.perms.clear();
@@ -1225,9 +1248,11 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
       }
     }
   }
-  for (int64_t s = 0; s < E; ++s)
+  for (int64_t s = 0; s < E; ++s) {
+    if (M.slot_ghost[s]) continue;     // a ghost's faces towards other parts are not in this mesh
     for (int lf = 0; lf < kNumFaces[M.slot_type[s]]; ++lf)
       if (M.slot_ftoff[(size_t)s * 6 + lf] < 0) { *err = "internal: unassigned face"; return -1; }
+  }
   // face blocks of up to 32 faces (uniform n)
   M.face_blocks.clear();
   for (int64_t f = 0; f < F; f += 32) {

@@ -48,6 +48,11 @@ struct MeshInput {
   const double* period;
   int N;
   int geometry = 0;   // 0: affine elements only; 1: vertex-interpolated (curved) maps allowed
+  // partition meshes: per element 1 for a ghost (a neighbour owned by another
+  // part: its face traces arrive by the halo exchange, no element work runs
+  // on it); a face with one ghost side and no partner, or with two ghost
+  // sides, is dropped.  Null: no ghosts.
+  const uint8_t* ghost = nullptr;
 };
 
 struct HostMesh {
@@ -91,8 +96,14 @@ struct HostMesh {
   std::vector<int16_t> perms;                // [nperm][2][n^2]: perm then inverse
   std::vector<double> dense;                 // [ndense][n^2][n^2]
   int n_perm = 0, n_dense = 0;
-  // per-type slot lists in caller order (naive scheduler)
+  // per-type slot lists in caller order (naive scheduler; ghosts excluded)
   std::vector<int64_t> type_slots[4];
+  // partition meshes: 1 for a ghost slot (no element work), and the count
+  std::vector<uint8_t> slot_ghost;
+  int64_t n_ghost = 0;
+  // per face, the two sides' caller elements and local faces (owner first)
+  std::vector<int64_t> face_e0, face_e1;
+  std::vector<int8_t> face_l0, face_l1;
   // physical quadrature points, caller order [n_elems][n^3][3]
   std::vector<double> quad_xyz;
   std::vector<double> x1d, w1d;

@@ -1,4 +1,5 @@
 // Kernels of the modal DG hot path; see dg_kernels.cuh for the phase layout.
+#include <algorithm>
 #include <cstdio>
 
 #include "dg_kernels.cuh"
@@ -184,25 +185,6 @@ __device__ __forceinline__ double ln_mean(double a, double b, double la, double 
   return d / (la - lb);
 }
 
-// 1 / ln_mean(a, b): (2/(a + b)) artanh(f)/f = (2/(a + b)) sum_k u^k/(2k+1)
-// for u < 1e-2 (through u^7), else (ln a - ln b)/(a - b).
-__device__ __forceinline__ double inv_ln_mean(double a, double b, double la, double lb) {
-  const double d = a - b, sm = a + b;
-  if (d * d < 1e-2 * sm * sm) {
-    const double is = 1.0 / sm, f = d * is, u = f * f;
-    double h = 1.0 / 15.0;
-    h = fma(h, u, 1.0 / 13.0);
-    h = fma(h, u, 1.0 / 11.0);
-    h = fma(h, u, 1.0 / 9.0);
-    h = fma(h, u, 1.0 / 7.0);
-    h = fma(h, u, 1.0 / 5.0);
-    h = fma(h, u, 1.0 / 3.0);
-    h = fma(h, u, 1.0);
-    return 2.0 * is * h;
-  }
-  return (la - lb) / d;
-}
-
 // Chandrashekar's two-point flux F#(L, R) contracted with m:
 //   F_rho = rho_ln (u_bar . m),  F_mom = p_hat m + u_bar F_rho,
 //   F_E = (1/(2 (gamma-1) beta_ln) - |u|^2_bar/2) F_rho + u_bar . F_mom,
@@ -210,9 +192,27 @@ __device__ __forceinline__ double inv_ln_mean(double a, double b, double la, dou
 __device__ __forceinline__ void two_point_flux(const double* L, int sl, const double* R, int sr, const double* m,
                                                double igm1, double* F) {
   const double rho_ln = ln_mean(L[0], R[0], L[5 * sl], R[5 * sr]);
-  const double ib_ln = inv_ln_mean(L[4 * sl], R[4 * sr], L[6 * sl], R[6 * sr]);
+  // beta: one reciprocal of beta_L + beta_R serves p_hat and the series
+  // branch of 1/beta_ln
+  const double bL = L[4 * sl], bR = R[4 * sr];
+  const double db = bL - bR, sb = bL + bR, isb = 1.0 / sb;
+  double ib_ln;
+  if (db * db < 1e-2 * sb * sb) {
+    const double f = db * isb, u2 = f * f;
+    double h = 1.0 / 15.0;
+    h = fma(h, u2, 1.0 / 13.0);
+    h = fma(h, u2, 1.0 / 11.0);
+    h = fma(h, u2, 1.0 / 9.0);
+    h = fma(h, u2, 1.0 / 7.0);
+    h = fma(h, u2, 1.0 / 5.0);
+    h = fma(h, u2, 1.0 / 3.0);
+    h = fma(h, u2, 1.0);
+    ib_ln = 2.0 * isb * h;
+  } else {
+    ib_ln = (L[6 * sl] - R[6 * sr]) / db;
+  }
   const double u = 0.5 * (L[sl] + R[sr]), v = 0.5 * (L[2 * sl] + R[2 * sr]), w = 0.5 * (L[3 * sl] + R[3 * sr]);
-  const double p_hat = 0.5 * (L[0] + R[0]) / (L[4 * sl] + R[4 * sr]);
+  const double p_hat = 0.5 * (L[0] + R[0]) * isb;
   const double q2 = 0.5 * (L[7 * sl] + R[7 * sr]);
   const double F0 = rho_ln * fma(u, m[0], fma(v, m[1], w * m[2]));
   F[0] = F0;
@@ -903,9 +903,13 @@ __device__ __forceinline__ void point_metric(int type, const double* wa, const d
 // with w_perp the product of the two other directions' weights.  For a
 // central F# this is the weak form's H (sum_l D_l^T G_l).  The face states
 // u~ are this element's traces (the face kernel takes the Riemann flux on
-// them).  sQ lives at the start of bufG; workspace: bufA [5 nQ] (nodal state,
-// then entropy variables), bufG: [kTP][nQ] two-point quantities, [kTP][6 n^2]
-// of the face states, [3][n^2][2][5] face sums.
+// them).  Every unordered node pair and every (face state, node) pair of a
+// line is evaluated once per direction (F# is symmetric) into shared memory,
+// then every node sums its line's terms.  sQ lives at the start of bufG;
+// workspace: bufA [5 nQ] (nodal state, then entropy variables, then the
+// accumulated H), bufG: [kTP][nQ] two-point quantities, [kTP][6 n^2] of the
+// face states, then one direction's [n^2][n(n-1)/2][5] pair fluxes and
+// [n^2][2][n][5] face-state fluxes.
 __device__ __noinline__ void element_forward_split(const Ctx& c, const TypeTab& T, int64_t s, double* bufA,
                                                    double* bufG, int lane) {
   const int n = T.n, nQ = T.nQ, n2 = n * n, nF = 6 * n2;
@@ -955,6 +959,9 @@ __device__ __noinline__ void element_forward_split(const Ctx& c, const TypeTab& 
   const double* S = dp + T.sbp;
   const double* w1 = dp + T.w1;
   const double* E = dp + T.ext;
+  const int np = n * (n - 1) / 2;         // unordered node pairs of a line
+  double* Fp = Gs;                        // [n^2 lines][np][5] pair fluxes of one direction
+  double* Ff = Fp + (size_t)n2 * np * 5;  // [n^2 lines][2 ends][n][5] face-state fluxes of one direction
   // the local face at the end `end` of coordinate l, and the index of a face
   // point from the two other coordinates' indices (x1 < x2 by coordinate)
   auto face_of = [&](int l, int end) {
@@ -969,65 +976,84 @@ __device__ __noinline__ void element_forward_split(const Ctx& c, const TypeTab& 
     const int ia = d.alpha == o1 ? x1 : x2, ib = d.beta == o1 ? x1 : x2;
     return lf * n2 + ia + ib * n;
   };
-  // face sums G[l][line][end] = sum_j E_end,j F#_l(u~_end, u_j)
-  for (int t = lane; t < 6 * n2; t += blockDim.x) {
-    const int l = t / (2 * n2), rem = t - l * 2 * n2, line = rem >> 1, end = rem & 1;
-    const int x1 = line / n, x2 = line - x1 * n;
-    const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;
-    const int st[3] = {n2, n, 1};
-    const int base = x1 * st[o1] + x2 * st[o2];
-    const int fp = face_point(face_of(l, end), l, x1, x2);
-    const double m[3] = {g.Jg[3 * l], g.Jg[3 * l + 1], g.Jg[3 * l + 2]};
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (int j = 0; j < n; ++j) {
-      double F[5];
-      two_point_flux(Pf + fp, nF, P + base + j * st[l], nQ, m, igm1, F);
-      const double ej = E[end * n + j];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) acc[k] = fma(ej, F[k], acc[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) Gs[t * 5 + k] = acc[k];
-  }
-  __syncthreads();
-  // per node: the three directions' line terms
-  double* H = c.H + c.slot_hoff[s];
-  for (int q = lane; q < nQ; q += blockDim.x) {
-    const int idx[3] = {q / n2, (q / n) % n, q % n};
-    const int st[3] = {n2, n, 1};
-    double h[5] = {0, 0, 0, 0, 0};
+  // H accumulates in bufA (the entropy variables are no longer needed)
+  for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = 0.0;
+  const int st[3] = {n2, n, 1};
 #pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-      const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;
+  for (int l = 0; l < 3; ++l) {
+    const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;
+    const double m[3] = {g.Jg[3 * l], g.Jg[3 * l + 1], g.Jg[3 * l + 2]};
+    const int lf_end[2] = {face_of(l, 0), face_of(l, 1)};
+    // every unordered node pair and every (face state, node) pair of every
+    // line of this direction once (F# is symmetric)
+    const int tasks = n2 * (np + 2 * n);
+    for (int t = lane; t < tasks; t += blockDim.x) {
+      double F[5];
+      int line, k;
+      if (t < n2 * np) {
+        line = t / np;
+        k = t - line * np;
+        int i = 0, kk = k;
+        while (kk >= n - 1 - i) {
+          kk -= n - 1 - i;
+          ++i;
+        }
+        const int j = i + 1 + kk;
+        const int x1 = line / n, x2 = line - x1 * n;
+        const int base = x1 * st[o1] + x2 * st[o2];
+        two_point_flux(P + base + i * st[l], nQ, P + base + j * st[l], nQ, m, igm1, F);
+        double* out = Fp + ((size_t)line * np + k) * 5;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) out[v] = F[v];
+      } else {
+        const int u = t - n2 * np;
+        line = u / (2 * n);
+        const int rem = u - line * 2 * n, end = rem / n, j = rem - end * n;
+        const int x1 = line / n, x2 = line - x1 * n;
+        const int base = x1 * st[o1] + x2 * st[o2];
+        two_point_flux(Pf + face_point(lf_end[end], l, x1, x2), nF, P + base + j * st[l], nQ, m, igm1, F);
+        double* out = Ff + (((size_t)line * 2 + end) * n + j) * 5;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) out[v] = F[v];
+      }
+    }
+    __syncthreads();
+    // per node: the line's terms of this direction
+    for (int q = lane; q < nQ; q += blockDim.x) {
+      const int idx[3] = {q / n2, (q / n) % n, q % n};
       const int x1 = idx[o1], x2 = idx[o2], ii = idx[l];
       const int line = x1 * n + x2;
-      const int base = q - ii * st[l];
-      const double m[3] = {g.Jg[3 * l], g.Jg[3 * l + 1], g.Jg[3 * l + 2]};
+      const double* Fl = Fp + (size_t)line * np * 5;
       double r[5] = {0, 0, 0, 0, 0};
       for (int j = 0; j < n; ++j) {
         if (j == ii) continue;
-        double F[5];
-        two_point_flux(P + q, nQ, P + base + j * st[l], nQ, m, igm1, F);
+        const int i0 = ii < j ? ii : j, j0 = ii < j ? j : ii;
+        const double* F = Fl + (i0 * (2 * n - i0 - 1) / 2 + (j0 - i0 - 1)) * 5;
         const double sij = -S[ii * n + j];
 #pragma unroll
         for (int k = 0; k < 5; ++k) r[k] = fma(sij, F[k], r[k]);
       }
 #pragma unroll
       for (int end = 0; end < 2; ++end) {
-        const double se = (end ? 1.0 : -1.0) * E[end * n + ii];
-        double F[5];
-        two_point_flux(P + q, nQ, Pf + face_point(face_of(l, end), l, x1, x2), nF, m, igm1, F);
-        const double* Gl = Gs + ((l * n2 + line) * 2 + end) * 5;
+        const double* Fe = Ff + ((size_t)line * 2 + end) * n * 5;
+        double G[5] = {0, 0, 0, 0, 0};
+        for (int j = 0; j < n; ++j) {
+          const double ej = E[end * n + j];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) r[k] = fma(se, Gl[k] - F[k], r[k]);
+          for (int k = 0; k < 5; ++k) G[k] = fma(ej, Fe[j * 5 + k], G[k]);
+        }
+        const double se = (end ? 1.0 : -1.0) * E[end * n + ii];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = fma(se, G[k] - Fe[ii * 5 + k], r[k]);
       }
       const double wp = w1[x1] * w1[x2];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) h[k] = fma(wp, r[k], h[k]);
+      for (int k = 0; k < 5; ++k) bufA[k * nQ + q] = fma(wp, r[k], bufA[k * nQ + q]);
     }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) H[k * nQ + q] = h[k];
+    __syncthreads();
   }
+  double* H = c.H + c.slot_hoff[s];
+  for (int w = lane; w < 5 * nQ; w += blockDim.x) H[w] = bufA[w];
   __syncthreads();
 }
 
@@ -2588,6 +2614,20 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
 }
 
 // Storage <-> caller layout copies (warp per element).
+// Halo exchange of a partition mesh: copies whole face-side trace blocks of
+// `per` doubles between the face buffer at the listed offsets and a packed
+// buffer (pack: buffer block k <- T[off[k]]; unpack: T[off[k]] <- block k).
+__global__ void halo_copy_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                 const int64_t* __restrict__ off, int64_t count, int per, int pack) {
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+    const int64_t o = off[k];
+    for (int w = threadIdx.x; w < per; w += blockDim.x) {
+      if (pack) dst[k * per + w] = src[o + w];
+      else dst[o + w] = src[k * per + w];
+    }
+  }
+}
+
 __global__ void rk_params_kernel(RkDyn* d, double* Q, double* K, double dt) {
   d->Q = Q;
   d->K = K;
@@ -2614,8 +2654,10 @@ int element_launch_smem_bytes(int nQmax, int wpb, bool split) {
   if (!split) return b;
   int n = 1;
   while (n * n * n < nQmax) ++n;
-  // bufA [5 nQ] + two-point quantities [kTP][nQ] + face states [kTP][6 n^2] + face sums [3][n^2][2][5]
-  const int sb = (5 * nQmax + kTP * nQmax + kTP * 6 * n * n + 30 * n * n) * (int)sizeof(double);
+  // bufA [5 nQ] + two-point quantities [kTP][nQ] + face states [kTP][6 n^2]
+  // + one direction's pair fluxes [n^2][n(n-1)/2][5] and face-state fluxes [n^2][2 n][5]
+  const int sb = (5 * nQmax + kTP * nQmax + kTP * 6 * n * n + n * n * (n * (n - 1) / 2) * 5 + n * n * 2 * n * 5) *
+                 (int)sizeof(double);
   return b > sb ? b : sb;
 }
 int face_block_threads(int n) { return 32 * n; }
@@ -2792,6 +2834,13 @@ void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
   int bytes = 32 * 5 * n * n * (int)sizeof(double);
   if (c.fgeo) face_kernel<true><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
   else face_kernel<false><<<(unsigned)nblocks, face_block_threads(n), bytes, st>>>(c);
+}
+
+void launch_halo_copy(const double* src, double* dst, const int64_t* off, int64_t count, int per, bool pack,
+                      cudaStream_t st) {
+  if (count <= 0) return;
+  const unsigned blocks = (unsigned)std::min<int64_t>(count, 65535);
+  halo_copy_kernel<<<blocks, 128, 0, st>>>(src, dst, off, count, per, pack ? 1 : 0);
 }
 
 void launch_rk_params(RkDyn* d, double* Q, double* K, double dt, cudaStream_t st) {

@@ -130,6 +130,79 @@ def kernel_roe(UL, UR, n, wS, gamma):
     return [wS * (0.5 * (FL[v] + FR[v]) - 0.5 * D[v]) for v in range(5)]
 
 
+def log(a):
+    return a.sqrt()          # one flop, like a square root
+
+
+exp = log
+
+
+def kernel_two_point_state(U, gm1):
+    """The element kernel's two-point quantities of a state (split form)."""
+    r = U[0]
+    ri = 1.0 / r
+    u, v, w = U[1] * ri, U[2] * ri, U[3] * ri
+    q2 = fma(u, u, fma(v, v, w * w))
+    p = gm1 * fma(-0.5 * r, q2, U[4])
+    b = 0.5 * r / p
+    return [r, u, v, w, b, log(r), log(b), q2]
+
+
+def kernel_ln_mean_series(a, b):
+    """The series branch of the logarithmic mean: the branch test,
+    f = d/(a + b), u = f^2 and the degree-8 polynomial."""
+    d, sm = a - b, a + b
+    (d * d, 1e-2 * sm * sm)         # the branch test (a comparison)
+    f = d / sm
+    u = f * f
+    g = Op()
+    for _ in range(8):
+        g = fma(g, u, Op())
+    return 0.5 * sm * g
+
+
+def kernel_two_point_flux(L, R, m, igm1):
+    """The kernels' Chandrashekar flux F#(L, R).m from two-point quantities
+    (series branch of both logarithmic means; one reciprocal of
+    beta_L + beta_R serves 1/beta_ln and p_hat)."""
+    rho_ln = kernel_ln_mean_series(L[0], R[0])
+    db, sb = L[4] - R[4], L[4] + R[4]
+    isb = 1.0 / sb
+    (db * db, 1e-2 * sb * sb)         # the branch test (a comparison)
+    u2 = (db * isb) * (db * isb)
+    h = Op()
+    for _ in range(7):
+        h = fma(h, u2, Op())
+    ib_ln = 2.0 * isb * h
+    u, v, w = 0.5 * (L[1] + R[1]), 0.5 * (L[2] + R[2]), 0.5 * (L[3] + R[3])
+    p_hat = 0.5 * (L[0] + R[0]) * isb
+    q2 = 0.5 * (L[7] + R[7])
+    F0 = rho_ln * fma(u, m[0], fma(v, m[1], w * m[2]))
+    F = [F0, fma(p_hat, m[0], u * F0), fma(p_hat, m[1], v * F0), fma(p_hat, m[2], w * F0)]
+    F.append(fma(fma(0.5 * igm1, ib_ln, -0.5 * q2), F0, fma(u, F[1], fma(v, F[2], w * F[3]))))
+    return F
+
+
+def kernel_entropy_variables(P, gamma, igm1):
+    lnp = P[5] - 0.6931471805599453 - P[6]
+    s = lnp - gamma * P[5]
+    b2 = 2.0 * P[4]
+    return [fma(gamma - s, igm1, -P[4] * P[7]), b2 * P[1], b2 * P[2], b2 * P[3], -b2]
+
+
+def kernel_from_entropy_variables(v, gamma, igm1):
+    b = -0.5 * v[4]
+    iv4 = 1.0 / v[4]
+    u, vv, w = -v[1] * iv4, -v[2] * iv4, -v[3] * iv4
+    q2 = fma(u, u, fma(vv, vv, w * w))
+    s = gamma - (gamma - 1.0) * fma(b, q2, v[0])
+    lb = log(b)
+    lr = -(s + 0.6931471805599453 + lb) * igm1
+    r = exp(lr)
+    p = 0.5 * r / b
+    return [r, r * u, r * vv, r * w, fma(p, igm1, 0.5 * r * q2)], [r, u, vv, w, b, lr, lb, q2]
+
+
 def derived_counts():
     from oracle import euler
     out = {
@@ -143,6 +216,11 @@ def derived_counts():
     # metric, per point: 3 x 5 outputs, each 3 products and 2 sums
     out["contravariant_transform_per_point"] = 3 * 5 * (3 + 2)
     out["f_F_per_point"] = out["oracle_euler_flux_per_point"] + out["contravariant_transform_per_point"]
+    # split form (hexahedra), the kernels' arrangement; ln and exp count one flop
+    out["split_two_point_state"] = counted(kernel_two_point_state, list(ops(5)), Op())
+    out["split_two_point_flux"] = counted(kernel_two_point_flux, list(ops(8)), list(ops(8)), list(ops(3)), Op())
+    out["split_entropy_variables"] = counted(kernel_entropy_variables, list(ops(8)), Op(), Op())
+    out["split_from_entropy_variables"] = counted(kernel_from_entropy_variables, list(ops(5)), Op(), Op())
     return out
 
 

@@ -5,7 +5,9 @@ elements (the oracle evaluates only the sampled elements and what they read):
   * the 64-instance serving batch (N from 2 to 5, sizes 4^3 to 20^3), three
     instances (the smallest, a middle one, the largest) checked;
   * the 12^3 Kuhn tetrahedral mesh at N = 3 and N = 5 (residual, and the
-    adjoint of 20 steps with checkpoints every 5 against central differences).
+    adjoint of 20 steps with checkpoints every 5 against central differences;
+    at N = 3 also the dot test against the oracle's complex-step derivative
+    through the same 20 steps).
 
 Each runs in the launch configuration of bench.py: balanced scheduler with
 the autotuner's tile shapes.  The state is the TGV with the seeded smooth
@@ -137,3 +139,34 @@ def test_kuhn_12cube_adjoint_central_differences(dg, N):
     fd = w @ (run(Qh + h * v) - run(Qh - h * v)) / (2 * h)
     ad = v @ mesh.get_state(mesh.rk_vjp(Q0, dt, K, 5, mesh.set_state(w)))
     assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
+
+
+def test_kuhn_12cube_dot_test_K20(dg):
+    """<J v, w> = <v, J^T w> through K = 20 steps (checkpoints every 5) on the
+    12^3 Kuhn tetrahedral mesh at N = 3: J^T w from dg_rk_vjp, J v from the
+    oracle's complex-step derivative Im Q_K(Q_0 + i h v)/h (h = 1e-30, exact
+    to rounding) through the same 20 steps, the oracle's residual spread over
+    the host's cores; bar 1e-11 relative.  (A finite difference cannot reach
+    this bar: the LF wave-speed maximum and |u.n| have kinks that a
+    perturbation crosses.)"""
+    from oracle_pool import PooledOracle
+    N = 3
+    box = di.box_mesh(12, "kuhn", seed=3)
+    mesh = dg.Mesh(box, N)
+    vals = point_values(mesh.quad_points(), box.n_elems, N, lambda x: di.perturbed_tgv_state(x, seed=3))
+    Q0 = mesh.project(torch.from_numpy(vals).cuda())
+    Qh = mesh.get_state(Q0)
+    nM = (N + 1) * (N + 2) * (N + 3) // 6
+    scale = np.abs(Qh.reshape(-1, 5, nM)).max(axis=(0, 2))
+    v = (di.random_vector(Qh.size, seed=43).reshape(-1, 5, nM) * scale[None, :, None]).reshape(-1)
+    w = di.random_vector(Qh.size, seed=44)
+    dt, K, h = 2e-4, 20, 1e-30
+    rhs = v @ mesh.get_state(mesh.rk_vjp(Q0, dt, K, 5, mesh.set_state(w)))
+    mesh.sync()
+    pool = PooledOracle(box, N, flux="lf")
+    try:
+        jv = pool.run(Qh + 1j * h * v, dt, K).imag / h
+    finally:
+        pool.close()
+    lhs = w @ jv
+    assert abs(lhs - rhs) < 1e-11 * abs(rhs), (lhs, rhs, abs(lhs - rhs) / abs(rhs))

@@ -9,6 +9,9 @@ partitioned run would follow, checked without a GPU):
     oracle; gathered, the residual equals the single-domain one bit for bit
     (the halo holds every state a rank's elements need -- any other entry is
     NaN and would poison the result);
+  * the trace-exchange plan of the device path (dg_halo_plan): the face keys
+    each rank packs for a peer arrive in exactly the order in which the peer
+    unpacks them;
   * the in-memory redistribution of Listing 2: new per-type weights, a new
     plan, and every rank sends the states of the elements it no longer owns
     to their new owners (the all-to-all exchange); afterwards each rank holds
@@ -94,6 +97,23 @@ def _worker(rank, ws, port, outdir):
     np.save(os.path.join(outdir, f"R{rank}.npy"), blocks(R, own))
     np.save(os.path.join(outdir, f"own{rank}.npy"), own)
 
+    # the trace-exchange plan of the device path (dg_halo_plan, host-only):
+    # the keys of the faces rank q packs for me arrive in my receive order
+    sf, rf, sk, rk = dg.halo_plan(box, N, part, ws, rank)
+    soff, roff = np.concatenate([[0], np.cumsum(sf)]), np.concatenate([[0], np.cumsum(rf)])
+    got = _exchange(dist, rank, ws, {q: sk[soff[q]:soff[q + 1]].astype(np.float64) for q in range(ws)},
+                    {q: int(rf[q]) if q != rank else 0 for q in range(ws)})
+    keys_ok = int(sf[rank] == 0 and rf[rank] == 0)
+    for q in range(ws):
+        if q != rank:
+            keys_ok &= int(np.array_equal(got.get(q, np.zeros(0)).astype(np.int64), rk[roff[q]:roff[q + 1]]))
+    # every received face touches one of my elements and one of q's
+    for q in range(ws):
+        for key in rk[roff[q]:roff[q + 1]]:
+            e0 = int(key) // 8
+            keys_ok &= int(part[e0] in (rank, q))
+    np.save(os.path.join(outdir, f"keys{rank}.npy"), np.array([keys_ok, int(rf.sum())]))
+
     # redistribution after a change of weights (Listing 2): send the states of
     # the elements that move to their new owners, receive the incoming ones
     part2, _, _ = dg.partition_plan(box, N, ws, type_weight=[1.0, 2.5, 1.7, 0.8])
@@ -138,6 +158,8 @@ def test_partitioned_residual_and_redistribution(tmp_path, ws):
         assert np.array_equal(Rr, ref)
         ok, moved = np.load(tmp_path / f"redist{r}.npy")
         assert ok == 1
+        keys_ok, received = np.load(tmp_path / f"keys{r}.npy")
+        assert keys_ok == 1 and received > 0
     assert np.all(seen == 1)
     part, _, _ = dg.partition_plan(box, N, ws)
     part2, _, _ = dg.partition_plan(box, N, ws, type_weight=[1.0, 2.5, 1.7, 0.8])
