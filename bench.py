@@ -1605,7 +1605,7 @@ def main():
                     help="steps of the Navier-Stokes adjoint timing (0 skips it)")
     ap.add_argument("--ns-ke-adjoint", type=int, default=1,
                     help="time the adjoint of the final kinetic energy through all NS steps (0 skips it)")
-    ap.add_argument("--ke-adjoint-memory", type=float, default=0.9,
+    ap.add_argument("--ke-adjoint-memory", type=float, default=0.95,
                     help="share of the free device memory the kinetic-energy adjoint may keep stage data in")
     ap.add_argument("--curved-steps", type=int, default=100,
                     help="steps of the curved-geometry leg (0 skips it)")

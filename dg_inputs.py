@@ -386,3 +386,12 @@ def batch_workload(n_instances: int = 64, seed: int = 5, m_min: int = 4, m_max: 
         hn = splitmix64((seed ^ (2 * i + 1 + (1 << 40))) & MASK64)
         out.append((m_min + hm % span, int(degrees[hn % len(degrees)]), seed + i))
     return out
+
+
+def vertex_velocities(xyz, amp=0.1):
+    """Constant vertex velocities of a mesh in motion: the periodic field
+    amp (sin y sin z, sin z sin x, sin x sin y) at every vertex (periodic
+    images move alike, so the mesh stays conforming and periodic)."""
+    x = np.asarray(xyz, dtype=np.float64)
+    return amp * np.stack([np.sin(x[:, 1]) * np.sin(x[:, 2]), np.sin(x[:, 2]) * np.sin(x[:, 0]),
+                           np.sin(x[:, 0]) * np.sin(x[:, 1])], axis=1)
