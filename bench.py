@@ -598,6 +598,12 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
                               "value": sp["value"], "unit": "DOF-updates/s", "split_form": sp,
                               "split_only": True}), flush=True)
         return
+    if args.moving_only:
+        mv = moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, None)
+        if rank == 0:
+            print(json.dumps({"metric": "FP64 RHS DOF-updates/s per RK stage (moving mesh)", "value": mv["value"],
+                              "unit": "DOF-updates/s", "moving": mv, "moving_only": True}), flush=True)
+        return
     if args.curved_only:
         # profiling aid: the curved-geometry leg alone (its affine ratio is omitted)
         cv = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, None)
@@ -869,6 +875,8 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
     batch = batch_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.batch_steps > 0 else None
     nsl = ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws) if args.ns_steps > 0 else None
     cvl = curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, value) if args.curved_steps > 0 else None
+    mvl = (moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, cvl["balanced"]["value"] if cvl else None)
+           if args.moving_steps > 0 else None)
     spl = split_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, value) if args.split_steps > 0 else None
     prt = (partitioned_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, rank)
            if args.partition_steps > 0 else None)
@@ -942,6 +950,8 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
         line["navier_stokes"] = nsl
     if cvl is not None:
         line["curved"] = cvl
+    if mvl is not None:
+        line["moving"] = mvl
     if spl is not None:
         line["split_form"] = spl
     if prt is not None:
@@ -1136,6 +1146,76 @@ def ns_leg(dg, dev, stream, args, barrier, max_over_ranks, ws):
 CURVED_WORKLOAD = ("16^3-cube periodic box, mixed hex/prism/pyramid (seed 2) with every vertex moved by up to "
                    "0.1 h per coordinate (dg_inputs.perturb_vertices, seed 11): trilinear hexahedra, prisms and "
                    "pyramids with pointwise J and dense per-element M^-1; N=4, Euler TGV, LF, FP64")
+
+
+MOVING_WORKLOAD = ("the curved 16^3 mixed box (every vertex moved by up to 0.1 h, seed 11) in motion: vertex v "
+                   "at x_v + t u_v with u = 0.5 (sin y sin z, sin z sin x, sin x sin y) "
+                   "(dg_inputs.vertex_velocities); per stage the geometry at the stage time from its polynomial "
+                   "coefficients, the moving-frame residual, and the mass solve with the LSERK stage value of J "
+                   "(Cholesky per prism and pyramid, pointwise for hexahedra); N=4, Euler TGV, LF, FP64")
+
+
+def moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, curved_value):
+    """Moving mesh (time-varying geometry): LSERK steps of the mass-weighted
+    state with the geometry and the projection of Algorithm 1 evaluated
+    afresh at every stage; its cost against the static curved mesh, and the
+    share of the per-stage geometry and mass-solve kernels."""
+    import torch
+    box = di.perturb_vertices(di.box_mesh(MESH_M, "mixed", seed=MESH_SEED), 0.1, seed=11)
+    vel = di.vertex_velocities(box.xyz, 0.5)
+    mesh = dg.MovingMesh(box, N_DEG, vel, scheduler="balanced")
+    warps = args.warps or 4
+    mesh.set_element_warps(warps)
+    n = N_DEG + 1
+    xyz = mesh.quad_points()
+    vals = di.tgv_state(xyz).reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()
+    Q0 = mesh.project(torch.from_numpy(vals).to(dev))
+    dt = 0.8 * tgv_dt(box, xyz, N_DEG)
+    dof = int(sum(n_modes(int(t), N_DEG) for t in box.etype))
+    steps = args.moving_steps
+    out = {"workload": MOVING_WORKLOAD, "elements": box.n_elems, "dof_per_var": dof, "steps": steps, "dt": dt,
+           "unit": "DOF-updates/s", "warps": warps,
+           "type_counts": dict(zip(("hex", "prism", "pyramid", "tet"), mesh.type_counts))}
+
+    def timed(Q, K, profile=False):
+        mesh.set_profiling(profile)
+        for _ in range(args.warmup):
+            mesh.rk_step(Q, K, dt, 1)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el = fa = 0.0
+        with timed_window("moving"):
+            e0.record(stream)
+            for _ in range(steps):
+                mesh.rk_step(Q, K, dt, 1)
+                if profile:
+                    a, b_, _, _ = mesh.phase_times()
+                    el += a
+                    fa += b_
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        mesh.set_profiling(False)
+        return max_over_ranks(e0.elapsed_time(e1)), el, fa
+
+    Q = Q0.clone()
+    K = torch.empty_like(Q)
+    ms, _, _ = timed(Q, K)
+    mesh.sync()
+    out["value"] = ws * dof * 5 * steps / (ms * 1e-3)
+    out["ms_per_step"] = ms / steps
+    out["mesh_time_end"] = mesh.time
+    out["finite"] = bool(torch.isfinite(Q).all())
+    Qp = Q0.clone()
+    msp, el, fa = timed(Qp, K, profile=True)
+    out["element_ms_per_step"] = el / steps
+    out["face_ms_per_step"] = fa / steps
+    out["geometry_and_mass_ms_per_step"] = (msp - el - fa) / steps
+    out["geometry_and_mass_share"] = (msp - el - fa) / msp
+    out["over_static_curved"] = out["value"] / curved_value if curved_value else None
+    return out
 
 
 def curved_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, affine_value):
@@ -1607,6 +1687,10 @@ def main():
                     help="time the adjoint of the final kinetic energy through all NS steps (0 skips it)")
     ap.add_argument("--ke-adjoint-memory", type=float, default=0.95,
                     help="share of the free device memory the kinetic-energy adjoint may keep stage data in")
+    ap.add_argument("--moving-steps", type=int, default=20,
+                    help="LSERK steps of the moving-mesh leg (0: skip)")
+    ap.add_argument("--moving-only", action="store_true",
+                    help="profiling aid: the moving-mesh leg alone")
     ap.add_argument("--curved-steps", type=int, default=100,
                     help="steps of the curved-geometry leg (0 skips it)")
     ap.add_argument("--partition-steps", type=int, default=20,

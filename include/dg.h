@@ -168,6 +168,49 @@ typedef struct {
 dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh** out);
 dg_status dg_mesh_destroy(dg_mesh* mesh);
 
+/* Moving mesh (Sec. 2: the mesh may move in time; Algorithm 1: the
+ * projection is then solved afresh because J depends on time).
+ * vertex_velocity: host [n_vertices][3], caller-owned, read during the call:
+ * vertex v sits at xyz[v] + t vertex_velocity[v] at mesh time t, which starts
+ * at 0 (the positions of desc).  Periodic images of one point must share
+ * its velocity.  Every hexahedron, prism and pyramid takes the pointwise
+ * (curved) geometry path, its map the vertex interpolant at every time, so
+ * J is a cubic and the contravariant metric a quadratic in t; their
+ * coefficients and the mesh velocity at every point stay in device memory
+ * (dg_mesh_geometry does not count them).  The residual is the moving-frame
+ * weak form: fluxes F(q) - q xdot in the volume and the LF flux in the frame
+ * of the face's normal mesh speed on the faces.  dg_rk_step evolves the
+ * mass-weighted state M Q: each stage solves M^ Q_s = (M Q)_s by Cholesky
+ * with M^ built from the LSERK stage values of t^k, so that a constant state
+ * stays constant (a discrete geometric conservation law), and advances the
+ * mesh time by nsteps dt; Q_store holds Q at the mesh time before and after.
+ * dg_rhs returns M(t)^{-1} (vol - surf) at the mesh time; dg_project and
+ * dg_load_vector use the geometry of the mesh time (dg_quad_points returns
+ * the points at t = 0).  Requirements: flux DG_FLUX_LF, no tetrahedra, the
+ * Euler equations, the weak volume form; the adjoint, the checkpointed steps
+ * and dg_autotune return DG_ERR_UNSUPPORTED.  An element that the motion turns
+ * inside out makes the next dg_sync return DG_ERR_MESH. */
+dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_velocity, cudaStream_t stream,
+                                dg_mesh** out);
+/* Host only (no device needed): the pointwise geometry of desc with every
+ * hexahedron, prism and pyramid on the curved path, per element
+ * ([9][nQ] weighted contravariant metric w (da/dxi)(J dxi/dx), [nQ] J, [nQ]
+ * 1/J, prisms and pyramids [nM][nM] M^{-1} = (V^T diag(w J) V)^{-1}), in
+ * caller element order, and per face with a curved owner ([3][n^2] unit
+ * normal, [n^2] w S at the owner's face points) in the order of (owner, the
+ * owner's local face), the owner being the smaller caller index.  With
+ * vertex_velocity (host [n_vertices][3]) it is the moving mesh's geometry at
+ * time t evaluated from the coefficients that dg_mesh_create_moving keeps; with
+ * NULL the static geometry of desc itself (t ignored).  Two-call pattern: the
+ * sizes are always written; elem_geo / face_geo (host, caller-owned) are
+ * filled when non-NULL.  DG_ERR_MESH if an element is inside out at t. */
+dg_status dg_geometry_at(const dg_mesh_desc* desc, const double* vertex_velocity, double t, int64_t* n_elem_doubles,
+                         int64_t* n_face_doubles, double* elem_geo, double* face_geo);
+/* The mesh time of a moving mesh (0 for a static one); dg_set_mesh_time sets
+ * it (DG_ERR_UNSUPPORTED for a static mesh). */
+dg_status dg_mesh_time(const dg_mesh* mesh, double* t);
+dg_status dg_set_mesh_time(dg_mesh* mesh, double t);
+
 /* Batch of independent meshes as one handle.  The paper advances one mesh at
  * one N; a batch evaluates Eq. 1 on each instance separately (no face couples
  * two instances), so every call below acts on all instances at once: one

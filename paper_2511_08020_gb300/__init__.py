@@ -90,6 +90,10 @@ _SIGS = {
     "dg_set_element_warps": [_P, ctypes.c_int],
     "dg_autotune": [_P, _P, ctypes.c_double, _P, _P, _P],
     "dg_phase_times": [_P, _P, _P],
+    "dg_mesh_create_moving": [ctypes.POINTER(MeshDesc), _P, _P, ctypes.POINTER(_P)],
+    "dg_mesh_time": [_P, _P],
+    "dg_set_mesh_time": [_P, ctypes.c_double],
+    "dg_geometry_at": [ctypes.POINTER(MeshDesc), _P, ctypes.c_double, _P, _P, _P, _P],
 }
 
 _lib = None
@@ -432,6 +436,51 @@ class Mesh:
 
     def sync(self, stream=None):
         _check(load().dg_sync(self.handle, _stream(stream)))
+
+
+def geometry_at(box, N, velocity=None, t=0.0):
+    """dg_geometry_at (host only): (element geometry, face geometry) of the box
+    with every non-tetrahedral element on the curved path, static (velocity
+    None) or of the moving mesh at time t."""
+    import numpy as np
+    d, keep = _desc(box, N, "lf", 1.4, "balanced", 0.1, "vertex")
+    vel = None if velocity is None else np.ascontiguousarray(velocity, dtype=np.float64)
+    ne, nf = ctypes.c_int64(), ctypes.c_int64()
+    vp = None if vel is None else _ptr(vel)
+    _check(load().dg_geometry_at(ctypes.byref(d), vp, float(t), ctypes.byref(ne), ctypes.byref(nf), None, None))
+    eg, fg = np.zeros(ne.value), np.zeros(nf.value)
+    _check(load().dg_geometry_at(ctypes.byref(d), vp, float(t), ctypes.byref(ne), ctypes.byref(nf), _ptr(eg), _ptr(fg)))
+    return eg, fg
+
+
+class MovingMesh(Mesh):
+    """A mesh whose vertices move at constant velocities (dg_mesh_create_moving):
+    vertex v sits at xyz[v] + t * velocity[v] at mesh time t (0 at creation).
+    rhs evaluates at the mesh time; rk_step advances the state and the mesh
+    time; project projects at the mesh time.  The Euler equations with the
+    LF flux on hexahedra, prisms and pyramids."""
+
+    def __init__(self, box, N, velocity, gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None):
+        import numpy as np
+        self.N = int(N)
+        self.flux = "lf"
+        d, keep = _desc(box, N, "lf", gamma, scheduler, imbalance_threshold, "vertex")
+        vel = np.ascontiguousarray(velocity, dtype=np.float64)
+        if vel.shape != keep["xyz"].shape:
+            raise ValueError("velocity must have the shape of the vertex coordinates")
+        h = ctypes.c_void_p()
+        _check(load().dg_mesh_create_moving(ctypes.byref(d), _ptr(vel), _stream(stream), ctypes.byref(h)))
+        self._adopt(h, keep["etype"].copy())
+        self.points_per_elem = np.full(self.n_elems, (self.N + 1) ** 3, dtype=np.int64)
+
+    @property
+    def time(self):
+        t = ctypes.c_double()
+        _check(load().dg_mesh_time(self.handle, ctypes.byref(t)))
+        return t.value
+
+    def set_time(self, t):
+        _check(load().dg_set_mesh_time(self.handle, float(t)))
 
 
 class Part(Mesh):

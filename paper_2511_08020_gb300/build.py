@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdg.so")
-SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_api.cu"]
+SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_moving.cu", "dg_api.cu"]
 PROBE_SRC = "fp64_probe.cu"
 PROBE_LIB = os.path.join(LIBDIR, "libfp64probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

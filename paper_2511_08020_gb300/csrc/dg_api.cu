@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/dg.h"
@@ -66,6 +67,13 @@ struct dg_mesh {
   std::vector<int64_t> send_count, recv_count, send_off, recv_off;
   int64_t* d_send_off = nullptr;
   int64_t* d_recv_off = nullptr;
+  // moving meshes (dg_mesh_create_moving): the geometry coefficients, the
+  // mesh time, the mass-weighted state and the stage state of dg_rk_step
+  bool moving = false;
+  double t_mesh = 0.0;
+  int max_nM_dense = 0;   // largest prism / pyramid mode count (shared memory of the mass kernel)
+  int64_t* d_slot_moff = nullptr;
+  double *d_mpool = nullptr, *d_fmot = nullptr, *d_Ut = nullptr, *d_S = nullptr;
   double gamma = 1.4;
   int scheduler = DG_SCHED_BALANCED;
   double threshold = 0.1;
@@ -352,7 +360,76 @@ struct dg_mesh {
     c.flux = flux;
     c.split = split;
     c.nQmax = nQmax;
+    if (moving) {
+      c.mpool = d_mpool;
+      c.slot_moff = d_slot_moff;
+      c.fmot = d_fmot;
+    }
     return c;
+  }
+
+  // ---- moving meshes
+  int grid_slots() const { return (int)std::max<int64_t>(1, std::min<int64_t>(h.n_elems, (int64_t)num_sms * 8)); }
+  void moving_geometry(double t, cudaStream_t st) {
+    dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, h.n_elems, h.n_faces, h.n, t, grid_slots(), st);
+  }
+  cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st) {
+    return dgk::launch_moving_mass(ctx(), h.n_elems, in, out, tau, weight, max_nM_dense, grid_slots(), st);
+  }
+  static void powers(double t, double tau[4]) {
+    tau[0] = 1.0;
+    tau[1] = t;
+    tau[2] = t * t;
+    tau[3] = t * t * t;
+  }
+  // Residual at the mesh time: M(t)^{-1} (vol - surf).
+  cudaError_t moving_rhs(const double* Q, double* R, cudaStream_t st) {
+    cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
+    parity = 0;
+    moving_geometry(t_mesh, st);
+    dgk::StageArgs a{Q, R, nullptr, 0.0, 0.0, 0.0};
+    element_phase(dgk::kFwd, a, st);
+    face_phase(st);
+    element_phase(dgk::kBwdRhs, a, st);
+    double tau[4];
+    powers(t_mesh, tau);
+    return moving_mass(R, R, tau, 0, st);
+  }
+  // LSERK(5,4) steps of the mass-weighted state Ut = M Q (K: its register).
+  // Stage s evaluates the residual at t_s = t + c_s dt on the geometry of
+  // t_s, from the stage state M^_s^{-1} Ut with M^_s built from the stage
+  // values y_k of t^k, which run through the same 2N-storage recursion
+  // (dy_k/dt = k t^(k-1)).
+  cudaError_t moving_rk(double* Q, double* K, double dt, int nsteps, cudaStream_t st) {
+    static const double kLsC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363183857.0,
+                                   2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+    cudaError_t e = cudaSuccess;
+    cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
+    parity = 0;
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+      const double t = t_mesh;
+      double y[4], Ky[4] = {0.0, 0.0, 0.0, 0.0};
+      powers(t, y);
+      if ((e = moving_mass(Q, d_Ut, y, 1, st)) != cudaSuccess) return e;
+      for (int s = 0; s < 5; ++s) {
+        const double ts = t + kLsC[s] * dt;
+        moving_geometry(ts, st);
+        if ((e = moving_mass(d_Ut, d_S, y, 0, st)) != cudaSuccess) return e;
+        dgk::StageArgs f{d_S, nullptr, nullptr, 0.0, 0.0, 0.0};
+        element_phase(dgk::kFwd, f, st);
+        face_phase(st);
+        dgk::StageArgs a{d_Ut, d_Ut, K, kLsA[s], kLsB[s], dt};
+        element_phase(dgk::kBwdRk, a, st);
+        const double dp[4] = {0.0, 1.0, 2.0 * ts, 3.0 * ts * ts};
+        for (int k = 0; k < 4; ++k) {
+          Ky[k] = kLsA[s] * Ky[k] + dt * dp[k];
+          y[k] += kLsB[s] * Ky[k];
+        }
+      }
+      if ((e = moving_mass(d_Ut, Q, y, 0, st)) != cudaSuccess) return e;
+      t_mesh = t + dt;
+    }
+    return cudaGetLastError();
   }
 
   bool ghost_slot(int64_t s) const { return !h.slot_ghost.empty() && h.slot_ghost[s]; }
@@ -696,7 +773,7 @@ struct dg_mesh {
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks_static, d_chunks_weighted, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
-                    d_slot_coff, d_cpool, d_fgeo, d_snrm};
+                    d_slot_coff, d_cpool, d_fgeo, d_snrm, d_slot_moff, d_mpool, d_fmot, d_Ut, d_S};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -760,6 +837,116 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, cudaStream_t stream, dg_mesh*
     return fail((dg_status)r, err);
   }
   return create_device_mesh(m, desc, stream, out);
+}
+
+dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_velocity, cudaStream_t stream,
+                                dg_mesh** out) {
+  if (!desc || !vertex_velocity || !out) return fail(DG_ERR_ARG, "null argument");
+  *out = nullptr;
+  dg_status st = check_desc(desc);
+  if (st != DG_OK) return st;
+  if (desc->flux != DG_FLUX_LF) return fail(DG_ERR_UNSUPPORTED, "a moving mesh takes the LF flux");
+  for (int64_t v = 0; v < 3 * desc->n_vertices; ++v)
+    if (!std::isfinite(vertex_velocity[v])) return fail(DG_ERR_ARG, "vertex velocities must be finite");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) return fail(DG_ERR_CUDA, "no CUDA device available (the library has no CPU path)");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  dgh::MeshInput in = input_of(desc);
+  in.force_curved = 1;
+  std::string err;
+  int r = dgh::build_mesh(in, &m->h, &err);
+  dgh::Motion mo;
+  if (r == 0) r = dgh::build_motion(m->h, in, vertex_velocity, &mo, &err);
+  size_t max_nM = 0;
+  for (const auto& T : m->h.tables.tabs)
+    if (T.type == dgk::PRISM || T.type == dgk::PYR) max_nM = std::max<size_t>(max_nM, (size_t)T.nM);
+  if (r == 0 && sizeof(double) * (max_nM * max_nM + 5 * max_nM) > 227 * 1024) {
+    err = "the mass matrix of this degree's prisms or pyramids exceeds one block's shared memory";
+    r = DG_ERR_UNSUPPORTED;
+  }
+  if (r != 0) {
+    delete m;
+    return fail((dg_status)r, err);
+  }
+  dg_mesh* made = nullptr;
+  st = create_device_mesh(m, desc, stream, &made);
+  if (st != DG_OK) return st;
+  made->moving = true;
+  made->max_nM_dense = (int)max_nM;
+  const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(1, made->h.n_dof);
+  cudaError_t e = upload(&made->d_slot_moff, mo.slot_moff);
+  if (e == cudaSuccess) e = upload(&made->d_mpool, mo.mpool);
+  if (e == cudaSuccess) e = upload(&made->d_fmot, mo.fpool);
+  if (e == cudaSuccess) e = cudaMalloc(&made->d_Ut, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&made->d_S, bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    made->release();
+    delete made;
+    return cuda_fail(e, "moving-mesh geometry");
+  }
+  *out = made;
+  return DG_OK;
+}
+
+dg_status dg_geometry_at(const dg_mesh_desc* desc, const double* vertex_velocity, double t, int64_t* n_elem_doubles,
+                         int64_t* n_face_doubles, double* elem_geo, double* face_geo) {
+  if (!desc || !n_elem_doubles || !n_face_doubles) return fail(DG_ERR_ARG, "null argument");
+  if (!std::isfinite(t)) return fail(DG_ERR_ARG, "t must be finite");
+  dgh::MeshInput in = input_of(desc);
+  in.force_curved = 1;
+  dgh::HostMesh h;
+  std::string err;
+  int r = dgh::build_mesh(in, &h, &err);
+  if (r != 0) return fail((dg_status)r, err);
+  std::vector<double> cp, fg;
+  if (vertex_velocity) {
+    dgh::Motion mo;
+    r = dgh::build_motion(h, in, vertex_velocity, &mo, &err);
+    if (r == 0) r = dgh::motion_geometry_at(h, mo, t, &cp, &fg, &err);
+    if (r != 0) return fail((dg_status)r, err);
+  } else {
+    cp = h.cpool;
+    fg = h.fgeo;
+  }
+  *n_elem_doubles = (int64_t)cp.size();
+  *n_face_doubles = (int64_t)fg.size();
+  // caller order: elements by caller index, faces by (owner, owner's local face)
+  if (elem_geo) {
+    size_t o = 0;
+    for (int64_t e = 0; e < h.n_elems; ++e) {
+      const int64_t sl = h.slot_of_elem[e];
+      const size_t len = (size_t)dgh::curved_block_doubles(h.tables.tabs[h.slot_tab[sl]]);
+      std::memcpy(elem_geo + o, cp.data() + h.slot_coff[sl], sizeof(double) * len);
+      o += len;
+    }
+  }
+  if (face_geo) {
+    std::vector<std::tuple<int64_t, int, int64_t>> key;
+    for (int64_t f = 0; f < h.n_faces; ++f)
+      if (h.faces[f].cgeo >= 0) key.emplace_back(h.face_e0[f], (int)h.face_l0[f], f);
+    std::sort(key.begin(), key.end());
+    const size_t per = (size_t)4 * h.n * h.n;
+    for (size_t k = 0; k < key.size(); ++k)
+      std::memcpy(face_geo + k * per, fg.data() + h.faces[std::get<2>(key[k])].cgeo, sizeof(double) * per);
+  }
+  return DG_OK;
+}
+
+dg_status dg_mesh_time(const dg_mesh* mesh, double* t) {
+  if (!mesh || !t) return fail(DG_ERR_ARG, "null argument");
+  *t = mesh->t_mesh;
+  return DG_OK;
+}
+
+dg_status dg_set_mesh_time(dg_mesh* mesh, double t) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (!mesh->moving) return fail(DG_ERR_UNSUPPORTED, "only a moving mesh has a time");
+  if (!std::isfinite(t)) return fail(DG_ERR_ARG, "t must be finite");
+  mesh->t_mesh = t;
+  return DG_OK;
 }
 
 dg_status dg_batch_create(const dg_mesh_desc* descs, int n_instances, cudaStream_t stream, dg_mesh** out) {
@@ -1201,6 +1388,17 @@ dg_status dg_quad_points(const dg_mesh* mesh, double* xyz_out) {
 
 dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cudaStream_t stream) {
   if (!mesh || !q_points || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) {
+    // Algorithm 1 at the mesh time: the load vector on the geometry of t,
+    // then the solve with M(t)
+    mesh->moving_geometry(mesh->t_mesh, stream);
+    dgk::StageArgs b{q_points, Q_store, nullptr, 0.0, 0.0, 0.0};
+    mesh->element_phase(dgk::kLoad, b, stream);
+    double tau[4];
+    dg_mesh::powers(mesh->t_mesh, tau);
+    DG_CUDA(mesh->moving_mass(Q_store, Q_store, tau, 0, stream));
+    return DG_OK;
+  }
   dgk::StageArgs a{q_points, Q_store, nullptr, 0.0, 0.0, 0.0};
   mesh->element_phase(dgk::kProject, a, stream);
   DG_CUDA(cudaGetLastError());
@@ -1209,6 +1407,7 @@ dg_status dg_project(dg_mesh* mesh, const double* q_points, double* Q_store, cud
 
 dg_status dg_load_vector(dg_mesh* mesh, const double* q_points, double* b_store, cudaStream_t stream) {
   if (!mesh || !q_points || !b_store) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) mesh->moving_geometry(mesh->t_mesh, stream);
   dgk::StageArgs a{q_points, b_store, nullptr, 0.0, 0.0, 0.0};
   mesh->element_phase(dgk::kLoad, a, stream);
   DG_CUDA(cudaGetLastError());
@@ -1226,6 +1425,11 @@ dg_status dg_eval_nodal(dg_mesh* mesh, const double* Q_store, double* u_points, 
 dg_status dg_rhs(dg_mesh* mesh, const double* Q_store, double* R_store, cudaStream_t stream) {
   if (!mesh || !Q_store || !R_store) return fail(DG_ERR_ARG, "null argument");
   if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "a partition mesh steps with dg_rk_prime / dg_rk_stage and the halo exchange");
+  if (mesh->moving) {
+    mesh->begin_timing(1);
+    DG_CUDA(mesh->moving_rhs(Q_store, R_store, stream));
+    return DG_OK;
+  }
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
   mesh->begin_timing(1);
@@ -1243,7 +1447,12 @@ dg_status dg_rk_step(dg_mesh* mesh, double* Q_store, double* K_store, double dt,
   if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return DG_OK;
   if (!(std::isfinite(dt))) return fail(DG_ERR_ARG, "dt must be finite");
-  if (!mesh->profiling) {
+  if (mesh->moving) {
+    // direct launches: every stage's geometry and mass matrix depend on the
+    // mesh time, passed by value
+    mesh->begin_timing(1);
+    DG_CUDA(mesh->moving_rk(Q_store, K_store, dt, nsteps, stream));
+  } else if (!mesh->profiling) {
     // replay the three captured graphs; a new state, register, dt or step
     // count only changes the arguments of the parameter node
     if (!mesh->gr_prime.x || mesh->r_sched != mesh->scheduler || mesh->r_fused != (int)mesh->fused) {
@@ -1332,6 +1541,7 @@ dg_status dg_rebalance_stats(const dg_mesh* mesh, int64_t* checks, int64_t* reba
 
 dg_status dg_rhs_vjp(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar, cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers static meshes");
   if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers whole meshes");
   if (mesh->split || mesh->flux == DG_FLUX_EC)
     return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
@@ -1375,6 +1585,7 @@ extern "C" {
 dg_status dg_rhs_vjp_noalloc(dg_mesh* mesh, const double* Q_store, const double* Rbar, double* Qbar,
                              cudaStream_t stream) {
   if (!mesh || !Q_store || !Rbar || !Qbar) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers static meshes");
   if (mesh->split || mesh->flux == DG_FLUX_EC)
     return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
   if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers whole meshes");
@@ -1453,6 +1664,7 @@ dg_status rk_vjp_reverse(dg_mesh* mesh, const double* ck, double dt, int nsteps,
 dg_status rk_vjp_args(dg_mesh* mesh, const void* a, const void* b, const void* c, int nsteps, int ckpt_every,
                       double dt) {
   if (!mesh || !a || !b || !c) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers static meshes");
   if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the adjoint covers whole meshes");
   if (mesh->split || mesh->flux == DG_FLUX_EC)
     return fail(DG_ERR_UNSUPPORTED, "the adjoint covers the weak form with the LF or Roe flux");
@@ -1541,6 +1753,7 @@ dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double
 dg_status dg_rk_step_checkpointed(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int nsteps,
                                   int ckpt_every, double* ckpt_store, cudaStream_t stream) {
   if (!mesh || !Q_store || !K_store || !ckpt_store) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "checkpointed steps serve the adjoint, which covers static meshes");
   if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "a partition mesh steps with dg_rk_prime / dg_rk_stage and the halo exchange");
   if (nsteps < 0 || ckpt_every < 1) return fail(DG_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
@@ -1582,6 +1795,7 @@ dg_status dg_set_volume_form(dg_mesh* mesh, int form) {
   if (form != DG_VOLUME_WEAK && form != DG_VOLUME_SPLIT) return fail(DG_ERR_ARG, "unknown volume form");
   if (form == DG_VOLUME_SPLIT) {
     if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the split form covers the Euler equations");
+    if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "the split form covers static affine meshes");
     if (mesh->h.n_curved > 0) return fail(DG_ERR_UNSUPPORTED, "the split form covers affine meshes");
   }
   mesh->split = form == DG_VOLUME_SPLIT;
@@ -1600,6 +1814,8 @@ dg_status dg_set_volume_form(dg_mesh* mesh, int form) {
 dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
+  if (physics == DG_NAVIER_STOKES && mesh->moving)
+    return fail(DG_ERR_UNSUPPORTED, "a moving mesh runs the Euler equations");
   if (physics == DG_NAVIER_STOKES && part_mesh(mesh))
     return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes needs a second halo exchange per stage; partition meshes run Euler");
   if (physics == DG_NAVIER_STOKES && (mesh->split || mesh->flux == DG_FLUX_EC))
@@ -1791,6 +2007,7 @@ dg_status dg_autotune(dg_mesh* mesh, const double* Q_store, double dt, int* best
                       cudaStream_t stream) {
   if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
   if (part_mesh(mesh)) return fail(DG_ERR_UNSUPPORTED, "the autotuner times dg_rk_step, which a partition mesh cannot run");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "the autotuner times the static stage graphs; set the tile shape with dg_set_element_warps");
   const char* cache = std::getenv("DG_AUTOTUNE_CACHE");
   const std::string key = autotune_key(mesh);
   const int ntab = (int)mesh->h.tables.tabs.size();
@@ -1948,6 +2165,10 @@ dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream) {
   DG_CUDA(cudaStreamSynchronize(stream));
   unsigned st = 0;
   DG_CUDA(cudaMemcpy(&st, mesh->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st & 4u) {
+    cudaMemset(mesh->d_status, 0, sizeof(unsigned));
+    return fail(DG_ERR_MESH, "the moving mesh turned an element inside out (J or the face area reached zero)");
+  }
   if (st & 1u) {
     cudaMemset(mesh->d_status, 0, sizeof(unsigned));
     return fail(DG_ERR_NONFINITE, "a non-finite state value was produced");

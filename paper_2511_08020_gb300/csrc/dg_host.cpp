@@ -749,6 +749,44 @@ bool curved_block(const TypeTab& T, const std::vector<double>& dpool, const doub
   return true;
 }
 
+// Adjugate of a 3x3 matrix (transpose of the cofactor matrix): adj(A) A = det(A) I.
+void adj3(const double A[3][3], double R[3][3]) {
+  R[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  R[0][1] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+  R[0][2] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+  R[1][0] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  R[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+  R[1][2] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+  R[2][0] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  R[2][1] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+  R[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+}
+
+// Coefficients of det(A + t B) = d0 + d1 t + d2 t^2 + d3 t^3 and of
+// adj(A + t B) = adj(A) + t D + t^2 adj(B) (adj is quadratic: D = adj(A + B)
+// - adj(A) - adj(B)).
+void det_adj_poly(const double A[3][3], const double B[3][3], double d[4], double adj[3][3][3]) {
+  double AB[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) AB[i][j] = A[i][j] + B[i][j];
+  double aA[3][3], aB[3][3], aAB[3][3];
+  adj3(A, aA);
+  adj3(B, aB);
+  adj3(AB, aAB);
+  d[0] = det3(A);
+  d[3] = det3(B);
+  d[1] = 0.0;
+  d[2] = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      d[1] += aA[i][j] * B[j][i];     // tr(adj(A) B)
+      d[2] += A[i][j] * aB[j][i];     // tr(A adj(B))
+      adj[0][i][j] = aA[i][j];
+      adj[1][i][j] = aAB[i][j] - aA[i][j] - aB[i][j];
+      adj[2][i][j] = aB[i][j];
+    }
+}
+
 int64_t curved_block_size(const TypeTab& T) {
   return 11 * (int64_t)T.nQ + ((T.type == dgk::PRISM || T.type == dgk::PYR) ? (int64_t)T.nM * T.nM : 0);
 }
@@ -818,8 +856,8 @@ int build_mesh(const MeshInput& in, HostMesh* out, std::string* err) {
         for (int d = 0; d < 3; ++d) c[d] += in.xyz[3 * V[m] + d] / kNumVerts[t];
       for (int d = 0; d < 3; ++d) centroid[e][d] = c[d];
     }
-    if (!is_affine) {
-      if (in.geometry != 1) { *err = "element is not an affine image of its reference element"; return -2; }
+    if (!is_affine || (in.force_curved && t != dgk::TET)) {
+      if (in.geometry != 1 && !in.force_curved) { *err = "element is not an affine image of its reference element"; return -2; }
       curved[e] = 1;   // pointwise geometry below; the affine record stays zero
       std::memset(&geo[e], 0, sizeof(geo[e]));
       for (int d = 0; d < 12; ++d) affine[e][d] = 0.0;
@@ -1444,6 +1482,207 @@ int build_batch(const std::vector<MeshInput>& ins, HostMesh* out, std::string* e
       (int64_t)M.fgeo.size() >= (int64_t)1 << 31) {
     *err = "batch too large for 32-bit face indices";
     return -7;
+  }
+  return 0;
+}
+
+int motion_geometry_at(const HostMesh& M, const Motion& mo, double t, std::vector<double>* cpool,
+                       std::vector<double>* fgeo, std::string* err) {
+  const int n2 = M.n * M.n;
+  const double tk[4] = {1.0, t, t * t, t * t * t};
+  cpool->assign(M.cpool.size(), 0.0);
+  fgeo->assign(M.fgeo.size(), 0.0);
+  for (int64_t s = 0; s < M.n_elems; ++s) {
+    const TypeTab& T = M.tables.tabs[M.slot_tab[s]];
+    const int nQ = T.nQ, nM = T.nM;
+    const double* m = mo.mpool.data() + mo.slot_moff[s];
+    double* cb = cpool->data() + M.slot_coff[s];
+    for (int q = 0; q < nQ; ++q) {
+      for (int i = 0; i < 9; ++i) {
+        double v = 0.0;
+        for (int k = 0; k < 3; ++k) v += tk[k] * m[(size_t)(9 * k + i) * nQ + q];
+        cb[(size_t)i * nQ + q] = v;
+      }
+      double J = 0.0;
+      for (int k = 0; k < 4; ++k) J += tk[k] * m[(size_t)(27 + k) * nQ + q];
+      if (!(J > 0.0)) { *err = "an element is inside out at this time"; return -2; }
+      cb[(size_t)9 * nQ + q] = J;
+      cb[(size_t)10 * nQ + q] = 1.0 / J;
+    }
+    if (T.type == dgk::PRISM || T.type == dgk::PYR) {
+      std::vector<double> Me((size_t)nM * nM, 0.0);
+      for (int k = 0; k < 4; ++k)
+        for (size_t w = 0; w < Me.size(); ++w) Me[w] += tk[k] * m[(size_t)34 * nQ + (size_t)k * nM * nM + w];
+      if (!spd_inverse(nM, Me.data(), cb + (size_t)11 * nQ)) { *err = "mass matrix not positive definite"; return -2; }
+    }
+  }
+  for (int64_t f = 0; f < M.n_faces; ++f) {
+    const dgk::FaceRec& R = M.faces[f];
+    if (R.cgeo < 0) continue;
+    const double* a = mo.fpool.data() + (size_t)3 * R.cgeo;
+    double* g = fgeo->data() + R.cgeo;
+    for (int p = 0; p < n2; ++p) {
+      double A[3];
+      for (int d = 0; d < 3; ++d) A[d] = a[(size_t)d * n2 + p] + t * a[(size_t)(3 + d) * n2 + p] + t * t * a[(size_t)(6 + d) * n2 + p];
+      const double S = std::sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+      if (!(S > 0.0)) { *err = "a face has zero area at this time"; return -2; }
+      for (int d = 0; d < 3; ++d) g[(size_t)d * n2 + p] = A[d] / S;
+      g[(size_t)3 * n2 + p] = S;
+    }
+  }
+  return 0;
+}
+
+int64_t curved_block_doubles(const dgk::TypeTab& T) { return curved_block_size(T); }
+
+int64_t motion_block_size(const dgk::TypeTab& T) {
+  return 34 * (int64_t)T.nQ + ((T.type == dgk::PRISM || T.type == dgk::PYR) ? 4 * (int64_t)T.nM * T.nM : 0);
+}
+
+int build_motion(const HostMesh& M, const MeshInput& in, const double* vel, Motion* out, std::string* err) {
+  const int64_t E = M.n_elems;
+  const int n = M.n, n2 = n * n;
+  const double* x = M.x1d.data();
+  for (int64_t s = 0; s < E; ++s)
+    if (M.slot_type[s] == dgk::TET) { *err = "moving meshes cover hexahedra, prisms and pyramids"; return -7; }
+  if (M.n_curved != E) { *err = "a moving mesh needs every element on the curved path"; return -7; }
+  out->slot_moff.assign(E, -1);
+  int64_t total = 0;
+  for (int64_t s = 0; s < E; ++s) {
+    out->slot_moff[s] = total;
+    total += motion_block_size(M.tables.tabs[M.slot_tab[s]]);
+  }
+  out->mpool.assign((size_t)total, 0.0);
+  std::vector<double> Vt[4];
+  for (int t = 1; t <= 2; ++t)
+    if (M.type_count[t]) Vt[t] = vandermonde(t, M.N, x);
+  for (int64_t s = 0; s < E; ++s) {
+    const int64_t e = M.elem_of_slot[s];
+    const int type = M.slot_type[s];
+    const TypeTab& T = M.tables.tabs[M.slot_tab[s]];
+    const int nQ = T.nQ, nM = T.nM;
+    const int64_t* V = in.verts + in.off[e];
+    double Xrel[24], Urel[24], u0[3];
+    for (int d = 0; d < 3; ++d) u0[d] = vel[3 * V[0] + d];
+    for (int v = 0; v < kNumVerts[type]; ++v)
+      for (int d = 0; d < 3; ++d) {
+        Xrel[3 * v + d] = in.xyz[3 * V[v] + d] - in.xyz[3 * V[0] + d];
+        Urel[3 * v + d] = vel[3 * V[v] + d] - u0[d];
+      }
+    const double* wq = M.tables.dpool.data() + T.W;
+    double* blk = out->mpool.data() + out->slot_moff[s];
+    std::vector<double> Jk((size_t)4 * nQ);
+    int sign = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+          const int q = (i * n + j) * n + k;
+          double F0[3][3], F1[3][3], xr[3], ur[3];
+          element_map(type, Xrel, x[i], x[j], x[k], F0, xr);
+          element_map(type, Urel, x[i], x[j], x[k], F1, ur);
+          double dk[4], ad[3][3][3];
+          det_adj_poly(F0, F1, dk, ad);
+          const int sg = dk[0] > 0 ? 1 : -1;
+          if (dk[0] == 0.0 || (sign != 0 && sg != sign)) { *err = "degenerate element"; return -2; }
+          sign = sg;
+          double cm[3][3];
+          collapse_metric(type, x[i], x[j], x[k], cm);
+          for (int c = 0; c < 3; ++c)
+            for (int l = 0; l < 3; ++l)
+              for (int d = 0; d < 3; ++d) {
+                double m = 0.0;
+                for (int kk = 0; kk < 3; ++kk) m += cm[l][kk] * sg * ad[c][kk][d];
+                blk[((size_t)c * 9 + l * 3 + d) * nQ + q] = wq[q] * m;
+              }
+          for (int c = 0; c < 4; ++c) {
+            Jk[(size_t)c * nQ + q] = sg * dk[c];
+            blk[(size_t)(27 + c) * nQ + q] = sg * dk[c];
+          }
+          for (int d = 0; d < 3; ++d) blk[(size_t)(31 + d) * nQ + q] = u0[d] + ur[d];
+        }
+    if (type == dgk::PRISM || type == dgk::PYR) {
+      const double* Vq = Vt[type].data();
+      for (int c = 0; c < 4; ++c) {
+        double* Mc = blk + (size_t)34 * nQ + (size_t)c * nM * nM;
+        for (int q = 0; q < nQ; ++q) {
+          const double* vq = Vq + (size_t)q * nM;
+          const double w = wq[q] * Jk[(size_t)c * nQ + q];
+          for (int a = 0; a < nM; ++a)
+            for (int b = 0; b <= a; ++b) Mc[(size_t)a * nM + b] += w * vq[a] * vq[b];
+        }
+        for (int a = 0; a < nM; ++a)
+          for (int b = a + 1; b < nM; ++b) Mc[(size_t)a * nM + b] = Mc[(size_t)b * nM + a];
+      }
+    }
+  }
+  // faces: the area vector w S n of the owner's face points (sign of det
+  // dx/dxi times the reference orientation, as the static curved faces) and
+  // the mesh velocity there
+  out->fpool.assign((size_t)M.n_curved_faces * 12 * n2, 0.0);
+  for (int64_t f = 0; f < M.n_faces; ++f) {
+    const dgk::FaceRec& R = M.faces[f];
+    if (R.cgeo < 0) { *err = "a moving mesh needs every face owner curved"; return -7; }
+    const int64_t e0 = M.face_e0[f];
+    const int l0 = M.face_l0[f];
+    const int t0 = in.type[e0];
+    const int64_t* V0 = in.verts + in.off[e0];
+    const int* fv = kFaceVerts[t0][l0];
+    const double* c0r = kRefVerts[t0][fv[0]];
+    const double* c1r = kRefVerts[t0][fv[1]];
+    const double* c2r = kRefVerts[t0][fv[2]];
+    const int nv = kFaceNV[t0][l0];
+    double tsr[3], ttr[3], nref[3], out_ref[3] = {0, 0, 0}, cen[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      tsr[k] = 0.5 * (c1r[k] - c0r[k]);
+      ttr[k] = 0.5 * (c2r[k] - c0r[k]);
+    }
+    cross(tsr, ttr, nref);
+    for (int v = 0; v < kNumVerts[t0]; ++v)
+      for (int k = 0; k < 3; ++k) cen[k] += kRefVerts[t0][v][k] / kNumVerts[t0];
+    for (int i = 0; i < nv; ++i)
+      for (int k = 0; k < 3; ++k) out_ref[k] += kRefVerts[t0][fv[i]][k] / nv - cen[k] / nv;
+    const double orient = (nref[0] * out_ref[0] + nref[1] * out_ref[1] + nref[2] * out_ref[2]) > 0 ? 1.0 : -1.0;
+    double Xrel[24], Urel[24], u0[3];
+    for (int d = 0; d < 3; ++d) u0[d] = vel[3 * V0[0] + d];
+    for (int v = 0; v < kNumVerts[t0]; ++v)
+      for (int d = 0; d < 3; ++d) {
+        Xrel[3 * v + d] = in.xyz[3 * V0[v] + d] - in.xyz[3 * V0[0] + d];
+        Urel[3 * v + d] = vel[3 * V0[v] + d] - u0[d];
+      }
+    const TypeTab& T0 = M.tables.tabs[M.slot_tab[M.slot_of_elem[e0]]];
+    const FaceDesc fd = T0.faces[l0];
+    const double* fw = M.tables.dpool.data() + T0.fw + (size_t)l0 * n2;
+    double* blk = out->fpool.data() + (size_t)3 * R.cgeo;
+    for (int ib = 0; ib < n; ++ib)
+      for (int ia = 0; ia < n; ++ia) {
+        const int p = ia + n * ib;
+        double abc[3];
+        abc[fd.fixed] = fd.end ? 1.0 : -1.0;
+        abc[fd.alpha] = x[ia];
+        abc[fd.beta] = x[ib];
+        double F0[3][3], F1[3][3], xr[3], ur[3];
+        element_map(t0, Xrel, abc[0], abc[1], abc[2], F0, xr);
+        element_map(t0, Urel, abc[0], abc[1], abc[2], F1, ur);
+        double a0[3], a1[3], b0[3], b1[3];
+        for (int d = 0; d < 3; ++d) {
+          a0[d] = F0[d][0] * tsr[0] + F0[d][1] * tsr[1] + F0[d][2] * tsr[2];
+          a1[d] = F1[d][0] * tsr[0] + F1[d][1] * tsr[1] + F1[d][2] * tsr[2];
+          b0[d] = F0[d][0] * ttr[0] + F0[d][1] * ttr[1] + F0[d][2] * ttr[2];
+          b1[d] = F1[d][0] * ttr[0] + F1[d][1] * ttr[1] + F1[d][2] * ttr[2];
+        }
+        double c0[3], c1a[3], c1b[3], c2[3];
+        cross(a0, b0, c0);
+        cross(a0, b1, c1a);
+        cross(a1, b0, c1b);
+        cross(a1, b1, c2);
+        const double sg = (det3(F0) > 0 ? 1.0 : -1.0) * orient * fw[p];
+        for (int d = 0; d < 3; ++d) {
+          blk[(size_t)(0 * 3 + d) * n2 + p] = sg * c0[d];
+          blk[(size_t)(1 * 3 + d) * n2 + p] = sg * (c1a[d] + c1b[d]);
+          blk[(size_t)(2 * 3 + d) * n2 + p] = sg * c2[d];
+          blk[(size_t)(9 + d) * n2 + p] = u0[d] + ur[d];
+        }
+      }
   }
   return 0;
 }

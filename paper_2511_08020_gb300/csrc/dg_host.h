@@ -53,6 +53,9 @@ struct MeshInput {
   // on it); a face with one ghost side and no partner, or with two ghost
   // sides, is dropped.  Null: no ghosts.
   const uint8_t* ghost = nullptr;
+  // moving meshes: every hexahedron, prism and pyramid takes the pointwise
+  // (curved) geometry path, affine or not, since the motion bends it
+  int force_curved = 0;
 };
 
 struct HostMesh {
@@ -127,6 +130,30 @@ uint64_t hilbert_key3(uint32_t x, uint32_t y, uint32_t z, int bits);
 // halo_elems[halo_off[p] .. halo_off[p+1]).  Plain meshes only.
 int partition_plan(const HostMesh& M, int nparts, const double* type_weight, std::vector<int64_t>* part_of_elem,
                    std::vector<int64_t>* halo_off, std::vector<int64_t>* halo_elems, std::string* err);
+
+// Moving meshes (constant vertex velocities, x_v(t) = x_v + t u_v with t
+// measured from the positions the mesh was built from): per element and face
+// the polynomial coefficients in t of the geometry.  dx/dxi = F0 + t F1 at
+// every point, so J (sign times det) is a cubic and the weighted contravariant
+// metric w (da/dxi) (J dxi/dx) a quadratic in t.  Per slot (mpool at
+// slot_moff[s]): [3][9][nQ] metric coefficients of t^0, t^1, t^2,
+// [4][nQ] J coefficients, [3][nQ] mesh velocity, and for prisms and pyramids
+// [4][nM][nM] the coefficients of M = V^T diag(w J) V.  Per curved-owner face
+// (fpool at 12 n^2 times the face's rank among the curved-owner faces, i.e.
+// 3 FaceRec::cgeo): [3][3][n^2] coefficients of the area vector
+// w S n and [3][n^2] the mesh velocity at the owner's face points.
+struct Motion {
+  std::vector<int64_t> slot_moff;
+  std::vector<double> mpool, fpool;
+};
+int build_motion(const HostMesh& M, const MeshInput& in, const double* vel, Motion* out, std::string* err);
+// The geometry of a moving mesh at time t evaluated on the host from the
+// coefficients, in the layouts of HostMesh::cpool (prisms and pyramids:
+// the inverse of sum_k t^k M_k) and HostMesh::fgeo.
+int motion_geometry_at(const HostMesh& M, const Motion& mo, double t, std::vector<double>* cpool,
+                       std::vector<double>* fgeo, std::string* err);
+int64_t motion_block_size(const dgk::TypeTab& T);
+int64_t curved_block_doubles(const dgk::TypeTab& T);   // per-slot doubles of HostMesh::cpool
 
 // Static per-element FP64 work estimate of one stage (initial chunk weights).
 double static_cost(const dgk::TypeTab& t);

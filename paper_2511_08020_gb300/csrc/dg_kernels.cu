@@ -83,6 +83,22 @@ __device__ __forceinline__ void lf_side(const double* U, const double* s, double
   lam = fma(h, sqrt(gamma * p * r), fabs(us));
 }
 
+__device__ __forceinline__ void moving_lf_side(const double* U, const double* s, double h, double sig, double gm1,
+                                               double gamma, double* F, double& lam) {
+  const double r = 1.0 / U[0];
+  const double ms = fma(U[1], s[0], fma(U[2], s[1], U[3] * s[2]));
+  const double us = ms * r;
+  const double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
+  const double p = gm1 * fma(-0.5 * r, m2, U[4]);
+  const double ur = us - sig;
+  F[0] = fma(-sig, U[0], ms);
+  F[1] = fma(U[1], ur, p * s[0]);
+  F[2] = fma(U[2], ur, p * s[1]);
+  F[3] = fma(U[3], ur, p * s[2]);
+  F[4] = fma(U[4], ur, p * us);
+  lam = fma(h, sqrt(gamma * p * r), fabs(ur));
+}
+
 __device__ __forceinline__ void flux_lf_scaled(const double* UL, const double* UR, const double* n, double wS,
                                                double gamma, double* Fs) {
   const double h = 0.5 * wS;
@@ -91,6 +107,23 @@ __device__ __forceinline__ void flux_lf_scaled(const double* UL, const double* U
   double FL[5], FR[5], lamL, lamR;
   lf_side(UL, s, h, gm1, gamma, FL, lamL);
   lf_side(UR, s, h, gm1, gamma, FR, lamR);
+  const double lam = fmax(lamL, lamR);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Fs[v] = fma(lam, UL[v] - UR[v], FL[v] + FR[v]);
+}
+
+// The same flux in a frame moving with normal speed sn = xdot.n at the point
+// (moving meshes): F_s(U) - sig U with sig = (wS/2) sn, and the wave speed
+// from the relative normal velocity, lam_s = max(|m.s/rho - sig| + (wS/2) c).
+__device__ __forceinline__ void flux_lf_moving_scaled(const double* UL, const double* UR, const double* n, double wS,
+                                                      double sn, double gamma, double* Fs) {
+  const double h = 0.5 * wS;
+  const double s[3] = {h * n[0], h * n[1], h * n[2]};
+  const double sig = h * sn;
+  const double gm1 = gamma - 1.0;
+  double FL[5], FR[5], lamL, lamR;
+  moving_lf_side(UL, s, h, sig, gm1, gamma, FL, lamL);
+  moving_lf_side(UR, s, h, sig, gm1, gamma, FR, lamR);
   const double lam = fmax(lamL, lamR);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Fs[v] = fma(lam, UL[v] - UR[v], FL[v] + FR[v]);
@@ -1086,6 +1119,8 @@ __device__ __noinline__ void element_forward_t(const Ctx& c, const TypeTab& T, i
   for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
   // a curved element reads its pointwise metric w (da/dxi)(J dxi/dx) instead
   const double* cm = CURVED ? c.cpool + c.slot_coff[s] : nullptr;
+  // moving mesh: the mesh velocity at the volume points
+  const double* xd = (CURVED && c.mpool) ? c.mpool + c.slot_moff[s] + 31 * nQ : nullptr;
   const double gm1 = c.gamma - 1.0;
   for (int q = lane; q < nQ; q += blockDim.x) {
     double U[5];
@@ -1104,6 +1139,22 @@ __device__ __noinline__ void element_forward_t(const Ctx& c, const TypeTab& T, i
     double u = U[1] * rinv, v = U[2] * rinv, w = U[3] * rinv;
     double p = gm1 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
     double Ep = U[4] + p;
+    if (CURVED && xd) {
+      // moving frame: (F(U) - U xdot) through the metric, W_l = M_l . xdot
+      const double x0 = xd[q], x1 = xd[nQ + q], x2 = xd[2 * nQ + q];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const double Vl = M[l][0] * u + M[l][1] * v + M[l][2] * w;
+        const double Rl = Vl - (M[l][0] * x0 + M[l][1] * x1 + M[l][2] * x2);
+        double* G = bufG + l * 5 * nQ + q;
+        G[0] = Rl * U[0];
+        G[nQ] = Rl * U[1] + p * M[l][0];
+        G[2 * nQ] = Rl * U[2] + p * M[l][1];
+        G[3 * nQ] = Rl * U[3] + p * M[l][2];
+        G[4 * nQ] = Rl * U[4] + Vl * p;
+      }
+      continue;
+    }
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       double Vl = M[l][0] * u + M[l][1] * v + M[l][2] * w;
@@ -1498,7 +1549,10 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
   // M_e^{-1} after it (prism, pyramid).  Tetrahedra are always affine.
   const int64_t coff = ANY ? c.slot_coff[s] : -1;
   const double* cblk = coff >= 0 ? c.cpool + coff : nullptr;
-  const bool dense = cblk && T.type != HEX;
+  // moving mesh: the backward phase returns vol - surf itself (the rate of
+  // the mass-weighted state; the mass matrix is solved separately)
+  const bool moving = ANY && c.mpool != nullptr;
+  const bool dense = cblk && T.type != HEX && (!moving || MODE == kLoad || MODE == kProject);
   if (MODE == kLoad) {
     // b = V^T W J q: pointwise J_q (curved) or the element's constant J
     const int64_t e = c.elem_of_slot[s];
@@ -1535,10 +1589,11 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     nodal_to_modal<ANY>(c, T, bufA, bufG, lane, ep);
     return;
   }
-  element_lift<ANY>(c, T, s, bufA, bufG, lane, c.T, -1.0, (cblk && T.type == HEX) ? cblk + 10 * nQ : nullptr);
+  element_lift<ANY>(c, T, s, bufA, bufG, lane, c.T, -1.0,
+                    (cblk && T.type == HEX && !moving) ? cblk + 10 * nQ : nullptr);
   const double invJ = cblk ? 1.0 : c.geo[s].invJ;
   if (MODE == kBwdRhs) {
-    Epilogue ep{Epilogue::kStore, true, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    Epilogue ep{Epilogue::kStore, !moving, invJ, io.Qout + qoff, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
     if (dense) {
       ep.Md = cblk + 11 * nQ;
       ep.rbuf = bufG + 5 * nQ;
@@ -1546,7 +1601,7 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     nodal_to_modal<ANY>(c, T, bufA, bufG, lane, ep);
     return;
   }
-  Epilogue ep{Epilogue::kRk, true, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
+  Epilogue ep{Epilogue::kRk, !moving, invJ, nullptr, io.Qin + qoff, io.Qout + qoff, io.K + qoff,
               MODE == kBwdRkFwd ? bufG : nullptr, io.a, io.b, io.dt};
   if (dense) {
     ep.Md = cblk + 11 * nQ;
@@ -2140,7 +2195,12 @@ __global__ void face_kernel(Ctx c) {
     }
     const double wS = cg ? c.fgeo[R.cgeo + 3 * n2 + p] : c.dpool[c.tabs[R.owner_tab].fw + R.owner_lf * n2 + p] * R.S;
     double Fs[5];
-    if (c.flux == 0) {
+    if (CURVED && c.fmot && cg) {
+      // moving mesh (LF only): the normal mesh speed at the owner's point
+      const double* xf = c.fmot + 3 * (int64_t)R.cgeo + 9 * n2 + p;
+      const double sn = nrm[0] * xf[0] + nrm[1] * xf[n2] + nrm[2] * xf[2 * n2];
+      flux_lf_moving_scaled(UL, UR, nrm, wS, sn, gamma, Fs);
+    } else if (c.flux == 0) {
       flux_lf_scaled(UL, UR, nrm, wS, gamma, Fs);   // wS F*
     } else if (c.flux == 2) {
       // entropy-conservative: Chandrashekar's F# contracted with wS n

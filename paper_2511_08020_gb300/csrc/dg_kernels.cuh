@@ -81,6 +81,16 @@ struct Ctx {
   const double* cpool;         // per curved slot: [9][nQ] metric, [nQ] J, [nQ] 1/J, (prism, pyramid) [nM][nM] M_e^{-1}
   const double* fgeo;          // per curved-owner face: [4][n^2] normal x, y, z and w S (FaceRec::cgeo)
   const double* snrm;          // curved meshes: per face side [3][n^2] outward normal at 3 * (side offset / 5)
+  // moving meshes (null otherwise): the polynomial-in-t geometry per slot
+  // (mpool at slot_moff: [3][9][nQ] metric, [4][nQ] J, [3][nQ] mesh velocity,
+  // prism / pyramid [4][nM][nM] mass matrix coefficients) and per curved-owner
+  // face (fmot at 3 FaceRec::cgeo: [3][3][n^2] area vector, [3][n^2]
+  // mesh velocity).  With mpool set, the volume flux is F(q) - q xdot, the
+  // face flux the moving-frame LF flux, and the backward phase returns the
+  // rate of the mass-weighted state (no M^{-1}).
+  const double* mpool = nullptr;
+  const int64_t* slot_moff = nullptr;
+  const double* fmot = nullptr;
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
@@ -157,5 +167,18 @@ int face_block_threads(int n);
 cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false,
                                       bool split = false);
 cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false);
+
+// Moving meshes.  Geometry at time t: the curved metric, J and 1/J of every
+// slot and the normals and w S of every curved-owner face, from the
+// coefficients; bit 2 of *status is set where J or S is no longer positive
+// (an element turned inside out).
+void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, int64_t n_slots, int64_t n_faces, int n,
+                            double t, int grid, cudaStream_t st);
+// Per slot: out = M^ in (weight = 1) or out = M^{-1} in (weight = 0), with
+// M^ = sum_k tau_k M_k (hexahedra in their scaled nodal storage: pointwise
+// J^ = sum_k tau_k J_k).  out may alias in.  max_nM: the largest prism /
+// pyramid mode count of the mesh (0 if none).
+cudaError_t launch_moving_mass(const Ctx& c, int64_t n_slots, const double* in, double* out, const double* tau,
+                               int weight, int max_nM, int grid, cudaStream_t st);
 
 }  // namespace dgk
