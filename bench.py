@@ -81,6 +81,26 @@ def element_flops(t, N):
     return 2 * 5 * macs_per_var + pointwise + epilogue
 
 
+def mass_flops(t, N, weight):
+    """FP64 flops of one stage mass-matrix call of one element (weight: the
+    product M^ q, else the solve): J^ = sum_k tau_k J_k per point (7), its
+    weight (1); hexahedra a pointwise scale per point and variable; prisms
+    and pyramids per product the two transforms and the pointwise w J^ (5 per
+    point), per solve two products with their subtraction and three FP64
+    corrections x += z (the FP32 factor and triangular solves not counted)."""
+    n = N + 1
+    nQ = n ** 3
+    if t == 0:
+        return 7 * nQ + 5 * nQ
+    nM = n_modes(t, N)
+    fwd, bwd = transform_macs(t, N)
+    prod = 2 * 5 * (fwd + bwd) + 5 * nQ
+    base = 8 * nQ
+    if weight:
+        return base + prod
+    return base + 2 * (prod + 5 * nM) + 3 * 5 * nM
+
+
 def transform_macs(t, N):
     """MACs per variable of the storage -> nodal and nodal -> storage
     transforms: the c, b, a passes and their transposes for prism, pyramid
@@ -1185,36 +1205,50 @@ def moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, curved_value)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        el = fa = 0.0
+        ph = np.zeros(6)
         with timed_window("moving"):
             e0.record(stream)
             for _ in range(steps):
                 mesh.rk_step(Q, K, dt, 1)
                 if profile:
                     a, b_, _, _ = mesh.phase_times()
-                    el += a
-                    fa += b_
+                    g, m, _, nm = mesh.moving_phase_times()
+                    ph += (a, b_, g, m, nm, 1)
             e1.record(stream)
             torch.cuda.synchronize()
         barrier()
         mesh.set_profiling(False)
-        return max_over_ranks(e0.elapsed_time(e1)), el, fa
+        return max_over_ranks(e0.elapsed_time(e1)), ph
 
     Q = Q0.clone()
     K = torch.empty_like(Q)
-    ms, _, _ = timed(Q, K)
+    ms, _ = timed(Q, K)
     mesh.sync()
     out["value"] = ws * dof * 5 * steps / (ms * 1e-3)
     out["ms_per_step"] = ms / steps
     out["mesh_time_end"] = mesh.time
     out["finite"] = bool(torch.isfinite(Q).all())
     Qp = Q0.clone()
-    msp, el, fa = timed(Qp, K, profile=True)
+    msp, (el, fa, geo, mass, n_mass, _) = timed(Qp, K, profile=True)
     out["element_ms_per_step"] = el / steps
     out["face_ms_per_step"] = fa / steps
-    out["geometry_and_mass_ms_per_step"] = (msp - el - fa) / steps
-    out["geometry_and_mass_share"] = (msp - el - fa) / msp
+    out["geometry_ms_per_step"] = geo / steps
+    out["mass_ms_per_step"] = mass / steps
+    out["mass_share"] = mass / msp
     out["over_static_curved"] = out["value"] / curved_value if curved_value else None
+    # the stage mass kernels: per step one product (M Q at the step's start)
+    # and five solves (stages 2-5 and the step's end), FP64 flops as the
+    # kernels evaluate them (the FP32 Cholesky preconditioner not counted)
+    fl_step = sum(mass_flops(int(t), N_DEG, 1) + 5 * mass_flops(int(t), N_DEG, 0) for t in box.etype)
+    achieved = fl_step / (mass / steps * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    clk = CLOCKS.summary(["moving"])
+    peak = props.multi_processor_count * 2 * 2 * (clk.get("sm_max_mhz") or 2070.0) / 1e6
+    out["clocks"] = clk
+    out["roofline"] = {"bound": "alu", "kernel": "stage mass kernels (FP64 products, FP32-preconditioned solves)",
+                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                       "flops_per_step": fl_step, "mass_launches_per_step": n_mass / steps,
+                       "peak_kind": "derived FP64: SMs x 2 DFMA/clk x 2 flop x max SM clock"}
     return out
 
 

@@ -580,6 +580,11 @@ dg_status dg_rebalance_stats(const dg_mesh* mesh, int64_t* checks, int64_t* reba
  * face-phase ms, number of element phases, number of face phases. */
 dg_status dg_set_profiling(dg_mesh* mesh, int on);
 dg_status dg_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream);
+/* Moving meshes, with profiling on: for the most recent dg_rk_step / dg_rhs
+ * call, host [4]: total ms of the per-stage geometry kernels, total ms of the
+ * stage mass-matrix kernels (products and solves), and their launch counts
+ * (events around each; synchronises `stream`). */
+dg_status dg_moving_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream);
 
 /* Synchronise `stream` and report sticky device errors (DG_ERR_NONFINITE). */
 dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream);

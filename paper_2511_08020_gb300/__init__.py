@@ -94,6 +94,7 @@ _SIGS = {
     "dg_mesh_time": [_P, _P],
     "dg_set_mesh_time": [_P, ctypes.c_double],
     "dg_geometry_at": [ctypes.POINTER(MeshDesc), _P, ctypes.c_double, _P, _P, _P, _P],
+    "dg_moving_phase_times": [_P, _P, _P],
 }
 
 _lib = None
@@ -481,6 +482,14 @@ class MovingMesh(Mesh):
 
     def set_time(self, t):
         _check(load().dg_set_mesh_time(self.handle, float(t)))
+
+    def moving_phase_times(self, stream=None):
+        """(geometry ms, mass-matrix ms, geometry launches, mass launches) of
+        the last call (profiling on)."""
+        import numpy as np
+        out = np.zeros(4)
+        _check(load().dg_moving_phase_times(self.handle, _ptr(out), _stream(stream)))
+        return float(out[0]), float(out[1]), int(out[2]), int(out[3])
 
 
 class Part(Mesh):

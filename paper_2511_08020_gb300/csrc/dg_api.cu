@@ -71,9 +71,9 @@ struct dg_mesh {
   // mesh time, the mass-weighted state and the stage state of dg_rk_step
   bool moving = false;
   double t_mesh = 0.0;
-  int max_nM_dense = 0;   // largest prism / pyramid mode count (shared memory of the mass kernel)
-  int64_t* d_slot_moff = nullptr;
+  int64_t *d_slot_moff = nullptr, *d_slot_mmoff = nullptr;
   double *d_mpool = nullptr, *d_fmot = nullptr, *d_Ut = nullptr, *d_S = nullptr;
+  float* d_mk32 = nullptr;
   double gamma = 1.4;
   int scheduler = DG_SCHED_BALANCED;
   double threshold = 0.1;
@@ -288,6 +288,7 @@ struct dg_mesh {
   int ev_used[2] = {0, 0};
   int pool = 1;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_elem[2], ev_face[2];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_geom, ev_mass;   // moving meshes (direct launches)
   int last_pool = -1;
 
   cudaEvent_t next_event() {
@@ -303,6 +304,10 @@ struct dg_mesh {
     ev_used[pool] = 0;
     ev_elem[pool].clear();
     ev_face[pool].clear();
+    if (which == 1) {
+      ev_geom.clear();
+      ev_mass.clear();
+    }
     last_pool = which;
   }
   template <class F>
@@ -316,6 +321,17 @@ struct dg_mesh {
     f();
     cudaEventRecordWithFlags(b, st, flags);
     (elem ? ev_elem[pool] : ev_face[pool]).push_back({a, b});
+  }
+  // the same around a moving mesh's geometry (mass = false) or mass kernels
+  template <class F>
+  auto timed_moving(bool mass, cudaStream_t st, F&& f) -> decltype(f()) {
+    if (!profiling) return f();
+    cudaEvent_t a = next_event(), b = next_event();
+    cudaEventRecord(a, st);
+    auto r = f();
+    cudaEventRecord(b, st);
+    (mass ? ev_mass : ev_geom).push_back({a, b});
+    return r;
   }
 
   dgk::Ctx ctx() const {
@@ -364,6 +380,8 @@ struct dg_mesh {
       c.mpool = d_mpool;
       c.slot_moff = d_slot_moff;
       c.fmot = d_fmot;
+      c.mk32 = d_mk32;
+      c.slot_mmoff = d_slot_mmoff;
     }
     return c;
   }
@@ -371,10 +389,33 @@ struct dg_mesh {
   // ---- moving meshes
   int grid_slots() const { return (int)std::max<int64_t>(1, std::min<int64_t>(h.n_elems, (int64_t)num_sms * 8)); }
   void moving_geometry(double t, cudaStream_t st) {
-    dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, h.n_elems, h.n_faces, h.n, t, grid_slots(), st);
+    timed_moving(false, st, [&] {
+      dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, h.n_elems, h.n_faces, h.n, t, grid_slots(), st);
+      return 0;
+    });
   }
+  // one launch per element type, each with the shared memory its own mass
+  // matrices need
   cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st) {
-    return dgk::launch_moving_mass(ctx(), h.n_elems, in, out, tau, weight, max_nM_dense, grid_slots(), st);
+    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, tau, weight, st); });
+  }
+  cudaError_t moving_mass_launches(const double* in, double* out, const double tau[4], int weight, cudaStream_t st) {
+    const dgk::Ctx c = ctx();
+    for (int t = 0; t < 3; ++t) {
+      const int64_t cnt = (int64_t)h.type_slots[t].size();
+      if (!cnt) continue;
+      int nM = 0, nQ = 0;
+      if (t != dgk::HEX)
+        for (const auto& T : h.tables.tabs)
+          if (T.type == t) {
+            nM = std::max(nM, T.nM);
+            nQ = std::max(nQ, T.nQ);
+          }
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cnt, (int64_t)num_sms * 8));
+      cudaError_t e = dgk::launch_moving_mass(c, d_type_slots[t], cnt, in, out, tau, weight, nM, nQ, grid, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   static void powers(double t, double tau[4]) {
     tau[0] = 1.0;
@@ -414,8 +455,10 @@ struct dg_mesh {
       for (int s = 0; s < 5; ++s) {
         const double ts = t + kLsC[s] * dt;
         moving_geometry(ts, st);
-        if ((e = moving_mass(d_Ut, d_S, y, 0, st)) != cudaSuccess) return e;
-        dgk::StageArgs f{d_S, nullptr, nullptr, 0.0, 0.0, 0.0};
+        // the first stage's state is Q itself (its solve would undo the
+        // product above up to rounding)
+        if (s > 0 && (e = moving_mass(d_Ut, d_S, y, 0, st)) != cudaSuccess) return e;
+        dgk::StageArgs f{s > 0 ? d_S : Q, nullptr, nullptr, 0.0, 0.0, 0.0};
         element_phase(dgk::kFwd, f, st);
         face_phase(st);
         dgk::StageArgs a{d_Ut, d_Ut, K, kLsA[s], kLsB[s], dt};
@@ -773,7 +816,8 @@ struct dg_mesh {
                     d_elem_of_slot, d_elem_qoff, d_elem_voff, d_geo, d_H, d_T, d_faces, d_fblocks, d_perms, d_dense, d_status,
                     d_cost, d_smns, d_counters, d_chunks_static, d_chunks_weighted, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
-                    d_slot_coff, d_cpool, d_fgeo, d_snrm, d_slot_moff, d_mpool, d_fmot, d_Ut, d_S};
+                    d_slot_coff, d_cpool, d_fgeo, d_snrm, d_slot_moff, d_mpool, d_fmot, d_Ut, d_S, d_slot_mmoff,
+                    d_mk32};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -862,8 +906,8 @@ dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_v
   size_t max_nM = 0;
   for (const auto& T : m->h.tables.tabs)
     if (T.type == dgk::PRISM || T.type == dgk::PYR) max_nM = std::max<size_t>(max_nM, (size_t)T.nM);
-  if (r == 0 && sizeof(double) * (max_nM * max_nM + 5 * max_nM) > 227 * 1024) {
-    err = "the mass matrix of this degree's prisms or pyramids exceeds one block's shared memory";
+  if (r == 0 && max_nM > 128) {
+    err = "the stage mass solve covers prisms and pyramids of up to 128 modes (N <= 5)";
     r = DG_ERR_UNSUPPORTED;
   }
   if (r != 0) {
@@ -874,9 +918,12 @@ dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_v
   st = create_device_mesh(m, desc, stream, &made);
   if (st != DG_OK) return st;
   made->moving = true;
-  made->max_nM_dense = (int)max_nM;
   const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(1, made->h.n_dof);
+  std::vector<float> mk32(mo.mmat.begin(), mo.mmat.end());
+  if (mk32.empty()) mk32.push_back(0.0f);
   cudaError_t e = upload(&made->d_slot_moff, mo.slot_moff);
+  if (e == cudaSuccess) e = upload(&made->d_slot_mmoff, mo.slot_mmoff);
+  if (e == cudaSuccess) e = upload(&made->d_mk32, mk32);
   if (e == cudaSuccess) e = upload(&made->d_mpool, mo.mpool);
   if (e == cudaSuccess) e = upload(&made->d_fmot, mo.fpool);
   if (e == cudaSuccess) e = cudaMalloc(&made->d_Ut, bytes);
@@ -2150,6 +2197,22 @@ dg_status dg_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream) {
   const int p = mesh->last_pool;
   for (int k = 0; k < 2; ++k) {
     const auto& v = k == 0 ? mesh->ev_elem[p] : mesh->ev_face[p];
+    for (const auto& ab : v) {
+      float ms = 0.f;
+      DG_CUDA(cudaEventElapsedTime(&ms, ab.first, ab.second));
+      out[k] += ms;
+    }
+    out[2 + k] = (double)v.size();
+  }
+  return DG_OK;
+}
+
+dg_status dg_moving_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream) {
+  if (!mesh || !out) return fail(DG_ERR_ARG, "null argument");
+  DG_CUDA(cudaStreamSynchronize(stream));
+  for (int i = 0; i < 4; ++i) out[i] = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    const auto& v = k == 0 ? mesh->ev_geom : mesh->ev_mass;
     for (const auto& ab : v) {
       float ms = 0.f;
       DG_CUDA(cudaEventElapsedTime(&ms, ab.first, ab.second));

@@ -1512,7 +1512,7 @@ int motion_geometry_at(const HostMesh& M, const Motion& mo, double t, std::vecto
     if (T.type == dgk::PRISM || T.type == dgk::PYR) {
       std::vector<double> Me((size_t)nM * nM, 0.0);
       for (int k = 0; k < 4; ++k)
-        for (size_t w = 0; w < Me.size(); ++w) Me[w] += tk[k] * m[(size_t)34 * nQ + (size_t)k * nM * nM + w];
+        for (size_t w = 0; w < Me.size(); ++w) Me[w] += tk[k] * mo.mmat[(size_t)mo.slot_mmoff[s] + (size_t)k * nM * nM + w];
       if (!spd_inverse(nM, Me.data(), cb + (size_t)11 * nQ)) { *err = "mass matrix not positive definite"; return -2; }
     }
   }
@@ -1535,9 +1535,7 @@ int motion_geometry_at(const HostMesh& M, const Motion& mo, double t, std::vecto
 
 int64_t curved_block_doubles(const dgk::TypeTab& T) { return curved_block_size(T); }
 
-int64_t motion_block_size(const dgk::TypeTab& T) {
-  return 34 * (int64_t)T.nQ + ((T.type == dgk::PRISM || T.type == dgk::PYR) ? 4 * (int64_t)T.nM * T.nM : 0);
-}
+int64_t motion_block_size(const dgk::TypeTab& T) { return 34 * (int64_t)T.nQ; }
 
 int build_motion(const HostMesh& M, const MeshInput& in, const double* vel, Motion* out, std::string* err) {
   const int64_t E = M.n_elems;
@@ -1547,12 +1545,19 @@ int build_motion(const HostMesh& M, const MeshInput& in, const double* vel, Moti
     if (M.slot_type[s] == dgk::TET) { *err = "moving meshes cover hexahedra, prisms and pyramids"; return -7; }
   if (M.n_curved != E) { *err = "a moving mesh needs every element on the curved path"; return -7; }
   out->slot_moff.assign(E, -1);
-  int64_t total = 0;
+  out->slot_mmoff.assign(E, -1);
+  int64_t total = 0, mtotal = 0;
   for (int64_t s = 0; s < E; ++s) {
+    const TypeTab& T = M.tables.tabs[M.slot_tab[s]];
     out->slot_moff[s] = total;
-    total += motion_block_size(M.tables.tabs[M.slot_tab[s]]);
+    total += motion_block_size(T);
+    if (T.type == dgk::PRISM || T.type == dgk::PYR) {
+      out->slot_mmoff[s] = mtotal;
+      mtotal += 4 * (int64_t)T.nM * T.nM;
+    }
   }
   out->mpool.assign((size_t)total, 0.0);
+  out->mmat.assign((size_t)mtotal, 0.0);
   std::vector<double> Vt[4];
   for (int t = 1; t <= 2; ++t)
     if (M.type_count[t]) Vt[t] = vandermonde(t, M.N, x);
@@ -1603,7 +1608,7 @@ int build_motion(const HostMesh& M, const MeshInput& in, const double* vel, Moti
     if (type == dgk::PRISM || type == dgk::PYR) {
       const double* Vq = Vt[type].data();
       for (int c = 0; c < 4; ++c) {
-        double* Mc = blk + (size_t)34 * nQ + (size_t)c * nM * nM;
+        double* Mc = out->mmat.data() + out->slot_mmoff[s] + (size_t)c * nM * nM;
         for (int q = 0; q < nQ; ++q) {
           const double* vq = Vq + (size_t)q * nM;
           const double w = wq[q] * Jk[(size_t)c * nQ + q];

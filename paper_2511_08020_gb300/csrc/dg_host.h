@@ -137,14 +137,14 @@ int partition_plan(const HostMesh& M, int nparts, const double* type_weight, std
 // every point, so J (sign times det) is a cubic and the weighted contravariant
 // metric w (da/dxi) (J dxi/dx) a quadratic in t.  Per slot (mpool at
 // slot_moff[s]): [3][9][nQ] metric coefficients of t^0, t^1, t^2,
-// [4][nQ] J coefficients, [3][nQ] mesh velocity, and for prisms and pyramids
-// [4][nM][nM] the coefficients of M = V^T diag(w J) V.  Per curved-owner face
-// (fpool at 12 n^2 times the face's rank among the curved-owner faces, i.e.
-// 3 FaceRec::cgeo): [3][3][n^2] coefficients of the area vector
-// w S n and [3][n^2] the mesh velocity at the owner's face points.
+// [4][nQ] J coefficients, [3][nQ] mesh velocity; for prisms and pyramids
+// (mmat at slot_mmoff[s], -1 for a hexahedron) [4][nM][nM] the coefficients
+// of M = V^T diag(w J) V.  Per curved-owner face (fpool at
+// 3 FaceRec::cgeo): [3][3][n^2] coefficients of the area vector w S n and
+// [3][n^2] the mesh velocity at the owner's face points.
 struct Motion {
-  std::vector<int64_t> slot_moff;
-  std::vector<double> mpool, fpool;
+  std::vector<int64_t> slot_moff, slot_mmoff;
+  std::vector<double> mpool, mmat, fpool;
 };
 int build_motion(const HostMesh& M, const MeshInput& in, const double* vel, Motion* out, std::string* err);
 // The geometry of a moving mesh at time t evaluated on the host from the

@@ -2705,6 +2705,228 @@ __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __
   for (int w = lane; w < 5 * nM; w += 32) b[w] = a[w];
 }
 
+// ------------------------------------------------------------------ moving meshes: stage mass matrices
+//
+// M^ = V^T diag(w J^) V with J^ = sum_k tau_k J_k per element (the stage
+// value of J of a moving mesh).  Hexahedra hold s = W^{1/2} V q, so M^ q in
+// their storage is J^ s pointwise and the solve a pointwise division.
+// Prisms and pyramids: the product M^ x runs as the two sum-factorised
+// transforms of the element kernel around the pointwise w J^ (FP64).  The
+// solve is iterative refinement in FP64 around an FP32 Cholesky factor of the
+// diagonally scaled S M^ S (S = diag(M^)^{-1/2}, condition number near
+// max J / min J): x0 = 0, r = b; three times z = S (L L^T)^{-1} S r in FP32,
+// x += z, r = b - M^ x in FP64.  Each FP32 solve gains about six digits,
+// so the third correction leaves the FP64 rounding of M^ x; FP64 work per
+// solve is two products, against nM^3 / 3 FP64 flops for an FP64 Cholesky
+// (FP64 issues at 1/64 of the FP32 rate on this part).
+//
+// smem: x, b, r [5][nM] and wJ [nQ] (FP64); bufA, bufB [5][nQ] (FP64,
+// transforms); L [nM][nM], s, rdiag [nM] (FP32).  Block: 5 warps.
+constexpr int kMassThreads = 160;
+constexpr int kMassRows = 4;   // rows per lane in the warp solves: nM <= 128
+
+__host__ __device__ __forceinline__ size_t mass_smem_doubles(int nM, int nQ) {
+  return 15 * (size_t)nM + (size_t)nQ + 10 * (size_t)nQ;
+}
+
+// r = b - M^ x (or r = M^ x when b is null); tid = threadIdx.x
+__device__ void mass_product(const Ctx& c, const TypeTab& T, const double* x, const double* wJ, const double* b,
+                             double* r, double* bufA, double* bufB, int tid) {
+  const int nQ = T.nQ, nM = T.nM;
+  modal_to_nodal_passes(c, T, x, bufA, bufB, tid);
+  for (int w = tid; w < 5 * nQ; w += blockDim.x) bufA[w] *= wJ[w % nQ];
+  __syncthreads();
+  Epilogue ep{Epilogue::kStore, false, 1.0, r, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+  nodal_to_modal_t<false>(c, T, bufA, bufB, tid, ep);
+  if (b) {
+    for (int w = tid; w < 5 * nM; w += blockDim.x) r[w] = b[w] - r[w];
+    __syncthreads();
+  }
+}
+
+// x += S (L L^T)^{-1} S r: warp 0 solves for the five variables at once
+// (ROWS rows per lane in registers, one shuffle per variable and pivot, the
+// rows already solved masked by a zero coefficient instead of a branch);
+// the other warps wait at the closing barrier.
+template <int ROWS>
+__device__ void mass_correct_t(const float* L, const float* sc, const float* rdiag, const double* r, double* x,
+                               int nM) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float y[5][ROWS], sl[ROWS];
+#pragma unroll
+    for (int m = 0; m < ROWS; ++m) {
+      const int i = lane + 32 * m;
+      sl[m] = i < nM ? sc[min(i, nM - 1)] : 0.0f;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) y[v][m] = i < nM ? sl[m] * (float)r[v * nM + min(i, nM - 1)] : 0.0f;
+    }
+    // L y = S r
+#pragma unroll
+    for (int m = 0; m < ROWS; ++m) {
+      const int jend = min(32, nM - 32 * m);
+      for (int jj = 0; jj < jend; ++jj) {
+        const int j = 32 * m + jj;
+        const float rdj = rdiag[j];
+        float yj[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          yj[v] = __shfl_sync(0xffffffffu, y[v][m], jj) * rdj;
+          y[v][m] = lane == jj ? yj[v] : y[v][m];
+        }
+#pragma unroll
+        for (int m2 = m; m2 < ROWS; ++m2) {
+          const int i = lane + 32 * m2;
+          const float lij = (i > j && i < nM) ? L[min(i, nM - 1) * nM + j] : 0.0f;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) y[v][m2] = fmaf(-lij, yj[v], y[v][m2]);
+        }
+      }
+    }
+    // L^T z = y
+#pragma unroll
+    for (int m = ROWS - 1; m >= 0; --m) {
+      const int jend = min(32, nM - 32 * m);
+      for (int jj = jend - 1; jj >= 0; --jj) {
+        const int j = 32 * m + jj;
+        const float rdj = rdiag[j];
+        float zj[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          zj[v] = __shfl_sync(0xffffffffu, y[v][m], jj) * rdj;
+          y[v][m] = lane == jj ? zj[v] : y[v][m];
+        }
+#pragma unroll
+        for (int m2 = 0; m2 <= m; ++m2) {
+          const int i = lane + 32 * m2;
+          const float lji = i < j ? L[j * nM + min(i, nM - 1)] : 0.0f;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) y[v][m2] = fmaf(-lji, zj[v], y[v][m2]);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < ROWS; ++m) {
+      const int i = lane + 32 * m;
+      if (i < nM) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) x[v * nM + i] += (double)(sl[m] * y[v][m]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void mass_correct(const float* L, const float* sc, const float* rdiag, const double* r,
+                                             double* x, int nM) {
+  if (nM <= 32) mass_correct_t<1>(L, sc, rdiag, r, x, nM);
+  else if (nM <= 64) mass_correct_t<2>(L, sc, rdiag, r, x, nM);
+  else if (nM <= 96) mass_correct_t<3>(L, sc, rdiag, r, x, nM);
+  else mass_correct_t<4>(L, sc, rdiag, r, x, nM);
+}
+
+__global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
+                                                                   const double* in, double* out, double t0, double t1,
+                                                                   double t2, double t3, int weight, int max_nM,
+                                                                   int max_nQ) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
+  double* x = sm;
+  double* b = x + 5 * max_nM;
+  double* r = b + 5 * max_nM;
+  double* wJ = r + 5 * max_nM;
+  double* bufA = wJ + max_nQ;
+  double* bufB = bufA + 5 * max_nQ;
+  float* L = reinterpret_cast<float*>(bufB + 5 * max_nQ);
+  float* sc = L + max_nM * max_nM;
+  float* rdiag = sc + max_nM;
+  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t s = list[e];
+    const TypeTab& T = c.tabs[c.slot_tab[s]];
+    const int nQ = T.nQ, nM = T.nM;
+    const int64_t qoff = c.slot_qoff[s];
+    const double* m = c.mpool + c.slot_moff[s];
+    if (T.type == HEX) {
+      for (int w = tid; w < 5 * nQ; w += bd) {
+        const int q = w % nQ;
+        const double J = fma(t3, m[30 * nQ + q], fma(t2, m[29 * nQ + q], fma(t1, m[28 * nQ + q], t0 * m[27 * nQ + q])));
+        const double v = in[qoff + w];
+        out[qoff + w] = weight ? v * J : v / J;
+      }
+      continue;   // block-uniform branch, no shared memory used
+    }
+    const double* W = c.dpool + T.W;
+    for (int q = tid; q < nQ; q += bd)
+      wJ[q] = W[q] * fma(t3, m[30 * nQ + q], fma(t2, m[29 * nQ + q], fma(t1, m[28 * nQ + q], t0 * m[27 * nQ + q])));
+    for (int w = tid; w < 5 * nM; w += bd) b[w] = in[qoff + w];
+    __syncthreads();
+    if (weight) {
+      mass_product(c, T, b, wJ, nullptr, r, bufA, bufB, tid);
+      for (int w = tid; w < 5 * nM; w += bd) out[qoff + w] = r[w];
+      __syncthreads();
+      continue;
+    }
+    // FP32 S M^ S from the FP32 coefficients (lower triangle)
+    const float* Mk = c.mk32 + c.slot_mmoff[s];
+    const int nn = nM * nM;
+    const float f0 = (float)t0, f1 = (float)t1, f2 = (float)t2, f3 = (float)t3;
+    for (int a = tid; a < nM; a += bd) {
+      const int w = a * nM + a;
+      sc[a] = rsqrtf(fmaf(f3, Mk[3 * nn + w], fmaf(f2, Mk[2 * nn + w], fmaf(f1, Mk[nn + w], f0 * Mk[w]))));
+    }
+    __syncthreads();
+    for (int w = tid; w < nn; w += bd) {
+      const int a = w / nM, k = w - a * nM;
+      if (k > a) continue;
+      L[w] = sc[a] * sc[k] * fmaf(f3, Mk[3 * nn + w], fmaf(f2, Mk[2 * nn + w], fmaf(f1, Mk[nn + w], f0 * Mk[w])));
+    }
+    __syncthreads();
+    // right-looking Cholesky, two columns per pass: columns j and j+1, then
+    // the rank-2 update of the trailing lower triangle (its pairs numbered
+    // row by row so every lane takes one); L's diagonal is kept as its
+    // reciprocal in rdiag
+    for (int j = 0; j < nM; j += 2) {
+      const bool two = j + 1 < nM;
+      const float rd = rsqrtf(L[j * nM + j]);
+      for (int i = j + 1 + tid; i < nM; i += bd) L[i * nM + j] *= rd;
+      if (tid == 0) rdiag[j] = rd;
+      __syncthreads();
+      if (two) {
+        const float l = L[(j + 1) * nM + j];
+        for (int i = j + 1 + tid; i < nM; i += bd) L[i * nM + j + 1] = fmaf(-L[i * nM + j], l, L[i * nM + j + 1]);
+        __syncthreads();
+        const float rd1 = rsqrtf(L[(j + 1) * nM + j + 1]);
+        for (int i = j + 2 + tid; i < nM; i += bd) L[i * nM + j + 1] *= rd1;
+        if (tid == 0) rdiag[j + 1] = rd1;
+        __syncthreads();
+      }
+      // trailing rows by warp, their columns by lane (the row's two
+      // multipliers loaded once per row)
+      const int j0 = j + (two ? 2 : 1);
+      for (int i = j0 + warp; i < nM; i += nwarps) {
+        const float li0 = L[i * nM + j], li1 = two ? L[i * nM + j + 1] : 0.0f;
+        for (int k = j0 + lane; k <= i; k += 32) {
+          float v = fmaf(-li0, L[k * nM + j], L[i * nM + k]);
+          if (two) v = fmaf(-li1, L[k * nM + j + 1], v);
+          L[i * nM + k] = v;
+        }
+      }
+      __syncthreads();
+    }
+    for (int w = tid; w < 5 * nM; w += bd) {
+      x[w] = 0.0;
+      r[w] = b[w];
+    }
+    __syncthreads();
+    for (int it = 0; it < 3; ++it) {
+      mass_correct(L, sc, rdiag, r, x, nM);
+      if (it < 2) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
+    }
+    for (int w = tid; w < 5 * nM; w += bd) out[qoff + w] = x[w];
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 int element_smem_bytes(int nQmax, int) { return 20 * nQmax * (int)sizeof(double); }
@@ -2924,5 +3146,20 @@ void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int
   permute_kernel<<<(unsigned)blocks, 32 * wpb, 0, st>>>(c, src, dst, E, to_storage);
 }
 
+
+cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
+                               const double* tau, int weight, int max_nM, int max_nQ, int grid, cudaStream_t st) {
+  if (max_nM > 32 * kMassRows) return cudaErrorInvalidValue;
+  size_t bytes = 0;
+  if (max_nM > 0)
+    bytes = sizeof(double) * mass_smem_doubles(max_nM, max_nQ) + sizeof(float) * ((size_t)max_nM * max_nM + 2 * (size_t)max_nM);
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(moving_mass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  moving_mass_kernel<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, tau[0], tau[1], tau[2], tau[3],
+                                                         weight, max_nM, max_nQ);
+  return cudaGetLastError();
+}
 
 }  // namespace dgk

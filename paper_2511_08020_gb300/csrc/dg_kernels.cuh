@@ -82,15 +82,18 @@ struct Ctx {
   const double* fgeo;          // per curved-owner face: [4][n^2] normal x, y, z and w S (FaceRec::cgeo)
   const double* snrm;          // curved meshes: per face side [3][n^2] outward normal at 3 * (side offset / 5)
   // moving meshes (null otherwise): the polynomial-in-t geometry per slot
-  // (mpool at slot_moff: [3][9][nQ] metric, [4][nQ] J, [3][nQ] mesh velocity,
-  // prism / pyramid [4][nM][nM] mass matrix coefficients) and per curved-owner
-  // face (fmot at 3 FaceRec::cgeo: [3][3][n^2] area vector, [3][n^2]
-  // mesh velocity).  With mpool set, the volume flux is F(q) - q xdot, the
-  // face flux the moving-frame LF flux, and the backward phase returns the
-  // rate of the mass-weighted state (no M^{-1}).
+  // (mpool at slot_moff: [3][9][nQ] metric, [4][nQ] J, [3][nQ] mesh
+  // velocity), per prism and pyramid the mass matrix coefficients
+  // [4][nM][nM] rounded to FP32 (mk32 at slot_mmoff: the preconditioner of
+  // the stage solves) and per curved-owner face (fmot at 3 FaceRec::cgeo:
+  // [3][3][n^2] area vector, [3][n^2] mesh velocity).  With mpool set, the
+  // volume flux is F(q) - q xdot, the face flux the moving-frame LF flux, and
+  // the backward phase returns the rate of the mass-weighted state (no M^{-1}).
   const double* mpool = nullptr;
   const int64_t* slot_moff = nullptr;
   const double* fmot = nullptr;
+  const float* mk32 = nullptr;
+  const int64_t* slot_mmoff = nullptr;
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
@@ -174,11 +177,12 @@ cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* bl
 // (an element turned inside out).
 void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, int64_t n_slots, int64_t n_faces, int n,
                             double t, int grid, cudaStream_t st);
-// Per slot: out = M^ in (weight = 1) or out = M^{-1} in (weight = 0), with
-// M^ = sum_k tau_k M_k (hexahedra in their scaled nodal storage: pointwise
-// J^ = sum_k tau_k J_k).  out may alias in.  max_nM: the largest prism /
-// pyramid mode count of the mesh (0 if none).
-cudaError_t launch_moving_mass(const Ctx& c, int64_t n_slots, const double* in, double* out, const double* tau,
-                               int weight, int max_nM, int grid, cudaStream_t st);
+// Per slot of list[0 .. n_slots): out = M^ in (weight = 1) or out = M^{-1} in
+// (weight = 0), with M^ = V^T diag(w J^) V and J^ = sum_k tau_k J_k
+// (hexahedra, in their scaled nodal storage: pointwise J^).  out may alias in.
+// max_nM / max_nQ: the largest prism / pyramid mode and point counts among
+// the listed slots (0 if none: shared memory).
+cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
+                               const double* tau, int weight, int max_nM, int max_nQ, int grid, cudaStream_t st);
 
 }  // namespace dgk
