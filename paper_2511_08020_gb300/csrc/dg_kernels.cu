@@ -2900,15 +2900,35 @@ __global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const 
         if (tid == 0) rdiag[j + 1] = rd1;
         __syncthreads();
       }
-      // trailing rows by warp, their columns by lane (the row's two
-      // multipliers loaded once per row)
+      // trailing rows by warp, four rows at a time (independent chains that
+      // share the column loads), their columns by lane; each row's two
+      // multipliers are loaded once
       const int j0 = j + (two ? 2 : 1);
-      for (int i = j0 + warp; i < nM; i += nwarps) {
-        const float li0 = L[i * nM + j], li1 = two ? L[i * nM + j + 1] : 0.0f;
-        for (int k = j0 + lane; k <= i; k += 32) {
-          float v = fmaf(-li0, L[k * nM + j], L[i * nM + k]);
-          if (two) v = fmaf(-li1, L[k * nM + j + 1], v);
-          L[i * nM + k] = v;
+      for (int i = j0 + warp; i < nM; i += 4 * nwarps) {
+        float l0[4], l1[4];
+        int last = i;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int ig = min(i + g * nwarps, nM - 1);
+          l0[g] = L[ig * nM + j];
+          l1[g] = two ? L[ig * nM + j + 1] : 0.0f;
+          if (i + g * nwarps < nM) last = i + g * nwarps;
+        }
+        for (int k = j0 + lane; k <= last; k += 32) {
+          const float c0 = L[k * nM + j], c1 = two ? L[k * nM + j + 1] : 0.0f;
+          float v[4];
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int ig = i + g * nwarps;
+            v[g] = (ig < nM && k <= ig) ? L[min(ig, nM - 1) * nM + k] : 0.0f;
+          }
+#pragma unroll
+          for (int g = 0; g < 4; ++g) v[g] = fmaf(-l1[g], c1, fmaf(-l0[g], c0, v[g]));
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int ig = i + g * nwarps;
+            if (ig < nM && k <= ig) L[ig * nM + k] = v[g];
+          }
         }
       }
       __syncthreads();
