@@ -396,10 +396,12 @@ struct dg_mesh {
   }
   // one launch per element type, each with the shared memory its own mass
   // matrices need
-  cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st) {
-    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, tau, weight, st); });
+  cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st,
+                          const double* x0 = nullptr) {
+    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, x0, tau, weight, st); });
   }
-  cudaError_t moving_mass_launches(const double* in, double* out, const double tau[4], int weight, cudaStream_t st) {
+  cudaError_t moving_mass_launches(const double* in, double* out, const double* x0, const double tau[4], int weight,
+                                   cudaStream_t st) {
     const dgk::Ctx c = ctx();
     for (int t = 0; t < 3; ++t) {
       const int64_t cnt = (int64_t)h.type_slots[t].size();
@@ -412,7 +414,7 @@ struct dg_mesh {
             nQ = std::max(nQ, T.nQ);
           }
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cnt, (int64_t)num_sms * 8));
-      cudaError_t e = dgk::launch_moving_mass(c, d_type_slots[t], cnt, in, out, tau, weight, nM, nQ, grid, st);
+      cudaError_t e = dgk::launch_moving_mass(c, d_type_slots[t], cnt, in, out, x0, tau, weight, nM, nQ, grid, st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -457,7 +459,8 @@ struct dg_mesh {
         moving_geometry(ts, st);
         // the first stage's state is Q itself (its solve would undo the
         // product above up to rounding)
-        if (s > 0 && (e = moving_mass(d_Ut, d_S, y, 0, st)) != cudaSuccess) return e;
+        // later stages start their solve from the previous stage's state
+        if (s > 0 && (e = moving_mass(d_Ut, d_S, y, 0, st, s == 1 ? Q : d_S)) != cudaSuccess) return e;
         dgk::StageArgs f{s > 0 ? d_S : Q, nullptr, nullptr, 0.0, 0.0, 0.0};
         element_phase(dgk::kFwd, f, st);
         face_phase(st);
@@ -469,7 +472,7 @@ struct dg_mesh {
           y[k] += kLsB[s] * Ky[k];
         }
       }
-      if ((e = moving_mass(d_Ut, Q, y, 0, st)) != cudaSuccess) return e;
+      if ((e = moving_mass(d_Ut, Q, y, 0, st, d_S)) != cudaSuccess) return e;
       t_mesh = t + dt;
     }
     return cudaGetLastError();

@@ -2714,16 +2714,22 @@ __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __
 // transforms of the element kernel around the pointwise w J^ (FP64).  The
 // solve is iterative refinement in FP64 around an FP32 Cholesky factor of the
 // diagonally scaled S M^ S (S = diag(M^)^{-1/2}, condition number near
-// max J / min J): x0 = 0, r = b; three times z = S (L L^T)^{-1} S r in FP32,
+// max J / min J): x = 0, r = b; three times z = S (L L^T)^{-1} S r in FP32,
 // x += z, r = b - M^ x in FP64.  Each FP32 solve gains about six digits,
-// so the third correction leaves the FP64 rounding of M^ x; FP64 work per
-// solve is two products, against nM^3 / 3 FP64 flops for an FP64 Cholesky
-// (FP64 issues at 1/64 of the FP32 rate on this part).
+// so the third correction leaves the FP64 rounding of M^ x.  Started from a
+// nearby state x0 instead (the previous stage's, about 1e-3 away), two
+// corrections reach the same.  FP64 work per solve is two products, against
+// nM^3 / 3 FP64 flops for an FP64 Cholesky (FP64 issues at 1/64 of the FP32
+// rate on this part).
 //
 // smem: x, b, r [5][nM] and wJ [nQ] (FP64); bufA, bufB [5][nQ] (FP64,
-// transforms); L [nM][nM], s, rdiag [nM] (FP32).  Block: 5 warps.
+// transforms); L (packed lower triangle), s, rdiag [nM] (FP32).  Block: 5
+// warps.
 constexpr int kMassThreads = 160;
 constexpr int kMassRows = 4;   // rows per lane in the warp solves: nM <= 128
+
+// the FP32 factor is kept packed: row i of the lower triangle at i (i + 1) / 2
+__host__ __device__ __forceinline__ int lro(int i) { return i * (i + 1) / 2; }
 
 __host__ __device__ __forceinline__ size_t mass_smem_doubles(int nM, int nQ) {
   return 15 * (size_t)nM + (size_t)nQ + 10 * (size_t)nQ;
@@ -2777,7 +2783,7 @@ __device__ void mass_correct_t(const float* L, const float* sc, const float* rdi
 #pragma unroll
         for (int m2 = m; m2 < ROWS; ++m2) {
           const int i = lane + 32 * m2;
-          const float lij = (i > j && i < nM) ? L[min(i, nM - 1) * nM + j] : 0.0f;
+          const float lij = (i > j && i < nM) ? L[lro(min(i, nM - 1)) + j] : 0.0f;
 #pragma unroll
           for (int v = 0; v < 5; ++v) y[v][m2] = fmaf(-lij, yj[v], y[v][m2]);
         }
@@ -2799,7 +2805,7 @@ __device__ void mass_correct_t(const float* L, const float* sc, const float* rdi
 #pragma unroll
         for (int m2 = 0; m2 <= m; ++m2) {
           const int i = lane + 32 * m2;
-          const float lji = i < j ? L[j * nM + min(i, nM - 1)] : 0.0f;
+          const float lji = i < j ? L[lro(j) + min(i, j)] : 0.0f;
 #pragma unroll
           for (int v = 0; v < 5; ++v) y[v][m2] = fmaf(-lji, zj[v], y[v][m2]);
         }
@@ -2825,10 +2831,10 @@ __device__ __forceinline__ void mass_correct(const float* L, const float* sc, co
   else mass_correct_t<4>(L, sc, rdiag, r, x, nM);
 }
 
-__global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
-                                                                   const double* in, double* out, double t0, double t1,
-                                                                   double t2, double t3, int weight, int max_nM,
-                                                                   int max_nQ) {
+__global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
+                                                                   const double* in, double* out, const double* x0,
+                                                                   double t0, double t1, double t2, double t3,
+                                                                   int weight, int max_nM, int max_nQ) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
   double* x = sm;
@@ -2838,7 +2844,7 @@ __global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const 
   double* bufA = wJ + max_nQ;
   double* bufB = bufA + 5 * max_nQ;
   float* L = reinterpret_cast<float*>(bufB + 5 * max_nQ);
-  float* sc = L + max_nM * max_nM;
+  float* sc = L + lro(max_nM);
   float* rdiag = sc + max_nM;
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
     const int64_t s = list[e];
@@ -2878,7 +2884,7 @@ __global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const 
     for (int w = tid; w < nn; w += bd) {
       const int a = w / nM, k = w - a * nM;
       if (k > a) continue;
-      L[w] = sc[a] * sc[k] * fmaf(f3, Mk[3 * nn + w], fmaf(f2, Mk[2 * nn + w], fmaf(f1, Mk[nn + w], f0 * Mk[w])));
+      L[lro(a) + k] = sc[a] * sc[k] * fmaf(f3, Mk[3 * nn + w], fmaf(f2, Mk[2 * nn + w], fmaf(f1, Mk[nn + w], f0 * Mk[w])));
     }
     __syncthreads();
     // right-looking Cholesky, two columns per pass: columns j and j+1, then
@@ -2887,16 +2893,16 @@ __global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const 
     // reciprocal in rdiag
     for (int j = 0; j < nM; j += 2) {
       const bool two = j + 1 < nM;
-      const float rd = rsqrtf(L[j * nM + j]);
-      for (int i = j + 1 + tid; i < nM; i += bd) L[i * nM + j] *= rd;
+      const float rd = rsqrtf(L[lro(j) + j]);
+      for (int i = j + 1 + tid; i < nM; i += bd) L[lro(i) + j] *= rd;
       if (tid == 0) rdiag[j] = rd;
       __syncthreads();
       if (two) {
-        const float l = L[(j + 1) * nM + j];
-        for (int i = j + 1 + tid; i < nM; i += bd) L[i * nM + j + 1] = fmaf(-L[i * nM + j], l, L[i * nM + j + 1]);
+        const float l = L[lro(j + 1) + j];
+        for (int i = j + 1 + tid; i < nM; i += bd) L[lro(i) + j + 1] = fmaf(-L[lro(i) + j], l, L[lro(i) + j + 1]);
         __syncthreads();
-        const float rd1 = rsqrtf(L[(j + 1) * nM + j + 1]);
-        for (int i = j + 2 + tid; i < nM; i += bd) L[i * nM + j + 1] *= rd1;
+        const float rd1 = rsqrtf(L[lro(j + 1) + j + 1]);
+        for (int i = j + 2 + tid; i < nM; i += bd) L[lro(i) + j + 1] *= rd1;
         if (tid == 0) rdiag[j + 1] = rd1;
         __syncthreads();
       }
@@ -2910,37 +2916,40 @@ __global__ void __launch_bounds__(kMassThreads) moving_mass_kernel(Ctx c, const 
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const int ig = min(i + g * nwarps, nM - 1);
-          l0[g] = L[ig * nM + j];
-          l1[g] = two ? L[ig * nM + j + 1] : 0.0f;
+          l0[g] = L[lro(ig) + j];
+          l1[g] = two ? L[lro(ig) + j + 1] : 0.0f;
           if (i + g * nwarps < nM) last = i + g * nwarps;
         }
         for (int k = j0 + lane; k <= last; k += 32) {
-          const float c0 = L[k * nM + j], c1 = two ? L[k * nM + j + 1] : 0.0f;
+          const float c0 = L[lro(k) + j], c1 = two ? L[lro(k) + j + 1] : 0.0f;
           float v[4];
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int ig = i + g * nwarps;
-            v[g] = (ig < nM && k <= ig) ? L[min(ig, nM - 1) * nM + k] : 0.0f;
+            v[g] = (ig < nM && k <= ig) ? L[lro(min(ig, nM - 1)) + k] : 0.0f;
           }
 #pragma unroll
           for (int g = 0; g < 4; ++g) v[g] = fmaf(-l1[g], c1, fmaf(-l0[g], c0, v[g]));
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int ig = i + g * nwarps;
-            if (ig < nM && k <= ig) L[ig * nM + k] = v[g];
+            if (ig < nM && k <= ig) L[lro(ig) + k] = v[g];
           }
         }
       }
       __syncthreads();
     }
+    // from x0 (a nearby state: one correction fewer) or from zero
     for (int w = tid; w < 5 * nM; w += bd) {
-      x[w] = 0.0;
+      x[w] = x0 ? x0[qoff + w] : 0.0;
       r[w] = b[w];
     }
     __syncthreads();
-    for (int it = 0; it < 3; ++it) {
+    if (x0) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
+    const int ncorr = x0 ? 2 : 3;
+    for (int it = 0; it < ncorr; ++it) {
       mass_correct(L, sc, rdiag, r, x, nM);
-      if (it < 2) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
+      if (it + 1 < ncorr) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
     }
     for (int w = tid; w < 5 * nM; w += bd) out[qoff + w] = x[w];
     __syncthreads();
@@ -3168,17 +3177,18 @@ void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int
 
 
 cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
-                               const double* tau, int weight, int max_nM, int max_nQ, int grid, cudaStream_t st) {
+                               const double* x0, const double* tau, int weight, int max_nM, int max_nQ, int grid,
+                               cudaStream_t st) {
   if (max_nM > 32 * kMassRows) return cudaErrorInvalidValue;
   size_t bytes = 0;
   if (max_nM > 0)
-    bytes = sizeof(double) * mass_smem_doubles(max_nM, max_nQ) + sizeof(float) * ((size_t)max_nM * max_nM + 2 * (size_t)max_nM);
+    bytes = sizeof(double) * mass_smem_doubles(max_nM, max_nQ) + sizeof(float) * ((size_t)lro(max_nM) + 2 * (size_t)max_nM);
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(moving_mass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
-  moving_mass_kernel<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, tau[0], tau[1], tau[2], tau[3],
-                                                         weight, max_nM, max_nQ);
+  moving_mass_kernel<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, x0, tau[0], tau[1], tau[2],
+                                                         tau[3], weight, max_nM, max_nQ);
   return cudaGetLastError();
 }
 

@@ -179,10 +179,12 @@ void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, int64_t n
                             double t, int grid, cudaStream_t st);
 // Per slot of list[0 .. n_slots): out = M^ in (weight = 1) or out = M^{-1} in
 // (weight = 0), with M^ = V^T diag(w J^) V and J^ = sum_k tau_k J_k
-// (hexahedra, in their scaled nodal storage: pointwise J^).  out may alias in.
+// (hexahedra, in their scaled nodal storage: pointwise J^).  x0 (or null):
+// a nearby solution the solve starts from.  out may alias in or x0.
 // max_nM / max_nQ: the largest prism / pyramid mode and point counts among
 // the listed slots (0 if none: shared memory).
 cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
-                               const double* tau, int weight, int max_nM, int max_nQ, int grid, cudaStream_t st);
+                               const double* x0, const double* tau, int weight, int max_nM, int max_nQ, int grid,
+                               cudaStream_t st);
 
 }  // namespace dgk

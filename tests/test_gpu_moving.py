@@ -1,11 +1,12 @@
 """GPU parity of the moving-mesh path (dg_mesh_create_moving) against the
 moving-mesh oracle (oracle/moving.py): the moving-frame residual at several
-mesh times on every element type at N = 1..4, LSERK steps with the discrete
+mesh times on every element type at N = 1..5, LSERK steps with the discrete
 geometric conservation law (the stage solves of Algorithm 1's projection
 with the stage values of J), the free stream kept through steps on a mesh in
 motion, conservation of int J q, zero velocity against the static curved
 path, projection at the mesh time, an element turned inside out reported by
-dg_sync, and the calls a moving mesh rejects."""
+dg_sync, and the calls a moving mesh rejects.  N = 5 prisms (126 modes)
+take the stage solve's widest configuration (four rows per lane)."""
 import numpy as np
 import pytest
 
@@ -41,7 +42,7 @@ def tgv(mo):
 
 
 CASES = [("hex", 2, 2), ("prism", 2, 3), ("pyramid", 2, 2), ("mixed", 2, 3), ("mixed", 3, 4), ("mixed", 2, 1),
-         ("hex", 3, 4)]
+         ("hex", 3, 4), ("prism", 2, 5), ("pyramid", 2, 5)]
 
 
 @pytest.mark.parametrize("kind,m,N", CASES)
@@ -60,7 +61,8 @@ def test_moving_rhs_parity(dg, kind, m, N):
 
 
 @pytest.mark.parametrize("kind,m,N,sched", [("mixed", 2, 3, "balanced"), ("pyramid", 2, 2, "naive"),
-                                            ("hex", 2, 2, "static"), ("prism", 2, 3, "balanced")])
+                                            ("hex", 2, 2, "static"), ("prism", 2, 3, "balanced"),
+                                            ("prism", 2, 5, "balanced")])
 def test_moving_rk_step_parity(dg, kind, m, N, sched):
     box, vel, mo, mesh = setup(dg, kind, m, N, scheduler=sched)
     Q = tgv(mo)
@@ -167,6 +169,10 @@ def test_moving_mesh_rejections(dg):
     four = make_box("four", 4, seed=1)
     with pytest.raises(dg.DGError):
         dg.MovingMesh(four, 2, di.vertex_velocities(four.xyz, 0.1))
+    with pytest.raises(dg.DGError):      # prisms of N = 6 have 196 modes: beyond the stage solve's 128
+        dg.MovingMesh(box, 6, vel)
+    with pytest.raises(dg.DGError):
+        dg.MovingMesh(box, 2, vel * np.nan)
     static = dg.Mesh(box, 2, geometry="vertex")
     with pytest.raises(dg.DGError):
         dg._check(dg.load().dg_set_mesh_time(static.handle, 0.1))
