@@ -459,8 +459,12 @@ dg_status dg_set_adjoint_storage(dg_mesh* mesh, int keep_stages);
  * 0 < fraction <= 0.95, default 0.5.  A larger share lets the forward pass
  * keep more final steps, so fewer segments are run twice (the self-contained
  * adjoint of a long trajectory); the store stays allocated until
- * dg_set_adjoint_storage(mesh, 0) or dg_mesh_destroy.  Results are bitwise
- * identical for every share. */
+ * dg_set_adjoint_storage(mesh, 0) or dg_mesh_destroy.  When the whole
+ * trajectory's stage data do not fit in the share, dg_rk_vjp keeps a compact
+ * form instead -- the nodal state per stage (and, Navier-Stokes, the nodal
+ * gradient), about half the bytes -- and every reverse stage rebuilds its
+ * face traces from them, so more final steps are kept.  Results are bitwise
+ * identical for every share and either form. */
 dg_status dg_set_adjoint_memory(dg_mesh* mesh, double fraction);
 
 /* Volume term of the hexahedra.  DG_VOLUME_WEAK (default): the weak form of

@@ -98,13 +98,20 @@ struct dg_mesh {
   struct StagePtrs {
     double *U, *T, *Vt, *DW;
   };
+  // compact: only the nodal state (and, Navier-Stokes, the nodal gradient)
+  // is kept per stage; the reverse stage rebuilds the face traces from them
+  // (kTraces).  dg_rk_vjp chooses it when the whole trajectory's full stage
+  // data do not fit in the memory share, so more stages are kept.
+  bool compact = false;
   size_t stage_doubles() const {
     const size_t hh = (size_t)std::max<int64_t>(1, h.h_total), tt = (size_t)std::max<int64_t>(1, h.t_total);
+    if (compact) return ns ? 4 * hh : hh;
     return ns ? 4 * (hh + tt) : hh + tt;
   }
   StagePtrs stage_ptrs(int g) const {
     const size_t hh = (size_t)std::max<int64_t>(1, h.h_total), tt = (size_t)std::max<int64_t>(1, h.t_total);
     double* b = d_sstore + (size_t)g * stage_doubles();
+    if (compact) return StagePtrs{b, nullptr, nullptr, ns ? b + hh : nullptr};
     StagePtrs P{b, b + hh, nullptr, nullptr};
     if (ns) {
       P.Vt = P.T + tt;
@@ -635,7 +642,8 @@ struct dg_mesh {
   void element_phase(int mode, const dgk::StageArgs& a, cudaStream_t st) {
     dgk::Ctx c = ctx();
     timed(true, st, [&] {
-      const bool per_elem = mode == dgk::kProject || mode == dgk::kEval || mode == dgk::kLoad;   // one-shot maps
+      const bool per_elem = mode == dgk::kProject || mode == dgk::kEval || mode == dgk::kLoad ||
+                            mode == dgk::kTraces;   // one-shot maps
       if (scheduler == DG_SCHED_BALANCED && !per_elem) {
         for (const auto& G : groups) {
           dgk::Ctx cg = c;
@@ -709,6 +717,11 @@ struct dg_mesh {
       ov_Vt = P.Vt;
       ov_DW = P.DW;
       va.stored = 1;
+      if (compact) {
+        // traces into the mesh's own face buffers (T, and Vt for Navier-Stokes)
+        dgk::StageArgs none{nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+        element_phase(dgk::kTraces, none, st);
+      }
     }
     const int64_t nb = (int64_t)h.face_blocks.size();
     if (ns) {
@@ -765,7 +778,7 @@ struct dg_mesh {
         if (stages) cudaMemcpyAsync(stages + (size_t)g * h.n_dof, Q, bytes, cudaMemcpyDeviceToDevice, st);
         if (keep) {
           const StagePtrs P = stage_ptrs(g);
-          cudaMemcpyAsync(P.T, d_T, tbytes, cudaMemcpyDeviceToDevice, st);
+          if (P.T) cudaMemcpyAsync(P.T, d_T, tbytes, cudaMemcpyDeviceToDevice, st);
           if (ns) {
             ov_Unod = P.U;
             ov_Vt = P.Vt;
@@ -1762,6 +1775,8 @@ dg_status dg_rk_vjp(dg_mesh* mesh, const double* Q0_store, double dt, int nsteps
   // are reversed without being recomputed.  The steps before tail0 only
   // place checkpoints.
   int tail0 = nsteps;
+  mesh->compact = false;
+  if (mesh->keep_stages && auto_ckpt(mesh, nsteps) < nsteps) mesh->compact = true;   // keep more stages
   if (mesh->keep_stages) {
     const int fit = auto_ckpt(mesh, nsteps);
     int t0 = std::max(0, nsteps - fit);
@@ -1794,6 +1809,7 @@ dg_status dg_rk_vjp_checkpointed(dg_mesh* mesh, const double* ckpt_store, double
   dg_status st = rk_vjp_args(mesh, ckpt_store, QKbar, Q0bar, nsteps, ckpt_every, dt);
   if (st != DG_OK) return st;
   if (ckpt_every < 1) return fail(DG_ERR_ARG, "ckpt_every must be >= 1 (the checkpoints' spacing)");
+  mesh->compact = false;   // one segment's full stage data at a time
   const size_t bytes = sizeof(double) * (size_t)mesh->h.n_dof;
   if (Q0bar != QKbar) DG_CUDA(cudaMemcpyAsync(Q0bar, QKbar, bytes, cudaMemcpyDeviceToDevice, stream));
   if (nsteps == 0) return DG_OK;

@@ -1533,6 +1533,26 @@ __device__ __forceinline__ void process_element(const Ctx& c, const StageArgs& i
     element_forward<ANY>(c, T, s, bufA, bufG, lane);
     return;
   }
+  if (MODE == kTraces) {
+    // the stage's face traces rebuilt from its kept nodal state (and the
+    // gradient traces from its kept nodal gradient) by the same trace
+    // writes as the forward phases: bitwise the values they wrote
+    const double* Un = c.Unod + c.slot_hoff[s];
+    for (int w = lane; w < 5 * nQ; w += blockDim.x) bufA[w] = Un[w];
+    __syncthreads();
+    write_traces(c, T, s, bufA, c.T, 1.0, lane);
+    if (c.ns) {
+      for (int d = 0; d < 3; ++d) {
+        const double* dW = c.DW + 3 * c.slot_hoff[s] + d * 5 * nQ;
+        __syncthreads();
+        for (int w = lane; w < 5 * nQ; w += blockDim.x) bufG[w] = dW[w];
+        __syncthreads();
+        write_traces(c, T, s, bufG, c.Vt, 1.0, lane, 3, (int64_t)d * 5 * T.n * T.n);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if (MODE == kEval) {
     const double* Q = io.Qin + qoff;
     for (int w = lane; w < 5 * nM; w += blockDim.x) bufG[w] = Q[w];
@@ -3076,6 +3096,7 @@ void launch_element(const Ctx& c, int mode, const StageArgs& a, const Sched& s, 
     case kProject: launch_mode<kProject>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kEval: launch_mode<kEval>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kLoad: launch_mode<kLoad>(c, a, s, balanced, grid, wpb, bytes, st); break;
+    case kTraces: launch_mode<kTraces>(c, a, s, balanced, grid, wpb, bytes, st); break;
     case kGather:   // one block per listed hexahedron
       if (s.count > 0) elem_naive_kernel<kGather, false><<<(unsigned)s.count, 32 * wpb, bytes, st>>>(c, a, s.list, s.count);
       break;

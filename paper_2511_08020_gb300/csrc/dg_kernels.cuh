@@ -36,7 +36,8 @@ enum ElemMode : int {
   kScatter = 6,    // hexahedra: scaled nodal storage -> caller modal coefficients
   kNsVolume = 7,   // Navier-Stokes: BR1 lifting, gradient traces, volume residual H
   kEval = 8,       // modal -> nodal values at the volume points (caller element order)
-  kLoad = 9        // load vector V^T W J q of point values (Algorithm 1's projection without M^{-1})
+  kLoad = 9,       // load vector V^T W J q of point values (Algorithm 1's projection without M^{-1})
+  kTraces = 10     // adjoint: face traces of a kept nodal state (Unod) and, Navier-Stokes, of a kept nodal gradient (DW)
 };
 
 struct Ctx {

@@ -84,8 +84,10 @@ def test_rk_vjp_parity(dg, kind, m, N, flux, reorder, nsteps, ckpt):
 
 @pytest.mark.parametrize("flux", ["lf", "roe"])
 def test_rk_vjp_stored_equals_recomputed(dg, flux):
-    """dg_rk_vjp with the per-stage forward data kept (default) and with every
-    reverse stage recomputing it from the stage state: bitwise equal."""
+    """dg_rk_vjp with the per-stage forward data kept (default), with every
+    reverse stage recomputing it from the stage state, and with the compact
+    store (a memory share too small for the trajectory: only the nodal state
+    kept, the traces rebuilt per reverse stage): bitwise equal."""
     box, o, mesh = setup(dg, "mixed", 3, 3, flux, 6)
     Q0 = state(o)
     Qs = mesh.set_state(Q0)
@@ -94,7 +96,11 @@ def test_rk_vjp_stored_equals_recomputed(dg, flux):
     mesh.set_adjoint_storage(False)
     recomputed = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
     mesh.set_adjoint_storage(True)
+    mesh.set_adjoint_memory(1e-9)
+    compact = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    mesh.set_adjoint_memory(0.5)
     assert torch.equal(kept, recomputed)
+    assert torch.equal(kept, compact)
 
 
 @pytest.mark.parametrize("nsteps,ckpt", [(4, 2), (5, 2), (3, 5)])

@@ -198,7 +198,14 @@ def test_ns_rk_vjp_stored_equals_recomputed(dg):
     kept = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
     mesh.set_adjoint_storage(False)
     recomputed = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    mesh.set_adjoint_storage(True)
+    # compact store: nodal state and gradient kept, traces and gradient
+    # traces rebuilt per reverse stage
+    mesh.set_adjoint_memory(1e-9)
+    compact = mesh.rk_vjp(Qs, 1e-3, 4, 2, Ws).clone()
+    mesh.set_adjoint_memory(0.5)
     assert torch.equal(kept, recomputed)
+    assert torch.equal(kept, compact)
 
 
 def test_ns_rk_checkpointed_split(dg):
