@@ -273,10 +273,12 @@ dg_status dg_partition_plan(const dg_mesh_desc* desc, int nparts, const double* 
  * computation match the whole mesh's, and a partitioned run reproduces the
  * whole mesh's residual and steps bit for bit on the owned elements.  No
  * element work runs on ghosts: their face traces arrive by the halo exchange
- * (dg_halo_pack / dg_halo_unpack).  A partition mesh runs the Euler equations
- * with the balanced or naive scheduler and steps stage by stage
- * (dg_rk_prime / dg_rk_stage); whole-residual calls (dg_rhs, dg_rk_step,
- * dg_autotune, the adjoint) return DG_ERR_UNSUPPORTED.  Synchronous. */
+ * (dg_halo_pack / dg_halo_unpack; for Navier-Stokes also the gradient traces,
+ * dg_halo_pack_gradients / dg_halo_unpack_gradients).  A partition mesh runs
+ * the Euler or the Navier-Stokes equations with the balanced or naive
+ * scheduler and steps stage by stage (dg_rk_prime / dg_rk_stage_lift /
+ * dg_rk_stage); whole-residual calls (dg_rhs, dg_rk_step, dg_autotune, the
+ * adjoint) return DG_ERR_UNSUPPORTED.  Synchronous. */
 dg_status dg_mesh_create_part(const dg_mesh_desc* desc, const int64_t* part_of_elem, int nparts, int part,
                               cudaStream_t stream, dg_mesh** out);
 
@@ -313,6 +315,16 @@ dg_status dg_halo_counts(const dg_mesh* mesh, int64_t* send_faces, int64_t* recv
 dg_status dg_halo_pack(dg_mesh* mesh, double* send, cudaStream_t stream);
 dg_status dg_halo_unpack(dg_mesh* mesh, const double* recv, cudaStream_t stream);
 
+/* Navier-Stokes, the second exchange of a stage (BR1: the flux needs the
+ * lifted gradient on both sides of a face): the same faces, peers and order
+ * as dg_halo_pack / dg_halo_unpack, 15 (N+1)^2 doubles per face (the
+ * gradient of the five primitive variables in three directions at the face
+ * points), packed from and unpacked into the gradient-trace buffer that
+ * dg_rk_stage_lift fills.  DG_ERR_UNSUPPORTED for the Euler equations.
+ * Asynchronous. */
+dg_status dg_halo_pack_gradients(dg_mesh* mesh, double* send, cudaStream_t stream);
+dg_status dg_halo_unpack_gradients(dg_mesh* mesh, const double* recv, cudaStream_t stream);
+
 /* Stage-wise LSERK(5,4) for partitioned runs (Sec. 2, Sec. 3).  dg_rk_prime
  * runs the forward phase of the first stage (state at the points, the
  * element's face traces, the volume term) on Q_store.  dg_rk_stage(stage =
@@ -320,8 +332,14 @@ dg_status dg_halo_unpack(dg_mesh* mesh, const double* recv, cudaStream_t stream)
  * LSERK update of Q_store and K_store, and -- unless last != 0 -- the forward
  * phase of the next stage on the new state (the next step's first stage
  * after stage 4).  One step: prime (first step only), then for every stage:
- * halo exchange, dg_rk_stage.  Works on any mesh.  Asynchronous. */
+ * halo exchange, dg_rk_stage.  Navier-Stokes splits the stage's face phase
+ * in two: dg_rk_stage_lift runs the BR1 lifting (face values W*, then the
+ * element volume phase: lifted gradient, its face traces, the volume term),
+ * the caller exchanges the gradient traces, and dg_rk_stage runs the flux
+ * face phase and the backward phase (DG_ERR_ARG if the lifting half has not
+ * run for the stage).  Works on any mesh.  Asynchronous. */
 dg_status dg_rk_prime(dg_mesh* mesh, const double* Q_store, cudaStream_t stream);
+dg_status dg_rk_stage_lift(dg_mesh* mesh, cudaStream_t stream);
 dg_status dg_rk_stage(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int stage, int last,
                       cudaStream_t stream);
 

@@ -95,6 +95,9 @@ _SIGS = {
     "dg_set_mesh_time": [_P, ctypes.c_double],
     "dg_geometry_at": [ctypes.POINTER(MeshDesc), _P, ctypes.c_double, _P, _P, _P, _P],
     "dg_moving_phase_times": [_P, _P, _P],
+    "dg_halo_pack_gradients": [_P, _P, _P],
+    "dg_halo_unpack_gradients": [_P, _P, _P],
+    "dg_rk_stage_lift": [_P, _P],
 }
 
 _lib = None
@@ -535,6 +538,24 @@ class Part(Mesh):
     def halo_unpack(self, recv, stream=None):
         _check(load().dg_halo_unpack(self.handle, _ptr(recv), _stream(stream)))
 
+    def halo_gradient_buffers(self):
+        """Send and receive buffers of the Navier-Stokes gradient-trace
+        exchange (three times the trace blocks)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        per = 3 * self.doubles_per_face
+        return (torch.empty(max(1, int(self.send_faces.sum())) * per, dtype=torch.float64, device=dev),
+                torch.empty(max(1, int(self.recv_faces.sum())) * per, dtype=torch.float64, device=dev))
+
+    def halo_pack_gradients(self, send, stream=None):
+        _check(load().dg_halo_pack_gradients(self.handle, _ptr(send), _stream(stream)))
+
+    def halo_unpack_gradients(self, recv, stream=None):
+        _check(load().dg_halo_unpack_gradients(self.handle, _ptr(recv), _stream(stream)))
+
+    def rk_stage_lift(self, stream=None):
+        _check(load().dg_rk_stage_lift(self.handle, _stream(stream)))
+
     def rk_prime(self, Q_store, stream=None):
         _check(load().dg_rk_prime(self.handle, _ptr(Q_store), _stream(stream)))
 
@@ -543,17 +564,23 @@ class Part(Mesh):
                                   _stream(stream)))
 
 
-def step_parts(parts, Qs, Ks, dt, nsteps, exchange):
+def step_parts(parts, Qs, Ks, dt, nsteps, exchange, exchange_gradients=None):
     """nsteps LSERK steps of a partitioned mesh: parts[i] advances Qs[i]
     (storage layout) with register Ks[i]; exchange() moves every part's packed
     halo blocks into its peers' receive buffers between the forward phase and
-    the face phase of every stage (pack and unpack are done here)."""
+    the face phase of every stage.  Navier-Stokes parts need the second
+    exchange, exchange_gradients(), of the gradient traces between the
+    lifting half of the stage (rk_stage_lift) and the flux half (rk_stage)."""
     for step in range(nsteps):
         if step == 0:
             for P, Q in zip(parts, Qs):
                 P.rk_prime(Q)
         for s in range(5):
             exchange()
+            if exchange_gradients is not None:
+                for P in parts:
+                    P.rk_stage_lift()
+                exchange_gradients()
             for P, Q, K in zip(parts, Qs, Ks):
                 P.rk_stage(Q, K, dt, s, last=(s == 4 and step == nsteps - 1))
 

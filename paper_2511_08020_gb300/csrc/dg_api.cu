@@ -103,6 +103,7 @@ struct dg_mesh {
   // (kTraces).  dg_rk_vjp chooses it when the whole trajectory's full stage
   // data do not fit in the memory share, so more stages are kept.
   bool compact = false;
+  bool lift_done = false;   // Navier-Stokes stage-wise stepping: dg_rk_stage_lift ran for the pending stage
   size_t stage_doubles() const {
     const size_t hh = (size_t)std::max<int64_t>(1, h.h_total), tt = (size_t)std::max<int64_t>(1, h.t_total);
     if (compact) return ns ? 4 * hh : hh;
@@ -1363,9 +1364,45 @@ dg_status dg_halo_unpack(dg_mesh* mesh, const double* recv, cudaStream_t stream)
   return DG_OK;
 }
 
+dg_status dg_halo_pack_gradients(dg_mesh* mesh, double* send, cudaStream_t stream) {
+  if (!mesh || (!send && !mesh->send_off.empty())) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->nparts == 0) return fail(DG_ERR_ARG, "not a partition mesh");
+  if (!mesh->ns) return fail(DG_ERR_UNSUPPORTED, "gradient traces exist for the Navier-Stokes equations");
+  if (mesh->send_off.empty()) return DG_OK;
+  dgk::launch_halo_copy(mesh->d_Vt, send, mesh->d_send_off, (int64_t)mesh->send_off.size(),
+                        15 * mesh->h.n * mesh->h.n, true, stream, 3);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_halo_unpack_gradients(dg_mesh* mesh, const double* recv, cudaStream_t stream) {
+  if (!mesh || (!recv && !mesh->recv_off.empty())) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->nparts == 0) return fail(DG_ERR_ARG, "not a partition mesh");
+  if (!mesh->ns) return fail(DG_ERR_UNSUPPORTED, "gradient traces exist for the Navier-Stokes equations");
+  if (mesh->recv_off.empty()) return DG_OK;
+  dgk::launch_halo_copy(recv, mesh->d_Vt, mesh->d_recv_off, (int64_t)mesh->recv_off.size(),
+                        15 * mesh->h.n * mesh->h.n, false, stream, 3);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_rk_stage_lift(dg_mesh* mesh, cudaStream_t stream) {
+  if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (!mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the lifting half-stage belongs to the Navier-Stokes equations");
+  DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
+  mesh->parity = 0;
+  mesh->begin_timing(1);
+  mesh->timed(false, stream, [&] { dgk::launch_faces_ns(mesh->ctx(), (int64_t)mesh->h.face_blocks.size(), mesh->h.n, 0, stream); });
+  dgk::StageArgs none{nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+  mesh->element_phase(dgk::kNsVolume, none, stream);
+  mesh->lift_done = true;
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 dg_status dg_rk_prime(dg_mesh* mesh, const double* Q_store, cudaStream_t stream) {
   if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
-  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "stage-wise stepping covers the Euler equations");
+  mesh->lift_done = false;
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
   mesh->begin_timing(1);
@@ -1380,11 +1417,19 @@ dg_status dg_rk_stage(dg_mesh* mesh, double* Q_store, double* K_store, double dt
   if (!mesh || !Q_store || !K_store) return fail(DG_ERR_ARG, "null argument");
   if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must lie in 0..4");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
-  if (mesh->ns) return fail(DG_ERR_UNSUPPORTED, "stage-wise stepping covers the Euler equations");
+  if (mesh->ns && !mesh->lift_done)
+    return fail(DG_ERR_ARG, "Navier-Stokes: dg_rk_stage_lift (and the gradient-trace exchange) first");
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
-  mesh->begin_timing(1);
-  mesh->face_phase(stream);
+  if (!mesh->ns) mesh->begin_timing(1);
+  if (mesh->ns) {
+    // the inviscid and viscous flux of the stage (the lifting half ran in
+    // dg_rk_stage_lift, before the gradient traces were exchanged)
+    mesh->timed(false, stream, [&] { dgk::launch_faces_ns(mesh->ctx(), (int64_t)mesh->h.face_blocks.size(), mesh->h.n, 1, stream); });
+    mesh->lift_done = false;
+  } else {
+    mesh->face_phase(stream);
+  }
   dgk::StageArgs a{Q_store, Q_store, K_store, kLsA[stage], kLsB[stage], dt};
   if (mesh->fused) {
     mesh->element_phase(last ? dgk::kBwdRk : dgk::kBwdRkFwd, a, stream);
@@ -1882,8 +1927,6 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
   if (physics == DG_NAVIER_STOKES && mesh->moving)
     return fail(DG_ERR_UNSUPPORTED, "a moving mesh runs the Euler equations");
-  if (physics == DG_NAVIER_STOKES && part_mesh(mesh))
-    return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes needs a second halo exchange per stage; partition meshes run Euler");
   if (physics == DG_NAVIER_STOKES && (mesh->split || mesh->flux == DG_FLUX_EC))
     return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes runs with the weak form and the LF or Roe flux");
   if (physics == DG_NAVIER_STOKES) {

@@ -2698,9 +2698,9 @@ __global__ void __launch_bounds__(224, 2) face_ns_vjp_kernel(Ctx c) {
 // `per` doubles between the face buffer at the listed offsets and a packed
 // buffer (pack: buffer block k <- T[off[k]]; unpack: T[off[k]] <- block k).
 __global__ void halo_copy_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                                 const int64_t* __restrict__ off, int64_t count, int per, int pack) {
+                                 const int64_t* __restrict__ off, int64_t count, int per, int pack, int mult) {
   for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
-    const int64_t o = off[k];
+    const int64_t o = mult * off[k];
     for (int w = threadIdx.x; w < per; w += blockDim.x) {
       if (pack) dst[k * per + w] = src[o + w];
       else dst[o + w] = src[k * per + w];
@@ -3169,10 +3169,10 @@ void launch_faces(const Ctx& c, int64_t nblocks, int n, cudaStream_t st) {
 }
 
 void launch_halo_copy(const double* src, double* dst, const int64_t* off, int64_t count, int per, bool pack,
-                      cudaStream_t st) {
+                      cudaStream_t st, int mult) {
   if (count <= 0) return;
   const unsigned blocks = (unsigned)std::min<int64_t>(count, 65535);
-  halo_copy_kernel<<<blocks, 128, 0, st>>>(src, dst, off, count, per, pack ? 1 : 0);
+  halo_copy_kernel<<<blocks, 128, 0, st>>>(src, dst, off, count, per, pack ? 1 : 0, mult);
 }
 
 void launch_rk_params(RkDyn* d, double* Q, double* K, double dt, cudaStream_t st) {

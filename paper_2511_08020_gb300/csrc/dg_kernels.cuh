@@ -157,9 +157,10 @@ void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int
 // is_rk_params_kernel recognises the node's function in a captured graph.
 void launch_rk_params(RkDyn* d, double* Q, double* K, double dt, cudaStream_t st);
 // partition meshes: pack (T -> buffer) or unpack (buffer -> T) count face-side
-// trace blocks of `per` doubles at the face-buffer offsets off[]
+// trace blocks of `per` doubles at the face-buffer offsets mult * off[]
+// (mult = 3: the gradient traces, laid out at three times the trace offsets)
 void launch_halo_copy(const double* src, double* dst, const int64_t* off, int64_t count, int per, bool pack,
-                      cudaStream_t st);
+                      cudaStream_t st, int mult = 1);
 void rk_params_node(cudaKernelNodeParams* p, void** args);
 bool is_rk_params_kernel(const void* func);
 int element_smem_bytes(int nQmax, int warps_per_block);
