@@ -112,20 +112,22 @@ class MovingOracle:
         return (shape_functions(m.etype[e], np.atleast_2d(ref)) @ self.vel[m.verts[e]]).T
 
     # ------------------------------------------------------------ residual (m2, m3)
-    def rate(self, Q, t):
-        """vol - surf at time t: the time derivative of Ut = M(t) Q."""
+    def rate(self, Q, t, elems=None):
+        """vol - surf at time t: the time derivative of Ut = M(t) Q (with
+        elems, only those elements' blocks, from the faces they touch)."""
         o = self.at(t)
         m = o.mesh
         R = np.zeros_like(np.asarray(Q, dtype=float))
+        elems = range(m.n_elems) if elems is None else elems
         fluxes = {}
-        for f in range(len(m.faces)):
+        for f in sorted({f for e in elems for f, _ in m.elem_faces[e]}):
             e0, l0, e1, _ = m.faces[f]
             phi0, phi1, wS, nrm = o.face_data(f)
             ref0 = m.face_geometry(f)[0]
             s = np.einsum("dp,dp->p", self.mesh_velocity(o, e0, ref0), nrm)
             UL, UR = m.block(Q, e0) @ phi0.T, m.block(Q, e1) @ phi1.T
             fluxes[f] = wS * ale_lax_friedrichs(UL, UR, nrm, s, self.gamma)
-        for e in range(m.n_elems):
+        for e in elems:
             op = o.ops[m.etype[e]]
             U = m.block(Q, e) @ op.V.T                                   # [5, nQ]
             F = physical_flux(U, self.gamma)                             # [3(d), 5, nQ]
@@ -161,19 +163,20 @@ class MovingOracle:
             out[m.dof_off[e]:m.dof_off[e + 1]] = (m.block(Q, e) @ self.mass(e, t, y, h)).ravel()
         return out
 
-    def unweighted(self, Ut, t, y=None, h=None):
-        """Q = M^{-1} Ut per element (Cholesky), M as in weighted."""
+    def unweighted(self, Ut, t, y=None, h=None, elems=None):
+        """Q = M^{-1} Ut per element (Cholesky), M as in weighted (with elems,
+        only those elements)."""
         m = self.mesh
         out = np.zeros_like(Ut)
-        for e in range(m.n_elems):
+        for e in (range(m.n_elems) if elems is None else elems):
             c = cho_factor(self.mass(e, t, y, h))
             out[m.dof_off[e]:m.dof_off[e + 1]] = cho_solve(c, m.block(Ut, e).T).T.ravel()
         return out
 
-    def rhs(self, Q, t):
+    def rhs(self, Q, t, elems=None):
         """M(t)^{-1} (vol - surf) (what the library's dg_rhs returns on a mesh
-        in motion)."""
-        return self.unweighted(self.rate(Q, t), t)
+        in motion); with elems, only those elements' blocks."""
+        return self.unweighted(self.rate(Q, t, elems), t, elems=elems)
 
     def project(self, fn, t):
         return self.at(t).project(fn)

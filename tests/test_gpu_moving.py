@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import dg_inputs as di
-from gpu_util import TOL, make_box, rel_err, var_index
+from gpu_util import FULL_SIZE_AMP, TOL, assert_sampled_parity, make_box, rel_err, var_index
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -140,6 +140,43 @@ def test_moving_projection_at_mesh_time(dg):
     got = mesh.get_state(Qs)
     ref = mo.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.1), t)
     assert rel_err(got, ref, var_index(o.mesh.nM)) < 1e-12
+
+
+def test_moving_benchmark_mesh_sampled(dg):
+    """The bench's moving workload -- the curved 16^3 mixed box (vertices moved
+    by up to 0.1 h, seed 11) with velocities 0.5 (sin y sin z, ...), N = 4,
+    balanced scheduler, 4 warps per element -- at mesh time 0.02: the
+    residual on 24 sampled elements (hexahedra among them) against the
+    oracle with the plain per-variable metric, and the free stream through
+    two LSERK steps of the whole mesh (the stage solves at full size)."""
+    from oracle.moving import MovingOracle
+    box = di.perturb_vertices(di.box_mesh(16, "mixed", seed=2), 0.1, seed=11)
+    vel = di.vertex_velocities(box.xyz, 0.5)
+    N, n = 4, 5
+    mesh = dg.MovingMesh(box, N, vel)
+    mesh.set_element_warps(4)
+    vals = di.perturbed_tgv_state(mesh.quad_points(), seed=3, amp=FULL_SIZE_AMP)
+    Qs = mesh.project(torch.from_numpy(vals.reshape(5, box.n_elems, n ** 3).transpose(1, 0, 2).copy()).cuda())
+    Q = mesh.get_state(Qs)
+    mesh.set_time(0.02)
+    R = mesh.get_state(mesh.rhs(Qs))
+    mesh.sync()
+    mo = MovingOracle(box, N, vel)
+    rng = np.random.default_rng(21)
+    hexes = np.where(box.etype == 0)[0]
+    elems = np.unique(np.concatenate([rng.choice(hexes, 6, replace=False), rng.choice(box.n_elems, 18, replace=False)]))
+    mask = np.zeros(len(Q), dtype=bool)
+    for e in elems:
+        mask[mo.mesh.dof_off[e]:mo.mesh.dof_off[e + 1]] = True
+    assert_sampled_parity(R, mo.rhs(Q, 0.02, elems), var_index(mo.mesh.nM), mask, label="moving 16^3")
+    # free stream at full size: a constant state through two steps in motion
+    mesh.set_time(0.0)
+    const = np.tile(CONST[None, :, None], (box.n_elems, 1, n ** 3))
+    Qc = mesh.project(torch.from_numpy(const).cuda())
+    Q0 = Qc.clone()
+    mesh.rk_step(Qc, mesh.empty(), 0.01, 2)
+    mesh.sync()
+    assert float((Qc - Q0).abs().max()) < 1e-12 * float(Q0.abs().max())
 
 
 def test_inside_out_element_is_reported(dg):
