@@ -936,10 +936,23 @@ dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_v
   if (st != DG_OK) return st;
   made->moving = true;
   const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(1, made->h.n_dof);
-  std::vector<float> mk32(mo.mmat.begin(), mo.mmat.end());
+  // the FP32 preconditioner's coefficients: per prism and pyramid the four
+  // lower triangles, packed row by row
+  std::vector<float> mk32;
+  std::vector<int64_t> slot_m32off(made->h.n_elems, -1);
+  for (int64_t sl = 0; sl < made->h.n_elems; ++sl) {
+    if (mo.slot_mmoff[sl] < 0) continue;
+    const int nM = made->h.tables.tabs[made->h.slot_tab[sl]].nM;
+    slot_m32off[sl] = (int64_t)mk32.size();
+    for (int k = 0; k < 4; ++k) {
+      const double* Mc = mo.mmat.data() + mo.slot_mmoff[sl] + (size_t)k * nM * nM;
+      for (int a = 0; a < nM; ++a)
+        for (int b = 0; b <= a; ++b) mk32.push_back((float)Mc[(size_t)a * nM + b]);
+    }
+  }
   if (mk32.empty()) mk32.push_back(0.0f);
   cudaError_t e = upload(&made->d_slot_moff, mo.slot_moff);
-  if (e == cudaSuccess) e = upload(&made->d_slot_mmoff, mo.slot_mmoff);
+  if (e == cudaSuccess) e = upload(&made->d_slot_mmoff, slot_m32off);
   if (e == cudaSuccess) e = upload(&made->d_mk32, mk32);
   if (e == cudaSuccess) e = upload(&made->d_mpool, mo.mpool);
   if (e == cudaSuccess) e = upload(&made->d_fmot, mo.fpool);

@@ -2770,22 +2770,21 @@ __device__ void mass_product(const Ctx& c, const TypeTab& T, const double* x, co
   }
 }
 
-// x += S (L L^T)^{-1} S r: warp 0 solves for the five variables at once
-// (ROWS rows per lane in registers, one shuffle per variable and pivot, the
-// rows already solved masked by a zero coefficient instead of a branch);
-// the other warps wait at the closing barrier.
+// x += S (L L^T)^{-1} S r: warp v solves for variable v (ROWS rows per lane
+// in registers, one shuffle per pivot, the rows already solved masked by a
+// zero coefficient instead of a branch).  The five warps run side by side.
 template <int ROWS>
 __device__ void mass_correct_t(const float* L, const float* sc, const float* rdiag, const double* r, double* x,
                                int nM) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    float y[5][ROWS], sl[ROWS];
+  const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (v < 5) {
+    const double* rv = r + v * nM;
+    float y[ROWS], sl[ROWS];
 #pragma unroll
     for (int m = 0; m < ROWS; ++m) {
       const int i = lane + 32 * m;
       sl[m] = i < nM ? sc[min(i, nM - 1)] : 0.0f;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) y[v][m] = i < nM ? sl[m] * (float)r[v * nM + min(i, nM - 1)] : 0.0f;
+      y[m] = i < nM ? sl[m] * (float)rv[min(i, nM - 1)] : 0.0f;
     }
     // L y = S r
 #pragma unroll
@@ -2793,19 +2792,13 @@ __device__ void mass_correct_t(const float* L, const float* sc, const float* rdi
       const int jend = min(32, nM - 32 * m);
       for (int jj = 0; jj < jend; ++jj) {
         const int j = 32 * m + jj;
-        const float rdj = rdiag[j];
-        float yj[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          yj[v] = __shfl_sync(0xffffffffu, y[v][m], jj) * rdj;
-          y[v][m] = lane == jj ? yj[v] : y[v][m];
-        }
+        const float yj = __shfl_sync(0xffffffffu, y[m], jj) * rdiag[j];
+        y[m] = lane == jj ? yj : y[m];
 #pragma unroll
         for (int m2 = m; m2 < ROWS; ++m2) {
           const int i = lane + 32 * m2;
           const float lij = (i > j && i < nM) ? L[lro(min(i, nM - 1)) + j] : 0.0f;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) y[v][m2] = fmaf(-lij, yj[v], y[v][m2]);
+          y[m2] = fmaf(-lij, yj, y[m2]);
         }
       }
     }
@@ -2815,29 +2808,21 @@ __device__ void mass_correct_t(const float* L, const float* sc, const float* rdi
       const int jend = min(32, nM - 32 * m);
       for (int jj = jend - 1; jj >= 0; --jj) {
         const int j = 32 * m + jj;
-        const float rdj = rdiag[j];
-        float zj[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          zj[v] = __shfl_sync(0xffffffffu, y[v][m], jj) * rdj;
-          y[v][m] = lane == jj ? zj[v] : y[v][m];
-        }
+        const float zj = __shfl_sync(0xffffffffu, y[m], jj) * rdiag[j];
+        y[m] = lane == jj ? zj : y[m];
 #pragma unroll
         for (int m2 = 0; m2 <= m; ++m2) {
           const int i = lane + 32 * m2;
           const float lji = i < j ? L[lro(j) + min(i, j)] : 0.0f;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) y[v][m2] = fmaf(-lji, zj[v], y[v][m2]);
+          y[m2] = fmaf(-lji, zj, y[m2]);
         }
       }
     }
+    double* xv = x + v * nM;
 #pragma unroll
     for (int m = 0; m < ROWS; ++m) {
       const int i = lane + 32 * m;
-      if (i < nM) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) x[v * nM + i] += (double)(sl[m] * y[v][m]);
-      }
+      if (i < nM) xv[i] += (double)(sl[m] * y[m]);
     }
   }
   __syncthreads();
@@ -2892,19 +2877,21 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
       __syncthreads();
       continue;
     }
-    // FP32 S M^ S from the FP32 coefficients (lower triangle)
+    // FP32 S M^ S from the FP32 coefficients, all four kept packed (lower
+    // triangle, the layout of L): contiguous loads, then the scaling in
+    // shared memory
+    const int np = lro(nM);
     const float* Mk = c.mk32 + c.slot_mmoff[s];
-    const int nn = nM * nM;
     const float f0 = (float)t0, f1 = (float)t1, f2 = (float)t2, f3 = (float)t3;
-    for (int a = tid; a < nM; a += bd) {
-      const int w = a * nM + a;
-      sc[a] = rsqrtf(fmaf(f3, Mk[3 * nn + w], fmaf(f2, Mk[2 * nn + w], fmaf(f1, Mk[nn + w], f0 * Mk[w]))));
-    }
+#pragma unroll 4
+    for (int u = tid; u < np; u += bd)
+      L[u] = fmaf(f3, Mk[3 * np + u], fmaf(f2, Mk[2 * np + u], fmaf(f1, Mk[np + u], f0 * Mk[u])));
     __syncthreads();
-    for (int w = tid; w < nn; w += bd) {
-      const int a = w / nM, k = w - a * nM;
-      if (k > a) continue;
-      L[lro(a) + k] = sc[a] * sc[k] * fmaf(f3, Mk[3 * nn + w], fmaf(f2, Mk[2 * nn + w], fmaf(f1, Mk[nn + w], f0 * Mk[w])));
+    for (int a = tid; a < nM; a += bd) sc[a] = rsqrtf(L[lro(a) + a]);
+    __syncthreads();
+    for (int a = warp; a < nM; a += nwarps) {
+      const float sa = sc[a];
+      for (int k = lane; k <= a; k += 32) L[lro(a) + k] *= sa * sc[k];
     }
     __syncthreads();
     // right-looking Cholesky, two columns per pass: columns j and j+1, then

@@ -84,9 +84,10 @@ struct Ctx {
   const double* snrm;          // curved meshes: per face side [3][n^2] outward normal at 3 * (side offset / 5)
   // moving meshes (null otherwise): the polynomial-in-t geometry per slot
   // (mpool at slot_moff: [3][9][nQ] metric, [4][nQ] J, [3][nQ] mesh
-  // velocity), per prism and pyramid the mass matrix coefficients
-  // [4][nM][nM] rounded to FP32 (mk32 at slot_mmoff: the preconditioner of
-  // the stage solves) and per curved-owner face (fmot at 3 FaceRec::cgeo:
+  // velocity), per prism and pyramid the mass matrix coefficients, four
+  // packed lower triangles rounded to FP32 (mk32 at slot_mmoff, row i of a
+  // triangle at i (i + 1) / 2: the preconditioner of the stage solves) and
+  // per curved-owner face (fmot at 3 FaceRec::cgeo:
   // [3][3][n^2] area vector, [3][n^2] mesh velocity).  With mpool set, the
   // volume flux is F(q) - q xdot, the face flux the moving-frame LF flux, and
   // the backward phase returns the rate of the mass-weighted state (no M^{-1}).
