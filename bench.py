@@ -885,10 +885,11 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
     e2e_value = ws * dof * 5 * args.steps / e2e_s
     e2e_ok = bool(torch.equal(torch.from_numpy(mesh.get_state(Qe)), host_out[(args.steps - 1) % 2]))
 
-    # per step: a forward prime and 5 element phases per launch group
-    # (tables sharing N and tile shape), and 5 face phases
+    # per step (one dg_rk_step call): the parameter node of the replayed
+    # graphs, a forward prime and 5 element phases per launch group (tables
+    # sharing N and tile shape), and 5 face phases
     n_groups = len({(N, w) for _, N, w in shapes_main})
-    gpu_launches = args.steps * (6 * n_groups + 5)
+    gpu_launches = args.steps * (1 + 6 * n_groups + 5)
 
     # the batch and Navier-Stokes legs time every rank's replica (barriers and
     # the max over ranks inside), so every rank runs them
