@@ -395,10 +395,11 @@ struct dg_mesh {
   }
 
   // ---- moving meshes
-  int grid_slots() const { return (int)std::max<int64_t>(1, std::min<int64_t>(h.n_elems, (int64_t)num_sms * 8)); }
   void moving_geometry(double t, cudaStream_t st) {
     timed_moving(false, st, [&] {
-      dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, h.n_elems, h.n_faces, h.n, t, grid_slots(), st);
+      // HBM-bound: enough blocks in flight to cover the loads' latency
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h.n_elems, (int64_t)num_sms * 32));
+      dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, h.n_elems, h.n_faces, h.n, t, grid, st);
       return 0;
     });
   }
