@@ -34,10 +34,16 @@ Readings (the paper prints no moving-mesh scheme; shared with the library):
     Ut is exactly M^_s times the constant.  (With the Jacobian at the stage
     time t_s instead, a constant state drifts by O(dt^5) per step.)
   * m6 hexahedra, prisms and pyramids (the types whose maps the motion
-    bends); Euler equations; LF surface flux.
+    bends); LF surface flux.
+  * m7 Navier-Stokes (BR1) on a moving mesh: the lifted gradient of W is a
+    physical-space gradient, so the lifting is the static curved one on the
+    geometry of the stage time (the BR1 reading of the Navier-Stokes
+    oracle); the viscous flux and its central face flux are unchanged; only
+    the convective flux moves to the moving frame (volume F(q) - q xdot,
+    face the moving-frame LF flux of m3).
 
 Parity: pinned by tests/test_oracle_moving.py -- zero velocity reduces to the
-static curved oracle; a constant state stays constant through LSERK steps on
+static curved oracle (Euler and Navier-Stokes); a constant state stays constant through LSERK steps on
 a mesh in motion (m5); the total of int J q over the mesh is conserved; the
 residual of a constant state equals the time derivative of the moments
 int J phi_i (central difference in t); and the advected density wave, an
@@ -51,10 +57,11 @@ import copy
 import numpy as np
 from scipy.linalg import cho_factor, cho_solve
 
-from .curved import CurvedOracle, curved_from_box, shape_functions
+from .curved import CurvedNSOracle, CurvedOracle, curved_from_box, shape_functions
 from .dg import LSERK_A, LSERK_B
 from .elements import TET
 from .euler import physical_flux, pressure, rabs, rmax
+from .navier_stokes import viscous_flux
 
 # Carpenter & Kennedy (1994), (5,4) "solution 3": the stage times
 LSERK_C = np.array([0.0,
@@ -82,16 +89,18 @@ def ale_lax_friedrichs(UL, UR, n, s, gamma):
 
 class MovingOracle:
     """Eq. 1 in the moving frame on a box whose vertices move at the constant
-    velocities `vel` [n_vertices, 3] (readings m1-m6).  States are modal
+    velocities `vel` [n_vertices, 3] (readings m1-m7).  States are modal
     coefficients Q in caller layout at a given time; the LSERK steps evolve
-    the mass-weighted Ut = M(t) Q internally."""
+    the mass-weighted Ut = M(t) Q internally.  mu = None: the Euler
+    equations; a viscosity mu (and Prandtl number Pr): Navier-Stokes (m7)."""
 
-    def __init__(self, box, N, vel, flux="lf", gamma=1.4):
+    def __init__(self, box, N, vel, flux="lf", gamma=1.4, mu=None, Pr=0.72):
         if flux != "lf":
             raise ValueError("the moving-mesh reading takes the LF flux")
         if np.any(np.asarray(box.etype) == TET):
             raise ValueError("the moving-mesh reading covers hexahedra, prisms and pyramids")
         self.box, self.N, self.gamma = box, int(N), gamma
+        self.mu, self.Pr = mu, Pr
         self.vel = np.asarray(vel, dtype=float)
         self._at = {}
         base = self.at(0.0)
@@ -103,7 +112,11 @@ class MovingOracle:
         if t not in self._at:
             b = copy.copy(self.box)
             b.xyz = np.asarray(self.box.xyz, dtype=float) + t * self.vel
-            self._at[t] = CurvedOracle(curved_from_box(b, self.N), flux="lf", gamma=self.gamma)
+            cm = curved_from_box(b, self.N)
+            if self.mu is None:
+                self._at[t] = CurvedOracle(cm, flux="lf", gamma=self.gamma)
+            else:
+                self._at[t] = CurvedNSOracle(cm, flux="lf", gamma=self.gamma, mu=self.mu, Pr=self.Pr)
         return self._at[t]
 
     def mesh_velocity(self, o, e, ref):
@@ -118,20 +131,36 @@ class MovingOracle:
         o = self.at(t)
         m = o.mesh
         R = np.zeros_like(np.asarray(Q, dtype=float))
-        elems = range(m.n_elems) if elems is None else elems
+        elems = list(range(m.n_elems)) if elems is None else list(elems)
+        faces1 = sorted({f for e in elems for f, _ in m.elem_faces[e]})
+        G = None
+        if self.mu is not None:
+            # m7: the BR1 lifted gradient on the geometry of time t, for the
+            # elements whose traces the faces need
+            lift_elems = sorted({x for f in faces1 for x in (m.faces[f][0], m.faces[f][2])})
+            faces2 = sorted({f for e in lift_elems for f, _ in m.elem_faces[e]})
+            wstar = {f: o.face_wstar(Q, f) for f in faces2}
+            G = {e: o.lifting(Q, e, wstar) for e in lift_elems}
         fluxes = {}
-        for f in sorted({f for e in elems for f, _ in m.elem_faces[e]}):
+        for f in faces1:
             e0, l0, e1, _ = m.faces[f]
             phi0, phi1, wS, nrm = o.face_data(f)
             ref0 = m.face_geometry(f)[0]
             s = np.einsum("dp,dp->p", self.mesh_velocity(o, e0, ref0), nrm)
             UL, UR = m.block(Q, e0) @ phi0.T, m.block(Q, e1) @ phi1.T
-            fluxes[f] = wS * ale_lax_friedrichs(UL, UR, nrm, s, self.gamma)
+            Fs = ale_lax_friedrichs(UL, UR, nrm, s, self.gamma)
+            if G is not None:
+                Fv = 0.5 * (viscous_flux(UL, G[e0] @ phi0.T, self.gamma, self.mu, self.Pr)
+                            + viscous_flux(UR, G[e1] @ phi1.T, self.gamma, self.mu, self.Pr))
+                Fs = Fs - np.einsum("dp,dvp->vp", nrm, Fv)
+            fluxes[f] = wS * Fs
         for e in elems:
             op = o.ops[m.etype[e]]
             U = m.block(Q, e) @ op.V.T                                   # [5, nQ]
             F = physical_flux(U, self.gamma)                             # [3(d), 5, nQ]
             F = F - self.mesh_velocity(o, e, op.pts)[:, None, :] * U[None]
+            if G is not None:
+                F = F - viscous_flux(U, G[e] @ op.V.T, self.gamma, self.mu, self.Pr)
             Fc = np.einsum("qkd,dvq->kvq", o.dxi_dx[e], F)
             vol = np.einsum("kqi,kvq->vi", op.G, (op.w * o.Jq[e]) * Fc)
             R[m.dof_off[e]:m.dof_off[e + 1]] = (vol - o.surface_term(Q, e, fluxes)).ravel()

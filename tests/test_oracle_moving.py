@@ -98,3 +98,39 @@ def test_convergence_on_a_moving_mesh():
             err += (w * Jq) @ (rho_h - rho) ** 2
         errs.append(math.sqrt(err))
     assert math.log2(errs[0] / errs[1]) > N + 0.2, errs
+
+
+# ---------------------------------------------------------------- Navier-Stokes (m7)
+def test_ns_zero_velocity_is_the_static_curved_ns_oracle():
+    from oracle.curved import CurvedNSOracle
+    box = di.perturb_vertices(di.box_mesh(2, "mixed", seed=1), 0.1)
+    N, mu = 2, 0.05
+    mo = MovingOracle(box, N, np.zeros_like(box.xyz), mu=mu)
+    co = CurvedNSOracle(curved_from_box(box, N), mu=mu, Pr=0.72)
+    Q = co.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.1))
+    R, Rref = mo.rhs(Q, 0.0), co.rhs(Q)
+    assert np.abs(R - Rref).max() <= 1e-14 * np.abs(Rref).max()
+
+
+def test_ns_with_zero_viscosity_is_the_euler_moving_oracle():
+    box = di.perturb_vertices(di.box_mesh(2, "mixed", seed=1), 0.1)
+    vel = di.vertex_velocities(box.xyz, 0.3)
+    a = MovingOracle(box, 2, vel, mu=0.0)
+    b = MovingOracle(box, 2, vel)
+    Q = b.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.1), 0.0)
+    np.testing.assert_array_equal(a.rate(Q, 0.07), b.rate(Q, 0.07))
+
+
+def test_ns_free_stream_and_conservation_in_motion():
+    """The viscous terms vanish on a constant state, so the discrete GCL keeps
+    it constant through LSERK steps in motion; the Navier-Stokes residual
+    conserves int J q (central viscous face flux)."""
+    box = di.perturb_vertices(di.box_mesh(2, "mixed", seed=1), 0.1)
+    mo = MovingOracle(box, 2, di.vertex_velocities(box.xyz, 0.3), mu=0.05)
+    Qc = constant(mo)
+    Q2 = mo.run(Qc, 0.0, 0.05, 2)
+    assert np.abs(Q2 - Qc).max() < 1e-13 * np.abs(Qc).max()
+    Q = mo.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.1), 0.0)
+    before = mo.integral(Q, 0.0)
+    after = mo.integral(mo.run(Q, 0.0, 0.02, 2), 0.04)
+    assert np.abs(after - before).max() < 1e-13 * np.abs(before).max()
