@@ -186,9 +186,13 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
  * mesh time by nsteps dt; Q_store holds Q at the mesh time before and after.
  * dg_rhs returns M(t)^{-1} (vol - surf) at the mesh time; dg_project and
  * dg_load_vector use the geometry of the mesh time (dg_quad_points returns
- * the points at t = 0).  Requirements: flux DG_FLUX_LF, no tetrahedra, the
- * Euler equations, the weak volume form; the adjoint, the checkpointed steps
- * and dg_autotune return DG_ERR_UNSUPPORTED.  An element that the motion turns
+ * the points at t = 0).  Navier-Stokes (dg_set_physics) runs the BR1 lifting
+ * on the geometry of each stage time -- the lifting of prisms and pyramids
+ * projects with M(t_s)^{-1}, three more stage solves between the two halves
+ * of the volume phase -- with the viscous fluxes unchanged and the convective
+ * flux in the moving frame.  Requirements: flux DG_FLUX_LF, no tetrahedra,
+ * the weak volume form; the adjoint, the checkpointed steps and dg_autotune
+ * return DG_ERR_UNSUPPORTED.  An element that the motion turns
  * inside out makes the next dg_sync return DG_ERR_MESH. */
 dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_velocity, cudaStream_t stream,
                                 dg_mesh** out);

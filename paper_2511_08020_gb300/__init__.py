@@ -461,8 +461,9 @@ class MovingMesh(Mesh):
     """A mesh whose vertices move at constant velocities (dg_mesh_create_moving):
     vertex v sits at xyz[v] + t * velocity[v] at mesh time t (0 at creation).
     rhs evaluates at the mesh time; rk_step advances the state and the mesh
-    time; project projects at the mesh time.  The Euler equations with the
-    LF flux on hexahedra, prisms and pyramids."""
+    time; project projects at the mesh time.  The Euler or (set_physics) the
+    Navier-Stokes equations with the LF flux on hexahedra, prisms and
+    pyramids."""
 
     def __init__(self, box, N, velocity, gamma=1.4, scheduler="balanced", imbalance_threshold=0.1, stream=None):
         import numpy as np

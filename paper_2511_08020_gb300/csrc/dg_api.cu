@@ -74,6 +74,8 @@ struct dg_mesh {
   int64_t *d_slot_moff = nullptr, *d_slot_mmoff = nullptr;
   double *d_mpool = nullptr, *d_fmot = nullptr, *d_Ut = nullptr, *d_S = nullptr;
   float* d_mk32 = nullptr;
+  double* d_lift = nullptr;   // Navier-Stokes on a moving mesh: lifting residuals / gradients [3][n_dof]
+  int lift_phase = 0;
   double gamma = 1.4;
   int scheduler = DG_SCHED_BALANCED;
   double threshold = 0.1;
@@ -390,6 +392,9 @@ struct dg_mesh {
       c.fmot = d_fmot;
       c.mk32 = d_mk32;
       c.slot_mmoff = d_slot_mmoff;
+      c.lift = d_lift;
+      c.lift_stride = h.n_dof;
+      c.lift_phase = lift_phase;
     }
     return c;
   }
@@ -399,20 +404,21 @@ struct dg_mesh {
     timed_moving(false, st, [&] {
       // HBM-bound: enough blocks in flight to cover the loads' latency
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h.n_elems, (int64_t)num_sms * 32));
-      dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, h.n_elems, h.n_faces, h.n, t, grid, st);
+      dgk::launch_moving_geometry(ctx(), d_cpool, d_fgeo, ns ? d_snrm : nullptr, h.n_elems, h.n_faces, h.n, t, grid,
+                                  st);
       return 0;
     });
   }
   // one launch per element type, each with the shared memory its own mass
   // matrices need
   cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st,
-                          const double* x0 = nullptr) {
-    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, x0, tau, weight, st); });
+                          const double* x0 = nullptr, bool dense_only = false) {
+    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, x0, tau, weight, st, dense_only); });
   }
   cudaError_t moving_mass_launches(const double* in, double* out, const double* x0, const double tau[4], int weight,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool dense_only = false) {
     const dgk::Ctx c = ctx();
-    for (int t = 0; t < 3; ++t) {
+    for (int t = dense_only ? 1 : 0; t < 3; ++t) {
       const int64_t cnt = (int64_t)h.type_slots[t].size();
       if (!cnt) continue;
       int nM = 0, nQ = 0;
@@ -434,6 +440,33 @@ struct dg_mesh {
     tau[2] = t * t;
     tau[3] = t * t * t;
   }
+  // The face phase of a moving mesh at time ts.  Navier-Stokes: the lifting
+  // values, then the volume phase in two halves around the lifting's
+  // M(ts)^{-1} for prisms and pyramids (three solves of five variables, the
+  // lifting residual of direction d in d_lift + d n_dof), then the flux.
+  cudaError_t moving_face_phase(double ts, cudaStream_t st) {
+    if (!ns) {
+      face_phase(st);
+      return cudaSuccess;
+    }
+    const int64_t nb = (int64_t)h.face_blocks.size();
+    timed(false, st, [&] { dgk::launch_faces_ns(ctx(), nb, h.n, 0, st); });
+    dgk::StageArgs none{nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+    lift_phase = 1;
+    element_phase(dgk::kNsVolume, none, st);
+    double tau[4];
+    powers(ts, tau);
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+      double* Ld = d_lift + (size_t)d * h.n_dof;
+      e = moving_mass(Ld, Ld, tau, 0, st, nullptr, true);
+    }
+    lift_phase = 2;
+    element_phase(dgk::kNsVolume, none, st);
+    lift_phase = 0;
+    timed(false, st, [&] { dgk::launch_faces_ns(ctx(), nb, h.n, 1, st); });
+    return e;
+  }
   // Residual at the mesh time: M(t)^{-1} (vol - surf).
   cudaError_t moving_rhs(const double* Q, double* R, cudaStream_t st) {
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
@@ -441,7 +474,8 @@ struct dg_mesh {
     moving_geometry(t_mesh, st);
     dgk::StageArgs a{Q, R, nullptr, 0.0, 0.0, 0.0};
     element_phase(dgk::kFwd, a, st);
-    face_phase(st);
+    cudaError_t e = moving_face_phase(t_mesh, st);
+    if (e != cudaSuccess) return e;
     element_phase(dgk::kBwdRhs, a, st);
     double tau[4];
     powers(t_mesh, tau);
@@ -472,7 +506,7 @@ struct dg_mesh {
         if (s > 0 && (e = moving_mass(d_Ut, d_S, y, 0, st, s == 1 ? Q : d_S)) != cudaSuccess) return e;
         dgk::StageArgs f{s > 0 ? d_S : Q, nullptr, nullptr, 0.0, 0.0, 0.0};
         element_phase(dgk::kFwd, f, st);
-        face_phase(st);
+        if ((e = moving_face_phase(ts, st)) != cudaSuccess) return e;
         dgk::StageArgs a{d_Ut, d_Ut, K, kLsA[s], kLsB[s], dt};
         element_phase(dgk::kBwdRk, a, st);
         const double dp[4] = {0.0, 1.0, 2.0 * ts, 3.0 * ts * ts};
@@ -835,7 +869,7 @@ struct dg_mesh {
                     d_cost, d_smns, d_counters, d_chunks_static, d_chunks_weighted, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
                     d_slot_coff, d_cpool, d_fgeo, d_snrm, d_slot_moff, d_mpool, d_fmot, d_Ut, d_S, d_slot_mmoff,
-                    d_mk32};
+                    d_mk32, d_lift};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -1939,8 +1973,6 @@ dg_status dg_set_volume_form(dg_mesh* mesh, int form) {
 dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
   if (physics != DG_EULER && physics != DG_NAVIER_STOKES) return fail(DG_ERR_ARG, "unknown physics");
-  if (physics == DG_NAVIER_STOKES && mesh->moving)
-    return fail(DG_ERR_UNSUPPORTED, "a moving mesh runs the Euler equations");
   if (physics == DG_NAVIER_STOKES && (mesh->split || mesh->flux == DG_FLUX_EC))
     return fail(DG_ERR_UNSUPPORTED, "Navier-Stokes runs with the weak form and the LF or Roe flux");
   if (physics == DG_NAVIER_STOKES) {
@@ -1951,6 +1983,9 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
     if (!mesh->d_Unod && cudaMalloc(&mesh->d_Unod, hb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     if (!mesh->d_L && cudaMalloc(&mesh->d_L, tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     if (!mesh->d_Vt && cudaMalloc(&mesh->d_Vt, 3 * tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
+    if (mesh->moving && !mesh->d_lift &&
+        cudaMalloc(&mesh->d_lift, 3 * sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.n_dof)) != cudaSuccess)
+      return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns, mesh->h.n_curved > 0));
     if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;
     mesh->mu = mu;

@@ -1311,11 +1311,28 @@ __device__ __noinline__ void element_ns_volume_t(const Ctx& c, const TypeTab& T,
   double Jg[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) Jg[k] = g.Jg[k];
+  // moving mesh (lift_phase != 0): prisms and pyramids split at the lifting's
+  // M(t)^{-1}; hexahedra run whole in phase 2
+  const bool dense_split = CURVED && c.lift_phase != 0 && T.type != HEX;
+  if (CURVED && c.lift_phase == 1 && !dense_split) return;
   {
     const double* Un = c.Unod + c.slot_hoff[s];
     for (int w = lane; w < 5 * nQ; w += blockDim.x) bufU[w] = Un[w];
   }
   __syncthreads();
+  if (dense_split && c.lift_phase == 2) {
+    // the solved modal gradient of every direction: nodal values, traces
+    for (int d = 0; d < 3; ++d) {
+      double* dW = bufDW + d * 5 * nQ;
+      const double* Gm = c.lift + (int64_t)d * c.lift_stride + c.slot_qoff[s];
+      double* sG = bufG + 5 * nQ;
+      for (int w = lane; w < 5 * T.nM; w += blockDim.x) sG[w] = Gm[w];
+      __syncthreads();
+      modal_to_nodal(c, T, sG, dW, bufG, lane);
+      write_traces(c, T, s, dW, c.Vt, 1.0, lane, 3, (int64_t)d * 5 * n2);
+      __syncthreads();
+    }
+  } else {
   // Lifting volume terms through the reference directions: with
   // M[l][d] = sum_k wA[l][k] Jg[k][d] (wA = w da_l/dxi_k, structurally sparse
   // per type), Hd = sum_l D_l^T (M[l][d] W) = sum_k Jg[k][d] P_k with
@@ -1417,6 +1434,12 @@ __device__ __noinline__ void element_ns_volume_t(const Ctx& c, const TypeTab& T,
         for (int w = lane; w < 5 * nQ; w += blockDim.x) dW[w] = -g.invJ * bufA[w] / wq[w % nQ];
       }
       __syncthreads();
+    } else if (dense_split) {
+      // phase 1: r_d = -V^T (lifting terms); M(t)^{-1} r_d is solved outside
+      Epilogue ep{Epilogue::kStore, false, -1.0, c.lift + (int64_t)d * c.lift_stride + c.slot_qoff[s], nullptr,
+                  nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
+      nodal_to_modal<false>(c, T, bufA, bufG, lane, ep);
+      continue;
     } else {
       double* sG = bufG + 5 * nQ;
       Epilogue ep{Epilogue::kStore, true, CURVED ? -1.0 : -g.invJ, sG, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0};
@@ -1433,6 +1456,8 @@ __device__ __noinline__ void element_ns_volume_t(const Ctx& c, const TypeTab& T,
       for (int w = lane; w < 5 * nQ; w += blockDim.x) out[w] = dW[w];
     }
     __syncthreads();
+  }
+  if (dense_split) return;   // phase 1 ends with the lifting residuals
   }
   // total contravariant flux G_l = sum_d M[l][d] (F_e - F_v)_d
   for (int q = lane; q < nQ; q += blockDim.x) {
@@ -1454,6 +1479,23 @@ __device__ __noinline__ void element_ns_volume_t(const Ctx& c, const TypeTab& T,
       point_metric(T.type, dp + T.wA + q * 9, Jg, M);
     }
     const double u = W[1], v = W[2], w = W[3], p = W[4], Ep = U[4] + p;
+    if (CURVED && c.mpool) {
+      // moving mesh: the convective flux in the moving frame, F(U) - U xdot
+      const double* xd = c.mpool + c.slot_moff[s] + 31 * nQ;
+      const double x0 = xd[q], x1 = xd[nQ + q], x2 = xd[2 * nQ + q];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const double Vl = M[l][0] * u + M[l][1] * v + M[l][2] * w;
+        const double Rl = Vl - (M[l][0] * x0 + M[l][1] * x1 + M[l][2] * x2);
+        double* G = bufG + l * 5 * nQ + q;
+        G[0] = Rl * U[0];
+        G[nQ] = Rl * U[1] + p * M[l][0] - (M[l][0] * Fv[0][1] + M[l][1] * Fv[1][1] + M[l][2] * Fv[2][1]);
+        G[2 * nQ] = Rl * U[2] + p * M[l][1] - (M[l][0] * Fv[0][2] + M[l][1] * Fv[1][2] + M[l][2] * Fv[2][2]);
+        G[3 * nQ] = Rl * U[3] + p * M[l][2] - (M[l][0] * Fv[0][3] + M[l][1] * Fv[1][3] + M[l][2] * Fv[2][3]);
+        G[4 * nQ] = Rl * U[4] + Vl * p - (M[l][0] * Fv[0][4] + M[l][1] * Fv[1][4] + M[l][2] * Fv[2][4]);
+      }
+      continue;
+    }
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       double Vl = M[l][0] * u + M[l][1] * v + M[l][2] * w;
@@ -2322,8 +2364,16 @@ __global__ void face_ns_kernel(Ctx c) {
         nrm[1] = c.fgeo[R.cgeo + n2 + p];
         nrm[2] = c.fgeo[R.cgeo + 2 * n2 + p];
       }
-      if (c.flux == 0) flux_lf(UL, UR, nrm, gamma, Fs);
-      else flux_roe(UL, UR, nrm, gamma, Fs);
+      if (CURVED && c.fmot && cg) {
+        // moving mesh: the LF flux in the frame of the normal mesh speed
+        const double* xf = c.fmot + 3 * (int64_t)R.cgeo + 9 * n2 + p;
+        const double sn = nrm[0] * xf[0] + nrm[1] * xf[n2] + nrm[2] * xf[2 * n2];
+        flux_lf_moving_scaled(UL, UR, nrm, 1.0, sn, gamma, Fs);
+      } else if (c.flux == 0) {
+        flux_lf(UL, UR, nrm, gamma, Fs);
+      } else {
+        flux_roe(UL, UR, nrm, gamma, Fs);
+      }
       const double* V0 = c.Vt + 3 * R.toff;
       const double* V1 = V0 + 15 * n2;
       double g[15], W[5], Fv[3][5];

@@ -96,6 +96,15 @@ struct Ctx {
   const double* fmot = nullptr;
   const float* mk32 = nullptr;
   const int64_t* slot_mmoff = nullptr;
+  // moving meshes, Navier-Stokes: the lifting of prisms and pyramids projects
+  // with M(t)^{-1}, solved between two volume phases.  lift_phase 1: those
+  // elements write r_d = -V^T (lifting terms) for d = 0..2 to lift (at
+  // d n_dof + the slot's storage offset) and stop; 2: they read the solved
+  // modal gradient there and finish; hexahedra (pointwise 1/J) run whole in
+  // phase 2.  0: the fused phase of static meshes.
+  double* lift = nullptr;
+  int64_t lift_stride = 0;
+  int lift_phase = 0;
 };
 
 // Adjoint arguments (storage layout, device).  rk == 0: Qbar = (dR/dQ)^T Rbar.
@@ -175,11 +184,12 @@ cudaError_t element_kernel_attributes(int nQmax, int warps_per_block, int* block
 cudaError_t element_kernel_attributes_ns(int nQmax, int warps_per_block, int* blocks_per_sm, bool curved = false);
 
 // Moving meshes.  Geometry at time t: the curved metric, J and 1/J of every
-// slot and the normals and w S of every curved-owner face, from the
+// slot, the normals and w S of every curved-owner face and, when snrm is not
+// null, both sides' own normals (the Navier-Stokes lifting), from the
 // coefficients; bit 2 of *status is set where J or S is no longer positive
 // (an element turned inside out).
-void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, int64_t n_slots, int64_t n_faces, int n,
-                            double t, int grid, cudaStream_t st);
+void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, double* snrm, int64_t n_slots,
+                            int64_t n_faces, int n, double t, int grid, cudaStream_t st);
 // Per slot of list[0 .. n_slots): out = M^ in (weight = 1) or out = M^{-1} in
 // (weight = 0), with M^ = V^T diag(w J^) V and J^ = sum_k tau_k J_k
 // (hexahedra, in their scaled nodal storage: pointwise J^).  x0 (or null):

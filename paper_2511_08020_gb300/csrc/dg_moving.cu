@@ -11,7 +11,8 @@
 namespace dgk {
 namespace {
 
-__global__ void moving_geometry_kernel(Ctx c, double* cpool, double* fgeo, int64_t E, int64_t nF, int n, double t) {
+__global__ void moving_geometry_kernel(Ctx c, double* cpool, double* fgeo, double* snrm, int64_t E, int64_t nF, int n,
+                                       double t) {
   for (int64_t s = blockIdx.x; s < E; s += gridDim.x) {
     const TypeTab& T = c.tabs[c.slot_tab[s]];
     const int nQ = T.nQ;
@@ -45,14 +46,33 @@ __global__ void moving_geometry_kernel(Ctx c, double* cpool, double* fgeo, int64
     for (int d = 0; d < 3; ++d) g[d * n2 + p] = A[d] * r;
     g[3 * n2 + p] = S;
     if (!(S > 0.0)) atomicOr(c.status, 4u);
+    if (snrm) {
+      // each side's own outward normals (the Navier-Stokes lifting): the
+      // owner's, and their negatives at the neighbour's points (a permuted
+      // point set; an interpolating map only joins flat triangular faces,
+      // whose normal is constant)
+      double* N0 = snrm + 3 * (R.toff / 5);
+      double* N1 = snrm + 3 * ((R.toff + 5 * (int64_t)n2) / 5);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) N0[d * n2 + p] = A[d] * r;
+      if (R.map >= 0) {
+        const int j = c.perms[(size_t)R.map + p];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) N1[d * n2 + j] = -A[d] * r;
+      } else if (p == 0) {
+        for (int k = 0; k < n2; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) N1[d * n2 + k] = -A[d] * r;
+      }
+    }
   }
 }
 
 }  // namespace
 
-void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, int64_t n_slots, int64_t n_faces, int n,
-                            double t, int grid, cudaStream_t st) {
-  moving_geometry_kernel<<<grid, 128, 0, st>>>(c, cpool, fgeo, n_slots, n_faces, n, t);
+void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, double* snrm, int64_t n_slots,
+                            int64_t n_faces, int n, double t, int grid, cudaStream_t st) {
+  moving_geometry_kernel<<<grid, 128, 0, st>>>(c, cpool, fgeo, snrm, n_slots, n_faces, n, t);
 }
 
 }  // namespace dgk
