@@ -1173,7 +1173,8 @@ MOVING_WORKLOAD = ("the curved 16^3 mixed box (every vertex moved by up to 0.1 h
                    "at x_v + t u_v with u = 0.5 (sin y sin z, sin z sin x, sin x sin y) "
                    "(dg_inputs.vertex_velocities); per stage the geometry at the stage time from its polynomial "
                    "coefficients, the moving-frame residual, and the mass solve with the LSERK stage value of J "
-                   "(Cholesky per prism and pyramid, pointwise for hexahedra); N=4, Euler TGV, LF, FP64")
+                   "(Cholesky per prism and pyramid, pointwise for hexahedra); N=4, Euler TGV (and Navier-Stokes "
+                   "Re 1600 in the navier_stokes key), LF, FP64")
 
 
 def moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, curved_value):
@@ -1246,6 +1247,32 @@ def moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, curved_value)
     clk = CLOCKS.summary(["moving"])
     peak = props.multi_processor_count * 2 * 2 * (clk.get("sm_max_mhz") or 2070.0) / 1e6
     out["clocks"] = clk
+    # Navier-Stokes on the same moving mesh (Re 1600 by the TGV scales):
+    # the lifting's three extra stage solves for prisms and pyramids
+    nsm = dg.MovingMesh(box, N_DEG, vel, scheduler="balanced")
+    nsm.set_element_warps(warps)
+    nsm.set_physics("navier_stokes", 1.0 / 1600.0, 0.72)
+    Qn = nsm.project(torch.from_numpy(vals).to(dev))
+    Kn = torch.empty_like(Qn)
+    for _ in range(args.warmup):
+        nsm.rk_step(Qn, Kn, dt, 1)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with timed_window("moving"):
+        e0.record(stream)
+        for _ in range(steps):
+            nsm.rk_step(Qn, Kn, dt, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ns_ms = max_over_ranks(e0.elapsed_time(e1))
+    nsm.sync()
+    out["navier_stokes"] = {"value": ws * dof * 5 * steps / (ns_ms * 1e-3), "ms_per_step": ns_ms / steps,
+                            "mu": 1.0 / 1600.0, "Pr": 0.72, "finite": bool(torch.isfinite(Qn).all()),
+                            "over_euler_moving": (ns_ms / steps) and out["ms_per_step"] / (ns_ms / steps)}
+    del nsm, Qn, Kn
     out["roofline"] = {"bound": "alu", "kernel": "stage mass kernels (FP64 products, FP32-preconditioned solves)",
                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                        "flops_per_step": fl_step, "mass_launches_per_step": n_mass / steps,
