@@ -412,11 +412,11 @@ struct dg_mesh {
   // one launch per element type, each with the shared memory its own mass
   // matrices need
   cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st,
-                          const double* x0 = nullptr, bool dense_only = false) {
-    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, x0, tau, weight, st, dense_only); });
+                          const double* x0 = nullptr, bool dense_only = false, int nblk = 1) {
+    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, x0, tau, weight, st, dense_only, nblk); });
   }
   cudaError_t moving_mass_launches(const double* in, double* out, const double* x0, const double tau[4], int weight,
-                                   cudaStream_t st, bool dense_only = false) {
+                                   cudaStream_t st, bool dense_only = false, int nblk = 1) {
     const dgk::Ctx c = ctx();
     for (int t = dense_only ? 1 : 0; t < 3; ++t) {
       const int64_t cnt = (int64_t)h.type_slots[t].size();
@@ -429,7 +429,8 @@ struct dg_mesh {
             nQ = std::max(nQ, T.nQ);
           }
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cnt, (int64_t)num_sms * 8));
-      cudaError_t e = dgk::launch_moving_mass(c, d_type_slots[t], cnt, in, out, x0, tau, weight, nM, nQ, grid, st);
+      cudaError_t e = dgk::launch_moving_mass(c, d_type_slots[t], cnt, in, out, x0, tau, weight, nM, nQ, grid, st,
+                                              nblk, h.n_dof);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -456,11 +457,8 @@ struct dg_mesh {
     element_phase(dgk::kNsVolume, none, st);
     double tau[4];
     powers(ts, tau);
-    cudaError_t e = cudaSuccess;
-    for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-      double* Ld = d_lift + (size_t)d * h.n_dof;
-      e = moving_mass(Ld, Ld, tau, 0, st, nullptr, true);
-    }
+    // the three directions with one factor of M(ts) per element
+    cudaError_t e = moving_mass(d_lift, d_lift, tau, 0, st, nullptr, true, 3);
     lift_phase = 2;
     element_phase(dgk::kNsVolume, none, st);
     lift_phase = 0;

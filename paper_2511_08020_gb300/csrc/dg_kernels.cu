@@ -2889,7 +2889,8 @@ __device__ __forceinline__ void mass_correct(const float* L, const float* sc, co
 __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
                                                                    const double* in, double* out, const double* x0,
                                                                    double t0, double t1, double t2, double t3,
-                                                                   int weight, int max_nM, int max_nQ) {
+                                                                   int weight, int max_nM, int max_nQ, int nblk,
+                                                                   int64_t blk_stride) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
   double* x = sm;
@@ -2908,11 +2909,12 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
     const int64_t qoff = c.slot_qoff[s];
     const double* m = c.mpool + c.slot_moff[s];
     if (T.type == HEX) {
-      for (int w = tid; w < 5 * nQ; w += bd) {
-        const int q = w % nQ;
+      for (int w = tid; w < 5 * nQ * nblk; w += bd) {
+        const int kb = w / (5 * nQ), wl = w - kb * 5 * nQ, q = wl % nQ;
+        const int64_t o = qoff + kb * blk_stride + wl;
         const double J = fma(t3, m[30 * nQ + q], fma(t2, m[29 * nQ + q], fma(t1, m[28 * nQ + q], t0 * m[27 * nQ + q])));
-        const double v = in[qoff + w];
-        out[qoff + w] = weight ? v * J : v / J;
+        const double v = in[o];
+        out[o] = weight ? v * J : v / J;
       }
       continue;   // block-uniform branch, no shared memory used
     }
@@ -2996,20 +2998,29 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
       }
       __syncthreads();
     }
-    // from x0 (a nearby state: one correction fewer) or from zero
-    for (int w = tid; w < 5 * nM; w += bd) {
-      x[w] = x0 ? x0[qoff + w] : 0.0;
-      r[w] = b[w];
+    // every block of five variables with the one factor (nblk > 1: the
+    // lifting's three directions), from x0 (a nearby solution: one
+    // correction fewer) or from zero
+    for (int kb = 0; kb < nblk; ++kb) {
+      const int64_t o = qoff + kb * blk_stride;
+      if (kb > 0) {
+        for (int w = tid; w < 5 * nM; w += bd) b[w] = in[o + w];
+        __syncthreads();
+      }
+      for (int w = tid; w < 5 * nM; w += bd) {
+        x[w] = x0 ? x0[o + w] : 0.0;
+        r[w] = b[w];
+      }
+      __syncthreads();
+      if (x0) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
+      const int ncorr = x0 ? 2 : 3;
+      for (int it = 0; it < ncorr; ++it) {
+        mass_correct(L, sc, rdiag, r, x, nM);
+        if (it + 1 < ncorr) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
+      }
+      for (int w = tid; w < 5 * nM; w += bd) out[o + w] = x[w];
+      __syncthreads();
     }
-    __syncthreads();
-    if (x0) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
-    const int ncorr = x0 ? 2 : 3;
-    for (int it = 0; it < ncorr; ++it) {
-      mass_correct(L, sc, rdiag, r, x, nM);
-      if (it + 1 < ncorr) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
-    }
-    for (int w = tid; w < 5 * nM; w += bd) out[qoff + w] = x[w];
-    __syncthreads();
   }
 }
 
@@ -3236,7 +3247,8 @@ void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int
 
 cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
                                const double* x0, const double* tau, int weight, int max_nM, int max_nQ, int grid,
-                               cudaStream_t st) {
+                               cudaStream_t st, int nblk, int64_t blk_stride) {
+  if (weight && nblk != 1) return cudaErrorInvalidValue;
   if (max_nM > 32 * kMassRows) return cudaErrorInvalidValue;
   size_t bytes = 0;
   if (max_nM > 0)
@@ -3246,7 +3258,7 @@ cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slot
     if (e != cudaSuccess) return e;
   }
   moving_mass_kernel<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, x0, tau[0], tau[1], tau[2],
-                                                         tau[3], weight, max_nM, max_nQ);
+                                                         tau[3], weight, max_nM, max_nQ, nblk, blk_stride);
   return cudaGetLastError();
 }
 

@@ -195,9 +195,11 @@ void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, double* s
 // (hexahedra, in their scaled nodal storage: pointwise J^).  x0 (or null):
 // a nearby solution the solve starts from.  out may alias in or x0.
 // max_nM / max_nQ: the largest prism / pyramid mode and point counts among
-// the listed slots (0 if none: shared memory).
+// the listed slots (0 if none: shared memory).  nblk (solves only): blocks of
+// five variables at the slot's storage offset + k blk_stride, all solved
+// with one factor of M^.
 cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
                                const double* x0, const double* tau, int weight, int max_nM, int max_nQ, int grid,
-                               cudaStream_t st);
+                               cudaStream_t st, int nblk = 1, int64_t blk_stride = 0);
 
 }  // namespace dgk
