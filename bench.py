@@ -221,6 +221,11 @@ FACE_POINT_FLOPS_NS = {"lift": 36, "lf": 101 + 2 * (13 + 66 + 30) + 10, "roe": 2
 # capture of the element kernel on the 16^3 N = 4 mesh; set to None whenever
 # the element kernel changes until it is captured again.
 NCU_TRAFFIC_FUSED_LAUNCH = (154.316032 + 144.723456) * 1e6
+# the same capture's executed FP64 rate: (2 DFMA + DMUL + DADD thread
+# instructions per cycle, all SMs) x the SM clock of the launch, and the FP64
+# pipe's busy fraction (the same rule: None once the kernel changes)
+NCU_FP64_FUSED_LAUNCH = {"executed_tflops": (2 * 215.843480 + 31.503288 + 1.640137) * 2.073804e9 / 1e12,
+                         "fp64_pipe_busy": 0.92798396}
 
 
 def fp64_probes():
@@ -933,6 +938,7 @@ def run_ours_legs(args, dg, torch, ws, rank, local, box, dev, stream, barrier, m
                                   f"{sm_max_ghz:.3f} GHz (max SM clock of the run)",
                      "dfma_loop_measured": dfma, "frac_of_dfma_loop": elem_tflops / dfma,
                      "traffic": NCU_TRAFFIC_FUSED_LAUNCH,
+                     "ncu_fp64": NCU_FP64_FUSED_LAUNCH,
                      "traffic_source": "ncu dram read+write of one fused element launch (16^3 mixed, N = 4)",
                      "algorithmic_bytes_per_stage": el_bytes_stage, "algorithmic_flops_per_stage": el_flops_stage,
                      "element_ms_per_step": elem_ms / steps_p, "face_ms_per_step": face_ms / steps_p,
