@@ -144,6 +144,39 @@ def test_batch_argument_checks_without_gpu(dg):
     assert ei.value.status == -3
 
 
+def test_moving_and_partition_argument_checks_without_gpu(dg):
+    """The moving-mesh and stage-wise entry points validate their arguments
+    before touching a device: a null or non-finite velocity field and null
+    handles are DG_ERR_ARG, a moving mesh with the Roe flux is
+    DG_ERR_UNSUPPORTED, and a valid moving mesh without a GPU is DG_ERR_CUDA
+    (no CPU path)."""
+    import ctypes
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    lib = dg.load()
+    box = di.perturb_vertices(di.box_mesh(2, "mixed", seed=1), 0.1)
+    d, keep = dg._desc(box, 2, flux="lf", geometry="vertex")
+    h = ctypes.c_void_p()
+    assert lib.dg_mesh_create_moving(ctypes.byref(d), None, None, ctypes.byref(h)) == -1
+    bad = np.full_like(box.xyz, np.nan)
+    assert lib.dg_mesh_create_moving(ctypes.byref(d), dg._ptr(bad), None, ctypes.byref(h)) == -1
+    vel = np.ascontiguousarray(di.vertex_velocities(box.xyz, 0.1))
+    droe, _ = dg._desc(box, 2, flux="roe", geometry="vertex")
+    assert lib.dg_mesh_create_moving(ctypes.byref(droe), dg._ptr(vel), None, ctypes.byref(h)) == -7
+    t = ctypes.c_double()
+    assert lib.dg_mesh_time(None, ctypes.byref(t)) == -1
+    assert lib.dg_set_mesh_time(None, 0.1) == -1
+    assert lib.dg_rk_stage_lift(None, None) == -1
+    assert lib.dg_halo_pack_gradients(None, None, None) == -1
+    assert lib.dg_halo_unpack_gradients(None, None, None) == -1
+    assert lib.dg_moving_phase_times(None, None, None) == -1
+    ne, nf = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.dg_geometry_at(None, None, 0.0, ctypes.byref(ne), ctypes.byref(nf), None, None) == -1
+    assert lib.dg_geometry_at(ctypes.byref(d), None, float("nan"), ctypes.byref(ne), ctypes.byref(nf), None, None) == -1
+    if not torch.cuda.is_available():
+        assert lib.dg_mesh_create_moving(ctypes.byref(d), dg._ptr(vel), None, ctypes.byref(h)) == -3
+
+
 @pytest.mark.parametrize("kind,m,N,reorder", [("mixed", 3, 3, False), ("four", 4, 2, True), ("hex", 2, 4, True),
                                               ("pyramid", 2, 2, True), ("prism", 2, 3, False)])
 def test_curved_host_setup_matches_oracle(dg, kind, m, N, reorder):
