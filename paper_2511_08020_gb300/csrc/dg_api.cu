@@ -2337,12 +2337,16 @@ dg_status dg_sync(dg_mesh* mesh, cudaStream_t stream) {
   DG_CUDA(cudaStreamSynchronize(stream));
   unsigned st = 0;
   DG_CUDA(cudaMemcpy(&st, mesh->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  // the flag is cleared on the caller's stream, so the next launch there
+  // starts from a clean status
   if (st & 4u) {
-    cudaMemset(mesh->d_status, 0, sizeof(unsigned));
+    DG_CUDA(cudaMemsetAsync(mesh->d_status, 0, sizeof(unsigned), stream));
+    DG_CUDA(cudaStreamSynchronize(stream));
     return fail(DG_ERR_MESH, "the moving mesh turned an element inside out (J or the face area reached zero)");
   }
   if (st & 1u) {
-    cudaMemset(mesh->d_status, 0, sizeof(unsigned));
+    DG_CUDA(cudaMemsetAsync(mesh->d_status, 0, sizeof(unsigned), stream));
+    DG_CUDA(cudaStreamSynchronize(stream));
     return fail(DG_ERR_NONFINITE, "a non-finite state value was produced");
   }
   return DG_OK;

@@ -2946,41 +2946,67 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
       for (int k = lane; k <= a; k += 32) L[lro(a) + k] *= sa * sc[k];
     }
     __syncthreads();
-    // right-looking Cholesky, two columns per pass: columns j and j+1, then
-    // the rank-2 update of the trailing lower triangle (its pairs numbered
-    // row by row so every lane takes one); L's diagonal is kept as its
-    // reciprocal in rdiag
-    for (int j = 0; j < nM; j += 2) {
-      const bool two = j + 1 < nM;
-      const float rd = rsqrtf(L[lro(j) + j]);
-      for (int i = j + 1 + tid; i < nM; i += bd) L[lro(i) + j] *= rd;
-      if (tid == 0) rdiag[j] = rd;
-      __syncthreads();
-      if (two) {
-        const float l = L[lro(j + 1) + j];
-        for (int i = j + 1 + tid; i < nM; i += bd) L[lro(i) + j + 1] = fmaf(-L[lro(i) + j], l, L[lro(i) + j + 1]);
-        __syncthreads();
-        const float rd1 = rsqrtf(L[lro(j + 1) + j + 1]);
-        for (int i = j + 2 + tid; i < nM; i += bd) L[lro(i) + j + 1] *= rd1;
-        if (tid == 0) rdiag[j + 1] = rd1;
-        __syncthreads();
+    // right-looking Cholesky in panels of four columns.  Warp 0 factors the
+    // panel in registers (rows by lane, one shuffle per pivot and per later
+    // panel column) and writes it back to L and, row by row, to pan; then the
+    // five warps apply the rank-4 update to the trailing lower triangle, four
+    // rows per warp at a time (independent chains that share each column's
+    // load).  Two barriers per panel.  L's diagonal is kept as its reciprocal
+    // in rdiag.  pan lives in the transform buffer, idle until the first
+    // product, on a 16-byte boundary.
+    float4* pan = reinterpret_cast<float4*>(bufA + ((15 * max_nM + max_nQ) & 1));
+    for (int j0 = 0; j0 < nM; j0 += 4) {
+      const int pw = min(4, nM - j0);
+      if (warp == 0) {
+        float p[kMassRows][4];
+#pragma unroll
+        for (int m = 0; m < kMassRows; ++m) {
+          const int i = j0 + lane + 32 * m, ic = min(i, nM - 1);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+            p[m][cc] = (i < nM && cc < pw && j0 + cc <= i) ? L[lro(ic) + min(j0 + cc, ic)] : 0.0f;
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          if (cc < pw) {
+            // row j0 + cc is lane cc of the first register row
+            const float rd = rsqrtf(__shfl_sync(0xffffffffu, p[0][cc], cc));
+            if (lane == 0) rdiag[j0 + cc] = rd;
+#pragma unroll
+            for (int m = 0; m < kMassRows; ++m)
+              if (lane + 32 * m > cc) p[m][cc] *= rd;
+#pragma unroll
+            for (int c2 = cc + 1; c2 < 4; ++c2) {
+              const float l = __shfl_sync(0xffffffffu, p[0][cc], c2);
+#pragma unroll
+              for (int m = 0; m < kMassRows; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < kMassRows; ++m) {
+          const int i = j0 + lane + 32 * m;
+          if (i < nM) {
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+              if (cc < pw && j0 + cc < i) L[lro(i) + j0 + cc] = p[m][cc];
+            if (i >= j0 + pw)
+              pan[i] = make_float4(p[m][0], pw > 1 ? p[m][1] : 0.0f, pw > 2 ? p[m][2] : 0.0f, pw > 3 ? p[m][3] : 0.0f);
+          }
+        }
       }
-      // trailing rows by warp, four rows at a time (independent chains that
-      // share the column loads), their columns by lane; each row's two
-      // multipliers are loaded once
-      const int j0 = j + (two ? 2 : 1);
-      for (int i = j0 + warp; i < nM; i += 4 * nwarps) {
-        float l0[4], l1[4];
+      __syncthreads();
+      const int jt = j0 + pw;
+      for (int i = jt + warp; i < nM; i += 4 * nwarps) {
+        float4 lr[4];
         int last = i;
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-          const int ig = min(i + g * nwarps, nM - 1);
-          l0[g] = L[lro(ig) + j];
-          l1[g] = two ? L[lro(ig) + j + 1] : 0.0f;
+          lr[g] = pan[min(i + g * nwarps, nM - 1)];
           if (i + g * nwarps < nM) last = i + g * nwarps;
         }
-        for (int k = j0 + lane; k <= last; k += 32) {
-          const float c0 = L[lro(k) + j], c1 = two ? L[lro(k) + j + 1] : 0.0f;
+        for (int k = jt + lane; k <= last; k += 32) {
+          const float4 ck = pan[k];
           float v[4];
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
@@ -2988,7 +3014,8 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
             v[g] = (ig < nM && k <= ig) ? L[lro(min(ig, nM - 1)) + k] : 0.0f;
           }
 #pragma unroll
-          for (int g = 0; g < 4; ++g) v[g] = fmaf(-l1[g], c1, fmaf(-l0[g], c0, v[g]));
+          for (int g = 0; g < 4; ++g)
+            v[g] = fmaf(-lr[g].w, ck.w, fmaf(-lr[g].z, ck.z, fmaf(-lr[g].y, ck.y, fmaf(-lr[g].x, ck.x, v[g]))));
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int ig = i + g * nwarps;
