@@ -191,8 +191,9 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
  * projects with M(t_s)^{-1}, three more stage solves between the two halves
  * of the volume phase -- with the viscous fluxes unchanged and the convective
  * flux in the moving frame.  Requirements: flux DG_FLUX_LF, no tetrahedra,
- * the weak volume form; the adjoint, the checkpointed steps and dg_autotune
- * return DG_ERR_UNSUPPORTED.  An element that the motion turns
+ * the weak volume form; the adjoint, the checkpointed steps, dg_autotune and
+ * the stage-by-stage calls of partitioned solves (dg_rk_prime, dg_rk_stage,
+ * dg_rk_stage_lift) return DG_ERR_UNSUPPORTED.  An element that the motion turns
  * inside out makes the next dg_sync return DG_ERR_MESH. */
 dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_velocity, cudaStream_t stream,
                                 dg_mesh** out);

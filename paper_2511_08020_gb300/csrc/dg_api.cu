@@ -74,7 +74,14 @@ struct dg_mesh {
   int64_t *d_slot_moff = nullptr, *d_slot_mmoff = nullptr;
   double *d_mpool = nullptr, *d_fmot = nullptr, *d_Ut = nullptr, *d_S = nullptr;
   float* d_mk32 = nullptr;
-  double* d_lift = nullptr;   // Navier-Stokes on a moving mesh: lifting residuals / gradients [3][n_dof]
+  double* d_lift = nullptr;   // Navier-Stokes on a moving mesh: lifting residuals [3][n_dof]
+  double* d_G = nullptr;      // ... and the lifted gradients that solve them [3][n_dof]
+  bool G_warm = false;        // d_G holds the previous stage's gradients (this call's)
+  // the FP32 factors of the last stage solve, at the offsets of d_mk32
+  // ([L][s][rdiag] per prism and pyramid), for the lifting of the same stage
+  float* d_fac = nullptr;
+  int64_t n_mk32 = 0;
+  bool fac_ready = false;
   int lift_phase = 0;
   double gamma = 1.4;
   int scheduler = DG_SCHED_BALANCED;
@@ -392,7 +399,8 @@ struct dg_mesh {
       c.fmot = d_fmot;
       c.mk32 = d_mk32;
       c.slot_mmoff = d_slot_mmoff;
-      c.lift = d_lift;
+      // phase 1 writes the lifting residuals, phase 2 reads the gradients
+      c.lift = lift_phase == 2 ? d_G : d_lift;
       c.lift_stride = h.n_dof;
       c.lift_phase = lift_phase;
     }
@@ -412,11 +420,14 @@ struct dg_mesh {
   // one launch per element type, each with the shared memory its own mass
   // matrices need
   cudaError_t moving_mass(const double* in, double* out, const double tau[4], int weight, cudaStream_t st,
-                          const double* x0 = nullptr, bool dense_only = false, int nblk = 1) {
-    return timed_moving(true, st, [&] { return moving_mass_launches(in, out, x0, tau, weight, st, dense_only, nblk); });
+                          const double* x0 = nullptr, bool dense_only = false, int nblk = 1,
+                          float* fac_out = nullptr, const float* fac_in = nullptr) {
+    return timed_moving(true, st, [&] {
+      return moving_mass_launches(in, out, x0, tau, weight, st, dense_only, nblk, fac_out, fac_in);
+    });
   }
   cudaError_t moving_mass_launches(const double* in, double* out, const double* x0, const double tau[4], int weight,
-                                   cudaStream_t st, bool dense_only = false, int nblk = 1) {
+                                   cudaStream_t st, bool dense_only, int nblk, float* fac_out, const float* fac_in) {
     const dgk::Ctx c = ctx();
     for (int t = dense_only ? 1 : 0; t < 3; ++t) {
       const int64_t cnt = (int64_t)h.type_slots[t].size();
@@ -430,7 +441,7 @@ struct dg_mesh {
           }
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cnt, (int64_t)num_sms * 8));
       cudaError_t e = dgk::launch_moving_mass(c, d_type_slots[t], cnt, in, out, x0, tau, weight, nM, nQ, grid, st,
-                                              nblk, h.n_dof);
+                                              nblk, h.n_dof, fac_out, fac_in);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -457,8 +468,15 @@ struct dg_mesh {
     element_phase(dgk::kNsVolume, none, st);
     double tau[4];
     powers(ts, tau);
-    // the three directions with one factor of M(ts) per element
-    cudaError_t e = moving_mass(d_lift, d_lift, tau, 0, st, nullptr, true, 3);
+    // the three directions with one factor of M(ts) per element -- the one
+    // the stage's state solve kept, whose matrix M^ of the stage values y_k
+    // differs from M(ts) by the stages' error in integrating t^k (about
+    // dt^2, far below the factor's FP32 rounding) -- started from the
+    // previous stage's gradients (one correction fewer) once this call has
+    // them
+    cudaError_t e = moving_mass(d_lift, d_G, tau, 0, st, G_warm ? d_G : nullptr, true, 3, nullptr,
+                                fac_ready ? d_fac : nullptr);
+    G_warm = true;
     lift_phase = 2;
     element_phase(dgk::kNsVolume, none, st);
     lift_phase = 0;
@@ -469,6 +487,8 @@ struct dg_mesh {
   cudaError_t moving_rhs(const double* Q, double* R, cudaStream_t st) {
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
     parity = 0;
+    G_warm = false;
+    fac_ready = false;
     moving_geometry(t_mesh, st);
     dgk::StageArgs a{Q, R, nullptr, 0.0, 0.0, 0.0};
     element_phase(dgk::kFwd, a, st);
@@ -483,25 +503,35 @@ struct dg_mesh {
   // Stage s evaluates the residual at t_s = t + c_s dt on the geometry of
   // t_s, from the stage state M^_s^{-1} Ut with M^_s built from the stage
   // values y_k of t^k, which run through the same 2N-storage recursion
-  // (dy_k/dt = k t^(k-1)).
+  // (dy_k/dt = k t^(k-1)).  The product Ut = M(t) Q runs once per call: a
+  // fourth-order scheme integrates k t^(k-1) (degree <= 2) exactly, so the
+  // last stage's y_k are the powers of t + dt and the Ut it leaves is
+  // M(t + dt) Q_{n+1} up to the rounding of the end-of-step solve -- the
+  // next step's product would only reproduce it.
   cudaError_t moving_rk(double* Q, double* K, double dt, int nsteps, cudaStream_t st) {
     static const double kLsC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363183857.0,
                                    2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
     cudaError_t e = cudaSuccess;
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned), st);
     parity = 0;
+    G_warm = false;   // a caller may change the state between calls
+    fac_ready = false;
+    float* keep = ns ? d_fac : nullptr;
     for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
       const double t = t_mesh;
       double y[4], Ky[4] = {0.0, 0.0, 0.0, 0.0};
       powers(t, y);
-      if ((e = moving_mass(Q, d_Ut, y, 1, st)) != cudaSuccess) return e;
+      if (step == 0 && (e = moving_mass(Q, d_Ut, y, 1, st)) != cudaSuccess) return e;
       for (int s = 0; s < 5; ++s) {
         const double ts = t + kLsC[s] * dt;
         moving_geometry(ts, st);
         // the first stage's state is Q itself (its solve would undo the
         // product above up to rounding)
         // later stages start their solve from the previous stage's state
-        if (s > 0 && (e = moving_mass(d_Ut, d_S, y, 0, st, s == 1 ? Q : d_S)) != cudaSuccess) return e;
+        if (s > 0) {
+          if ((e = moving_mass(d_Ut, d_S, y, 0, st, s == 1 ? Q : d_S, false, 1, keep)) != cudaSuccess) return e;
+          fac_ready = keep != nullptr;
+        }
         dgk::StageArgs f{s > 0 ? d_S : Q, nullptr, nullptr, 0.0, 0.0, 0.0};
         element_phase(dgk::kFwd, f, st);
         if ((e = moving_face_phase(ts, st)) != cudaSuccess) return e;
@@ -513,7 +543,10 @@ struct dg_mesh {
           y[k] += kLsB[s] * Ky[k];
         }
       }
-      if ((e = moving_mass(d_Ut, Q, y, 0, st, d_S)) != cudaSuccess) return e;
+      // the step's end: y_k are the powers of t + dt, so its factor serves
+      // the next step's first lifting as well
+      if ((e = moving_mass(d_Ut, Q, y, 0, st, d_S, false, 1, keep)) != cudaSuccess) return e;
+      fac_ready = keep != nullptr;
       t_mesh = t + dt;
     }
     return cudaGetLastError();
@@ -867,7 +900,7 @@ struct dg_mesh {
                     d_cost, d_smns, d_counters, d_chunks_static, d_chunks_weighted, d_stage,
                     d_Tv, d_Kbar, d_ckpt, d_Unod, d_L, d_Vt, d_fnrm, d_DW, d_Vtb, d_sstore, d_ckpt_q,
                     d_slot_coff, d_cpool, d_fgeo, d_snrm, d_slot_moff, d_mpool, d_fmot, d_Ut, d_S, d_slot_mmoff,
-                    d_mk32, d_lift};
+                    d_mk32, d_lift, d_G, d_fac};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& p : d_type_slots)
@@ -984,6 +1017,7 @@ dg_status dg_mesh_create_moving(const dg_mesh_desc* desc, const double* vertex_v
     }
   }
   if (mk32.empty()) mk32.push_back(0.0f);
+  made->n_mk32 = (int64_t)mk32.size();
   cudaError_t e = upload(&made->d_slot_moff, mo.slot_moff);
   if (e == cudaSuccess) e = upload(&made->d_slot_mmoff, slot_m32off);
   if (e == cudaSuccess) e = upload(&made->d_mk32, mk32);
@@ -1434,6 +1468,7 @@ dg_status dg_halo_unpack_gradients(dg_mesh* mesh, const double* recv, cudaStream
 
 dg_status dg_rk_stage_lift(dg_mesh* mesh, cudaStream_t stream) {
   if (!mesh) return fail(DG_ERR_ARG, "null mesh");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "a moving mesh steps with dg_rk_step: every stage needs the geometry of its time and a mass solve");
   if (!mesh->ns) return fail(DG_ERR_UNSUPPORTED, "the lifting half-stage belongs to the Navier-Stokes equations");
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
@@ -1448,6 +1483,7 @@ dg_status dg_rk_stage_lift(dg_mesh* mesh, cudaStream_t stream) {
 
 dg_status dg_rk_prime(dg_mesh* mesh, const double* Q_store, cudaStream_t stream) {
   if (!mesh || !Q_store) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "a moving mesh steps with dg_rk_step: every stage needs the geometry of its time and a mass solve");
   mesh->lift_done = false;
   DG_CUDA(cudaMemsetAsync(mesh->d_counters, 0, 2 * sizeof(unsigned), stream));
   mesh->parity = 0;
@@ -1461,6 +1497,7 @@ dg_status dg_rk_prime(dg_mesh* mesh, const double* Q_store, cudaStream_t stream)
 dg_status dg_rk_stage(dg_mesh* mesh, double* Q_store, double* K_store, double dt, int stage, int last,
                       cudaStream_t stream) {
   if (!mesh || !Q_store || !K_store) return fail(DG_ERR_ARG, "null argument");
+  if (mesh->moving) return fail(DG_ERR_UNSUPPORTED, "a moving mesh steps with dg_rk_step: every stage needs the geometry of its time and a mass solve");
   if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must lie in 0..4");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be finite");
   if (mesh->ns && !mesh->lift_done)
@@ -1981,8 +2018,13 @@ dg_status dg_set_physics(dg_mesh* mesh, int physics, double mu, double Pr) {
     if (!mesh->d_Unod && cudaMalloc(&mesh->d_Unod, hb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     if (!mesh->d_L && cudaMalloc(&mesh->d_L, tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     if (!mesh->d_Vt && cudaMalloc(&mesh->d_Vt, 3 * tb) != cudaSuccess) return fail(DG_ERR_OOM, "Navier-Stokes workspace");
-    if (mesh->moving && !mesh->d_lift &&
-        cudaMalloc(&mesh->d_lift, 3 * sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.n_dof)) != cudaSuccess)
+    const size_t lb = 3 * sizeof(double) * (size_t)std::max<int64_t>(1, mesh->h.n_dof);
+    if (mesh->moving && !mesh->d_lift && cudaMalloc(&mesh->d_lift, lb) != cudaSuccess)
+      return fail(DG_ERR_OOM, "Navier-Stokes workspace");
+    if (mesh->moving && !mesh->d_G && cudaMalloc(&mesh->d_G, lb) != cudaSuccess)
+      return fail(DG_ERR_OOM, "Navier-Stokes workspace");
+    if (mesh->moving && !mesh->d_fac &&
+        cudaMalloc(&mesh->d_fac, sizeof(float) * (size_t)std::max<int64_t>(1, mesh->n_mk32)) != cudaSuccess)
       return fail(DG_ERR_OOM, "Navier-Stokes workspace");
     DG_CUDA(dgk::element_kernel_attributes_ns(mesh->nQmax, mesh->wpb, &mesh->blocks_per_sm_ns, mesh->h.n_curved > 0));
     if (mesh->blocks_per_sm_ns < 1) mesh->blocks_per_sm_ns = 1;

@@ -2886,13 +2886,114 @@ __device__ __forceinline__ void mass_correct(const float* L, const float* sc, co
   else mass_correct_t<4>(L, sc, rdiag, r, x, nM);
 }
 
+// The FP32 factor L L^T = S M^ S of one element (S = diag(M^)^{-1/2}), from
+// the four packed FP32 coefficient triangles Mk and the powers f of the
+// stage time; pan: four floats per row on a 16-byte boundary (scratch).
+__device__ void mass_factor(const float* Mk, float f0, float f1, float f2, float f3, float* L, float* sc, float* rdiag,
+                            float4* pan, int nM) {
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
+  const int np = lro(nM);
+  // FP32 S M^ S from the FP32 coefficients, all four kept packed (lower
+  // triangle, the layout of L): contiguous loads, then the scaling in
+  // shared memory
+#pragma unroll 4
+  for (int u = tid; u < np; u += bd)
+    L[u] = fmaf(f3, Mk[3 * np + u], fmaf(f2, Mk[2 * np + u], fmaf(f1, Mk[np + u], f0 * Mk[u])));
+  __syncthreads();
+  for (int a = tid; a < nM; a += bd) sc[a] = rsqrtf(L[lro(a) + a]);
+  __syncthreads();
+  for (int a = warp; a < nM; a += nwarps) {
+    const float sa = sc[a];
+    for (int k = lane; k <= a; k += 32) L[lro(a) + k] *= sa * sc[k];
+  }
+  __syncthreads();
+  // right-looking Cholesky in panels of four columns.  Warp 0 factors the
+  // panel in registers (rows by lane, one shuffle per pivot and per later
+  // panel column) and writes it back to L and, row by row, to pan; then the
+  // five warps apply the rank-4 update to the trailing lower triangle, four
+  // rows per warp at a time (independent chains that share each column's
+  // load).  Two barriers per panel.  L's diagonal is kept as its reciprocal
+  // in rdiag.
+  for (int j0 = 0; j0 < nM; j0 += 4) {
+    const int pw = min(4, nM - j0);
+    if (warp == 0) {
+      float p[kMassRows][4];
+#pragma unroll
+      for (int m = 0; m < kMassRows; ++m) {
+        const int i = j0 + lane + 32 * m, ic = min(i, nM - 1);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+          p[m][cc] = (i < nM && cc < pw && j0 + cc <= i) ? L[lro(ic) + min(j0 + cc, ic)] : 0.0f;
+      }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        if (cc < pw) {
+          // row j0 + cc is lane cc of the first register row
+          const float rd = rsqrtf(__shfl_sync(0xffffffffu, p[0][cc], cc));
+          if (lane == 0) rdiag[j0 + cc] = rd;
+#pragma unroll
+          for (int m = 0; m < kMassRows; ++m)
+            if (lane + 32 * m > cc) p[m][cc] *= rd;
+#pragma unroll
+          for (int c2 = cc + 1; c2 < 4; ++c2) {
+            const float l = __shfl_sync(0xffffffffu, p[0][cc], c2);
+#pragma unroll
+            for (int m = 0; m < kMassRows; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < kMassRows; ++m) {
+        const int i = j0 + lane + 32 * m;
+        if (i < nM) {
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+            if (cc < pw && j0 + cc < i) L[lro(i) + j0 + cc] = p[m][cc];
+          if (i >= j0 + pw)
+            pan[i] = make_float4(p[m][0], pw > 1 ? p[m][1] : 0.0f, pw > 2 ? p[m][2] : 0.0f, pw > 3 ? p[m][3] : 0.0f);
+        }
+      }
+    }
+    __syncthreads();
+    const int jt = j0 + pw;
+    for (int i = jt + warp; i < nM; i += 4 * nwarps) {
+      float4 lr[4];
+      int last = i;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        lr[g] = pan[min(i + g * nwarps, nM - 1)];
+        if (i + g * nwarps < nM) last = i + g * nwarps;
+      }
+      for (int k = jt + lane; k <= last; k += 32) {
+        const float4 ck = pan[k];
+        float v[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int ig = i + g * nwarps;
+          v[g] = (ig < nM && k <= ig) ? L[lro(min(ig, nM - 1)) + k] : 0.0f;
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          v[g] = fmaf(-lr[g].w, ck.w, fmaf(-lr[g].z, ck.z, fmaf(-lr[g].y, ck.y, fmaf(-lr[g].x, ck.x, v[g]))));
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int ig = i + g * nwarps;
+          if (ig < nM && k <= ig) L[lro(ig) + k] = v[g];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
                                                                    const double* in, double* out, const double* x0,
                                                                    double t0, double t1, double t2, double t3,
                                                                    int weight, int max_nM, int max_nQ, int nblk,
-                                                                   int64_t blk_stride) {
+                                                                   int64_t blk_stride, float* fac_out,
+                                                                   const float* fac_in) {
   extern __shared__ double sm[];
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
+  const int tid = threadIdx.x, bd = blockDim.x;
   double* x = sm;
   double* b = x + 5 * max_nM;
   double* r = b + 5 * max_nM;
@@ -2929,101 +3030,31 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
       __syncthreads();
       continue;
     }
-    // FP32 S M^ S from the FP32 coefficients, all four kept packed (lower
-    // triangle, the layout of L): contiguous loads, then the scaling in
-    // shared memory
     const int np = lro(nM);
-    const float* Mk = c.mk32 + c.slot_mmoff[s];
-    const float f0 = (float)t0, f1 = (float)t1, f2 = (float)t2, f3 = (float)t3;
-#pragma unroll 4
-    for (int u = tid; u < np; u += bd)
-      L[u] = fmaf(f3, Mk[3 * np + u], fmaf(f2, Mk[2 * np + u], fmaf(f1, Mk[np + u], f0 * Mk[u])));
-    __syncthreads();
-    for (int a = tid; a < nM; a += bd) sc[a] = rsqrtf(L[lro(a) + a]);
-    __syncthreads();
-    for (int a = warp; a < nM; a += nwarps) {
-      const float sa = sc[a];
-      for (int k = lane; k <= a; k += 32) L[lro(a) + k] *= sa * sc[k];
-    }
-    __syncthreads();
-    // right-looking Cholesky in panels of four columns.  Warp 0 factors the
-    // panel in registers (rows by lane, one shuffle per pivot and per later
-    // panel column) and writes it back to L and, row by row, to pan; then the
-    // five warps apply the rank-4 update to the trailing lower triangle, four
-    // rows per warp at a time (independent chains that share each column's
-    // load).  Two barriers per panel.  L's diagonal is kept as its reciprocal
-    // in rdiag.  pan lives in the transform buffer, idle until the first
-    // product, on a 16-byte boundary.
-    float4* pan = reinterpret_cast<float4*>(bufA + ((15 * max_nM + max_nQ) & 1));
-    for (int j0 = 0; j0 < nM; j0 += 4) {
-      const int pw = min(4, nM - j0);
-      if (warp == 0) {
-        float p[kMassRows][4];
-#pragma unroll
-        for (int m = 0; m < kMassRows; ++m) {
-          const int i = j0 + lane + 32 * m, ic = min(i, nM - 1);
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc)
-            p[m][cc] = (i < nM && cc < pw && j0 + cc <= i) ? L[lro(ic) + min(j0 + cc, ic)] : 0.0f;
-        }
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          if (cc < pw) {
-            // row j0 + cc is lane cc of the first register row
-            const float rd = rsqrtf(__shfl_sync(0xffffffffu, p[0][cc], cc));
-            if (lane == 0) rdiag[j0 + cc] = rd;
-#pragma unroll
-            for (int m = 0; m < kMassRows; ++m)
-              if (lane + 32 * m > cc) p[m][cc] *= rd;
-#pragma unroll
-            for (int c2 = cc + 1; c2 < 4; ++c2) {
-              const float l = __shfl_sync(0xffffffffu, p[0][cc], c2);
-#pragma unroll
-              for (int m = 0; m < kMassRows; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
-            }
-          }
-        }
-#pragma unroll
-        for (int m = 0; m < kMassRows; ++m) {
-          const int i = j0 + lane + 32 * m;
-          if (i < nM) {
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-              if (cc < pw && j0 + cc < i) L[lro(i) + j0 + cc] = p[m][cc];
-            if (i >= j0 + pw)
-              pan[i] = make_float4(p[m][0], pw > 1 ? p[m][1] : 0.0f, pw > 2 ? p[m][2] : 0.0f, pw > 3 ? p[m][3] : 0.0f);
-          }
-        }
+    if (fac_in) {
+      // a factor kept from a solve with (nearly) the same matrix: the
+      // refinement below corrects for the difference in FP64
+      const float* F = fac_in + c.slot_mmoff[s];
+      for (int u = tid; u < np; u += bd) L[u] = F[u];
+      for (int a = tid; a < nM; a += bd) {
+        sc[a] = F[np + a];
+        rdiag[a] = F[np + nM + a];
       }
       __syncthreads();
-      const int jt = j0 + pw;
-      for (int i = jt + warp; i < nM; i += 4 * nwarps) {
-        float4 lr[4];
-        int last = i;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          lr[g] = pan[min(i + g * nwarps, nM - 1)];
-          if (i + g * nwarps < nM) last = i + g * nwarps;
-        }
-        for (int k = jt + lane; k <= last; k += 32) {
-          const float4 ck = pan[k];
-          float v[4];
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int ig = i + g * nwarps;
-            v[g] = (ig < nM && k <= ig) ? L[lro(min(ig, nM - 1)) + k] : 0.0f;
-          }
-#pragma unroll
-          for (int g = 0; g < 4; ++g)
-            v[g] = fmaf(-lr[g].w, ck.w, fmaf(-lr[g].z, ck.z, fmaf(-lr[g].y, ck.y, fmaf(-lr[g].x, ck.x, v[g]))));
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int ig = i + g * nwarps;
-            if (ig < nM && k <= ig) L[lro(ig) + k] = v[g];
-          }
+    } else {
+      // pan lives in the transform buffer, idle until the first product, on
+      // a 16-byte boundary
+      mass_factor(c.mk32 + c.slot_mmoff[s], (float)t0, (float)t1, (float)t2, (float)t3, L, sc, rdiag,
+                  reinterpret_cast<float4*>(bufA + ((15 * max_nM + max_nQ) & 1)), nM);
+      if (fac_out) {
+        // kept for a later solve (the lifting of the stage): [L][s][rdiag]
+        float* F = fac_out + c.slot_mmoff[s];
+        for (int u = tid; u < np; u += bd) F[u] = L[u];
+        for (int a = tid; a < nM; a += bd) {
+          F[np + a] = sc[a];
+          F[np + nM + a] = rdiag[a];
         }
       }
-      __syncthreads();
     }
     // every block of five variables with the one factor (nblk > 1: the
     // lifting's three directions), from x0 (a nearby solution: one
@@ -3274,8 +3305,10 @@ void launch_permute(const Ctx& c, const double* src, double* dst, int64_t E, int
 
 cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
                                const double* x0, const double* tau, int weight, int max_nM, int max_nQ, int grid,
-                               cudaStream_t st, int nblk, int64_t blk_stride) {
+                               cudaStream_t st, int nblk, int64_t blk_stride, float* fac_out,
+                               const float* fac_in) {
   if (weight && nblk != 1) return cudaErrorInvalidValue;
+  if (weight && (fac_out || fac_in)) return cudaErrorInvalidValue;
   if (max_nM > 32 * kMassRows) return cudaErrorInvalidValue;
   size_t bytes = 0;
   if (max_nM > 0)
@@ -3285,7 +3318,8 @@ cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slot
     if (e != cudaSuccess) return e;
   }
   moving_mass_kernel<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, x0, tau[0], tau[1], tau[2],
-                                                         tau[3], weight, max_nM, max_nQ, nblk, blk_stride);
+                                                         tau[3], weight, max_nM, max_nQ, nblk, blk_stride, fac_out,
+                                                         fac_in);
   return cudaGetLastError();
 }
 

@@ -197,9 +197,13 @@ void launch_moving_geometry(const Ctx& c, double* cpool, double* fgeo, double* s
 // max_nM / max_nQ: the largest prism / pyramid mode and point counts among
 // the listed slots (0 if none: shared memory).  nblk (solves only): blocks of
 // five variables at the slot's storage offset + k blk_stride, all solved
-// with one factor of M^.
+// with one factor of M^.  fac_out (solves only, or null): keep each prism's
+// and pyramid's FP32 factor there, at its c.mk32 offset; fac_in (or null):
+// use the factor kept there instead of forming one (the FP64 refinement
+// corrects for a matrix that differs from M^ within the FP32 rounding).
 cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slots, const double* in, double* out,
                                const double* x0, const double* tau, int weight, int max_nM, int max_nQ, int grid,
-                               cudaStream_t st, int nblk = 1, int64_t blk_stride = 0);
+                               cudaStream_t st, int nblk = 1, int64_t blk_stride = 0, float* fac_out = nullptr,
+                               const float* fac_in = nullptr);
 
 }  // namespace dgk

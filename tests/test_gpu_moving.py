@@ -278,3 +278,10 @@ def test_moving_mesh_rejections(dg):
     static = dg.Mesh(box, 2, geometry="vertex")
     with pytest.raises(dg.DGError):
         dg._check(dg.load().dg_set_mesh_time(static.handle, 0.1))
+    # the stage-by-stage entry points of partitioned solves: a moving mesh
+    # steps through dg_rk_step only
+    lib, K = dg.load(), mesh.empty()
+    for call in (lambda: lib.dg_rk_prime(mesh.handle, dg._ptr(Q), dg._stream(None)),
+                 lambda: lib.dg_rk_stage(mesh.handle, dg._ptr(Q), dg._ptr(K), 1e-3, 0, 0, dg._stream(None)),
+                 lambda: lib.dg_rk_stage_lift(mesh.handle, dg._stream(None))):
+        assert call() == -7      # DG_ERR_UNSUPPORTED
