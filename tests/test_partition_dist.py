@@ -15,7 +15,12 @@ partitioned run would follow, checked without a GPU):
   * the in-memory redistribution of Listing 2: new per-type weights, a new
     plan, and every rank sends the states of the elements it no longer owns
     to their new owners (the all-to-all exchange); afterwards each rank holds
-    exactly its new elements, with their states unchanged.
+    exactly its new elements, with their states unchanged;
+  * Navier-Stokes (BR1) needs the two exchanges of the device path per
+    stage: the halo states, then -- after each rank has lifted the gradients
+    of its own elements -- the halo's lifted gradients; the residual of the
+    own elements then equals the single-domain one bit for bit, and a rank
+    holds no gradient it neither computed nor received.
 """
 import os
 import socket
@@ -136,6 +141,64 @@ def _worker(rank, ws, port, outdir):
     dist.destroy_process_group()
 
 
+def _ns_worker(rank, ws, port, outdir):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import dg_inputs as di
+    import paper_2511_08020_gb300 as dg
+    from oracle.mesh import from_box
+    from oracle.navier_stokes import NSOracle
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    box = di.box_mesh(3, "mixed", seed=3)
+    N = 2
+    o = NSOracle(from_box(box, N), mu=0.05)
+    m = o.mesh
+    Qg = o.project(lambda x: di.perturbed_tgv_state(x, seed=4, amp=0.05))
+    part, off, halo = dg.partition_plan(box, N, ws)
+    own = [int(e) for e in np.nonzero(part == rank)[0]]
+    need = {q: [int(e) for e in halo[off[q]:off[q + 1]]] for q in range(ws)}
+    # exchange 1: the halo states
+    Ql = np.full_like(Qg, np.nan)
+    for e in own:
+        Ql[m.dof_off[e]:m.dof_off[e + 1]] = Qg[m.dof_off[e]:m.dof_off[e + 1]]
+    mine = {q: [e for e in need[q] if part[e] == rank] for q in range(ws)}
+    theirs = {q: [e for e in need[rank] if part[e] == q] for q in range(ws)}
+    blk = lambda e: m.dof_off[e + 1] - m.dof_off[e]
+    got = _exchange(dist, rank, ws,
+                    {q: np.concatenate([Ql[m.dof_off[e]:m.dof_off[e + 1]] for e in mine[q]] or [np.zeros(0)])
+                     for q in range(ws)},
+                    {q: int(sum(blk(e) for e in theirs[q])) for q in range(ws)})
+    for q, arr in got.items():
+        pos = 0
+        for e in theirs[q]:
+            Ql[m.dof_off[e]:m.dof_off[e + 1]] = arr[pos:pos + blk(e)]
+            pos += blk(e)
+    # the own elements' lifted gradients (their faces reach only the halo)
+    G = o.lifted_gradient(Ql, own)
+    # exchange 2: the halo's lifted gradients, [3, 5, nM] per element
+    gsize = lambda e: 3 * blk(e)
+    got = _exchange(dist, rank, ws,
+                    {q: np.concatenate([G[e].ravel() for e in mine[q]] or [np.zeros(0)]) for q in range(ws)},
+                    {q: int(sum(gsize(e) for e in theirs[q])) for q in range(ws)})
+    for q, arr in got.items():
+        pos = 0
+        for e in theirs[q]:
+            G[e] = arr[pos:pos + gsize(e)].reshape(3, 5, -1)
+            pos += gsize(e)
+    # the residual of the own elements from the states and gradients held
+    faces = sorted({f for e in own for f, _ in m.elem_faces[e]})
+    fluxes = {f: o.ns_face_flux(Ql, f, G) for f in faces}
+    R = np.concatenate([o.apply_minv(e, o.ns_volume_term(Ql, e, G) - o.surface_term(Ql, e, fluxes)).ravel()
+                        for e in own])
+    np.save(os.path.join(outdir, f"nsR{rank}.npy"), R)
+    np.save(os.path.join(outdir, f"nsown{rank}.npy"), np.array(own))
+    np.save(os.path.join(outdir, f"nsheld{rank}.npy"), np.array(sorted(G)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 @pytest.mark.parametrize("ws", [2, 3])
 def test_partitioned_residual_and_redistribution(tmp_path, ws):
     sys.path.insert(0, ROOT)
@@ -164,6 +227,33 @@ def test_partitioned_residual_and_redistribution(tmp_path, ws):
     part, _, _ = dg.partition_plan(box, N, ws)
     part2, _, _ = dg.partition_plan(box, N, ws, type_weight=[1.0, 2.5, 1.7, 0.8])
     assert np.any(part != part2)                   # the new weights do move elements
+
+
+def test_partitioned_navier_stokes_two_exchanges(tmp_path):
+    sys.path.insert(0, ROOT)
+    import dg_inputs as di
+    import paper_2511_08020_gb300 as dg
+    from oracle.mesh import from_box
+    from oracle.navier_stokes import NSOracle
+    ws = 2
+    torch.multiprocessing.spawn(_ns_worker, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True)
+    box = di.box_mesh(3, "mixed", seed=3)
+    N = 2
+    o = NSOracle(from_box(box, N), mu=0.05)
+    m = o.mesh
+    Qg = o.project(lambda x: di.perturbed_tgv_state(x, seed=4, amp=0.05))
+    R = o.rhs(Qg)
+    part, off, halo = dg.partition_plan(box, N, ws)
+    seen = np.zeros(box.n_elems, dtype=int)
+    for r in range(ws):
+        own = np.load(tmp_path / f"nsown{r}.npy")
+        seen[own] += 1
+        ref = np.concatenate([R[m.dof_off[e]:m.dof_off[e + 1]] for e in own])
+        assert np.array_equal(np.load(tmp_path / f"nsR{r}.npy"), ref)
+        held = set(np.load(tmp_path / f"nsheld{r}.npy").tolist())
+        assert held == set(own.tolist()) | set(halo[off[r]:off[r + 1]].tolist())
+        assert len(halo[off[r]:off[r + 1]]) > 0
+    assert np.all(seen == 1)
 
 
 def test_partition_plan_properties():
