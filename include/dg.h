@@ -609,8 +609,9 @@ dg_status dg_set_profiling(dg_mesh* mesh, int on);
 dg_status dg_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream);
 /* Moving meshes, with profiling on: for the most recent dg_rk_step / dg_rhs
  * call, host [4]: total ms of the per-stage geometry kernels, total ms of the
- * stage mass-matrix kernels (products and solves), and their launch counts
- * (events around each; synchronises `stream`). */
+ * stage mass-matrix kernels (products and solves), the number of geometry
+ * launches and the number of mass calls (a product or a solve, one launch
+ * per element type each; events around each; synchronises `stream`). */
 dg_status dg_moving_phase_times(dg_mesh* mesh, double* out, cudaStream_t stream);
 
 /* Synchronise `stream` and report sticky device errors (DG_ERR_NONFINITE). */

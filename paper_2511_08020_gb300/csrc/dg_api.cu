@@ -452,6 +452,26 @@ struct dg_mesh {
     tau[2] = t * t;
     tau[3] = t * t * t;
   }
+  // Whether the stage values y_k lie within tol of t^k (relative to
+  // max(1, |t|)^k).  1e-6: a factor of M^ built from y_k can stand in for
+  // one of M(t) in the lifting solves (M^ - M(t) stays near the factor's
+  // FP32 rounding for mesh velocity gradients up to about 10, and two
+  // corrections from the previous stage's gradients still reach FP64
+  // rounding).  1e-14: the Ut a step leaves can be carried into the next
+  // step in place of M(t + dt) Q (the scheme integrates t^k exactly up to
+  // the accuracy of its published coefficients, about 1e-15 at the
+  // benchmark's dt but 1e-11 at dt = 0.05, t = 1).
+  static bool stage_values_near(const double y[4], double t, double tol) {
+    double tau[4];
+    powers(t, tau);
+    const double sc = std::max(1.0, std::fabs(t));
+    double s = 1.0;
+    for (int k = 1; k < 4; ++k) {
+      s *= sc;
+      if (!(std::fabs(y[k] - tau[k]) <= tol * s)) return false;
+    }
+    return true;
+  }
   // The face phase of a moving mesh at time ts.  Navier-Stokes: the lifting
   // values, then the volume phase in two halves around the lifting's
   // M(ts)^{-1} for prisms and pyramids (three solves of five variables, the
@@ -503,11 +523,12 @@ struct dg_mesh {
   // Stage s evaluates the residual at t_s = t + c_s dt on the geometry of
   // t_s, from the stage state M^_s^{-1} Ut with M^_s built from the stage
   // values y_k of t^k, which run through the same 2N-storage recursion
-  // (dy_k/dt = k t^(k-1)).  The product Ut = M(t) Q runs once per call: a
-  // fourth-order scheme integrates k t^(k-1) (degree <= 2) exactly, so the
-  // last stage's y_k are the powers of t + dt and the Ut it leaves is
-  // M(t + dt) Q_{n+1} up to the rounding of the end-of-step solve -- the
-  // next step's product would only reproduce it.
+  // (dy_k/dt = k t^(k-1)).  The product Ut = M(t) Q runs at the first step
+  // of a call and after any step whose y_k end away from the powers of
+  // t + dt: a fourth-order scheme integrates k t^(k-1) (degree <= 2)
+  // exactly, so otherwise the Ut a step leaves is M(t + dt) Q_{n+1} up to
+  // the rounding of the end-of-step solve -- the next step's product would
+  // only reproduce it.
   cudaError_t moving_rk(double* Q, double* K, double dt, int nsteps, cudaStream_t st) {
     static const double kLsC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363183857.0,
                                    2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
@@ -517,11 +538,12 @@ struct dg_mesh {
     G_warm = false;   // a caller may change the state between calls
     fac_ready = false;
     float* keep = ns ? d_fac : nullptr;
+    bool carry = false;   // d_Ut holds M(t) Q of the step about to start
     for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
       const double t = t_mesh;
       double y[4], Ky[4] = {0.0, 0.0, 0.0, 0.0};
       powers(t, y);
-      if (step == 0 && (e = moving_mass(Q, d_Ut, y, 1, st)) != cudaSuccess) return e;
+      if (!carry && (e = moving_mass(Q, d_Ut, y, 1, st)) != cudaSuccess) return e;
       for (int s = 0; s < 5; ++s) {
         const double ts = t + kLsC[s] * dt;
         moving_geometry(ts, st);
@@ -530,7 +552,7 @@ struct dg_mesh {
         // later stages start their solve from the previous stage's state
         if (s > 0) {
           if ((e = moving_mass(d_Ut, d_S, y, 0, st, s == 1 ? Q : d_S, false, 1, keep)) != cudaSuccess) return e;
-          fac_ready = keep != nullptr;
+          fac_ready = keep != nullptr && stage_values_near(y, ts, 1e-6);
         }
         dgk::StageArgs f{s > 0 ? d_S : Q, nullptr, nullptr, 0.0, 0.0, 0.0};
         element_phase(dgk::kFwd, f, st);
@@ -546,7 +568,8 @@ struct dg_mesh {
       // the step's end: y_k are the powers of t + dt, so its factor serves
       // the next step's first lifting as well
       if ((e = moving_mass(d_Ut, Q, y, 0, st, d_S, false, 1, keep)) != cudaSuccess) return e;
-      fac_ready = keep != nullptr;
+      fac_ready = keep != nullptr && stage_values_near(y, t + dt, 1e-6);
+      carry = stage_values_near(y, t + dt, 1e-14);
       t_mesh = t + dt;
     }
     return cudaGetLastError();
