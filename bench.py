@@ -342,15 +342,15 @@ class timed_window:
         return False
 
 
-def interleaved_repeats(configs, timed_fn, reps):
+def interleaved_repeats(arms, timed_fn, reps):
     """Scheduler comparison with a spread: `reps` rounds, in each of which
-    every configuration (name, set-up callable) is set up and timed once by
+    every arm (name, set-up callable) is set up and timed once by
     timed_fn() -> ms per step; the order rotates every round.  Returns per
     name the repeats' ms per step with their median and quartiles."""
-    times = {name: [] for name, _ in configs}
+    times = {name: [] for name, _ in arms}
     for r in range(reps):
-        k = r % len(configs)
-        for name, setup in configs[k:] + configs[:k]:
+        k = r % len(arms)
+        for name, setup in arms[k:] + arms[:k]:
             setup()
             times[name].append(timed_fn())
     out = {}
