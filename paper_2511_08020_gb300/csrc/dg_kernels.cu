@@ -2796,6 +2796,7 @@ __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __
 // transforms); L (packed lower triangle), s, rdiag [nM] (FP32).  Block: 5
 // warps.
 constexpr int kMassThreads = 160;
+static_assert(kMassThreads % 32 == 0 && kMassThreads >= 64, "the factor needs warp 0 and at least one other warp");
 constexpr int kMassRows = 4;   // rows per lane in the warp solves: nM <= 128
 
 // the FP32 factor is kept packed: row i of the lower triangle at i (i + 1) / 2
@@ -2888,7 +2889,65 @@ __device__ __forceinline__ void mass_correct(const float* L, const float* sc, co
 
 // The FP32 factor L L^T = S M^ S of one element (S = diag(M^)^{-1/2}), from
 // the four packed FP32 coefficient triangles Mk and the powers f of the
-// stage time; pan: four floats per row on a 16-byte boundary (scratch).
+// stage time; pan: two buffers of four floats per row on a 16-byte boundary
+// (scratch).
+// One warp: columns jh .. jh+3 of the FP32 factor (rows jh .. nM-1, by lane
+// in registers).  With prev (the previous panel's rows, four values each),
+// its rank-4 update of these columns comes first (the earlier panels' updates
+// are in L already).  Leaves the factored columns in L, their reciprocal
+// diagonal in rdiag and the rows below the panel in out.
+__device__ __forceinline__ void mass_panel(float* L, float* rdiag, float4* out, const float4* prev, int jh, int nM,
+                                           int lane) {
+  const int hw = min(4, nM - jh);
+  float p[kMassRows][4];
+#pragma unroll
+  for (int m = 0; m < kMassRows; ++m) {
+    const int i = jh + lane + 32 * m, ic = min(i, nM - 1);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+      p[m][cc] = (i < nM && cc < hw && jh + cc <= i) ? L[lro(ic) + min(jh + cc, ic)] : 0.0f;
+  }
+  if (prev) {
+#pragma unroll
+    for (int m = 0; m < kMassRows; ++m) {
+      const float4 a = prev[min(jh + lane + 32 * m, nM - 1)];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const float4 bb = prev[min(jh + cc, nM - 1)];
+        p[m][cc] = fmaf(-a.w, bb.w, fmaf(-a.z, bb.z, fmaf(-a.y, bb.y, fmaf(-a.x, bb.x, p[m][cc]))));
+      }
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) {
+    if (cc < hw) {
+      // row jh + cc is lane cc of the first register row
+      const float rd = rsqrtf(__shfl_sync(0xffffffffu, p[0][cc], cc));
+      if (lane == 0) rdiag[jh + cc] = rd;
+#pragma unroll
+      for (int m = 0; m < kMassRows; ++m)
+        if (lane + 32 * m > cc) p[m][cc] *= rd;
+#pragma unroll
+      for (int c2 = cc + 1; c2 < 4; ++c2) {
+        const float l = __shfl_sync(0xffffffffu, p[0][cc], c2);
+#pragma unroll
+        for (int m = 0; m < kMassRows; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kMassRows; ++m) {
+    const int i = jh + lane + 32 * m;
+    if (i < nM) {
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
+        if (cc < hw && jh + cc < i) L[lro(i) + jh + cc] = p[m][cc];
+      if (i >= jh + hw)
+        out[i] = make_float4(p[m][0], hw > 1 ? p[m][1] : 0.0f, hw > 2 ? p[m][2] : 0.0f, hw > 3 ? p[m][3] : 0.0f);
+    }
+  }
+}
+
 __device__ void mass_factor(const float* Mk, float f0, float f1, float f2, float f3, float* L, float* sc, float* rdiag,
                             float4* pan, int nM) {
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
@@ -2907,82 +2966,53 @@ __device__ void mass_factor(const float* Mk, float f0, float f1, float f2, float
     for (int k = lane; k <= a; k += 32) L[lro(a) + k] *= sa * sc[k];
   }
   __syncthreads();
-  // right-looking Cholesky in panels of four columns.  Warp 0 factors the
-  // panel in registers (rows by lane, one shuffle per pivot and per later
-  // panel column) and writes it back to L and, row by row, to pan; then the
-  // five warps apply the rank-4 update to the trailing lower triangle, four
-  // rows per warp at a time (independent chains that share each column's
-  // load).  Two barriers per panel.  L's diagonal is kept as its reciprocal
-  // in rdiag.
-  for (int j0 = 0; j0 < nM; j0 += 4) {
-    const int pw = min(4, nM - j0);
+  // right-looking Cholesky in panels of four columns with one panel of
+  // lookahead: while warps 1-4 apply the current panel's rank-4 update to the
+  // trailing lower triangle beyond the next panel (four rows per warp at a
+  // time, independent chains that share each column's load), warp 0 applies
+  // it to the next panel's four columns in registers and factors them.  One
+  // barrier per panel.  L's diagonal is kept as its reciprocal in rdiag.
+  float4* cur = pan;
+  float4* nxt = pan + nM;
+  if (warp == 0) mass_panel(L, rdiag, cur, nullptr, 0, nM, lane);
+  __syncthreads();
+  for (int j0 = 0; j0 + 4 < nM; j0 += 4) {
+    const int jt = j0 + 4;   // the next panel
     if (warp == 0) {
-      float p[kMassRows][4];
+      mass_panel(L, rdiag, nxt, cur, jt, nM, lane);
+    } else {
+      const int j4 = jt + 4, wt = warp - 1, nwt = nwarps - 1;
+      for (int i = j4 + wt; i < nM; i += 4 * nwt) {
+        float4 lr[4];
+        int last = i;
 #pragma unroll
-      for (int m = 0; m < kMassRows; ++m) {
-        const int i = j0 + lane + 32 * m, ic = min(i, nM - 1);
+        for (int g = 0; g < 4; ++g) {
+          lr[g] = cur[min(i + g * nwt, nM - 1)];
+          if (i + g * nwt < nM) last = i + g * nwt;
+        }
+        for (int k = j4 + lane; k <= last; k += 32) {
+          const float4 ck = cur[k];
+          float v[4];
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc)
-          p[m][cc] = (i < nM && cc < pw && j0 + cc <= i) ? L[lro(ic) + min(j0 + cc, ic)] : 0.0f;
-      }
+          for (int g = 0; g < 4; ++g) {
+            const int ig = i + g * nwt;
+            v[g] = (ig < nM && k <= ig) ? L[lro(min(ig, nM - 1)) + k] : 0.0f;
+          }
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        if (cc < pw) {
-          // row j0 + cc is lane cc of the first register row
-          const float rd = rsqrtf(__shfl_sync(0xffffffffu, p[0][cc], cc));
-          if (lane == 0) rdiag[j0 + cc] = rd;
+          for (int g = 0; g < 4; ++g)
+            v[g] = fmaf(-lr[g].w, ck.w, fmaf(-lr[g].z, ck.z, fmaf(-lr[g].y, ck.y, fmaf(-lr[g].x, ck.x, v[g]))));
 #pragma unroll
-          for (int m = 0; m < kMassRows; ++m)
-            if (lane + 32 * m > cc) p[m][cc] *= rd;
-#pragma unroll
-          for (int c2 = cc + 1; c2 < 4; ++c2) {
-            const float l = __shfl_sync(0xffffffffu, p[0][cc], c2);
-#pragma unroll
-            for (int m = 0; m < kMassRows; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
+          for (int g = 0; g < 4; ++g) {
+            const int ig = i + g * nwt;
+            if (ig < nM && k <= ig) L[lro(ig) + k] = v[g];
           }
         }
       }
-#pragma unroll
-      for (int m = 0; m < kMassRows; ++m) {
-        const int i = j0 + lane + 32 * m;
-        if (i < nM) {
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc)
-            if (cc < pw && j0 + cc < i) L[lro(i) + j0 + cc] = p[m][cc];
-          if (i >= j0 + pw)
-            pan[i] = make_float4(p[m][0], pw > 1 ? p[m][1] : 0.0f, pw > 2 ? p[m][2] : 0.0f, pw > 3 ? p[m][3] : 0.0f);
-        }
-      }
     }
     __syncthreads();
-    const int jt = j0 + pw;
-    for (int i = jt + warp; i < nM; i += 4 * nwarps) {
-      float4 lr[4];
-      int last = i;
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        lr[g] = pan[min(i + g * nwarps, nM - 1)];
-        if (i + g * nwarps < nM) last = i + g * nwarps;
-      }
-      for (int k = jt + lane; k <= last; k += 32) {
-        const float4 ck = pan[k];
-        float v[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const int ig = i + g * nwarps;
-          v[g] = (ig < nM && k <= ig) ? L[lro(min(ig, nM - 1)) + k] : 0.0f;
-        }
-#pragma unroll
-        for (int g = 0; g < 4; ++g)
-          v[g] = fmaf(-lr[g].w, ck.w, fmaf(-lr[g].z, ck.z, fmaf(-lr[g].y, ck.y, fmaf(-lr[g].x, ck.x, v[g]))));
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const int ig = i + g * nwarps;
-          if (ig < nM && k <= ig) L[lro(ig) + k] = v[g];
-        }
-      }
-    }
-    __syncthreads();
+    float4* t = cur;
+    cur = nxt;
+    nxt = t;
   }
 }
 
