@@ -2790,11 +2790,13 @@ __global__ void permute_kernel(Ctx c, const double* __restrict__ src, double* __
 // nearby state x0 instead (the previous stage's, about 1e-3 away), two
 // corrections reach the same.  FP64 work per solve is two products, against
 // nM^3 / 3 FP64 flops for an FP64 Cholesky (FP64 issues at 1/64 of the FP32
-// rate on this part).
+// rate on this part).  A solve may keep its factor in global memory, and a
+// later solve with a matrix equal to M^ within the FP32 rounding may use it
+// instead of forming its own (the refinement runs with its own M^).
 //
 // smem: x, b, r [5][nM] and wJ [nQ] (FP64); bufA, bufB [5][nQ] (FP64,
-// transforms); L (packed lower triangle), s, rdiag [nM] (FP32).  Block: 5
-// warps.
+// transforms; during the factor, bufA holds its two panel buffers); L
+// (packed lower triangle), s, rdiag [nM] (FP32).  Block: 5 warps.
 constexpr int kMassThreads = 160;
 static_assert(kMassThreads % 32 == 0 && kMassThreads >= 64, "the factor needs warp 0 and at least one other warp");
 constexpr int kMassRows = 4;   // rows per lane in the warp solves: nM <= 128
