@@ -214,13 +214,19 @@ def test_moving_navier_stokes_steps_and_free_stream(dg):
     mesh = dg.MovingMesh(box, N, vel)
     mesh.set_physics("navier_stokes", mu, 0.72)
     Q = tgv(mo)
-    Qs = mesh.set_state(torch.from_numpy(Q).cuda())
-    mesh.rk_step(Qs, mesh.empty(), dt, 2)
-    Qg = mesh.get_state(Qs)
-    ref = mo.run(Q, 0.0, dt, 2)
     vidx = var_index(mo.mesh.nM)
-    assert rel_err(Qg - Q, ref - Q, vidx) < 1e-10
-    assert rel_err(Qg, ref, vidx) < TOL
+    # dt = 1e-3: the lifting solves use the stage solves' factors and M Q is
+    # carried between the steps; dt = 1e-2: the stage values miss the powers
+    # of the stage times by more than the library allows, so every lifting
+    # forms its own factor and every step its own M Q
+    for dt in (dt, 1e-2):
+        mesh.set_time(0.0)
+        Qs = mesh.set_state(torch.from_numpy(Q).cuda())
+        mesh.rk_step(Qs, mesh.empty(), dt, 2)
+        Qg = mesh.get_state(Qs)
+        ref = mo.run(Q, 0.0, dt, 2)
+        assert rel_err(Qg - Q, ref - Q, vidx) < 1e-10
+        assert rel_err(Qg, ref, vidx) < TOL
     mesh.set_time(0.0)
     Qc = mo.project(lambda x: np.repeat(CONST[:, None], len(x), axis=1), 0.0)
     Qcs = mesh.set_state(torch.from_numpy(Qc).cuda())

@@ -70,6 +70,46 @@ def test_stage_time_jacobian_drifts():
     assert drift > 1e-8, drift
 
 
+def _stage_values_of_powers(t, dt):
+    """The 2N-storage recursion of the scheme on dy_k/dt = k t^(k-1),
+    y_k(t) = t^k: the largest deviation of the stage values from t_s^k and
+    of the end values from (t + dt)^k, each relative to max(1, |t|)^k."""
+    y = np.array([1.0, t, t * t, t ** 3])
+    K = np.zeros(4)
+    worst = 0.0
+    for s in range(5):
+        ts = t + LSERK_C[s] * dt
+        sc = max(1.0, abs(ts)) ** np.arange(4)
+        if s > 0:
+            worst = max(worst, np.max(np.abs(y - ts ** np.arange(4)) / sc))
+        K = LSERK_A[s] * K + dt * np.array([0.0, 1.0, 2.0 * ts, 3.0 * ts * ts])
+        y = y + LSERK_B[s] * K
+    te = t + dt
+    end = np.max(np.abs(y - te ** np.arange(4)) / max(1.0, abs(te)) ** np.arange(4))
+    return worst, end
+
+
+@pytest.mark.parametrize("t", [0.0, 0.01, 2.5])
+def test_stage_values_of_the_powers_of_t(t):
+    """The scheme is fourth order, so its step integrates the cubic
+    polynomials t^k exactly up to the accuracy of its published coefficient
+    rationals (the end values are the powers of t + dt to about 1e-15 at
+    dt <= 1e-3); its internal stages are low order, so the stage values miss
+    t_s^k by O(dt^2).  A step may therefore carry M Q into the next step,
+    and a stage's factor may stand in for one of M(t_s), only at small dt --
+    the library checks both per step (1e-14 and 1e-6)."""
+    for dt in (6.6e-4, 1e-3):
+        worst, end = _stage_values_of_powers(t, dt)
+        assert end < 1e-14, (dt, end)
+        assert 1e-10 < worst < 1e-6, (dt, worst)
+    worst, end = _stage_values_of_powers(t, 0.01)
+    assert worst > 1e-6 and end > 1e-14
+    # the stage deviation shrinks like dt^2
+    w1, _ = _stage_values_of_powers(t, 1e-3)
+    w2, _ = _stage_values_of_powers(t, 5e-4)
+    assert 3.5 < w1 / w2 < 4.5
+
+
 def test_conservation_in_motion():
     mo, _ = moving("mixed", 2, 2)
     Q = mo.project(lambda x: di.perturbed_tgv_state(x, seed=3, amp=0.1), 0.0)
