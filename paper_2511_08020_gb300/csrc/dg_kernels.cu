@@ -2881,14 +2881,6 @@ __device__ void mass_correct_t(const float* L, const float* sc, const float* rdi
   __syncthreads();
 }
 
-__device__ __forceinline__ void mass_correct(const float* L, const float* sc, const float* rdiag, const double* r,
-                                             double* x, int nM) {
-  if (nM <= 32) mass_correct_t<1>(L, sc, rdiag, r, x, nM);
-  else if (nM <= 64) mass_correct_t<2>(L, sc, rdiag, r, x, nM);
-  else if (nM <= 96) mass_correct_t<3>(L, sc, rdiag, r, x, nM);
-  else mass_correct_t<4>(L, sc, rdiag, r, x, nM);
-}
-
 // The FP32 factor L L^T = S M^ S of one element (S = diag(M^)^{-1/2}), from
 // the four packed FP32 coefficient triangles Mk and the powers f of the
 // stage time; pan: two buffers of four floats per row on a 16-byte boundary
@@ -2898,12 +2890,13 @@ __device__ __forceinline__ void mass_correct(const float* L, const float* sc, co
 // its rank-4 update of these columns comes first (the earlier panels' updates
 // are in L already).  Leaves the factored columns in L, their reciprocal
 // diagonal in rdiag and the rows below the panel in out.
+template <int ROWS>
 __device__ __forceinline__ void mass_panel(float* L, float* rdiag, float4* out, const float4* prev, int jh, int nM,
                                            int lane) {
   const int hw = min(4, nM - jh);
-  float p[kMassRows][4];
+  float p[ROWS][4];
 #pragma unroll
-  for (int m = 0; m < kMassRows; ++m) {
+  for (int m = 0; m < ROWS; ++m) {
     const int i = jh + lane + 32 * m, ic = min(i, nM - 1);
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc)
@@ -2911,7 +2904,7 @@ __device__ __forceinline__ void mass_panel(float* L, float* rdiag, float4* out, 
   }
   if (prev) {
 #pragma unroll
-    for (int m = 0; m < kMassRows; ++m) {
+    for (int m = 0; m < ROWS; ++m) {
       const float4 a = prev[min(jh + lane + 32 * m, nM - 1)];
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
@@ -2927,18 +2920,18 @@ __device__ __forceinline__ void mass_panel(float* L, float* rdiag, float4* out, 
       const float rd = rsqrtf(__shfl_sync(0xffffffffu, p[0][cc], cc));
       if (lane == 0) rdiag[jh + cc] = rd;
 #pragma unroll
-      for (int m = 0; m < kMassRows; ++m)
+      for (int m = 0; m < ROWS; ++m)
         if (lane + 32 * m > cc) p[m][cc] *= rd;
 #pragma unroll
       for (int c2 = cc + 1; c2 < 4; ++c2) {
         const float l = __shfl_sync(0xffffffffu, p[0][cc], c2);
 #pragma unroll
-        for (int m = 0; m < kMassRows; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
+        for (int m = 0; m < ROWS; ++m) p[m][c2] = fmaf(-p[m][cc], l, p[m][c2]);
       }
     }
   }
 #pragma unroll
-  for (int m = 0; m < kMassRows; ++m) {
+  for (int m = 0; m < ROWS; ++m) {
     const int i = jh + lane + 32 * m;
     if (i < nM) {
 #pragma unroll
@@ -2950,6 +2943,7 @@ __device__ __forceinline__ void mass_panel(float* L, float* rdiag, float4* out, 
   }
 }
 
+template <int ROWS>
 __device__ void mass_factor(const float* Mk, float f0, float f1, float f2, float f3, float* L, float* sc, float* rdiag,
                             float4* pan, int nM) {
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
@@ -2976,12 +2970,12 @@ __device__ void mass_factor(const float* Mk, float f0, float f1, float f2, float
   // barrier per panel.  L's diagonal is kept as its reciprocal in rdiag.
   float4* cur = pan;
   float4* nxt = pan + nM;
-  if (warp == 0) mass_panel(L, rdiag, cur, nullptr, 0, nM, lane);
+  if (warp == 0) mass_panel<ROWS>(L, rdiag, cur, nullptr, 0, nM, lane);
   __syncthreads();
   for (int j0 = 0; j0 + 4 < nM; j0 += 4) {
     const int jt = j0 + 4;   // the next panel
     if (warp == 0) {
-      mass_panel(L, rdiag, nxt, cur, jt, nM, lane);
+      mass_panel<ROWS>(L, rdiag, nxt, cur, jt, nM, lane);
     } else {
       const int j4 = jt + 4, wt = warp - 1, nwt = nwarps - 1;
       for (int i = j4 + wt; i < nM; i += 4 * nwt) {
@@ -3018,7 +3012,8 @@ __device__ void mass_factor(const float* Mk, float f0, float f1, float f2, float
   }
 }
 
-__global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
+template <int ROWS, int MINB>
+__global__ void __launch_bounds__(kMassThreads, MINB) moving_mass_kernel(Ctx c, const int64_t* list, int64_t E,
                                                                    const double* in, double* out, const double* x0,
                                                                    double t0, double t1, double t2, double t3,
                                                                    int weight, int max_nM, int max_nQ, int nblk,
@@ -3076,7 +3071,7 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
     } else {
       // pan lives in the transform buffer, idle until the first product, on
       // a 16-byte boundary
-      mass_factor(c.mk32 + c.slot_mmoff[s], (float)t0, (float)t1, (float)t2, (float)t3, L, sc, rdiag,
+      mass_factor<ROWS>(c.mk32 + c.slot_mmoff[s], (float)t0, (float)t1, (float)t2, (float)t3, L, sc, rdiag,
                   reinterpret_cast<float4*>(bufA + ((15 * max_nM + max_nQ) & 1)), nM);
       if (fac_out) {
         // kept for a later solve (the lifting of the stage): [L][s][rdiag]
@@ -3105,7 +3100,7 @@ __global__ void __launch_bounds__(kMassThreads, 7) moving_mass_kernel(Ctx c, con
       if (x0) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
       const int ncorr = x0 ? 2 : 3;
       for (int it = 0; it < ncorr; ++it) {
-        mass_correct(L, sc, rdiag, r, x, nM);
+        mass_correct_t<ROWS>(L, sc, rdiag, r, x, nM);
         if (it + 1 < ncorr) mass_product(c, T, x, wJ, b, r, bufA, bufB, tid);
       }
       for (int w = tid; w < 5 * nM; w += bd) out[o + w] = x[w];
@@ -3345,13 +3340,22 @@ cudaError_t launch_moving_mass(const Ctx& c, const int64_t* list, int64_t n_slot
   size_t bytes = 0;
   if (max_nM > 0)
     bytes = sizeof(double) * mass_smem_doubles(max_nM, max_nQ) + sizeof(float) * ((size_t)lro(max_nM) + 2 * (size_t)max_nM);
-  if (bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(moving_mass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-  }
-  moving_mass_kernel<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, x0, tau[0], tau[1], tau[2],
-                                                         tau[3], weight, max_nM, max_nQ, nblk, blk_stride, fac_out,
-                                                         fac_in);
+  // rows per lane in the warp solves and the panel (nM <= 32 ROWS); with two
+  // (pyramids and prisms up to N = 3) eight blocks fit an SM's registers
+  auto launch = [&](auto kern) -> cudaError_t {
+    if (bytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kMassThreads, bytes, st>>>(c, list, n_slots, in, out, x0, tau[0], tau[1], tau[2], tau[3], weight,
+                                             max_nM, max_nQ, nblk, blk_stride, fac_out, fac_in);
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (max_nM <= 64) e = launch(moving_mass_kernel<2, 8>);
+  else if (max_nM <= 96) e = launch(moving_mass_kernel<3, 7>);
+  else e = launch(moving_mass_kernel<4, 7>);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
