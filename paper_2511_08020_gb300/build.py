@@ -1,6 +1,6 @@
 """Build libdg.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-The three translation units compile in parallel and link into
+The four translation units compile in parallel and link into
 paper_2511_08020_gb300/_lib/libdg.so.  The FP64 throughput probes of the
 benchmark (fp64_probe.cu) link into a library of their own,
 _lib/libfp64probe.so, so that libdg.so carries only the hot path.  Nothing is
