@@ -180,10 +180,12 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
  * (dg_mesh_geometry does not count them).  The residual is the moving-frame
  * weak form: fluxes F(q) - q xdot in the volume and the LF flux in the frame
  * of the face's normal mesh speed on the faces.  dg_rk_step evolves the
- * mass-weighted state M Q: each stage solves M^ Q_s = (M Q)_s by Cholesky
- * with M^ built from the LSERK stage values of t^k, so that a constant state
- * stays constant (a discrete geometric conservation law), and advances the
- * mesh time by nsteps dt; Q_store holds Q at the mesh time before and after.
+ * mass-weighted state M Q: each stage solves M^ Q_s = (M Q)_s with M^ built
+ * from the LSERK stage values of t^k, so that a constant state stays
+ * constant (a discrete geometric conservation law), and advances the mesh
+ * time by nsteps dt; Q_store holds Q at the mesh time before and after.  The
+ * solves reach the exact Cholesky solve to FP64 rounding (FP64 iterative
+ * refinement around an FP32 Cholesky factor).
  * dg_rhs returns M(t)^{-1} (vol - surf) at the mesh time; dg_project and
  * dg_load_vector use the geometry of the mesh time (dg_quad_points returns
  * the points at t = 0).  Navier-Stokes (dg_set_physics) runs the BR1 lifting
