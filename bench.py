@@ -226,6 +226,11 @@ NCU_TRAFFIC_FUSED_LAUNCH = (154.316032 + 144.723456) * 1e6
 # pipe's busy fraction (the same rule: None once the kernel changes)
 NCU_FP64_FUSED_LAUNCH = {"executed_tflops": (2 * 215.843480 + 31.503288 + 1.640137) * 2.073804e9 / 1e12,
                          "fp64_pipe_busy": 0.92798396}
+# dram__bytes_read.sum + dram__bytes_write.sum of one stage solve of the
+# moving leg (its launches for hexahedra, prisms and pyramids), from the
+# committed ncu capture of the mass kernel on the 16^3 N = 4 mesh in motion;
+# None whenever the mass kernel changes until it is captured again.
+NCU_TRAFFIC_MASS_SOLVE = (10.084608 + (210.038528 + 16.756480) + (233.019648 + 95.310336)) * 1e6
 
 
 def fp64_probes():
@@ -1283,7 +1288,9 @@ def moving_leg(dg, dev, stream, args, barrier, max_over_ranks, ws, curved_value)
     out["roofline"] = {"bound": "alu", "kernel": "stage mass kernels (FP64 products, FP32-preconditioned solves)",
                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                        "flops_per_step": fl_step, "mass_calls_per_step": n_mass / steps,
-                       "products_per_step": products,
+                       "products_per_step": products, "traffic_per_solve": NCU_TRAFFIC_MASS_SOLVE,
+                       "traffic_source": "ncu dram read+write of one stage solve (three launches, one per "
+                                         "element type; 16^3 N = 4 mesh in motion)",
                        "peak_kind": "derived FP64: SMs x 2 DFMA/clk x 2 flop x max SM clock"}
     return out
 
